@@ -1,0 +1,178 @@
+/*
+ * cdsigma -- Cholesky-factorised second-order electron propagator on one GPU.
+ *
+ * C ABI of the GPU library (libcdsigma.so, sm_103a).  Every call takes plain
+ * pointers and sizes; "device" arrays live in GPU memory owned by the caller,
+ * "host" arrays in host memory owned by the caller.  The library never frees
+ * or keeps caller memory.  Where a call needs scratch memory the caller passes
+ * a device workspace whose size the matching *_workspace_bytes() reports.
+ *
+ * Errors: every call returns a cds_status (0 = success).  Argument errors are
+ * detected before any launch and leave outputs untouched.  CUDA launch errors
+ * return CDS_ERR_CUDA.  Nothing is signalled by exceptions, traps or device
+ * asserts; device-side failures are written to status words the caller reads.
+ *
+ * Streams: calls enqueue work on the given stream.  Calls documented as
+ * "blocking" synchronise that stream before returning because their control
+ * flow depends on device results (the Cholesky rank, Newton convergence).
+ *
+ * Conventions shared by all calls
+ *  - Basis: N normalised s-type Gaussians; xyz[N][3] (bohr), alpha[N],
+ *    atom[N] (centre index of each function).
+ *  - Product densities I = (mu, nu), mu <= nu (paper Sec. II.A), packed as
+ *    I = nu*(nu+1)/2 + mu; npair = N*(N+1)/2.
+ *  - Cholesky vectors L[K][I], K = 0..M-1, row-major (vector-major).
+ *  - MO coefficients C[N][nmo] row-major, column p = MO p; eps[nmo] ascending,
+ *    the first nocc orbitals occupied.
+ *  - MO factors (paper Eq. transformation): Lov[i][a][K] = B^K_{i,nocc+a}
+ *    and Lp[t][r][K] = B^K_{orb[t], r}; K is the innermost (contiguous) index.
+ */
+#ifndef CDSIGMA_H
+#define CDSIGMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CDS_OK = 0,
+    CDS_ERR_ARG = 1,            /* invalid argument (size, null pointer, range) */
+    CDS_ERR_CUDA = 2,           /* a CUDA runtime call or launch failed */
+    CDS_ERR_NOT_PD = 3,         /* residual diagonal below -1e-10 * max initial diagonal */
+    CDS_ERR_RANK_CAP = 4,       /* more than max_rank Cholesky vectors needed */
+    CDS_ERR_NO_CONVERGENCE = 5, /* a Newton solve did not converge in max_iter */
+    CDS_ERR_WORKSPACE = 6,      /* workspace smaller than *_workspace_bytes() */
+    CDS_ERR_UNSUPPORTED = 7,    /* device or precision mode not supported */
+    CDS_ERR_TIMEOUT = 8         /* a bounded device-side wait gave up */
+} cds_status;
+
+typedef enum { CDS_SCHEME_FULL = 0, CDS_SCHEME_ATOMIC = 1 } cds_scheme;
+
+/* Arithmetic of the J-contractions in sigma2 / qp_solve.
+ * FP64: binary64 throughout.
+ * BF16X3: each factor split x = hi + lo (both bf16), products hi*hi + hi*lo +
+ *   lo*hi on tensor cores with fp32 accumulation; denominators and the
+ *   per-tile reductions in fp32, cross-tile sums and the Newton step in fp64. */
+typedef enum { CDS_PREC_FP64 = 0, CDS_PREC_BF16X3 = 2 } cds_precision;
+
+/* Newton status per orbital (paper Eq. NR). */
+enum { CDS_QP_OK = 0, CDS_QP_NO_CONVERGENCE = 1, CDS_QP_NONFINITE = 2 };
+
+/* Library version (major*10000 + minor*100 + patch). */
+int cds_version(void);
+
+/* Static description of a status code; never NULL. */
+const char* cds_errstr(int status);
+
+/* ------------------------------------------------------------------------
+ * Electron-repulsion integrals over s-type Gaussians (paper Sec. II.A,
+ * Eq. integral):  (rho_I|rho_J) = 2 pi^(5/2)/(p q sqrt(p+q)) K_I K_J F0(T).
+ * ---------------------------------------------------------------------- */
+
+/* D[I] = (rho_I|rho_I) for all npair pairs.
+ * xyz, alpha: device, as above.  D: device [npair] fp64 output. */
+int cds_eri_diag(int32_t nbf, const double* xyz, const double* alpha, double* D,
+                 cudaStream_t stream);
+
+/* cols[c][I] = (rho_I|rho_{piv[c]}) for c < ncol and all I.
+ * piv: device [ncol] int32 packed indices in [0, npair).  cols: device
+ * [ncol][npair] fp64 output.  Out-of-range pivots return CDS_ERR_ARG only when
+ * detectable on the host (ncol < 0); the kernel writes NaN columns for
+ * out-of-range device indices. */
+int cds_eri_columns(int32_t nbf, const double* xyz, const double* alpha,
+                    const int32_t* piv, int32_t ncol, double* cols, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Threshold-delta diagonal-pivoted incomplete Cholesky decomposition of the
+ * ERI supermatrix (paper Sec. II.A, Eq. gs_coulomb, Eq. CD, Eq. stricterr),
+ * ERI columns generated on the fly.
+ *   pivot: largest residual diagonal D_I over the candidate set; candidates
+ *          within 1e-12 * max(initial D) of it (and above delta_eff) are tied
+ *          and the lowest packed index wins;
+ *   stop:  when every candidate residual is <= delta_eff,
+ *          delta_eff = max(delta, npair * 2^-52 * max(initial D));
+ *   the chosen pair's residual is then set to exactly 0;
+ *   scheme FULL: all pairs are candidates; ATOMIC: only pairs with
+ *          atom[mu] == atom[nu] (atomic-CD pivot restriction, paper Sec. II.A).
+ * ---------------------------------------------------------------------- */
+
+/* Workspace needed by cds_cd_decompose for a basis of nbf functions. */
+size_t cds_cd_workspace_bytes(int32_t nbf);
+
+/* Blocking.  Inputs (device): xyz, alpha, atom.  Outputs (device, caller-owned):
+ *   L     [max_rank][npair] fp64, rows 0..M-1 written;
+ *   piv   [max_rank] int32 packed pivot index of each vector;
+ *   D     [npair] fp64 residual diagonal after the last step (the error
+ *         diagonal D_II of Eq. error_approx).
+ * Outputs (host): *M_out = number of vectors, *delta_eff_out (may be NULL).
+ * Returns CDS_ERR_RANK_CAP if max_rank vectors did not reach delta (L, piv
+ * then hold the first max_rank vectors and *M_out = max_rank), CDS_ERR_NOT_PD
+ * on a negative residual beyond roundoff. */
+int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
+                     const int32_t* atom, double delta, int32_t scheme, int32_t max_rank,
+                     double* L, int32_t* piv, double* D, int32_t* M_out,
+                     double* delta_eff_out, void* workspace, size_t workspace_bytes,
+                     cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * AO -> MO transform of the Cholesky vectors (paper Eq. transformation):
+ *   B^K_pq = sum_{mu,nu} C_{mu p} L^K_{mu nu} C_{nu q},  fp64.
+ * ---------------------------------------------------------------------- */
+
+size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, int32_t np);
+
+/* Asynchronous.  L: device [M][npair]; C: device [nbf][nmo]; orb: device [np]
+ * int32 MO indices in [0, nmo).  Outputs (device): Lov [nocc][nmo-nocc][M],
+ * Lp [np][nmo][M] (Lp may be NULL when np == 0). */
+int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
+              const double* C, const int32_t* orb, int32_t np, double* Lov, double* Lp,
+              void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Diagonal second-order self-energy (paper Eq. SE) and its energy derivative
+ * for np orbitals orb[t] at nE energies each:
+ *   sigma[t][e]  = Sigma_qq(E[t][e]),  dsigma[t][e] = dSigma_qq/dE (analytic),
+ * MO integrals recomputed tile by tile from the factors and never stored.
+ * Inputs are the outputs of cds_cd_to_mo plus eps (device [nmo]).
+ * ---------------------------------------------------------------------- */
+
+size_t cds_sigma2_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np,
+                                  int32_t nE, int32_t precision);
+
+/* Asynchronous.  Lp holds the factor rows of the np orbitals (Sigma_qq
+ * depends on q only through them); E: device [np][nE]; sigma, dsigma: device
+ * [np][nE] outputs (dsigma may be NULL).  precision: cds_precision.
+ * 1 <= nE <= 4096, np <= 65535. */
+int cds_sigma2_diag(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                    const double* Lp, int32_t np, const double* eps, const double* E,
+                    int32_t nE, int32_t precision, double* sigma, double* dsigma,
+                    void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Newton quasiparticle solve (paper Eq. qpapp, Eq. iter, Eq. ps, Eq. NR):
+ *   w <- w + (eps_q + Sigma(w) - w) P,  P = 1/(1 - dSigma/dw),  w0 = eps_q,
+ *   stop at |dw| <= conv.  Each iteration recomputes Sigma from the factors.
+ * ---------------------------------------------------------------------- */
+
+size_t cds_qp_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np,
+                              int32_t precision);
+
+/* Blocking.  Outputs (device, [np]): omega (final iterate), pole (pole
+ * strength of the last step), iters (Sigma evaluations), status (CDS_QP_*).
+ * Returns CDS_ERR_NO_CONVERGENCE if any orbital did not converge (all outputs
+ * are still written). */
+int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                 const double* Lp, const int32_t* orb, int32_t np, const double* eps,
+                 double conv, int32_t max_iter, int32_t precision, double* omega,
+                 double* pole, int32_t* iters, int32_t* status, void* workspace,
+                 size_t workspace_bytes, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CDSIGMA_H */

@@ -1,0 +1,193 @@
+// AO -> MO transform of the Cholesky vectors (paper Eq. transformation),
+// binary64:  B^K = C^T A^K C  with A^K the symmetric unpacked L^K.
+//
+// Per batch of kb vectors: unpack A^K (N x N), then two strided-batched FP64
+// GEMMs per output block,  T = C_occ^T A^K  (o x N)  and  Bov = T C_vir
+// (o x v), and the same for the requested orbital rows with C_P.  The second
+// GEMM writes straight into the K-innermost layouts Lov[i][a][K], Lp[t][r][K].
+// On this part FP64 issue rate, not HBM, bounds the transform.
+#include "common.cuh"
+
+namespace cds {
+
+constexpr int kGB = 64;   // output tile (rows and cols)
+constexpr int kGK = 16;   // depth of a shared-memory stage
+constexpr int kAoBatch = 32;
+
+struct StridedMat {
+    const double* p;
+    int64_t rs, cs, bs;   // element strides: row, column, batch
+};
+struct StridedOut {
+    double* p;
+    int64_t rs, cs, bs;
+};
+
+// C[b] (m x n) = A[b] (m x k) * B[b] (k x n), all operands by strides.
+// A_M_CONTIG: A's unit stride is along m; B_N_CONTIG: B's unit stride is along n.
+template <bool A_M_CONTIG, bool B_N_CONTIG>
+__global__ void __launch_bounds__(256)
+k_dgemm(int m, int n, int k, StridedMat A, StridedMat B, StridedOut C) {
+    __shared__ double As[kGK][kGB + 1];
+    __shared__ double Bs[kGK][kGB + 1];
+    const int tid = threadIdx.x;
+    const int tr = tid / 16, tc = tid % 16;
+    const int m0 = blockIdx.y * kGB, n0 = blockIdx.x * kGB;
+    const int64_t b = blockIdx.z;
+    const double* Ab = A.p + b * A.bs;
+    const double* Bb = B.p + b * B.bs;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < k; k0 += kGK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int idx = tid + 256 * r;
+            int mm, kk;
+            if (A_M_CONTIG) { mm = idx % kGB; kk = idx / kGB; }
+            else { kk = idx % kGK; mm = idx / kGK; }
+            int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < m && gk < k) ? Ab[gm * A.rs + gk * A.cs] : 0.0;
+            int nn;
+            if (B_N_CONTIG) { nn = idx % kGB; kk = idx / kGB; }
+            else { kk = idx % kGK; nn = idx / kGK; }
+            int gn = n0 + nn;
+            gk = k0 + kk;
+            Bs[kk][nn] = (gn < n && gk < k) ? Bb[gk * B.rs + gn * B.cs] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kGK; ++kk) {
+            double a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tr + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tc + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], bb[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double* Cb = C.p + b * C.bs;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gm = m0 + tr + 16 * i;
+        if (gm >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gn = n0 + tc + 16 * j;
+            if (gn < n) Cb[gm * C.rs + gn * C.cs] = acc[i][j];
+        }
+    }
+}
+
+// U[b][mu][nu] = L[K0+b][pair(mu,nu)]
+__global__ void k_unpack(const double* __restrict__ L, int64_t npair, int32_t K0, int32_t kb,
+                         int32_t N, double* __restrict__ U) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t per = (int64_t)N * N;
+    if (e >= per * kb) return;
+    int b = (int)(e / per);
+    int64_t r = e - b * per;
+    int mu = (int)(r / N), nu = (int)(r - (int64_t)mu * N);
+    int lo = min(mu, nu), hi = max(mu, nu);
+    U[e] = L[(int64_t)(K0 + b) * npair + (int64_t)hi * (hi + 1) / 2 + lo];
+}
+
+// Cp[mu][t] = C[mu][orb[t]]
+__global__ void k_gather_cols(const double* __restrict__ C, int32_t N, int32_t nmo,
+                              const int32_t* __restrict__ orb, int32_t np, double* __restrict__ Cp) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * np) return;
+    int mu = e / np, t = e % np;
+    int p = orb[t];
+    Cp[e] = (p >= 0 && p < nmo) ? C[(int64_t)mu * nmo + p] : __longlong_as_double(0x7ff8000000000000LL);
+}
+
+template <bool AM, bool BN>
+static int launch_dgemm(int m, int n, int k, int batch, StridedMat A, StridedMat B, StridedOut C,
+                        cudaStream_t s) {
+    if (m <= 0 || n <= 0 || batch <= 0) return CDS_OK;
+    dim3 grid((n + kGB - 1) / kGB, (m + kGB - 1) / kGB, batch);
+    k_dgemm<AM, BN><<<grid, 256, 0, s>>>(m, n, k, A, B, C);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
+struct AoLayout {
+    double* U;    // [kb][N][N]
+    double* T;    // [kb][max(o, np)][N]
+    double* Cp;   // [N][np]
+    size_t bytes;
+};
+
+static AoLayout ao_layout(void* ws, int32_t nbf, int32_t nocc, int32_t np) {
+    Carver c(ws);
+    AoLayout l;
+    l.U = c.take<double>((size_t)kAoBatch * nbf * nbf);
+    l.T = c.take<double>((size_t)kAoBatch * std::max(nocc, np) * nbf);
+    l.Cp = c.take<double>((size_t)nbf * std::max(np, 1));
+    l.bytes = c.off;
+    return l;
+}
+
+}  // namespace cds
+
+using namespace cds;
+
+extern "C" size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M,
+                                            int32_t np) {
+    (void)nmo; (void)M;
+    if (nbf <= 0 || nocc < 0 || np < 0) return 0;
+    return ao_layout(nullptr, nbf, nocc, np).bytes;
+}
+
+extern "C" int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
+                         const double* C, const int32_t* orb, int32_t np, double* Lov,
+                         double* Lp, void* workspace, size_t workspace_bytes,
+                         cudaStream_t stream) {
+    if (nbf <= 0 || nmo <= 0 || nmo > nbf || nocc < 0 || nocc > nmo || M < 0 || np < 0)
+        return CDS_ERR_ARG;
+    if (M == 0) return CDS_OK;
+    if (!L || !C || !Lov || (np > 0 && (!orb || !Lp))) return CDS_ERR_ARG;
+    AoLayout lay = ao_layout(workspace, nbf, nocc, np);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    const int64_t npair = npair_of(nbf);
+    const int32_t N = nbf, nv = nmo - nocc;
+    if (np > 0) {
+        k_gather_cols<<<(N * np + 255) / 256, 256, 0, stream>>>(C, N, nmo, orb, np, lay.Cp);
+        CDS_LAUNCH_CHECK();
+    }
+    for (int32_t K0 = 0; K0 < M; K0 += kAoBatch) {
+        int32_t kb = std::min(kAoBatch, M - K0);
+        int64_t tot = (int64_t)kb * N * N;
+        k_unpack<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(L, npair, K0, kb, N, lay.U);
+        CDS_LAUNCH_CHECK();
+        StridedMat U{lay.U, N, 1, (int64_t)N * N};
+        if (nocc > 0 && nv > 0) {
+            // T[b][i][nu] = sum_mu C[mu][i] U[b][mu][nu]
+            StridedMat Aop{C, 1, nmo, 0};
+            StridedOut Tout{lay.T, N, 1, (int64_t)nocc * N};
+            int st = launch_dgemm<true, true>(nocc, N, N, kb, Aop, U, Tout, stream);
+            if (st) return st;
+            // Lov[i][a][K0+b] = sum_nu T[b][i][nu] C[nu][nocc+a]
+            StridedMat Top{lay.T, N, 1, (int64_t)nocc * N};
+            StridedMat Cv{C + nocc, nmo, 1, 0};
+            StridedOut Out{Lov + K0, (int64_t)nv * M, M, 1};
+            st = launch_dgemm<false, true>(nocc, nv, N, kb, Top, Cv, Out, stream);
+            if (st) return st;
+        }
+        if (np > 0) {
+            StridedMat Aop{lay.Cp, 1, np, 0};
+            StridedOut Tout{lay.T, N, 1, (int64_t)np * N};
+            int st = launch_dgemm<true, true>(np, N, N, kb, Aop, U, Tout, stream);
+            if (st) return st;
+            StridedMat Top{lay.T, N, 1, (int64_t)np * N};
+            StridedMat Call{C, nmo, 1, 0};
+            StridedOut Out{Lp + K0, (int64_t)nmo * M, M, 1};
+            st = launch_dgemm<false, true>(np, nmo, N, kb, Top, Call, Out, stream);
+            if (st) return st;
+        }
+    }
+    return CDS_OK;
+}

@@ -1,0 +1,340 @@
+// Threshold-delta diagonal-pivoted Cholesky decomposition of the ERI
+// supermatrix, columns generated on the fly (paper Sec. II.A, Eq. gs_coulomb,
+// Eq. CD, Eq. stricterr).
+//
+// Left-looking form of the Gram-Schmidt steps: at step k with pivot P,
+//   L^k_I = [ (rho_I|rho_P) - sum_{K<k} L^K_I L^K_P ] / sqrt(D_P),
+//   D_I  -= (L^k_I)^2,  D_P := 0,
+// then the next pivot is the largest candidate residual (lowest index among
+// values within 1e-12 * max initial diagonal).  One launch of k_cd_update per
+// step streams L[0:k][*] once (coalesced along I, the dot product in FP64);
+// the grid-wide max is finished by the last block to arrive (no spin waits).
+// k_cd_select then picks the pivot.  Both kernels read a device control block
+// and return immediately once the decomposition has stopped, so the host can
+// enqueue steps ahead and only check the control block every few steps.
+#include "common.cuh"
+
+namespace cds {
+
+constexpr int kCdThreads = 256;
+constexpr int kCdChunk = 2048;   // pivot row L^K_P staged in shared memory in chunks
+constexpr double kTieRel = 1e-12;
+constexpr double kNotPdRel = 1e-10;
+constexpr int kHostCheckEvery = 32;
+
+struct CdCtrl {
+    double scale;      // max initial diagonal (all pairs)
+    double delta_eff;  // max(delta, npair * 2^-52 * scale)
+    double G;          // max candidate residual after the last update
+    double Dmin;       // min residual after the last update
+    double DP;         // residual of the current pivot
+    int64_t P;         // current pivot
+    int32_t done;      // decomposition stopped
+    int32_t status;    // cds_status
+    int32_t M;         // vectors produced
+    int32_t _pad;
+    unsigned int counter;  // last-block-done counter
+    unsigned int _pad2;
+};
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+    for (int o = 16; o; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ long long warp_min_ll(long long v) {
+    for (int o = 16; o; o >>= 1) {
+        long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+
+// Block-wide max / min of two doubles; result valid in thread 0.
+__device__ void block_maxmin(double& mx, double& mn) {
+    __shared__ double smx[32], smn[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    mx = warp_max(mx);
+    mn = warp_min(mn);
+    if (lane == 0) { smx[w] = mx; smn[w] = mn; }
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        mx = lane < nw ? smx[lane] : -INFINITY;
+        mn = lane < nw ? smn[lane] : INFINITY;
+        mx = warp_max(mx);
+        mn = warp_min(mn);
+    }
+    __syncthreads();
+}
+
+// Returns true in thread 0 of the last block to finish (after its partial is visible).
+__device__ bool last_block(unsigned int* counter) {
+    __shared__ bool am_last;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        unsigned int t = atomicAdd(counter, 1u);
+        am_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    return am_last;
+}
+
+// D = initial diagonal, candidate mask, scale = max D, G = max candidate D.
+__global__ void k_cd_init(PairSoA pd, const int32_t* __restrict__ atom,
+                          int32_t scheme, int64_t n, double delta, double* __restrict__ D,
+                          uint8_t* __restrict__ cand, double* __restrict__ blk_a,
+                          double* __restrict__ blk_b, CdCtrl* ctrl) {
+    double mx_all = -INFINITY, mx_cand = -INFINITY;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < n;
+         I += (int64_t)gridDim.x * blockDim.x) {
+        double p = pd.p[I], px = pd.Px[I], py = pd.Py[I], pz = pd.Pz[I], k = pd.K[I];
+        double d = eri_pair(p, px, py, pz, k, p, px, py, pz, k);
+        D[I] = d;
+        uint8_t c = 1;
+        if (scheme == CDS_SCHEME_ATOMIC) {
+            int32_t mu, nu;
+            unpack_pair(I, mu, nu);
+            c = atom[mu] == atom[nu];
+        }
+        cand[I] = c;
+        mx_all = fmax(mx_all, d);
+        if (c) mx_cand = fmax(mx_cand, fmax(d, 0.0));
+    }
+    double a = mx_all, b = -mx_cand;   // reuse max/min: min(-x) = -max(x)
+    block_maxmin(a, b);
+    if (threadIdx.x == 0) { blk_a[blockIdx.x] = a; blk_b[blockIdx.x] = b; }
+    if (last_block(&ctrl->counter)) {
+        double A = -INFINITY, B = INFINITY;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            A = fmax(A, __ldcg(blk_a + i));
+            B = fmin(B, __ldcg(blk_b + i));
+        }
+        block_maxmin(A, B);
+        if (threadIdx.x == 0) {
+            ctrl->scale = A;
+            ctrl->delta_eff = fmax(delta, (double)n * 2.220446049250313e-16 * A);
+            ctrl->G = -B;
+            ctrl->Dmin = 0.0;
+            ctrl->done = 0;
+            ctrl->status = CDS_OK;
+            ctrl->M = 0;
+            ctrl->counter = 0;
+        }
+    }
+}
+
+// Pivot for vector k (k vectors already made): stop test, rank cap, then the
+// lowest candidate index with max(D,0) >= G - 1e-12*scale and D > delta_eff.
+__global__ void k_cd_select(int64_t n, int32_t k, int32_t max_rank,
+                            const double* __restrict__ D, const uint8_t* __restrict__ cand,
+                            long long* __restrict__ blk_i, int32_t* __restrict__ piv,
+                            CdCtrl* ctrl) {
+    if (ctrl->done) return;
+    double G = ctrl->G, de = ctrl->delta_eff, scale = ctrl->scale;
+    if (ctrl->Dmin < -kNotPdRel * scale || !(G == G)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctrl->status = CDS_ERR_NOT_PD; ctrl->done = 1; ctrl->M = k;
+        }
+        return;
+    }
+    if (G <= de) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) { ctrl->done = 1; ctrl->M = k; }
+        return;
+    }
+    if (k >= max_rank) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctrl->status = CDS_ERR_RANK_CAP; ctrl->done = 1; ctrl->M = k;
+        }
+        return;
+    }
+    double thr = G - kTieRel * scale;
+    long long best = LLONG_MAX;
+    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < n;
+         I += (int64_t)gridDim.x * blockDim.x) {
+        double d = D[I];
+        if (cand[I] && fmax(d, 0.0) >= thr && d > de) { best = (long long)I; break; }
+    }
+    __shared__ long long sb[32];
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    best = warp_min_ll(best);
+    if (lane == 0) sb[w] = best;
+    __syncthreads();
+    if (w == 0) {
+        best = lane < (int)(blockDim.x >> 5) ? sb[lane] : LLONG_MAX;
+        best = warp_min_ll(best);
+        if (lane == 0) blk_i[blockIdx.x] = best;
+    }
+    if (last_block(&ctrl->counter)) {
+        long long b = LLONG_MAX;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            long long v = __ldcg(blk_i + i);
+            b = v < b ? v : b;
+        }
+        b = warp_min_ll(b);
+        if (lane == 0) sb[w] = b;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long m = LLONG_MAX;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = sb[i] < m ? sb[i] : m;
+            if (m < 0 || m >= n) {
+                // no candidate passed the test although G > delta_eff: the
+                // residual diagonal holds NaN or is otherwise inconsistent
+                ctrl->status = CDS_ERR_NOT_PD; ctrl->done = 1; ctrl->M = k;
+            } else {
+                ctrl->P = m;
+                ctrl->DP = __ldcg(D + m);
+                piv[k] = (int32_t)m;
+            }
+            ctrl->counter = 0;
+        }
+    }
+}
+
+// Vector k from pivot P: column, left-looking projection, residual update.
+__global__ void __launch_bounds__(kCdThreads)
+k_cd_update(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L, double* __restrict__ D,
+            const uint8_t* __restrict__ cand, double* __restrict__ blk_a,
+            double* __restrict__ blk_b, CdCtrl* ctrl) {
+    if (ctrl->done) return;
+    __shared__ double lp[kCdChunk];
+    const int64_t P = ctrl->P;
+    const double DP = ctrl->DP;
+    const double q = pd.p[P], qx = pd.Px[P], qy = pd.Py[P], qz = pd.Pz[P], kq = pd.K[P];
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const bool live = I < n;
+    double dot = 0.0;
+    const double* Lcol = L + (live ? I : 0);
+    for (int K0 = 0; K0 < k; K0 += kCdChunk) {
+        int kc = min(kCdChunk, k - K0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < kc; j += blockDim.x) lp[j] = L[(int64_t)(K0 + j) * n + P];
+        __syncthreads();
+        if (live) {
+            const double* src = Lcol + (int64_t)K0 * n;
+            int j = 0;
+            double d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+            for (; j + 4 <= kc; j += 4) {
+                d0 = fma(src[(int64_t)(j + 0) * n], lp[j + 0], d0);
+                d1 = fma(src[(int64_t)(j + 1) * n], lp[j + 1], d1);
+                d2 = fma(src[(int64_t)(j + 2) * n], lp[j + 2], d2);
+                d3 = fma(src[(int64_t)(j + 3) * n], lp[j + 3], d3);
+            }
+            for (; j < kc; ++j) d0 = fma(src[(int64_t)j * n], lp[j], d0);
+            dot += (d0 + d1) + (d2 + d3);
+        }
+    }
+    double mx = -INFINITY, mn = INFINITY;
+    if (live) {
+        double e = eri_pair(pd.p[I], pd.Px[I], pd.Py[I], pd.Pz[I], pd.K[I], q, qx, qy, qz, kq);
+        double l = (e - dot) / sqrt(DP);
+        L[(int64_t)k * n + I] = l;
+        double d = D[I] - l * l;
+        if (I == P) d = 0.0;
+        D[I] = d;
+        if (cand[I]) mx = fmax(d, 0.0);
+        mn = d;
+    }
+    block_maxmin(mx, mn);
+    if (threadIdx.x == 0) { blk_a[blockIdx.x] = mx; blk_b[blockIdx.x] = mn; }
+    if (last_block(&ctrl->counter)) {
+        double A = -INFINITY, B = INFINITY;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            A = fmax(A, __ldcg(blk_a + i));
+            B = fmin(B, __ldcg(blk_b + i));
+        }
+        block_maxmin(A, B);
+        if (threadIdx.x == 0) {
+            ctrl->G = A;
+            ctrl->Dmin = B;
+            ctrl->counter = 0;
+        }
+    }
+}
+
+struct CdLayout {
+    PairSoA pd;
+    uint8_t* cand;
+    double* blk_a;
+    double* blk_b;
+    long long* blk_i;
+    CdCtrl* ctrl;
+    size_t bytes;
+};
+
+static int cd_blocks(int64_t n) { return (int)((n + kCdThreads - 1) / kCdThreads); }
+static int sel_blocks(int64_t n) { return (int)std::min<int64_t>(4 * 152, (n + kCdThreads - 1) / kCdThreads); }
+
+static CdLayout cd_layout(void* ws, int32_t nbf) {
+    int64_t n = npair_of(nbf);
+    int nb = std::max(cd_blocks(n), 1);
+    Carver c(ws);
+    CdLayout l;
+    l.pd.p = c.take<double>(n);
+    l.pd.Px = c.take<double>(n);
+    l.pd.Py = c.take<double>(n);
+    l.pd.Pz = c.take<double>(n);
+    l.pd.K = c.take<double>(n);
+    l.cand = c.take<uint8_t>(n);
+    l.blk_a = c.take<double>(nb);
+    l.blk_b = c.take<double>(nb);
+    l.blk_i = c.take<long long>(nb);
+    l.ctrl = c.take<CdCtrl>(1);
+    l.bytes = c.off;
+    return l;
+}
+
+}  // namespace cds
+
+using namespace cds;
+
+extern "C" size_t cds_cd_workspace_bytes(int32_t nbf) {
+    if (nbf < 0) return 0;
+    return cd_layout(nullptr, nbf).bytes;
+}
+
+extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
+                                const int32_t* atom, double delta, int32_t scheme,
+                                int32_t max_rank, double* L, int32_t* piv, double* D,
+                                int32_t* M_out, double* delta_eff_out, void* workspace,
+                                size_t workspace_bytes, cudaStream_t stream) {
+    if (nbf <= 0 || !xyz || !alpha || !L || !piv || !D || !M_out || max_rank < 0)
+        return CDS_ERR_ARG;
+    if (!(delta >= 0.0)) return CDS_ERR_ARG;
+    if (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC) return CDS_ERR_ARG;
+    if (scheme == CDS_SCHEME_ATOMIC && !atom) return CDS_ERR_ARG;
+    int64_t n = npair_of(nbf);
+    CdLayout lay = cd_layout(workspace, nbf);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    int st = build_pairs(nbf, xyz, alpha, lay.pd, stream);
+    if (st) return st;
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, sizeof(CdCtrl), stream));
+    int nb = cd_blocks(n), ns = sel_blocks(n);
+    k_cd_init<<<nb, kCdThreads, 0, stream>>>(lay.pd, atom, scheme, n, delta, D, lay.cand,
+                                            lay.blk_a, lay.blk_b, lay.ctrl);
+    CDS_LAUNCH_CHECK();
+    k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, 0, max_rank, D, lay.cand, lay.blk_i, piv,
+                                              lay.ctrl);
+    CDS_LAUNCH_CHECK();
+    CdCtrl h{};
+    for (int32_t k0 = 0; k0 <= max_rank; k0 += kHostCheckEvery) {
+        int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
+        for (int32_t k = k0; k < k1; ++k) {
+            k_cd_update<<<nb, kCdThreads, 0, stream>>>(lay.pd, n, k, L, D, lay.cand, lay.blk_a,
+                                                      lay.blk_b, lay.ctrl);
+            k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, k + 1, max_rank, D, lay.cand,
+                                                      lay.blk_i, piv, lay.ctrl);
+        }
+        CDS_LAUNCH_CHECK();
+        CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, stream));
+        CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (h.done) break;
+    }
+    *M_out = h.M;
+    if (delta_eff_out) *delta_eff_out = h.delta_eff;
+    if (!h.done) return CDS_ERR_RANK_CAP;
+    return h.status;
+}

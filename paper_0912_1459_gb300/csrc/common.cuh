@@ -1,0 +1,87 @@
+// Shared device/host helpers of libcdsigma (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+#include <climits>
+#include <algorithm>
+
+#include "cdsigma.h"
+
+#define CDS_CUDA_TRY(expr)                                   \
+    do {                                                     \
+        cudaError_t _e = (expr);                             \
+        if (_e != cudaSuccess) return CDS_ERR_CUDA;          \
+    } while (0)
+
+#define CDS_LAUNCH_CHECK() CDS_CUDA_TRY(cudaGetLastError())
+
+namespace cds {
+
+constexpr double kTwoPi52 = 34.98683665524972;      // 2 pi^(5/2)
+constexpr double kHalfSqrtPi = 0.88622692545275801;  // sqrt(pi)/2
+constexpr double kPi = 3.14159265358979323846;
+
+inline int64_t npair_of(int32_t nbf) { return (int64_t)nbf * (nbf + 1) / 2; }
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+// Carves consecutive 256-byte-aligned regions out of a caller workspace.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(void* p) : base(static_cast<char*>(p)) {}
+    template <class T> T* take(size_t n) {
+        T* p = reinterpret_cast<T*>(base ? base + off : nullptr);
+        off = align_up(off + n * sizeof(T));
+        return p;
+    }
+};
+
+// Gaussian-product data of every product density (Sec. II.A), structure of
+// arrays so a warp reads consecutive pairs with coalesced loads.
+struct PairSoA {
+    double* p;    // exponent sum a_mu + a_nu
+    double* Px;   // product centre
+    double* Py;
+    double* Pz;
+    double* K;    // N_mu N_nu exp(-a_mu a_nu |A-B|^2 / p)
+};
+
+// Boys function F0(T) = (1/2) sqrt(pi/T) erf(sqrt T), 1 - T/3 below 1e-10.
+__device__ __forceinline__ double boys_f0(double T) {
+    if (T < 1e-10) return 1.0 - T * (1.0 / 3.0);
+    double x = sqrt(T);
+    return kHalfSqrtPi * erf(x) / x;
+}
+
+// (rho_I|rho_J) from the pair data of both densities (Eq. integral, s-type).
+__device__ __forceinline__ double eri_pair(double p, double px, double py, double pz,
+                                           double k, double q, double qx, double qy,
+                                           double qz, double kq) {
+    double dx = px - qx, dy = py - qy, dz = pz - qz;
+    double d2 = dx * dx + dy * dy + dz * dz;
+    double pq = p * q;
+    double s = p + q;
+    double T = pq / s * d2;
+    return kTwoPi52 / (pq * sqrt(s)) * k * kq * boys_f0(T);
+}
+
+// Decode a packed pair index I = nu(nu+1)/2 + mu into (mu, nu).
+__device__ __forceinline__ void unpack_pair(int64_t I, int32_t& mu, int32_t& nu) {
+    double r = sqrt(8.0 * (double)I + 1.0);
+    int64_t n = (int64_t)((r - 1.0) * 0.5);
+    while (n * (n + 1) / 2 > I) --n;
+    while ((n + 1) * (n + 2) / 2 <= I) ++n;
+    nu = (int32_t)n;
+    mu = (int32_t)(I - n * (n + 1) / 2);
+}
+
+}  // namespace cds
+
+// Internal entry points shared across translation units (not exported).
+namespace cds {
+int build_pairs(int32_t nbf, const double* xyz, const double* alpha, PairSoA pd,
+                cudaStream_t stream);
+}

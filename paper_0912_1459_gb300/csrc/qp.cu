@@ -1,0 +1,115 @@
+// Newton quasiparticle solve (paper Eq. qpapp, Eq. iter, Eq. ps, Eq. NR).
+//
+// Every iteration evaluates Sigma and dSigma/dw of all still-active orbitals
+// at their own current w (one self-energy pass with nE = 1, recomputing the
+// MO integrals from the factors), then a single small kernel applies
+//   P = 1/(1 - dSigma/dw),  w_new = w + (e_q + Sigma(w) - w) P
+// in FP64 and retires orbitals with |w_new - w| <= conv.
+#include "sigma_tc.cuh"
+
+namespace cds {
+
+__global__ void k_qp_init(const double* __restrict__ eps, const int32_t* __restrict__ orb,
+                          int32_t np, int32_t nmo, double* omega, double* pole, int32_t* iters,
+                          int32_t* status, int32_t* active, int32_t* nactive) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t == 0) *nactive = 0;
+    if (t >= np) return;
+    int q = orb[t];
+    bool ok = q >= 0 && q < nmo;
+    omega[t] = ok ? eps[q] : __longlong_as_double(0x7ff8000000000000LL);
+    pole[t] = 1.0;
+    iters[t] = 0;
+    status[t] = ok ? CDS_QP_NO_CONVERGENCE : CDS_QP_NONFINITE;
+    active[t] = ok ? 1 : 0;
+}
+
+__global__ void k_qp_step(const double* __restrict__ eps, const int32_t* __restrict__ orb,
+                          int32_t np, const double* __restrict__ sig,
+                          const double* __restrict__ dsig, double conv, double* omega,
+                          double* pole, int32_t* iters, int32_t* status, int32_t* active,
+                          int32_t* nactive) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np || !active[t]) return;
+    double w = omega[t];
+    double P = 1.0 / (1.0 - dsig[t]);
+    double wn = w + (eps[orb[t]] + sig[t] - w) * P;
+    iters[t] += 1;
+    pole[t] = P;
+    omega[t] = wn;
+    if (!isfinite(wn)) {
+        status[t] = CDS_QP_NONFINITE;
+        active[t] = 0;
+    } else if (fabs(wn - w) <= conv) {
+        status[t] = CDS_QP_OK;
+        active[t] = 0;
+    } else {
+        atomicAdd(nactive, 1);
+    }
+}
+
+struct QpLayout {
+    double* sig;
+    double* dsig;
+    int32_t* active;
+    int32_t* nactive;
+    void* sigma_ws;
+    size_t bytes;
+};
+
+static QpLayout qp_layout(void* ws, int32_t nmo, int32_t nocc, int32_t M, int32_t np,
+                          int32_t precision) {
+    Carver c(ws);
+    QpLayout l;
+    l.sig = c.take<double>(np);
+    l.dsig = c.take<double>(np);
+    l.active = c.take<int32_t>(np);
+    l.nactive = c.take<int32_t>(1);
+    size_t sw = sigma_ws_bytes(nmo, nocc, M, np, 1, precision);
+    l.sigma_ws = c.take<char>(sw);
+    l.bytes = c.off;
+    return l;
+}
+
+}  // namespace cds
+
+using namespace cds;
+
+extern "C" size_t cds_qp_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np,
+                                         int32_t precision) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || M < 0 || np < 0) return 0;
+    return qp_layout(nullptr, nmo, nocc, M, np, precision).bytes;
+}
+
+extern "C" int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                            const double* Lp, const int32_t* orb, int32_t np, const double* eps,
+                            double conv, int32_t max_iter, int32_t precision, double* omega,
+                            double* pole, int32_t* iters, int32_t* status, void* workspace,
+                            size_t workspace_bytes, cudaStream_t stream) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || M < 0 || np < 0 || np > 65535 || max_iter < 1 ||
+        !(conv >= 0.0))
+        return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_BF16X3) return CDS_ERR_UNSUPPORTED;
+    if (np == 0) return CDS_OK;
+    if (!Lp || !orb || !eps || !omega || !pole || !iters || !status) return CDS_ERR_ARG;
+    QpLayout lay = qp_layout(workspace, nmo, nocc, M, np, precision);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    int nb = (np + 127) / 128;
+    k_qp_init<<<nb, 128, 0, stream>>>(eps, orb, np, nmo, omega, pole, iters, status, lay.active,
+                                      lay.nactive);
+    CDS_LAUNCH_CHECK();
+    int32_t h_active = np;
+    for (int32_t it = 0; it < max_iter && h_active > 0; ++it) {
+        int st = sigma2_dispatch(nmo, nocc, M, Lov, Lp, np, eps, omega, 1, precision, lay.active,
+                                 lay.sig, lay.dsig, lay.sigma_ws, stream);
+        if (st) return st;
+        CDS_CUDA_TRY(cudaMemsetAsync(lay.nactive, 0, sizeof(int32_t), stream));
+        k_qp_step<<<nb, 128, 0, stream>>>(eps, orb, np, lay.sig, lay.dsig, conv, omega, pole,
+                                          iters, status, lay.active, lay.nactive);
+        CDS_LAUNCH_CHECK();
+        CDS_CUDA_TRY(cudaMemcpyAsync(&h_active, lay.nactive, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, stream));
+        CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    return h_active > 0 ? CDS_ERR_NO_CONVERGENCE : CDS_OK;
+}

@@ -1,0 +1,47 @@
+"""The C-ABI library loads without a GPU and exports every declared entry point."""
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_0912_1459_gb300", "libcdsigma.so")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(LIB):
+        from paper_0912_1459_gb300 import build as b
+        b.build()
+    from paper_0912_1459_gb300 import cdsigma
+    return cdsigma
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = lib.declared_symbols()
+    assert "cds_cd_decompose" in names and "cds_sigma2_diag" in names and "cds_qp_solve" in names
+    so = lib.load()
+    missing = [n for n in names if not hasattr(so, n)]
+    assert missing == []
+
+
+def test_host_only_calls(lib):
+    so = lib.load()
+    assert so.cds_version() >= 100
+    assert so.cds_errstr(4).decode().startswith("Cholesky rank cap")
+    assert so.cds_cd_workspace_bytes(24) > 300 * 5 * 8
+    assert so.cds_cd_workspace_bytes(-1) == 0
+    assert so.cds_sigma2_workspace_bytes(24, 6, 100, 2, 16, 0) > 0
+    assert so.cds_sigma2_workspace_bytes(24, 6, 100, 2, 0, 0) == 0
+
+
+def test_argument_errors_before_any_launch(lib):
+    so = lib.load()
+    # invalid sizes are rejected on the host, without touching a device
+    assert so.cds_cd_decompose(0, None, None, None, 1e-6, 0, 10, None, None, None, None, None,
+                               None, 0, None) == 1
+    assert so.cds_sigma2_diag(24, 6, 10, None, None, 1, None, None, 0, 0, None, None, None, 0,
+                              None) == 1
+    assert so.cds_sigma2_diag(24, 6, 10, None, None, 1, None, None, 4, 9, None, None, None, 0,
+                              None) == 7
+    assert so.cds_qp_solve(24, 6, 10, None, None, None, 1, None, 1e-5, 0, 0, None, None, None,
+                           None, None, 0, None) == 1

@@ -1,0 +1,167 @@
+"""GPU path against the CPU oracle, element by element, through the C ABI.
+
+Tolerances (FP64 path): integrals 1e-13 relative; Cholesky vectors and
+residuals 1e-11 absolute (values <= 2, about k*1e-16 of accumulated rounding
+after k steps); MO factors 1e-11 relative to their largest entry;
+self-energy, its derivative and the Newton roots 1e-10 Ha.  Pivot sequences
+must be identical (ties inside the 1e-12 band resolve to the same lowest
+index on both sides).  Sizes span several tiles and ragged tails: o = 6, 40,
+v = 18, 200 against 32-row blocks.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import eri
+from tests import oracle_pipeline as O
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_0912_1459_gb300 as G  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def basis_dev(m):
+    return dev(m.basis.xyz), dev(m.basis.alpha), dev(m.basis.atom.astype(np.int32))
+
+
+def gpu_cd(m, delta, scheme="full", max_rank=None):
+    xyz, a, at = basis_dev(m)
+    L, piv, D, de = G.cds_cd_decompose(xyz, a, at, delta, scheme, max_rank=max_rank)
+    torch.cuda.synchronize()
+    return L.cpu().numpy(), piv.cpu().numpy().astype(np.int64), D.cpu().numpy(), de
+
+
+@pytest.mark.parametrize("name", ["c0", "c1"])
+def test_eri_diag_and_columns(name):
+    m = O.molecule(name)
+    pd = O.pairs(name)
+    xyz, a, _ = basis_dev(m)
+    D = G.cds_eri_diag(xyz, a).cpu().numpy()
+    np.testing.assert_allclose(D, eri.eri_diagonal(pd), rtol=1e-13, atol=0)
+    rng = np.random.default_rng(0)
+    piv = rng.choice(pd.npair, 5, replace=False).astype(np.int32)
+    cols = G.cds_eri_columns(xyz, a, dev(piv)).cpu().numpy()
+    for c, P in enumerate(piv):
+        ref = eri.eri_column(pd, int(P))
+        np.testing.assert_allclose(cols[c], ref, rtol=1e-13, atol=1e-300)
+
+
+@pytest.mark.parametrize("name,delta,scheme", [
+    ("c0", 1e-6, "full"), ("c0", 1e-3, "full"), ("c0", 0.0, "full"), ("c0", 1e-6, "atomic"),
+    ("c1", 1e-4, "full"), ("c1", 1e-5, "full"), ("c1", 1e-6, "full"), ("c1", 1e-4, "atomic"),
+    ("c1", 1e-6, "atomic"),
+])
+def test_cd_parity(name, delta, scheme):
+    m = O.molecule(name)
+    ref = O.decomposition(name, delta, scheme)
+    L, piv, D, de = gpu_cd(m, delta, scheme)
+    assert de == pytest.approx(ref.delta_eff, rel=1e-14)
+    assert len(piv) == ref.M
+    assert np.array_equal(piv, ref.piv)
+    np.testing.assert_allclose(L, ref.L, rtol=0, atol=1e-11)
+    np.testing.assert_allclose(D, ref.D, rtol=0, atol=1e-11)
+
+
+def test_cd_empty_when_delta_exceeds_every_diagonal():
+    m = O.molecule("c0")
+    L, piv, D, de = gpu_cd(m, 100.0)
+    assert L.shape[0] == 0 and piv.shape[0] == 0
+    np.testing.assert_allclose(D, eri.eri_diagonal(O.pairs("c0")), rtol=1e-13)
+
+
+def test_cd_rank_cap_reports_and_keeps_prefix():
+    m = O.molecule("c0")
+    xyz, a, at = basis_dev(m)
+    with pytest.raises(G.CdsError) as ei:
+        G.cds_cd_decompose(xyz, a, at, 1e-6, "full", max_rank=10)
+    assert ei.value.status == 4
+    L = torch.empty((10, G.npair(m.nbf)), dtype=torch.float64, device=DEV)
+    with pytest.raises(G.CdsError):
+        G.cds_cd_decompose(xyz, a, at, 1e-6, "full", max_rank=10, L_out=L)
+    ref = O.decomposition("c0", 1e-6, "full")
+    np.testing.assert_allclose(L.cpu().numpy(), ref.L[:10], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-5)])
+def test_transform_parity(name, delta):
+    m = O.molecule(name)
+    ref = O.decomposition(name, delta)
+    orbs = np.concatenate([m.orbitals, [0, m.nbf - 1]]).astype(np.int32)
+    Lov, Lp = G.cds_cd_to_mo(dev(ref.L), dev(m.C), m.nocc, dev(orbs))
+    rov, rp = O.factors(name, ref.L, orbs)
+    scale = max(np.abs(rov).max(), np.abs(rp).max())
+    np.testing.assert_allclose(Lov.cpu().numpy(), rov, rtol=0, atol=1e-11 * scale)
+    np.testing.assert_allclose(Lp.cpu().numpy(), rp, rtol=0, atol=1e-11 * scale)
+
+
+@pytest.mark.parametrize("name,delta,nE", [("c0", 1e-6, 16), ("c1", 1e-5, 4)])
+def test_sigma_fp64_parity(name, delta, nE):
+    m = O.molecule(name)
+    ref = O.decomposition(name, delta)
+    rov, rp = O.factors(name, ref.L)
+    E = W.energy_grid(m.eps[m.orbitals], nE)
+    s, ds = G.cds_sigma2_diag(dev(rov), dev(rp), dev(m.eps), m.nocc, dev(E), "fp64")
+    rs, rds = O.sigma(name, rov, rp, E)
+    np.testing.assert_allclose(s.cpu().numpy(), rs, rtol=0, atol=1e-10)
+    np.testing.assert_allclose(ds.cpu().numpy(), rds, rtol=1e-10, atol=1e-10)
+
+
+@pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-5)])
+def test_qp_fp64_parity(name, delta):
+    m = O.molecule(name)
+    ref = O.decomposition(name, delta)
+    rov, rp = O.factors(name, ref.L)
+    w, P, it, st = G.cds_qp_solve(dev(rov), dev(rp), dev(m.orbitals), dev(m.eps), m.nocc,
+                                  conv=1e-5, max_iter=50, precision="fp64")
+    res = O.solve(name, rov, rp, m.orbitals)
+    np.testing.assert_allclose(w.cpu().numpy(), [r[0] for r in res], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(P.cpu().numpy(), [r[1] for r in res], rtol=1e-9, atol=0)
+    assert it.cpu().tolist() == [r[2] for r in res]
+    assert st.cpu().tolist() == [r[3] for r in res]
+
+
+def test_end_to_end_tiny_pipeline():
+    """CD -> transform -> Sigma -> Newton entirely on the GPU vs entirely in the oracle."""
+    m = O.molecule("c0")
+    xyz, a, at = basis_dev(m)
+    L, piv, D, de = G.cds_cd_decompose(xyz, a, at, m.delta, "full")
+    Lov, Lp = G.cds_cd_to_mo(L, dev(m.C), m.nocc, dev(m.orbitals))
+    E = W.energy_grid(m.eps[m.orbitals], m.nE)
+    s, ds = G.cds_sigma2_diag(Lov, Lp, dev(m.eps), m.nocc, dev(E), "fp64")
+    w, P, it, st = G.cds_qp_solve(Lov, Lp, dev(m.orbitals), dev(m.eps), m.nocc)
+    ref = O.decomposition("c0", m.delta)
+    rov, rp = O.factors("c0", ref.L)
+    rs, _ = O.sigma("c0", rov, rp, E)
+    res = O.solve("c0", rov, rp, m.orbitals)
+    np.testing.assert_allclose(s.cpu().numpy(), rs, atol=1e-10, rtol=0)
+    np.testing.assert_allclose(w.cpu().numpy(), [r[0] for r in res], atol=1e-10, rtol=0)
+
+
+def test_sigma_edge_cases():
+    m = O.molecule("c0")
+    ref = O.decomposition("c0", 1e-6)
+    # every orbital, one energy each: occupied and virtual q, ragged single block
+    orbs = np.arange(m.nbf, dtype=np.int32)
+    rov, rp = O.factors("c0", ref.L, orbs)
+    E = m.eps[:, None] + 0.013
+    s, ds = G.cds_sigma2_diag(dev(rov), dev(rp), dev(m.eps), m.nocc, dev(E), "fp64")
+    rs, rds = O.sigma("c0", rov, rp, E)
+    np.testing.assert_allclose(s.cpu().numpy(), rs, atol=1e-10, rtol=0)
+    # no orbitals: a no-op
+    s0, _ = G.cds_sigma2_diag(dev(rov), dev(rp[:0]), dev(m.eps), m.nocc, dev(E[:0]), "fp64")
+    assert s0.shape == (0, 1)
+    # a single Cholesky vector
+    rov1, rp1 = O.factors("c0", ref.L[:1], orbs[:3])
+    s1, _ = G.cds_sigma2_diag(dev(rov1), dev(rp1), dev(m.eps), m.nocc, dev(E[:3]), "fp64")
+    rs1, _ = O.sigma("c0", rov1, rp1, E[:3])
+    np.testing.assert_allclose(s1.cpu().numpy(), rs1, atol=1e-12, rtol=0)
