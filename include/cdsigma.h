@@ -53,11 +53,14 @@ typedef enum {
 typedef enum { CDS_SCHEME_FULL = 0, CDS_SCHEME_ATOMIC = 1 } cds_scheme;
 
 /* Arithmetic of the J-contractions in sigma2 / qp_solve.
- * FP64: binary64 throughout.
- * BF16X3: each factor split x = hi + lo (both bf16), products hi*hi + hi*lo +
- *   lo*hi on tensor cores with fp32 accumulation; denominators and the
- *   per-tile reductions in fp32, cross-tile sums and the Newton step in fp64. */
-typedef enum { CDS_PREC_FP64 = 0, CDS_PREC_BF16X3 = 2 } cds_precision;
+ * FP64: binary64 throughout (CUDA cores).
+ * BF16X3 / FP16X3: each factor split s*x = hi + lo with hi, lo bf16 (s = 1)
+ *   or fp16 (s = a power of two with max|s x| <= 1024); the products
+ *   hi*hi + hi*lo + lo*hi run on tcgen05 tensor cores with fp32 accumulation.
+ *   Denominators are double-fp32 pairs, per-element sums fp32, cross-tile sums
+ *   and the Newton step fp64.  FP16X3 carries ~22 significant bits per factor,
+ *   BF16X3 ~17. */
+typedef enum { CDS_PREC_FP64 = 0, CDS_PREC_BF16X3 = 2, CDS_PREC_FP16X3 = 3 } cds_precision;
 
 /* Newton status per orbital (paper Eq. NR). */
 enum { CDS_QP_OK = 0, CDS_QP_NO_CONVERGENCE = 1, CDS_QP_NONFINITE = 2 };
@@ -67,6 +70,10 @@ int cds_version(void);
 
 /* Static description of a status code; never NULL. */
 const char* cds_errstr(int status);
+
+/* Number of CUDA kernels this library has launched in this process (all
+ * devices, all streams); monotone, thread-safe. */
+unsigned long long cds_launch_count(void);
 
 /* ------------------------------------------------------------------------
  * Electron-repulsion integrals over s-type Gaussians (paper Sec. II.A,

@@ -32,12 +32,13 @@ def sigma2_from_factors(Lq: np.ndarray, Lov: np.ndarray, eps: np.ndarray,
     o, v = Lov.shape[0], Lov.shape[1]
     eo, ev = eps[:nocc], eps[nocc:]
     Lq_occ, Lq_vir = Lq[:nocc], Lq[nocc:]
-    # first sum: (qi|aj) = sum_K B^K_qi B^K_aj, stored as W[i, a, j]
-    W = np.einsum("ik,jak->iaj", Lq_occ, Lov)
-    num1 = (2.0 * W - W.transpose(2, 1, 0)) * W        # (qj|ai) = W[j, a, i]
-    den1 = ev[None, :, None] - eo[:, None, None] - eo[None, None, :]
+    Lov2 = Lov.reshape(o * v, -1)                      # row i*v + a
+    # first sum: (qi|aj) = sum_K B^K_qi B^K_aj, stored as Y[i, j, a]
+    Y = (Lq_occ @ Lov2.T).reshape(o, o, v)
+    num1 = (2.0 * Y - Y.transpose(1, 0, 2)) * Y        # (qj|ai) = Y[j, i, a]
+    den1 = ev[None, None, :] - eo[:, None, None] - eo[None, :, None]
     # second sum: (qa|ib) = sum_K B^K_qa B^K_ib, stored as U[a, i, b]
-    U = np.einsum("ak,ibk->aib", Lq_vir, Lov)
+    U = (Lq_vir @ Lov2.T).reshape(v, o, v)
     num2 = (2.0 * U - U.transpose(2, 1, 0)) * U        # (qb|ia) = U[b, i, a]
     den2 = eo[None, :, None] - ev[:, None, None] - ev[None, None, :]
     s1 = np.empty(E.shape[0])

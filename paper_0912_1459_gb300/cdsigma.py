@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "CDS_OK", 1: "CDS_ERR_ARG", 2: "CDS_ERR_CUDA", 3: "CDS_ERR_NO
                 4: "CDS_ERR_RANK_CAP", 5: "CDS_ERR_NO_CONVERGENCE", 6: "CDS_ERR_WORKSPACE",
                 7: "CDS_ERR_UNSUPPORTED", 8: "CDS_ERR_TIMEOUT"}
 SCHEMES = {"full": 0, "atomic": 1}
-PRECISIONS = {"fp64": 0, "bf16x3": 2}
+PRECISIONS = {"fp64": 0, "bf16x3": 2, "fp16x3": 3}
 QP_OK, QP_NO_CONVERGENCE, QP_NONFINITE = 0, 1, 2
 
 _lib: Optional[ctypes.CDLL] = None
@@ -34,6 +34,7 @@ _i32, _f64, _sz, _vp = ctypes.c_int32, ctypes.c_double, ctypes.c_size_t, ctypes.
 _SIGNATURES = {
     "cds_version": (ctypes.c_int, []),
     "cds_errstr": (ctypes.c_char_p, [ctypes.c_int]),
+    "cds_launch_count": (ctypes.c_ulonglong, []),
     "cds_eri_diag": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp]),
     "cds_eri_columns": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp]),
     "cds_cd_workspace_bytes": (_sz, [_i32]),
@@ -76,7 +77,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
 def declared_symbols(header: str = HEADER) -> list[str]:
     """Every function name declared in the public header."""
     text = open(header).read()
-    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char\*)\s+(cds_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|size_t|const char\*|unsigned long long)\s+(cds_\w+)\s*\(",
+                                 text, re.M)))
 
 
 def errstr(status: int) -> str:
@@ -114,6 +116,11 @@ def npair(nbf: int) -> int:
 
 def cds_version() -> int:
     return int(load().cds_version())
+
+
+def cds_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(load().cds_launch_count())
 
 
 def cds_eri_diag(xyz: torch.Tensor, alpha: torch.Tensor) -> torch.Tensor:

@@ -1,5 +1,14 @@
-// Library identity and status strings.
+// Library identity, status strings and the launch counter.
+#include <atomic>
+
 #include "common.cuh"
+
+namespace cds {
+static std::atomic<unsigned long long> g_launches{0};
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+}  // namespace cds
+
+extern "C" unsigned long long cds_launch_count(void) { return cds::g_launches.load(); }
 
 extern "C" int cds_version(void) { return 100; }
 

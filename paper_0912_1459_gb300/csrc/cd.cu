@@ -328,7 +328,8 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
             k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, k + 1, max_rank, D, lay.cand,
                                                       lay.blk_i, piv, lay.ctrl);
         }
-        CDS_LAUNCH_CHECK();
+        count_launches(2ull * (unsigned long long)(k1 - k0));
+        CDS_CUDA_TRY(cudaGetLastError());
         CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, stream));
         CDS_CUDA_TRY(cudaStreamSynchronize(stream));
         if (h.done) break;

@@ -15,7 +15,17 @@
         if (_e != cudaSuccess) return CDS_ERR_CUDA;          \
     } while (0)
 
-#define CDS_LAUNCH_CHECK() CDS_CUDA_TRY(cudaGetLastError())
+namespace cds {
+// Kernel launches issued by this library in this process (see cds_launch_count).
+void count_launches(unsigned long long n);
+}
+
+// Counts one launch and turns a launch error into CDS_ERR_CUDA.
+#define CDS_LAUNCH_CHECK()                 \
+    do {                                   \
+        cds::count_launches(1);            \
+        CDS_CUDA_TRY(cudaGetLastError());  \
+    } while (0)
 
 namespace cds {
 

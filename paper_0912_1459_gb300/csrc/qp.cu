@@ -89,7 +89,7 @@ extern "C" int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* 
     if (nmo <= 0 || nocc < 0 || nocc > nmo || M < 0 || np < 0 || np > 65535 || max_iter < 1 ||
         !(conv >= 0.0))
         return CDS_ERR_ARG;
-    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_BF16X3) return CDS_ERR_UNSUPPORTED;
+    if (precision != CDS_PREC_FP64 && !is_split16(precision)) return CDS_ERR_UNSUPPORTED;
     if (np == 0) return CDS_OK;
     if (!Lp || !orb || !eps || !omega || !pole || !iters || !status) return CDS_ERR_ARG;
     QpLayout lay = qp_layout(workspace, nmo, nocc, M, np, precision);

@@ -200,7 +200,7 @@ int sigma2_fp64(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const d
 size_t sigma_ws_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE,
                       int32_t precision) {
     if (precision == CDS_PREC_FP64) return fp64_part_bytes(nmo, nocc, np, nE);
-    if (precision == CDS_PREC_BF16X3) return tc_workspace_bytes(nmo, nocc, M, np, nE);
+    if (is_split16(precision)) return tc_workspace_bytes(nmo, nocc, M, np, nE);
     return 0;
 }
 
@@ -211,8 +211,9 @@ int sigma2_dispatch(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, con
     if (precision == CDS_PREC_FP64)
         return sigma2_fp64(nmo, nocc, M, Lov, Lp, np, eps, E, nE, active, sigma, dsigma,
                            static_cast<double*>(ws), stream);
-    if (precision == CDS_PREC_BF16X3)
-        return sigma2_tc(nmo, nocc, M, Lov, Lp, np, eps, E, nE, active, sigma, dsigma, ws, stream);
+    if (is_split16(precision))
+        return sigma2_tc(nmo, nocc, M, Lov, Lp, np, eps, E, nE, active, precision, sigma, dsigma,
+                         ws, stream);
     return CDS_ERR_UNSUPPORTED;
 }
 
@@ -237,7 +238,7 @@ extern "C" int cds_sigma2_diag(int32_t nmo, int32_t nocc, int32_t M, const doubl
                                double* dsigma, void* workspace, size_t workspace_bytes,
                                cudaStream_t stream) {
     if (!sigma_args_ok(nmo, nocc, M, np, nE)) return CDS_ERR_ARG;
-    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_BF16X3) return CDS_ERR_UNSUPPORTED;
+    if (precision != CDS_PREC_FP64 && !is_split16(precision)) return CDS_ERR_UNSUPPORTED;
     if (np == 0) return CDS_OK;
     if (!Lp || !eps || !E || !sigma || (nocc > 0 && nocc < nmo && !Lov)) return CDS_ERR_ARG;
     size_t need = sigma_ws_bytes(nmo, nocc, M, np, nE, precision);

@@ -1,13 +1,17 @@
 // Tensor-core path of the diagonal self-energy (paper Eq. SE) for sm_103a:
 // tcgen05 MMAs with TMEM accumulators, operands staged by TMA.
 //
-// Precision (BF16X3): every factor L^J_pq is split in FP64 into
-// hi = bf16(x) and lo = bf16(x - hi); each J-contraction is
-//   X = Ahi.Bhi + Ahi.Blo + Alo.Bhi
-// with FP32 accumulation in TMEM (the lo.lo product, ~2^-16 relative, is
-// dropped).  Denominators and per-tile sums are FP32, with denominators
-// closer than 1e-3 Ha to a pole recomputed in FP64; per-tile totals are
-// summed across tiles in FP64 in a fixed order.
+// Precision: every factor L^J_pq is split in FP64 into two 16-bit parts,
+// hi = r(s x) and lo = r(s x - hi), and each J-contraction is
+//   X = (Ahi.Bhi + Ahi.Blo + Alo.Bhi) / (s_A s_B)
+// with FP32 accumulation in TMEM (the lo.lo product is dropped).
+//   BF16X3: r = bf16, s = 1             (~2^-17 relative per factor)
+//   FP16X3: r = fp16, s = 2^k with max|s x| <= 1024, one power of two per
+//           array found on the device (~2^-22 relative per factor, absolute
+//           floor 2^-24 / s from fp16 subnormals).
+// Denominators are double-FP32 pairs, (c_hi - e_hi) + (c_lo - e_lo), exact
+// to ~1e-14 Ha so poles do not lose precision; per-element sums are FP32,
+// per-tile totals are summed across tiles in FP64 in a fixed order.
 //
 // Work item = (term, orbital t, spectator s, x-block pair A <= B), 128 x 128
 // blocks; see sigma.cuh for the exchange pairing.  Per item the CTA forms
@@ -23,9 +27,12 @@
 // and sets an error word instead of hanging.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "sigma_tc.cuh"
 
@@ -40,13 +47,16 @@ constexpr int STAGE_BYTES = 8 * TILE_BYTES;   // 64 KB
 constexpr int NUM_EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * NUM_EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr float POLE_GUARD = 1e-3f;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 256 + NUM_EPI_WARPS * 16 * 2 * 4;
 
-// kind::f16 instruction descriptor: D f32, A/B bf16, both K-major, M=N=128.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TB >> 3) << 17) |
-                           ((uint32_t)(TB >> 4) << 24);
+// kind::f16 instruction descriptor: D f32, A/B bf16 (format 1) or fp16
+// (format 0), both K-major, M = N = 128.
+template <bool BF16>
+__host__ __device__ constexpr uint32_t idesc() {
+    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) |
+           ((uint32_t)(TB >> 3) << 17) | ((uint32_t)(TB >> 4) << 24);
+}
 
 struct Maps {
     CUtensorMap m[2][4];   // [term][aq_hi, aq_lo, bk_hi, bk_lo]
@@ -55,8 +65,7 @@ struct Maps {
 struct Term {
     int32_t nx, ns, nb, bulk_s_dim;   // bulk_s_dim: 1 if spectator is dim 1 of the bulk map, else 2
     int64_t npb, nitems, item0;
-    const double* eps_s;
-    const double* eps_x;
+    int32_t eps_s_off, eps_x_off;     // offsets of the spectator / pair orbitals in eps
 };
 
 struct Params {
@@ -132,12 +141,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) |
            ((uint64_t)(512 >> 4) << 32) | ((uint64_t)1 << 46) | ((uint64_t)4 << 61);
 }
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t id,
+                                        uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
-        "l"(a), "l"(b), "r"(IDESC), "r"(acc));
+        "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile(
@@ -165,6 +175,15 @@ __device__ __forceinline__ float rcp_approx(float x) {
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
+// Sum of two float pairs (hi, lo) by Knuth's two-sum, renormalised; exact to
+// ~2^-44 relative, so small differences of O(1) energies keep their digits.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float v = s - a.x;
+    const float e = (a.x - (s - v)) + (b.x - v) + (a.y + b.y);
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 // Barrier over the 256 epilogue threads that also ORs a flag across them, so
 // every epilogue warp takes the same branch afterwards.
@@ -181,24 +200,52 @@ __device__ __forceinline__ bool epi_any(bool v) {
     return r != 0;
 }
 
-__device__ __forceinline__ bool decode(const Params& P, int64_t item, int& term, int& t, int& s,
-                                       int& A, int& B) {
+// Fields of one term in registers (selected, never indexed dynamically, so the
+// parameter block is not copied to local memory).
+struct TermR {
+    int32_t nx, ns, nb, bulk_s_dim;
+    int64_t npb, item0, first;   // first: global index of the term's first item
+    int32_t eps_s_off, eps_x_off;
+};
+
+__device__ __forceinline__ TermR term_regs(const Params& P, int term) {
+    TermR r;
+    r.nx = term ? P.term[1].nx : P.term[0].nx;
+    r.ns = term ? P.term[1].ns : P.term[0].ns;
+    r.nb = term ? P.term[1].nb : P.term[0].nb;
+    r.bulk_s_dim = term ? P.term[1].bulk_s_dim : P.term[0].bulk_s_dim;
+    r.npb = term ? P.term[1].npb : P.term[0].npb;
+    r.item0 = term ? P.term[1].item0 : P.term[0].item0;
+    r.first = term ? P.term[0].nitems : 0;
+    r.eps_s_off = term ? P.term[1].eps_s_off : P.term[0].eps_s_off;
+    r.eps_x_off = term ? P.term[1].eps_x_off : P.term[0].eps_x_off;
+    return r;
+}
+
+__device__ __forceinline__ TermR decode(const Params& P, int64_t item, int& term, int& t, int& s,
+                                        int& A, int& B) {
     term = item < P.term[0].nitems ? 0 : 1;
-    const Term& tm = P.term[term];
-    int64_t r = item - (term ? P.term[0].nitems : 0);
+    const TermR tm = term_regs(P, term);
+    int64_t r = item - tm.first;
     int64_t per_t = (int64_t)tm.ns * tm.npb;
     t = (int)(r / per_t);
     r -= (int64_t)t * per_t;
     s = (int)(r / tm.npb);
     block_pair(r - (int64_t)s * tm.npb, tm.nb, A, B);
-    return true;
+    return tm;
 }
 
-template <int EC>
+// SEP: hi.hi and the two cross products accumulate in separate TMEM tiles
+// (4 x 128 columns, one buffer); otherwise all three share one tile and two
+// buffers alternate between items.
+template <int EC, bool BF16, bool SEP>
 __global__ void __launch_bounds__(THREADS, 1)
-k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const double* __restrict__ E,
-           const int32_t* __restrict__ active, double* __restrict__ part,
+k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __restrict__ E2,
+           const float2* __restrict__ eps2, const int32_t* __restrict__ active,
+           const float* __restrict__ inv_scale, double* __restrict__ part,
            int32_t* __restrict__ err) {
+    constexpr uint32_t ID = idesc<BF16>();
+    constexpr int NBUF = SEP ? 1 : 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* stages = smem;
@@ -216,7 +263,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const double* __re
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NSTAGE; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], NUM_EPI_WARPS); }
+        for (int i = 0; i < NBUF; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], NUM_EPI_WARPS); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -240,9 +287,8 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const double* __re
             bool ok = true;
             for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
                 int term, t, s, A, B;
-                decode(P, item, term, t, s, A, B);
+                const TermR tm = decode(P, item, term, t, s, A, B);
                 if (active && !active[t]) continue;
-                const Term& tm = P.term[term];
                 const CUtensorMap* mq_hi = &maps.m[term][0];
                 const CUtensorMap* mq_lo = &maps.m[term][1];
                 const CUtensorMap* mb_hi = &maps.m[term][2];
@@ -289,6 +335,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const double* __re
                 if (!mbar_wait(&tempty[acc], aphase ^ 1u, verr)) break;
                 fence_after();
                 const uint32_t d1 = tmem + (uint32_t)acc * 256u, d2 = d1 + 128u;
+                const uint32_t d1x = SEP ? tmem + 256u : d1, d2x = SEP ? tmem + 384u : d2;
                 for (int kb = 0; kb < P.kblocks; ++kb) {
                     if (!mbar_wait(&full[stage], phase, verr)) { ok = false; break; }
                     fence_after();
@@ -303,19 +350,19 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const double* __re
                     for (int kk = 0; kk < KB / 16; ++kk) {
                         const uint32_t off = kk * 32;
                         const uint32_t first = (kb | kk) ? 1u : 0u;
-                        mma_bf16(d1, sdesc(a1h + off), sdesc(b1h + off), first);
-                        mma_bf16(d1, sdesc(a1h + off), sdesc(b1l + off), 1u);
-                        mma_bf16(d1, sdesc(a1l + off), sdesc(b1h + off), 1u);
-                        mma_bf16(d2, sdesc(a2h + off), sdesc(b2h + off), first);
-                        mma_bf16(d2, sdesc(a2h + off), sdesc(b2l + off), 1u);
-                        mma_bf16(d2, sdesc(a2l + off), sdesc(b2h + off), 1u);
+                        mma_f16(d1, sdesc(a1h + off), sdesc(b1h + off), ID, first);
+                        mma_f16(d1x, sdesc(a1h + off), sdesc(b1l + off), ID, SEP ? first : 1u);
+                        mma_f16(d1x, sdesc(a1l + off), sdesc(b1h + off), ID, 1u);
+                        mma_f16(d2, sdesc(a2h + off), sdesc(b2h + off), ID, first);
+                        mma_f16(d2x, sdesc(a2h + off), sdesc(b2l + off), ID, SEP ? first : 1u);
+                        mma_f16(d2x, sdesc(a2l + off), sdesc(b2h + off), ID, 1u);
                     }
                     mma_commit(&empty[stage]);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
                 if (!ok) break;
                 mma_commit(&tfull[acc]);
-                if (++acc == 2) { acc = 0; aphase ^= 1u; }
+                if (++acc == NBUF) { acc = 0; aphase ^= 1u; }
             }
         }
     } else {
@@ -324,70 +371,83 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const double* __re
         const int quad = warp & 3;     // TMEM lanes this warp may read
         const int half = ew >> 2;      // column half of the tile
         const int row = quad * 32 + lane;
+        const float inv = *inv_scale;  // 1 / (s_A s_B) of the 16-bit split
         int acc = 0;
         uint32_t aphase = 0;
         const int nE = P.nE;
         for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
             int term, t, s, A, B;
-            decode(P, item, term, t, s, A, B);
+            const TermR tm = decode(P, item, term, t, s, A, B);
             if (active && !active[t]) continue;
-            const Term& tm = P.term[term];
             const bool bad = !mbar_wait(&tfull[acc], aphase, verr) || *verr;
             if (epi_any(bad)) break;
             fence_after();
             const bool diag = A == B;
             const int x = A * TB + row;
             const bool xok = x < tm.nx;
-            const double es = tm.eps_s[s];
-            const double ex = xok ? tm.eps_x[x] : 0.0;
+            const bool warp_live = A * TB + quad * 32 < tm.nx;   // any valid row in this warp
+            // row part of the denominator, e_s - e_x, as a float pair
+            const float2 es = eps2[tm.eps_s_off + s];
+            const float2 ex = xok ? eps2[tm.eps_x_off + x] : make_float2(0.f, 0.f);
+            const float2 rb = df_add(es, make_float2(-ex.x, -ex.y));
             const uint32_t ta1 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 256u +
                                  (uint32_t)half * 64u;
             const uint32_t ta2 = ta1 + 128u;
             const int ybase = B * TB + half * 64;
-            const double* Et = E + (int64_t)t * nE;
-            double* out = part + (tm.item0 + (item - (term ? P.term[0].nitems : 0))) * (int64_t)nE * 2;
+            const int ncols = min(64, tm.nx - ybase);             // valid columns of this half
+            const float2* Et = E2 + (int64_t)t * nE;
+            const float2* ey2 = eps2 + tm.eps_x_off;
+            double* out = part + (tm.item0 + (item - tm.first)) * (int64_t)nE * 2;
             for (int e0 = 0; e0 < nE; e0 += EC) {
                 const int ne = min(EC, nE - e0);
-                float c[EC], as[EC], ad[EC];
+                // c = E + e_s - e_x as a float pair (hi, lo)
+                float ch[EC], cl[EC], as[EC], ad[EC];
 #pragma unroll
                 for (int e = 0; e < EC; ++e) {
-                    c[e] = e < ne ? (float)(Et[e0 + e] + es - ex) : 1.0f;
+                    const float2 c = df_add(Et[min(e0 + e, nE - 1)], rb);
+                    ch[e] = c.x;
+                    cl[e] = c.y;
                     as[e] = 0.f;
                     ad[e] = 0.f;
                 }
+                if (warp_live) {
 #pragma unroll 1
-                for (int cc = 0; cc < 64; cc += 16) {
-                    float x1[16], x2[16];
-                    tmem_ld16(ta1 + cc, x1);
-                    tmem_ld16(ta2 + cc, x2);
-                    tmem_wait_ld();
-                    float num[16], ey[16];
+                    for (int cc = 0; cc < ncols; cc += 16) {
+                        float x1[16], x2[16];
+                        tmem_ld16(ta1 + cc, x1);
+                        tmem_ld16(ta2 + cc, x2);
+                        if constexpr (SEP) {
+                            float y1[16], y2[16];
+                            tmem_ld16(ta1 + 256u + cc, y1);
+                            tmem_ld16(ta2 + 256u + cc, y2);
+                            tmem_wait_ld();
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int y = ybase + cc + j;
-                        const bool ok = xok && y < tm.nx;
-                        const float a = x1[j], b = x2[j];
-                        const float n = diag ? (2.f * a - b) * a : 2.f * (a * a + b * b - a * b);
-                        num[j] = ok ? n : 0.f;
-                        ey[j] = ok ? (float)tm.eps_x[y] : -1e30f;   // padding: 0 * tiny
-                    }
+                            for (int j = 0; j < 16; ++j) { x1[j] += y1[j]; x2[j] += y2[j]; }
+                        } else {
+                            tmem_wait_ld();
+                        }
+                        float num[16], eh[16], el[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < 16; ++j) {
+                            const int y = ybase + cc + j;
+                            const bool ok = xok && y < tm.nx;
+                            const float a = x1[j] * inv, b = x2[j] * inv;
+                            const float n = diag ? (2.f * a - b) * a : 2.f * (a * a + b * b - a * b);
+                            num[j] = ok ? n : 0.f;
+                            const float2 e2 = ok ? ey2[y] : make_float2(-1e30f, 0.f);  // padding: 0 * tiny
+                            eh[j] = e2.x;
+                            el[j] = e2.y;
+                        }
 #pragma unroll
-                        for (int e = 0; e < EC; ++e) {
-                            const float d = c[e] - ey[j];
-                            float r = rcp_approx(d);
-                            float tt = num[j] * r;
-                            if (fabsf(d) < POLE_GUARD && num[j] != 0.f && e < ne) {
-                                // close to a pole: the denominator in FP64
-                                const double dd = (Et[e0 + e] + es - ex) - tm.eps_x[ybase + cc + j];
-                                const double rr = 1.0 / dd;
-                                const double t64 = (double)num[j] * rr;
-                                tt = (float)t64;
-                                r = (float)rr;
+                        for (int j = 0; j < 16; ++j) {
+#pragma unroll
+                            for (int e = 0; e < EC; ++e) {
+                                const float d = (ch[e] - eh[j]) + (cl[e] - el[j]);
+                                const float r = rcp_approx(d);
+                                const float tt = num[j] * r;
+                                as[e] += tt;
+                                ad[e] = fmaf(-tt, r, ad[e]);
                             }
-                            as[e] += tt;
-                            ad[e] = fmaf(-tt, r, ad[e]);
                         }
                     }
                 }
@@ -423,7 +483,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const double* __re
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
-            if (++acc == 2) { acc = 0; aphase ^= 1u; }
+            if (++acc == NBUF) { acc = 0; aphase ^= 1u; }
         }
     }
 
@@ -436,17 +496,59 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const double* __re
     }
 }
 
-// hi = bf16(x), lo = bf16(x - hi); columns J >= M zero (rows padded to Mp).
-__global__ void k_split_bf16(const double* __restrict__ src, int64_t rows, int32_t M, int32_t Mp,
-                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+// amax[0] = max |x| over n doubles (non-negative doubles order like their bits).
+__global__ void k_absmax(const double* __restrict__ src, int64_t n, unsigned long long* amax) {
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(src[i]));
+    for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(amax, (unsigned long long)__double_as_longlong(m));
+}
+
+// Power-of-two scale with max|s x| <= 1024 (1 for bf16 or an all-zero array).
+__device__ __forceinline__ double split_scale(const unsigned long long* amax, bool bf16) {
+    double m = __longlong_as_double((long long)*amax);
+    if (bf16 || !(m > 0.0)) return 1.0;
+    int ex;
+    frexp(1024.0 / m, &ex);      // 1024/m = f 2^ex, f in [0.5, 1)
+    return ldexp(1.0, ex - 1);
+}
+
+// hi = r(s x), lo = r(s x - hi) in bf16 or fp16; columns J >= M are zero.
+template <typename T>
+__global__ void k_split16(const double* __restrict__ src, int64_t rows, int32_t M, int32_t Mp,
+                          const unsigned long long* __restrict__ amax, T* __restrict__ hi,
+                          T* __restrict__ lo) {
+    constexpr bool BF16 = std::is_same<T, __nv_bfloat16>::value;
+    const double sc = split_scale(amax, BF16);
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= rows * Mp) return;
     int64_t r = e / Mp;
     int J = (int)(e - r * Mp);
-    double x = J < M ? src[r * M + J] : 0.0;
-    __nv_bfloat16 h = __double2bfloat16(x);
-    hi[e] = h;
-    lo[e] = __double2bfloat16(x - (double)__bfloat162float(h));
+    double x = J < M ? src[r * M + J] * sc : 0.0;
+    if constexpr (BF16) {
+        __nv_bfloat16 h = __double2bfloat16(x);
+        hi[e] = h;
+        lo[e] = __double2bfloat16(x - (double)__bfloat162float(h));
+    } else {
+        __half h = __double2half(x);
+        hi[e] = h;
+        lo[e] = __double2half(x - (double)__half2float(h));
+    }
+}
+
+// FP64 values as (hi, lo) float pairs: hi = fl32(x), lo = fl32(x - hi).
+__global__ void k_to_pairs(const double* __restrict__ x, int64_t n, float2* __restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float h = (float)x[i];
+    out[i] = make_float2(h, (float)(x[i] - (double)h));
+}
+
+__global__ void k_inv_scale(const unsigned long long* __restrict__ amax, int bf16, float* inv) {
+    double sa = split_scale(amax, bf16 != 0), sb = split_scale(amax + 1, bf16 != 0);
+    *inv = (float)(1.0 / (sa * sb));
 }
 
 // sigma[t][e] from the per-item partials of both terms; NaN if a wait gave up.
@@ -480,8 +582,12 @@ __global__ void k_tc_reduce(const double* __restrict__ part, int64_t per_t0, int
 }
 
 struct TcLayout {
-    __nv_bfloat16 *lp_hi, *lp_lo, *lov_hi, *lov_lo;
+    uint16_t *lp_hi, *lp_lo, *lov_hi, *lov_lo;   // bf16 or fp16 bit patterns
     double* part;
+    unsigned long long* amax;                    // [2]: max |Lp|, max |Lov|
+    float* inv;                                  // 1 / (s_Lp s_Lov)
+    float2* eps2;                                // orbital energies as float pairs
+    float2* E2;                                  // energies as float pairs
     int32_t* err;
     size_t bytes;
 };
@@ -497,12 +603,16 @@ TcLayout tc_layout(void* ws, int32_t nmo, int32_t nocc, int32_t M, int32_t np, i
     const int32_t Mp = padded(std::max(M, 1)), nv = nmo - nocc;
     Carver c(ws);
     TcLayout l;
-    l.lp_hi = c.take<__nv_bfloat16>((size_t)np * nmo * Mp);
-    l.lp_lo = c.take<__nv_bfloat16>((size_t)np * nmo * Mp);
-    l.lov_hi = c.take<__nv_bfloat16>((size_t)nocc * nv * Mp);
-    l.lov_lo = c.take<__nv_bfloat16>((size_t)nocc * nv * Mp);
+    l.lp_hi = c.take<uint16_t>((size_t)np * nmo * Mp);
+    l.lp_lo = c.take<uint16_t>((size_t)np * nmo * Mp);
+    l.lov_hi = c.take<uint16_t>((size_t)nocc * nv * Mp);
+    l.lov_lo = c.take<uint16_t>((size_t)nocc * nv * Mp);
     int64_t items = tc_items(nocc, nv, np) + tc_items(nv, nocc, np);
     l.part = c.take<double>((size_t)std::max<int64_t>(items, 1) * nE * 2);
+    l.amax = c.take<unsigned long long>(2);
+    l.inv = c.take<float>(2);
+    l.eps2 = c.take<float2>((size_t)nmo);
+    l.E2 = c.take<float2>((size_t)std::max(np, 1) * nE);
     l.err = c.take<int32_t>(4);
     l.bytes = c.off;
     return l;
@@ -521,8 +631,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     return fn;
 }
 
-// 3-D bf16 map {d0 (J, contiguous), d1, d2} with byte strides s1, s2.
-bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
+// 3-D 16-bit map {d0 (J, contiguous), d1, d2} with byte strides s1, s2.
+bool make_map(CUtensorMap* m, bool bf16, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
               uint64_t s1, uint64_t s2, uint32_t b1, uint32_t b2) {
     auto enc = encoder();
     if (!enc) return false;
@@ -530,10 +640,22 @@ bool make_map(CUtensorMap* m, const void* base, uint64_t d0, uint64_t d1, uint64
     cuuint64_t strides[2] = {s1, s2};
     cuuint32_t box[3] = {(cuuint32_t)KB, b1, b2};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides,
+    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+                     const_cast<void*>(base), dims, strides,
                      box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+// Separate hi.hi / cross accumulators (default) or the shared double-buffered
+// form; CDS_TC_SHARED_ACC=1 selects the latter (for comparisons).
+bool separate_accumulators() {
+    static int v = -1;
+    if (v < 0) {
+        const char* e = getenv("CDS_TC_SHARED_ACC");
+        v = (e && e[0] == '1') ? 0 : 1;
+    }
+    return v == 1;
 }
 
 int device_sms() {
@@ -561,28 +683,72 @@ size_t tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int3
     return tc::tc_layout(nullptr, nmo, nocc, M, np, nE).bytes;
 }
 
-int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
-              int32_t np, const double* eps, const double* E, int32_t nE,
-              const int32_t* active, double* sigma, double* dsigma, void* ws,
-              cudaStream_t stream) {
-    using namespace tc;
-    if (!device_ok()) return CDS_ERR_UNSUPPORTED;
-    const int32_t nv = nmo - nocc;
-    const int32_t Mp = padded(std::max(M, 1));
-    TcLayout lay = tc_layout(ws, nmo, nocc, M, np, nE);
-    // split the factors into bf16 hi/lo operand arrays
-    {
-        int64_t n1 = (int64_t)np * nmo * Mp;
-        k_split_bf16<<<(unsigned)((n1 + 255) / 256), 256, 0, stream>>>(Lp, (int64_t)np * nmo, M, Mp,
-                                                                      lay.lp_hi, lay.lp_lo);
+namespace tc {
+template <int EC, bool BF16, bool SEP>
+static int launch_tc(int grid, const Maps& maps, const Params& P, const int32_t* active,
+                     const TcLayout& lay, cudaStream_t stream) {
+    CDS_CUDA_TRY(cudaFuncSetAttribute(k_sigma_tc<EC, BF16, SEP>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+    k_sigma_tc<EC, BF16, SEP><<<grid, THREADS, SMEM_BYTES, stream>>>(
+        maps, P, lay.E2, lay.eps2, active, lay.inv, lay.part, lay.err);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
+template <bool SEP>
+static int launch_any(int grid, bool bf16, int nE, const Maps& maps, const Params& P,
+                      const int32_t* active, const TcLayout& lay, cudaStream_t stream) {
+    if (nE == 1)
+        return bf16 ? launch_tc<1, true, SEP>(grid, maps, P, active, lay, stream)
+                    : launch_tc<1, false, SEP>(grid, maps, P, active, lay, stream);
+    return bf16 ? launch_tc<16, true, SEP>(grid, maps, P, active, lay, stream)
+                : launch_tc<16, false, SEP>(grid, maps, P, active, lay, stream);
+}
+
+template <typename T>
+static int split_all(const double* Lp, const double* Lov, int64_t rows_p, int64_t rows_ov,
+                     int32_t M, int32_t Mp, const TcLayout& lay, cudaStream_t stream) {
+    constexpr bool BF16 = std::is_same<T, __nv_bfloat16>::value;
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.amax, 0, 2 * sizeof(unsigned long long), stream));
+    if (!BF16) {
+        k_absmax<<<4 * 152, 256, 0, stream>>>(Lp, rows_p * M, lay.amax);
         CDS_LAUNCH_CHECK();
-        int64_t n2 = (int64_t)nocc * nv * Mp;
-        if (n2 > 0) {
-            k_split_bf16<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(
-                Lov, (int64_t)nocc * nv, M, Mp, lay.lov_hi, lay.lov_lo);
+        if (rows_ov > 0) {
+            k_absmax<<<4 * 152, 256, 0, stream>>>(Lov, rows_ov * M, lay.amax + 1);
             CDS_LAUNCH_CHECK();
         }
     }
+    int64_t n1 = rows_p * Mp;
+    k_split16<T><<<(unsigned)((n1 + 255) / 256), 256, 0, stream>>>(
+        Lp, rows_p, M, Mp, lay.amax, (T*)lay.lp_hi, (T*)lay.lp_lo);
+    CDS_LAUNCH_CHECK();
+    int64_t n2 = rows_ov * Mp;
+    if (n2 > 0) {
+        k_split16<T><<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(
+            Lov, rows_ov, M, Mp, lay.amax + 1, (T*)lay.lov_hi, (T*)lay.lov_lo);
+        CDS_LAUNCH_CHECK();
+    }
+    k_inv_scale<<<1, 1, 0, stream>>>(lay.amax, BF16 ? 1 : 0, lay.inv);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+}  // namespace tc
+
+int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
+              int32_t np, const double* eps, const double* E, int32_t nE,
+              const int32_t* active, int32_t precision, double* sigma, double* dsigma, void* ws,
+              cudaStream_t stream) {
+    using namespace tc;
+    if (!device_ok()) return CDS_ERR_UNSUPPORTED;
+    const bool bf16 = precision == CDS_PREC_BF16X3;
+    const int32_t nv = nmo - nocc;
+    const int32_t Mp = padded(std::max(M, 1));
+    TcLayout lay = tc_layout(ws, nmo, nocc, M, np, nE);
+    int st = bf16 ? split_all<__nv_bfloat16>(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M, Mp,
+                                             lay, stream)
+                  : split_all<__half>(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M, Mp, lay,
+                                      stream);
+    if (st) return st;
     Params P{};
     Maps maps;
     memset(&maps, 0, sizeof(maps));
@@ -602,16 +768,16 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
         tm.item0 = item0;
         item0 += tm.nitems;
         tm.bulk_s_dim = k == 0 ? 1 : 2;
-        tm.eps_s = k == 0 ? eps + nocc : eps;
-        tm.eps_x = k == 0 ? eps : eps + nocc;
+        tm.eps_s_off = k == 0 ? nocc : 0;
+        tm.eps_x_off = k == 0 ? 0 : nocc;
         if (tm.nitems == 0) continue;
-        const __nv_bfloat16* qb_hi = lay.lp_hi + (k == 0 ? 0 : (size_t)nocc * Mp);
-        const __nv_bfloat16* qb_lo = lay.lp_lo + (k == 0 ? 0 : (size_t)nocc * Mp);
-        bool ok = make_map(&maps.m[k][0], qb_hi, Mp, nx[k], np, rowb, rowb * nmo, TB, 1) &&
-                  make_map(&maps.m[k][1], qb_lo, Mp, nx[k], np, rowb, rowb * nmo, TB, 1) &&
-                  make_map(&maps.m[k][2], lay.lov_hi, Mp, nv, nocc, rowb, rowb * nv,
+        const uint16_t* qb_hi = lay.lp_hi + (k == 0 ? 0 : (size_t)nocc * Mp);
+        const uint16_t* qb_lo = lay.lp_lo + (k == 0 ? 0 : (size_t)nocc * Mp);
+        bool ok = make_map(&maps.m[k][0], bf16, qb_hi, Mp, nx[k], np, rowb, rowb * nmo, TB, 1) &&
+                  make_map(&maps.m[k][1], bf16, qb_lo, Mp, nx[k], np, rowb, rowb * nmo, TB, 1) &&
+                  make_map(&maps.m[k][2], bf16, lay.lov_hi, Mp, nv, nocc, rowb, rowb * nv,
                            k == 0 ? 1 : TB, k == 0 ? TB : 1) &&
-                  make_map(&maps.m[k][3], lay.lov_lo, Mp, nv, nocc, rowb, rowb * nv,
+                  make_map(&maps.m[k][3], bf16, lay.lov_lo, Mp, nv, nocc, rowb, rowb * nv,
                            k == 0 ? 1 : TB, k == 0 ? TB : 1);
         if (!ok) return CDS_ERR_CUDA;
     }
@@ -620,19 +786,16 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
     const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
     CDS_CUDA_TRY(cudaMemsetAsync(lay.err, 0, sizeof(int32_t), stream));
     if (nitems > 0) {
-        int grid = (int)std::min<int64_t>(nitems, device_sms());
-        if (nE == 1) {
-            CDS_CUDA_TRY(cudaFuncSetAttribute(k_sigma_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)SMEM_BYTES));
-            k_sigma_tc<1><<<grid, THREADS, SMEM_BYTES, stream>>>(maps, P, E, active, lay.part, lay.err);
-        } else {
-            CDS_CUDA_TRY(cudaFuncSetAttribute(k_sigma_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              (int)SMEM_BYTES));
-            k_sigma_tc<16><<<grid, THREADS, SMEM_BYTES, stream>>>(maps, P, E, active, lay.part, lay.err);
-        }
+        k_to_pairs<<<(nmo + 255) / 256, 256, 0, stream>>>(eps, nmo, lay.eps2);
         CDS_LAUNCH_CHECK();
-    }
-    if (nitems == 0) {
+        k_to_pairs<<<(unsigned)(((int64_t)np * nE + 255) / 256), 256, 0, stream>>>(E, (int64_t)np * nE,
+                                                                                 lay.E2);
+        CDS_LAUNCH_CHECK();
+        int grid = (int)std::min<int64_t>(nitems, device_sms());
+        st = separate_accumulators() ? launch_any<true>(grid, bf16, nE, maps, P, active, lay, stream)
+                                     : launch_any<false>(grid, bf16, nE, maps, P, active, lay, stream);
+        if (st) return st;
+    } else {
         CDS_CUDA_TRY(cudaMemsetAsync(lay.part, 0, sizeof(double) * 2 * nE, stream));
     }
     const int64_t per0 = np ? P.term[0].nitems / np : 0, per1 = np ? P.term[1].nitems / np : 0;

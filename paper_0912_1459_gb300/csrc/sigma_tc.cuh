@@ -1,4 +1,4 @@
-// Tensor-core (tcgen05, BF16 split-precision) path of the self-energy.
+// Tensor-core (tcgen05, 16-bit split-precision) path of the self-energy.
 #pragma once
 
 #include "sigma.cuh"
@@ -9,8 +9,12 @@ size_t tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int3
 
 int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
               int32_t np, const double* eps, const double* E, int32_t nE,
-              const int32_t* active, double* sigma, double* dsigma, void* ws,
+              const int32_t* active, int32_t precision, double* sigma, double* dsigma, void* ws,
               cudaStream_t stream);
+
+inline bool is_split16(int32_t precision) {
+    return precision == CDS_PREC_BF16X3 || precision == CDS_PREC_FP16X3;
+}
 
 size_t sigma_ws_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE,
                       int32_t precision);

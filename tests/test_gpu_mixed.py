@@ -1,4 +1,4 @@
-"""Split-precision (BF16X3, tcgen05) self-energy and Newton solve vs the FP64 oracle.
+"""Split-precision (BF16X3 / FP16X3, tcgen05) self-energy and Newton solve vs the FP64 oracle.
 
 Bar (the benchmark spec): quasiparticle energies within 0.1 meV = 3.67e-6 Ha of the
 FP64 oracle.  Sigma on the energy grid: |dSigma| <= 3.67e-6 Ha + 1e-5 |Sigma|
@@ -30,14 +30,15 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
 @pytest.mark.parametrize("name,delta,nE", [("c0", 1e-6, 16), ("c0", 1e-6, 1), ("c1", 1e-5, 16),
                                           ("c1", 1e-5, 5)])
-def test_sigma_bf16x3_vs_oracle(name, delta, nE):
+def test_sigma_split_vs_oracle(name, delta, nE, prec):
     m = O.molecule(name)
     ref = O.decomposition(name, delta)
     rov, rp = O.factors(name, ref.L)
     E = W.energy_grid(m.eps[m.orbitals], nE)
-    s, ds = G.cds_sigma2_diag(dev(rov), dev(rp), dev(m.eps), m.nocc, dev(E), "bf16x3")
+    s, ds = G.cds_sigma2_diag(dev(rov), dev(rp), dev(m.eps), m.nocc, dev(E), prec)
     rs, rds = O.sigma(name, rov, rp, E)
     s = s.cpu().numpy()
     ds = ds.cpu().numpy()
@@ -47,23 +48,25 @@ def test_sigma_bf16x3_vs_oracle(name, delta, nE):
     assert np.all(np.abs(ds - rds) <= 1e-5 * (1 + np.abs(rds)))
 
 
-def test_sigma_bf16x3_matches_fp64_gpu_path():
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+def test_sigma_split_matches_fp64_gpu_path(prec):
     m = O.molecule("c1")
     ref = O.decomposition("c1", 1e-5)
     rov, rp = O.factors("c1", ref.L)
     E = W.energy_grid(m.eps[m.orbitals], 3, 0.02)
     a, _ = G.cds_sigma2_diag(dev(rov), dev(rp), dev(m.eps), m.nocc, dev(E), "fp64")
-    b, _ = G.cds_sigma2_diag(dev(rov), dev(rp), dev(m.eps), m.nocc, dev(E), "bf16x3")
+    b, _ = G.cds_sigma2_diag(dev(rov), dev(rp), dev(m.eps), m.nocc, dev(E), prec)
     assert np.abs(a.cpu().numpy() - b.cpu().numpy()).max() <= TOL_QP
 
 
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
 @pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-5)])
-def test_qp_bf16x3_within_tenth_of_mev(name, delta):
+def test_qp_split_within_tenth_of_mev(name, delta, prec):
     m = O.molecule(name)
     ref = O.decomposition(name, delta)
     rov, rp = O.factors(name, ref.L)
     w, P, it, st = G.cds_qp_solve(dev(rov), dev(rp), dev(m.orbitals), dev(m.eps), m.nocc,
-                                  conv=1e-5, max_iter=50, precision="bf16x3")
+                                  conv=1e-5, max_iter=50, precision=prec)
     res = O.solve(name, rov, rp, m.orbitals)
     w = w.cpu().numpy()
     st = st.cpu().numpy()
