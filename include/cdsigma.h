@@ -47,7 +47,8 @@ typedef enum {
     CDS_ERR_NO_CONVERGENCE = 5, /* a Newton solve did not converge in max_iter */
     CDS_ERR_WORKSPACE = 6,      /* workspace smaller than *_workspace_bytes() */
     CDS_ERR_UNSUPPORTED = 7,    /* device or precision mode not supported */
-    CDS_ERR_TIMEOUT = 8         /* a bounded device-side wait gave up */
+    CDS_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up */
+    CDS_ERR_CAPACITY = 9        /* problem too large for the allocation-free entry point */
 } cds_status;
 
 typedef enum { CDS_SCHEME_FULL = 0, CDS_SCHEME_ATOMIC = 1 } cds_scheme;
@@ -124,6 +125,32 @@ int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
                      double* L, int32_t* piv, double* D, int32_t* M_out,
                      double* delta_eff_out, void* workspace, size_t workspace_bytes,
                      cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Allocation-free Cholesky decomposition.  The paper has no counterpart: this
+ * is a service for callers that cannot allocate device memory where they call
+ * (GPU memory owned by another runtime or pool they cannot reach, a plugin
+ * that must not grow the device footprint).  Same arguments, semantics and
+ * results as cds_cd_decompose, without the workspace: the scratch is a fixed
+ * device array inside the library (CDS_CD_STATIC_SCRATCH_BYTES, held on every
+ * GPU that loads the library until the process exits).  The call allocates
+ * nothing (no cudaMalloc, no library allocator).  Its first call on a device
+ * resolves the array's device address with that device current; make that
+ * first call before any stream capture.  Calls share the array: two calls
+ * whose GPU work overlaps race.  Returns CDS_ERR_CAPACITY when the basis needs
+ * more scratch than the array holds (nbf > cds_cd_static_max_nbf()).
+ * ---------------------------------------------------------------------- */
+
+#define CDS_CD_STATIC_SCRATCH_BYTES (4u << 20)
+
+/* Blocking; see cds_cd_decompose for the arguments. */
+int cds_cd_decompose_static(int32_t nbf, const double* xyz, const double* alpha,
+                            const int32_t* atom, double delta, int32_t scheme, int32_t max_rank,
+                            double* L, int32_t* piv, double* D, int32_t* M_out,
+                            double* delta_eff_out, cudaStream_t stream);
+
+/* Largest basis the allocation-free entry point accepts (host only). */
+int cds_cd_static_max_nbf(void);
 
 /* ------------------------------------------------------------------------
  * AO -> MO transform of the Cholesky vectors (paper Eq. transformation):

@@ -23,7 +23,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "cdsigma.h")
 CDS_OK = 0
 STATUS_NAMES = {0: "CDS_OK", 1: "CDS_ERR_ARG", 2: "CDS_ERR_CUDA", 3: "CDS_ERR_NOT_PD",
                 4: "CDS_ERR_RANK_CAP", 5: "CDS_ERR_NO_CONVERGENCE", 6: "CDS_ERR_WORKSPACE",
-                7: "CDS_ERR_UNSUPPORTED", 8: "CDS_ERR_TIMEOUT"}
+                7: "CDS_ERR_UNSUPPORTED", 8: "CDS_ERR_TIMEOUT", 9: "CDS_ERR_CAPACITY"}
 SCHEMES = {"full": 0, "atomic": 1}
 PRECISIONS = {"fp64": 0, "bf16x3": 2, "fp16x3": 3}
 QP_OK, QP_NO_CONVERGENCE, QP_NONFINITE = 0, 1, 2
@@ -41,6 +41,10 @@ _SIGNATURES = {
     "cds_cd_decompose": (ctypes.c_int, [_i32, _vp, _vp, _vp, _f64, _i32, _i32, _vp, _vp, _vp,
                                         ctypes.POINTER(_i32), ctypes.POINTER(_f64), _vp, _sz,
                                         _vp]),
+    "cds_cd_decompose_static": (ctypes.c_int, [_i32, _vp, _vp, _vp, _f64, _i32, _i32, _vp, _vp,
+                                               _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f64),
+                                               _vp]),
+    "cds_cd_static_max_nbf": (ctypes.c_int, []),
     "cds_cd_to_mo_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "cds_cd_to_mo": (ctypes.c_int, [_i32, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp,
                                     _sz, _vp]),
@@ -184,6 +188,32 @@ def cds_cd_decompose(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,
                               ctypes.byref(de), _p(workspace), workspace.numel(), _stream(dev))
     _check(st, "cds_cd_decompose")
     return L_out[:M.value], piv[:M.value], D, de.value
+
+
+def cds_cd_decompose_static(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,
+                            delta: float, scheme: str, L_out: torch.Tensor, piv_out: torch.Tensor,
+                            D_out: torch.Tensor):
+    """The allocation-free decomposition: outputs are caller tensors
+    (L_out [max_rank, npair] float64, piv_out [max_rank] int32, D_out [npair]
+    float64); the library's fixed device scratch replaces the workspace.
+    Returns (M, delta_eff)."""
+    lib = load()
+    xyz = _dev(xyz, torch.float64, "xyz")
+    alpha = _dev(alpha, torch.float64, "alpha")
+    atom = _dev(atom, torch.int32, "atom")
+    for t, dt, nm in ((L_out, torch.float64, "L_out"), (piv_out, torch.int32, "piv_out"),
+                      (D_out, torch.float64, "D_out")):
+        if not (t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise ValueError(f"{nm} must be a contiguous CUDA {dt} tensor")
+    n = alpha.shape[0]
+    M = _i32(0)
+    de = _f64(0.0)
+    st = lib.cds_cd_decompose_static(n, _p(xyz), _p(alpha), _p(atom), float(delta),
+                                     SCHEMES[scheme], int(L_out.shape[0]), _p(L_out),
+                                     _p(piv_out), _p(D_out), ctypes.byref(M), ctypes.byref(de),
+                                     _stream(alpha.device))
+    _check(st, "cds_cd_decompose_static")
+    return M.value, de.value
 
 
 def cds_cd_to_mo(L: torch.Tensor, C: torch.Tensor, nocc: int, orbitals: torch.Tensor,

@@ -23,6 +23,7 @@ extern "C" const char* cds_errstr(int status) {
         case CDS_ERR_WORKSPACE: return "workspace too small";
         case CDS_ERR_UNSUPPORTED: return "unsupported device or precision";
         case CDS_ERR_TIMEOUT: return "bounded device wait gave up";
+        case CDS_ERR_CAPACITY: return "problem exceeds the allocation-free scratch array";
         default: return "unknown status";
     }
 }
