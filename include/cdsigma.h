@@ -61,7 +61,13 @@ typedef enum { CDS_SCHEME_FULL = 0, CDS_SCHEME_ATOMIC = 1 } cds_scheme;
  *   Denominators are double-fp32 pairs, per-element sums fp32, cross-tile sums
  *   and the Newton step fp64.  FP16X3 carries ~22 significant bits per factor,
  *   BF16X3 ~17. */
-typedef enum { CDS_PREC_FP64 = 0, CDS_PREC_BF16X3 = 2, CDS_PREC_FP16X3 = 3 } cds_precision;
+typedef enum {
+    CDS_PREC_FP64 = 0,
+    CDS_PREC_BF16X3 = 2,
+    CDS_PREC_FP16X3 = 3,
+    CDS_PREC_F32X2 = 4   /* transform only: (hi, lo) float pairs with exact product and sum
+                            errors, ~2^-44 relative per operation, on the FP32 units */
+} cds_precision;
 
 /* Newton status per orbital (paper Eq. NR). */
 enum { CDS_QP_OK = 0, CDS_QP_NO_CONVERGENCE = 1, CDS_QP_NONFINITE = 2 };
@@ -160,11 +166,13 @@ int cds_cd_static_max_nbf(void);
 size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, int32_t np);
 
 /* Asynchronous.  L: device [M][npair]; C: device [nbf][nmo]; orb: device [np]
- * int32 MO indices in [0, nmo).  Outputs (device): Lov [nocc][nmo-nocc][M],
- * Lp [np][nmo][M] (Lp may be NULL when np == 0). */
+ * int32 MO indices in [0, nmo).  precision: CDS_PREC_FP64 or CDS_PREC_F32X2.
+ * Outputs (device, fp64): Lov [nocc][nmo-nocc][M], Lp [np][nmo][M] (Lp may be
+ * NULL when np == 0). */
 int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
-              const double* C, const int32_t* orb, int32_t np, double* Lov, double* Lp,
-              void* workspace, size_t workspace_bytes, cudaStream_t stream);
+                 const double* C, const int32_t* orb, int32_t np, int32_t precision,
+                 double* Lov, double* Lp, void* workspace, size_t workspace_bytes,
+                 cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * Diagonal second-order self-energy (paper Eq. SE) and its energy derivative

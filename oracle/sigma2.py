@@ -5,8 +5,8 @@ Eq. SE (spatial orbitals, i, j occupied; a, b virtual):
   Sigma_qq(w) = sum_{i,j,a} (2(qi|aj) - (qj|ai)) (qi|aj) / (w + e_a - e_i - e_j)
               + sum_{i,a,b} (2(qa|ib) - (qb|ia)) (qa|ib) / (w + e_i - e_a - e_b)
 
-with the MO integrals recomputed from the Cholesky factors by Eq. aomo
-(Sec. III: "ERIs needed during the iterative solution are recomputed").
+with the MO integrals recomputed from the Cholesky factors by Eq. aomo at
+every evaluation, as the paper does in its Newton iterations (Sec. III).
 The pole strength of Eq. ps needs dSigma/dw, taken analytically:
 dSigma/dw = - sum numerator / denominator^2.
 

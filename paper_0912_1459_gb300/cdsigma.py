@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "CDS_OK", 1: "CDS_ERR_ARG", 2: "CDS_ERR_CUDA", 3: "CDS_ERR_NO
                 4: "CDS_ERR_RANK_CAP", 5: "CDS_ERR_NO_CONVERGENCE", 6: "CDS_ERR_WORKSPACE",
                 7: "CDS_ERR_UNSUPPORTED", 8: "CDS_ERR_TIMEOUT", 9: "CDS_ERR_CAPACITY"}
 SCHEMES = {"full": 0, "atomic": 1}
-PRECISIONS = {"fp64": 0, "bf16x3": 2, "fp16x3": 3}
+PRECISIONS = {"fp64": 0, "bf16x3": 2, "fp16x3": 3, "f32x2": 4}
 QP_OK, QP_NO_CONVERGENCE, QP_NONFINITE = 0, 1, 2
 
 _lib: Optional[ctypes.CDLL] = None
@@ -46,8 +46,8 @@ _SIGNATURES = {
                                                _vp]),
     "cds_cd_static_max_nbf": (ctypes.c_int, []),
     "cds_cd_to_mo_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
-    "cds_cd_to_mo": (ctypes.c_int, [_i32, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp,
-                                    _sz, _vp]),
+    "cds_cd_to_mo": (ctypes.c_int, [_i32, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _i32, _vp, _vp,
+                                    _vp, _sz, _vp]),
     "cds_sigma2_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32, _i32]),
     "cds_sigma2_diag": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _i32,
                                        _vp, _vp, _vp, _sz, _vp]),
@@ -217,9 +217,10 @@ def cds_cd_decompose_static(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.
 
 
 def cds_cd_to_mo(L: torch.Tensor, C: torch.Tensor, nocc: int, orbitals: torch.Tensor,
-                 workspace: Optional[torch.Tensor] = None):
+                 workspace: Optional[torch.Tensor] = None, precision: str = "fp64"):
     """AO->MO transform of the Cholesky vectors (paper Eq. transformation).
 
+    precision: "fp64" or "f32x2" (float-pair arithmetic on the FP32 units).
     Returns (Lov [o, v, M], Lp [np, nmo, M])."""
     lib = load()
     L = _dev(L, torch.float64, "L")
@@ -234,8 +235,9 @@ def cds_cd_to_mo(L: torch.Tensor, C: torch.Tensor, nocc: int, orbitals: torch.Te
     need = lib.cds_cd_to_mo_workspace_bytes(nbf, nmo, nocc, M, np_)
     if workspace is None or workspace.numel() < need:
         workspace = _workspace(need, dev)
-    _check(lib.cds_cd_to_mo(nbf, nmo, nocc, M, _p(L), _p(C), _p(orb), np_, _p(Lov), _p(Lp),
-                            _p(workspace), workspace.numel(), _stream(dev)), "cds_cd_to_mo")
+    _check(lib.cds_cd_to_mo(nbf, nmo, nocc, M, _p(L), _p(C), _p(orb), np_, PRECISIONS[precision],
+                            _p(Lov), _p(Lp), _p(workspace), workspace.numel(), _stream(dev)),
+           "cds_cd_to_mo")
     return Lov, Lp
 
 

@@ -6,6 +6,14 @@
 // (o x v), and the same for the requested orbital rows with C_P.  The second
 // GEMM writes straight into the K-innermost layouts Lov[i][a][K], Lp[t][r][K].
 // On this part FP64 issue rate, not HBM, bounds the transform.
+//
+// F32X2 (double-FP32) form for the split-precision pipeline: every operand is
+// held as an (hi, lo) pair of floats (hi = fl32(x), lo = fl32(x - hi)) and
+// every multiply-add keeps the exact product error (FMA) and the exact sum
+// error (two-sum), ~2^-44 relative per operation on the 78 TFLOP/s FP32
+// units instead of the 1.25 TFLOP/s FP64 ones.  Tensor-core splits cannot
+// serve here: C = S^-1/2 Q has |C| up to ~1e3, the transform cancels ~1e6
+// relative, and the tensor-core FP32 accumulation truncates.
 #include "common.cuh"
 
 namespace cds {
@@ -81,6 +89,126 @@ k_dgemm(int m, int n, int k, StridedMat A, StridedMat B, StridedOut C) {
     }
 }
 
+struct PairMat {
+    const float2* p;
+    int64_t rs, cs, bs;
+};
+template <typename T>
+struct OutMat {
+    T* p;
+    int64_t rs, cs, bs;
+};
+
+// acc += a * b in (hi, lo) float-pair arithmetic.
+__device__ __forceinline__ void df_fma(float2& acc, float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float pe = fmaf(a.x, b.x, -p);        // exact error of the leading product
+    pe = fmaf(a.x, b.y, pe);
+    pe = fmaf(a.y, b.x, pe);
+    const float s = acc.x + p;            // two-sum of the leading parts
+    const float bp = s - acc.x;
+    const float err = (acc.x - (s - bp)) + (p - bp);
+    acc.x = s;
+    acc.y += err + pe;
+}
+
+__device__ __forceinline__ void store_out(double* p, float2 v) { p[0] = (double)v.x + (double)v.y; }
+__device__ __forceinline__ void store_out(float2* p, float2 v) {
+    const float h = v.x + v.y;
+    p[0] = make_float2(h, v.y - (h - v.x));
+}
+
+// C[b] = A[b] * B[b] in float-pair arithmetic; same tiling as k_dgemm.
+template <bool A_M_CONTIG, bool B_N_CONTIG, typename TOut>
+__global__ void __launch_bounds__(256)
+k_dfgemm(int m, int n, int k, PairMat A, PairMat B, OutMat<TOut> C) {
+    __shared__ float2 As[kGK][kGB + 1];
+    __shared__ float2 Bs[kGK][kGB + 1];
+    const int tid = threadIdx.x;
+    const int tr = tid / 16, tc = tid % 16;
+    const int m0 = blockIdx.y * kGB, n0 = blockIdx.x * kGB;
+    const int64_t b = blockIdx.z;
+    const float2* Ab = A.p + b * A.bs;
+    const float2* Bb = B.p + b * B.bs;
+    const float2 zero = make_float2(0.f, 0.f);
+    float2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = zero;
+    for (int k0 = 0; k0 < k; k0 += kGK) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int idx = tid + 256 * r;
+            int mm, kk;
+            if (A_M_CONTIG) { mm = idx % kGB; kk = idx / kGB; }
+            else { kk = idx % kGK; mm = idx / kGK; }
+            int gm = m0 + mm, gk = k0 + kk;
+            As[kk][mm] = (gm < m && gk < k) ? Ab[gm * A.rs + gk * A.cs] : zero;
+            int nn;
+            if (B_N_CONTIG) { nn = idx % kGB; kk = idx / kGB; }
+            else { kk = idx % kGK; nn = idx / kGK; }
+            int gn = n0 + nn;
+            gk = k0 + kk;
+            Bs[kk][nn] = (gn < n && gk < k) ? Bb[gk * B.rs + gn * B.cs] : zero;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kGK; ++kk) {
+            float2 a[4], bb[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tr + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tc + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) df_fma(acc[i][j], a[i], bb[j]);
+        }
+        __syncthreads();
+    }
+    TOut* Cb = C.p + b * C.bs;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int gm = m0 + tr + 16 * i;
+        if (gm >= m) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int gn = n0 + tc + 16 * j;
+            if (gn < n) store_out(Cb + gm * C.rs + gn * C.cs, acc[i][j]);
+        }
+    }
+}
+
+__device__ __forceinline__ float2 to_pair(double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
+// U[b][mu][nu] = pair(L[K0+b][pair(mu,nu)])
+__global__ void k_unpack_pairs(const double* __restrict__ L, int64_t npair, int32_t K0,
+                               int32_t kb, int32_t N, float2* __restrict__ U) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t per = (int64_t)N * N;
+    if (e >= per * kb) return;
+    int b = (int)(e / per);
+    int64_t r = e - b * per;
+    int mu = (int)(r / N), nu = (int)(r - (int64_t)mu * N);
+    int lo = min(mu, nu), hi = max(mu, nu);
+    U[e] = to_pair(L[(int64_t)(K0 + b) * npair + (int64_t)hi * (hi + 1) / 2 + lo]);
+}
+
+// Cq[mu][j] = pair(C[mu][col(j)]) with col(j) = j (all MOs) or orb[j].
+__global__ void k_pair_cols(const double* __restrict__ C, int32_t N, int32_t nmo,
+                            const int32_t* __restrict__ orb, int32_t ncol, float2* __restrict__ Cq) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * ncol) return;
+    int mu = e / ncol, j = e % ncol;
+    int p = orb ? orb[j] : j;
+    Cq[e] = (p >= 0 && p < nmo) ? to_pair(C[(int64_t)mu * nmo + p])
+                                : make_float2(__int_as_float(0x7fc00000), 0.f);
+}
+
 // U[b][mu][nu] = L[K0+b][pair(mu,nu)]
 __global__ void k_unpack(const double* __restrict__ L, int64_t npair, int32_t K0, int32_t kb,
                          int32_t N, double* __restrict__ U) {
@@ -114,21 +242,79 @@ static int launch_dgemm(int m, int n, int k, int batch, StridedMat A, StridedMat
     return CDS_OK;
 }
 
+template <bool AM, bool BN, typename TOut>
+static int launch_dfgemm(int m, int n, int k, int batch, PairMat A, PairMat B, OutMat<TOut> C,
+                         cudaStream_t s) {
+    if (m <= 0 || n <= 0 || batch <= 0) return CDS_OK;
+    dim3 grid((n + kGB - 1) / kGB, (m + kGB - 1) / kGB, batch);
+    k_dfgemm<AM, BN, TOut><<<grid, 256, 0, s>>>(m, n, k, A, B, C);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
 struct AoLayout {
-    double* U;    // [kb][N][N]
+    double* U;    // [kb][N][N]             (float pairs in the F32X2 form)
     double* T;    // [kb][max(o, np)][N]
     double* Cp;   // [N][np]
+    double* Cq;   // [N][nmo] float pairs of C (F32X2 form)
     size_t bytes;
 };
 
-static AoLayout ao_layout(void* ws, int32_t nbf, int32_t nocc, int32_t np) {
+static AoLayout ao_layout(void* ws, int32_t nbf, int32_t nmo, int32_t nocc, int32_t np) {
     Carver c(ws);
     AoLayout l;
     l.U = c.take<double>((size_t)kAoBatch * nbf * nbf);
     l.T = c.take<double>((size_t)kAoBatch * std::max(nocc, np) * nbf);
     l.Cp = c.take<double>((size_t)nbf * std::max(np, 1));
+    l.Cq = c.take<double>((size_t)nbf * nmo);
     l.bytes = c.off;
     return l;
+}
+
+// The float-pair transform: same blocks and layouts as the FP64 one.
+static int cd_to_mo_f32x2(int32_t N, int32_t nmo, int32_t nocc, int32_t M, const double* L,
+                          const double* C, const int32_t* orb, int32_t np, double* Lov,
+                          double* Lp, const AoLayout& lay, cudaStream_t stream) {
+    const int64_t npair = npair_of(N);
+    const int32_t nv = nmo - nocc;
+    float2* Cq = reinterpret_cast<float2*>(lay.Cq);
+    float2* Cp = reinterpret_cast<float2*>(lay.Cp);
+    float2* U = reinterpret_cast<float2*>(lay.U);
+    float2* T = reinterpret_cast<float2*>(lay.T);
+    k_pair_cols<<<(N * nmo + 255) / 256, 256, 0, stream>>>(C, N, nmo, nullptr, nmo, Cq);
+    CDS_LAUNCH_CHECK();
+    if (np > 0) {
+        k_pair_cols<<<(N * np + 255) / 256, 256, 0, stream>>>(C, N, nmo, orb, np, Cp);
+        CDS_LAUNCH_CHECK();
+    }
+    for (int32_t K0 = 0; K0 < M; K0 += kAoBatch) {
+        int32_t kb = std::min(kAoBatch, M - K0);
+        int64_t tot = (int64_t)kb * N * N;
+        k_unpack_pairs<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(L, npair, K0, kb, N, U);
+        CDS_LAUNCH_CHECK();
+        PairMat Um{U, N, 1, (int64_t)N * N};
+        if (nocc > 0 && nv > 0) {
+            int st = launch_dfgemm<true, true, float2>(nocc, N, N, kb, PairMat{Cq, 1, nmo, 0}, Um,
+                                                       OutMat<float2>{T, N, 1, (int64_t)nocc * N},
+                                                       stream);
+            if (st) return st;
+            st = launch_dfgemm<false, true, double>(
+                nocc, nv, N, kb, PairMat{T, N, 1, (int64_t)nocc * N}, PairMat{Cq + nocc, nmo, 1, 0},
+                OutMat<double>{Lov + K0, (int64_t)nv * M, M, 1}, stream);
+            if (st) return st;
+        }
+        if (np > 0) {
+            int st = launch_dfgemm<true, true, float2>(np, N, N, kb, PairMat{Cp, 1, np, 0}, Um,
+                                                       OutMat<float2>{T, N, 1, (int64_t)np * N},
+                                                       stream);
+            if (st) return st;
+            st = launch_dfgemm<false, true, double>(
+                np, nmo, N, kb, PairMat{T, N, 1, (int64_t)np * N}, PairMat{Cq, nmo, 1, 0},
+                OutMat<double>{Lp + K0, (int64_t)nmo * M, M, 1}, stream);
+            if (st) return st;
+        }
+    }
+    return CDS_OK;
 }
 
 }  // namespace cds
@@ -137,21 +323,24 @@ using namespace cds;
 
 extern "C" size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M,
                                             int32_t np) {
-    (void)nmo; (void)M;
+    (void)M;
     if (nbf <= 0 || nocc < 0 || np < 0) return 0;
-    return ao_layout(nullptr, nbf, nocc, np).bytes;
+    return ao_layout(nullptr, nbf, nmo, nocc, np).bytes;
 }
 
 extern "C" int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
-                         const double* C, const int32_t* orb, int32_t np, double* Lov,
-                         double* Lp, void* workspace, size_t workspace_bytes,
+                         const double* C, const int32_t* orb, int32_t np, int32_t precision,
+                         double* Lov, double* Lp, void* workspace, size_t workspace_bytes,
                          cudaStream_t stream) {
     if (nbf <= 0 || nmo <= 0 || nmo > nbf || nocc < 0 || nocc > nmo || M < 0 || np < 0)
         return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return CDS_ERR_UNSUPPORTED;
     if (M == 0) return CDS_OK;
     if (!L || !C || !Lov || (np > 0 && (!orb || !Lp))) return CDS_ERR_ARG;
-    AoLayout lay = ao_layout(workspace, nbf, nocc, np);
+    AoLayout lay = ao_layout(workspace, nbf, nmo, nocc, np);
     if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    if (precision == CDS_PREC_F32X2)
+        return cd_to_mo_f32x2(nbf, nmo, nocc, M, L, C, orb, np, Lov, Lp, lay, stream);
     const int64_t npair = npair_of(nbf);
     const int32_t N = nbf, nv = nmo - nocc;
     if (np > 0) {

@@ -16,7 +16,8 @@
 
 namespace cds {
 
-constexpr int kCdThreads = 256;
+constexpr int kCdThreads = 128;
+constexpr int kCdPairs = 2;      // pairs per thread in k_cd_update
 constexpr int kCdChunk = 2048;   // pivot row L^K_P staged in shared memory in chunks
 constexpr double kTieRel = 1e-12;
 constexpr double kNotPdRel = 1e-10;
@@ -195,6 +196,8 @@ __global__ void k_cd_select(int64_t n, int32_t k, int32_t max_rank,
 }
 
 // Vector k from pivot P: column, left-looking projection, residual update.
+// Each thread owns kCdPairs pairs, blockDim.x * kCdPairs apart, so one grid of
+// ~npair / (kCdThreads * kCdPairs) small blocks is resident in a single wave.
 __global__ void __launch_bounds__(kCdThreads)
 k_cd_update(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L, double* __restrict__ D,
             const uint8_t* __restrict__ cand, double* __restrict__ blk_a,
@@ -204,39 +207,55 @@ k_cd_update(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L, double* __
     const int64_t P = ctrl->P;
     const double DP = ctrl->DP;
     const double q = pd.p[P], qx = pd.Px[P], qy = pd.Py[P], qz = pd.Pz[P], kq = pd.K[P];
-    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const bool live = I < n;
-    double dot = 0.0;
-    const double* Lcol = L + (live ? I : 0);
+    const int64_t I0 = (int64_t)blockIdx.x * blockDim.x * kCdPairs + threadIdx.x;
+    int64_t Is[kCdPairs];
+    bool live[kCdPairs];
+#pragma unroll
+    for (int r = 0; r < kCdPairs; ++r) {
+        Is[r] = I0 + (int64_t)r * blockDim.x;
+        live[r] = Is[r] < n;
+    }
+    // 4 independent partial sums per pair: 8 loads of L in flight per thread
+    double dot[kCdPairs][4] = {};
+    int64_t Ic[kCdPairs];
+#pragma unroll
+    for (int r = 0; r < kCdPairs; ++r) Ic[r] = live[r] ? Is[r] : 0;   // dead lanes read pair 0
     for (int K0 = 0; K0 < k; K0 += kCdChunk) {
         int kc = min(kCdChunk, k - K0);
         __syncthreads();
         for (int j = threadIdx.x; j < kc; j += blockDim.x) lp[j] = L[(int64_t)(K0 + j) * n + P];
         __syncthreads();
-        if (live) {
-            const double* src = Lcol + (int64_t)K0 * n;
-            int j = 0;
-            double d0 = 0, d1 = 0, d2 = 0, d3 = 0;
-            for (; j + 4 <= kc; j += 4) {
-                d0 = fma(src[(int64_t)(j + 0) * n], lp[j + 0], d0);
-                d1 = fma(src[(int64_t)(j + 1) * n], lp[j + 1], d1);
-                d2 = fma(src[(int64_t)(j + 2) * n], lp[j + 2], d2);
-                d3 = fma(src[(int64_t)(j + 3) * n], lp[j + 3], d3);
+        const double* src = L + (int64_t)K0 * n;
+        int j = 0;
+        for (; j + 4 <= kc; j += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const double lu = lp[j + u];
+                const double* row = src + (int64_t)(j + u) * n;
+#pragma unroll
+                for (int r = 0; r < kCdPairs; ++r) dot[r][u] = fma(row[Ic[r]], lu, dot[r][u]);
             }
-            for (; j < kc; ++j) d0 = fma(src[(int64_t)j * n], lp[j], d0);
-            dot += (d0 + d1) + (d2 + d3);
+        }
+        for (; j < kc; ++j) {
+#pragma unroll
+            for (int r = 0; r < kCdPairs; ++r)
+                dot[r][0] = fma(src[(int64_t)j * n + Ic[r]], lp[j], dot[r][0]);
         }
     }
     double mx = -INFINITY, mn = INFINITY;
-    if (live) {
+    const double rs = sqrt(DP);
+#pragma unroll
+    for (int r = 0; r < kCdPairs; ++r) {
+        if (!live[r]) continue;
+        const int64_t I = Is[r];
         double e = eri_pair(pd.p[I], pd.Px[I], pd.Py[I], pd.Pz[I], pd.K[I], q, qx, qy, qz, kq);
-        double l = (e - dot) / sqrt(DP);
+        double l = (e - ((dot[r][0] + dot[r][1]) + (dot[r][2] + dot[r][3]))) / rs;
         L[(int64_t)k * n + I] = l;
         double d = D[I] - l * l;
         if (I == P) d = 0.0;
         D[I] = d;
-        if (cand[I]) mx = fmax(d, 0.0);
-        mn = d;
+        if (cand[I]) mx = fmax(mx, fmax(d, 0.0));
+        mn = fmin(mn, d);
     }
     block_maxmin(mx, mn);
     if (threadIdx.x == 0) { blk_a[blockIdx.x] = mx; blk_b[blockIdx.x] = mn; }
@@ -266,6 +285,9 @@ struct CdLayout {
 };
 
 static int cd_blocks(int64_t n) { return (int)((n + kCdThreads - 1) / kCdThreads); }
+static int upd_blocks(int64_t n) {
+    return (int)((n + (int64_t)kCdThreads * kCdPairs - 1) / ((int64_t)kCdThreads * kCdPairs));
+}
 static int sel_blocks(int64_t n) { return (int)std::min<int64_t>(4 * 152, (n + kCdThreads - 1) / kCdThreads); }
 
 static CdLayout cd_layout(void* ws, int32_t nbf) {
@@ -312,7 +334,7 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
     int st = build_pairs(nbf, xyz, alpha, lay.pd, stream);
     if (st) return st;
     CDS_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, sizeof(CdCtrl), stream));
-    int nb = cd_blocks(n), ns = sel_blocks(n);
+    int nb = cd_blocks(n), ns = sel_blocks(n), nu = upd_blocks(n);
     k_cd_init<<<nb, kCdThreads, 0, stream>>>(lay.pd, atom, scheme, n, delta, D, lay.cand,
                                             lay.blk_a, lay.blk_b, lay.ctrl);
     CDS_LAUNCH_CHECK();
@@ -323,7 +345,7 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
     for (int32_t k0 = 0; k0 <= max_rank; k0 += kHostCheckEvery) {
         int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
         for (int32_t k = k0; k < k1; ++k) {
-            k_cd_update<<<nb, kCdThreads, 0, stream>>>(lay.pd, n, k, L, D, lay.cand, lay.blk_a,
+            k_cd_update<<<nu, kCdThreads, 0, stream>>>(lay.pd, n, k, L, D, lay.cand, lay.blk_a,
                                                       lay.blk_b, lay.ctrl);
             k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, k + 1, max_rank, D, lay.cand,
                                                       lay.blk_i, piv, lay.ctrl);

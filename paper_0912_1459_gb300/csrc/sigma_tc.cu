@@ -48,7 +48,10 @@ constexpr int NUM_EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * NUM_EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
-constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 256 + NUM_EPI_WARPS * 16 * 2 * 4;
+constexpr int RED_E = 64;                     // energies reduced per CTA barrier pair
+constexpr int EPS_SMEM = 2048;                // orbital-energy pairs staged in shared memory
+constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 256 + NUM_EPI_WARPS * RED_E * 2 * 4 +
+                              EPS_SMEM * 8;
 
 // kind::f16 instruction descriptor: D f32, A/B bf16 (format 1) or fp16
 // (format 0), both K-major, M = N = 128.
@@ -72,6 +75,7 @@ struct Params {
     Term term[2];
     int32_t kblocks;
     int32_t nE;
+    int32_t nmo;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -255,7 +259,8 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
     uint64_t* tfull = bars + 2 * NSTAGE;
     uint64_t* tempty = tfull + 2;
     uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
-    float* red = (float*)(smem + NSTAGE * STAGE_BYTES + 256);   // [8 warps][16][2]
+    float* red = (float*)(smem + NSTAGE * STAGE_BYTES + 256);   // [8 warps][RED_E][2]
+    float2* seps = (float2*)(red + NUM_EPI_WARPS * RED_E * 2);   // [EPS_SMEM]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
@@ -375,6 +380,13 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
         int acc = 0;
         uint32_t aphase = 0;
         const int nE = P.nE;
+        // orbital energies as float pairs, from shared memory when they fit
+        const float2* epsv = eps2;
+        if (P.nmo <= EPS_SMEM) {
+            for (int i = threadIdx.x - 64; i < P.nmo; i += 32 * NUM_EPI_WARPS) seps[i] = eps2[i];
+            epi_bar();
+            epsv = seps;
+        }
         for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
             int term, t, s, A, B;
             const TermR tm = decode(P, item, term, t, s, A, B);
@@ -387,8 +399,8 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
             const bool xok = x < tm.nx;
             const bool warp_live = A * TB + quad * 32 < tm.nx;   // any valid row in this warp
             // row part of the denominator, e_s - e_x, as a float pair
-            const float2 es = eps2[tm.eps_s_off + s];
-            const float2 ex = xok ? eps2[tm.eps_x_off + x] : make_float2(0.f, 0.f);
+            const float2 es = epsv[tm.eps_s_off + s];
+            const float2 ex = xok ? epsv[tm.eps_x_off + x] : make_float2(0.f, 0.f);
             const float2 rb = df_add(es, make_float2(-ex.x, -ex.y));
             const uint32_t ta1 = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)acc * 256u +
                                  (uint32_t)half * 64u;
@@ -396,7 +408,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
             const int ybase = B * TB + half * 64;
             const int ncols = min(64, tm.nx - ybase);             // valid columns of this half
             const float2* Et = E2 + (int64_t)t * nE;
-            const float2* ey2 = eps2 + tm.eps_x_off;
+            const float2* ey2 = epsv + tm.eps_x_off;
             double* out = part + (tm.item0 + (item - tm.first)) * (int64_t)nE * 2;
             for (int e0 = 0; e0 < nE; e0 += EC) {
                 const int ne = min(EC, nE - e0);
@@ -459,26 +471,34 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
                         ad[e] += __shfl_xor_sync(0xffffffffu, ad[e], o);
                     }
                 }
+                // per-warp partials of this energy chunk; the CTA-wide sum of a
+                // group of RED_E energies needs one barrier pair
+                const int g0 = e0 % RED_E;
                 if (lane == 0) {
 #pragma unroll
                     for (int e = 0; e < EC; ++e) {
-                        red[(ew * 16 + e) * 2] = as[e];
-                        red[(ew * 16 + e) * 2 + 1] = ad[e];
+                        if (e < ne) {
+                            red[(ew * RED_E + g0 + e) * 2] = as[e];
+                            red[(ew * RED_E + g0 + e) * 2 + 1] = ad[e];
+                        }
                     }
                 }
-                epi_bar();
-                const int idx = ew * 32 + lane;
-                if (idx < ne) {
-                    double sv = 0.0, dv = 0.0;
+                if (g0 + EC >= RED_E || e0 + EC >= nE) {
+                    epi_bar();
+                    const int gstart = e0 - g0;
+                    const int gn = min(RED_E, nE - gstart);
+                    for (int idx = ew * 32 + lane; idx < gn; idx += 32 * NUM_EPI_WARPS) {
+                        double sv = 0.0, dv = 0.0;
 #pragma unroll
-                    for (int w = 0; w < NUM_EPI_WARPS; ++w) {
-                        sv += (double)red[(w * 16 + idx) * 2];
-                        dv += (double)red[(w * 16 + idx) * 2 + 1];
+                        for (int w = 0; w < NUM_EPI_WARPS; ++w) {
+                            sv += (double)red[(w * RED_E + idx) * 2];
+                            dv += (double)red[(w * RED_E + idx) * 2 + 1];
+                        }
+                        out[(gstart + idx) * 2] = sv;
+                        out[(gstart + idx) * 2 + 1] = dv;
                     }
-                    out[(e0 + idx) * 2] = sv;
-                    out[(e0 + idx) * 2 + 1] = dv;
+                    epi_bar();
                 }
-                epi_bar();
             }
             fence_before();
             __syncwarp();
@@ -783,6 +803,7 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
     }
     P.kblocks = Mp / KB;
     P.nE = nE;
+    P.nmo = nmo;
     const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
     CDS_CUDA_TRY(cudaMemsetAsync(lay.err, 0, sizeof(int32_t), stream));
     if (nitems > 0) {

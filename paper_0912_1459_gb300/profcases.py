@@ -1,0 +1,64 @@
+"""Small, self-contained cases for profiling one kernel at a time.
+
+Each case builds only the inputs of one library call at C60 shape (N = 840,
+o = 180, v = 660) and runs it twice, so an ``ncu -k <kernel> -c <n>`` capture
+holds a few GB of device memory at most and replays in seconds:
+
+  python -m paper_0912_1459_gb300.profcases transform   # k_dfgemm / k_dgemm
+  python -m paper_0912_1459_gb300.profcases sigma1      # k_sigma_tc, nE = 1
+  python -m paper_0912_1459_gb300.profcases sigma64     # k_sigma_tc, nE = 64
+  python -m paper_0912_1459_gb300.profcases cd          # k_cd_update (C60, 1024 steps max)
+
+Factors are seeded random numbers of the right shape and magnitude (the
+kernels' cost does not depend on their values).
+"""
+from __future__ import annotations
+
+import os
+import sys
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+from . import cdsigma as G  # noqa: E402
+
+
+def main(mode: str) -> None:
+    dev = torch.device("cuda:0")
+
+    def d(a):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+    m = W.config2()
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    if mode in ("transform", "transform64"):
+        L = torch.randn((128, G.npair(m.nbf)), dtype=torch.float64, device=dev, generator=g) * 1e-2
+        prec = "fp64" if mode == "transform64" else "f32x2"
+        for _ in range(2):
+            G.cds_cd_to_mo(L, d(m.C), m.nocc, d(m.orbitals), precision=prec)
+    elif mode in ("sigma1", "sigma64"):
+        nE = 64 if mode == "sigma64" else 1
+        Lov = torch.randn((m.nocc, m.nbf - m.nocc, 896), dtype=torch.float64, device=dev,
+                          generator=g) * 1e-2
+        Lp = torch.randn((2, m.nbf, 896), dtype=torch.float64, device=dev, generator=g) * 1e-2
+        E = d(W.energy_grid(m.eps[m.orbitals[9:11]], nE))
+        for _ in range(2):
+            G.cds_sigma2_diag(Lov, Lp, d(m.eps), m.nocc, E, "bf16x3")
+    elif mode == "cd":
+        G.cds_cd_decompose(d(m.basis.xyz), d(m.basis.alpha), d(m.basis.atom.astype(np.int32)),
+                           1e-4, "full", max_rank=1024)
+    else:
+        raise SystemExit(f"unknown case {mode!r}")
+    torch.cuda.synchronize()
+    print("ok", mode)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1] if len(sys.argv) > 1 else "sigma1")

@@ -120,3 +120,20 @@ def test_mixed_within_tenth_of_mev_full_size(run, prec):
     assert qp.sum() >= 3
     assert np.all(stmx.cpu().numpy()[qp] == 0)
     assert np.abs(wmx.cpu().numpy()[qp] - w64[qp]).max() <= TOL_QP
+
+
+def test_mixed_pipeline_end_to_end(run):
+    """The benchmark's split-precision pipeline (float-pair transform, BF16X3
+    self-energy) against the all-FP64 GPU path: quasiparticle energies within
+    0.1 meV."""
+    m, L, piv, D, de, Lov, Lp = run
+    Lov2, Lp2 = G.cds_cd_to_mo(L, dev(m.C), m.nocc, dev(m.orbitals), precision="f32x2")
+    sel = [9, 10, 11, 15]
+    selt = torch.tensor(sel, device=DEV)
+    orbs = dev(m.orbitals[sel])
+    eps = dev(m.eps)
+    w64, P64, _, st64 = G.cds_qp_solve(Lov, Lp[selt], orbs, eps, m.nocc, precision="fp64")
+    wmx, _, _, stmx = G.cds_qp_solve(Lov2, Lp2[selt], orbs, eps, m.nocc, precision="bf16x3")
+    qp = (st64.cpu().numpy() == 0) & (P64.cpu().numpy() >= 0.5)
+    assert qp.sum() >= 3
+    assert np.abs(wmx.cpu().numpy()[qp] - w64.cpu().numpy()[qp]).max() <= TOL_QP

@@ -112,6 +112,24 @@ def test_transform_parity(name, delta):
     np.testing.assert_allclose(Lp.cpu().numpy(), rp, rtol=0, atol=1e-11 * scale)
 
 
+@pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-5)])
+def test_transform_float_pairs(name, delta):
+    """F32X2 transform against the oracle within 1e-10 (|C|^T |A| |C|)_pq: the
+    float-pair arithmetic carries ~2^-44 per operation over N terms."""
+    m = O.molecule(name)
+    ref = O.decomposition(name, delta)
+    orbs = m.orbitals.astype(np.int32)
+    Lov, Lp = G.cds_cd_to_mo(dev(ref.L), dev(m.C), m.nocc, dev(orbs), precision="f32x2")
+    rov, rp = O.factors(name, ref.L, orbs)
+    from oracle import ao2mo
+    absC = np.abs(m.C)
+    Lov, Lp = Lov.cpu().numpy(), Lp.cpu().numpy()
+    for K in range(0, ref.M, max(1, ref.M // 7)):
+        bound = absC.T @ np.abs(ao2mo.unpack(ref.L[K], m.nbf)) @ absC
+        assert np.all(np.abs(Lov[:, :, K] - rov[:, :, K]) <= 1e-10 * bound[:m.nocc, m.nocc:])
+        assert np.all(np.abs(Lp[:, :, K] - rp[:, :, K]) <= 1e-10 * bound[orbs, :])
+
+
 @pytest.mark.parametrize("name,delta,nE", [("c0", 1e-6, 16), ("c1", 1e-5, 4)])
 def test_sigma_fp64_parity(name, delta, nE):
     m = O.molecule(name)
