@@ -213,6 +213,85 @@ int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
                  double* pole, int32_t* iters, int32_t* status, void* workspace,
                  size_t workspace_bytes, cudaStream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many molecules of uneven size, orbital and energy counts in
+ * one call per stage (not in the paper, which treats one molecule; each
+ * molecule's results are those of the single-molecule calls above).
+ * Molecule m is described by cds_mol; its arrays sit back to back in
+ * concatenated buffers at the element offsets cds_batch_offsets returns,
+ * offs[m * CDS_BATCH_NOFF + k], with k:
+ *   0 basis functions (xyz uses 3x, alpha, atom)   1 pairs (D)
+ *   2 L [max_rank][npair]                            3 piv [max_rank]
+ *   4 C [nbf][nbf]                                   5 eps [nbf]
+ *   6 orbitals: orb, omega, pole, iters, status [np] 7 energies: E, sigma, dsigma [np][nE]
+ *   8 Lov [nocc][nbf-nocc][M]                        9 Lp [np][nbf][M]
+ * (row nmol holds the totals).  Local MO indices in orb; atom indices are the
+ * molecule's own.  The workspace (cds_batch_workspace_bytes) holds a
+ * scratch part shared by the decomposition and the transform and a part
+ * holding the self-energy / Newton state that a graph (below) refers to.
+ * ---------------------------------------------------------------------- */
+
+typedef struct {
+    int32_t nbf;       /* basis functions (= MOs) */
+    int32_t nocc;      /* occupied orbitals */
+    int32_t np;        /* orbitals whose Sigma / quasiparticle is wanted */
+    int32_t nE;        /* energies per orbital on the Sigma grid (>= 1) */
+    int32_t max_rank;  /* capacity of the molecule's Cholesky buffer */
+} cds_mol;
+
+#define CDS_BATCH_NOFF 10
+
+/* Host only.  offs: host [(nmol + 1) * CDS_BATCH_NOFF]. */
+int cds_batch_offsets(int32_t nmol, const cds_mol* mols, int64_t* offs);
+
+size_t cds_batch_workspace_bytes(int32_t nmol, const cds_mol* mols, int32_t precision);
+
+/* Blocking.  Per molecule as cds_cd_decompose (delta and scheme shared);
+ * M_out: host [nmol].  One update and one pivot-select launch per step for
+ * the whole batch.  Returns the first non-OK molecule status. */
+int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const double* xyz,
+                           const double* alpha, const int32_t* atom, double delta,
+                           int32_t scheme, double* L, int32_t* piv, double* D, int32_t* M_out,
+                           void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* Asynchronous.  M: host [nmol] ranks.  Per molecule as cds_cd_to_mo. */
+int cds_batch_cd_to_mo(int32_t nmol, const cds_mol* mols, const int32_t* M, const double* L,
+                       const double* C, const int32_t* orb, int32_t precision, double* Lov,
+                       double* Lp, void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* Blocking (descriptor upload), then one persistent tensor-core launch over
+ * the items of every molecule.  precision: BF16X3 or FP16X3.  stamps:
+ * device [nmol + 1] or NULL (unused here). */
+int cds_batch_sigma2(int32_t nmol, const cds_mol* mols, const int32_t* M, const double* Lov,
+                     const double* Lp, const double* eps, const double* E, int32_t precision,
+                     double* sigma, double* dsigma, unsigned long long* stamps, void* workspace,
+                     size_t workspace_bytes, cudaStream_t stream);
+
+/* Blocking.  Newton for every molecule's orbitals, one batched Sigma pass per
+ * iteration.  stamps (device [nmol + 1], may be NULL): [0] = %globaltimer at
+ * the start, [1 + m] = time the last orbital of molecule m retired. */
+int cds_batch_qp_solve(int32_t nmol, const cds_mol* mols, const int32_t* M, const double* Lov,
+                       const double* Lp, const int32_t* orb, const double* eps, double conv,
+                       int32_t max_iter, int32_t precision, double* omega, double* pole,
+                       int32_t* iters, int32_t* status, unsigned long long* stamps,
+                       void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* A CUDA graph of the batched Sigma grid (sigma, dsigma) followed by the
+ * Newton solve with exactly max_iter passes (converged orbitals skip their
+ * work): captured by the library (blocking), replayed by cds_graph_launch
+ * with one launch.  Every pointer and the workspace must stay valid, and
+ * Lov/Lp/E/eps are re-read at each replay.  Library-owned; free with
+ * cds_graph_destroy. */
+typedef struct cds_graph cds_graph;
+int cds_batch_graph_create(int32_t nmol, const cds_mol* mols, const int32_t* M, const double* Lov,
+                           const double* Lp, const int32_t* orb, const double* eps,
+                           const double* E, int32_t precision, double conv, int32_t max_iter,
+                           double* sigma, double* dsigma, double* omega, double* pole,
+                           int32_t* iters, int32_t* status, unsigned long long* stamps,
+                           void* workspace, size_t workspace_bytes, cds_graph** out);
+int cds_graph_launch(cds_graph* graph, cudaStream_t stream);
+int cds_graph_destroy(cds_graph* graph);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,35 @@ _SIGNATURES = {
 }
 
 
+class CdsMol(ctypes.Structure):
+    """One molecule of a batch (the C struct cds_mol)."""
+    _fields_ = [("nbf", ctypes.c_int32), ("nocc", ctypes.c_int32), ("np", ctypes.c_int32),
+                ("nE", ctypes.c_int32), ("max_rank", ctypes.c_int32)]
+
+
+BATCH_NOFF = 10
+BATCH_KEYS = ("basis", "pair", "L", "piv", "C", "eps", "orb", "E", "ov", "p")
+
+_mp = ctypes.POINTER(CdsMol)
+_SIGNATURES.update({
+    "cds_batch_offsets": (ctypes.c_int, [_i32, _mp, ctypes.POINTER(ctypes.c_int64)]),
+    "cds_batch_workspace_bytes": (_sz, [_i32, _mp, _i32]),
+    "cds_batch_cd_decompose": (ctypes.c_int, [_i32, _mp, _vp, _vp, _vp, _f64, _i32, _vp, _vp, _vp,
+                                              ctypes.POINTER(_i32), _vp, _sz, _vp]),
+    "cds_batch_cd_to_mo": (ctypes.c_int, [_i32, _mp, ctypes.POINTER(_i32), _vp, _vp, _vp, _i32, _vp,
+                                          _vp, _vp, _sz, _vp]),
+    "cds_batch_sigma2": (ctypes.c_int, [_i32, _mp, ctypes.POINTER(_i32), _vp, _vp, _vp, _vp, _i32,
+                                        _vp, _vp, _vp, _vp, _sz, _vp]),
+    "cds_batch_qp_solve": (ctypes.c_int, [_i32, _mp, ctypes.POINTER(_i32), _vp, _vp, _vp, _vp, _f64,
+                                          _i32, _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "cds_batch_graph_create": (ctypes.c_int, [_i32, _mp, ctypes.POINTER(_i32), _vp, _vp, _vp, _vp,
+                                              _vp, _i32, _f64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
+                                              _vp, _vp, _sz, ctypes.POINTER(_vp)]),
+    "cds_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "cds_graph_destroy": (ctypes.c_int, [_vp]),
+})
+
+
 class CdsError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -295,3 +324,115 @@ def cds_qp_solve(Lov: torch.Tensor, Lp: torch.Tensor, orbitals: torch.Tensor, ep
         st = CDS_OK
     _check(st, "cds_qp_solve")
     return omega, pole, iters, status
+
+
+# ---------------------------------------------------------------------------
+# batched form
+# ---------------------------------------------------------------------------
+class Batch:
+    """A batch of molecules in concatenated device buffers (cds_mol layout).
+
+    ``mols``: list of (nbf, nocc, np, nE, max_rank).  Holds the offsets, the
+    workspace and the output buffers; the methods call the cds_batch_* entry
+    points and return per-molecule views."""
+
+    def __init__(self, mols, device, precision: str = "bf16x3"):
+        self.lib = load()
+        self.dev = torch.device(device)
+        self.n = len(mols)
+        self.mols = (CdsMol * self.n)(*[CdsMol(*m) for m in mols])
+        offs = (ctypes.c_int64 * ((self.n + 1) * BATCH_NOFF))()
+        _check(self.lib.cds_batch_offsets(self.n, self.mols, offs), "cds_batch_offsets")
+        o = list(offs)
+        self.off = [dict(zip(BATCH_KEYS, o[i * BATCH_NOFF:(i + 1) * BATCH_NOFF]))
+                    for i in range(self.n + 1)]
+        self.total = self.off[self.n]
+        self.prec = precision
+        need = self.lib.cds_batch_workspace_bytes(self.n, self.mols, PRECISIONS[precision])
+        self.ws = _workspace(need, self.dev)
+        f64 = dict(dtype=torch.float64, device=self.dev)
+        i32 = dict(dtype=torch.int32, device=self.dev)
+        t = self.total
+        self.L = torch.empty(max(t["L"], 1), **f64)
+        self.piv = torch.empty(max(t["piv"], 1), **i32)
+        self.D = torch.empty(max(t["pair"], 1), **f64)
+        self.Lov = torch.zeros(max(t["ov"], 1), **f64)
+        self.Lp = torch.zeros(max(t["p"], 1), **f64)
+        self.sigma = torch.empty(max(t["E"], 1), **f64)
+        self.dsigma = torch.empty(max(t["E"], 1), **f64)
+        self.omega = torch.empty(max(t["orb"], 1), **f64)
+        self.pole = torch.empty(max(t["orb"], 1), **f64)
+        self.iters = torch.empty(max(t["orb"], 1), **i32)
+        self.status = torch.empty(max(t["orb"], 1), **i32)
+        self.stamps = torch.zeros(self.n + 1, dtype=torch.int64, device=self.dev)
+        self.M = (_i32 * self.n)()
+
+    def _s(self):
+        return _stream(self.dev)
+
+    def cd_decompose(self, xyz, alpha, atom, delta, scheme="full"):
+        st = self.lib.cds_batch_cd_decompose(self.n, self.mols, _p(xyz), _p(alpha), _p(atom),
+                                             float(delta), SCHEMES[scheme], _p(self.L), _p(self.piv),
+                                             _p(self.D), self.M, _p(self.ws), self.ws.numel(),
+                                             self._s())
+        _check(st, "cds_batch_cd_decompose")
+        return list(self.M)
+
+    def cd_to_mo(self, C, orb, precision="f32x2"):
+        _check(self.lib.cds_batch_cd_to_mo(self.n, self.mols, self.M, _p(self.L), _p(C), _p(orb),
+                                           PRECISIONS[precision], _p(self.Lov), _p(self.Lp),
+                                           _p(self.ws), self.ws.numel(), self._s()),
+               "cds_batch_cd_to_mo")
+
+    def sigma2(self, eps, E):
+        _check(self.lib.cds_batch_sigma2(self.n, self.mols, self.M, _p(self.Lov), _p(self.Lp), _p(eps),
+                                         _p(E), PRECISIONS[self.prec], _p(self.sigma), _p(self.dsigma),
+                                         None, _p(self.ws), self.ws.numel(), self._s()),
+               "cds_batch_sigma2")
+
+    def qp_solve(self, orb, eps, conv=1e-5, max_iter=50):
+        st = self.lib.cds_batch_qp_solve(self.n, self.mols, self.M, _p(self.Lov), _p(self.Lp), _p(orb),
+                                         _p(eps), float(conv), int(max_iter), PRECISIONS[self.prec],
+                                         _p(self.omega), _p(self.pole), _p(self.iters),
+                                         _p(self.status), _p(self.stamps), _p(self.ws),
+                                         self.ws.numel(), self._s())
+        if st not in (CDS_OK, 5):
+            _check(st, "cds_batch_qp_solve")
+
+    def graph(self, orb, eps, E, conv=1e-5, max_iter=50):
+        """Capture the Sigma-grid + Newton stage as a CUDA graph (BatchGraph)."""
+        h = ctypes.c_void_p()
+        st = self.lib.cds_batch_graph_create(self.n, self.mols, self.M, _p(self.Lov), _p(self.Lp),
+                                             _p(orb), _p(eps), _p(E), PRECISIONS[self.prec],
+                                             float(conv), int(max_iter), _p(self.sigma),
+                                             _p(self.dsigma), _p(self.omega), _p(self.pole),
+                                             _p(self.iters), _p(self.status), _p(self.stamps),
+                                             _p(self.ws), self.ws.numel(), ctypes.byref(h))
+        _check(st, "cds_batch_graph_create")
+        return BatchGraph(self.lib, h, self)
+
+    def view(self, key: str, c: int, shape):
+        """Molecule c's part of a concatenated buffer."""
+        buf = {"L": self.L, "piv": self.piv, "D": self.D, "ov": self.Lov, "p": self.Lp,
+               "sigma": self.sigma, "dsigma": self.dsigma, "omega": self.omega, "pole": self.pole,
+               "iters": self.iters, "status": self.status}[key]
+        base = {"L": "L", "piv": "piv", "D": "pair", "ov": "ov", "p": "p", "sigma": "E",
+                "dsigma": "E", "omega": "orb", "pole": "orb", "iters": "orb", "status": "orb"}[key]
+        o = self.off[c][base]
+        size = 1
+        for d in shape:
+            size *= d
+        return buf[o:o + size].view(*shape)
+
+
+class BatchGraph:
+    def __init__(self, lib, handle, batch):
+        self.lib, self.h, self.batch = lib, handle, batch
+
+    def launch(self):
+        _check(self.lib.cds_graph_launch(self.h, _stream(self.batch.dev)), "cds_graph_launch")
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.cds_graph_destroy(self.h)
+            self.h = None

@@ -12,7 +12,10 @@
 // k_cd_select then picks the pivot.  Both kernels read a device control block
 // and return immediately once the decomposition has stopped, so the host can
 // enqueue steps ahead and only check the control block every few steps.
+#include <vector>
+
 #include "common.cuh"
+#include "sigma_tc.cuh"
 
 namespace cds {
 
@@ -72,26 +75,29 @@ __device__ void block_maxmin(double& mx, double& mn) {
     __syncthreads();
 }
 
-// Returns true in thread 0 of the last block to finish (after its partial is visible).
-__device__ bool last_block(unsigned int* counter) {
+// True (in every thread) for the last of nblk blocks to finish, after the
+// partials of all of them are visible.
+__device__ bool last_block(unsigned int* counter, int nblk) {
     __shared__ bool am_last;
     __threadfence();
     if (threadIdx.x == 0) {
         unsigned int t = atomicAdd(counter, 1u);
-        am_last = (t == gridDim.x - 1);
+        am_last = (t == (unsigned int)nblk - 1);
     }
     __syncthreads();
     return am_last;
 }
 
 // D = initial diagonal, candidate mask, scale = max D, G = max candidate D.
-__global__ void k_cd_init(PairSoA pd, const int32_t* __restrict__ atom,
-                          int32_t scheme, int64_t n, double delta, double* __restrict__ D,
-                          uint8_t* __restrict__ cand, double* __restrict__ blk_a,
-                          double* __restrict__ blk_b, CdCtrl* ctrl) {
+// bid / nblk: this block's index and the number of blocks working on the
+// molecule (the grid of the single-molecule kernel, a slice of a batch grid).
+__device__ void cd_init_body(PairSoA pd, const int32_t* __restrict__ atom, int32_t scheme,
+                             int64_t n, double delta, double* __restrict__ D,
+                             uint8_t* __restrict__ cand, double* __restrict__ blk_a,
+                             double* __restrict__ blk_b, CdCtrl* ctrl, int bid, int nblk) {
     double mx_all = -INFINITY, mx_cand = -INFINITY;
-    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < n;
-         I += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t I = bid * (int64_t)blockDim.x + threadIdx.x; I < n;
+         I += (int64_t)nblk * blockDim.x) {
         double p = pd.p[I], px = pd.Px[I], py = pd.Py[I], pz = pd.Pz[I], k = pd.K[I];
         double d = eri_pair(p, px, py, pz, k, p, px, py, pz, k);
         D[I] = d;
@@ -107,10 +113,10 @@ __global__ void k_cd_init(PairSoA pd, const int32_t* __restrict__ atom,
     }
     double a = mx_all, b = -mx_cand;   // reuse max/min: min(-x) = -max(x)
     block_maxmin(a, b);
-    if (threadIdx.x == 0) { blk_a[blockIdx.x] = a; blk_b[blockIdx.x] = b; }
-    if (last_block(&ctrl->counter)) {
+    if (threadIdx.x == 0) { blk_a[bid] = a; blk_b[bid] = b; }
+    if (last_block(&ctrl->counter, nblk)) {
         double A = -INFINITY, B = INFINITY;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
             A = fmax(A, __ldcg(blk_a + i));
             B = fmin(B, __ldcg(blk_b + i));
         }
@@ -128,34 +134,40 @@ __global__ void k_cd_init(PairSoA pd, const int32_t* __restrict__ atom,
     }
 }
 
+__global__ void k_cd_init(PairSoA pd, const int32_t* __restrict__ atom, int32_t scheme, int64_t n,
+                          double delta, double* __restrict__ D, uint8_t* __restrict__ cand,
+                          double* __restrict__ blk_a, double* __restrict__ blk_b, CdCtrl* ctrl) {
+    cd_init_body(pd, atom, scheme, n, delta, D, cand, blk_a, blk_b, ctrl, blockIdx.x, gridDim.x);
+}
+
 // Pivot for vector k (k vectors already made): stop test, rank cap, then the
 // lowest candidate index with max(D,0) >= G - 1e-12*scale and D > delta_eff.
-__global__ void k_cd_select(int64_t n, int32_t k, int32_t max_rank,
-                            const double* __restrict__ D, const uint8_t* __restrict__ cand,
-                            long long* __restrict__ blk_i, int32_t* __restrict__ piv,
-                            CdCtrl* ctrl) {
+__device__ void cd_select_body(int64_t n, int32_t k, int32_t max_rank,
+                               const double* __restrict__ D, const uint8_t* __restrict__ cand,
+                               long long* __restrict__ blk_i, int32_t* __restrict__ piv,
+                               CdCtrl* ctrl, int bid, int nblk) {
     if (ctrl->done) return;
     double G = ctrl->G, de = ctrl->delta_eff, scale = ctrl->scale;
     if (ctrl->Dmin < -kNotPdRel * scale || !(G == G)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (bid == 0 && threadIdx.x == 0) {
             ctrl->status = CDS_ERR_NOT_PD; ctrl->done = 1; ctrl->M = k;
         }
         return;
     }
     if (G <= de) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) { ctrl->done = 1; ctrl->M = k; }
+        if (bid == 0 && threadIdx.x == 0) { ctrl->done = 1; ctrl->M = k; }
         return;
     }
     if (k >= max_rank) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (bid == 0 && threadIdx.x == 0) {
             ctrl->status = CDS_ERR_RANK_CAP; ctrl->done = 1; ctrl->M = k;
         }
         return;
     }
     double thr = G - kTieRel * scale;
     long long best = LLONG_MAX;
-    for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < n;
-         I += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t I = bid * (int64_t)blockDim.x + threadIdx.x; I < n;
+         I += (int64_t)nblk * blockDim.x) {
         double d = D[I];
         if (cand[I] && fmax(d, 0.0) >= thr && d > de) { best = (long long)I; break; }
     }
@@ -167,11 +179,11 @@ __global__ void k_cd_select(int64_t n, int32_t k, int32_t max_rank,
     if (w == 0) {
         best = lane < (int)(blockDim.x >> 5) ? sb[lane] : LLONG_MAX;
         best = warp_min_ll(best);
-        if (lane == 0) blk_i[blockIdx.x] = best;
+        if (lane == 0) blk_i[bid] = best;
     }
-    if (last_block(&ctrl->counter)) {
+    if (last_block(&ctrl->counter, nblk)) {
         long long b = LLONG_MAX;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
             long long v = __ldcg(blk_i + i);
             b = v < b ? v : b;
         }
@@ -195,19 +207,27 @@ __global__ void k_cd_select(int64_t n, int32_t k, int32_t max_rank,
     }
 }
 
+__global__ void k_cd_select(int64_t n, int32_t k, int32_t max_rank, const double* __restrict__ D,
+                            const uint8_t* __restrict__ cand, long long* __restrict__ blk_i,
+                            int32_t* __restrict__ piv, CdCtrl* ctrl) {
+    cd_select_body(n, k, max_rank, D, cand, blk_i, piv, ctrl, blockIdx.x, gridDim.x);
+}
+
 // Vector k from pivot P: column, left-looking projection, residual update.
 // Each thread owns kCdPairs pairs, blockDim.x * kCdPairs apart, so one grid of
 // ~npair / (kCdThreads * kCdPairs) small blocks is resident in a single wave.
-__global__ void __launch_bounds__(kCdThreads)
-k_cd_update(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L, double* __restrict__ D,
-            const uint8_t* __restrict__ cand, double* __restrict__ blk_a,
-            double* __restrict__ blk_b, CdCtrl* ctrl) {
+__device__ __forceinline__ void cd_update_body(PairSoA pd, int64_t n, int32_t k,
+                                               double* __restrict__ L, double* __restrict__ D,
+                                               const uint8_t* __restrict__ cand,
+                                               double* __restrict__ blk_a,
+                                               double* __restrict__ blk_b, CdCtrl* ctrl, int bid,
+                                               int nblk) {
     if (ctrl->done) return;
     __shared__ double lp[kCdChunk];
     const int64_t P = ctrl->P;
     const double DP = ctrl->DP;
     const double q = pd.p[P], qx = pd.Px[P], qy = pd.Py[P], qz = pd.Pz[P], kq = pd.K[P];
-    const int64_t I0 = (int64_t)blockIdx.x * blockDim.x * kCdPairs + threadIdx.x;
+    const int64_t I0 = (int64_t)bid * blockDim.x * kCdPairs + threadIdx.x;
     int64_t Is[kCdPairs];
     bool live[kCdPairs];
 #pragma unroll
@@ -258,10 +278,10 @@ k_cd_update(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L, double* __
         mn = fmin(mn, d);
     }
     block_maxmin(mx, mn);
-    if (threadIdx.x == 0) { blk_a[blockIdx.x] = mx; blk_b[blockIdx.x] = mn; }
-    if (last_block(&ctrl->counter)) {
+    if (threadIdx.x == 0) { blk_a[bid] = mx; blk_b[bid] = mn; }
+    if (last_block(&ctrl->counter, nblk)) {
         double A = -INFINITY, B = INFINITY;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
             A = fmax(A, __ldcg(blk_a + i));
             B = fmin(B, __ldcg(blk_b + i));
         }
@@ -272,6 +292,13 @@ k_cd_update(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L, double* __
             ctrl->counter = 0;
         }
     }
+}
+
+__global__ void __launch_bounds__(kCdThreads)
+k_cd_update(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L, double* __restrict__ D,
+            const uint8_t* __restrict__ cand, double* __restrict__ blk_a,
+            double* __restrict__ blk_b, CdCtrl* ctrl) {
+    cd_update_body(pd, n, k, L, D, cand, blk_a, blk_b, ctrl, blockIdx.x, gridDim.x);
 }
 
 struct CdLayout {
@@ -361,3 +388,161 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
     if (!h.done) return CDS_ERR_RANK_CAP;
     return h.status;
 }
+
+// ===========================================================================
+// Batched decomposition: the steps of many molecules advance together, one
+// update and one select launch per step for the whole batch; each block
+// finds its molecule from the per-molecule block ranges.
+// ===========================================================================
+namespace cds {
+
+struct CdMol {
+    PairSoA pd;
+    const int32_t* atom;
+    double* L;
+    double* D;
+    uint8_t* cand;
+    int32_t* piv;
+    double* blk_a;
+    double* blk_b;
+    long long* blk_i;
+    CdCtrl* ctrl;
+    int64_t n;
+    int32_t max_rank;
+    int32_t b0_init, nb_init, b0_upd, nb_upd, b0_sel, nb_sel;
+};
+
+// Molecule owning block bid of a batch grid (kind: 0 init, 1 update, 2 select).
+__device__ __forceinline__ int find_mol(const CdMol* mols, int nmol, int bid, int kind) {
+    int lo = 0, hi = nmol - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int b0 = kind == 0 ? mols[mid].b0_init : kind == 1 ? mols[mid].b0_upd : mols[mid].b0_sel;
+        if (b0 <= bid) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void k_bcd_init(const CdMol* __restrict__ mols, int nmol, int32_t scheme, double delta) {
+    const int c = find_mol(mols, nmol, blockIdx.x, 0);
+    const CdMol& m = mols[c];
+    cd_init_body(m.pd, m.atom, scheme, m.n, delta, m.D, m.cand, m.blk_a, m.blk_b, m.ctrl,
+                 blockIdx.x - m.b0_init, m.nb_init);
+}
+
+__global__ void k_bcd_select(const CdMol* __restrict__ mols, int nmol, int32_t k) {
+    const int c = find_mol(mols, nmol, blockIdx.x, 2);
+    const CdMol& m = mols[c];
+    cd_select_body(m.n, k, m.max_rank, m.D, m.cand, m.blk_i, m.piv, m.ctrl,
+                   blockIdx.x - m.b0_sel, m.nb_sel);
+}
+
+__global__ void __launch_bounds__(kCdThreads) k_bcd_update(const CdMol* __restrict__ mols, int nmol,
+                                                           int32_t k) {
+    const int c = find_mol(mols, nmol, blockIdx.x, 1);
+    const CdMol& m = mols[c];
+    if (k >= m.max_rank) return;
+    cd_update_body(m.pd, m.n, k, m.L, m.D, m.cand, m.blk_a, m.blk_b, m.ctrl,
+                   blockIdx.x - m.b0_upd, m.nb_upd);
+}
+
+struct CdBatchLayout {
+    CdMol* mols;          // device descriptors
+    CdCtrl* ctrl;         // [nmol]
+    char* per_mol;        // pair data, masks, block partials of every molecule
+    size_t bytes;
+};
+
+static size_t cd_mol_bytes(int64_t n) {
+    const size_t nb = (size_t)std::max(cd_blocks(n), 1);
+    return 5 * align_up(n * sizeof(double)) + align_up(n) + 3 * align_up(nb * sizeof(double));
+}
+
+static CdBatchLayout cd_batch_layout(void* ws, int32_t nmol, const BatchMol* mols) {
+    Carver c(ws);
+    CdBatchLayout l;
+    l.mols = c.take<CdMol>(std::max(nmol, 1));
+    l.ctrl = c.take<CdCtrl>(std::max(nmol, 1));
+    size_t per = 0;
+    for (int i = 0; i < nmol; ++i) per += cd_mol_bytes(npair_of(mols[i].nbf));
+    l.per_mol = c.take<char>(std::max<size_t>(per, 1));
+    l.bytes = c.off;
+    return l;
+}
+
+size_t cd_batch_workspace_bytes(int32_t nmol, const BatchMol* mols) {
+    return cd_batch_layout(nullptr, nmol, mols).bytes;
+}
+
+// Blocking: M[c] receives molecule c's rank; returns the first non-OK status.
+int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* off,
+                       const double* xyz, const double* alpha, const int32_t* atom, double delta,
+                       int32_t scheme, double* L, int32_t* piv, double* D, int32_t* M_out,
+                       void* ws, size_t ws_bytes, cudaStream_t stream) {
+    CdBatchLayout lay = cd_batch_layout(ws, nmol, mols);
+    if (!ws || ws_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    std::vector<CdMol> h(nmol);
+    char* p = lay.per_mol;
+    int b_init = 0, b_upd = 0, b_sel = 0, kmax = 0;
+    for (int c = 0; c < nmol; ++c) {
+        const int64_t n = npair_of(mols[c].nbf);
+        const size_t nb = (size_t)std::max(cd_blocks(n), 1);
+        CdMol& m = h[c];
+        Carver cv(p);
+        m.pd.p = cv.take<double>(n);
+        m.pd.Px = cv.take<double>(n);
+        m.pd.Py = cv.take<double>(n);
+        m.pd.Pz = cv.take<double>(n);
+        m.pd.K = cv.take<double>(n);
+        m.cand = cv.take<uint8_t>(n);
+        m.blk_a = cv.take<double>(nb);
+        m.blk_b = cv.take<double>(nb);
+        m.blk_i = cv.take<long long>(nb);
+        p += cd_mol_bytes(n);
+        m.atom = atom + off[c].basis;
+        m.L = L + off[c].L;
+        m.D = D + off[c].pair;
+        m.piv = piv + off[c].piv;
+        m.ctrl = lay.ctrl + c;
+        m.n = n;
+        m.max_rank = mols[c].max_rank;
+        m.b0_init = b_init; m.nb_init = cd_blocks(n); b_init += m.nb_init;
+        m.b0_upd = b_upd; m.nb_upd = upd_blocks(n); b_upd += m.nb_upd;
+        m.b0_sel = b_sel; m.nb_sel = sel_blocks(n); b_sel += m.nb_sel;
+        kmax = std::max(kmax, mols[c].max_rank);
+        int st = build_pairs(mols[c].nbf, xyz + 3 * off[c].basis, alpha + off[c].basis, m.pd, stream);
+        if (st) return st;
+    }
+    CDS_CUDA_TRY(cudaMemcpyAsync(lay.mols, h.data(), sizeof(CdMol) * nmol, cudaMemcpyHostToDevice,
+                                 stream));
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, sizeof(CdCtrl) * nmol, stream));
+    k_bcd_init<<<b_init, kCdThreads, 0, stream>>>(lay.mols, nmol, scheme, delta);
+    CDS_LAUNCH_CHECK();
+    k_bcd_select<<<b_sel, kCdThreads, 0, stream>>>(lay.mols, nmol, 0);
+    CDS_LAUNCH_CHECK();
+    std::vector<CdCtrl> hc(nmol);
+    for (int32_t k0 = 0; k0 <= kmax; k0 += kHostCheckEvery) {
+        int32_t k1 = std::min(kmax, k0 + kHostCheckEvery);
+        for (int32_t k = k0; k < k1; ++k) {
+            k_bcd_update<<<b_upd, kCdThreads, 0, stream>>>(lay.mols, nmol, k);
+            k_bcd_select<<<b_sel, kCdThreads, 0, stream>>>(lay.mols, nmol, k + 1);
+        }
+        count_launches(2ull * (unsigned long long)(k1 - k0));
+        CDS_CUDA_TRY(cudaGetLastError());
+        CDS_CUDA_TRY(cudaMemcpyAsync(hc.data(), lay.ctrl, sizeof(CdCtrl) * nmol,
+                                     cudaMemcpyDeviceToHost, stream));
+        CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+        bool all = true;
+        for (int c = 0; c < nmol; ++c) all = all && hc[c].done;
+        if (all) break;
+    }
+    int status = CDS_OK;
+    for (int c = 0; c < nmol; ++c) {
+        M_out[c] = hc[c].M;
+        int st = hc[c].done ? hc[c].status : CDS_ERR_RANK_CAP;
+        if (st && !status) status = st;
+    }
+    return status;
+}
+
+}  // namespace cds

@@ -33,6 +33,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <type_traits>
+#include <vector>
 
 #include "sigma_tc.cuh"
 
@@ -208,29 +209,30 @@ __device__ __forceinline__ bool epi_any(bool v) {
 // parameter block is not copied to local memory).
 struct TermR {
     int32_t nx, ns, nb, bulk_s_dim;
-    int64_t npb, item0, first;   // first: global index of the term's first item
+    int64_t npb, item0, first;   // first: index of the term's first item within its molecule
     int32_t eps_s_off, eps_x_off;
 };
 
-__device__ __forceinline__ TermR term_regs(const Params& P, int term) {
+__device__ __forceinline__ TermR term_regs(const Term& t0, const Term& t1, int term) {
     TermR r;
-    r.nx = term ? P.term[1].nx : P.term[0].nx;
-    r.ns = term ? P.term[1].ns : P.term[0].ns;
-    r.nb = term ? P.term[1].nb : P.term[0].nb;
-    r.bulk_s_dim = term ? P.term[1].bulk_s_dim : P.term[0].bulk_s_dim;
-    r.npb = term ? P.term[1].npb : P.term[0].npb;
-    r.item0 = term ? P.term[1].item0 : P.term[0].item0;
-    r.first = term ? P.term[0].nitems : 0;
-    r.eps_s_off = term ? P.term[1].eps_s_off : P.term[0].eps_s_off;
-    r.eps_x_off = term ? P.term[1].eps_x_off : P.term[0].eps_x_off;
+    r.nx = term ? t1.nx : t0.nx;
+    r.ns = term ? t1.ns : t0.ns;
+    r.nb = term ? t1.nb : t0.nb;
+    r.bulk_s_dim = term ? t1.bulk_s_dim : t0.bulk_s_dim;
+    r.npb = term ? t1.npb : t0.npb;
+    r.item0 = term ? t1.item0 : t0.item0;
+    r.first = term ? t0.nitems : 0;
+    r.eps_s_off = term ? t1.eps_s_off : t0.eps_s_off;
+    r.eps_x_off = term ? t1.eps_x_off : t0.eps_x_off;
     return r;
 }
 
-__device__ __forceinline__ TermR decode(const Params& P, int64_t item, int& term, int& t, int& s,
-                                        int& A, int& B) {
-    term = item < P.term[0].nitems ? 0 : 1;
-    const TermR tm = term_regs(P, term);
-    int64_t r = item - tm.first;
+// (term, orbital t, spectator s, block pair A <= B) of item r of one molecule.
+__device__ __forceinline__ TermR decode(const Term& t0, const Term& t1, int64_t r, int& term,
+                                        int& t, int& s, int& A, int& B) {
+    term = r < t0.nitems ? 0 : 1;
+    const TermR tm = term_regs(t0, t1, term);
+    r -= tm.first;
     int64_t per_t = (int64_t)tm.ns * tm.npb;
     t = (int)(r / per_t);
     r -= (int64_t)t * per_t;
@@ -239,15 +241,88 @@ __device__ __forceinline__ TermR decode(const Params& P, int64_t item, int& term
     return tm;
 }
 
+// One molecule of a batch, in global memory.  Offsets are in elements of the
+// batch-wide arrays the kernel receives (E2, eps2, part, active).
+struct alignas(64) MolDesc {
+    CUtensorMap m[2][4];     // [term][aq_hi, aq_lo, bk_hi, bk_lo]
+    Term term[2];
+    int64_t item_begin;      // batch-wide index of the molecule's first item
+    int64_t part_base;       // element offset of its first item's partial row
+    int64_t E_off;           // its first energy pair
+    int64_t eps_off;         // its first orbital-energy pair
+    int32_t kblocks, nE, nmo, act_off;
+    float inv;               // 1 / (s_A s_B) of its 16-bit split
+    int32_t pad_[3];
+};
+
+// Everything a role needs to know about one work item.
+struct View {
+    TermR tm;
+    int term, t, s, A, B;
+    int kblocks, nE;
+    const CUtensorMap* maps;   // the four maps of the item's term
+    const float2* Et;          // energies of orbital t
+    const float2* epsv;        // orbital energies of the molecule
+    double* out;               // partial row of the item
+    bool act;
+    float inv;
+    int mol;
+};
+
+constexpr int MAX_BATCH_SMEM = 512;   // molecules whose first-item index is cached in smem
+
+template <bool BATCH>
+__device__ __forceinline__ View make_view(int64_t item, const Maps& maps, const Params& P,
+                                          const MolDesc* mols, const int64_t* s_begin, int nmol,
+                                          const float2* E2, const float2* epsv,
+                                          const int32_t* active, const float* inv_scale,
+                                          double* part) {
+    View v;
+    if constexpr (!BATCH) {
+        v.tm = decode(P.term[0], P.term[1], item, v.term, v.t, v.s, v.A, v.B);
+        v.maps = &maps.m[v.term][0];
+        v.kblocks = P.kblocks;
+        v.nE = P.nE;
+        v.Et = E2 + (int64_t)v.t * P.nE;
+        v.epsv = epsv;
+        v.out = part + (v.tm.item0 + (item - v.tm.first)) * (int64_t)P.nE * 2;
+        v.act = !active || active[v.t];
+        v.inv = *inv_scale;
+        v.mol = 0;
+    } else {
+        int lo = 0, hi = nmol - 1;   // last molecule whose first item is <= item
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            const int64_t b = mid < MAX_BATCH_SMEM ? s_begin[mid] : mols[mid].item_begin;
+            if (b <= item) lo = mid; else hi = mid - 1;
+        }
+        const MolDesc* md = mols + lo;
+        const int64_t r = item - md->item_begin;
+        v.tm = decode(md->term[0], md->term[1], r, v.term, v.t, v.s, v.A, v.B);
+        v.maps = &md->m[v.term][0];
+        v.kblocks = md->kblocks;
+        v.nE = md->nE;
+        v.Et = E2 + md->E_off + (int64_t)v.t * md->nE;
+        v.epsv = epsv + md->eps_off;
+        v.out = part + md->part_base + r * (int64_t)md->nE * 2;
+        v.act = !active || active[md->act_off + v.t];
+        v.inv = md->inv;
+        v.mol = lo;
+    }
+    return v;
+}
+
 // SEP: hi.hi and the two cross products accumulate in separate TMEM tiles
 // (4 x 128 columns, one buffer); otherwise all three share one tile and two
-// buffers alternate between items.
-template <int EC, bool BF16, bool SEP>
+// buffers alternate between items.  BATCH: items of many molecules, described
+// by MolDesc records in global memory, in one persistent launch.
+template <int EC, bool BF16, bool SEP, bool BATCH>
 __global__ void __launch_bounds__(THREADS, 1)
-k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __restrict__ E2,
+k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __restrict__ mols,
+           int32_t nmol, int64_t nitems_batch, const float2* __restrict__ E2,
            const float2* __restrict__ eps2, const int32_t* __restrict__ active,
            const float* __restrict__ inv_scale, double* __restrict__ part,
-           int32_t* __restrict__ err) {
+           unsigned long long* __restrict__ stamps, int32_t* __restrict__ err) {
     constexpr uint32_t ID = idesc<BF16>();
     constexpr int NBUF = SEP ? 1 : 2;
     extern __shared__ uint8_t smem_raw[];
@@ -261,11 +336,16 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
     uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
     float* red = (float*)(smem + NSTAGE * STAGE_BYTES + 256);   // [8 warps][RED_E][2]
     float2* seps = (float2*)(red + NUM_EPI_WARPS * RED_E * 2);   // [EPS_SMEM]
+    int64_t* s_begin = (int64_t*)seps;                          // batch: first item per molecule
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
+    const int64_t nitems = BATCH ? nitems_batch : P.term[0].nitems + P.term[1].nitems;
     volatile int32_t* verr = err;
 
+    if (BATCH) {
+        for (int i = threadIdx.x; i < min(nmol, MAX_BATCH_SMEM); i += blockDim.x)
+            s_begin[i] = mols[i].item_begin;
+    }
     if (threadIdx.x == 0) {
         for (int i = 0; i < NSTAGE; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         for (int i = 0; i < NBUF; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], NUM_EPI_WARPS); }
@@ -281,6 +361,8 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
     __syncthreads();
     fence_after();
     const uint32_t tmem = *tmem_slot;
+#define CDS_VIEW(item_) make_view<BATCH>(item_, maps, P, mols, s_begin, nmol, E2, eps2, active, \
+                                         inv_scale, part)
 
     if (warp == 0) {
         if (lane == 0) {
@@ -291,18 +373,19 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
             for (int i = 0; i < NSTAGE; ++i) last_parity[i] = -1;
             bool ok = true;
             for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-                int term, t, s, A, B;
-                const TermR tm = decode(P, item, term, t, s, A, B);
-                if (active && !active[t]) continue;
-                const CUtensorMap* mq_hi = &maps.m[term][0];
-                const CUtensorMap* mq_lo = &maps.m[term][1];
-                const CUtensorMap* mb_hi = &maps.m[term][2];
-                const CUtensorMap* mb_lo = &maps.m[term][3];
+                const View v = CDS_VIEW(item);
+                if (!v.act) continue;
+                const int t = v.t, s = v.s, A = v.A, B = v.B;
+                const CUtensorMap* mq_hi = v.maps + 0;
+                const CUtensorMap* mq_lo = v.maps + 1;
+                const CUtensorMap* mb_hi = v.maps + 2;
+                const CUtensorMap* mb_lo = v.maps + 3;
                 const bool diag = A == B;
                 const uint32_t bytes = (diag ? 4u : 8u) * TILE_BYTES;
-                const int bA1 = tm.bulk_s_dim == 2 ? A * TB : s, bA2 = tm.bulk_s_dim == 2 ? s : A * TB;
-                const int bB1 = tm.bulk_s_dim == 2 ? B * TB : s, bB2 = tm.bulk_s_dim == 2 ? s : B * TB;
-                for (int kb = 0; kb < P.kblocks; ++kb) {
+                const bool sd2 = v.tm.bulk_s_dim == 2;
+                const int bA1 = sd2 ? A * TB : s, bA2 = sd2 ? s : A * TB;
+                const int bB1 = sd2 ? B * TB : s, bB2 = sd2 ? s : B * TB;
+                for (int kb = 0; kb < v.kblocks; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, verr)) { ok = false; break; }
                     mbar_arrive_expect_tx(&full[stage], bytes);
                     last_parity[stage] = (int32_t)phase;
@@ -333,15 +416,14 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
             uint32_t phase = 0, aphase = 0;
             bool ok = true;
             for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
-                int term, t, s, A, B;
-                decode(P, item, term, t, s, A, B);
-                if (active && !active[t]) continue;
-                const bool diag = A == B;
+                const View v = CDS_VIEW(item);
+                if (!v.act) continue;
+                const bool diag = v.A == v.B;
                 if (!mbar_wait(&tempty[acc], aphase ^ 1u, verr)) break;
                 fence_after();
                 const uint32_t d1 = tmem + (uint32_t)acc * 256u, d2 = d1 + 128u;
                 const uint32_t d1x = SEP ? tmem + 256u : d1, d2x = SEP ? tmem + 384u : d2;
-                for (int kb = 0; kb < P.kblocks; ++kb) {
+                for (int kb = 0; kb < v.kblocks; ++kb) {
                     if (!mbar_wait(&full[stage], phase, verr)) { ok = false; break; }
                     fence_after();
                     const uint32_t base = smem_u32(stages + stage * STAGE_BYTES);
@@ -376,24 +458,26 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
         const int quad = warp & 3;     // TMEM lanes this warp may read
         const int half = ew >> 2;      // column half of the tile
         const int row = quad * 32 + lane;
-        const float inv = *inv_scale;  // 1 / (s_A s_B) of the 16-bit split
         int acc = 0;
         uint32_t aphase = 0;
-        const int nE = P.nE;
         // orbital energies as float pairs, from shared memory when they fit
-        const float2* epsv = eps2;
-        if (P.nmo <= EPS_SMEM) {
+        const float2* seps_or_null = nullptr;
+        if (!BATCH && P.nmo <= EPS_SMEM) {
             for (int i = threadIdx.x - 64; i < P.nmo; i += 32 * NUM_EPI_WARPS) seps[i] = eps2[i];
             epi_bar();
-            epsv = seps;
+            seps_or_null = seps;
         }
         for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
-            int term, t, s, A, B;
-            const TermR tm = decode(P, item, term, t, s, A, B);
-            if (active && !active[t]) continue;
+            const View v = CDS_VIEW(item);
+            if (!v.act) continue;
+            const TermR& tm = v.tm;
+            const int nE = v.nE;
+            const float inv = v.inv;
+            const float2* epsv = seps_or_null ? seps_or_null : v.epsv;
             const bool bad = !mbar_wait(&tfull[acc], aphase, verr) || *verr;
             if (epi_any(bad)) break;
             fence_after();
+            const int s = v.s, A = v.A, B = v.B;
             const bool diag = A == B;
             const int x = A * TB + row;
             const bool xok = x < tm.nx;
@@ -407,9 +491,9 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
             const uint32_t ta2 = ta1 + 128u;
             const int ybase = B * TB + half * 64;
             const int ncols = min(64, tm.nx - ybase);             // valid columns of this half
-            const float2* Et = E2 + (int64_t)t * nE;
+            const float2* Et = v.Et;
             const float2* ey2 = epsv + tm.eps_x_off;
-            double* out = part + (tm.item0 + (item - tm.first)) * (int64_t)nE * 2;
+            double* out = v.out;
             for (int e0 = 0; e0 < nE; e0 += EC) {
                 const int ne = min(EC, nE - e0);
                 // c = E + e_s - e_x as a float pair (hi, lo)
@@ -504,6 +588,8 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[acc]);
             if (++acc == NBUF) { acc = 0; aphase ^= 1u; }
+            // completion time of the molecule's latest item (per-molecule latency)
+            if (stamps && ew == 0 && lane == 0) atomicMax(stamps + v.mol, gtimer());
         }
     }
 
@@ -514,6 +600,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const float2* __re
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS));
     }
+#undef CDS_VIEW
 }
 
 // amax[0] = max |x| over n doubles (non-negative doubles order like their bits).
@@ -707,10 +794,10 @@ namespace tc {
 template <int EC, bool BF16, bool SEP>
 static int launch_tc(int grid, const Maps& maps, const Params& P, const int32_t* active,
                      const TcLayout& lay, cudaStream_t stream) {
-    CDS_CUDA_TRY(cudaFuncSetAttribute(k_sigma_tc<EC, BF16, SEP>,
+    CDS_CUDA_TRY(cudaFuncSetAttribute(k_sigma_tc<EC, BF16, SEP, false>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    k_sigma_tc<EC, BF16, SEP><<<grid, THREADS, SMEM_BYTES, stream>>>(
-        maps, P, lay.E2, lay.eps2, active, lay.inv, lay.part, lay.err);
+    k_sigma_tc<EC, BF16, SEP, false><<<grid, THREADS, SMEM_BYTES, stream>>>(
+        maps, P, nullptr, 0, 0, lay.E2, lay.eps2, active, lay.inv, lay.part, nullptr, lay.err);
     CDS_LAUNCH_CHECK();
     return CDS_OK;
 }
@@ -824,6 +911,331 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
     k_tc_reduce<<<grid, 256, 0, stream>>>(lay.part, per0, P.term[0].nitems, per1, nE, active,
                                          lay.err, sigma, dsigma);
     CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
+
+// ===========================================================================
+// Batched form: the items of many molecules in one persistent launch.
+// ===========================================================================
+namespace tc {
+
+// Per-orbital reduction record of a batch (one per solved orbital).
+struct OrbRed {
+    int64_t base0, per0;     // element offset and count of the orbital's first-sum rows
+    int64_t base1, per1;     // and second-sum rows (rows are nE * 2 doubles)
+    int64_t out_off;         // sigma/dsigma offset of (orbital, energy 0)
+    int32_t nE, act_idx;
+};
+
+__global__ void k_tc_reduce_batch(const double* __restrict__ part, const OrbRed* __restrict__ orbs,
+                                  const int32_t* __restrict__ active,
+                                  const int32_t* __restrict__ err, double* __restrict__ sigma,
+                                  double* __restrict__ dsigma) {
+    const OrbRed o = orbs[blockIdx.y];
+    const int e = blockIdx.x;
+    if (e >= o.nE || (active && !active[o.act_idx])) return;
+    double sv = 0.0, dv = 0.0;
+    for (int64_t i = threadIdx.x; i < o.per0 + o.per1; i += blockDim.x) {
+        const int64_t at = (i < o.per0 ? o.base0 + i * o.nE * 2 : o.base1 + (i - o.per0) * o.nE * 2) + e * 2;
+        sv += part[at];
+        dv += part[at + 1];
+    }
+    __shared__ double ss[32], sd[32];
+    for (int off = 16; off; off >>= 1) {
+        sv += __shfl_xor_sync(0xffffffffu, sv, off);
+        dv += __shfl_xor_sync(0xffffffffu, dv, off);
+    }
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) { ss[w] = sv; sd[w] = dv; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += ss[i]; b += sd[i]; }
+        if (*err) a = b = __longlong_as_double(0x7ff8000000000000LL);
+        sigma[o.out_off + e] = a;
+        if (dsigma) dsigma[o.out_off + e] = b;
+    }
+}
+
+// 1/(s_A s_B) of molecule c into both descriptor sets.
+__global__ void k_inv_scale_batch(const unsigned long long* __restrict__ amax, int bf16, int nmol,
+                                  MolDesc* grid_set, MolDesc* newton_set) {
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nmol) return;
+    double sa = split_scale(amax + 2 * c, bf16 != 0), sb = split_scale(amax + 2 * c + 1, bf16 != 0);
+    float inv = (float)(1.0 / (sa * sb));
+    grid_set[c].inv = inv;
+    newton_set[c].inv = inv;
+}
+
+struct BatchLayout {
+    MolDesc* grid_set;
+    MolDesc* newton_set;
+    OrbRed* grid_red;
+    OrbRed* newton_red;
+    uint16_t *hi, *lo;          // split operands of all molecules
+    double* part;
+    unsigned long long* amax;   // [nmol][2]
+    float2* eps2;               // [sum nbf]
+    float2* E2;                 // [sum np*nE]
+    float2* w2;                 // [sum np]  (Newton energies)
+    int32_t* err;
+    size_t bytes;
+    int64_t grid_items, newton_items;
+};
+
+static int64_t mol_items(const BatchMol& b) {
+    return tc_items(b.nocc, b.nbf - b.nocc, b.np) + tc_items(b.nbf - b.nocc, b.nocc, b.np);
+}
+
+static BatchLayout batch_layout(void* ws, int32_t nmol, const BatchMol* mols) {
+    int64_t split = 0, nbf_all = 0, E_all = 0, np_all = 0, part_rows = 0, part_elems = 0;
+    for (int c = 0; c < nmol; ++c) {
+        const BatchMol& b = mols[c];
+        const int64_t Mp = padded(std::max(b.max_rank, 1));
+        split += ((int64_t)b.np * b.nbf + (int64_t)b.nocc * (b.nbf - b.nocc)) * Mp;
+        nbf_all += b.nbf;
+        E_all += (int64_t)b.np * b.nE;
+        np_all += b.np;
+        const int64_t it = mol_items(b);
+        part_rows += it;
+        part_elems += it * std::max(b.nE, 1) * 2;
+    }
+    Carver c(ws);
+    BatchLayout l;
+    l.grid_set = c.take<MolDesc>(std::max(nmol, 1));
+    l.newton_set = c.take<MolDesc>(std::max(nmol, 1));
+    l.grid_red = c.take<OrbRed>(std::max<int64_t>(np_all, 1));
+    l.newton_red = c.take<OrbRed>(std::max<int64_t>(np_all, 1));
+    l.hi = c.take<uint16_t>(std::max<int64_t>(split, 1));
+    l.lo = c.take<uint16_t>(std::max<int64_t>(split, 1));
+    l.part = c.take<double>(std::max<int64_t>(part_elems, 2));
+    l.amax = c.take<unsigned long long>(2 * std::max(nmol, 1));
+    l.eps2 = c.take<float2>(std::max<int64_t>(nbf_all, 1));
+    l.E2 = c.take<float2>(std::max<int64_t>(E_all, 1));
+    l.w2 = c.take<float2>(std::max<int64_t>(np_all, 1));
+    l.err = c.take<int32_t>(4);
+    l.bytes = c.off;
+    l.grid_items = part_rows;
+    l.newton_items = part_rows;
+    return l;
+}
+
+}  // namespace tc
+
+size_t tc_batch_workspace_bytes(int32_t nmol, const BatchMol* mols) {
+    return tc::batch_layout(nullptr, nmol, mols).bytes;
+}
+
+// Host part: tensor maps, descriptors and reduction records of both passes
+// (the 64-energy grid and the one-energy Newton pass), copied to the device
+// once; blocking (the records live in host memory until the copy is done).
+int tc_batch_setup(int32_t nmol, const BatchMol* mols, const int32_t* M, int32_t precision,
+                   void* ws, cudaStream_t stream) {
+    using namespace tc;
+    if (!device_ok()) return CDS_ERR_UNSUPPORTED;
+    const bool bf16 = precision == CDS_PREC_BF16X3;
+    BatchLayout lay = batch_layout(ws, nmol, mols);
+    std::vector<MolDesc> grid(nmol), newton(nmol);
+    std::vector<OrbRed> gred, nred;
+    int64_t split_off = 0, eps_off = 0, E_off = 0, w_off = 0, item_begin = 0, part_grid = 0,
+            part_newton = 0, out_grid = 0;
+    for (int c = 0; c < nmol; ++c) {
+        const BatchMol& b = mols[c];
+        const int32_t nbf = b.nbf, nocc = b.nocc, nv = nbf - nocc, np = b.np;
+        const int32_t Mp_cap = padded(std::max(b.max_rank, 1));
+        const int32_t Mp = padded(std::max(M[c], 1));
+        if (M[c] > b.max_rank) return CDS_ERR_ARG;
+        const uint16_t* lp_hi = lay.hi + split_off;
+        const uint16_t* lp_lo = lay.lo + split_off;
+        const uint16_t* ov_hi = lp_hi + (int64_t)np * nbf * Mp_cap;
+        const uint16_t* ov_lo = lp_lo + (int64_t)np * nbf * Mp_cap;
+        MolDesc d;
+        memset(&d, 0, sizeof(d));
+        const uint64_t rowb = (uint64_t)Mp * 2;   // rows are packed at the actual Mp
+        const int32_t nx[2] = {nocc, nv}, ns[2] = {nv, nocc};
+        int64_t it0 = 0;
+        for (int k = 0; k < 2; ++k) {
+            Term& tm = d.term[k];
+            tm.nx = nx[k];
+            tm.ns = ns[k];
+            tm.nb = nblocks_of(std::max(nx[k], 1), TB);
+            tm.npb = npairs_of(tm.nb);
+            tm.nitems = tc_items(nx[k], ns[k], np);
+            tm.item0 = it0;
+            it0 += tm.nitems;
+            tm.bulk_s_dim = k == 0 ? 1 : 2;
+            tm.eps_s_off = k == 0 ? nocc : 0;
+            tm.eps_x_off = k == 0 ? 0 : nocc;
+            if (tm.nitems == 0) continue;
+            const uint16_t* qh = lp_hi + (k == 0 ? 0 : (size_t)nocc * Mp);
+            const uint16_t* ql = lp_lo + (k == 0 ? 0 : (size_t)nocc * Mp);
+            bool ok = make_map(&d.m[k][0], bf16, qh, Mp, nx[k], np, rowb, rowb * nbf, TB, 1) &&
+                      make_map(&d.m[k][1], bf16, ql, Mp, nx[k], np, rowb, rowb * nbf, TB, 1) &&
+                      make_map(&d.m[k][2], bf16, ov_hi, Mp, nv, nocc, rowb, rowb * nv,
+                               k == 0 ? 1 : TB, k == 0 ? TB : 1) &&
+                      make_map(&d.m[k][3], bf16, ov_lo, Mp, nv, nocc, rowb, rowb * nv,
+                               k == 0 ? 1 : TB, k == 0 ? TB : 1);
+            if (!ok) return CDS_ERR_CUDA;
+        }
+        d.kblocks = Mp / KB;
+        d.nmo = nbf;
+        d.eps_off = eps_off;
+        d.act_off = (int32_t)w_off;
+        d.inv = 1.f;
+        d.item_begin = item_begin;
+        MolDesc g = d, n = d;
+        g.nE = b.nE;
+        g.E_off = E_off;
+        g.part_base = part_grid;
+        n.nE = 1;
+        n.E_off = w_off;
+        n.part_base = part_newton;
+        grid[c] = g;
+        newton[c] = n;
+        const int64_t per0 = np ? d.term[0].nitems / np : 0, per1 = np ? d.term[1].nitems / np : 0;
+        for (int t = 0; t < np; ++t) {
+            OrbRed r;
+            r.per0 = per0;
+            r.per1 = per1;
+            r.base0 = part_grid + t * per0 * b.nE * 2;
+            r.base1 = part_grid + (d.term[0].nitems + t * per1) * b.nE * 2;
+            r.nE = b.nE;
+            r.out_off = out_grid + (int64_t)t * b.nE;
+            r.act_idx = (int32_t)(w_off + t);
+            gred.push_back(r);
+            r.base0 = part_newton + t * per0 * 2;
+            r.base1 = part_newton + (d.term[0].nitems + t * per1) * 2;
+            r.nE = 1;
+            r.out_off = w_off + t;
+            nred.push_back(r);
+        }
+        const int64_t items = d.term[0].nitems + d.term[1].nitems;
+        item_begin += items;
+        part_grid += items * b.nE * 2;
+        part_newton += items * 2;
+        split_off += ((int64_t)np * nbf + (int64_t)nocc * nv) * Mp_cap;
+        eps_off += nbf;
+        E_off += (int64_t)np * b.nE;
+        out_grid += (int64_t)np * b.nE;
+        w_off += np;
+    }
+    CDS_CUDA_TRY(cudaMemcpyAsync(lay.grid_set, grid.data(), sizeof(MolDesc) * nmol,
+                                 cudaMemcpyHostToDevice, stream));
+    CDS_CUDA_TRY(cudaMemcpyAsync(lay.newton_set, newton.data(), sizeof(MolDesc) * nmol,
+                                 cudaMemcpyHostToDevice, stream));
+    if (!gred.empty()) {
+        CDS_CUDA_TRY(cudaMemcpyAsync(lay.grid_red, gred.data(), sizeof(OrbRed) * gred.size(),
+                                     cudaMemcpyHostToDevice, stream));
+        CDS_CUDA_TRY(cudaMemcpyAsync(lay.newton_red, nred.data(), sizeof(OrbRed) * nred.size(),
+                                     cudaMemcpyHostToDevice, stream));
+    }
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    return CDS_OK;
+}
+
+// Device part 1 (capturable): float pairs of eps, the 16-bit split of every
+// molecule's factors (rows packed at the molecule's actual Mp) and the split
+// scales.  Lov/Lp/eps offsets come from the same table as tc_batch_setup.
+int tc_batch_split(int32_t nmol, const BatchMol* mols, const int32_t* M, const BatchOffsets* off,
+                   const double* Lov, const double* Lp, const double* eps, int32_t precision,
+                   void* ws, cudaStream_t stream) {
+    using namespace tc;
+    const bool bf16 = precision == CDS_PREC_BF16X3;
+    BatchLayout lay = batch_layout(ws, nmol, mols);
+    int64_t split_off = 0, nbf_all = 0;
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.amax, 0, sizeof(unsigned long long) * 2 * nmol, stream));
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.err, 0, sizeof(int32_t), stream));
+    for (int c = 0; c < nmol; ++c) {
+        const BatchMol& b = mols[c];
+        const int32_t nbf = b.nbf, nocc = b.nocc, nv = nbf - nocc, np = b.np;
+        const int32_t Mp_cap = padded(std::max(b.max_rank, 1));
+        const int32_t Mp = padded(std::max(M[c], 1));
+        const double* lp = Lp + off[c].p;
+        const double* lov = Lov + off[c].ov;
+        uint16_t* lp_hi = lay.hi + split_off;
+        uint16_t* lp_lo = lay.lo + split_off;
+        uint16_t* ov_hi = lp_hi + (int64_t)np * nbf * Mp_cap;
+        uint16_t* ov_lo = lp_lo + (int64_t)np * nbf * Mp_cap;
+        const int64_t rp = (int64_t)np * nbf, ro = (int64_t)nocc * nv;
+        if (!bf16) {
+            if (rp) { k_absmax<<<2 * 152, 256, 0, stream>>>(lp, rp * M[c], lay.amax + 2 * c); CDS_LAUNCH_CHECK(); }
+            if (ro) { k_absmax<<<2 * 152, 256, 0, stream>>>(lov, ro * M[c], lay.amax + 2 * c + 1); CDS_LAUNCH_CHECK(); }
+        }
+        if (rp) {
+            if (bf16)
+                k_split16<__nv_bfloat16><<<(unsigned)((rp * Mp + 255) / 256), 256, 0, stream>>>(
+                    lp, rp, M[c], Mp, lay.amax + 2 * c, (__nv_bfloat16*)lp_hi, (__nv_bfloat16*)lp_lo);
+            else
+                k_split16<__half><<<(unsigned)((rp * Mp + 255) / 256), 256, 0, stream>>>(
+                    lp, rp, M[c], Mp, lay.amax + 2 * c, (__half*)lp_hi, (__half*)lp_lo);
+            CDS_LAUNCH_CHECK();
+        }
+        if (ro) {
+            if (bf16)
+                k_split16<__nv_bfloat16><<<(unsigned)((ro * Mp + 255) / 256), 256, 0, stream>>>(
+                    lov, ro, M[c], Mp, lay.amax + 2 * c + 1, (__nv_bfloat16*)ov_hi, (__nv_bfloat16*)ov_lo);
+            else
+                k_split16<__half><<<(unsigned)((ro * Mp + 255) / 256), 256, 0, stream>>>(
+                    lov, ro, M[c], Mp, lay.amax + 2 * c + 1, (__half*)ov_hi, (__half*)ov_lo);
+            CDS_LAUNCH_CHECK();
+        }
+        k_to_pairs<<<(nbf + 255) / 256, 256, 0, stream>>>(eps + off[c].eps, nbf, lay.eps2 + nbf_all);
+        CDS_LAUNCH_CHECK();
+        split_off += ((int64_t)np * nbf + (int64_t)nocc * nv) * Mp_cap;
+        nbf_all += nbf;
+    }
+    k_inv_scale_batch<<<(nmol + 127) / 128, 128, 0, stream>>>(lay.amax, bf16 ? 1 : 0, nmol,
+                                                              lay.grid_set, lay.newton_set);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
+// Device part 2 (capturable): one persistent launch over every molecule's
+// items, then the per-orbital reduction.  pass 0: grid energies E (batch
+// order [mol][orbital][energy]); pass 1: Newton, one energy per orbital from
+// E (batch order [mol][orbital]) with the active mask.
+int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_total,
+                  int32_t max_nE, int64_t np_total, const double* E, const int32_t* active,
+                  int32_t precision, double* sigma, double* dsigma, unsigned long long* stamps,
+                  void* ws, cudaStream_t stream) {
+    using namespace tc;
+    const bool bf16 = precision == CDS_PREC_BF16X3;
+    BatchLayout lay = batch_layout(ws, nmol, mols);
+    float2* Ep = pass == 0 ? lay.E2 : lay.w2;
+    const int64_t nE_pairs = pass == 0 ? nE_total : np_total;
+    if (nE_pairs > 0) {
+        k_to_pairs<<<(unsigned)((nE_pairs + 255) / 256), 256, 0, stream>>>(E, nE_pairs, Ep);
+        CDS_LAUNCH_CHECK();
+    }
+    const MolDesc* set = pass == 0 ? lay.grid_set : lay.newton_set;
+    const int64_t nitems = lay.grid_items;
+    if (nitems > 0) {
+        const int grid = (int)std::min<int64_t>(nitems, device_sms());
+        Maps dummy_maps;
+        memset(&dummy_maps, 0, sizeof(dummy_maps));
+        Params dummy{};
+        const float2* epsv = lay.eps2;
+        if (pass == 1) {
+            auto kern = bf16 ? k_sigma_tc<1, true, true, true> : k_sigma_tc<1, false, true, true>;
+            CDS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+            kern<<<grid, THREADS, SMEM_BYTES, stream>>>(dummy_maps, dummy, set, nmol, nitems, Ep, epsv,
+                                                        active, nullptr, lay.part, stamps, lay.err);
+        } else {
+            auto kern = bf16 ? k_sigma_tc<16, true, true, true> : k_sigma_tc<16, false, true, true>;
+            CDS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+            kern<<<grid, THREADS, SMEM_BYTES, stream>>>(dummy_maps, dummy, set, nmol, nitems, Ep, epsv,
+                                                        nullptr, nullptr, lay.part, stamps, lay.err);
+        }
+        CDS_LAUNCH_CHECK();
+    }
+    if (np_total > 0) {
+        dim3 g((unsigned)std::max(pass == 0 ? max_nE : 1, 1), (unsigned)np_total);
+        k_tc_reduce_batch<<<g, 256, 0, stream>>>(lay.part, pass == 0 ? lay.grid_red : lay.newton_red,
+                                                 pass == 0 ? nullptr : active, lay.err, sigma, dsigma);
+        CDS_LAUNCH_CHECK();
+    }
     return CDS_OK;
 }
 

@@ -12,6 +12,26 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
               const int32_t* active, int32_t precision, double* sigma, double* dsigma, void* ws,
               cudaStream_t stream);
 
+// One molecule of a batch (host side) and the element offsets of its arrays
+// in the concatenated batch buffers.
+struct BatchMol {
+    int32_t nbf, nocc, np, nE, max_rank;
+};
+struct BatchOffsets {
+    int64_t basis, pair, L, piv, C, eps, orb, E, ov, p;
+};
+
+size_t tc_batch_workspace_bytes(int32_t nmol, const BatchMol* mols);
+int tc_batch_setup(int32_t nmol, const BatchMol* mols, const int32_t* M, int32_t precision,
+                   void* ws, cudaStream_t stream);
+int tc_batch_split(int32_t nmol, const BatchMol* mols, const int32_t* M, const BatchOffsets* off,
+                   const double* Lov, const double* Lp, const double* eps, int32_t precision,
+                   void* ws, cudaStream_t stream);
+int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_total,
+                  int32_t max_nE, int64_t np_total, const double* E, const int32_t* active,
+                  int32_t precision, double* sigma, double* dsigma, unsigned long long* stamps,
+                  void* ws, cudaStream_t stream);
+
 inline bool is_split16(int32_t precision) {
     return precision == CDS_PREC_BF16X3 || precision == CDS_PREC_FP16X3;
 }
