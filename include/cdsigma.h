@@ -292,6 +292,20 @@ int cds_batch_graph_create(int32_t nmol, const cds_mol* mols, const int32_t* M, 
 int cds_graph_launch(cds_graph* graph, cudaStream_t stream);
 int cds_graph_destroy(cds_graph* graph);
 
+/* ------------------------------------------------------------------------
+ * Kernel configuration of the tensor-core self-energy, process-wide (no
+ * counterpart in the paper; set by the autotuner, which times graph replays
+ * of a batch and keeps the fastest choice).
+ *   CDS_TUNE_ENERGY_CHUNK: energies per epilogue pass of the batched grid
+ *     pass, 8 or 16 (default 16);
+ *   CDS_TUNE_ITEM_ORDER: 0 = work items interleaved across the persistent
+ *     CTAs (default), 1 = each CTA takes a contiguous range.
+ * Graphs keep the configuration they were captured with.
+ * ---------------------------------------------------------------------- */
+enum { CDS_TUNE_ENERGY_CHUNK = 0, CDS_TUNE_ITEM_ORDER = 1 };
+int cds_tune_set(int32_t knob, int32_t value);   /* CDS_ERR_ARG on an invalid pair */
+int cds_tune_get(int32_t knob);                  /* -1 for an unknown knob */
+
 #ifdef __cplusplus
 }
 #endif

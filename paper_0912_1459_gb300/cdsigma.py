@@ -82,6 +82,8 @@ _SIGNATURES.update({
                                               _vp, _i32, _f64, _i32, _vp, _vp, _vp, _vp, _vp, _vp,
                                               _vp, _vp, _sz, ctypes.POINTER(_vp)]),
     "cds_graph_launch": (ctypes.c_int, [_vp, _vp]),
+    "cds_tune_set": (ctypes.c_int, [_i32, _i32]),
+    "cds_tune_get": (ctypes.c_int, [_i32]),
     "cds_graph_destroy": (ctypes.c_int, [_vp]),
 })
 
@@ -436,3 +438,14 @@ class BatchGraph:
         if getattr(self, "h", None):
             self.lib.cds_graph_destroy(self.h)
             self.h = None
+
+
+TUNE_ENERGY_CHUNK, TUNE_ITEM_ORDER = 0, 1
+
+
+def cds_tune_set(knob: int, value: int) -> None:
+    _check(load().cds_tune_set(knob, value), "cds_tune_set")
+
+
+def cds_tune_get(knob: int) -> int:
+    return int(load().cds_tune_get(knob))

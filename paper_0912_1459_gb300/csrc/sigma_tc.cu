@@ -33,6 +33,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <type_traits>
+#include <atomic>
 #include <vector>
 
 #include "sigma_tc.cuh"
@@ -316,13 +317,24 @@ __device__ __forceinline__ View make_view(int64_t item, const Maps& maps, const 
 // (4 x 128 columns, one buffer); otherwise all three share one tile and two
 // buffers alternate between items.  BATCH: items of many molecules, described
 // by MolDesc records in global memory, in one persistent launch.
+// Items of CTA c: interleaved (c, c + G, c + 2G, ...) or, with blocked order,
+// the contiguous range [c n / G, (c + 1) n / G).  k-th item, or -1 when done.
+__device__ __forceinline__ int64_t item_at(int64_t k, int64_t n, int order) {
+    if (order == 0) {
+        const int64_t it = blockIdx.x + k * gridDim.x;
+        return it < n ? it : -1;
+    }
+    const int64_t b = n * blockIdx.x / gridDim.x, e = n * (blockIdx.x + 1) / gridDim.x;
+    return b + k < e ? b + k : -1;
+}
+
 template <int EC, bool BF16, bool SEP, bool BATCH>
 __global__ void __launch_bounds__(THREADS, 1)
 k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __restrict__ mols,
            int32_t nmol, int64_t nitems_batch, const float2* __restrict__ E2,
            const float2* __restrict__ eps2, const int32_t* __restrict__ active,
            const float* __restrict__ inv_scale, double* __restrict__ part,
-           unsigned long long* __restrict__ stamps, int32_t* __restrict__ err) {
+           unsigned long long* __restrict__ stamps, int32_t* __restrict__ err, int32_t order) {
     constexpr uint32_t ID = idesc<BF16>();
     constexpr int NBUF = SEP ? 1 : 2;
     extern __shared__ uint8_t smem_raw[];
@@ -372,7 +384,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
             int32_t last_parity[NSTAGE];
             for (int i = 0; i < NSTAGE; ++i) last_parity[i] = -1;
             bool ok = true;
-            for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            for (int64_t kq = 0, item; ok && (item = item_at(kq, nitems, order)) >= 0; ++kq) {
                 const View v = CDS_VIEW(item);
                 if (!v.act) continue;
                 const int t = v.t, s = v.s, A = v.A, B = v.B;
@@ -415,7 +427,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
             int stage = 0, acc = 0;
             uint32_t phase = 0, aphase = 0;
             bool ok = true;
-            for (int64_t item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            for (int64_t kq = 0, item; ok && (item = item_at(kq, nitems, order)) >= 0; ++kq) {
                 const View v = CDS_VIEW(item);
                 if (!v.act) continue;
                 const bool diag = v.A == v.B;
@@ -467,7 +479,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
             epi_bar();
             seps_or_null = seps;
         }
-        for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        for (int64_t kq = 0, item; (item = item_at(kq, nitems, order)) >= 0; ++kq) {
             const View v = CDS_VIEW(item);
             if (!v.act) continue;
             const TermR& tm = v.tm;
@@ -754,6 +766,13 @@ bool make_map(CUtensorMap* m, bool bf16, const void* base, uint64_t d0, uint64_t
     return r == CUDA_SUCCESS;
 }
 
+// Run-time kernel configuration chosen by the autotuner (cds_tune_set):
+// energies per epilogue pass of the batched grid pass, and item order.
+static std::atomic<int> g_energy_chunk{16};
+static std::atomic<int> g_item_order{0};
+int tune_energy_chunk() { return g_energy_chunk.load(); }
+int tune_item_order() { return g_item_order.load(); }
+
 // Separate hi.hi / cross accumulators (default) or the shared double-buffered
 // form; CDS_TC_SHARED_ACC=1 selects the latter (for comparisons).
 bool separate_accumulators() {
@@ -797,7 +816,8 @@ static int launch_tc(int grid, const Maps& maps, const Params& P, const int32_t*
     CDS_CUDA_TRY(cudaFuncSetAttribute(k_sigma_tc<EC, BF16, SEP, false>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     k_sigma_tc<EC, BF16, SEP, false><<<grid, THREADS, SMEM_BYTES, stream>>>(
-        maps, P, nullptr, 0, 0, lay.E2, lay.eps2, active, lay.inv, lay.part, nullptr, lay.err);
+        maps, P, nullptr, 0, 0, lay.E2, lay.eps2, active, lay.inv, lay.part, nullptr, lay.err,
+        tune_item_order());
     CDS_LAUNCH_CHECK();
     return CDS_OK;
 }
@@ -1217,17 +1237,18 @@ int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_t
         memset(&dummy_maps, 0, sizeof(dummy_maps));
         Params dummy{};
         const float2* epsv = lay.eps2;
-        if (pass == 1) {
-            auto kern = bf16 ? k_sigma_tc<1, true, true, true> : k_sigma_tc<1, false, true, true>;
-            CDS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-            kern<<<grid, THREADS, SMEM_BYTES, stream>>>(dummy_maps, dummy, set, nmol, nitems, Ep, epsv,
-                                                        active, nullptr, lay.part, stamps, lay.err);
-        } else {
-            auto kern = bf16 ? k_sigma_tc<16, true, true, true> : k_sigma_tc<16, false, true, true>;
-            CDS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-            kern<<<grid, THREADS, SMEM_BYTES, stream>>>(dummy_maps, dummy, set, nmol, nitems, Ep, epsv,
-                                                        nullptr, nullptr, lay.part, stamps, lay.err);
-        }
+        const int order = tune_item_order();
+        decltype(&k_sigma_tc<1, true, true, true>) kern;
+        if (pass == 1)
+            kern = bf16 ? k_sigma_tc<1, true, true, true> : k_sigma_tc<1, false, true, true>;
+        else if (tune_energy_chunk() == 8)
+            kern = bf16 ? k_sigma_tc<8, true, true, true> : k_sigma_tc<8, false, true, true>;
+        else
+            kern = bf16 ? k_sigma_tc<16, true, true, true> : k_sigma_tc<16, false, true, true>;
+        CDS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
+        kern<<<grid, THREADS, SMEM_BYTES, stream>>>(dummy_maps, dummy, set, nmol, nitems, Ep, epsv,
+                                                    pass == 1 ? active : nullptr, nullptr, lay.part,
+                                                    stamps, lay.err, order);
         CDS_LAUNCH_CHECK();
     }
     if (np_total > 0) {
@@ -1240,3 +1261,25 @@ int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_t
 }
 
 }  // namespace cds
+
+extern "C" int cds_tune_set(int32_t knob, int32_t value) {
+    using namespace cds::tc;
+    if (knob == CDS_TUNE_ENERGY_CHUNK) {
+        if (value != 8 && value != 16) return CDS_ERR_ARG;
+        g_energy_chunk = value;
+        return CDS_OK;
+    }
+    if (knob == CDS_TUNE_ITEM_ORDER) {
+        if (value != 0 && value != 1) return CDS_ERR_ARG;
+        g_item_order = value;
+        return CDS_OK;
+    }
+    return CDS_ERR_ARG;
+}
+
+extern "C" int cds_tune_get(int32_t knob) {
+    using namespace cds::tc;
+    if (knob == CDS_TUNE_ENERGY_CHUNK) return g_energy_chunk.load();
+    if (knob == CDS_TUNE_ITEM_ORDER) return g_item_order.load();
+    return -1;
+}
