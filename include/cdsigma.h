@@ -214,6 +214,37 @@ int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
                  size_t workspace_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Adjoint (no counterpart in the paper, which does not differentiate; the
+ * derivative of Eq. SE, Eq. iter and Eq. transformation).  For a loss l of
+ * converged quasiparticle energies w_t with upstream gradients g_t:
+ *   dl/dtheta = sum_t g_t P_t (de_qt/dtheta + dSigma_t/dtheta),
+ *   P_t = 1/(1 - dSigma_t/dw) at w_t (the implicit-function theorem),
+ * with dSigma/dX_xy = (4 X_xy - 2 X_yx) / D_xy for the MO integrals
+ * X = (qx|sy), recomputed tile by tile in FP64 (never stored).
+ * ---------------------------------------------------------------------- */
+
+size_t cds_qp_gradient_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np);
+
+/* Asynchronous, FP64.  Inputs as cds_qp_solve plus omega (device [np],
+ * converged roots) and g (device [np] upstream gradients).  Outputs (device):
+ * d_eps [nmo], d_Lov [nocc][nmo-nocc][M], d_Lp [np][nmo][M].  Workspace holds
+ * dSigma/dX for every orbital: np*(o*v*o + v*o*v) doubles plus copies of the
+ * factors.  Requires 0 < nocc < nmo. */
+int cds_qp_gradient(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
+                    const int32_t* orb, int32_t np, const double* eps, const double* omega,
+                    const double* g, double* d_eps, double* d_Lov, double* d_Lp, void* workspace,
+                    size_t workspace_bytes, cudaStream_t stream);
+
+size_t cds_cd_to_mo_backward_workspace_bytes(int32_t nbf, int32_t nmo, int32_t np);
+
+/* Asynchronous, FP64.  dl/dC [nbf][nmo] (device, overwritten) from dl/dLov
+ * and dl/dLp through the transform of cds_cd_to_mo. */
+int cds_cd_to_mo_backward(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
+                          const double* C, const int32_t* orb, int32_t np, const double* dLov,
+                          const double* dLp, double* dC, void* workspace, size_t workspace_bytes,
+                          cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Batched form: many molecules of uneven size, orbital and energy counts in
  * one call per stage (not in the paper, which treats one molecule; each
  * molecule's results are those of the single-molecule calls above).

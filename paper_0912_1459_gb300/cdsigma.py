@@ -449,3 +449,97 @@ def cds_tune_set(knob: int, value: int) -> None:
 
 def cds_tune_get(knob: int) -> int:
     return int(load().cds_tune_get(knob))
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------
+_SIGNATURES.update({
+    "cds_qp_gradient_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32]),
+    "cds_qp_gradient": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp,
+                                       _vp, _vp, _vp, _sz, _vp]),
+    "cds_cd_to_mo_backward_workspace_bytes": (_sz, [_i32, _i32, _i32]),
+    "cds_cd_to_mo_backward": (ctypes.c_int, [_i32, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp,
+                                             _vp, _vp, _sz, _vp]),
+})
+
+
+def cds_qp_gradient(Lov, Lp, orbitals, eps, nocc, omega, g):
+    """dl/d(eps, Lov, Lp) for upstream gradients g of converged roots omega."""
+    lib = load()
+    Lov = _dev(Lov, torch.float64, "Lov")
+    Lp = _dev(Lp, torch.float64, "Lp")
+    orb = _dev(orbitals, torch.int32, "orbitals")
+    eps = _dev(eps, torch.float64, "eps")
+    omega = _dev(omega, torch.float64, "omega")
+    g = _dev(g, torch.float64, "g")
+    dev = Lp.device
+    np_, nmo, M = Lp.shape
+    d_eps = torch.empty(nmo, dtype=torch.float64, device=dev)
+    d_Lov = torch.empty_like(Lov)
+    d_Lp = torch.empty_like(Lp)
+    ws = _workspace(lib.cds_qp_gradient_workspace_bytes(nmo, nocc, M, np_), dev)
+    _check(lib.cds_qp_gradient(nmo, nocc, M, _p(Lov), _p(Lp), _p(orb), np_, _p(eps), _p(omega),
+                               _p(g), _p(d_eps), _p(d_Lov), _p(d_Lp), _p(ws), ws.numel(),
+                               _stream(dev)), "cds_qp_gradient")
+    return d_eps, d_Lov, d_Lp
+
+
+def cds_cd_to_mo_backward(L, C, nocc, orbitals, d_Lov, d_Lp):
+    """dl/dC from dl/dLov and dl/dLp through the AO->MO transform."""
+    lib = load()
+    L = _dev(L, torch.float64, "L")
+    C = _dev(C, torch.float64, "C")
+    orb = _dev(orbitals, torch.int32, "orbitals")
+    d_Lov = _dev(d_Lov, torch.float64, "d_Lov")
+    d_Lp = _dev(d_Lp, torch.float64, "d_Lp")
+    nbf, nmo = C.shape
+    dC = torch.empty_like(C)
+    ws = _workspace(lib.cds_cd_to_mo_backward_workspace_bytes(nbf, nmo, orb.shape[0]), C.device)
+    _check(lib.cds_cd_to_mo_backward(nbf, nmo, nocc, L.shape[0], _p(L), _p(C), _p(orb), orb.shape[0],
+                                     _p(d_Lov), _p(d_Lp), _p(dC), _p(ws), ws.numel(),
+                                     _stream(C.device)), "cds_cd_to_mo_backward")
+    return dC
+
+
+class QPEnergies(torch.autograd.Function):
+    """Quasiparticle energies of the given orbitals as a differentiable
+    function of (eps, Lov, Lp): forward = cds_qp_solve, backward = the
+    hand-written adjoint (cds_qp_gradient) at the converged roots."""
+
+    @staticmethod
+    def forward(ctx, eps, Lov, Lp, orbitals, nocc, conv=1e-12, max_iter=100, precision="fp64"):
+        w, P, it, st = cds_qp_solve(Lov, Lp, orbitals, eps, nocc, conv=conv, max_iter=max_iter,
+                                    precision=precision)
+        ctx.save_for_backward(eps, Lov, Lp, orbitals, w)
+        ctx.nocc = nocc
+        ctx.mark_non_differentiable(st)
+        return w, st
+
+    @staticmethod
+    def backward(ctx, gw, gst):
+        eps, Lov, Lp, orbitals, w = ctx.saved_tensors
+        if gw is None:
+            return (None,) * 8
+        d_eps, d_Lov, d_Lp = cds_qp_gradient(Lov, Lp, orbitals, eps, ctx.nocc, w, gw.contiguous())
+        return d_eps, d_Lov, d_Lp, None, None, None, None, None
+
+
+class MOFactors(torch.autograd.Function):
+    """(Lov, Lp) = cds_cd_to_mo(L, C) with the transform adjoint for dC."""
+
+    @staticmethod
+    def forward(ctx, C, L, nocc, orbitals):
+        Lov, Lp = cds_cd_to_mo(L, C, nocc, orbitals)
+        ctx.save_for_backward(C, L, orbitals)
+        ctx.nocc = nocc
+        return Lov, Lp
+
+    @staticmethod
+    def backward(ctx, g_ov, g_p):
+        C, L, orbitals = ctx.saved_tensors
+        g_ov = torch.zeros((ctx.nocc, C.shape[1] - ctx.nocc, L.shape[0]), dtype=torch.float64,
+                           device=C.device) if g_ov is None else g_ov.contiguous()
+        g_p = torch.zeros((orbitals.shape[0], C.shape[1], L.shape[0]), dtype=torch.float64,
+                          device=C.device) if g_p is None else g_p.contiguous()
+        return cds_cd_to_mo_backward(L, C, ctx.nocc, orbitals, g_ov, g_p), None, None, None

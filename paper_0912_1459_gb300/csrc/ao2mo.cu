@@ -33,7 +33,7 @@ struct StridedOut {
 
 // C[b] (m x n) = A[b] (m x k) * B[b] (k x n), all operands by strides.
 // A_M_CONTIG: A's unit stride is along m; B_N_CONTIG: B's unit stride is along n.
-template <bool A_M_CONTIG, bool B_N_CONTIG>
+template <bool A_M_CONTIG, bool B_N_CONTIG, bool ACC = false>
 __global__ void __launch_bounds__(256)
 k_dgemm(int m, int n, int k, StridedMat A, StridedMat B, StridedOut C) {
     __shared__ double As[kGK][kGB + 1];
@@ -84,7 +84,10 @@ k_dgemm(int m, int n, int k, StridedMat A, StridedMat B, StridedOut C) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             int gn = n0 + tc + 16 * j;
-            if (gn < n) Cb[gm * C.rs + gn * C.cs] = acc[i][j];
+            if (gn < n) {
+                double* dst = Cb + gm * C.rs + gn * C.cs;
+                *dst = ACC ? *dst + acc[i][j] : acc[i][j];
+            }
         }
     }
 }
@@ -232,14 +235,57 @@ __global__ void k_gather_cols(const double* __restrict__ C, int32_t N, int32_t n
     Cp[e] = (p >= 0 && p < nmo) ? C[(int64_t)mu * nmo + p] : __longlong_as_double(0x7ff8000000000000LL);
 }
 
-template <bool AM, bool BN>
+template <bool AM, bool BN, bool ACC = false>
 static int launch_dgemm(int m, int n, int k, int batch, StridedMat A, StridedMat B, StridedOut C,
                         cudaStream_t s) {
     if (m <= 0 || n <= 0 || batch <= 0) return CDS_OK;
     dim3 grid((n + kGB - 1) / kGB, (m + kGB - 1) / kGB, batch);
-    k_dgemm<AM, BN><<<grid, 256, 0, s>>>(m, n, k, A, B, C);
+    k_dgemm<AM, BN, ACC><<<grid, 256, 0, s>>>(m, n, k, A, B, C);
     CDS_LAUNCH_CHECK();
     return CDS_OK;
+}
+
+// Strided-batched FP64 GEMM for other translation units; picks the load
+// pattern from the unit strides.  accumulate: C += A B (batch entries must
+// then write disjoint C).
+int launch_dgemm_strided(int m, int n, int k, int batch, const double* A, int64_t ars, int64_t acs,
+                         int64_t abs_, const double* B, int64_t brs, int64_t bcs, int64_t bbs,
+                         double* C, int64_t crs, int64_t ccs, int64_t cbs, cudaStream_t s,
+                         bool accumulate = false) {
+    StridedMat Am{A, ars, acs, abs_}, Bm{B, brs, bcs, bbs};
+    StridedOut Cm{C, crs, ccs, cbs};
+    const bool am = ars == 1, bn = bcs == 1;
+    if (accumulate) {
+        if (am && bn) return launch_dgemm<true, true, true>(m, n, k, batch, Am, Bm, Cm, s);
+        if (am) return launch_dgemm<true, false, true>(m, n, k, batch, Am, Bm, Cm, s);
+        if (bn) return launch_dgemm<false, true, true>(m, n, k, batch, Am, Bm, Cm, s);
+        return launch_dgemm<false, false, true>(m, n, k, batch, Am, Bm, Cm, s);
+    }
+    if (am && bn) return launch_dgemm<true, true>(m, n, k, batch, Am, Bm, Cm, s);
+    if (am) return launch_dgemm<true, false>(m, n, k, batch, Am, Bm, Cm, s);
+    if (bn) return launch_dgemm<false, true>(m, n, k, batch, Am, Bm, Cm, s);
+    return launch_dgemm<false, false>(m, n, k, batch, Am, Bm, Cm, s);
+}
+
+// U2[mu][b][nu] = L[K0+b][pair(mu,nu)] (vector index inside the row, so the
+// contraction over (vector, nu) is one GEMM dimension).
+__global__ void k_unpack_t(const double* __restrict__ L, int64_t npair, int32_t K0, int32_t kb,
+                           int32_t N, double* __restrict__ U2) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= (int64_t)N * kb * N) return;
+    const int nu = (int)(e % N);
+    const int64_t r = e / N;
+    const int b = (int)(r % kb), mu = (int)(r / kb);
+    const int lo = min(mu, nu), hi = max(mu, nu);
+    U2[e] = L[(int64_t)(K0 + b) * npair + (int64_t)hi * (hi + 1) / 2 + lo];
+}
+
+// dC[mu][orb[t]] += dCp[mu][t]
+__global__ void k_scatter_cols(const double* __restrict__ dCp, int32_t N, int32_t np,
+                               const int32_t* __restrict__ orb, int32_t nmo, double* __restrict__ dC) {
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    for (int t = 0; t < np; ++t) dC[(int64_t)e * nmo + orb[t]] += dCp[(int64_t)e * np + t];
 }
 
 template <bool AM, bool BN, typename TOut>
@@ -377,6 +423,86 @@ extern "C" int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, c
             st = launch_dgemm<false, true>(np, nmo, N, kb, Top, Call, Out, stream);
             if (st) return st;
         }
+    }
+    return CDS_OK;
+}
+
+// Adjoint of the transform: given dl/dLov and dl/dLp, dl/dC through
+//   Lov^K = C_occ^T A^K C_vir,   Lp^K[t] = C_{.,q_t}^T A^K C   (Eq. transformation):
+//   dC_occ += A^K C_vir dLov^K^T,  dC_vir += A^K C_occ dLov^K,
+//   dC_{.,q_t} += A^K C dLp^K[t]^T,  dC += A^K C_P dLp^K.
+extern "C" size_t cds_cd_to_mo_backward_workspace_bytes(int32_t nbf, int32_t nmo, int32_t np) {
+    if (nbf <= 0 || nmo <= 0 || np < 0) return 0;
+    Carver c(nullptr);
+    c.take<double>((size_t)nbf * kAoBatch * nbf);                       // U2
+    c.take<double>((size_t)kAoBatch * nbf * std::max(nmo, np));          // T
+    c.take<double>((size_t)nbf * std::max(np, 1));                       // C_P, dCp
+    c.take<double>((size_t)nbf * std::max(np, 1));
+    return c.off;
+}
+
+extern "C" int cds_cd_to_mo_backward(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M,
+                                     const double* L, const double* C, const int32_t* orb,
+                                     int32_t np, const double* dLov, const double* dLp,
+                                     double* dC, void* workspace, size_t workspace_bytes,
+                                     cudaStream_t stream) {
+    if (nbf <= 0 || nmo <= 0 || nmo > nbf || nocc <= 0 || nocc >= nmo || M < 0 || np < 0)
+        return CDS_ERR_ARG;
+    if (!L || !C || !dLov || !dC || (np > 0 && (!orb || !dLp))) return CDS_ERR_ARG;
+    if (!workspace || workspace_bytes < cds_cd_to_mo_backward_workspace_bytes(nbf, nmo, np))
+        return CDS_ERR_WORKSPACE;
+    const int32_t N = nbf, nv = nmo - nocc;
+    const int64_t npair = npair_of(nbf);
+    Carver cv(workspace);
+    double* U2 = cv.take<double>((size_t)N * kAoBatch * N);
+    double* T = cv.take<double>((size_t)kAoBatch * N * std::max(nmo, np));
+    double* Cp = cv.take<double>((size_t)N * std::max(np, 1));
+    double* dCp = cv.take<double>((size_t)N * std::max(np, 1));
+    CDS_CUDA_TRY(cudaMemsetAsync(dC, 0, sizeof(double) * (size_t)N * nmo, stream));
+    if (np > 0) {
+        k_gather_cols<<<(N * np + 255) / 256, 256, 0, stream>>>(C, N, nmo, orb, np, Cp);
+        CDS_LAUNCH_CHECK();
+        CDS_CUDA_TRY(cudaMemsetAsync(dCp, 0, sizeof(double) * (size_t)N * np, stream));
+    }
+    for (int32_t K0 = 0; K0 < M; K0 += kAoBatch) {
+        const int32_t kb = std::min(kAoBatch, M - K0);
+        const int64_t tot = (int64_t)N * kb * N;
+        k_unpack_t<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(L, npair, K0, kb, N, U2);
+        CDS_LAUNCH_CHECK();
+        // T[b] = C_vir dLov^K^T   (N x o);  dLov^K[i][a] = dLov[(i v + a) M + K]
+        int st = launch_dgemm_strided(N, nocc, nv, kb, C + nocc, nmo, 1, 0, dLov + K0, M,
+                                      (int64_t)nv * M, 1, T, nocc, 1, (int64_t)N * nocc, stream);
+        if (st) return st;
+        st = launch_dgemm_strided(N, nocc, kb * N, 1, U2, (int64_t)kb * N, 1, 0, T, nocc, 1, 0, dC,
+                                  nmo, 1, 0, stream, true);
+        if (st) return st;
+        // T[b] = C_occ dLov^K   (N x v)
+        st = launch_dgemm_strided(N, nv, nocc, kb, C, nmo, 1, 0, dLov + K0, (int64_t)nv * M, M, 1, T,
+                                  nv, 1, (int64_t)N * nv, stream);
+        if (st) return st;
+        st = launch_dgemm_strided(N, nv, kb * N, 1, U2, (int64_t)kb * N, 1, 0, T, nv, 1, 0,
+                                  dC + nocc, nmo, 1, 0, stream, true);
+        if (st) return st;
+        if (np > 0) {
+            // T[b] = C dLp^K^T   (N x np);  dLp^K[t][r] = dLp[(t nmo + r) M + K]
+            st = launch_dgemm_strided(N, np, nmo, kb, C, nmo, 1, 0, dLp + K0, M, (int64_t)nmo * M, 1,
+                                      T, np, 1, (int64_t)N * np, stream);
+            if (st) return st;
+            st = launch_dgemm_strided(N, np, kb * N, 1, U2, (int64_t)kb * N, 1, 0, T, np, 1, 0, dCp,
+                                      np, 1, 0, stream, true);
+            if (st) return st;
+            // T[b] = C_P dLp^K   (N x nmo)
+            st = launch_dgemm_strided(N, nmo, np, kb, Cp, np, 1, 0, dLp + K0, (int64_t)nmo * M, M, 1,
+                                      T, nmo, 1, (int64_t)N * nmo, stream);
+            if (st) return st;
+            st = launch_dgemm_strided(N, nmo, kb * N, 1, U2, (int64_t)kb * N, 1, 0, T, nmo, 1, 0, dC,
+                                      nmo, 1, 0, stream, true);
+            if (st) return st;
+        }
+    }
+    if (np > 0) {
+        k_scatter_cols<<<(N + 255) / 256, 256, 0, stream>>>(dCp, N, np, orb, nmo, dC);
+        CDS_LAUNCH_CHECK();
     }
     return CDS_OK;
 }
