@@ -65,8 +65,9 @@ typedef enum {
     CDS_PREC_FP64 = 0,
     CDS_PREC_BF16X3 = 2,
     CDS_PREC_FP16X3 = 3,
-    CDS_PREC_F32X2 = 4   /* transform only: (hi, lo) float pairs with exact product and sum
-                            errors, ~2^-44 relative per operation, on the FP32 units */
+    CDS_PREC_F32X2 = 4   /* decomposition and transform: (hi, lo) float pairs with exact
+                            product and sum errors, ~2^-44 relative per operation, on the
+                            FP32 units */
 } cds_precision;
 
 /* Newton status per orbital (paper Eq. NR). */
@@ -117,7 +118,12 @@ int cds_eri_columns(int32_t nbf, const double* xyz, const double* alpha,
 /* Workspace needed by cds_cd_decompose for a basis of nbf functions. */
 size_t cds_cd_workspace_bytes(int32_t nbf);
 
-/* Blocking.  Inputs (device): xyz, alpha, atom.  Outputs (device, caller-owned):
+/* Blocking.  precision: CDS_PREC_FP64 (binary64 throughout) or CDS_PREC_F32X2
+ * (the projections sum_K L^K_I L^K_P in float-pair arithmetic, ~2^-44 relative
+ * per step, with the vectors held as float pairs while the decomposition runs;
+ * integral columns, L^k, the residual diagonal and the pivot search stay FP64;
+ * L is returned in FP64 either way).
+ * Inputs (device): xyz, alpha, atom.  Outputs (device, caller-owned):
  *   L     [max_rank][npair] fp64, rows 0..M-1 written;
  *   piv   [max_rank] int32 packed pivot index of each vector;
  *   D     [npair] fp64 residual diagonal after the last step (the error
@@ -128,7 +134,7 @@ size_t cds_cd_workspace_bytes(int32_t nbf);
  * on a negative residual beyond roundoff. */
 int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
                      const int32_t* atom, double delta, int32_t scheme, int32_t max_rank,
-                     double* L, int32_t* piv, double* D, int32_t* M_out,
+                     int32_t precision, double* L, int32_t* piv, double* D, int32_t* M_out,
                      double* delta_eff_out, void* workspace, size_t workspace_bytes,
                      cudaStream_t stream);
 

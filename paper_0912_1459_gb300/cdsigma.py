@@ -38,8 +38,8 @@ _SIGNATURES = {
     "cds_eri_diag": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp]),
     "cds_eri_columns": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp]),
     "cds_cd_workspace_bytes": (_sz, [_i32]),
-    "cds_cd_decompose": (ctypes.c_int, [_i32, _vp, _vp, _vp, _f64, _i32, _i32, _vp, _vp, _vp,
-                                        ctypes.POINTER(_i32), ctypes.POINTER(_f64), _vp, _sz,
+    "cds_cd_decompose": (ctypes.c_int, [_i32, _vp, _vp, _vp, _f64, _i32, _i32, _i32, _vp, _vp,
+                                        _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f64), _vp, _sz,
                                         _vp]),
     "cds_cd_decompose_static": (ctypes.c_int, [_i32, _vp, _vp, _vp, _f64, _i32, _i32, _vp, _vp,
                                                _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f64),
@@ -188,7 +188,8 @@ def default_max_rank(nbf: int) -> int:
 
 def cds_cd_decompose(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor, delta: float,
                      scheme: str = "full", max_rank: Optional[int] = None,
-                     L_out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None):
+                     L_out: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                     precision: str = "fp64"):
     """Pivoted Cholesky decomposition of the ERI supermatrix (paper Sec. II.A).
 
     Returns (L [M, npair], piv [M] int32, D [npair] residual diagonal, delta_eff).
@@ -215,7 +216,8 @@ def cds_cd_decompose(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,
     M = _i32(0)
     de = _f64(0.0)
     st = lib.cds_cd_decompose(n, _p(xyz), _p(alpha), _p(atom), float(delta), SCHEMES[scheme],
-                              int(max_rank), _p(L_out), _p(piv), _p(D), ctypes.byref(M),
+                              int(max_rank), PRECISIONS[precision], _p(L_out), _p(piv), _p(D),
+                              ctypes.byref(M),
                               ctypes.byref(de), _p(workspace), workspace.numel(), _stream(dev))
     _check(st, "cds_cd_decompose")
     return L_out[:M.value], piv[:M.value], D, de.value

@@ -6,12 +6,16 @@
 //   L^k_I = [ (rho_I|rho_P) - sum_{K<k} L^K_I L^K_P ] / sqrt(D_P),
 //   D_I  -= (L^k_I)^2,  D_P := 0,
 // then the next pivot is the largest candidate residual (lowest index among
-// values within 1e-12 * max initial diagonal).  One launch of k_cd_update per
-// step streams L[0:k][*] once (coalesced along I, the dot product in FP64);
-// the grid-wide max is finished by the last block to arrive (no spin waits).
-// k_cd_select then picks the pivot.  Both kernels read a device control block
-// and return immediately once the decomposition has stopped, so the host can
-// enqueue steps ahead and only check the control block every few steps.
+// values within 1e-12 * max initial diagonal).  A step is two launches:
+// k_cd_project makes the integral column (FP64, on a few blocks) while its
+// other blocks stream L[0:k][*] once for the projections (coalesced along I);
+// k_cd_update forms L^k and the residuals, and the last of its blocks to
+// arrive finishes the grid-wide extrema and picks the next pivot (no spin
+// waits).  k_cd_select picks the first pivot only.
+// All kernels read a device control block and return at once after the
+// decomposition has stopped, so the host enqueues steps ahead and checks the
+// control block only every few steps.
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -20,7 +24,11 @@
 namespace cds {
 
 constexpr int kCdThreads = 128;
-constexpr int kCdPairs = 2;      // pairs per thread in k_cd_update
+constexpr int kUpdWarps = 8;                  // k_cd_update: warps splitting the K sum
+constexpr int kUpdThreads = 32 * kUpdWarps;
+constexpr int kUpdPairs = 64;                 // k_cd_project: pairs per projection tile
+constexpr int kStepPer = 2;                   // k_cd_update: pairs per thread
+constexpr int kStepChunk = kStepPer * kUpdThreads;   // k_cd_update: contiguous pairs per block
 constexpr int kCdChunk = 2048;   // pivot row L^K_P staged in shared memory in chunks
 constexpr double kTieRel = 1e-12;
 constexpr double kNotPdRel = 1e-10;
@@ -32,6 +40,7 @@ struct CdCtrl {
     double G;          // max candidate residual after the last update
     double Dmin;       // min residual after the last update
     double DP;         // residual of the current pivot
+    double rDP;        // 1 / sqrt(DP)
     int64_t P;         // current pivot
     int32_t done;      // decomposition stopped
     int32_t status;    // cds_status
@@ -98,7 +107,7 @@ __device__ void cd_init_body(PairSoA pd, const int32_t* __restrict__ atom, int32
     double mx_all = -INFINITY, mx_cand = -INFINITY;
     for (int64_t I = bid * (int64_t)blockDim.x + threadIdx.x; I < n;
          I += (int64_t)nblk * blockDim.x) {
-        double p = pd.p[I], px = pd.Px[I], py = pd.Py[I], pz = pd.Pz[I], k = pd.K[I];
+        double p = pd.p[I], px = pd.Px[I], py = pd.Py[I], pz = pd.Pz[I], k = pd.Kp[I];
         double d = eri_pair(p, px, py, pz, k, p, px, py, pz, k);
         D[I] = d;
         uint8_t c = 1;
@@ -200,6 +209,7 @@ __device__ void cd_select_body(int64_t n, int32_t k, int32_t max_rank,
             } else {
                 ctrl->P = m;
                 ctrl->DP = __ldcg(D + m);
+                ctrl->rDP = 1.0 / sqrt(ctrl->DP);
                 piv[k] = (int32_t)m;
             }
             ctrl->counter = 0;
@@ -213,97 +223,372 @@ __global__ void k_cd_select(int64_t n, int32_t k, int32_t max_rank, const double
     cd_select_body(n, k, max_rank, D, cand, blk_i, piv, ctrl, blockIdx.x, gridDim.x);
 }
 
-// Vector k from pivot P: column, left-looking projection, residual update.
-// Each thread owns kCdPairs pairs, blockDim.x * kCdPairs apart, so one grid of
-// ~npair / (kCdThreads * kCdPairs) small blocks is resident in a single wave.
-__device__ __forceinline__ void cd_update_body(PairSoA pd, int64_t n, int32_t k,
-                                               double* __restrict__ L, double* __restrict__ D,
-                                               const uint8_t* __restrict__ cand,
-                                               double* __restrict__ blk_a,
-                                               double* __restrict__ blk_b, CdCtrl* ctrl, int bid,
-                                               int nblk) {
-    if (ctrl->done) return;
-    __shared__ double lp[kCdChunk];
+// acc += a * b in (hi, lo) float pairs: exact product error by FMA, exact
+// sum error by two-sum (~2^-44 relative per step on the FP32 units).
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+    const float s = a.x + b.x;
+    const float bp = s - a.x;
+    float e = (a.x - (s - bp)) + (b.x - bp);
+    e += a.y + b.y;
+    const float h = s + e;
+    return make_float2(h, e - (h - s));
+}
+
+__device__ __forceinline__ void df_fma(float2& acc, float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float pe = fmaf(a.x, b.x, -p);
+    pe = fmaf(a.x, b.y, pe);
+    pe = fmaf(a.y, b.x, pe);
+    const float s = acc.x + p;
+    const float bp = s - acc.x;
+    const float err = (acc.x - (s - bp)) + (p - bp);
+    acc.x = s;
+    acc.y += err + pe;
+}
+
+// Integral column (rho_I|rho_P) of step k into ecol (grid-stride over the
+// pairs of the molecule, 256 per pass).  Most pairs lie far from a compact
+// pivot density (T >= 36: one reciprocal square root, no error function); the
+// few that need erf are gathered in shared memory and evaluated together, so
+// the warps do not all run the erf path for one lane each.
+__device__ __forceinline__ void cd_eri_body(PairSoA pd, int64_t n, const CdCtrl* ctrl,
+                                            double* __restrict__ ecol, int bid, int nblk) {
+    __shared__ double near_x[kUpdThreads], near_s[kUpdThreads], near_k[kUpdThreads];
+    __shared__ int near_i[kUpdThreads];
+    __shared__ int near_n;
     const int64_t P = ctrl->P;
-    const double DP = ctrl->DP;
-    const double q = pd.p[P], qx = pd.Px[P], qy = pd.Py[P], qz = pd.Pz[P], kq = pd.K[P];
-    const int64_t I0 = (int64_t)bid * blockDim.x * kCdPairs + threadIdx.x;
-    int64_t Is[kCdPairs];
-    bool live[kCdPairs];
-#pragma unroll
-    for (int r = 0; r < kCdPairs; ++r) {
-        Is[r] = I0 + (int64_t)r * blockDim.x;
-        live[r] = Is[r] < n;
-    }
-    // 4 independent partial sums per pair: 8 loads of L in flight per thread
-    double dot[kCdPairs][4] = {};
-    int64_t Ic[kCdPairs];
-#pragma unroll
-    for (int r = 0; r < kCdPairs; ++r) Ic[r] = live[r] ? Is[r] : 0;   // dead lanes read pair 0
-    for (int K0 = 0; K0 < k; K0 += kCdChunk) {
-        int kc = min(kCdChunk, k - K0);
+    const double q = pd.p[P], qx = pd.Px[P], qy = pd.Py[P], qz = pd.Pz[P], kq = pd.Kp[P];
+    for (int64_t I0 = (int64_t)bid * kUpdThreads; I0 < n; I0 += (int64_t)nblk * kUpdThreads) {
+        if (threadIdx.x == 0) near_n = 0;
         __syncthreads();
-        for (int j = threadIdx.x; j < kc; j += blockDim.x) lp[j] = L[(int64_t)(K0 + j) * n + P];
-        __syncthreads();
-        const double* src = L + (int64_t)K0 * n;
-        int j = 0;
-        for (; j + 4 <= kc; j += 4) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const double lu = lp[j + u];
-                const double* row = src + (int64_t)(j + u) * n;
-#pragma unroll
-                for (int r = 0; r < kCdPairs; ++r) dot[r][u] = fma(row[Ic[r]], lu, dot[r][u]);
+        const int64_t I = I0 + threadIdx.x;
+        if (I < n) {
+            double x, sm;
+            eri_xs(pd.p[I], pd.Px[I], pd.Py[I], pd.Pz[I], q, qx, qy, qz, x, sm);
+            const double kk = pd.Kp[I] * kq;
+            if (eri_is_far(x, sm)) {
+                ecol[I] = eri_far(kk, x);
+            } else {
+                const int slot = atomicAdd(&near_n, 1);
+                near_x[slot] = x;
+                near_s[slot] = sm;
+                near_k[slot] = kk;
+                near_i[slot] = threadIdx.x;
             }
         }
-        for (; j < kc; ++j) {
+        __syncthreads();
+        const int cnt = near_n;
+        for (int j = threadIdx.x; j < cnt; j += kUpdThreads)
+            ecol[I0 + near_i[j]] = eri_near(near_k[j], near_x[j], near_s[j]);
+        __syncthreads();   // near_n is reset by the next pass
+    }
+}
+
+// Projection sum_{K<k} L^K_I L^K_P for one tile of kUpdPairs pairs, stored in
+// row k of L (the slot vector k will occupy).  Lane l of every warp holds
+// pairs l and l + 32 of the tile; the kUpdWarps warps split the K sum (warp w
+// takes the staged rows j = w mod kUpdWarps, four rows per iteration: 8 loads
+// of L in flight per thread), and their partial sums are added in a fixed
+// order, so the result does not depend on scheduling.
+//
+// DF: the stored vectors are (hi, lo) float pairs in the 8 bytes of each L
+// element, and the projection runs and is stored in float-pair arithmetic on
+// the FP32 units.
+template <bool DF>
+__device__ __forceinline__ void cd_dot_body(int64_t n, int32_t k, double* __restrict__ L,
+                                            const CdCtrl* ctrl, int tile) {
+    __shared__ double lp_raw[kCdChunk];
+    __shared__ double red[kUpdWarps][kUpdPairs];
+    const int64_t P = ctrl->P;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)tile * kUpdPairs;
+    int64_t Ic[2];
 #pragma unroll
-            for (int r = 0; r < kCdPairs; ++r)
-                dot[r][0] = fma(src[(int64_t)j * n + Ic[r]], lp[j], dot[r][0]);
+    for (int r = 0; r < 2; ++r) {
+        const int64_t I = base + lane + 32 * r;
+        Ic[r] = I < n ? I : 0;   // dead lanes read pair 0
+    }
+    double dot[2][4] = {};
+    float2 dfd[2][4];
+    if constexpr (DF) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) dfd[r][u] = make_float2(0.f, 0.f);
+    }
+    for (int K0 = 0; K0 < k; K0 += kCdChunk) {
+        const int kc = min(kCdChunk, k - K0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < kc; j += blockDim.x) lp_raw[j] = L[(int64_t)(K0 + j) * n + P];
+        __syncthreads();
+        int j = w;
+        constexpr int S = kUpdWarps;
+        if constexpr (DF) {
+            const float2* lp = reinterpret_cast<const float2*>(lp_raw);
+            const float2* src = reinterpret_cast<const float2*>(L) + (int64_t)K0 * n;
+            for (; j + 3 * S < kc; j += 4 * S) {
+                float2 v[4][2];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) v[u][r] = src[(int64_t)(j + u * S) * n + Ic[r]];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const float2 lu = lp[j + u * S];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) df_fma(dfd[r][u], v[u][r], lu);
+                }
+            }
+            for (; j < kc; j += S) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) df_fma(dfd[r][0], src[(int64_t)j * n + Ic[r]], lp[j]);
+            }
+        } else {
+            const double* lp = lp_raw;
+            const double* src = L + (int64_t)K0 * n;
+            for (; j + 3 * S < kc; j += 4 * S) {
+                double v[4][2];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) v[u][r] = src[(int64_t)(j + u * S) * n + Ic[r]];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const double lu = lp[j + u * S];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) dot[r][u] = fma(v[u][r], lu, dot[r][u]);
+                }
+            }
+            for (; j < kc; j += S) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) dot[r][0] = fma(src[(int64_t)j * n + Ic[r]], lp[j], dot[r][0]);
+            }
         }
     }
-    double mx = -INFINITY, mn = INFINITY;
-    const double rs = sqrt(DP);
+    float2(*red2)[kUpdPairs] = reinterpret_cast<float2(*)[kUpdPairs]>(red);
 #pragma unroll
-    for (int r = 0; r < kCdPairs; ++r) {
-        if (!live[r]) continue;
-        const int64_t I = Is[r];
-        double e = eri_pair(pd.p[I], pd.Px[I], pd.Py[I], pd.Pz[I], pd.K[I], q, qx, qy, qz, kq);
-        double l = (e - ((dot[r][0] + dot[r][1]) + (dot[r][2] + dot[r][3]))) / rs;
-        L[(int64_t)k * n + I] = l;
-        double d = D[I] - l * l;
-        if (I == P) d = 0.0;
-        D[I] = d;
-        if (cand[I]) mx = fmax(mx, fmax(d, 0.0));
-        mn = fmin(mn, d);
+    for (int r = 0; r < 2; ++r) {
+        if constexpr (DF)
+            red2[w][lane + 32 * r] = df_add(df_add(dfd[r][0], dfd[r][1]), df_add(dfd[r][2], dfd[r][3]));
+        else
+            red[w][lane + 32 * r] = (dot[r][0] + dot[r][1]) + (dot[r][2] + dot[r][3]);
     }
-    block_maxmin(mx, mn);
-    if (threadIdx.x == 0) { blk_a[bid] = mx; blk_b[bid] = mn; }
-    if (last_block(&ctrl->counter, nblk)) {
-        double A = -INFINITY, B = INFINITY;
-        for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-            A = fmax(A, __ldcg(blk_a + i));
-            B = fmin(B, __ldcg(blk_b + i));
-        }
-        block_maxmin(A, B);
-        if (threadIdx.x == 0) {
-            ctrl->G = A;
-            ctrl->Dmin = B;
-            ctrl->counter = 0;
+    __syncthreads();
+    const int64_t I = base + threadIdx.x;
+    if (threadIdx.x < kUpdPairs && I < n) {
+        if constexpr (DF) {
+            float2 sum = red2[0][threadIdx.x];
+#pragma unroll
+            for (int v = 1; v < kUpdWarps; ++v) sum = df_add(sum, red2[v][threadIdx.x]);
+            reinterpret_cast<float2*>(L)[(int64_t)k * n + I] = sum;
+        } else {
+            double sum = red[0][threadIdx.x];
+#pragma unroll
+            for (int v = 1; v < kUpdWarps; ++v) sum += red[v][threadIdx.x];
+            L[(int64_t)k * n + I] = sum;
         }
     }
 }
 
-__global__ void __launch_bounds__(kCdThreads)
-k_cd_update(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L, double* __restrict__ D,
-            const uint8_t* __restrict__ cand, double* __restrict__ blk_a,
-            double* __restrict__ blk_b, CdCtrl* ctrl) {
-    cd_update_body(pd, n, k, L, D, cand, blk_a, blk_b, ctrl, blockIdx.x, gridDim.x);
+// Order-preserving map of binary64 values to int64 (its own inverse), so the
+// residual extrema reduce on the integer units instead of the narrow FP64 pipe.
+__device__ __forceinline__ long long key_of(double d) {
+    const long long b = __double_as_longlong(d);
+    return b < 0 ? (b ^ 0x7fffffffffffffffLL) : b;
+}
+__device__ __forceinline__ double value_of(long long s) {
+    return __longlong_as_double(s < 0 ? (s ^ 0x7fffffffffffffffLL) : s);
+}
+__device__ __forceinline__ long long warp_max_ll(long long v) {
+    for (int o = 16; o; o >>= 1) {
+        long long w = __shfl_xor_sync(0xffffffffu, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+// Block-wide max / min of two int64 values, returned in every thread.
+__device__ void block_maxmin_ll(long long& mx, long long& mn) {
+    __shared__ long long smx[32], smn[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    mx = warp_max_ll(mx);
+    mn = warp_min_ll(mn);
+    if (lane == 0) { smx[w] = mx; smn[w] = mn; }
+    __syncthreads();
+    if (w == 0) {
+        long long a = lane < nw ? smx[lane] : LLONG_MIN;
+        long long b = lane < nw ? smn[lane] : LLONG_MAX;
+        a = warp_max_ll(a);
+        b = warp_min_ll(b);
+        if (lane == 0) { smx[0] = a; smn[0] = b; }
+    }
+    __syncthreads();
+    mx = smx[0];
+    mn = smn[0];
+    __syncthreads();
+}
+__device__ long long block_min_ll(long long v) {
+    long long dummy = LLONG_MIN;
+    block_maxmin_ll(dummy, v);
+    return v;
+}
+
+// Vector k, the residual update and the pivot of step k+1, one launch:
+//   L^k_I = (ecol_I - proj_I) / sqrt(D_P),  D_I -= (L^k_I)^2,  D_P := 0.
+// Block b owns the contiguous pairs [b*kStepChunk, (b+1)*kStepChunk) and
+// records the largest candidate max(D,0) and the smallest D of its range.
+// The last block to arrive finishes both extrema, applies the stop tests and,
+// if the decomposition goes on, picks the next pivot: the lowest candidate
+// index with max(D,0) >= G - 1e-12*scale and D > delta_eff.  That index lies
+// in the lowest block whose own maximum passes the test (a block maximum that
+// passes without any entry passing, possible only when the band reaches below
+// delta_eff, moves the search to the next such block).  DF: proj and L^k are
+// (hi, lo) float pairs.
+template <bool DF>
+__device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_rank,
+                                             double* __restrict__ L, double* __restrict__ D,
+                                             const uint8_t* __restrict__ cand,
+                                             const double* __restrict__ ecol,
+                                             long long* __restrict__ blk_a,
+                                             long long* __restrict__ blk_b,
+                                             int32_t* __restrict__ piv, CdCtrl* ctrl, int bid,
+                                             int nblk) {
+    const int64_t P = ctrl->P;
+    const double rDP = ctrl->rDP;
+    long long mx = -1, mn = LLONG_MAX;   // bits of max(D,0) over candidates (-1: none), key of min D
+    const int64_t base = (int64_t)bid * kStepChunk;
+#pragma unroll
+    for (int r = 0; r < kStepPer; ++r) {
+        const int64_t I = base + r * kUpdThreads + threadIdx.x;
+        if (I < n) {
+            double* slot = L + (int64_t)k * n + I;
+            double proj = 0.0;
+            if (k > 0) {
+                if constexpr (DF) {
+                    const float2 f = *reinterpret_cast<const float2*>(slot);
+                    proj = (double)f.x + (double)f.y;
+                } else {
+                    proj = *slot;
+                }
+            }
+            const double l = (ecol[I] - proj) * rDP;
+            if constexpr (DF) {
+                const float h = (float)l;
+                *reinterpret_cast<float2*>(slot) = make_float2(h, (float)(l - (double)h));
+            } else {
+                *slot = l;
+            }
+            double d = D[I] - l * l;
+            if (I == P) d = 0.0;
+            D[I] = d;
+            const long long bits = __double_as_longlong(d);
+            if (cand[I]) mx = max(mx, bits > 0 ? bits : 0LL);
+            mn = min(mn, key_of(d));
+        }
+    }
+    block_maxmin_ll(mx, mn);
+    if (threadIdx.x == 0) { blk_a[bid] = mx; blk_b[bid] = mn; }
+    if (!last_block(&ctrl->counter, nblk)) return;
+
+    long long A = -1, B = LLONG_MAX;
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        A = max(A, __ldcg(blk_a + i));
+        B = min(B, __ldcg(blk_b + i));
+    }
+    block_maxmin_ll(A, B);
+    const double G = A < 0 ? -INFINITY : __longlong_as_double(A);
+    const double Dmin = value_of(B);
+    const double scale = ctrl->scale, de = ctrl->delta_eff;
+    const int32_t made = k + 1;
+    int32_t status = CDS_OK;
+    bool stop = true;
+    long long pick = -1;
+    if (Dmin < -kNotPdRel * scale || !(G == G)) {
+        status = CDS_ERR_NOT_PD;
+    } else if (G <= de) {
+        status = CDS_OK;
+    } else if (made >= max_rank) {
+        status = CDS_ERR_RANK_CAP;
+    } else {
+        const double thr = G - kTieRel * scale;
+        int from = 0;
+        for (;;) {
+            long long bl = LLONG_MAX;
+            for (int i = from + threadIdx.x; i < nblk; i += blockDim.x) {
+                const double m = __longlong_as_double(__ldcg(blk_a + i));   // -1: NaN, fails
+                if (m >= thr && m > de) { bl = i; break; }
+            }
+            bl = block_min_ll(bl);
+            if (bl == LLONG_MAX) break;
+            long long best = LLONG_MAX;
+#pragma unroll
+            for (int r = 0; r < kStepPer; ++r) {
+                const int64_t I = bl * kStepChunk + r * kUpdThreads + threadIdx.x;
+                if (I < n) {
+                    const double d = __ldcg(D + I);
+                    if (cand[I] && fmax(d, 0.0) >= thr && d > de) best = min(best, (long long)I);
+                }
+            }
+            best = block_min_ll(best);
+            if (best != LLONG_MAX) { pick = best; break; }
+            from = (int)bl + 1;
+        }
+        if (pick >= 0) stop = false;
+        else status = CDS_ERR_NOT_PD;   // G > delta_eff but no entry passes: D is inconsistent
+    }
+    if (threadIdx.x == 0) {
+        ctrl->G = G;
+        ctrl->Dmin = Dmin;
+        if (stop) {
+            ctrl->status = status;
+            ctrl->done = 1;
+            ctrl->M = made;
+        } else {
+            ctrl->P = pick;
+            ctrl->DP = __ldcg(D + pick);
+            ctrl->rDP = 1.0 / sqrt(ctrl->DP);
+            piv[made] = (int32_t)pick;
+        }
+        ctrl->counter = 0;
+    }
+}
+
+// Step k, part 1: blocks [0, neri) make the integral column, the rest the
+// projections, one tile each.  The two have no dependence on each other; the
+// integral blocks come first in the grid, so their FP64 work overlaps the
+// streaming of L by the projection blocks.
+template <bool DF>
+__global__ void __launch_bounds__(kUpdThreads, 4)
+k_cd_project(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L,
+             double* __restrict__ ecol, int neri, const CdCtrl* ctrl) {
+    if (ctrl->done) return;
+    if ((int)blockIdx.x < neri) cd_eri_body(pd, n, ctrl, ecol, blockIdx.x, neri);
+    else if (k > 0) cd_dot_body<DF>(n, k, L, ctrl, blockIdx.x - neri);
+}
+
+// Step k, part 2: vector k, residuals, next pivot.
+template <bool DF>
+__global__ void __launch_bounds__(kUpdThreads)
+k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
+            double* __restrict__ D, const uint8_t* __restrict__ cand,
+            const double* __restrict__ ecol, double* __restrict__ blk_a,
+            double* __restrict__ blk_b, int32_t* __restrict__ piv, CdCtrl* ctrl) {
+    if (ctrl->done) return;
+    cd_step_body<DF>(n, k, max_rank, L, D, cand, ecol, reinterpret_cast<long long*>(blk_a),
+                     reinterpret_cast<long long*>(blk_b), piv, ctrl, blockIdx.x, gridDim.x);
+}
+
+// Float pairs (hi, lo) of the first count elements of L back to FP64, in place.
+__global__ void k_pairs_to_fp64(double* __restrict__ L, int64_t count) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float2 v = reinterpret_cast<const float2*>(L)[i];
+    L[i] = (double)v.x + (double)v.y;
 }
 
 struct CdLayout {
     PairSoA pd;
     uint8_t* cand;
+    double* ecol;     // integral column of the current step
     double* blk_a;
     double* blk_b;
     long long* blk_i;
@@ -312,22 +597,36 @@ struct CdLayout {
 };
 
 static int cd_blocks(int64_t n) { return (int)((n + kCdThreads - 1) / kCdThreads); }
-static int upd_blocks(int64_t n) {
-    return (int)((n + (int64_t)kCdThreads * kCdPairs - 1) / ((int64_t)kCdThreads * kCdPairs));
+static int dot_tiles(int64_t n) { return (int)((n + kUpdPairs - 1) / kUpdPairs); }
+// integral-column blocks of k_cd_project: two per SM at most (grid-stride)
+static int eri_blocks(int64_t n, int nsm) {
+    return (int)std::min<int64_t>(2 * nsm, (n + kUpdThreads - 1) / kUpdThreads);
+}
+static int step_blocks(int64_t n) { return (int)std::max<int64_t>(1, (n + kStepChunk - 1) / kStepChunk); }
+// block partials are shared by the init, update and select grids (each at
+// most cd_blocks blocks)
+static int part_blocks(int64_t n) { return std::max(cd_blocks(n), 1); }
+static int sm_count() {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+        return 152;
+    return nsm;
 }
 static int sel_blocks(int64_t n) { return (int)std::min<int64_t>(4 * 152, (n + kCdThreads - 1) / kCdThreads); }
 
 static CdLayout cd_layout(void* ws, int32_t nbf) {
     int64_t n = npair_of(nbf);
-    int nb = std::max(cd_blocks(n), 1);
+    int nb = part_blocks(n);
     Carver c(ws);
     CdLayout l;
     l.pd.p = c.take<double>(n);
     l.pd.Px = c.take<double>(n);
     l.pd.Py = c.take<double>(n);
     l.pd.Pz = c.take<double>(n);
-    l.pd.K = c.take<double>(n);
+    l.pd.Kp = c.take<double>(n);
     l.cand = c.take<uint8_t>(n);
+    l.ecol = c.take<double>(n);
     l.blk_a = c.take<double>(nb);
     l.blk_b = c.take<double>(nb);
     l.blk_i = c.take<long long>(nb);
@@ -347,11 +646,13 @@ extern "C" size_t cds_cd_workspace_bytes(int32_t nbf) {
 
 extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
                                 const int32_t* atom, double delta, int32_t scheme,
-                                int32_t max_rank, double* L, int32_t* piv, double* D,
-                                int32_t* M_out, double* delta_eff_out, void* workspace,
-                                size_t workspace_bytes, cudaStream_t stream) {
+                                int32_t max_rank, int32_t precision, double* L, int32_t* piv,
+                                double* D, int32_t* M_out, double* delta_eff_out,
+                                void* workspace, size_t workspace_bytes, cudaStream_t stream) {
     if (nbf <= 0 || !xyz || !alpha || !L || !piv || !D || !M_out || max_rank < 0)
         return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return CDS_ERR_UNSUPPORTED;
+    const bool df = precision == CDS_PREC_F32X2;
     if (!(delta >= 0.0)) return CDS_ERR_ARG;
     if (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC) return CDS_ERR_ARG;
     if (scheme == CDS_SCHEME_ATOMIC && !atom) return CDS_ERR_ARG;
@@ -361,7 +662,9 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
     int st = build_pairs(nbf, xyz, alpha, lay.pd, stream);
     if (st) return st;
     CDS_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, sizeof(CdCtrl), stream));
-    int nb = cd_blocks(n), ns = sel_blocks(n), nu = upd_blocks(n);
+    const int nsm = sm_count();
+    const int nb = cd_blocks(n), ns = sel_blocks(n);
+    const int ne = eri_blocks(n, nsm), np_ = ne + dot_tiles(n), nu = step_blocks(n);
     k_cd_init<<<nb, kCdThreads, 0, stream>>>(lay.pd, atom, scheme, n, delta, D, lay.cand,
                                             lay.blk_a, lay.blk_b, lay.ctrl);
     CDS_LAUNCH_CHECK();
@@ -372,10 +675,19 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
     for (int32_t k0 = 0; k0 <= max_rank; k0 += kHostCheckEvery) {
         int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
         for (int32_t k = k0; k < k1; ++k) {
-            k_cd_update<<<nu, kCdThreads, 0, stream>>>(lay.pd, n, k, L, D, lay.cand, lay.blk_a,
-                                                      lay.blk_b, lay.ctrl);
-            k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, k + 1, max_rank, D, lay.cand,
-                                                      lay.blk_i, piv, lay.ctrl);
+            if (df) {
+                k_cd_project<true><<<np_, kUpdThreads, 0, stream>>>(lay.pd, n, k, L, lay.ecol, ne,
+                                                                    lay.ctrl);
+                k_cd_update<true><<<nu, kUpdThreads, 0, stream>>>(n, k, max_rank, L, D, lay.cand,
+                                                                  lay.ecol, lay.blk_a, lay.blk_b,
+                                                                  piv, lay.ctrl);
+            } else {
+                k_cd_project<false><<<np_, kUpdThreads, 0, stream>>>(lay.pd, n, k, L, lay.ecol, ne,
+                                                                     lay.ctrl);
+                k_cd_update<false><<<nu, kUpdThreads, 0, stream>>>(n, k, max_rank, L, D, lay.cand,
+                                                                   lay.ecol, lay.blk_a, lay.blk_b,
+                                                                   piv, lay.ctrl);
+            }
         }
         count_launches(2ull * (unsigned long long)(k1 - k0));
         CDS_CUDA_TRY(cudaGetLastError());
@@ -385,6 +697,11 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
     }
     *M_out = h.M;
     if (delta_eff_out) *delta_eff_out = h.delta_eff;
+    if (df && h.M > 0) {
+        const int64_t cnt = (int64_t)h.M * n;
+        k_pairs_to_fp64<<<(unsigned)((cnt + 255) / 256), 256, 0, stream>>>(L, cnt);
+        CDS_LAUNCH_CHECK();
+    }
     if (!h.done) return CDS_ERR_RANK_CAP;
     return h.status;
 }
@@ -402,6 +719,7 @@ struct CdMol {
     double* L;
     double* D;
     uint8_t* cand;
+    double* ecol;
     int32_t* piv;
     double* blk_a;
     double* blk_b;
@@ -409,15 +727,20 @@ struct CdMol {
     CdCtrl* ctrl;
     int64_t n;
     int32_t max_rank;
-    int32_t b0_init, nb_init, b0_upd, nb_upd, b0_sel, nb_sel;
+    int32_t b0_init, nb_init, b0_sel, nb_sel, b0_epi, nb_epi;
+    int32_t b0_prj, nb_eri, nb_dot;   // project grid: nb_eri integral blocks, then nb_dot tiles
 };
 
-// Molecule owning block bid of a batch grid (kind: 0 init, 1 update, 2 select).
+// Molecule owning block bid of a batch grid (kind: 0 init, 1 project,
+// 2 select, 3 update).
 __device__ __forceinline__ int find_mol(const CdMol* mols, int nmol, int bid, int kind) {
     int lo = 0, hi = nmol - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        const int b0 = kind == 0 ? mols[mid].b0_init : kind == 1 ? mols[mid].b0_upd : mols[mid].b0_sel;
+        const int b0 = kind == 0 ? mols[mid].b0_init
+                     : kind == 1 ? mols[mid].b0_prj
+                     : kind == 2 ? mols[mid].b0_sel
+                                 : mols[mid].b0_epi;
         if (b0 <= bid) lo = mid; else hi = mid - 1;
     }
     return lo;
@@ -437,13 +760,24 @@ __global__ void k_bcd_select(const CdMol* __restrict__ mols, int nmol, int32_t k
                    blockIdx.x - m.b0_sel, m.nb_sel);
 }
 
-__global__ void __launch_bounds__(kCdThreads) k_bcd_update(const CdMol* __restrict__ mols, int nmol,
-                                                           int32_t k) {
+__global__ void __launch_bounds__(kUpdThreads, 3) k_bcd_project(const CdMol* __restrict__ mols,
+                                                                int nmol, int32_t k) {
     const int c = find_mol(mols, nmol, blockIdx.x, 1);
     const CdMol& m = mols[c];
-    if (k >= m.max_rank) return;
-    cd_update_body(m.pd, m.n, k, m.L, m.D, m.cand, m.blk_a, m.blk_b, m.ctrl,
-                   blockIdx.x - m.b0_upd, m.nb_upd);
+    if (k >= m.max_rank || m.ctrl->done) return;
+    const int local = blockIdx.x - m.b0_prj;
+    if (local < m.nb_eri) cd_eri_body(m.pd, m.n, m.ctrl, m.ecol, local, m.nb_eri);
+    else if (k > 0) cd_dot_body<false>(m.n, k, m.L, m.ctrl, local - m.nb_eri);
+}
+
+__global__ void __launch_bounds__(kUpdThreads) k_bcd_update(const CdMol* __restrict__ mols,
+                                                            int nmol, int32_t k) {
+    const int c = find_mol(mols, nmol, blockIdx.x, 3);
+    const CdMol& m = mols[c];
+    if (k >= m.max_rank || m.ctrl->done) return;
+    cd_step_body<false>(m.n, k, m.max_rank, m.L, m.D, m.cand, m.ecol,
+                        reinterpret_cast<long long*>(m.blk_a), reinterpret_cast<long long*>(m.blk_b),
+                        m.piv, m.ctrl, blockIdx.x - m.b0_epi, m.nb_epi);
 }
 
 struct CdBatchLayout {
@@ -454,8 +788,8 @@ struct CdBatchLayout {
 };
 
 static size_t cd_mol_bytes(int64_t n) {
-    const size_t nb = (size_t)std::max(cd_blocks(n), 1);
-    return 5 * align_up(n * sizeof(double)) + align_up(n) + 3 * align_up(nb * sizeof(double));
+    const size_t nb = (size_t)part_blocks(n);
+    return 6 * align_up(n * sizeof(double)) + align_up(n) + 3 * align_up(nb * sizeof(double));
 }
 
 static CdBatchLayout cd_batch_layout(void* ws, int32_t nmol, const BatchMol* mols) {
@@ -483,18 +817,20 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
     if (!ws || ws_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
     std::vector<CdMol> h(nmol);
     char* p = lay.per_mol;
-    int b_init = 0, b_upd = 0, b_sel = 0, kmax = 0;
+    int b_init = 0, b_prj = 0, b_sel = 0, b_epi = 0, kmax = 0;
+    const int nsm = sm_count();
     for (int c = 0; c < nmol; ++c) {
         const int64_t n = npair_of(mols[c].nbf);
-        const size_t nb = (size_t)std::max(cd_blocks(n), 1);
+        const size_t nb = (size_t)part_blocks(n);
         CdMol& m = h[c];
         Carver cv(p);
         m.pd.p = cv.take<double>(n);
         m.pd.Px = cv.take<double>(n);
         m.pd.Py = cv.take<double>(n);
         m.pd.Pz = cv.take<double>(n);
-        m.pd.K = cv.take<double>(n);
+        m.pd.Kp = cv.take<double>(n);
         m.cand = cv.take<uint8_t>(n);
+        m.ecol = cv.take<double>(n);
         m.blk_a = cv.take<double>(nb);
         m.blk_b = cv.take<double>(nb);
         m.blk_i = cv.take<long long>(nb);
@@ -507,7 +843,9 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
         m.n = n;
         m.max_rank = mols[c].max_rank;
         m.b0_init = b_init; m.nb_init = cd_blocks(n); b_init += m.nb_init;
-        m.b0_upd = b_upd; m.nb_upd = upd_blocks(n); b_upd += m.nb_upd;
+        m.b0_prj = b_prj; m.nb_eri = eri_blocks(n, nsm); m.nb_dot = dot_tiles(n);
+        b_prj += m.nb_eri + m.nb_dot;
+        m.b0_epi = b_epi; m.nb_epi = step_blocks(n); b_epi += m.nb_epi;
         m.b0_sel = b_sel; m.nb_sel = sel_blocks(n); b_sel += m.nb_sel;
         kmax = std::max(kmax, mols[c].max_rank);
         int st = build_pairs(mols[c].nbf, xyz + 3 * off[c].basis, alpha + off[c].basis, m.pd, stream);
@@ -524,8 +862,8 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
     for (int32_t k0 = 0; k0 <= kmax; k0 += kHostCheckEvery) {
         int32_t k1 = std::min(kmax, k0 + kHostCheckEvery);
         for (int32_t k = k0; k < k1; ++k) {
-            k_bcd_update<<<b_upd, kCdThreads, 0, stream>>>(lay.mols, nmol, k);
-            k_bcd_select<<<b_sel, kCdThreads, 0, stream>>>(lay.mols, nmol, k + 1);
+            k_bcd_project<<<b_prj, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
+            k_bcd_update<<<b_epi, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
         }
         count_launches(2ull * (unsigned long long)(k1 - k0));
         CDS_CUDA_TRY(cudaGetLastError());

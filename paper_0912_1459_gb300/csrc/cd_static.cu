@@ -63,8 +63,8 @@ extern "C" int cds_cd_decompose_static(int32_t nbf, const double* xyz, const dou
     void* ws = nullptr;
     int st = scratch_address(&ws);
     if (st) return st;
-    return cds_cd_decompose(nbf, xyz, alpha, atom, delta, scheme, max_rank, L, piv, D, M_out,
-                            delta_eff_out, ws, kStaticBytes, stream);
+    return cds_cd_decompose(nbf, xyz, alpha, atom, delta, scheme, max_rank, CDS_PREC_FP64, L, piv,
+                            D, M_out, delta_eff_out, ws, kStaticBytes, stream);
 }
 
 extern "C" int cds_cd_static_max_nbf(void) {

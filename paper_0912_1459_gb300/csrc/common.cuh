@@ -56,26 +56,48 @@ struct PairSoA {
     double* Px;   // product centre
     double* Py;
     double* Pz;
-    double* K;    // N_mu N_nu exp(-a_mu a_nu |A-B|^2 / p)
+    double* Kp;   // N_mu N_nu exp(-a_mu a_nu |A-B|^2 / p) / p
 };
 
-// Boys function F0(T) = (1/2) sqrt(pi/T) erf(sqrt T), 1 - T/3 below 1e-10.
-__device__ __forceinline__ double boys_f0(double T) {
-    if (T < 1e-10) return 1.0 - T * (1.0 / 3.0);
-    double x = sqrt(T);
-    return kHalfSqrtPi * erf(x) / x;
+// Above T = 36 the Boys function needs no error function: erfc(6) ~ 2.2e-17 is
+// below half an ulp of 1, so erf(sqrt T) rounds to exactly 1 in binary64.
+constexpr double kErfOneT = 36.0;
+constexpr double kPi3 = 31.006276680299816;   // pi^3 = 2 pi^(5/2) * sqrt(pi)/2
+
+// (rho_I|rho_J) = 2 pi^(5/2) K_I K_J / (p q sqrt(p+q)) F0(T), T = x / s with
+// x = p q |P-Q|^2 and s = p + q (Eq. integral, s-type).  The pair data hold
+// K/p, so no division is needed.
+__device__ __forceinline__ void eri_xs(double p, double px, double py, double pz, double q,
+                                       double qx, double qy, double qz, double& x, double& s) {
+    const double dx = px - qx, dy = py - qy, dz = pz - qz;
+    x = p * q * (dx * dx + dy * dy + dz * dz);
+    s = p + q;
+}
+// T >= kErfOneT: F0(T) = (1/2) sqrt(pi/T) exactly, and the integral reduces to
+// pi^3 (K_I/p)(K_J/q) / sqrt(x) (the point-charge form).
+__device__ __forceinline__ bool eri_is_far(double x, double s) { return x >= kErfOneT * s; }
+__device__ __forceinline__ double eri_far(double kk, double x) { return kPi3 * kk * rsqrt(x); }
+// T < kErfOneT: F0 through erf(sqrt T), or 1 - T/3 below T = 1e-10.  kk = (K_I/p)(K_J/q).
+__device__ __forceinline__ double eri_near(double kk, double x, double s) {
+    const double rs = rsqrt(s);
+    const double T = x * (rs * rs);
+    double f;
+    if (T < 1e-10) {
+        f = 1.0 - T * (1.0 / 3.0);
+    } else {
+        const double rT = rsqrt(T);
+        f = kHalfSqrtPi * rT * erf(T * rT);
+    }
+    return kTwoPi52 * kk * rs * f;
 }
 
 // (rho_I|rho_J) from the pair data of both densities (Eq. integral, s-type).
 __device__ __forceinline__ double eri_pair(double p, double px, double py, double pz,
-                                           double k, double q, double qx, double qy,
+                                           double kp, double q, double qx, double qy,
                                            double qz, double kq) {
-    double dx = px - qx, dy = py - qy, dz = pz - qz;
-    double d2 = dx * dx + dy * dy + dz * dz;
-    double pq = p * q;
-    double s = p + q;
-    double T = pq / s * d2;
-    return kTwoPi52 / (pq * sqrt(s)) * k * kq * boys_f0(T);
+    double x, s;
+    eri_xs(p, px, py, pz, q, qx, qy, qz, x, s);
+    return eri_is_far(x, s) ? eri_far(kp * kq, x) : eri_near(kp * kq, x, s);
 }
 
 // Decode a packed pair index I = nu(nu+1)/2 + mu into (mu, nu).

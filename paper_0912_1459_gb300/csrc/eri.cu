@@ -7,7 +7,7 @@ namespace cds {
 // Gaussian-product data of pair I from the basis (Sec. II.A).
 __device__ __forceinline__ void pair_of(int64_t I, const double* __restrict__ xyz,
                                         const double* __restrict__ alpha, double& p,
-                                        double& px, double& py, double& pz, double& k) {
+                                        double& px, double& py, double& pz, double& kp) {
     int32_t mu, nu;
     unpack_pair(I, mu, nu);
     double am = alpha[mu], an = alpha[nu];
@@ -21,7 +21,7 @@ __device__ __forceinline__ void pair_of(int64_t I, const double* __restrict__ xy
     px = (am * ax + an * bx) / p;
     py = (am * ay + an * by) / p;
     pz = (am * az + an * bz) / p;
-    k = nm * nn * exp(-am * an / p * r2);
+    kp = nm * nn * exp(-am * an / p * r2) / p;
 }
 
 __global__ void k_build_pairs(int32_t nbf, const double* __restrict__ xyz,
@@ -30,7 +30,7 @@ __global__ void k_build_pairs(int32_t nbf, const double* __restrict__ xyz,
     if (I >= npair) return;
     double p, px, py, pz, k;
     pair_of(I, xyz, alpha, p, px, py, pz, k);
-    pd.p[I] = p; pd.Px[I] = px; pd.Py[I] = py; pd.Pz[I] = pz; pd.K[I] = k;
+    pd.p[I] = p; pd.Px[I] = px; pd.Py[I] = py; pd.Pz[I] = pz; pd.Kp[I] = k;
 }
 
 int build_pairs(int32_t nbf, const double* xyz, const double* alpha, PairSoA pd,

@@ -7,7 +7,8 @@ holds a few GB of device memory at most and replays in seconds:
   python -m paper_0912_1459_gb300.profcases transform   # k_dfgemm / k_dgemm
   python -m paper_0912_1459_gb300.profcases sigma1      # k_sigma_tc, nE = 1
   python -m paper_0912_1459_gb300.profcases sigma64     # k_sigma_tc, nE = 64
-  python -m paper_0912_1459_gb300.profcases cd          # k_cd_update (C60, 1024 steps max)
+  python -m paper_0912_1459_gb300.profcases cd          # k_cd_update, FP64 (C60, 1024 steps max)
+  python -m paper_0912_1459_gb300.profcases cdf         # k_cd_update, float pairs
 
 Factors are seeded random numbers of the right shape and magnitude (the
 kernels' cost does not depend on their values).
@@ -51,9 +52,10 @@ def main(mode: str) -> None:
         E = d(W.energy_grid(m.eps[m.orbitals[9:11]], nE))
         for _ in range(2):
             G.cds_sigma2_diag(Lov, Lp, d(m.eps), m.nocc, E, "bf16x3")
-    elif mode == "cd":
+    elif mode in ("cd", "cdf"):
         G.cds_cd_decompose(d(m.basis.xyz), d(m.basis.alpha), d(m.basis.atom.astype(np.int32)),
-                           1e-4, "full", max_rank=1024)
+                           1e-4, "full", max_rank=1024,
+                           precision="f32x2" if mode == "cdf" else "fp64")
     else:
         raise SystemExit(f"unknown case {mode!r}")
     torch.cuda.synchronize()

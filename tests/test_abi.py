@@ -37,7 +37,7 @@ def test_host_only_calls(lib):
 def test_argument_errors_before_any_launch(lib):
     so = lib.load()
     # invalid sizes are rejected on the host, without touching a device
-    assert so.cds_cd_decompose(0, None, None, None, 1e-6, 0, 10, None, None, None, None, None,
+    assert so.cds_cd_decompose(0, None, None, None, 1e-6, 0, 10, 0, None, None, None, None, None,
                                None, 0, None) == 1
     assert so.cds_sigma2_diag(24, 6, 10, None, None, 1, None, None, 0, 0, None, None, None, 0,
                               None) == 1

@@ -34,9 +34,10 @@ def basis_dev(m):
     return dev(m.basis.xyz), dev(m.basis.alpha), dev(m.basis.atom.astype(np.int32))
 
 
-def gpu_cd(m, delta, scheme="full", max_rank=None):
+def gpu_cd(m, delta, scheme="full", max_rank=None, precision="fp64"):
     xyz, a, at = basis_dev(m)
-    L, piv, D, de = G.cds_cd_decompose(xyz, a, at, delta, scheme, max_rank=max_rank)
+    L, piv, D, de = G.cds_cd_decompose(xyz, a, at, delta, scheme, max_rank=max_rank,
+                                       precision=precision)
     torch.cuda.synchronize()
     return L.cpu().numpy(), piv.cpu().numpy().astype(np.int64), D.cpu().numpy(), de
 
@@ -78,6 +79,32 @@ def test_cd_parity(name, delta, scheme):
     np.testing.assert_allclose(L[:, sub].T @ L[:, sub], ref.L[:, sub].T @ ref.L[:, sub],
                                rtol=0, atol=1e-11)
     np.testing.assert_allclose(D, ref.D, rtol=0, atol=1e-11)
+
+
+@pytest.mark.parametrize("name,delta,scheme", [
+    ("c0", 1e-6, "full"), ("c1", 1e-4, "full"), ("c1", 1e-6, "full"), ("c1", 1e-5, "atomic"),
+])
+def test_cd_f32x2_parity(name, delta, scheme):
+    """Float-pair projections (~2^-44 per step instead of 2^-53): the same
+    pivots as the oracle, vectors and residuals within 1e-9, L^T L within
+    1e-9 on sampled pairs."""
+    m = O.molecule(name)
+    ref = O.decomposition(name, delta, scheme)
+    L, piv, D, de = gpu_cd(m, delta, scheme, precision="f32x2")
+    assert de == pytest.approx(ref.delta_eff, rel=1e-14)
+    assert np.array_equal(piv, ref.piv)
+    np.testing.assert_allclose(L, ref.L, rtol=0, atol=1e-9)
+    sub = np.random.default_rng(2).choice(L.shape[1], min(L.shape[1], 600), replace=False)
+    np.testing.assert_allclose(L[:, sub].T @ L[:, sub], ref.L[:, sub].T @ ref.L[:, sub],
+                               rtol=0, atol=1e-9)
+    np.testing.assert_allclose(D, ref.D, rtol=0, atol=1e-9)
+
+
+def test_cd_precision_rejected():
+    m = O.molecule("c0")
+    with pytest.raises(G.CdsError) as ei:
+        gpu_cd(m, 1e-6, precision="bf16x3")
+    assert ei.value.status == 7
 
 
 def test_cd_empty_when_delta_exceeds_every_diagonal():
