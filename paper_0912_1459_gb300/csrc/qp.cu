@@ -100,8 +100,9 @@ extern "C" int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* 
     CDS_LAUNCH_CHECK();
     int32_t h_active = np;
     for (int32_t it = 0; it < max_iter && h_active > 0; ++it) {
+        // the factors do not change during the solve: split them once
         int st = sigma2_dispatch(nmo, nocc, M, Lov, Lp, np, eps, omega, 1, precision, lay.active,
-                                 lay.sig, lay.dsig, lay.sigma_ws, stream);
+                                 lay.sig, lay.dsig, lay.sigma_ws, stream, it == 0);
         if (st) return st;
         CDS_CUDA_TRY(cudaMemsetAsync(lay.nactive, 0, sizeof(int32_t), stream));
         k_qp_step<<<nb, 128, 0, stream>>>(eps, orb, np, lay.sig, lay.dsig, conv, omega, pole,

@@ -207,13 +207,13 @@ size_t sigma_ws_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t 
 int sigma2_dispatch(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
                     int32_t np, const double* eps, const double* E, int32_t nE,
                     int32_t precision, const int32_t* active, double* sigma, double* dsigma,
-                    void* ws, cudaStream_t stream) {
+                    void* ws, cudaStream_t stream, bool resplit) {
     if (precision == CDS_PREC_FP64)
         return sigma2_fp64(nmo, nocc, M, Lov, Lp, np, eps, E, nE, active, sigma, dsigma,
                            static_cast<double*>(ws), stream);
     if (is_split16(precision))
         return sigma2_tc(nmo, nocc, M, Lov, Lp, np, eps, E, nE, active, precision, sigma, dsigma,
-                         ws, stream);
+                         ws, stream, resplit);
     return CDS_ERR_UNSUPPORTED;
 }
 

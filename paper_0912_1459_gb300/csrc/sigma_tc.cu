@@ -864,14 +864,16 @@ static int split_all(const double* Lp, const double* Lov, int64_t rows_p, int64_
 int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
               int32_t np, const double* eps, const double* E, int32_t nE,
               const int32_t* active, int32_t precision, double* sigma, double* dsigma, void* ws,
-              cudaStream_t stream) {
+              cudaStream_t stream, bool resplit) {
     using namespace tc;
     if (!device_ok()) return CDS_ERR_UNSUPPORTED;
     const bool bf16 = precision == CDS_PREC_BF16X3;
     const int32_t nv = nmo - nocc;
     const int32_t Mp = padded(std::max(M, 1));
     TcLayout lay = tc_layout(ws, nmo, nocc, M, np, nE);
-    int st = bf16 ? split_all<__nv_bfloat16>(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M, Mp,
+    int st = CDS_OK;
+    if (resplit)
+        st = bf16 ? split_all<__nv_bfloat16>(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M, Mp,
                                              lay, stream)
                   : split_all<__half>(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M, Mp, lay,
                                       stream);

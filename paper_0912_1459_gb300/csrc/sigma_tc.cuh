@@ -7,10 +7,12 @@ namespace cds {
 
 size_t tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE);
 
+// resplit = false reuses the 16-bit operand splits a previous call with the
+// same Lov, Lp and workspace left in ws (the Newton iterations of one solve).
 int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
               int32_t np, const double* eps, const double* E, int32_t nE,
               const int32_t* active, int32_t precision, double* sigma, double* dsigma, void* ws,
-              cudaStream_t stream);
+              cudaStream_t stream, bool resplit = true);
 
 // One molecule of a batch (host side) and the element offsets of its arrays
 // in the concatenated batch buffers.
@@ -42,6 +44,6 @@ size_t sigma_ws_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t 
 int sigma2_dispatch(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
                     int32_t np, const double* eps, const double* E, int32_t nE,
                     int32_t precision, const int32_t* active, double* sigma, double* dsigma,
-                    void* ws, cudaStream_t stream);
+                    void* ws, cudaStream_t stream, bool resplit = true);
 
 }  // namespace cds

@@ -218,3 +218,27 @@ def test_sigma_edge_cases():
     s1, _ = G.cds_sigma2_diag(dev(rov1), dev(rp1), dev(m.eps), m.nocc, dev(E[:3]), "fp64")
     rs1, _ = O.sigma("c0", rov1, rp1, E[:3])
     np.testing.assert_allclose(s1.cpu().numpy(), rs1, atol=1e-12, rtol=0)
+
+
+def test_tiny_case_against_stored_oracle_values():
+    """The whole FP64 path on the tiny case against tests/golden/c0_oracle.json."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "c0_oracle.json")) as f:
+        g = json.load(f)
+    m = O.molecule("c0")
+    xyz, a, at = basis_dev(m)
+    L, piv, D, de = G.cds_cd_decompose(xyz, a, at, g["delta"], "full")
+    assert piv.cpu().tolist() == g["cd"]["piv"]
+    orbs = dev(np.asarray(g["orbitals"]))
+    Lov, Lp = G.cds_cd_to_mo(L, dev(m.C), m.nocc, orbs)
+    eps = dev(m.eps)
+    E = dev(m.eps[g["orbitals"]][:, None])
+    s, ds = G.cds_sigma2_diag(Lov, Lp, eps, m.nocc, E, "fp64")
+    np.testing.assert_allclose(s.cpu().numpy()[:, 0], g["sigma_at_eps"], rtol=0, atol=1e-10)
+    np.testing.assert_allclose(ds.cpu().numpy()[:, 0], g["dsigma_at_eps"], rtol=1e-9)
+    w, P, it, st = G.cds_qp_solve(Lov, Lp, orbs, eps, m.nocc, precision="fp64")
+    for t, r in enumerate(g["qp"]):
+        assert int(it[t]) == r["iters"] and int(st[t]) == r["status"]
+        assert float(w[t]) == pytest.approx(r["omega"], abs=1e-9)
+        assert float(P[t]) == pytest.approx(r["pole"], rel=1e-8)
