@@ -10,8 +10,10 @@ every evaluation, as the paper does in its Newton iterations (Sec. III).
 The pole strength of Eq. ps needs dSigma/dw, taken analytically:
 dSigma/dw = - sum numerator / denominator^2.
 
-``sigma2_spin_orbital`` and ``mp2_energy`` are independent formulations
-(spin-orbital antisymmetrised integrals; Eq. MP2) used only as pins.
+``mp2_from_factors`` is Eq. MP2 on the same factors (the correlation energy
+the paper sets beside Eq. SE).  ``sigma2_spin_orbital`` and ``mp2_energy``
+are independent formulations (spin-orbital antisymmetrised integrals; Eq. MP2
+from explicit MO integrals) used only as pins.
 """
 from __future__ import annotations
 
@@ -111,6 +113,26 @@ def sigma2_spin_orbital(g: np.ndarray, eps: np.ndarray, nocc: int, q: int,
             for a in vir:
                 s += 0.5 * anti(i, j, qs, a) ** 2 / (w + eps[a[0]] - eps[i[0]] - eps[j[0]])
     return s
+
+
+def mp2_from_factors(Lov: np.ndarray, eps: np.ndarray, nocc: int, pairs: bool = False):
+    """MP2 correlation energy, Eq. MP2, with (ai|bj) = sum_K B^K_ia B^K_jb
+    recomputed from the factors (Eq. aomo).
+
+    Lov [o, v, M].  For each occupied i the integrals of all (j, a, b) come
+    from one matrix product, X[a, j, b] = (ia|jb); the exchange integral
+    (aj|bi) = (ib|ja) is X[b, j, a].  With ``pairs=True`` returns the per-i
+    sums e_i = sum_{j,a,b} (...) [o] instead of their total."""
+    o, v, M = Lov.shape
+    eo, ev = eps[:nocc], eps[nocc:]
+    Lov2 = Lov.reshape(o * v, M)
+    e = np.zeros(o)
+    for i in range(o):
+        X = (Lov[i] @ Lov2.T).reshape(v, o, v)
+        Xx = X.transpose(2, 1, 0)
+        D = eo[i] + eo[None, :, None] - ev[:, None, None] - ev[None, None, :]
+        e[i] = ((2 * X - Xx) * X / D).sum()
+    return e if pairs else float(e.sum())
 
 
 def mp2_energy(g: np.ndarray, eps: np.ndarray, nocc: int) -> float:

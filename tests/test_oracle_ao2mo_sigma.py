@@ -7,6 +7,9 @@
   explicit spin sums, (c) the MP2 identity sum_i Sigma^(2p1h)_ii(e_i) = E_MP2
   = -sum_a Sigma^(2h1p)_aa(e_a) with E_MP2 from Eq. MP2, and (d) the
   one-occupied/one-virtual closed form.
+* Eq. MP2 from the factors equals the explicit-integral loop, splits per
+  occupied orbital into the 2p1h self-energy at e_i, and reduces to the
+  o = v = 1 closed form.
 * dSigma/dw equals a central difference; every pole residue is >= 0, so
   dSigma/dw < 0 and 0 < P <= 1 (Eq. ps).
 * Newton (Eq. iter) converges to a root of w = e_q + Sigma(w) that a
@@ -75,6 +78,26 @@ def test_mp2_identity(c0):
     assert emp2 < 0
     assert abs(occ_sum - emp2) <= 1e-12 * abs(emp2)
     assert abs(vir_sum + emp2) <= 1e-12 * abs(emp2)
+
+
+def test_mp2_from_factors_pins(c0):
+    """Eq. MP2 from the factors against the explicit-integral quadruple loop
+    (an O(N^5) transform of the explicit AO tensor, delta = 0), the per-i
+    split against the 2p1h self-energy at e_i, and the o = v = 1 closed form
+    (ia|ia)^2 / (2 (e_i - e_a))."""
+    m, pd, r, g4, Lov, Lp = c0
+    e_fac = sigma2.mp2_from_factors(Lov, m.eps, m.nocc)
+    assert abs(e_fac - sigma2.mp2_energy(g4, m.eps, m.nocc)) <= 1e-11 * abs(e_fac)
+    e_i = sigma2.mp2_from_factors(Lov, m.eps, m.nocc, pairs=True)
+    for i in range(m.nocc):
+        two_p1h = sigma2.sigma2_from_factors(Lp[i], Lov, m.eps, m.nocc, [m.eps[i]], parts=True)[1][0]
+        assert abs(e_i[i] - two_p1h) <= 1e-12 * abs(e_fac)
+    assert np.all(e_i < 0)
+    rng = np.random.default_rng(5)
+    L1 = rng.standard_normal((1, 1, 7))
+    eps = np.array([-0.6, 0.4])
+    x = float(L1[0, 0] @ L1[0, 0])
+    assert sigma2.mp2_from_factors(L1, eps, 1) == pytest.approx(x * x / (2 * (-0.6 - 0.4)), rel=1e-14)
 
 
 def test_one_occupied_one_virtual_closed_form():
