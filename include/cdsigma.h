@@ -220,6 +220,27 @@ int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
                  size_t workspace_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * MP2 correlation energy (paper Eq. MP2), the ground-state companion of
+ * Eq. SE on the same factors:
+ *   E = sum_{i,j,a,b} (2 (ai|bj) - (aj|bi)) (ai|bj) / (e_i + e_j - e_a - e_b),
+ *   (ai|bj) = sum_K Lov[i][a][K] Lov[j][b][K], recomputed tile by tile.
+ * For each i the sum over j, a, b is the second sum of Eq. SE with q := i at
+ * E = e_i, and the call runs on the self-energy kernels (FP64, or the
+ * tensor-core split precisions).
+ * ---------------------------------------------------------------------- */
+
+size_t cds_mp2_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t precision);
+
+/* Asynchronous.  Inputs (device): Lov [nocc][nmo-nocc][M] fp64, eps [nmo].
+ * Outputs (device, caller-owned, either may be NULL but not both):
+ * e_pair [nocc] = sum_{j,a,b} for each occupied i; e_total [1] = sum of
+ * e_pair in a fixed order.  A tensor-core wait that gives up writes NaN.
+ * precision: CDS_PREC_FP64, CDS_PREC_BF16X3 or CDS_PREC_FP16X3. */
+int cds_mp2_energy(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                   const double* eps, int32_t precision, double* e_pair, double* e_total,
+                   void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Adjoint (no counterpart in the paper, which does not differentiate; the
  * derivative of Eq. SE, Eq. iter and Eq. transformation).  For a loss l of
  * converged quasiparticle energies w_t with upstream gradients g_t:

@@ -115,23 +115,28 @@ def sigma2_spin_orbital(g: np.ndarray, eps: np.ndarray, nocc: int, q: int,
     return s
 
 
-def mp2_from_factors(Lov: np.ndarray, eps: np.ndarray, nocc: int, pairs: bool = False):
+def mp2_from_factors(Lov: np.ndarray, eps: np.ndarray, nocc: int, pairs: bool = False,
+                     rows=None):
     """MP2 correlation energy, Eq. MP2, with (ai|bj) = sum_K B^K_ia B^K_jb
     recomputed from the factors (Eq. aomo).
 
     Lov [o, v, M].  For each occupied i the integrals of all (j, a, b) come
     from one matrix product, X[a, j, b] = (ia|jb); the exchange integral
     (aj|bi) = (ib|ja) is X[b, j, a].  With ``pairs=True`` returns the per-i
-    sums e_i = sum_{j,a,b} (...) [o] instead of their total."""
+    sums e_i = sum_{j,a,b} (...) [o] instead of their total; ``rows`` limits
+    them to a subset of i (then only those e_i are returned)."""
     o, v, M = Lov.shape
     eo, ev = eps[:nocc], eps[nocc:]
     Lov2 = Lov.reshape(o * v, M)
-    e = np.zeros(o)
-    for i in range(o):
+    idx = range(o) if rows is None else [int(i) for i in rows]
+    e = np.zeros(len(idx))
+    for n, i in enumerate(idx):
         X = (Lov[i] @ Lov2.T).reshape(v, o, v)
         Xx = X.transpose(2, 1, 0)
         D = eo[i] + eo[None, :, None] - ev[:, None, None] - ev[None, None, :]
-        e[i] = ((2 * X - Xx) * X / D).sum()
+        e[n] = ((2 * X - Xx) * X / D).sum()
+    if rows is not None:
+        return e
     return e if pairs else float(e.sum())
 
 

@@ -54,6 +54,8 @@ _SIGNATURES = {
     "cds_qp_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "cds_qp_solve": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _f64, _i32, _i32,
                                     _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "cds_mp2_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32]),
+    "cds_mp2_energy": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
 }
 
 
@@ -328,6 +330,32 @@ def cds_qp_solve(Lov: torch.Tensor, Lp: torch.Tensor, orbitals: torch.Tensor, ep
         st = CDS_OK
     _check(st, "cds_qp_solve")
     return omega, pole, iters, status
+
+
+def cds_mp2_energy(Lov: torch.Tensor, eps: torch.Tensor, nocc: int, precision: str = "fp64",
+                   workspace: Optional[torch.Tensor] = None):
+    """MP2 correlation energy (paper Eq. MP2) from the factors.
+
+    Returns (e_total [1], e_pair [nocc]) as device tensors: e_pair[i] is the
+    sum over j, a, b for occupied i."""
+    lib = load()
+    Lov = _dev(Lov, torch.float64, "Lov")
+    eps = _dev(eps, torch.float64, "eps")
+    dev = Lov.device
+    o, v, M = Lov.shape
+    if o != nocc:
+        raise ValueError("Lov must be [nocc, nvirt, M]")
+    nmo = nocc + v
+    prec = PRECISIONS[precision]
+    e_total = torch.empty(1, dtype=torch.float64, device=dev)
+    e_pair = torch.empty(max(nocc, 1), dtype=torch.float64, device=dev)
+    need = lib.cds_mp2_workspace_bytes(nmo, nocc, M, prec)
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    st = lib.cds_mp2_energy(nmo, nocc, M, _p(Lov), _p(eps), prec, _p(e_pair), _p(e_total),
+                            _p(workspace), workspace.numel(), _stream(dev))
+    _check(st, "cds_mp2_energy")
+    return e_total, e_pair[:nocc]
 
 
 # ---------------------------------------------------------------------------

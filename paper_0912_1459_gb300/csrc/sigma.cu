@@ -197,6 +197,64 @@ int sigma2_fp64(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const d
     return CDS_OK;
 }
 
+__global__ void k_sum_fixed(const double* __restrict__ x, int32_t n, double* __restrict__ out) {
+    __shared__ double sh[256];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v += x[i];
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+int sum_fixed(const double* x, int32_t n, double* out, cudaStream_t stream) {
+    if (!out) return CDS_OK;
+    k_sum_fixed<<<1, 256, 0, stream>>>(x, n, out);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
+// Eq. MP2 as the second sum of Eq. SE with q := i, spectator j, E := e_i:
+// both operands are rows of Lov, and the energies E of "orbital" i are eps.
+static SigmaTerm mp2_term(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                          const double* eps) {
+    const int32_t nv = nmo - nocc;
+    SigmaTerm t;
+    t.Aq = Lov; t.sAt = (int64_t)nv * M; t.sAx = M;
+    t.Bk = Lov; t.sBs = (int64_t)nv * M; t.sBy = M;
+    t.eps_s = eps; t.eps_x = eps ? eps + nocc : nullptr; t.nx = nv; t.ns = nocc;
+    return t;
+}
+
+static size_t mp2_fp64_bytes(int32_t nmo, int32_t nocc) {
+    const SigmaTerm t = mp2_term(nmo, nocc, 1, nullptr, nullptr);
+    return align_up((size_t)std::max<int64_t>(items_of(t, nocc, kTB64), 1) * 2 * sizeof(double)) +
+           align_up((size_t)std::max(nocc, 1) * sizeof(double));
+}
+
+static int mp2_fp64(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* eps,
+                    double* e_pair, double* e_total, void* ws, cudaStream_t stream) {
+    const SigmaTerm t = mp2_term(nmo, nocc, M, Lov, eps);
+    const int64_t n = items_of(t, nocc, kTB64);
+    Carver c(ws);
+    double* part = c.take<double>((size_t)std::max<int64_t>(n, 1) * 2);
+    double* ep = c.take<double>((size_t)std::max(nocc, 1));
+    if (e_pair) ep = e_pair;
+    if (n == 0 || M == 0) {
+        CDS_CUDA_TRY(cudaMemsetAsync(ep, 0, sizeof(double) * std::max(nocc, 1), stream));
+        return sum_fixed(ep, nocc, e_total, stream);
+    }
+    k_sigma_fp64<<<(unsigned)n, 256, 0, stream>>>(t, M, 1, eps, nullptr, 0, part);
+    CDS_LAUNCH_CHECK();
+    k_sigma_reduce<<<dim3(1, nocc), 256, 0, stream>>>(part, 0, 0, n / nocc, 1, nullptr, ep,
+                                                     nullptr);
+    CDS_LAUNCH_CHECK();
+    return sum_fixed(ep, nocc, e_total, stream);
+}
+
 size_t sigma_ws_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE,
                       int32_t precision) {
     if (precision == CDS_PREC_FP64) return fp64_part_bytes(nmo, nocc, np, nE);
@@ -245,4 +303,30 @@ extern "C" int cds_sigma2_diag(int32_t nmo, int32_t nocc, int32_t M, const doubl
     if (need && (!workspace || workspace_bytes < need)) return CDS_ERR_WORKSPACE;
     return sigma2_dispatch(nmo, nocc, M, Lov, Lp, np, eps, E, nE, precision, nullptr, sigma,
                            dsigma, workspace, stream);
+}
+
+extern "C" size_t cds_mp2_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t precision) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || M < 0) return 0;
+    if (precision == CDS_PREC_FP64) return mp2_fp64_bytes(nmo, nocc);
+    if (is_split16(precision)) return tc_mp2_workspace_bytes(nmo, nocc, M);
+    return 0;
+}
+
+extern "C" int cds_mp2_energy(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                              const double* eps, int32_t precision, double* e_pair,
+                              double* e_total, void* workspace, size_t workspace_bytes,
+                              cudaStream_t stream) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || M < 0 || nocc > 65535) return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && !is_split16(precision)) return CDS_ERR_UNSUPPORTED;
+    if (!eps || (!e_pair && !e_total) || (nocc > 0 && nocc < nmo && M > 0 && !Lov))
+        return CDS_ERR_ARG;
+    if (nocc == 0) {
+        if (e_total) CDS_CUDA_TRY(cudaMemsetAsync(e_total, 0, sizeof(double), stream));
+        return CDS_OK;
+    }
+    const size_t need = cds_mp2_workspace_bytes(nmo, nocc, M, precision);
+    if (!workspace || workspace_bytes < need) return CDS_ERR_WORKSPACE;
+    if (precision == CDS_PREC_FP64)
+        return mp2_fp64(nmo, nocc, M, Lov, eps, e_pair, e_total, workspace, stream);
+    return mp2_tc(nmo, nocc, M, Lov, eps, precision, e_pair, e_total, workspace, stream);
 }

@@ -938,6 +938,114 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
 
 
 // ===========================================================================
+// MP2 correlation energy (Eq. MP2) on the same kernel.  For occupied i, j the
+// sum over a, b is the second sum of Eq. SE with orbital q := i, spectator
+// j and E := e_i, and both operands are rows of Lov: the orbital tiles come
+// from Lov[i], the spectator tiles from Lov[j].  So the item list is term 1
+// only, with nocc "orbitals", and the per-orbital totals are the per-i sums
+// e_i = sum_{j,a,b}.
+// ===========================================================================
+namespace tc {
+struct Mp2Layout {
+    TcLayout tc;      // lp_hi / lp_lo unused
+    double* epair;    // [nocc] when the caller passes none
+    size_t bytes;
+};
+
+Mp2Layout mp2_layout(void* ws, int32_t nmo, int32_t nocc, int32_t M) {
+    const int32_t Mp = padded(std::max(M, 1)), nv = nmo - nocc;
+    Carver c(ws);
+    Mp2Layout l;
+    l.tc.lp_hi = l.tc.lp_lo = nullptr;
+    l.tc.lov_hi = c.take<uint16_t>((size_t)nocc * nv * Mp);
+    l.tc.lov_lo = c.take<uint16_t>((size_t)nocc * nv * Mp);
+    l.tc.part = c.take<double>((size_t)std::max<int64_t>(tc_items(nv, nocc, nocc), 1) * 2);
+    l.tc.amax = c.take<unsigned long long>(2);
+    l.tc.inv = c.take<float>(2);
+    l.tc.eps2 = c.take<float2>((size_t)nmo);
+    l.tc.E2 = c.take<float2>((size_t)std::max(nocc, 1));
+    l.tc.err = c.take<int32_t>(4);
+    l.epair = c.take<double>((size_t)std::max(nocc, 1));
+    l.tc.bytes = l.bytes = c.off;
+    return l;
+}
+}  // namespace tc
+
+size_t tc_mp2_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M) {
+    return tc::mp2_layout(nullptr, nmo, nocc, M).bytes;
+}
+
+int mp2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* eps,
+           int32_t precision, double* e_pair, double* e_total, void* ws, cudaStream_t stream) {
+    using namespace tc;
+    if (!device_ok()) return CDS_ERR_UNSUPPORTED;
+    const bool bf16 = precision == CDS_PREC_BF16X3;
+    const int32_t nv = nmo - nocc;
+    const int32_t Mp = padded(std::max(M, 1));
+    Mp2Layout ml = mp2_layout(ws, nmo, nocc, M);
+    const TcLayout& lay = ml.tc;
+    double* ep = e_pair ? e_pair : ml.epair;
+    const int64_t nitems = tc_items(nv, nocc, nocc);
+    if (nitems == 0 || M == 0) {
+        CDS_CUDA_TRY(cudaMemsetAsync(ep, 0, sizeof(double) * std::max(nocc, 1), stream));
+        return sum_fixed(ep, nocc, e_total, stream);
+    }
+    // one array feeds both operands: one scale, inv = 1 / s^2
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.amax, 0, 2 * sizeof(unsigned long long), stream));
+    const int64_t rows = (int64_t)nocc * nv, n = rows * Mp;
+    if (!bf16) {
+        k_absmax<<<4 * 152, 256, 0, stream>>>(Lov, rows * M, lay.amax);
+        CDS_LAUNCH_CHECK();
+        CDS_CUDA_TRY(cudaMemcpyAsync(lay.amax + 1, lay.amax, sizeof(unsigned long long),
+                                     cudaMemcpyDeviceToDevice, stream));
+        k_split16<__half><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+            Lov, rows, M, Mp, lay.amax, (__half*)lay.lov_hi, (__half*)lay.lov_lo);
+    } else {
+        k_split16<__nv_bfloat16><<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+            Lov, rows, M, Mp, lay.amax, (__nv_bfloat16*)lay.lov_hi, (__nv_bfloat16*)lay.lov_lo);
+    }
+    CDS_LAUNCH_CHECK();
+    k_inv_scale<<<1, 1, 0, stream>>>(lay.amax, bf16 ? 1 : 0, lay.inv);
+    CDS_LAUNCH_CHECK();
+    Params P{};
+    Maps maps;
+    memset(&maps, 0, sizeof(maps));
+    const uint64_t rowb = (uint64_t)Mp * 2;
+    Term& tm = P.term[1];
+    tm.nx = nv;
+    tm.ns = nocc;
+    tm.nb = nblocks_of(nv, TB);
+    tm.npb = npairs_of(tm.nb);
+    tm.nitems = nitems;
+    tm.item0 = 0;
+    tm.bulk_s_dim = 2;
+    tm.eps_s_off = 0;
+    tm.eps_x_off = nocc;
+    // orbital tiles Lov[i][A-block], spectator tiles Lov[j][B-block]: the same map
+    if (!make_map(&maps.m[1][0], bf16, lay.lov_hi, Mp, nv, nocc, rowb, rowb * nv, TB, 1) ||
+        !make_map(&maps.m[1][1], bf16, lay.lov_lo, Mp, nv, nocc, rowb, rowb * nv, TB, 1))
+        return CDS_ERR_CUDA;
+    maps.m[1][2] = maps.m[1][0];
+    maps.m[1][3] = maps.m[1][1];
+    P.kblocks = Mp / KB;
+    P.nE = 1;
+    P.nmo = nmo;
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.err, 0, sizeof(int32_t), stream));
+    k_to_pairs<<<(nmo + 255) / 256, 256, 0, stream>>>(eps, nmo, lay.eps2);
+    CDS_LAUNCH_CHECK();
+    k_to_pairs<<<(nocc + 255) / 256, 256, 0, stream>>>(eps, nocc, lay.E2);   // E_i = e_i
+    CDS_LAUNCH_CHECK();
+    const int grid = (int)std::min<int64_t>(nitems, device_sms());
+    int st = separate_accumulators() ? launch_any<true>(grid, bf16, 1, maps, P, nullptr, lay, stream)
+                                     : launch_any<false>(grid, bf16, 1, maps, P, nullptr, lay, stream);
+    if (st) return st;
+    k_tc_reduce<<<dim3(1, nocc), 256, 0, stream>>>(lay.part, 0, 0, nitems / nocc, 1, nullptr,
+                                                  lay.err, ep, nullptr);
+    CDS_LAUNCH_CHECK();
+    return sum_fixed(ep, nocc, e_total, stream);
+}
+
+// ===========================================================================
 // Batched form: the items of many molecules in one persistent launch.
 // ===========================================================================
 namespace tc {

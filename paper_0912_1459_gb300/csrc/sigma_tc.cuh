@@ -14,6 +14,14 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
               const int32_t* active, int32_t precision, double* sigma, double* dsigma, void* ws,
               cudaStream_t stream, bool resplit = true);
 
+// MP2 correlation energy (Eq. MP2) on the tensor-core kernel: e_pair[i] =
+// sum_{j,a,b}, e_total = sum_i e_pair[i] (either may be null).
+size_t tc_mp2_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M);
+int mp2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* eps,
+           int32_t precision, double* e_pair, double* e_total, void* ws, cudaStream_t stream);
+// out[0] = sum of x[0..n) in a fixed order (nothing if out is null).
+int sum_fixed(const double* x, int32_t n, double* out, cudaStream_t stream);
+
 // One molecule of a batch (host side) and the element offsets of its arrays
 // in the concatenated batch buffers.
 struct BatchMol {

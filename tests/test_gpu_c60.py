@@ -173,3 +173,19 @@ def test_cd_f32x2_full_size(run):
     qp = (st64.cpu().numpy() == 0) & (P64.cpu().numpy() >= 0.5)
     assert qp.sum() >= 3
     assert np.abs(wmx.cpu().numpy()[qp] - w64.cpu().numpy()[qp]).max() <= TOL_QP
+
+
+def test_mp2_full_size(run):
+    """Eq. MP2 at C60 size on the benchmark's factors: the FP64 and BF16X3
+    per-i sums of two occupied orbitals against the oracle (1e-10 and 1e-5
+    relative), and the BF16X3 total against the FP64 total (1e-5)."""
+    m, L, piv, D, de, Lov, Lp = run
+    eps = dev(m.eps)
+    rows = [0, m.nocc - 1]
+    ref = sigma2.mp2_from_factors(Lov.cpu().numpy(), m.eps, m.nocc, rows=rows)
+    t64, e64 = G.cds_mp2_energy(Lov, eps, m.nocc, "fp64")
+    tbf, ebf = G.cds_mp2_energy(Lov, eps, m.nocc, "bf16x3")
+    e64, ebf = e64.cpu().numpy(), ebf.cpu().numpy()
+    np.testing.assert_allclose(e64[rows], ref, rtol=1e-10)
+    np.testing.assert_allclose(ebf[rows], ref, rtol=1e-5)
+    assert abs(float(tbf) - float(t64)) <= 1e-5 * abs(float(t64))

@@ -230,7 +230,7 @@ def test_tiny_case_against_stored_oracle_values():
     xyz, a, at = basis_dev(m)
     L, piv, D, de = G.cds_cd_decompose(xyz, a, at, g["delta"], "full")
     assert piv.cpu().tolist() == g["cd"]["piv"]
-    orbs = dev(np.asarray(g["orbitals"]))
+    orbs = dev(np.asarray(g["orbitals"], dtype=np.int32))
     Lov, Lp = G.cds_cd_to_mo(L, dev(m.C), m.nocc, orbs)
     eps = dev(m.eps)
     E = dev(m.eps[g["orbitals"]][:, None])
