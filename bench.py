@@ -45,6 +45,7 @@ UNIT = "solves/s"
 WORKLOAD = "c60-shaped N=840 o=180 v=660 (truncated icosahedron, 14 s-Gaussians/centre)"
 HARTREE_EV = 27.211396     # Sec. III conversion factor
 L2_BYTES = 129 * 2 ** 20
+CD_TRAFFIC_RATIO = 1.0073   # ncu DRAM bytes / algorithmic bytes of k_cd_project (C60, k = 700)
 
 
 def parse():
@@ -370,6 +371,12 @@ def run_ours(args, dist: Dist):
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
+    if tr_prec != "fp64":
+        # DRAM bytes of one decomposition: the algorithmic bytes times the ratio
+        # measured by ncu on k_cd_project at k = 700 (1.9925 GB read + 8.7 MB
+        # written against 1.978 GB + one new vector)
+        roof["cd"]["traffic"] = fm["cd_bytes"] * CD_TRAFFIC_RATIO
+        roof["cd"]["traffic_unit"] = "bytes per decomposition"
     dominant = max(med, key=med.get)
 
     # ---- FP64 GPU arm on a subset, and mixed-vs-FP64 accuracy ----

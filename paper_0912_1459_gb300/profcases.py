@@ -53,9 +53,15 @@ def main(mode: str) -> None:
         for _ in range(2):
             G.cds_sigma2_diag(Lov, Lp, d(m.eps), m.nocc, E, "bf16x3")
     elif mode in ("cd", "cdf"):
-        G.cds_cd_decompose(d(m.basis.xyz), d(m.basis.alpha), d(m.basis.atom.astype(np.int32)),
-                           1e-4, "full", max_rank=1024,
-                           precision="f32x2" if mode == "cdf" else "fp64")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        L, _, _, _ = G.cds_cd_decompose(d(m.basis.xyz), d(m.basis.alpha),
+                                        d(m.basis.atom.astype(np.int32)), 1e-4, "full",
+                                        max_rank=1024,
+                                        precision="f32x2" if mode == "cdf" else "fp64")
+        b.record()
+        torch.cuda.synchronize()
+        print(f"decomposition: M = {L.shape[0]}, {a.elapsed_time(b):.1f} ms")
     else:
         raise SystemExit(f"unknown case {mode!r}")
     torch.cuda.synchronize()
