@@ -45,7 +45,6 @@ UNIT = "solves/s"
 WORKLOAD = "c60-shaped N=840 o=180 v=660 (truncated icosahedron, 14 s-Gaussians/centre)"
 HARTREE_EV = 27.211396     # Sec. III conversion factor
 L2_BYTES = 129 * 2 ** 20
-CD_TRAFFIC_RATIO = 1.0073   # ncu DRAM bytes / algorithmic bytes of k_cd_project (C60, k = 700)
 
 
 def parse():
@@ -331,6 +330,9 @@ def run_ours(args, dist: Dist):
 
     # ---- rooflines (per call, CUDA events on the launching stream) ----
     fm = flops_model(m, M)
+    cd_stats = G.cdsigma.cds_cd_stats(m.nbf, cd_ws, "f32x2" if tr_prec != "fp64" else "fp64")
+    cd_bytes = float(npr) * (8.0 * cd_stats["streamed"] + 8.0 * cd_stats["extra"] +
+                             32.0 * cd_stats["passes"] + 89.0 * M)
     pk = peaks()
     iters = it.cpu().numpy()
     med = {k: statistics.median(v) for k, v in stage_ms.items()}
@@ -344,10 +346,14 @@ def run_ours(args, dist: Dist):
                       "note": "FP64 projections npair*M^2 flops; peak = nominal FP64 rate"}
     else:
         roof["cd"] = {"bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
-                      "achieved": fm["cd_bytes"] / (med["cd"] / 1e3) / 1e9,
-                      "note": "float-pair projections stream the stored vectors once per "
-                              "step: npair*(4 M(M-1) + 73 M) bytes per decomposition; "
-                              "stage time of k_cd_update + k_cd_select"}
+                      "achieved": cd_bytes / (med["cd"] / 1e3) / 1e9,
+                      "note": (f"speculative float-pair projections: {cd_stats['passes']} "
+                               f"streaming passes over {M} steps read {cd_stats['streamed']} "
+                               f"stored vectors in total; bytes = npair*(8*streamed + "
+                               f"8*extra + 32*passes + 89*M); stage time of k_cd_project_spec "
+                               f"+ k_cd_update"),
+                      "cd_stats": cd_stats,
+                      "plain_left_looking_bytes": fm["cd_bytes"]}
     if tr_prec == "fp64":
         roof["transform"] = {"bound": "alu", "unit": "TFLOP/s", "peak": pk["fp64_tflops"],
                              "achieved": fm["transform"] / (med["transform"] / 1e3) / 1e12,
@@ -371,12 +377,7 @@ def run_ours(args, dist: Dist):
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
-    if tr_prec != "fp64":
-        # DRAM bytes of one decomposition: the algorithmic bytes times the ratio
-        # measured by ncu on k_cd_project at k = 700 (1.9925 GB read + 8.7 MB
-        # written against 1.978 GB + one new vector)
-        roof["cd"]["traffic"] = fm["cd_bytes"] * CD_TRAFFIC_RATIO
-        roof["cd"]["traffic_unit"] = "bytes per decomposition"
+    # (traffic stays null until an ncu capture of the current CD kernels exists)
     dominant = max(med, key=med.get)
 
     # ---- FP64 GPU arm on a subset, and mixed-vs-FP64 accuracy ----

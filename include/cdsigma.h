@@ -122,7 +122,12 @@ size_t cds_cd_workspace_bytes(int32_t nbf);
  * (the projections sum_K L^K_I L^K_P in float-pair arithmetic, ~2^-44 relative
  * per step, with the vectors held as float pairs while the decomposition runs;
  * integral columns, L^k, the residual diagonal and the pivot search stay FP64;
- * L is returned in FP64 either way).
+ * L is returned in FP64 either way).  F32X2 also speculates: one streaming
+ * pass forms the projections of the step's pivot and of three likely next
+ * pivots (the largest residuals of other blocks), and the following steps
+ * whose pivots are among them reuse those projections plus the few vectors
+ * made since.  The pivot rule and the result are those of the plain
+ * algorithm; only the grouping of each sum differs (see cds_cd_stats).
  * Inputs (device): xyz, alpha, atom.  Outputs (device, caller-owned):
  *   L     [max_rank][npair] fp64, rows 0..M-1 written;
  *   piv   [max_rank] int32 packed pivot index of each vector;
@@ -137,6 +142,17 @@ int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
                      int32_t precision, double* L, int32_t* piv, double* D, int32_t* M_out,
                      double* delta_eff_out, void* workspace, size_t workspace_bytes,
                      cudaStream_t stream);
+
+/* Work counters of the last cds_cd_decompose that used this workspace
+ * (blocking; reads the workspace's control block).  passes = steps that
+ * streamed the stored vectors, streamed = vectors read by those passes in
+ * total, extra = vectors added to a candidate projection by the steps in
+ * between (F32X2 speculative projections: a pass forms the projections of
+ * the pivot and of three likely next pivots; a later step whose pivot is
+ * among them adds only the vectors made since).  FP64 streams at every step:
+ * passes = M, streamed = M(M-1)/2, extra = 0. */
+int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precision, int32_t* passes,
+                 int64_t* streamed, int64_t* extra, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * Allocation-free Cholesky decomposition.  The paper has no counterpart: this

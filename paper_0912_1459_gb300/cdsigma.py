@@ -54,6 +54,8 @@ _SIGNATURES = {
     "cds_qp_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "cds_qp_solve": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _f64, _i32, _i32,
                                     _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "cds_cd_stats": (ctypes.c_int, [_i32, _vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int64), _vp]),
     "cds_mp2_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32]),
     "cds_mp2_energy": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
 }
@@ -223,6 +225,17 @@ def cds_cd_decompose(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,
                               ctypes.byref(de), _p(workspace), workspace.numel(), _stream(dev))
     _check(st, "cds_cd_decompose")
     return L_out[:M.value], piv[:M.value], D, de.value
+
+
+def cds_cd_stats(nbf: int, workspace: torch.Tensor, precision: str = "fp64") -> dict:
+    """Work counters of the last decomposition run in ``workspace``: streaming
+    passes, vectors streamed by them, vectors added between passes."""
+    lib = load()
+    p, st_, ex = _i32(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.cds_cd_stats(int(nbf), _p(workspace), PRECISIONS[precision], ctypes.byref(p),
+                            ctypes.byref(st_), ctypes.byref(ex), _stream(workspace.device)),
+           "cds_cd_stats")
+    return {"passes": p.value, "streamed": st_.value, "extra": ex.value}
 
 
 def cds_cd_decompose_static(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,

@@ -12,6 +12,9 @@
 // k_cd_update forms L^k and the residuals, and the last of its blocks to
 // arrive finishes the grid-wide extrema and picks the next pivot (no spin
 // waits).  k_cd_select picks the first pivot only.
+// The float-pair form streams L only at the first step of a batch, forming
+// the projections of four candidate pivots at once (k_cd_project_spec);
+// steps whose pivot is among them reuse those (cd_spec_dot_body).
 // All kernels read a device control block and return at once after the
 // decomposition has stopped, so the host enqueues steps ahead and checks the
 // control block only every few steps.
@@ -33,6 +36,15 @@ constexpr int kCdChunk = 2048;   // pivot row L^K_P staged in shared memory in c
 constexpr double kTieRel = 1e-12;
 constexpr double kNotPdRel = 1e-10;
 constexpr int kHostCheckEvery = 32;
+#ifndef CDS_KSPEC
+#define CDS_KSPEC 4
+#endif
+#ifndef CDS_KSPEC_ROWS
+#define CDS_KSPEC_ROWS 4
+#endif
+constexpr int kSpec = CDS_KSPEC;          // candidate pivots per speculative projection pass
+constexpr int kSpecRows = CDS_KSPEC_ROWS; // rows of L in flight per thread and iteration
+constexpr int kSpecChunk = 1024;  // pivot columns staged per shared-memory chunk
 
 struct CdCtrl {
     double scale;      // max initial diagonal (all pairs)
@@ -41,6 +53,7 @@ struct CdCtrl {
     double Dmin;       // min residual after the last update
     double DP;         // residual of the current pivot
     double rDP;        // 1 / sqrt(DP)
+    float2 rDPf;       // the same as a float pair
     int64_t P;         // current pivot
     int32_t done;      // decomposition stopped
     int32_t status;    // cds_status
@@ -48,6 +61,13 @@ struct CdCtrl {
     int32_t _pad;
     unsigned int counter;  // last-block-done counter
     unsigned int _pad2;
+    // speculative projections (float-pair mode): the pivots of the current
+    // batch's candidate set, the batch's first step, the slot of the current
+    // pivot in the set, and whether this step streams L (a new batch)
+    long long S[kSpec];
+    int32_t k0, slot, pass, passes;     // passes: batches started (streaming passes)
+    long long streamed;                  // sum over passes of the vectors streamed (k0)
+    long long extra;                     // sum over continued steps of the vectors added (k - k0)
 };
 
 __device__ __forceinline__ double warp_max(double v) {
@@ -210,7 +230,19 @@ __device__ void cd_select_body(int64_t n, int32_t k, int32_t max_rank,
                 ctrl->P = m;
                 ctrl->DP = __ldcg(D + m);
                 ctrl->rDP = 1.0 / sqrt(ctrl->DP);
+                {
+                    const float h = (float)ctrl->rDP;
+                    ctrl->rDPf = make_float2(h, (float)(ctrl->rDP - (double)h));
+                }
                 piv[k] = (int32_t)m;
+                ctrl->S[0] = m;
+                for (int i = 1; i < kSpec; ++i) ctrl->S[i] = -1;
+                ctrl->k0 = k;
+                ctrl->slot = 0;
+                ctrl->pass = 1;
+                ctrl->passes = 1;
+                ctrl->streamed = k;
+                ctrl->extra = 0;
             }
             ctrl->counter = 0;
         }
@@ -223,8 +255,10 @@ __global__ void k_cd_select(int64_t n, int32_t k, int32_t max_rank, const double
     cd_select_body(n, k, max_rank, D, cand, blk_i, piv, ctrl, blockIdx.x, gridDim.x);
 }
 
-// acc += a * b in (hi, lo) float pairs: exact product error by FMA, exact
-// sum error by two-sum (~2^-44 relative per step on the FP32 units).
+// Float-pair ("double-float") arithmetic: a value is hi + lo with two FP32
+// numbers, |lo| <= ulp(hi)/2; products get their exact error from an FMA and
+// sums from two-sum, so each operation is good to ~2^-44 relative, on the
+// FP32 units (the FP64 pipe of this part does 2 FMA/clk/SM).
 __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
     const float s = a.x + b.x;
     const float bp = s - a.x;
@@ -234,6 +268,32 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b) {
     return make_float2(h, e - (h - s));
 }
 
+__device__ __forceinline__ float2 df_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    const float h = p + e;
+    return make_float2(h, e - (h - p));
+}
+
+// 1/sqrt(x) for x > 0: a FP32 seed y, then one third-order Newton-type
+// correction y (1 + r/2 + 3 r^2/8) with the residual r = 1 - x y^2 formed in
+// float pairs (the seed's error ~2^-22 becomes ~2^-64, below the pair's own).
+__device__ __forceinline__ float2 df_rsqrt(float2 x) {
+    const float y = rsqrtf(x.x);
+    const float y2 = y * y;
+    const float2 yy = make_float2(y2, fmaf(y, y, -y2));
+    const float2 r2 = df_add(make_float2(1.f, 0.f), df_neg(df_mul(x, yy)));
+    const float r = r2.x + r2.y;
+    const float c = y * (r * fmaf(0.375f, r, 0.5f));
+    const float h = y + c;
+    return make_float2(h, c - (h - y));
+}
+
+// acc += a * b in float pairs.
 __device__ __forceinline__ void df_fma(float2& acc, float2 a, float2 b) {
     const float p = a.x * b.x;
     float pe = fmaf(a.x, b.x, -p);
@@ -244,6 +304,75 @@ __device__ __forceinline__ void df_fma(float2& acc, float2 a, float2 b) {
     const float err = (acc.x - (s - bp)) + (p - bp);
     acc.x = s;
     acc.y += err + pe;
+}
+
+// Pair data as float pairs (float-pair decomposition).
+struct PairF2 {
+    float2 *p, *Px, *Py, *Pz, *Kp;
+};
+
+__device__ __forceinline__ float2 to_f2(double x) {
+    const float h = (float)x;
+    return make_float2(h, (float)(x - (double)h));
+}
+
+__global__ void k_pairs_to_f2(PairSoA pd, PairF2 pf, int64_t n) {
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (I >= n) return;
+    pf.p[I] = to_f2(pd.p[I]);
+    pf.Px[I] = to_f2(pd.Px[I]);
+    pf.Py[I] = to_f2(pd.Py[I]);
+    pf.Pz[I] = to_f2(pd.Pz[I]);
+    pf.Kp[I] = to_f2(pd.Kp[I]);
+}
+
+constexpr float kPi3Hi = (float)kPi3;
+constexpr float kPi3Lo = (float)(kPi3 - (double)kPi3Hi);
+
+// Integral column of the float-pair decomposition: the far pairs (T >= 36,
+// the point-charge form pi^3 (K_I/p)(K_P/q) / sqrt(p q |P-Q|^2)) in float-pair
+// arithmetic from the float-pair pair data, the others gathered and evaluated
+// in FP64 as in cd_eri_body.  Values below the FP32 range (|K/p| < 1e-38,
+// pairs of far-apart centres) come out as 0, an absolute error far below
+// any other in the decomposition.  The column is stored as float pairs.
+__device__ __forceinline__ void cd_eri_body_df(PairSoA pd, PairF2 pf, int64_t n,
+                                               const CdCtrl* ctrl, float2* __restrict__ ecol,
+                                               int bid, int nblk) {
+    __shared__ int near_i[kUpdThreads];
+    __shared__ int near_n;
+    const int64_t P = ctrl->P;
+    const float2 q = pf.p[P], qx = pf.Px[P], qy = pf.Py[P], qz = pf.Pz[P], kq = pf.Kp[P];
+    const float2 pi3kq = df_mul(make_float2(kPi3Hi, kPi3Lo), kq);
+    for (int64_t I0 = (int64_t)bid * kUpdThreads; I0 < n; I0 += (int64_t)nblk * kUpdThreads) {
+        if (threadIdx.x == 0) near_n = 0;
+        __syncthreads();
+        const int64_t I = I0 + threadIdx.x;
+        if (I < n) {
+            const float2 pI = pf.p[I];
+            const float2 dx = df_add(pf.Px[I], df_neg(qx));
+            const float2 dy = df_add(pf.Py[I], df_neg(qy));
+            const float2 dz = df_add(pf.Pz[I], df_neg(qz));
+            const float2 d2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+            const float2 x = df_mul(df_mul(pI, q), d2);
+            // T = x / (p + q) >= 36: either formula is exact to rounding at the edge
+            if (x.x >= kErfOneT * (pI.x + q.x)) {
+                ecol[I] = df_mul(df_mul(pf.Kp[I], pi3kq), df_rsqrt(x));
+            } else {
+                near_i[atomicAdd(&near_n, 1)] = threadIdx.x;
+            }
+        }
+        __syncthreads();
+        const int cnt = near_n;
+        const double qd = pd.p[P], qxd = pd.Px[P], qyd = pd.Py[P], qzd = pd.Pz[P], kqd = pd.Kp[P];
+        for (int j = threadIdx.x; j < cnt; j += kUpdThreads) {
+            const int64_t J = I0 + near_i[j];
+            double x, sm;
+            eri_xs(pd.p[J], pd.Px[J], pd.Py[J], pd.Pz[J], qd, qxd, qyd, qzd, x, sm);
+            ecol[J] = to_f2(eri_is_far(x, sm) ? eri_far(pd.Kp[J] * kqd, x)
+                                              : eri_near(pd.Kp[J] * kqd, x, sm));
+        }
+        __syncthreads();   // near_n is reset by the next pass
+    }
 }
 
 // Integral column (rho_I|rho_P) of step k into ecol (grid-stride over the
@@ -390,6 +519,91 @@ __device__ __forceinline__ void cd_dot_body(int64_t n, int32_t k, double* __rest
     }
 }
 
+// Speculative projections (float-pair mode).  At the first step k0 of a
+// batch one pass over L[0:k0] forms, for the batch's kSpec candidate pivots
+// S_s (S_0 is the step's own pivot),
+//   G_s[I] = sum_{K<k0} L^K_I L^K_{S_s}      (float pairs, [kSpec][npair]).
+// A later step k of the batch whose pivot is S_s takes its projection as
+// G_s[I] + sum_{k0<=K<k} L^K_I L^K_{S_s} and streams nothing; a pivot outside
+// the set, or a full batch, starts the next batch.  The sums are the same as
+// the plain left-looking ones, grouped differently.  Tile layout as
+// cd_dot_body, with kSpec accumulators per pair instead of four partial sums.
+static_assert(kSpec * kUpdPairs <= kUpdThreads, "one (candidate, pair) output per thread");
+__device__ __forceinline__ void cd_spec_dot_body(int64_t n, int32_t k,
+                                                 const double* __restrict__ L,
+                                                 float2* __restrict__ G, const CdCtrl* ctrl,
+                                                 int tile) {
+    __shared__ float2 lp[kSpec][kSpecChunk];   // pivot columns; then the warp partials
+    __shared__ long long S[kSpec];
+    if (threadIdx.x < kSpec) S[threadIdx.x] = ctrl->S[threadIdx.x];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t base = (int64_t)tile * kUpdPairs;
+    int64_t Ic[2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int64_t I = base + lane + 32 * r;
+        Ic[r] = I < n ? I : 0;   // dead lanes read pair 0
+    }
+    float2 acc[2][kSpec];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < kSpec; ++c) acc[r][c] = make_float2(0.f, 0.f);
+    const float2* Lf = reinterpret_cast<const float2*>(L);
+    constexpr int SW = kUpdWarps;
+    for (int K0 = 0; K0 < k; K0 += kSpecChunk) {
+        const int kc = min(kSpecChunk, k - K0);
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < kSpec * kc; idx += blockDim.x) {
+            const int c = idx / kc, j = idx - c * kc;
+            lp[c][j] = S[c] >= 0 ? Lf[(int64_t)(K0 + j) * n + S[c]] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        const float2* src = Lf + (int64_t)K0 * n;
+        int j = w;
+        for (; j + (kSpecRows - 1) * SW < kc; j += kSpecRows * SW) {
+            float2 v[kSpecRows][2];
+#pragma unroll
+            for (int u = 0; u < kSpecRows; ++u)
+#pragma unroll
+                for (int r = 0; r < 2; ++r) v[u][r] = src[(int64_t)(j + u * SW) * n + Ic[r]];
+#pragma unroll
+            for (int u = 0; u < kSpecRows; ++u)
+#pragma unroll
+                for (int c = 0; c < kSpec; ++c) {
+                    const float2 lu = lp[c][j + u * SW];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) df_fma(acc[r][c], v[u][r], lu);
+                }
+        }
+        for (; j < kc; j += SW) {
+            float2 v[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) v[r] = src[(int64_t)j * n + Ic[r]];
+#pragma unroll
+            for (int c = 0; c < kSpec; ++c)
+#pragma unroll
+                for (int r = 0; r < 2; ++r) df_fma(acc[r][c], v[r], lp[c][j]);
+        }
+    }
+    __syncthreads();
+    float2(*red)[kSpec][kUpdPairs] = reinterpret_cast<float2(*)[kSpec][kUpdPairs]>(&lp[0][0]);
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < kSpec; ++c) red[w][c][lane + 32 * r] = acc[r][c];
+    __syncthreads();
+    const int c = threadIdx.x / kUpdPairs, pp = threadIdx.x - c * kUpdPairs;
+    const int64_t I = base + pp;
+    if (c < kSpec && I < n) {
+        float2 sum = red[0][c][pp];
+#pragma unroll
+        for (int v = 1; v < kUpdWarps; ++v) sum = df_add(sum, red[v][c][pp]);
+        G[(int64_t)c * n + I] = sum;
+    }
+    __syncthreads();   // red aliases lp, which the next tile restages
+}
+
 // Order-preserving map of binary64 values to int64 (its own inverse), so the
 // residual extrema reduce on the integer units instead of the narrow FP64 pipe.
 __device__ __forceinline__ long long key_of(double d) {
@@ -443,50 +657,92 @@ __device__ long long block_min_ll(long long v) {
 // passes without any entry passing, possible only when the band reaches below
 // delta_eff, moves the search to the next such block).  DF: proj and L^k are
 // (hi, lo) float pairs.
-template <bool DF>
+template <bool DF, bool SPEC>
 __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_rank,
                                              double* __restrict__ L, double* __restrict__ D,
                                              const uint8_t* __restrict__ cand,
                                              const double* __restrict__ ecol,
+                                             const float2* __restrict__ Gp,
                                              long long* __restrict__ blk_a,
                                              long long* __restrict__ blk_b,
+                                             long long* __restrict__ blk_i,
                                              int32_t* __restrict__ piv, CdCtrl* ctrl, int bid,
                                              int nblk) {
+    static_assert(!SPEC || DF, "speculative projections are a float-pair mode");
     const int64_t P = ctrl->P;
     const double rDP = ctrl->rDP;
+    const float2 rDPf = ctrl->rDPf;
     long long mx = -1, mn = LLONG_MAX;   // bits of max(D,0) over candidates (-1: none), key of min D
     const int64_t base = (int64_t)bid * kStepChunk;
+    // SPEC: projection = G_slot + the vectors made since the batch began
+    int32_t k0 = 0, extra = 0;
+    const float2* Gs = Gp;
+    float2 lpP[kSpec - 1];
+    if constexpr (SPEC) {
+        k0 = ctrl->k0;
+        extra = k - k0;
+        Gs = Gp + (int64_t)ctrl->slot * n;
+        const float2* Lf = reinterpret_cast<const float2*>(L);
+#pragma unroll
+        for (int i = 0; i < kSpec - 1; ++i)
+            lpP[i] = i < extra ? Lf[(int64_t)(k0 + i) * n + P] : make_float2(0.f, 0.f);
+    }
+    long long mx_i = LLONG_MAX;   // SPEC: lowest index holding the block's candidate maximum
 #pragma unroll
     for (int r = 0; r < kStepPer; ++r) {
         const int64_t I = base + r * kUpdThreads + threadIdx.x;
         if (I < n) {
             double* slot = L + (int64_t)k * n + I;
-            double proj = 0.0;
-            if (k > 0) {
-                if constexpr (DF) {
-                    const float2 f = *reinterpret_cast<const float2*>(slot);
-                    proj = (double)f.x + (double)f.y;
-                } else {
-                    proj = *slot;
-                }
-            }
-            const double l = (ecol[I] - proj) * rDP;
-            if constexpr (DF) {
-                const float h = (float)l;
-                *reinterpret_cast<float2*>(slot) = make_float2(h, (float)(l - (double)h));
+            double d;
+            if constexpr (SPEC) {
+                // everything but the residual in float pairs (column, projection, L^k)
+                float2 acc = Gs[I];
+                const float2* Lf = reinterpret_cast<const float2*>(L);
+#pragma unroll
+                for (int i = 0; i < kSpec - 1; ++i)
+                    if (i < extra) df_fma(acc, Lf[(int64_t)(k0 + i) * n + I], lpP[i]);
+                const float2 e = reinterpret_cast<const float2*>(ecol)[I];
+                const float2 lf = df_mul(df_add(e, df_neg(acc)), rDPf);
+                *reinterpret_cast<float2*>(slot) = lf;
+                const float2 l2 = df_mul(lf, lf);
+                d = D[I] - ((double)l2.x + (double)l2.y);
             } else {
-                *slot = l;
+                double proj = 0.0;
+                if (k > 0) {
+                    if constexpr (DF) {
+                        const float2 f = *reinterpret_cast<const float2*>(slot);
+                        proj = (double)f.x + (double)f.y;
+                    } else {
+                        proj = *slot;
+                    }
+                }
+                const double l = (ecol[I] - proj) * rDP;
+                if constexpr (DF) {
+                    const float h = (float)l;
+                    *reinterpret_cast<float2*>(slot) = make_float2(h, (float)(l - (double)h));
+                } else {
+                    *slot = l;
+                }
+                d = D[I] - l * l;
             }
-            double d = D[I] - l * l;
             if (I == P) d = 0.0;
             D[I] = d;
             const long long bits = __double_as_longlong(d);
-            if (cand[I]) mx = max(mx, bits > 0 ? bits : 0LL);
+            if (cand[I]) {
+                const long long key = bits > 0 ? bits : 0LL;
+                if (key > mx) { mx = key; mx_i = I; }   // I increases with r: lowest index kept
+            }
             mn = min(mn, key_of(d));
         }
     }
+    long long mine = mx;
     block_maxmin_ll(mx, mn);
-    if (threadIdx.x == 0) { blk_a[bid] = mx; blk_b[bid] = mn; }
+    if constexpr (SPEC) mx_i = block_min_ll(mine == mx && mx >= 0 ? mx_i : LLONG_MAX);
+    if (threadIdx.x == 0) {
+        blk_a[bid] = mx;
+        blk_b[bid] = mn;
+        if constexpr (SPEC) blk_i[bid] = mx >= 0 ? mx_i : -1;
+    }
     if (!last_block(&ctrl->counter, nblk)) return;
 
     long long A = -1, B = LLONG_MAX;
@@ -535,6 +791,46 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
         if (pick >= 0) stop = false;
         else status = CDS_ERR_NOT_PD;   // G > delta_eff but no entry passes: D is inconsistent
     }
+    // SPEC: does step k+1 continue the batch (its pivot is in the candidate
+    // set and the batch is not full), or start a new one?  A new set holds the
+    // pivot and the maxima of the blocks with the largest residuals.
+    __shared__ long long s_spec[kSpec];
+    __shared__ int s_hit;
+    if constexpr (SPEC) {
+        if (!stop) {
+            if (threadIdx.x == 0) {
+                s_hit = -1;
+                if (made - ctrl->k0 < kSpec)
+                    for (int c = 0; c < kSpec; ++c)
+                        if (ctrl->S[c] == pick) s_hit = c;
+                s_spec[0] = pick;
+            }
+            __syncthreads();
+            if (s_hit < 0) {
+                const long long de_key = __double_as_longlong(de);
+                for (int c = 1; c < kSpec; ++c) {
+                    long long best = -1, dummy = LLONG_MAX;
+                    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+                        const long long key = __ldcg(blk_a + i), idx = __ldcg(blk_i + i);
+                        bool taken = idx == pick;
+                        for (int e = 1; e < c; ++e) taken = taken || idx == s_spec[e];
+                        if (!taken && idx >= 0 && key > de_key && key > best) best = key;
+                    }
+                    block_maxmin_ll(best, dummy);
+                    long long first = LLONG_MAX;
+                    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+                        const long long key = __ldcg(blk_a + i), idx = __ldcg(blk_i + i);
+                        bool taken = idx == pick;
+                        for (int e = 1; e < c; ++e) taken = taken || idx == s_spec[e];
+                        if (!taken && idx >= 0 && best >= 0 && key == best && i < first) first = i;
+                    }
+                    first = block_min_ll(first);
+                    if (threadIdx.x == 0) s_spec[c] = first == LLONG_MAX ? -1 : __ldcg(blk_i + first);
+                    __syncthreads();
+                }
+            }
+        }
+    }
     if (threadIdx.x == 0) {
         ctrl->G = G;
         ctrl->Dmin = Dmin;
@@ -546,7 +842,25 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
             ctrl->P = pick;
             ctrl->DP = __ldcg(D + pick);
             ctrl->rDP = 1.0 / sqrt(ctrl->DP);
+            {
+                const float h = (float)ctrl->rDP;
+                ctrl->rDPf = make_float2(h, (float)(ctrl->rDP - (double)h));
+            }
             piv[made] = (int32_t)pick;
+            if constexpr (SPEC) {
+                if (s_hit >= 0) {
+                    ctrl->slot = s_hit;
+                    ctrl->pass = 0;
+                    ctrl->extra += made - ctrl->k0;
+                } else {
+                    for (int c = 0; c < kSpec; ++c) ctrl->S[c] = s_spec[c];
+                    ctrl->k0 = made;
+                    ctrl->slot = 0;
+                    ctrl->pass = 1;
+                    ctrl->passes += 1;
+                    ctrl->streamed += made;
+                }
+            }
         }
         ctrl->counter = 0;
     }
@@ -565,16 +879,32 @@ k_cd_project(PairSoA pd, int64_t n, int32_t k, double* __restrict__ L,
     else if (k > 0) cd_dot_body<DF>(n, k, L, ctrl, blockIdx.x - neri);
 }
 
+// Step k, part 1 of the speculative float-pair form, on a resident grid:
+// every block takes its share of the integral column, then, when step k
+// starts a batch, projection tiles in turn.
+__global__ void __launch_bounds__(kUpdThreads, 4)
+k_cd_project_spec(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __restrict__ L,
+                  float2* __restrict__ G, float2* __restrict__ ecol, int ntiles,
+                  const CdCtrl* ctrl) {
+    if (ctrl->done) return;
+    cd_eri_body_df(pd, pf, n, ctrl, ecol, blockIdx.x, gridDim.x);
+    if (ctrl->pass == 0) return;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) cd_spec_dot_body(n, k, L, G, ctrl, t);
+}
+
 // Step k, part 2: vector k, residuals, next pivot.
-template <bool DF>
+template <bool DF, bool SPEC>
 __global__ void __launch_bounds__(kUpdThreads)
 k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
             double* __restrict__ D, const uint8_t* __restrict__ cand,
-            const double* __restrict__ ecol, double* __restrict__ blk_a,
-            double* __restrict__ blk_b, int32_t* __restrict__ piv, CdCtrl* ctrl) {
+            const double* __restrict__ ecol, const float2* __restrict__ G,
+            double* __restrict__ blk_a, double* __restrict__ blk_b,
+            long long* __restrict__ blk_i, int32_t* __restrict__ piv, CdCtrl* ctrl) {
     if (ctrl->done) return;
-    cd_step_body<DF>(n, k, max_rank, L, D, cand, ecol, reinterpret_cast<long long*>(blk_a),
-                     reinterpret_cast<long long*>(blk_b), piv, ctrl, blockIdx.x, gridDim.x);
+    cd_step_body<DF, SPEC>(n, k, max_rank, L, D, cand, ecol, G,
+                           reinterpret_cast<long long*>(blk_a),
+                           reinterpret_cast<long long*>(blk_b), blk_i, piv, ctrl, blockIdx.x,
+                           gridDim.x);
 }
 
 // Float pairs (hi, lo) of the first count elements of L back to FP64, in place.
@@ -589,6 +919,8 @@ struct CdLayout {
     PairSoA pd;
     uint8_t* cand;
     double* ecol;     // integral column of the current step
+    float2* G;        // [kSpec][npair] candidate projections (float-pair mode)
+    PairF2 pf;        // pair data as float pairs (float-pair mode)
     double* blk_a;
     double* blk_b;
     long long* blk_i;
@@ -615,7 +947,8 @@ static int sm_count() {
 }
 static int sel_blocks(int64_t n) { return (int)std::min<int64_t>(4 * 152, (n + kCdThreads - 1) / kCdThreads); }
 
-static CdLayout cd_layout(void* ws, int32_t nbf) {
+// spec: room for the candidate projections of the float-pair mode
+static CdLayout cd_layout(void* ws, int32_t nbf, bool spec = true) {
     int64_t n = npair_of(nbf);
     int nb = part_blocks(n);
     Carver c(ws);
@@ -627,6 +960,12 @@ static CdLayout cd_layout(void* ws, int32_t nbf) {
     l.pd.Kp = c.take<double>(n);
     l.cand = c.take<uint8_t>(n);
     l.ecol = c.take<double>(n);
+    l.G = spec ? c.take<float2>((size_t)kSpec * n) : nullptr;
+    l.pf.p = spec ? c.take<float2>(n) : nullptr;
+    l.pf.Px = spec ? c.take<float2>(n) : nullptr;
+    l.pf.Py = spec ? c.take<float2>(n) : nullptr;
+    l.pf.Pz = spec ? c.take<float2>(n) : nullptr;
+    l.pf.Kp = spec ? c.take<float2>(n) : nullptr;
     l.blk_a = c.take<double>(nb);
     l.blk_b = c.take<double>(nb);
     l.blk_i = c.take<long long>(nb);
@@ -635,13 +974,37 @@ static CdLayout cd_layout(void* ws, int32_t nbf) {
     return l;
 }
 
+size_t cd_workspace_bytes_for(int32_t nbf, bool f32x2) {
+    if (nbf < 0) return 0;
+    return cd_layout(nullptr, nbf, f32x2).bytes;
+}
+
 }  // namespace cds
 
 using namespace cds;
 
-extern "C" size_t cds_cd_workspace_bytes(int32_t nbf) {
-    if (nbf < 0) return 0;
-    return cd_layout(nullptr, nbf).bytes;
+// Enough for either precision.
+extern "C" size_t cds_cd_workspace_bytes(int32_t nbf) { return cd_workspace_bytes_for(nbf, true); }
+
+extern "C" int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precision,
+                            int32_t* passes, int64_t* streamed, int64_t* extra,
+                            cudaStream_t stream) {
+    if (nbf <= 0 || !workspace || !passes || !streamed || !extra) return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return CDS_ERR_UNSUPPORTED;
+    CdLayout lay = cd_layout(const_cast<void*>(workspace), nbf, precision == CDS_PREC_F32X2);
+    CdCtrl h{};
+    CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, stream));
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (precision == CDS_PREC_F32X2) {
+        *passes = h.passes;
+        *streamed = h.streamed;
+        *extra = h.extra;
+    } else {   // the FP64 form streams L at every step
+        *passes = h.M;
+        *streamed = (int64_t)h.M * (h.M - 1) / 2;
+        *extra = 0;
+    }
+    return CDS_OK;
 }
 
 extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
@@ -657,14 +1020,19 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
     if (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC) return CDS_ERR_ARG;
     if (scheme == CDS_SCHEME_ATOMIC && !atom) return CDS_ERR_ARG;
     int64_t n = npair_of(nbf);
-    CdLayout lay = cd_layout(workspace, nbf);
+    CdLayout lay = cd_layout(workspace, nbf, df);
     if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
     int st = build_pairs(nbf, xyz, alpha, lay.pd, stream);
     if (st) return st;
+    if (df) {
+        k_pairs_to_f2<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(lay.pd, lay.pf, n);
+        CDS_LAUNCH_CHECK();
+    }
     CDS_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, sizeof(CdCtrl), stream));
     const int nsm = sm_count();
     const int nb = cd_blocks(n), ns = sel_blocks(n);
     const int ne = eri_blocks(n, nsm), np_ = ne + dot_tiles(n), nu = step_blocks(n);
+    const int nres = (int)std::min<int64_t>(4 * nsm, dot_tiles(n));   // resident grid
     k_cd_init<<<nb, kCdThreads, 0, stream>>>(lay.pd, atom, scheme, n, delta, D, lay.cand,
                                             lay.blk_a, lay.blk_b, lay.ctrl);
     CDS_LAUNCH_CHECK();
@@ -676,17 +1044,18 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
         int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
         for (int32_t k = k0; k < k1; ++k) {
             if (df) {
-                k_cd_project<true><<<np_, kUpdThreads, 0, stream>>>(lay.pd, n, k, L, lay.ecol, ne,
-                                                                    lay.ctrl);
-                k_cd_update<true><<<nu, kUpdThreads, 0, stream>>>(n, k, max_rank, L, D, lay.cand,
-                                                                  lay.ecol, lay.blk_a, lay.blk_b,
-                                                                  piv, lay.ctrl);
+                k_cd_project_spec<<<nres, kUpdThreads, 0, stream>>>(
+                    lay.pd, lay.pf, n, k, L, lay.G, reinterpret_cast<float2*>(lay.ecol),
+                    dot_tiles(n), lay.ctrl);
+                k_cd_update<true, true><<<nu, kUpdThreads, 0, stream>>>(
+                    n, k, max_rank, L, D, lay.cand, lay.ecol, lay.G, lay.blk_a, lay.blk_b,
+                    lay.blk_i, piv, lay.ctrl);
             } else {
                 k_cd_project<false><<<np_, kUpdThreads, 0, stream>>>(lay.pd, n, k, L, lay.ecol, ne,
                                                                      lay.ctrl);
-                k_cd_update<false><<<nu, kUpdThreads, 0, stream>>>(n, k, max_rank, L, D, lay.cand,
-                                                                   lay.ecol, lay.blk_a, lay.blk_b,
-                                                                   piv, lay.ctrl);
+                k_cd_update<false, false><<<nu, kUpdThreads, 0, stream>>>(
+                    n, k, max_rank, L, D, lay.cand, lay.ecol, nullptr, lay.blk_a, lay.blk_b,
+                    lay.blk_i, piv, lay.ctrl);
             }
         }
         count_launches(2ull * (unsigned long long)(k1 - k0));
@@ -775,9 +1144,10 @@ __global__ void __launch_bounds__(kUpdThreads) k_bcd_update(const CdMol* __restr
     const int c = find_mol(mols, nmol, blockIdx.x, 3);
     const CdMol& m = mols[c];
     if (k >= m.max_rank || m.ctrl->done) return;
-    cd_step_body<false>(m.n, k, m.max_rank, m.L, m.D, m.cand, m.ecol,
-                        reinterpret_cast<long long*>(m.blk_a), reinterpret_cast<long long*>(m.blk_b),
-                        m.piv, m.ctrl, blockIdx.x - m.b0_epi, m.nb_epi);
+    cd_step_body<false, false>(m.n, k, m.max_rank, m.L, m.D, m.cand, m.ecol, nullptr,
+                               reinterpret_cast<long long*>(m.blk_a),
+                               reinterpret_cast<long long*>(m.blk_b), m.blk_i, m.piv, m.ctrl,
+                               blockIdx.x - m.b0_epi, m.nb_epi);
 }
 
 struct CdBatchLayout {

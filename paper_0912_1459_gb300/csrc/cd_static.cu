@@ -57,7 +57,7 @@ extern "C" int cds_cd_decompose_static(int32_t nbf, const double* xyz, const dou
                                        int32_t* M_out, double* delta_eff_out,
                                        cudaStream_t stream) {
     if (nbf <= 0) return CDS_ERR_ARG;
-    const size_t need = cds_cd_workspace_bytes(nbf);
+    const size_t need = cds::cd_workspace_bytes_for(nbf, false);
     if (need == 0) return CDS_ERR_ARG;
     if (need > kStaticBytes) return CDS_ERR_CAPACITY;
     void* ws = nullptr;
@@ -71,7 +71,7 @@ extern "C" int cds_cd_static_max_nbf(void) {
     int32_t lo = 1, hi = 1 << 16;
     while (lo < hi) {   // largest nbf whose workspace fits the static scratch
         int32_t mid = lo + (hi - lo + 1) / 2;
-        if (cds_cd_workspace_bytes(mid) <= kStaticBytes) lo = mid; else hi = mid - 1;
+        if (cds::cd_workspace_bytes_for(mid, false) <= kStaticBytes) lo = mid; else hi = mid - 1;
     }
     return lo;
 }

@@ -116,4 +116,7 @@ __device__ __forceinline__ void unpack_pair(int64_t I, int32_t& mu, int32_t& nu)
 namespace cds {
 int build_pairs(int32_t nbf, const double* xyz, const double* alpha, PairSoA pd,
                 cudaStream_t stream);
+// Workspace of cds_cd_decompose for one precision (f32x2 needs the candidate
+// projections as well).
+size_t cd_workspace_bytes_for(int32_t nbf, bool f32x2);
 }
