@@ -121,63 +121,119 @@ __device__ __forceinline__ void store_out(float2* p, float2 v) {
     p[0] = make_float2(h, v.y - (h - v.x));
 }
 
-// C[b] = A[b] * B[b] in float-pair arithmetic; same tiling as k_dgemm.
-template <bool A_M_CONTIG, bool B_N_CONTIG, typename TOut>
-__global__ void __launch_bounds__(256)
-k_dfgemm(int m, int n, int k, PairMat A, PairMat B, OutMat<TOut> C) {
-    __shared__ float2 As[kGK][kGB + 1];
+// C[b] = A[b] * B[b] in float-pair arithmetic.  Tile: 16*RM rows starting
+// at row m_off + 16*RM*blockIdx.y, 64 columns; each of the 256 threads owns
+// RM x 4 outputs.  The next K stage is fetched into registers while the
+// current one is consumed from shared memory.  RM < 4 serves the last rows of
+// a short m (the 20 orbital rows, the tail of o) without padding to 64.
+#ifndef CDS_DFGEMM_PF
+#define CDS_DFGEMM_PF 1
+#endif
+// PF: fetch the next K stage into registers during the current one (more
+// registers: 2 instead of 3 blocks per SM for RM = 4).
+constexpr bool kDfPrefetch = CDS_DFGEMM_PF != 0;
+
+template <int RM, bool A_M_CONTIG, bool B_N_CONTIG, typename TOut>
+__global__ void __launch_bounds__(256, (kDfPrefetch && RM == 4) ? 2 : 3)
+k_dfgemm(int m, int n, int k, int m_off, PairMat A, PairMat B, OutMat<TOut> C) {
+    constexpr int BM = 16 * RM;
+    constexpr int NA = BM * kGK / 256;
+    constexpr int NB = kGB * kGK / 256;
+    __shared__ float2 As[kGK][BM + 1];
     __shared__ float2 Bs[kGK][kGB + 1];
     const int tid = threadIdx.x;
     const int tr = tid / 16, tc = tid % 16;
-    const int m0 = blockIdx.y * kGB, n0 = blockIdx.x * kGB;
+    const int m0 = m_off + blockIdx.y * BM, n0 = blockIdx.x * kGB;
     const int64_t b = blockIdx.z;
     const float2* Ab = A.p + b * A.bs;
     const float2* Bb = B.p + b * B.bs;
     const float2 zero = make_float2(0.f, 0.f);
-    float2 acc[4][4];
+    float2 acc[RM][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RM; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = zero;
-    for (int k0 = 0; k0 < k; k0 += kGK) {
+    float2 ra[NA], rb[NB];
+    auto a_pos = [&](int r, int& mm, int& kk) {
+        const int idx = tid + 256 * r;
+        if (A_M_CONTIG) { mm = idx % BM; kk = idx / BM; }
+        else { kk = idx % kGK; mm = idx / kGK; }
+    };
+    auto b_pos = [&](int r, int& nn, int& kk) {
+        const int idx = tid + 256 * r;
+        if (B_N_CONTIG) { nn = idx % kGB; kk = idx / kGB; }
+        else { kk = idx % kGK; nn = idx / kGK; }
+    };
+    auto fetch = [&](int k0) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            int idx = tid + 256 * r;
+        for (int r = 0; r < NA; ++r) {
             int mm, kk;
-            if (A_M_CONTIG) { mm = idx % kGB; kk = idx / kGB; }
-            else { kk = idx % kGK; mm = idx / kGK; }
-            int gm = m0 + mm, gk = k0 + kk;
-            As[kk][mm] = (gm < m && gk < k) ? Ab[gm * A.rs + gk * A.cs] : zero;
-            int nn;
-            if (B_N_CONTIG) { nn = idx % kGB; kk = idx / kGB; }
-            else { kk = idx % kGK; nn = idx / kGK; }
-            int gn = n0 + nn;
-            gk = k0 + kk;
-            Bs[kk][nn] = (gn < n && gk < k) ? Bb[gk * B.rs + gn * B.cs] : zero;
+            a_pos(r, mm, kk);
+            const int gm = m0 + mm, gk = k0 + kk;
+            ra[r] = (gm < m && gk < k) ? Ab[gm * A.rs + gk * A.cs] : zero;
         }
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            int nn, kk;
+            b_pos(r, nn, kk);
+            const int gn = n0 + nn, gk = k0 + kk;
+            rb[r] = (gn < n && gk < k) ? Bb[gk * B.rs + gn * B.cs] : zero;
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int r = 0; r < NA; ++r) {
+            int mm, kk;
+            a_pos(r, mm, kk);
+            As[kk][mm] = ra[r];
+        }
+#pragma unroll
+        for (int r = 0; r < NB; ++r) {
+            int nn, kk;
+            b_pos(r, nn, kk);
+            Bs[kk][nn] = rb[r];
+        }
+    };
+    if (kDfPrefetch) {
+        fetch(0);
+        stash();
         __syncthreads();
+    }
+    for (int k0 = 0; k0 < k; k0 += kGK) {
+        const bool more = k0 + kGK < k;
+        if (!kDfPrefetch) {
+            fetch(k0);
+            stash();
+            __syncthreads();
+        } else if (more) {
+            fetch(k0 + kGK);
+        }
 #pragma unroll 4
         for (int kk = 0; kk < kGK; ++kk) {
-            float2 a[4], bb[4];
+            float2 a[RM], bb[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][tr + 16 * i];
+            for (int i = 0; i < RM; ++i) a[i] = As[kk][tr + 16 * i];
 #pragma unroll
             for (int j = 0; j < 4; ++j) bb[j] = Bs[kk][tc + 16 * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < RM; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) df_fma(acc[i][j], a[i], bb[j]);
         }
         __syncthreads();
+        if (kDfPrefetch && more) {
+            stash();
+            __syncthreads();
+        }
     }
     TOut* Cb = C.p + b * C.bs;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        int gm = m0 + tr + 16 * i;
+    for (int i = 0; i < RM; ++i) {
+        const int gm = m0 + tr + 16 * i;
         if (gm >= m) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int gn = n0 + tc + 16 * j;
+            const int gn = n0 + tc + 16 * j;
             if (gn < n) store_out(Cb + gm * C.rs + gn * C.cs, acc[i][j]);
         }
     }
@@ -209,6 +265,19 @@ __global__ void k_pair_cols(const double* __restrict__ C, int32_t N, int32_t nmo
     int mu = e / ncol, j = e % ncol;
     int p = orb ? orb[j] : j;
     Cq[e] = (p >= 0 && p < nmo) ? to_pair(C[(int64_t)mu * nmo + p])
+                                : make_float2(__int_as_float(0x7fc00000), 0.f);
+}
+
+// Cj[mu][j] = pair(C[mu][j]) for j < nocc, pair(C[mu][orb[j - nocc]]) after.
+__global__ void k_pair_cols_joint(const double* __restrict__ C, int32_t N, int32_t nmo,
+                                  int32_t nocc, const int32_t* __restrict__ orb, int32_t np,
+                                  float2* __restrict__ Cj) {
+    const int nc = nocc + np;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N * nc) return;
+    int mu = e / nc, j = e % nc;
+    int p = j < nocc ? j : orb[j - nocc];
+    Cj[e] = (p >= 0 && p < nmo) ? to_pair(C[(int64_t)mu * nmo + p])
                                 : make_float2(__int_as_float(0x7fc00000), 0.f);
 }
 
@@ -288,21 +357,36 @@ __global__ void k_scatter_cols(const double* __restrict__ dCp, int32_t N, int32_
     for (int t = 0; t < np; ++t) dC[(int64_t)e * nmo + orb[t]] += dCp[(int64_t)e * np + t];
 }
 
+// 64-row tiles for the bulk of m, then one narrower tile for the rest.
 template <bool AM, bool BN, typename TOut>
 static int launch_dfgemm(int m, int n, int k, int batch, PairMat A, PairMat B, OutMat<TOut> C,
                          cudaStream_t s) {
     if (m <= 0 || n <= 0 || batch <= 0) return CDS_OK;
-    dim3 grid((n + kGB - 1) / kGB, (m + kGB - 1) / kGB, batch);
-    k_dfgemm<AM, BN, TOut><<<grid, 256, 0, s>>>(m, n, k, A, B, C);
-    CDS_LAUNCH_CHECK();
+    const unsigned gx = (unsigned)((n + kGB - 1) / kGB);
+    const int full = m / 64 * 64, rest = m - full;
+    if (full > 0) {
+        k_dfgemm<4, AM, BN, TOut><<<dim3(gx, full / 64, batch), 256, 0, s>>>(m, n, k, 0, A, B, C);
+        CDS_LAUNCH_CHECK();
+    }
+    if (rest > 32) {
+        k_dfgemm<4, AM, BN, TOut><<<dim3(gx, 1, batch), 256, 0, s>>>(m, n, k, full, A, B, C);
+        CDS_LAUNCH_CHECK();
+    } else if (rest > 16) {
+        k_dfgemm<2, AM, BN, TOut><<<dim3(gx, 1, batch), 256, 0, s>>>(m, n, k, full, A, B, C);
+        CDS_LAUNCH_CHECK();
+    } else if (rest > 0) {
+        k_dfgemm<1, AM, BN, TOut><<<dim3(gx, 1, batch), 256, 0, s>>>(m, n, k, full, A, B, C);
+        CDS_LAUNCH_CHECK();
+    }
     return CDS_OK;
 }
 
 struct AoLayout {
     double* U;    // [kb][N][N]             (float pairs in the F32X2 form)
-    double* T;    // [kb][max(o, np)][N]
+    double* T;    // [kb][o + np][N]
     double* Cp;   // [N][np]
     double* Cq;   // [N][nmo] float pairs of C (F32X2 form)
+    double* Cj;   // [N][o + np] float pairs of C_occ and C_P (F32X2 form)
     size_t bytes;
 };
 
@@ -310,53 +394,55 @@ static AoLayout ao_layout(void* ws, int32_t nbf, int32_t nmo, int32_t nocc, int3
     Carver c(ws);
     AoLayout l;
     l.U = c.take<double>((size_t)kAoBatch * nbf * nbf);
-    l.T = c.take<double>((size_t)kAoBatch * std::max(nocc, np) * nbf);
+    l.T = c.take<double>((size_t)kAoBatch * std::max(nocc + np, 1) * nbf);
     l.Cp = c.take<double>((size_t)nbf * std::max(np, 1));
     l.Cq = c.take<double>((size_t)nbf * nmo);
+    l.Cj = c.take<double>((size_t)nbf * std::max(nocc + np, 1));
     l.bytes = c.off;
     return l;
 }
 
-// The float-pair transform: same blocks and layouts as the FP64 one.
+// The float-pair transform.  Per batch of vectors one GEMM forms the
+// occupied and the requested orbital rows together, T = [C_occ | C_P]^T A^K
+// ((o + np) x N), then Lov = T_occ C_vir and Lp = T_P C.
 static int cd_to_mo_f32x2(int32_t N, int32_t nmo, int32_t nocc, int32_t M, const double* L,
                           const double* C, const int32_t* orb, int32_t np, double* Lov,
                           double* Lp, const AoLayout& lay, cudaStream_t stream) {
     const int64_t npair = npair_of(N);
-    const int32_t nv = nmo - nocc;
+    const int32_t nv = nmo - nocc, nc = nocc + np;
     float2* Cq = reinterpret_cast<float2*>(lay.Cq);
-    float2* Cp = reinterpret_cast<float2*>(lay.Cp);
+    float2* Cj = reinterpret_cast<float2*>(lay.Cj);
     float2* U = reinterpret_cast<float2*>(lay.U);
     float2* T = reinterpret_cast<float2*>(lay.T);
+    const bool ov = nocc > 0 && nv > 0;
+    if (!ov && np == 0) return CDS_OK;
     k_pair_cols<<<(N * nmo + 255) / 256, 256, 0, stream>>>(C, N, nmo, nullptr, nmo, Cq);
     CDS_LAUNCH_CHECK();
-    if (np > 0) {
-        k_pair_cols<<<(N * np + 255) / 256, 256, 0, stream>>>(C, N, nmo, orb, np, Cp);
-        CDS_LAUNCH_CHECK();
-    }
+    k_pair_cols_joint<<<(N * nc + 255) / 256, 256, 0, stream>>>(C, N, nmo, nocc, orb, np, Cj);
+    CDS_LAUNCH_CHECK();
     for (int32_t K0 = 0; K0 < M; K0 += kAoBatch) {
         int32_t kb = std::min(kAoBatch, M - K0);
         int64_t tot = (int64_t)kb * N * N;
         k_unpack_pairs<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(L, npair, K0, kb, N, U);
         CDS_LAUNCH_CHECK();
         PairMat Um{U, N, 1, (int64_t)N * N};
-        if (nocc > 0 && nv > 0) {
-            int st = launch_dfgemm<true, true, float2>(nocc, N, N, kb, PairMat{Cq, 1, nmo, 0}, Um,
-                                                       OutMat<float2>{T, N, 1, (int64_t)nocc * N},
-                                                       stream);
-            if (st) return st;
+        // rows of the occupied block only when Lov is wanted
+        const int32_t r0 = ov ? 0 : nocc, rows = nc - r0;
+        int st = launch_dfgemm<true, true, float2>(rows, N, N, kb, PairMat{Cj + r0, 1, nc, 0}, Um,
+                                                   OutMat<float2>{T + (int64_t)r0 * N, N, 1,
+                                                                  (int64_t)nc * N},
+                                                   stream);
+        if (st) return st;
+        if (ov) {
             st = launch_dfgemm<false, true, double>(
-                nocc, nv, N, kb, PairMat{T, N, 1, (int64_t)nocc * N}, PairMat{Cq + nocc, nmo, 1, 0},
+                nocc, nv, N, kb, PairMat{T, N, 1, (int64_t)nc * N}, PairMat{Cq + nocc, nmo, 1, 0},
                 OutMat<double>{Lov + K0, (int64_t)nv * M, M, 1}, stream);
             if (st) return st;
         }
         if (np > 0) {
-            int st = launch_dfgemm<true, true, float2>(np, N, N, kb, PairMat{Cp, 1, np, 0}, Um,
-                                                       OutMat<float2>{T, N, 1, (int64_t)np * N},
-                                                       stream);
-            if (st) return st;
             st = launch_dfgemm<false, true, double>(
-                np, nmo, N, kb, PairMat{T, N, 1, (int64_t)np * N}, PairMat{Cq, nmo, 1, 0},
-                OutMat<double>{Lp + K0, (int64_t)nmo * M, M, 1}, stream);
+                np, nmo, N, kb, PairMat{T + (int64_t)nocc * N, N, 1, (int64_t)nc * N},
+                PairMat{Cq, nmo, 1, 0}, OutMat<double>{Lp + K0, (int64_t)nmo * M, M, 1}, stream);
             if (st) return st;
         }
     }

@@ -42,8 +42,13 @@ def main(mode: str) -> None:
     if mode in ("transform", "transform64"):
         L = torch.randn((128, G.npair(m.nbf)), dtype=torch.float64, device=dev, generator=g) * 1e-2
         prec = "fp64" if mode == "transform64" else "f32x2"
-        for _ in range(2):
+        for rep in range(2):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
             G.cds_cd_to_mo(L, d(m.C), m.nocc, d(m.orbitals), precision=prec)
+            b.record()
+            torch.cuda.synchronize()
+            print(f"transform of {L.shape[0]} vectors: {a.elapsed_time(b):.2f} ms")
     elif mode in ("sigma1", "sigma64"):
         nE = 64 if mode == "sigma64" else 1
         Lov = torch.randn((m.nocc, m.nbf - m.nocc, 896), dtype=torch.float64, device=dev,
