@@ -326,13 +326,15 @@ __global__ void k_pairs_to_f2(PairSoA pd, PairF2 pf, int64_t n) {
     pf.Kp[I] = to_f2(pd.Kp[I]);
 }
 
+constexpr float kFarT = 36.f;   // erf(sqrt T) rounds to 1 in binary64 above
+constexpr float kMidT = 16.f;   // erfc(sqrt T) small enough for FP32 above
 constexpr float kPi3Hi = (float)kPi3;
 constexpr float kPi3Lo = (float)(kPi3 - (double)kPi3Hi);
 
-// Integral column of the float-pair decomposition: the far pairs (T >= 36,
-// the point-charge form pi^3 (K_I/p)(K_P/q) / sqrt(p q |P-Q|^2)) in float-pair
-// arithmetic from the float-pair pair data, the others gathered and evaluated
-// in FP64 as in cd_eri_body.  Values below the FP32 range (|K/p| < 1e-38,
+// Integral column of the float-pair decomposition: pairs with T >= 16 in
+// float-pair arithmetic from the float-pair pair data (the point-charge form
+// pi^3 (K_I/p)(K_P/q) / sqrt(p q |P-Q|^2), times 1 - erfc(sqrt T) below
+// T = 36), the others gathered and evaluated in FP64 as in cd_eri_body.  Values below the FP32 range (|K/p| < 1e-38,
 // pairs of far-apart centres) come out as 0, an absolute error far below
 // any other in the decomposition.  The column is stored as float pairs.
 __device__ __forceinline__ void cd_eri_body_df(PairSoA pd, PairF2 pf, int64_t n,
@@ -354,9 +356,14 @@ __device__ __forceinline__ void cd_eri_body_df(PairSoA pd, PairF2 pf, int64_t n,
             const float2 dz = df_add(pf.Pz[I], df_neg(qz));
             const float2 d2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
             const float2 x = df_mul(df_mul(pI, q), d2);
-            // T = x / (p + q) >= 36: either formula is exact to rounding at the edge
-            if (x.x >= kErfOneT * (pI.x + q.x)) {
-                ecol[I] = df_mul(df_mul(pf.Kp[I], pi3kq), df_rsqrt(x));
+            const float sf = pI.x + q.x;
+            if (x.x >= kMidT * sf) {
+                // T >= 16: F0 = (1/2) sqrt(pi/T) (1 - erfc(sqrt T)), and erfc(sqrt T)
+                // <= 1.6e-8 is needed only to FP32 precision (its error then stays
+                // below 1e-14 of F0); above T = 36 it is below half an ulp
+                float2 e = df_mul(df_mul(pf.Kp[I], pi3kq), df_rsqrt(x));
+                if (x.x < kFarT * sf) e = df_mul(e, make_float2(1.f, -erfcf(sqrtf(x.x / sf))));
+                ecol[I] = e;
             } else {
                 near_i[atomicAdd(&near_n, 1)] = threadIdx.x;
             }

@@ -431,6 +431,12 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
                 const View v = CDS_VIEW(item);
                 if (!v.act) continue;
                 const bool diag = v.A == v.B;
+                // columns of both tiles come from block B: a ragged last block
+                // runs with N = its valid rows rounded up to 16 (M = 128 takes
+                // N = 16..256 in steps of 16); the epilogue reads only valid columns
+                const int nyB = min(TB, v.tm.nx - v.B * TB);
+                const uint32_t NB = (uint32_t)((nyB + 15) & ~15);
+                const uint32_t IDn = (ID & ~(0x3Fu << 17)) | ((NB >> 3) << 17);
                 if (!mbar_wait(&tempty[acc], aphase ^ 1u, verr)) break;
                 fence_after();
                 const uint32_t d1 = tmem + (uint32_t)acc * 256u, d2 = d1 + 128u;
@@ -449,12 +455,12 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
                     for (int kk = 0; kk < KB / 16; ++kk) {
                         const uint32_t off = kk * 32;
                         const uint32_t first = (kb | kk) ? 1u : 0u;
-                        mma_f16(d1, sdesc(a1h + off), sdesc(b1h + off), ID, first);
-                        mma_f16(d1x, sdesc(a1h + off), sdesc(b1l + off), ID, SEP ? first : 1u);
-                        mma_f16(d1x, sdesc(a1l + off), sdesc(b1h + off), ID, 1u);
-                        mma_f16(d2, sdesc(a2h + off), sdesc(b2h + off), ID, first);
-                        mma_f16(d2x, sdesc(a2h + off), sdesc(b2l + off), ID, SEP ? first : 1u);
-                        mma_f16(d2x, sdesc(a2l + off), sdesc(b2h + off), ID, 1u);
+                        mma_f16(d1, sdesc(a1h + off), sdesc(b1h + off), IDn, first);
+                        mma_f16(d1x, sdesc(a1h + off), sdesc(b1l + off), IDn, SEP ? first : 1u);
+                        mma_f16(d1x, sdesc(a1l + off), sdesc(b1h + off), IDn, 1u);
+                        mma_f16(d2, sdesc(a2h + off), sdesc(b2h + off), IDn, first);
+                        mma_f16(d2x, sdesc(a2h + off), sdesc(b2l + off), IDn, SEP ? first : 1u);
+                        mma_f16(d2x, sdesc(a2l + off), sdesc(b2h + off), IDn, 1u);
                     }
                     mma_commit(&empty[stage]);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }

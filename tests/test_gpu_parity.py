@@ -242,3 +242,23 @@ def test_tiny_case_against_stored_oracle_values():
         assert int(it[t]) == r["iters"] and int(st[t]) == r["status"]
         assert float(w[t]) == pytest.approx(r["omega"], abs=1e-9)
         assert float(P[t]) == pytest.approx(r["pole"], rel=1e-8)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "f32x2"])
+def test_cd_stats_counters(precision):
+    """cds_cd_stats: FP64 streams at every step; the float-pair form streams at
+    the first step of each batch of at most four, and a continued step adds
+    between one and three vectors."""
+    m = O.molecule("c1")
+    xyz, a, at = basis_dev(m)
+    ws = torch.empty(G.load().cds_cd_workspace_bytes(m.nbf), dtype=torch.uint8, device=DEV)
+    L, piv, D, de = G.cds_cd_decompose(xyz, a, at, 1e-5, "full", workspace=ws, precision=precision)
+    M = L.shape[0]
+    st = G.cdsigma.cds_cd_stats(m.nbf, ws, precision)
+    if precision == "fp64":
+        assert st == {"passes": M, "streamed": M * (M - 1) // 2, "extra": 0}
+    else:
+        assert (M + 3) // 4 <= st["passes"] <= M
+        assert 0 < st["streamed"] < M * (M - 1) // 2
+        cont = M - st["passes"]
+        assert cont <= st["extra"] <= 3 * cont
