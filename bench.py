@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--no-fp64-arm", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-mp2", action="store_true")
+    p.add_argument("--newton", default="cached", choices=["cached", "recompute"],
+                   help="Newton from the numerators the Sigma-grid stage keeps, or recomputing "
+                        "the integrals every iteration (split precisions)")
     return p.parse_args()
 
 
@@ -241,6 +244,9 @@ def run_ours(args, dist: Dist):
     npr = G.npair(m.nbf)
     Lbuf = torch.empty((max_rank, npr), dtype=torch.float64, device=device)
     cd_ws = torch.empty(lib.cds_cd_workspace_bytes(m.nbf), dtype=torch.uint8, device=device)
+    cached = args.newton == "cached" and prec != "fp64"
+    cache = (torch.empty(lib.cds_sigma2_cache_bytes(m.nbf, m.nocc, n_orb), dtype=torch.uint8,
+                         device=device) if cached else None)
 
     def step(xyz, al, at, C, eps, orbs, E, ws=None):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -251,10 +257,18 @@ def run_ours(args, dist: Dist):
         Lov, Lp = G.cds_cd_to_mo(L, C, m.nocc, orbs, workspace=ws and ws.get("tr"),
                                  precision=tr_prec)
         ev[2].record()
-        sig, dsig = G.cds_sigma2_diag(Lov, Lp, eps, m.nocc, E, prec, workspace=ws and ws.get("sg"))
-        ev[3].record()
-        w, P, it, st = G.cds_qp_solve(Lov, Lp, orbs, eps, m.nocc, conv=1e-5, max_iter=50,
-                                      precision=prec, workspace=ws and ws.get("qp"))
+        if cached:
+            sig, dsig, _ = G.cds_sigma2_diag_cache(Lov, Lp, eps, m.nocc, E, prec, cache=cache,
+                                                   workspace=ws and ws.get("sg"))
+            ev[3].record()
+            w, P, it, st = G.cds_qp_solve_cached(cache, orbs, eps, m.nbf, m.nocc, conv=1e-5,
+                                                 max_iter=50, workspace=ws and ws.get("qpc"))
+        else:
+            sig, dsig = G.cds_sigma2_diag(Lov, Lp, eps, m.nocc, E, prec,
+                                          workspace=ws and ws.get("sg"))
+            ev[3].record()
+            w, P, it, st = G.cds_qp_solve(Lov, Lp, orbs, eps, m.nocc, conv=1e-5, max_iter=50,
+                                          precision=prec, workspace=ws and ws.get("qp"))
         ev[4].record()
         return (L, Lov, Lp, sig, dsig, w, P, it, st), ev
 
@@ -270,6 +284,8 @@ def run_ours(args, dist: Dist):
         "qp": torch.empty(lib.cds_qp_workspace_bytes(m.nbf, m.nocc, M, n_orb,
                                                       G.cdsigma.PRECISIONS[prec]),
                           dtype=torch.uint8, device=device),
+        "qpc": torch.empty(max(lib.cds_qp_cached_workspace_bytes(m.nbf, m.nocc, n_orb), 1),
+                           dtype=torch.uint8, device=device),
     }
     for _ in range(max(args.warmup - 1, 0)):
         out, _ = step(xyz, al, at, C, eps, orbs, E, ws)
@@ -370,10 +386,17 @@ def run_ours(args, dist: Dist):
                           "achieved": sig_flops_grid / (med["sigma_grid"] / 1e3) / 1e12,
                           "note": "64 energies: the fused denominator epilogue (fp32/MUFU) bounds it"}
     sig_flops_qp = split * fm["sigma_pass"] * sig_passes_qp
-    roof["qp"] = {"bound": "tensor" if prec != "fp64" else "alu", "unit": "TFLOP/s",
-                  "peak": pk["bf16_tflops"] if prec != "fp64" else pk["fp64_tflops"],
-                  "achieved": sig_flops_qp / (med["qp"] / 1e3) / 1e12,
-                  "note": f"{sig_passes_qp} Sigma passes (nE=1); {split} split products per MAC"}
+    if cached:
+        per_orb = lib.cds_sigma2_cache_bytes(m.nbf, m.nocc, n_orb) / n_orb
+        roof["qp"] = {"bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
+                      "achieved": sig_passes_qp * per_orb / (med["qp"] / 1e3) / 1e9,
+                      "note": f"{sig_passes_qp} Sigma passes (nE=1) from cached numerators, "
+                              f"{per_orb / 1e6:.0f} MB streamed per orbital pass"}
+    else:
+        roof["qp"] = {"bound": "tensor" if prec != "fp64" else "alu", "unit": "TFLOP/s",
+                      "peak": pk["bf16_tflops"] if prec != "fp64" else pk["fp64_tflops"],
+                      "achieved": sig_flops_qp / (med["qp"] / 1e3) / 1e12,
+                      "note": f"{sig_passes_qp} Sigma passes (nE=1); {split} split products per MAC"}
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
@@ -431,6 +454,7 @@ def run_ours(args, dist: Dist):
                    "delta": args.delta, "scheme": args.scheme, "cholesky_rank": M,
                    "orbitals": n_orb, "energies_per_orbital": m.nE, "newton_conv_Ha": 1e-5,
                    "precision": prec, "transform_precision": tr_prec,
+                   "newton": "cached numerators" if cached else "recomputed integrals",
                    "parallelism": f"replicas{dist.world}",
                    "l2": "inputs larger than L2 (L is %.1f GB, Lov %.0f MB)" % (M * npr * 8 / 1e9, Lov.numel() * 8 / 1e6)},
         "stages_ms": med,

@@ -236,6 +236,40 @@ int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
                  size_t workspace_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Cached numerators ("pole-cached" Newton).  In Eq. SE every element's
+ * numerator (2 X_xy - X_yx) X_xy is independent of the energy; only the
+ * denominator E + e_s - e_x - e_y moves.  cds_sigma2_diag_cache runs
+ * cds_sigma2_diag (split precisions) and also stores the numerators of every
+ * work item, as computed by the tensor-core epilogue, in a caller buffer of
+ * cds_sigma2_cache_bytes (~0.38 GB per orbital at C60 shapes);
+ * cds_qp_solve_cached then runs the Newton iteration of cds_qp_solve with
+ * each Sigma(w) evaluated from that buffer, streaming it once per pass
+ * instead of recomputing the integrals.  Per element the arithmetic is the
+ * epilogue's; only the order of the sums differs.
+ * ---------------------------------------------------------------------- */
+
+size_t cds_sigma2_cache_bytes(int32_t nmo, int32_t nocc, int32_t np);
+
+/* As cds_sigma2_diag (precision CDS_PREC_BF16X3 or CDS_PREC_FP16X3), plus
+ * cache (device, caller-owned, >= cds_sigma2_cache_bytes): the numerators of
+ * the orbitals Lp[0..np).  Asynchronous. */
+int cds_sigma2_diag_cache(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                          const double* Lp, int32_t np, const double* eps, const double* E,
+                          int32_t nE, int32_t precision, double* sigma, double* dsigma,
+                          void* cache, size_t cache_bytes, void* workspace,
+                          size_t workspace_bytes, cudaStream_t stream);
+
+size_t cds_qp_cached_workspace_bytes(int32_t nmo, int32_t nocc, int32_t np);
+
+/* As cds_qp_solve, with Sigma from a cache that cds_sigma2_diag_cache filled
+ * for the same orbitals (orb[t] = the orbital of Lp[t]).  Blocking. */
+int cds_qp_solve_cached(int32_t nmo, int32_t nocc, int32_t np, const int32_t* orb,
+                        const double* eps, double conv, int32_t max_iter, const void* cache,
+                        size_t cache_bytes, double* omega, double* pole, int32_t* iters,
+                        int32_t* status, void* workspace, size_t workspace_bytes,
+                        cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * MP2 correlation energy (paper Eq. MP2), the ground-state companion of
  * Eq. SE on the same factors:
  *   E = sum_{i,j,a,b} (2 (ai|bj) - (aj|bi)) (ai|bj) / (e_i + e_j - e_a - e_b),

@@ -56,6 +56,12 @@ _SIGNATURES = {
                                     _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "cds_cd_stats": (ctypes.c_int, [_i32, _vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64), _vp]),
+    "cds_sigma2_cache_bytes": (_sz, [_i32, _i32, _i32]),
+    "cds_sigma2_diag_cache": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _i32,
+                                             _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
+    "cds_qp_cached_workspace_bytes": (_sz, [_i32, _i32, _i32]),
+    "cds_qp_solve_cached": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _f64, _i32, _vp, _sz, _vp, _vp,
+                                           _vp, _vp, _vp, _sz, _vp]),
     "cds_mp2_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32]),
     "cds_mp2_energy": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
 }
@@ -342,6 +348,64 @@ def cds_qp_solve(Lov: torch.Tensor, Lp: torch.Tensor, orbitals: torch.Tensor, ep
     if st == 5 and not raise_on_nonconvergence:
         st = CDS_OK
     _check(st, "cds_qp_solve")
+    return omega, pole, iters, status
+
+
+def cds_sigma2_diag_cache(Lov: torch.Tensor, Lp: torch.Tensor, eps: torch.Tensor, nocc: int,
+                          E: torch.Tensor, precision: str = "bf16x3",
+                          cache: Optional[torch.Tensor] = None,
+                          workspace: Optional[torch.Tensor] = None):
+    """cds_sigma2_diag that also keeps every work item's numerators.
+
+    Returns (sigma, dsigma, cache); pass the cache to cds_qp_solve_cached."""
+    lib = load()
+    Lov = _dev(Lov, torch.float64, "Lov")
+    Lp = _dev(Lp, torch.float64, "Lp")
+    eps = _dev(eps, torch.float64, "eps")
+    E = _dev(E, torch.float64, "E")
+    dev = Lp.device
+    np_, nmo, M = Lp.shape
+    nE = E.shape[1]
+    prec = PRECISIONS[precision]
+    sigma = torch.empty((np_, nE), dtype=torch.float64, device=dev)
+    dsigma = torch.empty((np_, nE), dtype=torch.float64, device=dev)
+    cb = lib.cds_sigma2_cache_bytes(nmo, nocc, np_)
+    if cache is None or cache.numel() < cb:
+        cache = torch.empty(max(cb, 1), dtype=torch.uint8, device=dev)
+    need = lib.cds_sigma2_workspace_bytes(nmo, nocc, M, np_, nE, prec)
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    st = lib.cds_sigma2_diag_cache(nmo, nocc, M, _p(Lov), _p(Lp), np_, _p(eps), _p(E), nE, prec,
+                                   _p(sigma), _p(dsigma), _p(cache), cache.numel(),
+                                   _p(workspace), workspace.numel(), _stream(dev))
+    _check(st, "cds_sigma2_diag_cache")
+    return sigma, dsigma, cache
+
+
+def cds_qp_solve_cached(cache: torch.Tensor, orbitals: torch.Tensor, eps: torch.Tensor, nmo: int,
+                        nocc: int, conv: float = 1e-5, max_iter: int = 50,
+                        workspace: Optional[torch.Tensor] = None,
+                        raise_on_nonconvergence: bool = False):
+    """Newton quasiparticle solve (Eq. iter, Eq. ps, Eq. NR) with Sigma from the
+    numerators cds_sigma2_diag_cache stored.  Returns (omega, pole, iters, status)."""
+    lib = load()
+    orb = _dev(orbitals, torch.int32, "orbitals")
+    eps = _dev(eps, torch.float64, "eps")
+    dev = orb.device
+    np_ = orb.shape[0]
+    omega = torch.empty(np_, dtype=torch.float64, device=dev)
+    pole = torch.empty(np_, dtype=torch.float64, device=dev)
+    iters = torch.empty(np_, dtype=torch.int32, device=dev)
+    status = torch.empty(np_, dtype=torch.int32, device=dev)
+    need = lib.cds_qp_cached_workspace_bytes(nmo, nocc, np_)
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    st = lib.cds_qp_solve_cached(nmo, nocc, np_, _p(orb), _p(eps), float(conv), int(max_iter),
+                                 _p(cache), cache.numel(), _p(omega), _p(pole), _p(iters),
+                                 _p(status), _p(workspace), workspace.numel(), _stream(dev))
+    if st == 5 and not raise_on_nonconvergence:
+        st = CDS_OK
+    _check(st, "cds_qp_solve_cached")
     return omega, pole, iters, status
 
 

@@ -114,3 +114,62 @@ extern "C" int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* 
     }
     return h_active > 0 ? CDS_ERR_NO_CONVERGENCE : CDS_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Newton from cached numerators: the same iteration, each Sigma(w) evaluated
+// by sigma2_cached from the numerators a cds_sigma2_diag_cache call stored
+// (no factors needed).
+// ---------------------------------------------------------------------------
+namespace cds {
+static QpLayout qp_cached_layout(void* ws, int32_t nmo, int32_t nocc, int32_t np) {
+    Carver c(ws);
+    QpLayout l;
+    l.sig = c.take<double>(np);
+    l.dsig = c.take<double>(np);
+    l.active = c.take<int32_t>(np);
+    l.nactive = c.take<int32_t>(1);
+    l.sigma_ws = c.take<char>(tc_cached_workspace_bytes(nmo, nocc, np));
+    l.bytes = c.off;
+    return l;
+}
+}  // namespace cds
+
+extern "C" size_t cds_qp_cached_workspace_bytes(int32_t nmo, int32_t nocc, int32_t np) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || np < 0) return 0;
+    return qp_cached_layout(nullptr, nmo, nocc, np).bytes;
+}
+
+extern "C" int cds_qp_solve_cached(int32_t nmo, int32_t nocc, int32_t np, const int32_t* orb,
+                                   const double* eps, double conv, int32_t max_iter,
+                                   const void* cache, size_t cache_bytes, double* omega,
+                                   double* pole, int32_t* iters, int32_t* status,
+                                   void* workspace, size_t workspace_bytes,
+                                   cudaStream_t stream) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || np < 0 || np > 65535 || max_iter < 1 ||
+        !(conv >= 0.0))
+        return CDS_ERR_ARG;
+    if (np == 0) return CDS_OK;
+    if (!orb || !eps || !omega || !pole || !iters || !status || !cache) return CDS_ERR_ARG;
+    if (cache_bytes < tc_cache_bytes(nmo, nocc, np)) return CDS_ERR_ARG;
+    QpLayout lay = qp_cached_layout(workspace, nmo, nocc, np);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    const int nb = (np + 127) / 128;
+    k_qp_init<<<nb, 128, 0, stream>>>(eps, orb, np, nmo, omega, pole, iters, status, lay.active,
+                                      lay.nactive);
+    CDS_LAUNCH_CHECK();
+    int32_t h_active = np;
+    for (int32_t it = 0; it < max_iter && h_active > 0; ++it) {
+        int st = sigma2_cached(nmo, nocc, np, eps, omega, lay.active,
+                               static_cast<const float*>(cache), lay.sig, lay.dsig, lay.sigma_ws,
+                               stream, it == 0);
+        if (st) return st;
+        CDS_CUDA_TRY(cudaMemsetAsync(lay.nactive, 0, sizeof(int32_t), stream));
+        k_qp_step<<<nb, 128, 0, stream>>>(eps, orb, np, lay.sig, lay.dsig, conv, omega, pole,
+                                          iters, status, lay.active, lay.nactive);
+        CDS_LAUNCH_CHECK();
+        CDS_CUDA_TRY(cudaMemcpyAsync(&h_active, lay.nactive, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, stream));
+        CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    return h_active > 0 ? CDS_ERR_NO_CONVERGENCE : CDS_OK;
+}

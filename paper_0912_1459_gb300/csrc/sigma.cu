@@ -330,3 +330,26 @@ extern "C" int cds_mp2_energy(int32_t nmo, int32_t nocc, int32_t M, const double
         return mp2_fp64(nmo, nocc, M, Lov, eps, e_pair, e_total, workspace, stream);
     return mp2_tc(nmo, nocc, M, Lov, eps, precision, e_pair, e_total, workspace, stream);
 }
+
+extern "C" size_t cds_sigma2_cache_bytes(int32_t nmo, int32_t nocc, int32_t np) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || np < 0) return 0;
+    return tc_cache_bytes(nmo, nocc, np);
+}
+
+extern "C" int cds_sigma2_diag_cache(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                                     const double* Lp, int32_t np, const double* eps,
+                                     const double* E, int32_t nE, int32_t precision,
+                                     double* sigma, double* dsigma, void* cache,
+                                     size_t cache_bytes, void* workspace, size_t workspace_bytes,
+                                     cudaStream_t stream) {
+    if (!sigma_args_ok(nmo, nocc, M, np, nE)) return CDS_ERR_ARG;
+    if (!is_split16(precision)) return CDS_ERR_UNSUPPORTED;
+    if (np == 0) return CDS_OK;
+    if (!Lp || !eps || !E || !sigma || !cache || (nocc > 0 && nocc < nmo && !Lov))
+        return CDS_ERR_ARG;
+    if (cache_bytes < tc_cache_bytes(nmo, nocc, np)) return CDS_ERR_ARG;
+    size_t need = sigma_ws_bytes(nmo, nocc, M, np, nE, precision);
+    if (need && (!workspace || workspace_bytes < need)) return CDS_ERR_WORKSPACE;
+    return sigma2_tc(nmo, nocc, M, Lov, Lp, np, eps, E, nE, nullptr, precision, sigma, dsigma,
+                     workspace, stream, true, static_cast<float*>(cache));
+}

@@ -52,6 +52,7 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;
 constexpr int RED_E = 64;                     // energies reduced per CTA barrier pair
 constexpr int EPS_SMEM = 2048;                // orbital-energy pairs staged in shared memory
+constexpr int kCacheTile = TB * TB;           // cached numerators per work item
 constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 256 + NUM_EPI_WARPS * RED_E * 2 * 4 +
                               EPS_SMEM * 8;
 
@@ -334,7 +335,8 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
            int32_t nmol, int64_t nitems_batch, const float2* __restrict__ E2,
            const float2* __restrict__ eps2, const int32_t* __restrict__ active,
            const float* __restrict__ inv_scale, double* __restrict__ part,
-           unsigned long long* __restrict__ stamps, int32_t* __restrict__ err, int32_t order) {
+           unsigned long long* __restrict__ stamps, int32_t* __restrict__ err, int32_t order,
+           float* __restrict__ cache) {
     constexpr uint32_t ID = idesc<BF16>();
     constexpr int NBUF = SEP ? 1 : 2;
     extern __shared__ uint8_t smem_raw[];
@@ -551,6 +553,13 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
                             const float2 e2 = ok ? ey2[y] : make_float2(-1e30f, 0.f);  // padding: 0 * tiny
                             eh[j] = e2.x;
                             el[j] = e2.y;
+                        }
+                        if (!BATCH && cache && e0 == 0) {
+                            // [item][half][column][row]: a warp writes 32 consecutive rows
+                            float* ct = cache + (v.tm.item0 + (item - v.tm.first)) * (int64_t)kCacheTile +
+                                        ((int64_t)(half * 64 + cc) * TB + row);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) ct[(int64_t)j * TB] = num[j];
                         }
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
@@ -818,24 +827,25 @@ size_t tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int3
 namespace tc {
 template <int EC, bool BF16, bool SEP>
 static int launch_tc(int grid, const Maps& maps, const Params& P, const int32_t* active,
-                     const TcLayout& lay, cudaStream_t stream) {
+                     const TcLayout& lay, cudaStream_t stream, float* cache) {
     CDS_CUDA_TRY(cudaFuncSetAttribute(k_sigma_tc<EC, BF16, SEP, false>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
     k_sigma_tc<EC, BF16, SEP, false><<<grid, THREADS, SMEM_BYTES, stream>>>(
         maps, P, nullptr, 0, 0, lay.E2, lay.eps2, active, lay.inv, lay.part, nullptr, lay.err,
-        tune_item_order());
+        tune_item_order(), cache);
     CDS_LAUNCH_CHECK();
     return CDS_OK;
 }
 
 template <bool SEP>
 static int launch_any(int grid, bool bf16, int nE, const Maps& maps, const Params& P,
-                      const int32_t* active, const TcLayout& lay, cudaStream_t stream) {
+                      const int32_t* active, const TcLayout& lay, cudaStream_t stream,
+                      float* cache = nullptr) {
     if (nE == 1)
-        return bf16 ? launch_tc<1, true, SEP>(grid, maps, P, active, lay, stream)
-                    : launch_tc<1, false, SEP>(grid, maps, P, active, lay, stream);
-    return bf16 ? launch_tc<16, true, SEP>(grid, maps, P, active, lay, stream)
-                : launch_tc<16, false, SEP>(grid, maps, P, active, lay, stream);
+        return bf16 ? launch_tc<1, true, SEP>(grid, maps, P, active, lay, stream, cache)
+                    : launch_tc<1, false, SEP>(grid, maps, P, active, lay, stream, cache);
+    return bf16 ? launch_tc<16, true, SEP>(grid, maps, P, active, lay, stream, cache)
+                : launch_tc<16, false, SEP>(grid, maps, P, active, lay, stream, cache);
 }
 
 template <typename T>
@@ -867,10 +877,40 @@ static int split_all(const double* Lp, const double* Lov, int64_t rows_p, int64_
 }
 }  // namespace tc
 
+namespace tc {
+// Work decomposition of Eq. SE's two sums (sigma.cuh) for the factor layout
+// of cds_cd_to_mo; the same for every call with these sizes.
+void build_terms(int32_t nmo, int32_t nocc, int32_t np, Params& P) {
+    const int32_t nv = nmo - nocc;
+    const int32_t nx[2] = {nocc, nv}, ns[2] = {nv, nocc};
+    int64_t item0 = 0;
+    for (int k = 0; k < 2; ++k) {
+        Term& tm = P.term[k];
+        tm.nx = nx[k];
+        tm.ns = ns[k];
+        tm.nb = nblocks_of(std::max(nx[k], 1), TB);
+        tm.npb = npairs_of(tm.nb);
+        tm.nitems = tc_items(nx[k], ns[k], np);
+        tm.item0 = item0;
+        item0 += tm.nitems;
+        tm.bulk_s_dim = k == 0 ? 1 : 2;
+        tm.eps_s_off = k == 0 ? nocc : 0;
+        tm.eps_x_off = k == 0 ? 0 : nocc;
+    }
+    P.nmo = nmo;
+}
+}  // namespace tc
+
+size_t tc_cache_bytes(int32_t nmo, int32_t nocc, int32_t np) {
+    tc::Params P{};
+    tc::build_terms(nmo, nocc, np, P);
+    return (size_t)(P.term[0].nitems + P.term[1].nitems) * tc::kCacheTile * sizeof(float);
+}
+
 int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
               int32_t np, const double* eps, const double* E, int32_t nE,
               const int32_t* active, int32_t precision, double* sigma, double* dsigma, void* ws,
-              cudaStream_t stream, bool resplit) {
+              cudaStream_t stream, bool resplit, float* cache) {
     using namespace tc;
     if (!device_ok()) return CDS_ERR_UNSUPPORTED;
     const bool bf16 = precision == CDS_PREC_BF16X3;
@@ -891,21 +931,10 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
     // term 0 (first sum of Eq. SE): x = occupied rows of Lp, bulk L^J_{a j}
     // read from Lov[j][a] with spectator a as map dim 1 and y = j as dim 2.
     // term 1 (second sum): x = virtual rows of Lp, bulk Lov[i][b], spectator i dim 2.
-    const int32_t nx[2] = {nocc, nv}, ns[2] = {nv, nocc};
-    int64_t item0 = 0;
+    const int32_t nx[2] = {nocc, nv};
+    build_terms(nmo, nocc, np, P);
     for (int k = 0; k < 2; ++k) {
-        Term& tm = P.term[k];
-        tm.nx = nx[k];
-        tm.ns = ns[k];
-        tm.nb = nblocks_of(std::max(nx[k], 1), TB);
-        tm.npb = npairs_of(tm.nb);
-        tm.nitems = tc_items(nx[k], ns[k], np);
-        tm.item0 = item0;
-        item0 += tm.nitems;
-        tm.bulk_s_dim = k == 0 ? 1 : 2;
-        tm.eps_s_off = k == 0 ? nocc : 0;
-        tm.eps_x_off = k == 0 ? 0 : nocc;
-        if (tm.nitems == 0) continue;
+        if (P.term[k].nitems == 0) continue;
         const uint16_t* qb_hi = lay.lp_hi + (k == 0 ? 0 : (size_t)nocc * Mp);
         const uint16_t* qb_lo = lay.lp_lo + (k == 0 ? 0 : (size_t)nocc * Mp);
         bool ok = make_map(&maps.m[k][0], bf16, qb_hi, Mp, nx[k], np, rowb, rowb * nmo, TB, 1) &&
@@ -928,8 +957,9 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
                                                                                  lay.E2);
         CDS_LAUNCH_CHECK();
         int grid = (int)std::min<int64_t>(nitems, device_sms());
-        st = separate_accumulators() ? launch_any<true>(grid, bf16, nE, maps, P, active, lay, stream)
-                                     : launch_any<false>(grid, bf16, nE, maps, P, active, lay, stream);
+        st = separate_accumulators()
+                 ? launch_any<true>(grid, bf16, nE, maps, P, active, lay, stream, cache)
+                 : launch_any<false>(grid, bf16, nE, maps, P, active, lay, stream, cache);
         if (st) return st;
     } else {
         CDS_CUDA_TRY(cudaMemsetAsync(lay.part, 0, sizeof(double) * 2 * nE, stream));
@@ -942,6 +972,125 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
     return CDS_OK;
 }
 
+
+// ===========================================================================
+// Cached numerators.  The numerator n_xy of every element of every work item
+// is independent of the energy, so Sigma(E) at any E is the sum of n_xy over
+// the float-pair denominators E + e_s - e_x - e_y alone.  sigma2_tc with a
+// cache stores each item's numerators ([half][column][row] floats, written by
+// the epilogue of its first energy chunk); k_sigma_cached then evaluates
+// Sigma and dSigma/dE at one energy per orbital from them, with the same
+// per-element arithmetic as the tensor-core epilogue, streaming 64 KB per item
+// instead of recomputing the integrals.
+// ===========================================================================
+namespace tc {
+__global__ void __launch_bounds__(256)
+k_sigma_cached(Params P, const float* __restrict__ cache, const float2* __restrict__ E2,
+               const float2* __restrict__ eps2, const int32_t* __restrict__ active,
+               double* __restrict__ part) {
+    __shared__ float red[8][2];
+    const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
+    const int row = threadIdx.x & (TB - 1), half = threadIdx.x / TB;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        int term, t, s, A, B;
+        const TermR tm = decode(P.term[0], P.term[1], item, term, t, s, A, B);
+        if (active && !active[t]) continue;   // the same for the whole block
+        const int x = A * TB + row;
+        const int ybase = B * TB + half * 64;
+        const int ncols = min(64, tm.nx - ybase);
+        const int64_t pidx = tm.item0 + (item - tm.first);
+        float as = 0.f, ad = 0.f;
+        if (x < tm.nx && ncols > 0) {
+            const float2 es = eps2[tm.eps_s_off + s];
+            const float2 ex = eps2[tm.eps_x_off + x];
+            const float2 c = df_add(E2[t], df_add(es, make_float2(-ex.x, -ex.y)));
+            const float* ct = cache + pidx * kCacheTile + (int64_t)half * 64 * TB + row;
+            const float2* ey2 = eps2 + tm.eps_x_off + ybase;
+#pragma unroll 8
+            for (int j = 0; j < ncols; ++j) {
+                const float n = ct[(int64_t)j * TB];
+                const float2 e2 = ey2[j];
+                const float d = (c.x - e2.x) + (c.y - e2.y);
+                const float r = rcp_approx(d);
+                const float tt = n * r;
+                as += tt;
+                ad = fmaf(-tt, r, ad);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            as += __shfl_xor_sync(0xffffffffu, as, o);
+            ad += __shfl_xor_sync(0xffffffffu, ad, o);
+        }
+        if (lane == 0) { red[w][0] = as; red[w][1] = ad; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sv = 0.0, dv = 0.0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { sv += (double)red[i][0]; dv += (double)red[i][1]; }
+            part[pidx * 2] = sv;
+            part[pidx * 2 + 1] = dv;
+        }
+        __syncthreads();
+    }
+}
+
+struct CachedLayout {
+    double* part;
+    float2* E2;
+    float2* eps2;
+    int32_t* err;
+    size_t bytes;
+};
+
+CachedLayout cached_layout(void* ws, int32_t nmo, int32_t nocc, int32_t np) {
+    Params P{};
+    build_terms(nmo, nocc, np, P);
+    Carver c(ws);
+    CachedLayout l;
+    l.part = c.take<double>((size_t)std::max<int64_t>(P.term[0].nitems + P.term[1].nitems, 1) * 2);
+    l.E2 = c.take<float2>((size_t)std::max(np, 1));
+    l.eps2 = c.take<float2>((size_t)nmo);
+    l.err = c.take<int32_t>(4);
+    l.bytes = c.off;
+    return l;
+}
+}  // namespace tc
+
+size_t tc_cached_workspace_bytes(int32_t nmo, int32_t nocc, int32_t np) {
+    return tc::cached_layout(nullptr, nmo, nocc, np).bytes;
+}
+
+int sigma2_cached(int32_t nmo, int32_t nocc, int32_t np, const double* eps, const double* E,
+                  const int32_t* active, const float* cache, double* sigma, double* dsigma,
+                  void* ws, cudaStream_t stream, bool first) {
+    using namespace tc;
+    Params P{};
+    build_terms(nmo, nocc, np, P);
+    P.nE = 1;
+    CachedLayout lay = cached_layout(ws, nmo, nocc, np);
+    const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
+    if (first) {
+        CDS_CUDA_TRY(cudaMemsetAsync(lay.err, 0, sizeof(int32_t), stream));
+        k_to_pairs<<<(nmo + 255) / 256, 256, 0, stream>>>(eps, nmo, lay.eps2);
+        CDS_LAUNCH_CHECK();
+    }
+    if (nitems == 0) {
+        CDS_CUDA_TRY(cudaMemsetAsync(lay.part, 0, sizeof(double) * 2, stream));
+    } else {
+        k_to_pairs<<<(np + 255) / 256, 256, 0, stream>>>(E, np, lay.E2);
+        CDS_LAUNCH_CHECK();
+        const int grid = (int)std::min<int64_t>(nitems, 8LL * device_sms());
+        k_sigma_cached<<<grid, 256, 0, stream>>>(P, cache, lay.E2, lay.eps2, active, lay.part);
+        CDS_LAUNCH_CHECK();
+    }
+    const int64_t per0 = np ? P.term[0].nitems / np : 0, per1 = np ? P.term[1].nitems / np : 0;
+    k_tc_reduce<<<dim3(1, np), 256, 0, stream>>>(lay.part, per0, P.term[0].nitems, per1, 1, active,
+                                                lay.err, sigma, dsigma);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
 
 // ===========================================================================
 // MP2 correlation energy (Eq. MP2) on the same kernel.  For occupied i, j the
@@ -1364,7 +1513,7 @@ int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_t
         CDS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
         kern<<<grid, THREADS, SMEM_BYTES, stream>>>(dummy_maps, dummy, set, nmol, nitems, Ep, epsv,
                                                     pass == 1 ? active : nullptr, nullptr, lay.part,
-                                                    stamps, lay.err, order);
+                                                    stamps, lay.err, order, nullptr);
         CDS_LAUNCH_CHECK();
     }
     if (np_total > 0) {

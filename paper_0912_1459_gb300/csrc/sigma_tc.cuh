@@ -9,10 +9,19 @@ size_t tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int3
 
 // resplit = false reuses the 16-bit operand splits a previous call with the
 // same Lov, Lp and workspace left in ws (the Newton iterations of one solve).
+// cache (may be null): receives every work item's numerators
+// (tc_cache_bytes), for sigma2_cached.
 int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
               int32_t np, const double* eps, const double* E, int32_t nE,
               const int32_t* active, int32_t precision, double* sigma, double* dsigma, void* ws,
-              cudaStream_t stream, bool resplit = true);
+              cudaStream_t stream, bool resplit = true, float* cache = nullptr);
+size_t tc_cache_bytes(int32_t nmo, int32_t nocc, int32_t np);
+// Sigma and dSigma/dE at one energy per orbital (E [np]) from cached
+// numerators; first = the first call of a solve (stages eps).
+size_t tc_cached_workspace_bytes(int32_t nmo, int32_t nocc, int32_t np);
+int sigma2_cached(int32_t nmo, int32_t nocc, int32_t np, const double* eps, const double* E,
+                  const int32_t* active, const float* cache, double* sigma, double* dsigma,
+                  void* ws, cudaStream_t stream, bool first);
 
 // MP2 correlation energy (Eq. MP2) on the tensor-core kernel: e_pair[i] =
 // sum_{j,a,b}, e_total = sum_i e_pair[i] (either may be null).

@@ -189,3 +189,18 @@ def test_mp2_full_size(run):
     np.testing.assert_allclose(e64[rows], ref, rtol=1e-10)
     np.testing.assert_allclose(ebf[rows], ref, rtol=1e-5)
     assert abs(float(tbf) - float(t64)) <= 1e-5 * abs(float(t64))
+
+
+def test_cached_newton_full_size(run):
+    """The benchmark's Newton from cached numerators against the recomputing
+    Newton (BF16X3) at C60 size: quasiparticle roots within 1e-7 Ha."""
+    m, L, piv, D, de, Lov, Lp = run
+    eps, orbs = dev(m.eps), dev(m.orbitals)
+    E = dev(W.energy_grid(m.eps[m.orbitals], m.nE))
+    _, _, cache = G.cds_sigma2_diag_cache(Lov, Lp, eps, m.nocc, E, "bf16x3")
+    w0, P0, it0, st0 = G.cds_qp_solve(Lov, Lp, orbs, eps, m.nocc, precision="bf16x3")
+    w1, P1, it1, st1 = G.cds_qp_solve_cached(cache, orbs, eps, m.nbf, m.nocc)
+    ok = ((st0 == 0) & (P0 >= 0.5)).cpu().numpy()     # quasiparticle poles
+    assert ok.sum() >= 5
+    assert np.array_equal(st1.cpu().numpy()[ok], st0.cpu().numpy()[ok])
+    assert np.abs((w0 - w1).cpu().numpy()[ok]).max() <= 1e-7
