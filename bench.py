@@ -60,6 +60,9 @@ def parse():
     p.add_argument("--no-fp64-arm", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-mp2", action="store_true")
+    p.add_argument("--no-fuse", action="store_true",
+                   help="run the decomposition and the transform as two calls (stage times "
+                        "of each) instead of the pipelined cds_cd_decompose_to_mo")
     p.add_argument("--newton", default="cached", choices=["cached", "recompute"],
                    help="Newton from the numerators the Sigma-grid stage keeps, or recomputing "
                         "the integrals every iteration (split precisions)")
@@ -213,6 +216,8 @@ def peaks():
         # probe on this pool measured 1.25 and 78 TFLOP/s)
         "fp64_tflops": 1.25,
         "fp32_tflops": 78.0,
+        # FP32 instruction issue: 152 SMs x 128 lanes x 2.07 GHz (nominal clock)
+        "fp32_issue_tinstr": 152 * 128 * 2.07e9 / 1e12,
     }
 
 
@@ -248,15 +253,32 @@ def run_ours(args, dist: Dist):
     cache = (torch.empty(lib.cds_sigma2_cache_bytes(m.nbf, m.nocc, n_orb), dtype=torch.uint8,
                          device=device) if cached else None)
 
+    fused = not args.no_fuse and tr_prec != "fp64"
+    if fused:
+        nv = m.nbf - m.nocc
+        lov_buf = torch.empty(m.nocc * nv * max_rank, dtype=torch.float64, device=device)
+        lp_buf = torch.empty(n_orb * m.nbf * max_rank, dtype=torch.float64, device=device)
+        fz_ws = torch.empty(lib.cds_cd_decompose_to_mo_workspace_bytes(m.nbf, m.nbf, m.nocc,
+                                                                       max_rank, n_orb),
+                            dtype=torch.uint8, device=device)
+
     def step(xyz, al, at, C, eps, orbs, E, ws=None):
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
         ev[0].record()
-        L, piv, D, de = G.cds_cd_decompose(xyz, al, at, args.delta, args.scheme, L_out=Lbuf,
-                                           workspace=cd_ws, precision=tr_prec)
-        ev[1].record()
-        Lov, Lp = G.cds_cd_to_mo(L, C, m.nocc, orbs, workspace=ws and ws.get("tr"),
-                                 precision=tr_prec)
-        ev[2].record()
+        if fused:
+            # decomposition and transform pipelined in one call: one stage
+            L, piv, D, de, Lov, Lp = G.cds_cd_decompose_to_mo(
+                xyz, al, at, args.delta, C, m.nocc, orbs, args.scheme, L_out=Lbuf,
+                Lov_out=lov_buf, Lp_out=lp_buf, workspace=fz_ws)
+            ev[1].record()
+            ev[2].record()
+        else:
+            L, piv, D, de = G.cds_cd_decompose(xyz, al, at, args.delta, args.scheme, L_out=Lbuf,
+                                               workspace=cd_ws, precision=tr_prec)
+            ev[1].record()
+            Lov, Lp = G.cds_cd_to_mo(L, C, m.nocc, orbs, workspace=ws and ws.get("tr"),
+                                     precision=tr_prec)
+            ev[2].record()
         if cached:
             sig, dsig, _ = G.cds_sigma2_diag_cache(Lov, Lp, eps, m.nocc, E, prec, cache=cache,
                                                    workspace=ws and ws.get("sg"))
@@ -346,12 +368,13 @@ def run_ours(args, dist: Dist):
 
     # ---- rooflines (per call, CUDA events on the launching stream) ----
     fm = flops_model(m, M)
-    cd_stats = G.cdsigma.cds_cd_stats(m.nbf, cd_ws, "f32x2" if tr_prec != "fp64" else "fp64")
+    cd_stats = G.cdsigma.cds_cd_stats(m.nbf, fz_ws if fused else cd_ws,
+                                      "f32x2" if tr_prec != "fp64" else "fp64")
     cd_bytes = float(npr) * (8.0 * cd_stats["streamed"] + 8.0 * cd_stats["extra"] +
                              32.0 * cd_stats["passes"] + 89.0 * M)
     pk = peaks()
     iters = it.cpu().numpy()
-    med = {k: statistics.median(v) for k, v in stage_ms.items()}
+    med = {k: max(statistics.median(v), 1e-6) for k, v in stage_ms.items()}
     sig_passes_grid = n_orb
     sig_passes_qp = int(iters.sum())
     split = 1 if prec == "fp64" else 3
@@ -397,10 +420,29 @@ def run_ours(args, dist: Dist):
                       "peak": pk["bf16_tflops"] if prec != "fp64" else pk["fp64_tflops"],
                       "achieved": sig_flops_qp / (med["qp"] / 1e3) / 1e12,
                       "note": f"{sig_passes_qp} Sigma passes (nE=1); {split} split products per MAC"}
+    if fused:
+        # one stage for both; both parts are bound by FP32 instruction issue
+        # (float-pair arithmetic): 12 FP32 instructions per float-pair
+        # multiply-add in the projections, 11 in the transform GEMMs
+        N, o, nv = m.nbf, m.nocc, m.nbf - m.nocc
+        tr_macs = float(M) * N * ((o + n_orb) * N + o * nv + n_orb * N)
+        instr = (12.0 * 4 * cd_stats["streamed"] + 12.0 * cd_stats["extra"]) * npr + 11.0 * tr_macs
+        med["cd_transform"] = med.pop("cd")
+        med.pop("transform")
+        roof.pop("cd")
+        roof.pop("transform")
+        roof["cd_transform"] = {
+            "bound": "alu", "unit": "T FP32 instr/s", "peak": pk["fp32_issue_tinstr"],
+            "achieved": instr / (med["cd_transform"] / 1e3) / 1e12,
+            "note": (f"pipelined decomposition + transform (cds_cd_decompose_to_mo): float-pair "
+                     f"FMAs of the projections ({cd_stats['passes']} streaming passes, "
+                     f"{cd_stats['streamed']} vectors streamed) and of the transform GEMMs; "
+                     f"peak = 152 SMs x 128 FP32 lanes x 2.07 GHz"),
+            "cd_stats": cd_stats}
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
-    # (traffic stays null until an ncu capture of the current CD kernels exists)
+    # (traffic stays null until an ncu capture of the current kernels exists)
     dominant = max(med, key=med.get)
 
     # ---- FP64 GPU arm on a subset, and mixed-vs-FP64 accuracy ----

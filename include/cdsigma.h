@@ -197,6 +197,29 @@ int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double
                  cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
+ * Decomposition and transform in one call (float-pair form).  Runs
+ * cds_cd_decompose(F32X2) and cds_cd_to_mo(F32X2) with the transform of each
+ * batch of 32 finished vectors overlapped with the decomposition of the next
+ * ones, on two library streams (the decomposition's at the highest
+ * priority), joined to `stream` on return.  The results are those of the two
+ * calls in sequence.
+ * Inputs and outputs as cds_cd_decompose and cds_cd_to_mo, except:
+ *   Lov  [nocc][nmo-nocc][M] and Lp [np][nmo][M] are written compact for the
+ *        final rank M, into caller buffers of room for max_rank in place of M;
+ *   the workspace (cds_cd_decompose_to_mo_workspace_bytes) holds both calls'
+ *        workspaces and max_rank-strided staging copies of Lov and Lp.
+ * Blocking, like cds_cd_decompose.
+ * ---------------------------------------------------------------------- */
+size_t cds_cd_decompose_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc,
+                                              int32_t max_rank, int32_t np);
+int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const double* alpha,
+                           const int32_t* atom, double delta, int32_t scheme, int32_t max_rank,
+                           const double* C, int32_t nmo, int32_t nocc, const int32_t* orb,
+                           int32_t np, double* L, int32_t* piv, double* D, int32_t* M_out,
+                           double* delta_eff_out, double* Lov, double* Lp, void* workspace,
+                           size_t workspace_bytes, cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
  * Diagonal second-order self-energy (paper Eq. SE) and its energy derivative
  * for np orbitals orb[t] at nE energies each:
  *   sigma[t][e]  = Sigma_qq(E[t][e]),  dsigma[t][e] = dSigma_qq/dE (analytic),

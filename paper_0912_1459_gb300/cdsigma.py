@@ -56,6 +56,10 @@ _SIGNATURES = {
                                     _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "cds_cd_stats": (ctypes.c_int, [_i32, _vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64), _vp]),
+    "cds_cd_decompose_to_mo_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
+    "cds_cd_decompose_to_mo": (ctypes.c_int, [_i32, _vp, _vp, _vp, _f64, _i32, _i32, _vp, _i32, _i32,
+                                              _vp, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32),
+                                              ctypes.POINTER(_f64), _vp, _vp, _vp, _sz, _vp]),
     "cds_sigma2_cache_bytes": (_sz, [_i32, _i32, _i32]),
     "cds_sigma2_diag_cache": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _i32,
                                              _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
@@ -231,6 +235,56 @@ def cds_cd_decompose(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,
                               ctypes.byref(de), _p(workspace), workspace.numel(), _stream(dev))
     _check(st, "cds_cd_decompose")
     return L_out[:M.value], piv[:M.value], D, de.value
+
+
+def cds_cd_decompose_to_mo(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,
+                           delta: float, C: torch.Tensor, nocc: int, orbitals: torch.Tensor,
+                           scheme: str = "full", max_rank: Optional[int] = None,
+                           L_out: Optional[torch.Tensor] = None,
+                           Lov_out: Optional[torch.Tensor] = None,
+                           Lp_out: Optional[torch.Tensor] = None,
+                           workspace: Optional[torch.Tensor] = None):
+    """Float-pair decomposition and transform in one pipelined call.
+
+    Returns (L [M, npair], piv [M], D, delta_eff, Lov [o, v, M], Lp [np, nmo, M])."""
+    lib = load()
+    xyz = _dev(xyz, torch.float64, "xyz")
+    alpha = _dev(alpha, torch.float64, "alpha")
+    atom = _dev(atom, torch.int32, "atom")
+    C = _dev(C, torch.float64, "C")
+    orb = _dev(orbitals, torch.int32, "orbitals")
+    dev = alpha.device
+    n = alpha.shape[0]
+    nbf, nmo = C.shape
+    if nbf != n:
+        raise ValueError("C must be [nbf, nmo]")
+    npr = npair(n)
+    if max_rank is None:
+        max_rank = L_out.shape[0] if L_out is not None else default_max_rank(n)
+    if L_out is None:
+        L_out = torch.empty((max_rank, npr), dtype=torch.float64, device=dev)
+    np_ = orb.shape[0]
+    nv = nmo - nocc
+    if Lov_out is None or Lov_out.numel() < nocc * nv * max_rank:
+        Lov_out = torch.empty(max(nocc * nv * max_rank, 1), dtype=torch.float64, device=dev)
+    if Lp_out is None or Lp_out.numel() < np_ * nmo * max_rank:
+        Lp_out = torch.empty(max(np_ * nmo * max_rank, 1), dtype=torch.float64, device=dev)
+    piv = torch.empty(max(max_rank, 1), dtype=torch.int32, device=dev)
+    D = torch.empty(npr, dtype=torch.float64, device=dev)
+    need = lib.cds_cd_decompose_to_mo_workspace_bytes(n, nmo, nocc, max_rank, np_)
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    M, de = _i32(0), _f64(0.0)
+    st = lib.cds_cd_decompose_to_mo(n, _p(xyz), _p(alpha), _p(atom), float(delta),
+                                    SCHEMES[scheme], int(max_rank), _p(C), nmo, nocc, _p(orb),
+                                    np_, _p(L_out), _p(piv), _p(D), ctypes.byref(M),
+                                    ctypes.byref(de), _p(Lov_out), _p(Lp_out), _p(workspace),
+                                    workspace.numel(), _stream(dev))
+    _check(st, "cds_cd_decompose_to_mo")
+    Mv = M.value
+    Lov = Lov_out.view(-1)[:nocc * nv * Mv].view(nocc, nv, Mv)
+    Lp = Lp_out.view(-1)[:np_ * nmo * Mv].view(np_, nmo, Mv)
+    return L_out[:Mv], piv[:Mv], D, de.value, Lov, Lp
 
 
 def cds_cd_stats(nbf: int, workspace: torch.Tensor, precision: str = "fp64") -> dict:

@@ -14,6 +14,8 @@
 // units instead of the 1.25 TFLOP/s FP64 ones.  Tensor-core splits cannot
 // serve here: C = S^-1/2 Q has |C| up to ~1e3, the transform cancels ~1e6
 // relative, and the tensor-core FP32 accumulation truncates.
+#include <mutex>
+
 #include "common.cuh"
 
 namespace cds {
@@ -257,6 +259,19 @@ __global__ void k_unpack_pairs(const double* __restrict__ L, int64_t npair, int3
     U[e] = to_pair(L[(int64_t)(K0 + b) * npair + (int64_t)hi * (hi + 1) / 2 + lo]);
 }
 
+// The same from vectors already held as float pairs.
+__global__ void k_unpack_f2(const float2* __restrict__ Lf, int64_t npair, int32_t K0, int32_t kb,
+                            int32_t N, float2* __restrict__ U) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t per = (int64_t)N * N;
+    if (e >= per * kb) return;
+    int b = (int)(e / per);
+    int64_t r = e - b * per;
+    int mu = (int)(r / N), nu = (int)(r - (int64_t)mu * N);
+    int lo = min(mu, nu), hi = max(mu, nu);
+    U[e] = Lf[(int64_t)(K0 + b) * npair + (int64_t)hi * (hi + 1) / 2 + lo];
+}
+
 // Cq[mu][j] = pair(C[mu][col(j)]) with col(j) = j (all MOs) or orb[j].
 __global__ void k_pair_cols(const double* __restrict__ C, int32_t N, int32_t nmo,
                             const int32_t* __restrict__ orb, int32_t ncol, float2* __restrict__ Cq) {
@@ -405,46 +420,69 @@ static AoLayout ao_layout(void* ws, int32_t nbf, int32_t nmo, int32_t nocc, int3
 // The float-pair transform.  Per batch of vectors one GEMM forms the
 // occupied and the requested orbital rows together, T = [C_occ | C_P]^T A^K
 // ((o + np) x N), then Lov = T_occ C_vir and Lp = T_P C.
-static int cd_to_mo_f32x2(int32_t N, int32_t nmo, int32_t nocc, int32_t M, const double* L,
-                          const double* C, const int32_t* orb, int32_t np, double* Lov,
-                          double* Lp, const AoLayout& lay, cudaStream_t stream) {
+static int f32x2_columns(int32_t N, int32_t nmo, int32_t nocc, const double* C, const int32_t* orb,
+                         int32_t np, const AoLayout& lay, cudaStream_t stream) {
+    const int32_t nc = nocc + np;
+    k_pair_cols<<<(N * nmo + 255) / 256, 256, 0, stream>>>(C, N, nmo, nullptr, nmo,
+                                                           reinterpret_cast<float2*>(lay.Cq));
+    CDS_LAUNCH_CHECK();
+    k_pair_cols_joint<<<(N * nc + 255) / 256, 256, 0, stream>>>(C, N, nmo, nocc, orb, np,
+                                                                reinterpret_cast<float2*>(lay.Cj));
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
+// Vectors [K0, K0 + kb) (FP64 rows of L, or float-pair rows when Lf is given)
+// into Lov[i][a][K] and Lp[t][r][K], K stride ldK.
+static int f32x2_batch(int32_t N, int32_t nmo, int32_t nocc, int32_t np, const double* L,
+                       const float2* Lf, int32_t K0, int32_t kb, int64_t ldK, double* Lov,
+                       double* Lp, const AoLayout& lay, cudaStream_t stream) {
     const int64_t npair = npair_of(N);
     const int32_t nv = nmo - nocc, nc = nocc + np;
-    float2* Cq = reinterpret_cast<float2*>(lay.Cq);
-    float2* Cj = reinterpret_cast<float2*>(lay.Cj);
+    const float2* Cq = reinterpret_cast<const float2*>(lay.Cq);
+    const float2* Cj = reinterpret_cast<const float2*>(lay.Cj);
     float2* U = reinterpret_cast<float2*>(lay.U);
     float2* T = reinterpret_cast<float2*>(lay.T);
     const bool ov = nocc > 0 && nv > 0;
-    if (!ov && np == 0) return CDS_OK;
-    k_pair_cols<<<(N * nmo + 255) / 256, 256, 0, stream>>>(C, N, nmo, nullptr, nmo, Cq);
-    CDS_LAUNCH_CHECK();
-    k_pair_cols_joint<<<(N * nc + 255) / 256, 256, 0, stream>>>(C, N, nmo, nocc, orb, np, Cj);
-    CDS_LAUNCH_CHECK();
-    for (int32_t K0 = 0; K0 < M; K0 += kAoBatch) {
-        int32_t kb = std::min(kAoBatch, M - K0);
-        int64_t tot = (int64_t)kb * N * N;
+    if ((!ov && np == 0) || kb <= 0) return CDS_OK;
+    const int64_t tot = (int64_t)kb * N * N;
+    if (Lf)
+        k_unpack_f2<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(Lf, npair, K0, kb, N, U);
+    else
         k_unpack_pairs<<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(L, npair, K0, kb, N, U);
-        CDS_LAUNCH_CHECK();
-        PairMat Um{U, N, 1, (int64_t)N * N};
-        // rows of the occupied block only when Lov is wanted
-        const int32_t r0 = ov ? 0 : nocc, rows = nc - r0;
-        int st = launch_dfgemm<true, true, float2>(rows, N, N, kb, PairMat{Cj + r0, 1, nc, 0}, Um,
-                                                   OutMat<float2>{T + (int64_t)r0 * N, N, 1,
-                                                                  (int64_t)nc * N},
-                                                   stream);
+    CDS_LAUNCH_CHECK();
+    PairMat Um{U, N, 1, (int64_t)N * N};
+    // rows of the occupied block only when Lov is wanted
+    const int32_t r0 = ov ? 0 : nocc, rows = nc - r0;
+    int st = launch_dfgemm<true, true, float2>(rows, N, N, kb, PairMat{Cj + r0, 1, nc, 0}, Um,
+                                               OutMat<float2>{T + (int64_t)r0 * N, N, 1,
+                                                              (int64_t)nc * N},
+                                               stream);
+    if (st) return st;
+    if (ov) {
+        st = launch_dfgemm<false, true, double>(
+            nocc, nv, N, kb, PairMat{T, N, 1, (int64_t)nc * N}, PairMat{Cq + nocc, nmo, 1, 0},
+            OutMat<double>{Lov + K0, (int64_t)nv * ldK, ldK, 1}, stream);
         if (st) return st;
-        if (ov) {
-            st = launch_dfgemm<false, true, double>(
-                nocc, nv, N, kb, PairMat{T, N, 1, (int64_t)nc * N}, PairMat{Cq + nocc, nmo, 1, 0},
-                OutMat<double>{Lov + K0, (int64_t)nv * M, M, 1}, stream);
-            if (st) return st;
-        }
-        if (np > 0) {
-            st = launch_dfgemm<false, true, double>(
-                np, nmo, N, kb, PairMat{T + (int64_t)nocc * N, N, 1, (int64_t)nc * N},
-                PairMat{Cq, nmo, 1, 0}, OutMat<double>{Lp + K0, (int64_t)nmo * M, M, 1}, stream);
-            if (st) return st;
-        }
+    }
+    if (np > 0) {
+        st = launch_dfgemm<false, true, double>(
+            np, nmo, N, kb, PairMat{T + (int64_t)nocc * N, N, 1, (int64_t)nc * N},
+            PairMat{Cq, nmo, 1, 0}, OutMat<double>{Lp + K0, (int64_t)nmo * ldK, ldK, 1}, stream);
+        if (st) return st;
+    }
+    return CDS_OK;
+}
+
+static int cd_to_mo_f32x2(int32_t N, int32_t nmo, int32_t nocc, int32_t M, const double* L,
+                          const double* C, const int32_t* orb, int32_t np, double* Lov,
+                          double* Lp, const AoLayout& lay, cudaStream_t stream) {
+    int st = f32x2_columns(N, nmo, nocc, C, orb, np, lay, stream);
+    if (st) return st;
+    for (int32_t K0 = 0; K0 < M; K0 += kAoBatch) {
+        st = f32x2_batch(N, nmo, nocc, np, L, nullptr, K0, std::min(kAoBatch, M - K0), M, Lov, Lp,
+                         lay, stream);
+        if (st) return st;
     }
     return CDS_OK;
 }
@@ -591,4 +629,145 @@ extern "C" int cds_cd_to_mo_backward(int32_t nbf, int32_t nmo, int32_t nocc, int
         CDS_LAUNCH_CHECK();
     }
     return CDS_OK;
+}
+
+// ===========================================================================
+// Decomposition and transform as one pipelined call (float-pair form).  The
+// transform of a batch of vectors needs only those vectors, so batch j is
+// transformed on a second stream while the decomposition computes the next
+// ones: the steps that stream nothing leave most of the GPU idle, and the
+// transform GEMMs fill it.  The transform reads the float-pair rows directly
+// and writes Lov / Lp with a K stride of max_rank (the rank is unknown until
+// the end); two strided copies compact them at the end.
+// ===========================================================================
+namespace cds {
+namespace {
+
+struct PipeStreams {
+    cudaStream_t cd = nullptr, tr = nullptr;
+};
+
+int pipeline_streams(PipeStreams* out) {
+    static std::mutex lock;
+    static PipeStreams per_dev[64];
+    int dev = 0;
+    CDS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return CDS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> guard(lock);
+    PipeStreams& p = per_dev[dev];
+    if (!p.cd) {
+        int lo = 0, hi = 0;
+        CDS_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CDS_CUDA_TRY(cudaStreamCreateWithPriority(&p.cd, cudaStreamNonBlocking, hi));
+        CDS_CUDA_TRY(cudaStreamCreateWithPriority(&p.tr, cudaStreamNonBlocking, lo));
+    }
+    *out = p;
+    return CDS_OK;
+}
+
+// stream `waiter` waits for the work enqueued so far on `on`
+int stream_wait(cudaStream_t waiter, cudaStream_t on) {
+    cudaEvent_t ev;
+    CDS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CDS_CUDA_TRY(cudaEventRecord(ev, on));
+    CDS_CUDA_TRY(cudaStreamWaitEvent(waiter, ev, 0));
+    CDS_CUDA_TRY(cudaEventDestroy(ev));
+    return CDS_OK;
+}
+
+struct FusedLayout {
+    void* cd;
+    size_t cd_bytes;
+    AoLayout ao;
+    double* lov_cap;   // [nocc][nv][max_rank]
+    double* lp_cap;    // [np][nmo][max_rank]
+    size_t bytes;
+};
+
+FusedLayout fused_layout(void* ws, int32_t nbf, int32_t nmo, int32_t nocc, int32_t max_rank,
+                         int32_t np) {
+    FusedLayout l;
+    l.cd_bytes = cd_workspace_bytes_for(nbf, true);
+    Carver c(ws);
+    l.cd = c.take<char>(l.cd_bytes);
+    const size_t ao_bytes = ao_layout(nullptr, nbf, nmo, nocc, np).bytes;
+    char* ao = c.take<char>(ao_bytes);
+    l.ao = ao_layout(ao, nbf, nmo, nocc, np);
+    l.lov_cap = c.take<double>((size_t)std::max<int64_t>((int64_t)nocc * (nmo - nocc) * max_rank, 1));
+    l.lp_cap = c.take<double>((size_t)std::max<int64_t>((int64_t)np * nmo * max_rank, 1));
+    l.bytes = c.off;
+    return l;
+}
+
+}  // namespace
+}  // namespace cds
+
+extern "C" size_t cds_cd_decompose_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc,
+                                                         int32_t max_rank, int32_t np) {
+    if (nbf <= 0 || nmo <= 0 || nmo > nbf || nocc < 0 || nocc > nmo || max_rank < 0 || np < 0)
+        return 0;
+    return fused_layout(nullptr, nbf, nmo, nocc, max_rank, np).bytes;
+}
+
+extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const double* alpha,
+                                      const int32_t* atom, double delta, int32_t scheme,
+                                      int32_t max_rank, const double* C, int32_t nmo,
+                                      int32_t nocc, const int32_t* orb, int32_t np, double* L,
+                                      int32_t* piv, double* D, int32_t* M_out,
+                                      double* delta_eff_out, double* Lov, double* Lp,
+                                      void* workspace, size_t workspace_bytes,
+                                      cudaStream_t stream) {
+    if (nbf <= 0 || nmo <= 0 || nmo > nbf || nocc < 0 || nocc > nmo || np < 0 || max_rank < 0)
+        return CDS_ERR_ARG;
+    if (!C || !Lov || !M_out || (np > 0 && (!orb || !Lp))) return CDS_ERR_ARG;
+    FusedLayout lay = fused_layout(workspace, nbf, nmo, nocc, max_rank, np);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    PipeStreams ps;
+    int st = pipeline_streams(&ps);
+    if (st) return st;
+    if ((st = stream_wait(ps.cd, stream)) || (st = stream_wait(ps.tr, stream))) return st;
+    st = f32x2_columns(nbf, nmo, nocc, C, orb, np, lay.ao, ps.tr);
+    if (st) return st;
+    const float2* Lf = reinterpret_cast<const float2*>(L);
+    int32_t next = 0;   // first vector not yet handed to the transform
+    CdChunkHook hook = [&](int32_t rows, bool done) -> int {
+        while (next < rows && (done || next + kAoBatch <= rows)) {
+            const int32_t kb = std::min(kAoBatch, rows - next);
+            int s2 = f32x2_batch(nbf, nmo, nocc, np, nullptr, Lf, next, kb, max_rank, lay.lov_cap,
+                                 lay.lp_cap, lay.ao, ps.tr);
+            if (s2) return s2;
+            next += kb;
+        }
+        return CDS_OK;
+    };
+    int32_t M = 0;
+    const int cd_st = cd_decompose_run(nbf, xyz, alpha, atom, delta, scheme, max_rank,
+                                       CDS_PREC_F32X2, L, piv, D, &M, delta_eff_out, lay.cd,
+                                       lay.cd_bytes, ps.cd, &hook, ps.tr);
+    *M_out = M;
+    const int32_t nv = nmo - nocc;
+    if (M > 0 && (cd_st == CDS_OK || cd_st == CDS_ERR_RANK_CAP)) {
+        // the last host check reports the stop, so every vector has been
+        // handed over; should any remain, take them from the converted rows
+        if (next < M) {
+            if ((st = stream_wait(ps.tr, ps.cd))) return st;
+            for (; next < M; next += kAoBatch)
+                if ((st = f32x2_batch(nbf, nmo, nocc, np, L, nullptr, next,
+                                      std::min(kAoBatch, M - next), max_rank, lay.lov_cap,
+                                      lay.lp_cap, lay.ao, ps.tr)))
+                    return st;
+        }
+        if (nocc > 0 && nv > 0)
+            CDS_CUDA_TRY(cudaMemcpy2DAsync(Lov, (size_t)M * sizeof(double), lay.lov_cap,
+                                           (size_t)max_rank * sizeof(double),
+                                           (size_t)M * sizeof(double), (size_t)nocc * nv,
+                                           cudaMemcpyDeviceToDevice, ps.tr));
+        if (np > 0)
+            CDS_CUDA_TRY(cudaMemcpy2DAsync(Lp, (size_t)M * sizeof(double), lay.lp_cap,
+                                           (size_t)max_rank * sizeof(double),
+                                           (size_t)M * sizeof(double), (size_t)np * nmo,
+                                           cudaMemcpyDeviceToDevice, ps.tr));
+    }
+    if ((st = stream_wait(stream, ps.cd)) || (st = stream_wait(stream, ps.tr))) return st;
+    return cd_st;
 }

@@ -1014,11 +1014,18 @@ extern "C" int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precisio
     return CDS_OK;
 }
 
-extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
-                                const int32_t* atom, double delta, int32_t scheme,
-                                int32_t max_rank, int32_t precision, double* L, int32_t* piv,
-                                double* D, int32_t* M_out, double* delta_eff_out,
-                                void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+namespace cds {
+
+// The decomposition of cds_cd_decompose.  on_chunk (may be null) runs after
+// every host check with the number of rows of L that are final and whether
+// the decomposition has stopped; before the float-pair rows are converted to
+// FP64 at the end, stream waits for convert_after (may be null), so work that
+// reads the float-pair rows can run on another stream meanwhile.
+int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const int32_t* atom,
+                     double delta, int32_t scheme, int32_t max_rank, int32_t precision, double* L,
+                     int32_t* piv, double* D, int32_t* M_out, double* delta_eff_out,
+                     void* workspace, size_t workspace_bytes, cudaStream_t stream,
+                     const CdChunkHook* on_chunk, cudaStream_t convert_after) {
     if (nbf <= 0 || !xyz || !alpha || !L || !piv || !D || !M_out || max_rank < 0)
         return CDS_ERR_ARG;
     if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return CDS_ERR_UNSUPPORTED;
@@ -1069,11 +1076,22 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
         CDS_CUDA_TRY(cudaGetLastError());
         CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, stream));
         CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (on_chunk && *on_chunk) {
+            st = (*on_chunk)(h.done ? h.M : k1, h.done != 0);
+            if (st) return st;
+        }
         if (h.done) break;
     }
     *M_out = h.M;
     if (delta_eff_out) *delta_eff_out = h.delta_eff;
     if (df && h.M > 0) {
+        if (convert_after) {
+            cudaEvent_t ev;
+            CDS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            CDS_CUDA_TRY(cudaEventRecord(ev, convert_after));
+            CDS_CUDA_TRY(cudaStreamWaitEvent(stream, ev, 0));
+            CDS_CUDA_TRY(cudaEventDestroy(ev));
+        }
         const int64_t cnt = (int64_t)h.M * n;
         k_pairs_to_fp64<<<(unsigned)((cnt + 255) / 256), 256, 0, stream>>>(L, cnt);
         CDS_LAUNCH_CHECK();
@@ -1081,6 +1099,19 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
     if (!h.done) return CDS_ERR_RANK_CAP;
     return h.status;
 }
+
+}  // namespace cds
+
+extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
+                                const int32_t* atom, double delta, int32_t scheme,
+                                int32_t max_rank, int32_t precision, double* L, int32_t* piv,
+                                double* D, int32_t* M_out, double* delta_eff_out,
+                                void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+    return cds::cd_decompose_run(nbf, xyz, alpha, atom, delta, scheme, max_rank, precision, L,
+                                 piv, D, M_out, delta_eff_out, workspace, workspace_bytes, stream,
+                                 nullptr, nullptr);
+}
+
 
 // ===========================================================================
 // Batched decomposition: the steps of many molecules advance together, one

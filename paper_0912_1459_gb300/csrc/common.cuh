@@ -6,6 +6,7 @@
 #include <math.h>
 #include <climits>
 #include <algorithm>
+#include <functional>
 
 #include "cdsigma.h"
 
@@ -119,4 +120,11 @@ int build_pairs(int32_t nbf, const double* xyz, const double* alpha, PairSoA pd,
 // Workspace of cds_cd_decompose for one precision (f32x2 needs the candidate
 // projections as well).
 size_t cd_workspace_bytes_for(int32_t nbf, bool f32x2);
+// Called after each host check of the decomposition: (rows of L final, stopped).
+using CdChunkHook = std::function<int(int32_t, bool)>;
+int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const int32_t* atom,
+                     double delta, int32_t scheme, int32_t max_rank, int32_t precision, double* L,
+                     int32_t* piv, double* D, int32_t* M_out, double* delta_eff_out,
+                     void* workspace, size_t workspace_bytes, cudaStream_t stream,
+                     const CdChunkHook* on_chunk, cudaStream_t convert_after);
 }

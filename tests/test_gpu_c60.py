@@ -204,3 +204,22 @@ def test_cached_newton_full_size(run):
     assert ok.sum() >= 5
     assert np.array_equal(st1.cpu().numpy()[ok], st0.cpu().numpy()[ok])
     assert np.abs((w0 - w1).cpu().numpy()[ok]).max() <= 1e-7
+
+
+def test_fused_pipeline_full_size(run):
+    """The benchmark's pipelined decomposition + transform at C60 size against
+    the FP64 path's pivots and the separate float-pair calls' factors."""
+    m, L, piv, D, de, Lov, Lp = run
+    L2, piv2, D2, de2, Lov2, Lp2 = G.cds_cd_decompose_to_mo(
+        dev(m.basis.xyz), dev(m.basis.alpha), dev(m.basis.atom.astype(np.int32)), 1e-4,
+        dev(m.C), m.nocc, dev(m.orbitals), max_rank=2048)
+    assert np.array_equal(piv2.cpu().numpy().astype(np.int64), piv)
+    Lf, _, _, _ = G.cds_cd_decompose(dev(m.basis.xyz), dev(m.basis.alpha),
+                                     dev(m.basis.atom.astype(np.int32)), 1e-4, "full",
+                                     max_rank=2048, precision="f32x2")
+    Lov3, Lp3 = G.cds_cd_to_mo(Lf, dev(m.C), m.nocc, dev(m.orbitals), precision="f32x2")
+    assert torch.equal(L2, Lf)
+    # the pipelined transform reads the float-pair rows, the separate one their
+    # FP64 conversion (last-bit rounding, magnified by the cancellation)
+    assert (Lov2 - Lov3).abs().max().item() <= 1e-8 * Lov3.abs().max().item()
+    assert (Lp2 - Lp3).abs().max().item() <= 1e-8 * Lp3.abs().max().item()

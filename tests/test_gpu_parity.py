@@ -262,3 +262,25 @@ def test_cd_stats_counters(precision):
         assert 0 < st["streamed"] < M * (M - 1) // 2
         cont = M - st["passes"]
         assert cont <= st["extra"] <= 3 * cont
+
+
+@pytest.mark.parametrize("name,delta,orbs", [("c1", 1e-5, None), ("c0", 1e-6, []), ("c1", 1e-4, [39, 40])])
+def test_fused_decompose_to_mo_matches_separate_calls(name, delta, orbs):
+    """cds_cd_decompose_to_mo (float-pair CD with the transform overlapped) gives
+    the pivots and vectors of cds_cd_decompose(F32X2) and the factors of
+    cds_cd_to_mo(F32X2) on them.  The pipelined transform reads the float-pair
+    rows directly, the separate one their FP64 conversion, whose rounding the
+    transform's cancellation (|C| ~ 1e3) magnifies: 1e-8 of the largest entry."""
+    m = O.molecule(name)
+    xyz, a, at = basis_dev(m)
+    orb = dev(np.asarray(m.orbitals if orbs is None else orbs, dtype=np.int32))
+    L1, piv1, D1, de1 = G.cds_cd_decompose(xyz, a, at, delta, "full", precision="f32x2")
+    Lov1, Lp1 = G.cds_cd_to_mo(L1, dev(m.C), m.nocc, orb, precision="f32x2")
+    L2, piv2, D2, de2, Lov2, Lp2 = G.cds_cd_decompose_to_mo(xyz, a, at, delta, dev(m.C), m.nocc,
+                                                           orb)
+    assert torch.equal(piv1, piv2) and torch.equal(L1, L2) and torch.equal(D1, D2)
+    assert Lov2.shape == Lov1.shape and Lp2.shape == Lp1.shape
+    scale = Lov1.abs().max().item()
+    assert (Lov1 - Lov2).abs().max().item() <= 1e-8 * scale
+    if Lp1.numel():
+        assert (Lp1 - Lp2).abs().max().item() <= 1e-8 * Lp1.abs().max().item()
