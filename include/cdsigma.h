@@ -430,10 +430,13 @@ int cds_graph_destroy(cds_graph* graph);
  *   CDS_TUNE_ENERGY_CHUNK: energies per epilogue pass of the batched grid
  *     pass, 8 or 16 (default 16);
  *   CDS_TUNE_ITEM_ORDER: 0 = work items interleaved across the persistent
- *     CTAs (default), 1 = each CTA takes a contiguous range.
+ *     CTAs (default), 1 = each CTA takes a contiguous range;
+ *   CDS_TUNE_NEWTON_CACHE: 1 = the batched grid pass keeps the numerators
+ *     and the batched Newton passes evaluate Sigma from them (default), 0 =
+ *     each Newton pass recomputes the integrals.
  * Graphs keep the configuration they were captured with.
  * ---------------------------------------------------------------------- */
-enum { CDS_TUNE_ENERGY_CHUNK = 0, CDS_TUNE_ITEM_ORDER = 1 };
+enum { CDS_TUNE_ENERGY_CHUNK = 0, CDS_TUNE_ITEM_ORDER = 1, CDS_TUNE_NEWTON_CACHE = 2 };
 int cds_tune_set(int32_t knob, int32_t value);   /* CDS_ERR_ARG on an invalid pair */
 int cds_tune_get(int32_t knob);                  /* -1 for an unknown knob */
 

@@ -601,7 +601,7 @@ class BatchGraph:
             self.h = None
 
 
-TUNE_ENERGY_CHUNK, TUNE_ITEM_ORDER = 0, 1
+TUNE_ENERGY_CHUNK, TUNE_ITEM_ORDER, TUNE_NEWTON_CACHE = 0, 1, 2
 
 
 def cds_tune_set(knob: int, value: int) -> None:

@@ -176,10 +176,15 @@ int sigma_qp_stage(int32_t nmol, const std::vector<BatchMol>& bm, const std::vec
     }
     int st = tc_batch_split(nmol, bm.data(), M, off.data(), Lov, Lp, eps, precision, lay.tc, stream);
     if (st) return st;
+    // Newton from cached numerators: the grid pass stores them, or else the
+    // first Newton pass (which recomputes) does
+    const bool cached = tc::tune_newton_cache() != 0;
+    bool have_cache = false;
     if (sigma) {
         st = tc_batch_pass(nmol, bm.data(), 0, tot.E, max_nE, np_all, E, nullptr, precision, sigma,
-                           dsigma, nullptr, lay.tc, stream);
+                           dsigma, nullptr, lay.tc, stream, cached ? 1 : 0);
         if (st) return st;
+        have_cache = cached;
     }
     if (!omega) return CDS_OK;
     const int nb = (int)((np_all + 127) / 128);
@@ -188,9 +193,11 @@ int sigma_qp_stage(int32_t nmol, const std::vector<BatchMol>& bm, const std::vec
     CDS_LAUNCH_CHECK();
     int32_t h_active = (int32_t)np_all;
     for (int32_t it = 0; it < max_iter && (fixed_iters || h_active > 0); ++it) {
+        const int32_t mode = !cached ? 0 : have_cache ? 2 : 1;
         st = tc_batch_pass(nmol, bm.data(), 1, tot.E, max_nE, np_all, omega, lay.active, precision,
-                           lay.sig, lay.dsig, nullptr, lay.tc, stream);
+                           lay.sig, lay.dsig, nullptr, lay.tc, stream, mode);
         if (st) return st;
+        have_cache = cached;
         CDS_CUDA_TRY(cudaMemsetAsync(lay.nactive, 0, sizeof(int32_t), stream));
         k_bqp_step<<<std::max(nb, 1), 128, 0, stream>>>(lay.meta, np_all, eps, orb, lay.sig, lay.dsig,
                                                        conv, omega, pole, iters, status, lay.active,

@@ -554,9 +554,10 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
                             eh[j] = e2.x;
                             el[j] = e2.y;
                         }
-                        if (!BATCH && cache && e0 == 0) {
+                        if (cache && e0 == 0) {
                             // [item][half][column][row]: a warp writes 32 consecutive rows
-                            float* ct = cache + (v.tm.item0 + (item - v.tm.first)) * (int64_t)kCacheTile +
+                            // (item: the call's, or the batch's, running item index)
+                            float* ct = cache + item * (int64_t)kCacheTile +
                                         ((int64_t)(half * 64 + cc) * TB + row);
 #pragma unroll
                             for (int j = 0; j < 16; ++j) ct[(int64_t)j * TB] = num[j];
@@ -785,8 +786,10 @@ bool make_map(CUtensorMap* m, bool bf16, const void* base, uint64_t d0, uint64_t
 // energies per epilogue pass of the batched grid pass, and item order.
 static std::atomic<int> g_energy_chunk{16};
 static std::atomic<int> g_item_order{0};
+static std::atomic<int> g_newton_cache{1};
 int tune_energy_chunk() { return g_energy_chunk.load(); }
 int tune_item_order() { return g_item_order.load(); }
+int tune_newton_cache() { return g_newton_cache.load(); }
 
 // Separate hi.hi / cross accumulators (default) or the shared double-buffered
 // form; CDS_TC_SHARED_ACC=1 selects the latter (for comparisons).
@@ -1266,6 +1269,7 @@ struct BatchLayout {
     float2* E2;                 // [sum np*nE]
     float2* w2;                 // [sum np]  (Newton energies)
     int32_t* err;
+    float* cache;               // [items][kCacheTile] numerators of the grid pass
     size_t bytes;
     int64_t grid_items, newton_items;
 };
@@ -1301,6 +1305,7 @@ static BatchLayout batch_layout(void* ws, int32_t nmol, const BatchMol* mols) {
     l.E2 = c.take<float2>(std::max<int64_t>(E_all, 1));
     l.w2 = c.take<float2>(std::max<int64_t>(np_all, 1));
     l.err = c.take<int32_t>(4);
+    l.cache = c.take<float>((size_t)std::max<int64_t>(part_rows, 1) * kCacheTile);
     l.bytes = c.off;
     l.grid_items = part_rows;
     l.newton_items = part_rows;
@@ -1481,10 +1486,76 @@ int tc_batch_split(int32_t nmol, const BatchMol* mols, const int32_t* M, const B
 // items, then the per-orbital reduction.  pass 0: grid energies E (batch
 // order [mol][orbital][energy]); pass 1: Newton, one energy per orbital from
 // E (batch order [mol][orbital]) with the active mask.
+namespace tc {
+// Newton pass of a batch from the numerators its grid pass stored: as
+// k_sigma_cached, each item's molecule found by binary search over the
+// molecules' first items.
+__global__ void __launch_bounds__(256)
+k_sigma_cached_batch(const MolDesc* __restrict__ mols, int32_t nmol, int64_t nitems,
+                     const float* __restrict__ cache, const float2* __restrict__ w2,
+                     const float2* __restrict__ eps2, const int32_t* __restrict__ active,
+                     double* __restrict__ part) {
+    __shared__ float red[8][2];
+    const int row = threadIdx.x & (TB - 1), half = threadIdx.x / TB;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        int lo = 0, hi = nmol - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (mols[mid].item_begin <= item) lo = mid; else hi = mid - 1;
+        }
+        const MolDesc* md = mols + lo;
+        const int64_t r = item - md->item_begin;
+        int term, t, s, A, B;
+        const TermR tm = decode(md->term[0], md->term[1], r, term, t, s, A, B);
+        if (active && !active[md->act_off + t]) continue;   // the same for the whole block
+        const int x = A * TB + row;
+        const int ybase = B * TB + half * 64;
+        const int ncols = min(64, tm.nx - ybase);
+        float as = 0.f, ad = 0.f;
+        if (x < tm.nx && ncols > 0) {
+            const float2* ev = eps2 + md->eps_off;
+            const float2 es = ev[tm.eps_s_off + s];
+            const float2 ex = ev[tm.eps_x_off + x];
+            const float2 c = df_add(w2[md->E_off + (int64_t)t * md->nE],
+                                    df_add(es, make_float2(-ex.x, -ex.y)));
+            const float* ct = cache + item * kCacheTile + (int64_t)half * 64 * TB + row;
+            const float2* ey2 = ev + tm.eps_x_off + ybase;
+#pragma unroll 8
+            for (int j = 0; j < ncols; ++j) {
+                const float n = ct[(int64_t)j * TB];
+                const float2 e2 = ey2[j];
+                const float d = (c.x - e2.x) + (c.y - e2.y);
+                const float rr = rcp_approx(d);
+                const float tt = n * rr;
+                as += tt;
+                ad = fmaf(-tt, rr, ad);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            as += __shfl_xor_sync(0xffffffffu, as, o);
+            ad += __shfl_xor_sync(0xffffffffu, ad, o);
+        }
+        if (lane == 0) { red[w][0] = as; red[w][1] = ad; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double sv = 0.0, dv = 0.0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) { sv += (double)red[i][0]; dv += (double)red[i][1]; }
+            double* out = part + md->part_base + r * (int64_t)md->nE * 2;
+            out[0] = sv;
+            out[1] = dv;
+        }
+        __syncthreads();
+    }
+}
+}  // namespace tc
+
 int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_total,
                   int32_t max_nE, int64_t np_total, const double* E, const int32_t* active,
                   int32_t precision, double* sigma, double* dsigma, unsigned long long* stamps,
-                  void* ws, cudaStream_t stream) {
+                  void* ws, cudaStream_t stream, int32_t cache_mode) {
     using namespace tc;
     const bool bf16 = precision == CDS_PREC_BF16X3;
     BatchLayout lay = batch_layout(ws, nmol, mols);
@@ -1496,7 +1567,12 @@ int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_t
     }
     const MolDesc* set = pass == 0 ? lay.grid_set : lay.newton_set;
     const int64_t nitems = lay.grid_items;
-    if (nitems > 0) {
+    if (nitems > 0 && cache_mode == 2) {
+        const int grid = (int)std::min<int64_t>(nitems, 8LL * device_sms());
+        k_sigma_cached_batch<<<grid, 256, 0, stream>>>(set, nmol, nitems, lay.cache, Ep, lay.eps2,
+                                                       active, lay.part);
+        CDS_LAUNCH_CHECK();
+    } else if (nitems > 0) {
         const int grid = (int)std::min<int64_t>(nitems, device_sms());
         Maps dummy_maps;
         memset(&dummy_maps, 0, sizeof(dummy_maps));
@@ -1513,7 +1589,8 @@ int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_t
         CDS_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
         kern<<<grid, THREADS, SMEM_BYTES, stream>>>(dummy_maps, dummy, set, nmol, nitems, Ep, epsv,
                                                     pass == 1 ? active : nullptr, nullptr, lay.part,
-                                                    stamps, lay.err, order, nullptr);
+                                                    stamps, lay.err, order,
+                                                    cache_mode == 1 ? lay.cache : nullptr);
         CDS_LAUNCH_CHECK();
     }
     if (np_total > 0) {
@@ -1539,6 +1616,11 @@ extern "C" int cds_tune_set(int32_t knob, int32_t value) {
         g_item_order = value;
         return CDS_OK;
     }
+    if (knob == CDS_TUNE_NEWTON_CACHE) {
+        if (value != 0 && value != 1) return CDS_ERR_ARG;
+        g_newton_cache = value;
+        return CDS_OK;
+    }
     return CDS_ERR_ARG;
 }
 
@@ -1546,5 +1628,6 @@ extern "C" int cds_tune_get(int32_t knob) {
     using namespace cds::tc;
     if (knob == CDS_TUNE_ENERGY_CHUNK) return g_energy_chunk.load();
     if (knob == CDS_TUNE_ITEM_ORDER) return g_item_order.load();
+    if (knob == CDS_TUNE_NEWTON_CACHE) return g_newton_cache.load();
     return -1;
 }

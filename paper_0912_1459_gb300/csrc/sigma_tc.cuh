@@ -46,10 +46,15 @@ int tc_batch_setup(int32_t nmol, const BatchMol* mols, const int32_t* M, int32_t
 int tc_batch_split(int32_t nmol, const BatchMol* mols, const int32_t* M, const BatchOffsets* off,
                    const double* Lov, const double* Lp, const double* eps, int32_t precision,
                    void* ws, cudaStream_t stream);
+// cache_mode: 0 none, 1 the tensor-core pass also stores the numerators,
+// 2 Sigma from the stored numerators (Newton passes only).
 int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_total,
                   int32_t max_nE, int64_t np_total, const double* E, const int32_t* active,
                   int32_t precision, double* sigma, double* dsigma, unsigned long long* stamps,
-                  void* ws, cudaStream_t stream);
+                  void* ws, cudaStream_t stream, int32_t cache_mode);
+namespace tc {
+int tune_newton_cache();   // CDS_TUNE_NEWTON_CACHE
+}
 
 inline bool is_split16(int32_t precision) {
     return precision == CDS_PREC_BF16X3 || precision == CDS_PREC_FP16X3;

@@ -5,10 +5,11 @@ Eight clusters of the batched workload (centre counts U{4..40}, 10
 s-Gaussians each, o = N/5, delta = 1e-5, U{4..16} orbitals on U{8..64}
 energies).  The batch reproduces the single-molecule results: the same
 pivots and Cholesky vectors, the same transform, the self-energy and Newton
-results of the same tensor-core kernel within 1e-12 (only the order items
-are scheduled in differs), and one molecule against the FP64 oracle within
-the mixed-precision bar.  The captured CUDA graph replays to the same
-results, twice in a row.
+results of the same kernels within 1e-12 (only the order items are
+scheduled in differs; Newton from the cached numerators, and with the
+recomputing passes), and one molecule against the FP64 oracle within the
+mixed-precision bar.  The captured CUDA graph replays to the same results,
+twice in a row.
 """
 import numpy as np
 import pytest
@@ -54,13 +55,17 @@ def batch():
     return mols, b, M, dict(xyz=xyz, al=al, at=at, C=Cc, eps=eps, orb=orb, E=E)
 
 
-def single(m):
+def single(m, cached=True):
     L, piv, D, de = G.cds_cd_decompose(dev(m.basis.xyz), dev(m.basis.alpha),
                                        dev(m.basis.atom.astype(np.int32)), m.delta, "full")
     Lov, Lp = G.cds_cd_to_mo(L, dev(m.C), m.nocc, dev(m.orbitals), precision="f32x2")
     E = dev(W.energy_grid(m.eps[m.orbitals], m.nE))
-    s, ds = G.cds_sigma2_diag(Lov, Lp, dev(m.eps), m.nocc, E, "bf16x3")
-    w, P, it, st = G.cds_qp_solve(Lov, Lp, dev(m.orbitals), dev(m.eps), m.nocc, precision="bf16x3")
+    s, ds, cache = G.cds_sigma2_diag_cache(Lov, Lp, dev(m.eps), m.nocc, E, "bf16x3")
+    if cached:
+        w, P, it, st = G.cds_qp_solve_cached(cache, dev(m.orbitals), dev(m.eps), m.nbf, m.nocc)
+    else:
+        w, P, it, st = G.cds_qp_solve(Lov, Lp, dev(m.orbitals), dev(m.eps), m.nocc,
+                                      precision="bf16x3")
     return L, piv, Lov, Lp, s, w, P, it, st
 
 
@@ -79,6 +84,27 @@ def test_batch_matches_single_molecule_calls(batch):
         torch.testing.assert_close(b.view("omega", c, (np_,)), w, rtol=0, atol=1e-12)
         assert torch.equal(b.view("iters", c, (np_,)), it)
         assert torch.equal(b.view("status", c, (np_,)), st)
+
+
+def test_batch_recomputing_newton_matches_single_calls(batch):
+    """CDS_TUNE_NEWTON_CACHE = 0: the batched Newton passes recompute the
+    integrals, like cds_qp_solve."""
+    mols, b, M, inp = batch
+    G.cdsigma.cds_tune_set(G.cdsigma.TUNE_NEWTON_CACHE, 0)
+    try:
+        b.sigma2(inp["eps"], inp["E"])
+        b.qp_solve(inp["orb"], inp["eps"])
+        torch.cuda.synchronize()
+        for c, m in enumerate(mols):
+            *_, w, P, it, st = single(m, cached=False)
+            np_ = len(m.orbitals)
+            torch.testing.assert_close(b.view("omega", c, (np_,)), w, rtol=0, atol=1e-12)
+            assert torch.equal(b.view("status", c, (np_,)), st)
+    finally:
+        G.cdsigma.cds_tune_set(G.cdsigma.TUNE_NEWTON_CACHE, 1)
+        b.sigma2(inp["eps"], inp["E"])
+        b.qp_solve(inp["orb"], inp["eps"])
+        torch.cuda.synchronize()
 
 
 def test_batch_molecule_against_oracle(batch):
