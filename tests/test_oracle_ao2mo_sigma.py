@@ -163,3 +163,35 @@ def test_newton_reports_non_convergence(c0):
         return s[0], ds[0]
     w, P, it, st = qp.newton_qp(f, m.eps[5], conv=1e-5, max_iter=1)
     assert st == qp.QP_NO_CONVERGENCE and it == 1
+
+
+def test_bracketed_qp_finds_the_unique_root_of_the_pole_free_interval(c0):
+    """Safeguarded Newton: its root is the one brentq finds between the two
+    poles nearest e_q (an independent bracketing solver), with 0 < P <= 1;
+    where plain Newton stays in that interval it finds the same root; the
+    bracket comes from a direct loop over the Eq. SE denominators."""
+    m, pd, r, g4, Lov, Lp = c0
+    found = 0
+    for q in range(m.nbf):
+        def f(x, q=q):
+            a, d = sigma2.sigma2_from_factors(Lp[q], Lov, m.eps, m.nocc, [x])
+            return a[0], d[0]
+        lo, hi = qp.pole_bracket(m.eps, m.nocc, m.eps[q])
+        # the bracket by a plain loop over every denominator
+        o = m.nocc
+        den = [m.eps[i] + m.eps[j] - m.eps[a] for i in range(o) for j in range(o)
+               for a in range(o, m.nbf)]
+        den += [m.eps[a] + m.eps[b] - m.eps[i] for a in range(o, m.nbf) for b in range(o, m.nbf)
+                for i in range(o)]
+        den = np.array(den)
+        assert lo == den[den < m.eps[q]].max() and hi == den[den > m.eps[q]].min()
+        w, P, it, st = qp.bracketed_qp(f, m.eps[q], lo, hi, conv=1e-12, max_iter=200)
+        assert st == qp.QP_OK and lo < w < hi and 0 < P <= 1
+        root = brentq(lambda x: x - m.eps[q] - f(x)[0], lo + 1e-12 * abs(lo), hi - 1e-12 * abs(hi),
+                      xtol=1e-14)
+        assert abs(w - root) <= 1e-10
+        wn, Pn, itn, stn = qp.newton_qp(f, m.eps[q], conv=1e-12, max_iter=200)
+        if stn == qp.QP_OK and lo < wn < hi:
+            assert abs(wn - w) <= 1e-10
+            found += 1
+    assert found >= 1
