@@ -483,6 +483,20 @@ def run_ours(args, dist: Dist):
                                    "fp64_lower_bound": n_orb / fp64_stage_s},
         }
 
+    # ---- safeguarded Newton on the same numerators (quasiparticle roots) ----
+    bracketed = None
+    if cached:
+        torch.cuda.synchronize()
+        a0 = time.perf_counter()
+        wb, Pb, itb, stb, brb = G.cds_qp_solve_bracketed_cached(cache, orbs, eps, m.nbf, m.nocc)
+        torch.cuda.synchronize()
+        bracketed = {"ms": (time.perf_counter() - a0) * 1e3,
+                     "iters": itb.cpu().tolist(), "status": stb.cpu().tolist(),
+                     "omega_Ha": wb.cpu().numpy().tolist(), "pole": Pb.cpu().numpy().tolist(),
+                     "note": "Newton kept inside the pole-free interval around each e_q "
+                             "(cds_qp_solve_bracketed_cached): the quasiparticle root of every "
+                             "orbital; wall time incl. the host-side bracket"}
+
     # ---- MP2 correlation energy (Eq. MP2) on the same factors ----
     mp2 = None
     if not args.no_mp2:
@@ -510,6 +524,7 @@ def run_ours(args, dist: Dist):
         "peaks": pk,
         "fp64_arm": fp64,
         "mp2": mp2,
+        "bracketed_newton": bracketed,
     }
     if not args.no_batched:
         result["batched"] = run_batched(args, device)

@@ -292,6 +292,23 @@ int cds_qp_solve_cached(int32_t nmo, int32_t nocc, int32_t np, const int32_t* or
                         int32_t* status, void* workspace, size_t workspace_bytes,
                         cudaStream_t stream);
 
+/* Safeguarded Newton from cached numerators (not in the paper; a variant of
+ * Eq. iter).  Every pole of Sigma_qq lies at e_i + e_j - e_a or e_a + e_b -
+ * e_i, and between neighbouring poles f(w) = w - e_q - Sigma(w) rises from
+ * -inf to +inf, so the interval around e_q holds exactly one root: the
+ * quasiparticle solution connected to the orbital.  From w = e_q the Newton
+ * step is kept while it stays inside the current bracket of that root and
+ * replaced by the midpoint otherwise.  bracket (device, [np][2], caller-
+ * owned) receives the final bracket; the initial one (the nearest poles, a
+ * side without a pole taken 10 Ha away) is formed on the host.  Blocking;
+ * otherwise as cds_qp_solve_cached. */
+int cds_qp_solve_bracketed_cached(int32_t nmo, int32_t nocc, int32_t np, const int32_t* orb,
+                                  const double* eps, double conv, int32_t max_iter,
+                                  const void* cache, size_t cache_bytes, double* omega,
+                                  double* pole, int32_t* iters, int32_t* status,
+                                  double* bracket, void* workspace, size_t workspace_bytes,
+                                  cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * MP2 correlation energy (paper Eq. MP2), the ground-state companion of
  * Eq. SE on the same factors:

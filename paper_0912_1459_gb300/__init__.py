@@ -5,10 +5,10 @@ of ``include/cdsigma.h``; ``cdsigma`` is its thin binding.
 """
 from .cdsigma import (CdsError, cds_cd_decompose, cds_cd_decompose_to_mo, cds_cd_stats, cds_cd_to_mo, cds_eri_columns,
                       cds_eri_diag, cds_launch_count, cds_mp2_energy, cds_qp_solve,
-                      cds_qp_solve_cached, cds_sigma2_diag, cds_sigma2_diag_cache, cds_version,
+                      cds_qp_solve_bracketed_cached, cds_qp_solve_cached, cds_sigma2_diag, cds_sigma2_diag_cache, cds_version,
                       declared_symbols, load, npair)
 
 __all__ = ["CdsError", "cds_cd_decompose", "cds_cd_decompose_to_mo", "cds_cd_stats", "cds_cd_to_mo", "cds_eri_columns",
            "cds_eri_diag", "cds_launch_count", "cds_mp2_energy", "cds_qp_solve",
-           "cds_qp_solve_cached", "cds_sigma2_diag", "cds_sigma2_diag_cache", "cds_version",
+           "cds_qp_solve_bracketed_cached", "cds_qp_solve_cached", "cds_sigma2_diag", "cds_sigma2_diag_cache", "cds_version",
            "declared_symbols", "load", "npair"]

@@ -66,6 +66,8 @@ _SIGNATURES = {
     "cds_qp_cached_workspace_bytes": (_sz, [_i32, _i32, _i32]),
     "cds_qp_solve_cached": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _f64, _i32, _vp, _sz, _vp, _vp,
                                            _vp, _vp, _vp, _sz, _vp]),
+    "cds_qp_solve_bracketed_cached": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _f64, _i32, _vp, _sz,
+                                                     _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "cds_mp2_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32]),
     "cds_mp2_energy": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
 }
@@ -461,6 +463,35 @@ def cds_qp_solve_cached(cache: torch.Tensor, orbitals: torch.Tensor, eps: torch.
         st = CDS_OK
     _check(st, "cds_qp_solve_cached")
     return omega, pole, iters, status
+
+
+def cds_qp_solve_bracketed_cached(cache: torch.Tensor, orbitals: torch.Tensor, eps: torch.Tensor,
+                                  nmo: int, nocc: int, conv: float = 1e-5, max_iter: int = 100,
+                                  workspace: Optional[torch.Tensor] = None,
+                                  raise_on_nonconvergence: bool = False):
+    """Safeguarded Newton inside the pole-free interval around each e_q, Sigma
+    from cached numerators.  Returns (omega, pole, iters, status, bracket [np, 2])."""
+    lib = load()
+    orb = _dev(orbitals, torch.int32, "orbitals")
+    eps = _dev(eps, torch.float64, "eps")
+    dev = orb.device
+    np_ = orb.shape[0]
+    omega = torch.empty(np_, dtype=torch.float64, device=dev)
+    pole = torch.empty(np_, dtype=torch.float64, device=dev)
+    iters = torch.empty(np_, dtype=torch.int32, device=dev)
+    status = torch.empty(np_, dtype=torch.int32, device=dev)
+    bracket = torch.empty((np_, 2), dtype=torch.float64, device=dev)
+    need = lib.cds_qp_cached_workspace_bytes(nmo, nocc, np_)
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    st = lib.cds_qp_solve_bracketed_cached(nmo, nocc, np_, _p(orb), _p(eps), float(conv),
+                                           int(max_iter), _p(cache), cache.numel(), _p(omega),
+                                           _p(pole), _p(iters), _p(status), _p(bracket),
+                                           _p(workspace), workspace.numel(), _stream(dev))
+    if st == 5 and not raise_on_nonconvergence:
+        st = CDS_OK
+    _check(st, "cds_qp_solve_bracketed_cached")
+    return omega, pole, iters, status, bracket
 
 
 def cds_mp2_energy(Lov: torch.Tensor, eps: torch.Tensor, nocc: int, precision: str = "fp64",

@@ -5,6 +5,10 @@
 // MO integrals from the factors), then a single small kernel applies
 //   P = 1/(1 - dSigma/dw),  w_new = w + (e_q + Sigma(w) - w) P
 // in FP64 and retires orbitals with |w_new - w| <= conv.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "sigma_tc.cuh"
 
 namespace cds {
@@ -166,6 +170,146 @@ extern "C" int cds_qp_solve_cached(int32_t nmo, int32_t nocc, int32_t np, const 
         CDS_CUDA_TRY(cudaMemsetAsync(lay.nactive, 0, sizeof(int32_t), stream));
         k_qp_step<<<nb, 128, 0, stream>>>(eps, orb, np, lay.sig, lay.dsig, conv, omega, pole,
                                           iters, status, lay.active, lay.nactive);
+        CDS_LAUNCH_CHECK();
+        CDS_CUDA_TRY(cudaMemcpyAsync(&h_active, lay.nactive, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, stream));
+        CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    return h_active > 0 ? CDS_ERR_NO_CONVERGENCE : CDS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Safeguarded Newton (not in the paper): every pole of Sigma_qq lies at
+// e_i + e_j - e_a or e_a + e_b - e_i, and between neighbouring poles
+// f(w) = w - e_q - Sigma(w) rises from -inf to +inf (all residues >= 0), so
+// the interval around e_q holds one root.  The Newton step is kept while it
+// stays inside the current bracket of that root, otherwise the step bisects.
+// ---------------------------------------------------------------------------
+namespace cds {
+namespace {
+
+// Nearest poles below / above e (strict).  Poles are s - z with s a sum of
+// two occupied (z virtual) or two virtual (z occupied) energies; with the
+// pair sums sorted, for each z the pair sum that brings s - z closest to e on
+// either side is found by binary search (then checked in the same floating
+// point as the poles are formed, (e_x + e_y) - e_z).
+struct PoleSets {
+    std::vector<double> soo, svv, eo, ev;   // sorted pair sums and energies
+};
+
+PoleSets pole_sets(const std::vector<double>& e, int32_t nocc) {
+    PoleSets p;
+    p.eo.assign(e.begin(), e.begin() + nocc);
+    p.ev.assign(e.begin() + nocc, e.end());
+    for (double x : p.eo)
+        for (double y : p.eo) p.soo.push_back(x + y);
+    for (double x : p.ev)
+        for (double y : p.ev) p.svv.push_back(x + y);
+    std::sort(p.soo.begin(), p.soo.end());
+    std::sort(p.svv.begin(), p.svv.end());
+    return p;
+}
+
+void pole_bracket_host(const PoleSets& ps, double e, double* lo, double* hi) {
+    double L = -INFINITY, H = INFINITY;
+    auto scan = [&](const std::vector<double>& S, const std::vector<double>& Z) {
+        if (S.empty()) return;
+        for (double z : Z) {
+            // below: the largest s with s - z < e
+            auto it = std::lower_bound(S.begin(), S.end(), e + z);
+            for (auto k = it; k != S.end() && *k - z < e; ++k) L = std::max(L, *k - z);
+            while (it != S.begin()) {
+                --it;
+                if (*it - z < e) { L = std::max(L, *it - z); break; }
+            }
+            // above: the smallest s with s - z > e
+            auto jt = std::upper_bound(S.begin(), S.end(), e + z);
+            for (auto k = jt; k != S.begin() && *(k - 1) - z > e; --k) H = std::min(H, *(k - 1) - z);
+            for (; jt != S.end(); ++jt)
+                if (*jt - z > e) { H = std::min(H, *jt - z); break; }
+        }
+    };
+    scan(ps.soo, ps.ev);   // e_i + e_j - e_a
+    scan(ps.svv, ps.eo);   // e_a + e_b - e_i
+    *lo = std::isfinite(L) ? L : e - 10.0;
+    *hi = std::isfinite(H) ? H : e + 10.0;
+}
+
+__global__ void k_qp_step_bracketed(const double* __restrict__ eps, const int32_t* __restrict__ orb,
+                                    int32_t np, const double* __restrict__ sig,
+                                    const double* __restrict__ dsig, double conv, double* omega,
+                                    double* pole, double* brk, int32_t* iters, int32_t* status,
+                                    int32_t* active, int32_t* nactive) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= np || !active[t]) return;
+    const double w = omega[t], eq = eps[orb[t]];
+    const double f = w - eq - sig[t], fp = 1.0 - dsig[t];
+    double lo = brk[2 * t], hi = brk[2 * t + 1];
+    if (f < 0.0) lo = w; else hi = w;
+    double wn = w - f / fp;
+    if (!(lo < wn && wn < hi)) wn = 0.5 * (lo + hi);
+    brk[2 * t] = lo;
+    brk[2 * t + 1] = hi;
+    iters[t] += 1;
+    pole[t] = 1.0 / fp;
+    omega[t] = wn;
+    if (!isfinite(wn)) {
+        status[t] = CDS_QP_NONFINITE;
+        active[t] = 0;
+    } else if (fabs(wn - w) <= conv) {
+        status[t] = CDS_QP_OK;
+        active[t] = 0;
+    } else {
+        atomicAdd(nactive, 1);
+    }
+}
+
+}  // namespace
+}  // namespace cds
+
+extern "C" int cds_qp_solve_bracketed_cached(int32_t nmo, int32_t nocc, int32_t np,
+                                             const int32_t* orb, const double* eps, double conv,
+                                             int32_t max_iter, const void* cache,
+                                             size_t cache_bytes, double* omega, double* pole,
+                                             int32_t* iters, int32_t* status, double* bracket,
+                                             void* workspace, size_t workspace_bytes,
+                                             cudaStream_t stream) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || np < 0 || np > 65535 || max_iter < 1 ||
+        !(conv >= 0.0))
+        return CDS_ERR_ARG;
+    if (np == 0) return CDS_OK;
+    if (!orb || !eps || !omega || !pole || !iters || !status || !bracket || !cache)
+        return CDS_ERR_ARG;
+    if (cache_bytes < tc_cache_bytes(nmo, nocc, np)) return CDS_ERR_ARG;
+    QpLayout lay = qp_cached_layout(workspace, nmo, nocc, np);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    // brackets on the host from the orbital energies
+    std::vector<double> e(nmo), br(2 * (size_t)np);
+    std::vector<int32_t> o(np);
+    CDS_CUDA_TRY(cudaMemcpyAsync(e.data(), eps, sizeof(double) * nmo, cudaMemcpyDeviceToHost, stream));
+    CDS_CUDA_TRY(cudaMemcpyAsync(o.data(), orb, sizeof(int32_t) * np, cudaMemcpyDeviceToHost, stream));
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    const PoleSets ps = pole_sets(e, nocc);
+    for (int32_t t = 0; t < np; ++t) {
+        const double eq = (o[t] >= 0 && o[t] < nmo) ? e[o[t]] : NAN;
+        pole_bracket_host(ps, eq, &br[2 * t], &br[2 * t + 1]);
+    }
+    CDS_CUDA_TRY(cudaMemcpyAsync(bracket, br.data(), sizeof(double) * 2 * np,
+                                 cudaMemcpyHostToDevice, stream));
+    const int nb = (np + 127) / 128;
+    k_qp_init<<<nb, 128, 0, stream>>>(eps, orb, np, nmo, omega, pole, iters, status, lay.active,
+                                      lay.nactive);
+    CDS_LAUNCH_CHECK();
+    int32_t h_active = np;
+    for (int32_t it = 0; it < max_iter && h_active > 0; ++it) {
+        int st = sigma2_cached(nmo, nocc, np, eps, omega, lay.active,
+                               static_cast<const float*>(cache), lay.sig, lay.dsig, lay.sigma_ws,
+                               stream, it == 0);
+        if (st) return st;
+        CDS_CUDA_TRY(cudaMemsetAsync(lay.nactive, 0, sizeof(int32_t), stream));
+        k_qp_step_bracketed<<<nb, 128, 0, stream>>>(eps, orb, np, lay.sig, lay.dsig, conv, omega,
+                                                    pole, bracket, iters, status, lay.active,
+                                                    lay.nactive);
         CDS_LAUNCH_CHECK();
         CDS_CUDA_TRY(cudaMemcpyAsync(&h_active, lay.nactive, sizeof(int32_t),
                                      cudaMemcpyDeviceToHost, stream));

@@ -223,3 +223,28 @@ def test_fused_pipeline_full_size(run):
     # FP64 conversion (last-bit rounding, magnified by the cancellation)
     assert (Lov2 - Lov3).abs().max().item() <= 1e-8 * Lov3.abs().max().item()
     assert (Lp2 - Lp3).abs().max().item() <= 1e-8 * Lp3.abs().max().item()
+
+
+def test_bracketed_newton_full_size(run):
+    """Safeguarded Newton at C60 size: every orbital converges inside its
+    pole-free interval with 0 < P <= 1; the HOMO against the oracle's bracketed
+    solve on the GPU's factors within 0.1 meV."""
+    from oracle import qp
+    m, L, piv, D, de, Lov, Lp = run
+    eps, orbs = dev(m.eps), dev(m.orbitals)
+    E = dev(W.energy_grid(m.eps[m.orbitals], 2))
+    _, _, cache = G.cds_sigma2_diag_cache(Lov, Lp, eps, m.nocc, E, "bf16x3")
+    w, P, it, st, br = G.cds_qp_solve_bracketed_cached(cache, orbs, eps, m.nbf, m.nocc)
+    w, P, st = w.cpu().numpy(), P.cpu().numpy(), st.cpu().numpy()
+    assert np.all(st == 0) and np.all((P > 0) & (P <= 1))
+    t = int(np.where(m.orbitals == m.nocc - 1)[0][0])     # HOMO
+    q = int(m.orbitals[t])
+    lo, hi = qp.pole_bracket(m.eps, m.nocc, m.eps[q])
+    assert lo < w[t] < hi
+    rov, rp = Lov.cpu().numpy(), Lp[t].cpu().numpy()
+
+    def f(x):
+        a, d = sigma2.sigma2_from_factors(rp, rov, m.eps, m.nocc, [x])
+        return a[0], d[0]
+    wr, Pr, itr, str_ = qp.bracketed_qp(f, m.eps[q], lo, hi)
+    assert str_ == 0 and abs(w[t] - wr) <= TOL_QP

@@ -65,3 +65,32 @@ def test_cache_too_small_is_rejected():
     small = torch.empty(16, dtype=torch.uint8, device=DEV)
     with pytest.raises(G.CdsError):
         G.cds_qp_solve_cached(small, dev(m.orbitals), dev(m.eps), m.nbf, m.nocc)
+
+
+@pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-5)])
+def test_bracketed_newton_against_oracle(name, delta):
+    """Safeguarded Newton (cds_qp_solve_bracketed_cached, BF16X3 numerators)
+    against the oracle's bracketed solve on the same factors: every orbital
+    converges, inside the oracle's pole-free interval, within 0.1 meV of the
+    oracle's root, with the same pole strength to 1e-4."""
+    from oracle import qp, sigma2
+    m = O.molecule(name)
+    ref = O.decomposition(name, delta)
+    Lov, Lp = O.factors(name, ref.L)
+    eps, orbs = dev(m.eps), dev(m.orbitals)
+    import workloads as W
+    E = dev(W.energy_grid(m.eps[m.orbitals], 4))
+    _, _, cache = G.cds_sigma2_diag_cache(dev(Lov), dev(Lp), eps, m.nocc, E, "bf16x3")
+    w, P, it, st, br = G.cds_qp_solve_bracketed_cached(cache, orbs, eps, m.nbf, m.nocc)
+    w, P, st, br = w.cpu().numpy(), P.cpu().numpy(), st.cpu().numpy(), br.cpu().numpy()
+    for t, q in enumerate(m.orbitals):
+        lo, hi = qp.pole_bracket(m.eps, m.nocc, m.eps[q])
+
+        def f(x, t=t):
+            a, d = sigma2.sigma2_from_factors(Lp[t], Lov, m.eps, m.nocc, [x])
+            return a[0], d[0]
+        wr, Pr, itr, str_ = qp.bracketed_qp(f, m.eps[q], lo, hi)
+        assert st[t] == 0 and str_ == 0
+        assert lo < w[t] < hi and br[t, 0] <= w[t] <= br[t, 1]
+        assert abs(w[t] - wr) <= TOL_QP
+        assert abs(P[t] - Pr) <= 1e-4 * abs(Pr)
