@@ -48,7 +48,7 @@ typedef enum {
     CDS_ERR_WORKSPACE = 6,      /* workspace smaller than *_workspace_bytes() */
     CDS_ERR_UNSUPPORTED = 7,    /* device or precision mode not supported */
     CDS_ERR_TIMEOUT = 8,        /* a bounded device-side wait gave up */
-    CDS_ERR_CAPACITY = 9        /* problem too large for the allocation-free entry point */
+    CDS_ERR_CAPACITY = 9        /* a fixed-capacity output or static scratch is too small */
 } cds_status;
 
 typedef enum { CDS_SCHEME_FULL = 0, CDS_SCHEME_ATOMIC = 1 } cds_scheme;
@@ -195,6 +195,41 @@ int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double
                  const double* C, const int32_t* orb, int32_t np, int32_t precision,
                  double* Lov, double* Lp, void* workspace, size_t workspace_bytes,
                  cudaStream_t stream);
+
+/* ------------------------------------------------------------------------
+ * Atomic Cholesky basis and the V-approximation (paper Sec. II.A, atomic CD;
+ * Eq. int_approx, Eq. error_approx).  For every unique atom (the exponents
+ * of the functions on one centre, in basis order) the isolated atom's one-
+ * centre ERI matrix is decomposed by the pivot rule of cds_cd_decompose at
+ * delta; its pivots, on every atom of that type, are the basis densities
+ * rho~_K.  With the metric V_KL = (rho~_K|rho~_L) = L_m L_m^T,
+ *   B = L_m^-1 (rho~|rho_I),  (rho_I|rho_J) ~ sum_K B^K_I B^K_J,
+ * the factor form of Eq. CD: B goes to cds_cd_to_mo in place of L (M = naux).
+ * ---------------------------------------------------------------------- */
+
+/* Workspace of cds_acd_aux_pairs for atoms of at most max_atom_funcs functions. */
+size_t cds_acd_workspace_bytes(int32_t max_atom_funcs);
+
+/* Blocking.  Inputs (device): alpha [nbf], atom [nbf] (centre of each
+ * function).  Output (host, caller-owned): aux [capacity] packed pair indices
+ * of the basis densities, centres ascending, each centre's in its type's
+ * pivot order; *naux their number.  CDS_ERR_CAPACITY if more than capacity
+ * (*naux still set).  Atoms must fit cds_cd_static_max_nbf(). */
+int cds_acd_aux_pairs(int32_t nbf, const double* alpha, const int32_t* atom, double delta,
+                      int32_t* aux, int32_t capacity, int32_t* naux, void* workspace,
+                      size_t workspace_bytes, cudaStream_t stream);
+
+size_t cds_ri_workspace_bytes(int32_t naux);
+
+/* Blocking.  Inputs (device): xyz, alpha as cds_cd_decompose; aux [naux]
+ * (naux <= 4096) packed pair indices of the basis densities.  Output
+ * (device, caller-owned): B [naux][npair].  CDS_ERR_NOT_PD if the metric is
+ * not positive definite to working precision (a Cholesky pivot at or below
+ * 1e-12 x its diagonal, e.g. a density listed twice); CDS_ERR_ARG on an
+ * index outside the basis. */
+int cds_ri_factors(int32_t nbf, const double* xyz, const double* alpha, const int32_t* aux,
+                   int32_t naux, double* B, void* workspace, size_t workspace_bytes,
+                   cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * Decomposition and transform in one call (float-pair form).  Runs

@@ -60,6 +60,11 @@ _SIGNATURES = {
     "cds_cd_decompose_to_mo": (ctypes.c_int, [_i32, _vp, _vp, _vp, _f64, _i32, _i32, _vp, _i32, _i32,
                                               _vp, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32),
                                               ctypes.POINTER(_f64), _vp, _vp, _vp, _sz, _vp]),
+    "cds_acd_workspace_bytes": (_sz, [_i32]),
+    "cds_acd_aux_pairs": (ctypes.c_int, [_i32, _vp, _vp, _f64, _vp, _i32, ctypes.POINTER(_i32), _vp,
+                                         _sz, _vp]),
+    "cds_ri_workspace_bytes": (_sz, [_i32]),
+    "cds_ri_factors": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _sz, _vp]),
     "cds_sigma2_cache_bytes": (_sz, [_i32, _i32, _i32]),
     "cds_sigma2_diag_cache": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _i32,
                                              _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
@@ -287,6 +292,43 @@ def cds_cd_decompose_to_mo(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.T
     Lov = Lov_out.view(-1)[:nocc * nv * Mv].view(nocc, nv, Mv)
     Lp = Lp_out.view(-1)[:np_ * nmo * Mv].view(np_, nmo, Mv)
     return L_out[:Mv], piv[:Mv], D, de.value, Lov, Lp
+
+
+def cds_acd_aux_pairs(alpha: torch.Tensor, atom: torch.Tensor, delta: float) -> torch.Tensor:
+    """Packed pair indices of the atomic Cholesky basis (Sec. II.A, atomic CD),
+    as an int32 tensor on the basis' device."""
+    lib = load()
+    alpha = _dev(alpha, torch.float64, "alpha")
+    atom = _dev(atom, torch.int32, "atom")
+    dev = alpha.device
+    n = alpha.shape[0]
+    na = int(torch.bincount(atom.long()).max().item()) if n else 1
+    ws = _workspace(lib.cds_acd_workspace_bytes(na), dev)
+    cap = n * (n + 1) // 2
+    out = (ctypes.c_int32 * max(cap, 1))()
+    cnt = _i32(0)
+    st = lib.cds_acd_aux_pairs(n, _p(alpha), _p(atom), float(delta), out, cap, ctypes.byref(cnt),
+                               _p(ws), ws.numel(), _stream(dev))
+    _check(st, "cds_acd_aux_pairs")
+    return torch.tensor(list(out[:cnt.value]), dtype=torch.int32, device=dev)
+
+
+def cds_ri_factors(xyz: torch.Tensor, alpha: torch.Tensor, aux: torch.Tensor) -> torch.Tensor:
+    """B [naux, npair]: the V-approximation (Eq. int_approx) over the basis
+    densities aux, in the factor form of the Cholesky vectors."""
+    lib = load()
+    xyz = _dev(xyz, torch.float64, "xyz")
+    alpha = _dev(alpha, torch.float64, "alpha")
+    aux = _dev(aux, torch.int32, "aux")
+    dev = alpha.device
+    n = alpha.shape[0]
+    naux = aux.shape[0]
+    B = torch.empty((naux, npair(n)), dtype=torch.float64, device=dev)
+    ws = _workspace(lib.cds_ri_workspace_bytes(naux), dev)
+    st = lib.cds_ri_factors(n, _p(xyz), _p(alpha), _p(aux), naux, _p(B), _p(ws), ws.numel(),
+                            _stream(dev))
+    _check(st, "cds_ri_factors")
+    return B
 
 
 def cds_cd_stats(nbf: int, workspace: torch.Tensor, precision: str = "fp64") -> dict:

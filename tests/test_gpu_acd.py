@@ -1,0 +1,107 @@
+"""Atomic Cholesky basis and the V-approximation (Sec. II.A atomic CD,
+Eq. int_approx, Eq. error_approx) on the GPU against the oracle.
+
+The oracle's basis and factors are pinned in test_oracle_acd.py.  Here:
+* cds_acd_aux_pairs equals oracle acd.aux_pairs exactly (integer work);
+* cds_ri_factors: B element by element within 1e-10 of the largest |B| (the
+  Cholesky factor of the metric and the forward substitution are unique), and
+  B^T B on the basis densities reproduces their exact columns;
+* Eq. error_approx on the GPU's B: every one-centre density's error is <= delta
+  (the isolated atoms' bound) and no diagonal error is negative;
+* the whole method with B in place of the Cholesky vectors (transform,
+  Newton) agrees with the oracle run on the oracle's B (roots within 1e-8 Ha);
+* edge cases: an index outside the basis and an empty basis.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle_pipeline as O
+from oracle import acd, eri
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_0912_1459_gb300 as G  # noqa: E402
+
+DEV = torch.device("cuda:0")
+CASES = [("c0", 1e-6), ("c0", 1e-3), ("c1", 1e-4)]
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def gpu_basis(name, delta):
+    m = O.molecule(name)
+    aux = G.cds_acd_aux_pairs(dev(m.basis.alpha), dev(m.basis.atom.astype(np.int32)), delta)
+    return m, aux
+
+
+@pytest.mark.parametrize("name,delta", CASES)
+def test_aux_pairs_match_oracle(name, delta):
+    m, aux = gpu_basis(name, delta)
+    ref = acd.aux_pairs(m.basis.alpha, m.basis.atom, delta)
+    assert aux.cpu().numpy().astype(np.int64).tolist() == ref.tolist()
+
+
+@pytest.mark.parametrize("name,delta", CASES)
+def test_ri_factors_match_oracle(name, delta):
+    m, aux = gpu_basis(name, delta)
+    pd = O.pairs(name)
+    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux).cpu().numpy()
+    ref = acd.ri_factors(pd, aux.cpu().numpy().astype(np.int64))
+    assert B.shape == ref.shape
+    np.testing.assert_allclose(B, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+    # exact on the basis densities: (B^T B)[aux] = their ERI columns
+    a = aux.cpu().numpy().astype(np.int64)
+    cols = np.stack([eri.eri_column(pd, int(P)) for P in a])
+    np.testing.assert_allclose(B.T @ B[:, a], cols.T, rtol=0, atol=1e-10 * np.abs(cols).max())
+
+
+@pytest.mark.parametrize("name,delta", CASES)
+def test_error_bound_on_gpu_factors(name, delta):
+    m, aux = gpu_basis(name, delta)
+    pd = O.pairs(name)
+    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux).cpu().numpy()
+    err = eri.eri_diagonal(pd) - (B * B).sum(axis=0)
+    scale = eri.eri_diagonal(pd).max()
+    at = m.basis.atom
+    one = at[pd.mu] == at[pd.nu]
+    assert err[one].max() <= delta * (1 + 1e-9) + 1e-12 * scale
+    assert err.min() >= -1e-10 * scale
+
+
+@pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-4)])
+def test_qp_with_ri_factors(name, delta):
+    """Transform and Newton on the GPU's B vs the oracle pipeline on the oracle's B.
+
+    The two B agree to 1e-10 of max|B| (rounding of the substitution); the
+    transform's cancellation magnifies that as in the fused pipeline, so the
+    roots are held to 1e-8 Ha (0.3 micro-eV) and the pole strengths to 1e-7."""
+    m, aux = gpu_basis(name, delta)
+    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux)
+    Lov, Lp = G.cds_cd_to_mo(B, dev(m.C), m.nocc, dev(m.orbitals))
+    w, P, it, st = G.cds_qp_solve(Lov, Lp, dev(m.orbitals), dev(m.eps), m.nocc)
+    ref_B = acd.ri_factors(O.pairs(name), aux.cpu().numpy().astype(np.int64))
+    rov, rp = O.factors(name, ref_B)
+    res = O.solve(name, rov, rp, m.orbitals)
+    np.testing.assert_allclose(w.cpu().numpy(), [r[0] for r in res], atol=1e-8, rtol=0)
+    np.testing.assert_allclose(P.cpu().numpy(), [r[1] for r in res], rtol=1e-7, atol=0)
+
+
+def test_ri_edge_cases():
+    m, aux = gpu_basis("c0", 1e-6)
+    xyz, alpha = dev(m.basis.xyz), dev(m.basis.alpha)
+    bad = aux.clone()
+    bad[-1] = m.nbf * (m.nbf + 1) // 2          # one past the last pair
+    with pytest.raises(G.CdsError):
+        G.cds_ri_factors(xyz, alpha, bad)
+    empty = G.cds_ri_factors(xyz, alpha, aux[:0])
+    assert empty.shape == (0, m.nbf * (m.nbf + 1) // 2)
+    # a repeated basis density makes the metric singular
+    dup = torch.cat([aux, aux[:1]])
+    with pytest.raises(G.CdsError):
+        G.cds_ri_factors(xyz, alpha, dup)

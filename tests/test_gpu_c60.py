@@ -248,3 +248,32 @@ def test_bracketed_newton_full_size(run):
         return a[0], d[0]
     wr, Pr, itr, str_ = qp.bracketed_qp(f, m.eps[q], lo, hi)
     assert str_ == 0 and abs(w[t] - wr) <= TOL_QP
+
+
+def test_acd_ri_full_size(run):
+    """Atomic Cholesky basis and V-approximation at C60 size: the basis equals
+    the oracle's, sampled columns of B equal the oracle's L_m^-1 (rho~|rho_I)
+    within 1e-10 of max|B|, every one-centre density's error is <= delta, and
+    the quasiparticle solve on B converges for the quasiparticle poles."""
+    from oracle import acd
+    from scipy.linalg import cholesky, solve_triangular
+    m = run[0]
+    pd = eri.PairData(m.basis.xyz, m.basis.alpha)
+    aux = G.cds_acd_aux_pairs(dev(m.basis.alpha), dev(m.basis.atom.astype(np.int32)), 1e-4)
+    a = aux.cpu().numpy().astype(np.int64)
+    assert a.tolist() == acd.aux_pairs(m.basis.alpha, m.basis.atom, 1e-4).tolist()
+    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux)
+    rng = np.random.default_rng(11)
+    cols = np.sort(rng.choice(pd.npair, 3000, replace=False))
+    Lm = cholesky(eri.eri_from_pairs(pd, a[:, None], a[None, :]), lower=True)
+    ref = solve_triangular(Lm, eri.eri_from_pairs(pd, a[:, None], cols[None, :]), lower=True)
+    Bh = B[:, torch.from_numpy(cols).to(DEV)].cpu().numpy()
+    np.testing.assert_allclose(Bh, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+    err = eri.eri_diagonal(pd) - (B * B).sum(dim=0).cpu().numpy()
+    one = m.basis.atom[pd.mu] == m.basis.atom[pd.nu]
+    assert err[one].max() <= 1e-4 * (1 + 1e-9)
+    assert err.min() >= -1e-10 * eri.eri_diagonal(pd).max()
+    Lov, Lp = G.cds_cd_to_mo(B, dev(m.C), m.nocc, dev(m.orbitals))
+    w, P, it, st = G.cds_qp_solve(Lov, Lp, dev(m.orbitals), dev(m.eps), m.nocc)
+    qp = (P >= 0.5).cpu().numpy()
+    assert qp.sum() >= 5 and np.all(st.cpu().numpy()[qp] == 0)
