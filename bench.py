@@ -586,11 +586,12 @@ def run_acd(m, delta, orbs, eps, prec, w_cd, P_cd):
     at = torch.from_numpy(m.basis.atom.astype(np.int32)).to(dev)
     C = torch.from_numpy(m.C).to(dev)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    G.cds_ri_factors(xyz, al, G.cds_acd_aux_pairs(al, at, delta)[:8], "f32x2")   # warm-up
     torch.cuda.synchronize()
     ev[0].record()
     aux = G.cds_acd_aux_pairs(al, at, delta)
     ev[1].record()
-    B = G.cds_ri_factors(xyz, al, aux)
+    B = G.cds_ri_factors(xyz, al, aux, "f32x2")
     ev[2].record()
     Lov, Lp = G.cds_cd_to_mo(B, C, m.nocc, orbs, precision="f32x2")
     ev[3].record()
@@ -604,8 +605,8 @@ def run_acd(m, delta, orbs, eps, prec, w_cd, P_cd):
             "qp_ms": t[3], "status": st.cpu().tolist(),
             "qp_vs_full_cd_meV": diff[qp].tolist(),
             "note": "one-centre basis densities of the isolated atoms' CD at the same delta; "
-                    "B = L_m^-1 (rho~|rho) on the GPU (FP64), then the step's transform and "
-                    "Newton (recomputing form); times of one cold call each"}
+                    "B = L_m^-1 (rho~|rho) on the GPU (float pairs), then the step's transform "
+                    "and Newton (recomputing form); times of one call each after a warm-up"}
 
 
 # ----------------------------------------------------------------------------

@@ -219,17 +219,21 @@ int cds_acd_aux_pairs(int32_t nbf, const double* alpha, const int32_t* atom, dou
                       int32_t* aux, int32_t capacity, int32_t* naux, void* workspace,
                       size_t workspace_bytes, cudaStream_t stream);
 
-size_t cds_ri_workspace_bytes(int32_t naux);
+size_t cds_ri_workspace_bytes(int32_t nbf, int32_t naux, int32_t precision);
 
 /* Blocking.  Inputs (device): xyz, alpha as cds_cd_decompose; aux [naux]
- * (naux <= 4096) packed pair indices of the basis densities.  Output
- * (device, caller-owned): B [naux][npair].  CDS_ERR_NOT_PD if the metric is
- * not positive definite to working precision (a Cholesky pivot at or below
- * 1e-12 x its diagonal, e.g. a density listed twice); CDS_ERR_ARG on an
- * index outside the basis. */
+ * packed pair indices of the basis densities.  Output (device, caller-
+ * owned): B [naux][npair].  The factors come from forward substitution with
+ * the basis as fixed pivots (B restricted to the basis' columns is L_m^T, so
+ * the metric factor is formed on the way).  precision: CDS_PREC_FP64, or
+ * CDS_PREC_F32X2 (integrals and the substitution in float pairs; B ~1e-9 of
+ * max|B| from the FP64 result; workspace holds naux x npair float pairs).
+ * CDS_ERR_NOT_PD if the metric is not positive definite to working precision
+ * (a Cholesky pivot at or below 1e-12 x its diagonal, e.g. a density listed
+ * twice); CDS_ERR_ARG on an index outside the basis. */
 int cds_ri_factors(int32_t nbf, const double* xyz, const double* alpha, const int32_t* aux,
-                   int32_t naux, double* B, void* workspace, size_t workspace_bytes,
-                   cudaStream_t stream);
+                   int32_t naux, int32_t precision, double* B, void* workspace,
+                   size_t workspace_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * Decomposition and transform in one call (float-pair form).  Runs

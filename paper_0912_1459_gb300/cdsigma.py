@@ -63,8 +63,8 @@ _SIGNATURES = {
     "cds_acd_workspace_bytes": (_sz, [_i32]),
     "cds_acd_aux_pairs": (ctypes.c_int, [_i32, _vp, _vp, _f64, _vp, _i32, ctypes.POINTER(_i32), _vp,
                                          _sz, _vp]),
-    "cds_ri_workspace_bytes": (_sz, [_i32]),
-    "cds_ri_factors": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _vp, _vp, _sz, _vp]),
+    "cds_ri_workspace_bytes": (_sz, [_i32, _i32, _i32]),
+    "cds_ri_factors": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _i32, _vp, _vp, _sz, _vp]),
     "cds_sigma2_cache_bytes": (_sz, [_i32, _i32, _i32]),
     "cds_sigma2_diag_cache": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _i32,
                                              _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
@@ -313,9 +313,12 @@ def cds_acd_aux_pairs(alpha: torch.Tensor, atom: torch.Tensor, delta: float) -> 
     return torch.tensor(list(out[:cnt.value]), dtype=torch.int32, device=dev)
 
 
-def cds_ri_factors(xyz: torch.Tensor, alpha: torch.Tensor, aux: torch.Tensor) -> torch.Tensor:
+def cds_ri_factors(xyz: torch.Tensor, alpha: torch.Tensor, aux: torch.Tensor,
+                   precision: str = "fp64") -> torch.Tensor:
     """B [naux, npair]: the V-approximation (Eq. int_approx) over the basis
-    densities aux, in the factor form of the Cholesky vectors."""
+    densities aux, in the factor form of the Cholesky vectors.
+
+    precision: "fp64" or "f32x2" (integrals and substitution in float pairs)."""
     lib = load()
     xyz = _dev(xyz, torch.float64, "xyz")
     alpha = _dev(alpha, torch.float64, "alpha")
@@ -324,8 +327,9 @@ def cds_ri_factors(xyz: torch.Tensor, alpha: torch.Tensor, aux: torch.Tensor) ->
     n = alpha.shape[0]
     naux = aux.shape[0]
     B = torch.empty((naux, npair(n)), dtype=torch.float64, device=dev)
-    ws = _workspace(lib.cds_ri_workspace_bytes(naux), dev)
-    st = lib.cds_ri_factors(n, _p(xyz), _p(alpha), _p(aux), naux, _p(B), _p(ws), ws.numel(),
+    prec = PRECISIONS[precision]
+    ws = _workspace(lib.cds_ri_workspace_bytes(n, naux, prec), dev)
+    st = lib.cds_ri_factors(n, _p(xyz), _p(alpha), _p(aux), naux, prec, _p(B), _p(ws), ws.numel(),
                             _stream(dev))
     _check(st, "cds_ri_factors")
     return B

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "eri_col.cuh"
 
 namespace cds {
 namespace {
@@ -41,76 +42,240 @@ AcdLayout acd_layout(void* ws, int32_t na) {
     return l;
 }
 
-// V[k][l] = cols[k][aux[l]] (the metric from the basis densities' columns);
-// d0[k] = V[k][k].
-__global__ void k_gather_metric(const double* __restrict__ cols, int64_t npair,
-                                const int32_t* __restrict__ aux, int32_t naux,
-                                double* __restrict__ V, double* __restrict__ d0) {
-    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= (int64_t)naux * naux) return;
-    const int32_t k = (int32_t)(e / naux), l = (int32_t)(e - (int64_t)k * naux);
-    const double v = cols[(int64_t)k * npair + aux[l]];
-    V[e] = v;
-    if (k == l) d0[k] = v;
-}
+// The factors by forward substitution with the basis as fixed pivots:
+//   B[k][I] = (X[k][I] - sum_{j<k} Lm[k][j] B[j][I]) / Lm[k][k],
+// X[k] = (rho~_k|rho).  The metric's factor need not be formed first: B
+// restricted to the basis' own columns is L_m^T, so Lm[k][j] = B[j][aux[k]]
+// (j < k) once row j is final, and Lm[k][k] is the square root of the Schur
+// complement X[k][aux[k]] - sum_j Lm[k][j]^2.  Rows go kRiR at a time:
+// k_ri_panel gathers the finished part of their Lm rows and factors the
+// kRiR x kRiR block of the Schur complement (FP64, a few hundred values);
+// k_ri_rows then streams every earlier row once for all kRiR new rows.
+// FP64 form: X is made in B and replaced row by row.  Float-pair form: X and
+// the finished rows live as float pairs in the workspace (the operand the
+// stream reads), and each finished row is also written to B in FP64.
+constexpr int kRiR = 8;      // rows per pass
+constexpr int kRiJ = 256;    // earlier rows staged per shared-memory tile
+constexpr int kRiT = 256;    // threads per block
+constexpr int kRiEriPasses = 4;   // integral kernel: passes of kRiT pairs per block
 
-// In-place lower Cholesky factor of the small metric (one block, right-
-// looking).  status: 0, or 1 if a pivot is not finite or falls to
-// kSingular x its original diagonal d0: the metric is then singular to
-// working precision (e.g. a basis density listed twice) and B would carry
-// errors of 1e6 x the rounding or more.
+// A Cholesky pivot at or below kSingular x its metric diagonal: the metric is
+// singular to working precision (e.g. a basis density listed twice) and B
+// would carry 1e6 x the rounding or more.
 constexpr double kSingular = 1e-12;
-__global__ void __launch_bounds__(256) k_chol_small(double* __restrict__ V, int32_t n,
-                                                    const double* __restrict__ d0,
-                                                    int32_t* __restrict__ status) {
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    for (int32_t j = 0; j < n; ++j) {
-        if (threadIdx.x == 0) {
-            const double d = V[(int64_t)j * n + j];
-            if (!(d > kSingular * d0[j]) || !(d < INFINITY)) bad = 1;
-            else V[(int64_t)j * n + j] = sqrt(d);
-        }
-        __syncthreads();
-        if (bad) break;
-        const double djj = V[(int64_t)j * n + j];
-        for (int32_t i = j + 1 + threadIdx.x; i < n; i += blockDim.x) V[(int64_t)i * n + j] /= djj;
-        __syncthreads();
-        // trailing lower triangle: V[i][k] -= V[i][j] V[k][j], j < k <= i
-        const int64_t m = n - 1 - j;
-        for (int64_t e = threadIdx.x; e < m * (m + 1) / 2; e += blockDim.x) {
-            int64_t r = (int64_t)((sqrt(8.0 * (double)e + 1.0) - 1.0) * 0.5);
-            while (r * (r + 1) / 2 > e) --r;
-            while ((r + 1) * (r + 2) / 2 <= e) ++r;
-            const int32_t i = j + 1 + (int32_t)r, k = j + 1 + (int32_t)(e - r * (r + 1) / 2);
-            V[(int64_t)i * n + k] -= V[(int64_t)i * n + j] * V[(int64_t)k * n + j];
-        }
-        __syncthreads();
+
+struct RiLayout {
+    PairSoA pd;
+    PairF2 pf;        // float-pair form only
+    float2* Xf;       // [naux][n], float-pair form only
+    double* Lrow;     // [kRiR][naux]
+    float2* Lrowf;    // [kRiR][naux], float-pair form only
+    double* Lblk;     // [kRiR][kRiR]: the block's factor (FP64 form)
+    float2* Lblkf;    // [kRiR][kRiR]: -factor below the diagonal, 1/diagonal on it
+    int32_t* status;
+    size_t bytes;
+};
+
+RiLayout ri_layout(void* ws, int64_t n, int32_t naux, bool df) {
+    Carver c(ws);
+    RiLayout l{};
+    const size_t nn = (size_t)std::max<int64_t>(n, 1), na = (size_t)std::max(naux, 1);
+    l.pd = PairSoA{c.take<double>(nn), c.take<double>(nn), c.take<double>(nn),
+                   c.take<double>(nn), c.take<double>(nn)};
+    if (df) {
+        l.pf = PairF2{c.take<float2>(nn), c.take<float2>(nn), c.take<float2>(nn),
+                      c.take<float2>(nn), c.take<float2>(nn)};
+        l.Xf = c.take<float2>(na * nn);
+        l.Lrowf = c.take<float2>((size_t)kRiR * na);
+        l.Lblkf = c.take<float2>((size_t)kRiR * kRiR);
     }
-    if (threadIdx.x == 0) *status = bad;
+    l.Lrow = c.take<double>((size_t)kRiR * na);
+    l.Lblk = c.take<double>((size_t)kRiR * kRiR);
+    l.status = c.take<int32_t>(4);
+    l.bytes = c.off;
+    return l;
 }
 
-// Row k of the forward substitution, in place:
-//   B[k][I] = (B[k][I] - sum_{j<k} Lm[k][j] B[j][I]) / Lm[k][k]
-// (rows j < k are final).  The row of Lm is staged in shared memory.
-constexpr int kRiRow = 4096;
-__global__ void __launch_bounds__(256) k_ri_row(const double* __restrict__ Lm, int32_t naux,
-                                                int32_t k, double* __restrict__ B, int64_t n) {
-    __shared__ double lk[kRiRow];
-    for (int j = threadIdx.x; j <= k; j += blockDim.x) lk[j] = Lm[(int64_t)k * naux + j];
-    __syncthreads();
-    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (I >= n) return;
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    int j = 0;
-    for (; j + 4 <= k; j += 4) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] = fma(lk[j + u], B[(int64_t)(j + u) * n + I], s[u]);
+// Row y of X: (rho~_{aux[y]}|rho_I) for all I, FP64 into B or float pairs
+// into Xf.
+template <bool DF>
+__global__ void __launch_bounds__(kRiT) k_ri_eri(PairSoA pd, PairF2 pf, int64_t n,
+                                                 const int32_t* __restrict__ aux,
+                                                 double* __restrict__ B, float2* __restrict__ Xf) {
+    const int64_t P = aux[blockIdx.y];
+    if (DF) eri_column_df<kRiT>(pd, pf, n, P, Xf + (int64_t)blockIdx.y * n, blockIdx.x, gridDim.x);
+    else eri_column_fp64<kRiT>(pd, n, P, B + (int64_t)blockIdx.y * n, blockIdx.x, gridDim.x);
+}
+
+template <bool DF>
+__device__ __forceinline__ double x_at(const double* B, const float2* Xf, int64_t e) {
+    if (DF) {
+        const float2 v = Xf[e];
+        return (double)v.x + (double)v.y;
     }
-    for (; j < k; ++j) s[0] = fma(lk[j], B[(int64_t)j * n + I], s[0]);
-    double* b = B + (int64_t)k * n + I;
-    *b = (*b - ((s[0] + s[1]) + (s[2] + s[3]))) / lk[k];
+    return B[e];
+}
+
+// Lrow[r][j] = B[j][aux[k0+r]] for j < k0 (final rows); the lower Cholesky
+// factor of S[r][s] = X[k0+r][aux[k0+s]] - sum_j Lrow[r][j] Lrow[s][j]
+// (s <= r < nr) into Lblk / Lblkf.  status = 1 on a pivot that is not finite
+// or falls to kSingular x X[k0+r][aux[k0+r]].
+template <bool DF>
+__global__ void __launch_bounds__(kRiT) k_ri_panel(const double* __restrict__ B,
+                                                   const float2* __restrict__ Xf, int64_t n,
+                                                   const int32_t* __restrict__ aux, int32_t k0,
+                                                   int32_t nr, RiLayout lay, int32_t naux_ld) {
+    __shared__ double S[kRiR][kRiR];
+    __shared__ double d0[kRiR];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int64_t e = tid; e < (int64_t)nr * k0; e += blockDim.x) {
+        const int r = (int)(e / k0), j = (int)(e - (int64_t)r * k0);
+        const double v = B[(int64_t)j * n + aux[k0 + r]];
+        lay.Lrow[(int64_t)r * naux_ld + j] = v;
+        if (DF) lay.Lrowf[(int64_t)r * naux_ld + j] = to_f2(v);
+    }
+    __syncthreads();
+    // one warp per lower-triangle entry (r, s)
+    for (int e = warp; e < nr * (nr + 1) / 2; e += blockDim.x / 32) {
+        int r = 0;
+        while ((r + 1) * (r + 2) / 2 <= e) ++r;
+        const int s2 = e - r * (r + 1) / 2;
+        const double* a = lay.Lrow + (int64_t)r * naux_ld;
+        const double* b = lay.Lrow + (int64_t)s2 * naux_ld;
+        double acc = 0.0;
+        for (int j = lane; j < k0; j += 32) acc = fma(a[j], b[j], acc);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const double x = x_at<DF>(B, Xf, (int64_t)(k0 + r) * n + aux[k0 + s2]);
+            S[r][s2] = x - acc;
+            if (s2 == r) d0[r] = x;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int bad = 0;
+        for (int j = 0; j < nr; ++j) {
+            double d = S[j][j];
+            for (int q = 0; q < j; ++q) d -= S[j][q] * S[j][q];
+            if (!(d > kSingular * d0[j]) || !(d < INFINITY)) { bad = 1; d = 1.0; }
+            S[j][j] = sqrt(d);
+            for (int i = j + 1; i < nr; ++i) {
+                double v = S[i][j];
+                for (int q = 0; q < j; ++q) v -= S[i][q] * S[j][q];
+                S[i][j] = v / S[j][j];
+            }
+        }
+        for (int i = 0; i < kRiR; ++i)
+            for (int j = 0; j < kRiR; ++j) {
+                const bool in = i < nr && j <= i;
+                lay.Lblk[i * kRiR + j] = in ? S[i][j] : 0.0;
+                if (DF)
+                    lay.Lblkf[i * kRiR + j] =
+                        !in ? make_float2(0.f, 0.f) : (i == j ? to_f2(1.0 / S[i][i]) : to_f2(-S[i][j]));
+            }
+        if (bad) *lay.status = 1;
+    }
+}
+
+// Rows k0 .. k0+nr-1 from X (in those rows) and the final rows j < k0.  One
+// pair column I per thread: each earlier row is read once for all nr rows,
+// then the kRiR x kRiR block is solved in registers.
+__global__ void __launch_bounds__(kRiT) k_ri_rows(double* __restrict__ B, int64_t n, int32_t k0,
+                                                  int32_t nr, const double* __restrict__ Lrow,
+                                                  int32_t ldr, const double* __restrict__ Lblk) {
+    __shared__ double ls[kRiJ][kRiR];
+    __shared__ double lb[kRiR][kRiR];
+    const int tid = threadIdx.x;
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + tid;
+    const bool valid = I < n;
+    double s[kRiR];
+#pragma unroll
+    for (int r = 0; r < kRiR; ++r) s[r] = 0.0;
+    for (int j0 = 0; j0 < k0; j0 += kRiJ) {
+        const int jn = min(kRiJ, k0 - j0);
+        __syncthreads();
+        for (int e = tid; e < kRiJ * kRiR; e += blockDim.x) {
+            const int r = e / kRiJ, jj = e - r * kRiJ;
+            ls[jj][r] = (r < nr && jj < jn) ? Lrow[(int64_t)r * ldr + j0 + jj] : 0.0;
+        }
+        __syncthreads();
+        if (valid) {
+            const double* col = B + (int64_t)j0 * n + I;
+            for (int jj = 0; jj < jn; ++jj) {
+                const double b = col[(int64_t)jj * n];
+#pragma unroll
+                for (int r = 0; r < kRiR; ++r) s[r] = fma(ls[jj][r], b, s[r]);
+            }
+        }
+    }
+    if (tid < kRiR * kRiR) lb[tid / kRiR][tid % kRiR] = Lblk[tid];
+    __syncthreads();
+    if (!valid) return;
+    double bv[kRiR];
+#pragma unroll
+    for (int r = 0; r < kRiR; ++r) {
+        if (r < nr) {
+            double* out = B + (int64_t)(k0 + r) * n + I;
+            double x = *out - s[r];
+#pragma unroll
+            for (int q = 0; q < r; ++q) x = fma(-lb[r][q], bv[q], x);
+            bv[r] = x / lb[r][r];
+            *out = bv[r];
+        }
+    }
+}
+
+// The same in float pairs: the earlier rows and X are read from Xf, each new
+// row is written to Xf (float pairs) and to B (FP64).
+__global__ void __launch_bounds__(kRiT) k_ri_rows_df(double* __restrict__ B,
+                                                     float2* __restrict__ Xf, int64_t n,
+                                                     int32_t k0, int32_t nr,
+                                                     const float2* __restrict__ Lrowf, int32_t ldr,
+                                                     const float2* __restrict__ Lblkf) {
+    __shared__ float2 ls[kRiJ][kRiR];
+    __shared__ float2 lb[kRiR][kRiR];
+    const int tid = threadIdx.x;
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + tid;
+    const bool valid = I < n;
+    const float2 zero = make_float2(0.f, 0.f);
+    float2 s[kRiR];
+#pragma unroll
+    for (int r = 0; r < kRiR; ++r) s[r] = zero;
+    for (int j0 = 0; j0 < k0; j0 += kRiJ) {
+        const int jn = min(kRiJ, k0 - j0);
+        __syncthreads();
+        for (int e = tid; e < kRiJ * kRiR; e += blockDim.x) {
+            const int r = e / kRiJ, jj = e - r * kRiJ;
+            ls[jj][r] = (r < nr && jj < jn) ? Lrowf[(int64_t)r * ldr + j0 + jj] : zero;
+        }
+        __syncthreads();
+        if (valid) {
+            const float2* col = Xf + (int64_t)j0 * n + I;
+            for (int jj = 0; jj < jn; ++jj) {
+                const float2 b = col[(int64_t)jj * n];
+#pragma unroll
+                for (int r = 0; r < kRiR; ++r) df_fma(s[r], ls[jj][r], b);
+            }
+        }
+    }
+    if (tid < kRiR * kRiR) lb[tid / kRiR][tid % kRiR] = Lblkf[tid];
+    __syncthreads();
+    if (!valid) return;
+    float2 bv[kRiR];
+#pragma unroll
+    for (int r = 0; r < kRiR; ++r) {
+        if (r < nr) {
+            const int64_t e = (int64_t)(k0 + r) * n + I;
+            float2 x = df_add(Xf[e], df_neg(s[r]));
+#pragma unroll
+            for (int q = 0; q < r; ++q) df_fma(x, lb[r][q], bv[q]);
+            x = df_add(x, zero);   // renormalise after the accumulation
+            bv[r] = df_mul(x, lb[r][r]);
+            Xf[e] = bv[r];
+            B[e] = (double)bv[r].x + (double)bv[r].y;
+        }
+    }
 }
 
 }  // namespace
@@ -186,28 +351,23 @@ extern "C" int cds_acd_aux_pairs(int32_t nbf, const double* alpha, const int32_t
     return count > capacity ? CDS_ERR_CAPACITY : CDS_OK;
 }
 
-extern "C" size_t cds_ri_workspace_bytes(int32_t naux) {
-    if (naux < 0) return 0;
-    Carver c(nullptr);
-    c.take<double>((size_t)std::max<int64_t>((int64_t)naux * naux, 1));
-    c.take<double>((size_t)std::max(naux, 1));
-    c.take<int32_t>(4);
-    return c.off;
+extern "C" size_t cds_ri_workspace_bytes(int32_t nbf, int32_t naux, int32_t precision) {
+    if (nbf <= 0 || naux < 0) return 0;
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return 0;
+    return ri_layout(nullptr, npair_of(nbf), naux, precision == CDS_PREC_F32X2).bytes;
 }
 
 extern "C" int cds_ri_factors(int32_t nbf, const double* xyz, const double* alpha,
-                              const int32_t* aux, int32_t naux, double* B, void* workspace,
-                              size_t workspace_bytes, cudaStream_t stream) {
-    if (nbf <= 0 || naux < 0 || naux > 65535 || naux > kRiRow || !xyz || !alpha ||
-        (naux > 0 && (!aux || !B)))
+                              const int32_t* aux, int32_t naux, int32_t precision, double* B,
+                              void* workspace, size_t workspace_bytes, cudaStream_t stream) {
+    if (nbf <= 0 || naux < 0 || !xyz || !alpha || (naux > 0 && (!aux || !B)))
         return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return CDS_ERR_UNSUPPORTED;
     if (naux == 0) return CDS_OK;
-    if (!workspace || workspace_bytes < cds_ri_workspace_bytes(naux)) return CDS_ERR_WORKSPACE;
-    Carver c(workspace);
-    double* V = c.take<double>((size_t)naux * naux);
-    double* d0 = c.take<double>((size_t)naux);
-    int32_t* status = c.take<int32_t>(4);
+    const bool df = precision == CDS_PREC_F32X2;
     const int64_t n = npair_of(nbf);
+    RiLayout lay = ri_layout(workspace, n, naux, df);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
     {   // every basis density must be a pair of this basis
         std::vector<int32_t> h(naux);
         CDS_CUDA_TRY(cudaMemcpyAsync(h.data(), aux, sizeof(int32_t) * naux, cudaMemcpyDeviceToHost,
@@ -216,22 +376,41 @@ extern "C" int cds_ri_factors(int32_t nbf, const double* xyz, const double* alph
         for (int32_t P : h)
             if (P < 0 || P >= n) return CDS_ERR_ARG;
     }
-    int st = cds_eri_columns(nbf, xyz, alpha, aux, naux, B, stream);   // (rho~_K|rho_I)
+    int st = build_pairs(nbf, xyz, alpha, lay.pd, stream);
     if (st) return st;
-    const int64_t nn = (int64_t)naux * naux;
-    k_gather_metric<<<(unsigned)((nn + 255) / 256), 256, 0, stream>>>(B, n, aux, naux, V, d0);
-    CDS_LAUNCH_CHECK();
-    k_chol_small<<<1, 256, 0, stream>>>(V, naux, d0, status);
-    CDS_LAUNCH_CHECK();
-    int32_t h = 0;
-    CDS_CUDA_TRY(cudaMemcpyAsync(&h, status, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
-    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
-    if (h) return CDS_ERR_NOT_PD;
-    const unsigned g = (unsigned)((n + 255) / 256);
-    for (int32_t k = 0; k < naux; ++k) {
-        k_ri_row<<<g, 256, 0, stream>>>(V, naux, k, B, n);
+    const unsigned gn = (unsigned)((n + kRiT - 1) / kRiT);
+    if (df) {
+        k_pairs_to_f2<<<gn, kRiT, 0, stream>>>(lay.pd, lay.pf, n);
+        CDS_LAUNCH_CHECK();
     }
-    count_launches((unsigned long long)naux);
+    // X = (rho~_K|rho_I), one block row of grid per basis density
+    const unsigned ge = (unsigned)std::max<int64_t>(1, (n + (int64_t)kRiT * kRiEriPasses - 1) /
+                                                           ((int64_t)kRiT * kRiEriPasses));
+    for (int32_t y0 = 0; y0 < naux; y0 += 65535) {
+        const unsigned gy = (unsigned)std::min(65535, naux - y0);
+        if (df)
+            k_ri_eri<true><<<dim3(ge, gy), kRiT, 0, stream>>>(lay.pd, lay.pf, n, aux + y0, nullptr,
+                                                              lay.Xf + (int64_t)y0 * n);
+        else
+            k_ri_eri<false><<<dim3(ge, gy), kRiT, 0, stream>>>(lay.pd, lay.pf, n, aux + y0,
+                                                               B + (int64_t)y0 * n, nullptr);
+        CDS_LAUNCH_CHECK();
+    }
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.status, 0, sizeof(int32_t), stream));
+    for (int32_t k0 = 0; k0 < naux; k0 += kRiR) {
+        const int32_t nr = std::min(kRiR, naux - k0);
+        if (df) {
+            k_ri_panel<true><<<1, kRiT, 0, stream>>>(B, lay.Xf, n, aux, k0, nr, lay, naux);
+            k_ri_rows_df<<<gn, kRiT, 0, stream>>>(B, lay.Xf, n, k0, nr, lay.Lrowf, naux, lay.Lblkf);
+        } else {
+            k_ri_panel<false><<<1, kRiT, 0, stream>>>(B, nullptr, n, aux, k0, nr, lay, naux);
+            k_ri_rows<<<gn, kRiT, 0, stream>>>(B, n, k0, nr, lay.Lrow, naux, lay.Lblk);
+        }
+    }
+    count_launches(2ull * ((naux + kRiR - 1) / kRiR));
     CDS_CUDA_TRY(cudaGetLastError());
-    return CDS_OK;
+    int32_t h = 0;
+    CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.status, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    return h ? CDS_ERR_NOT_PD : CDS_OK;
 }

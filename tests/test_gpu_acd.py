@@ -4,13 +4,16 @@ Eq. int_approx, Eq. error_approx) on the GPU against the oracle.
 The oracle's basis and factors are pinned in test_oracle_acd.py.  Here:
 * cds_acd_aux_pairs equals oracle acd.aux_pairs exactly (integer work);
 * cds_ri_factors: B element by element within 1e-10 of the largest |B| (the
-  Cholesky factor of the metric and the forward substitution are unique), and
-  B^T B on the basis densities reproduces their exact columns;
+  Cholesky factor of the metric and the forward substitution are unique;
+  float-pair form: 1e-9, measured 4e-11 at C60 size), and B^T B on the basis
+  densities reproduces their exact columns;
 * Eq. error_approx on the GPU's B: every one-centre density's error is <= delta
   (the isolated atoms' bound) and no diagonal error is negative;
 * the whole method with B in place of the Cholesky vectors (transform,
-  Newton) agrees with the oracle run on the oracle's B (roots within 1e-8 Ha);
-* edge cases: an index outside the basis and an empty basis.
+  Newton) agrees with the oracle run on the oracle's B (roots within 1e-8 Ha,
+  float pairs 1e-7 Ha);
+* edge cases: an index outside the basis, an empty basis, a single density, a
+  repeated density (singular metric), an unsupported precision.
 """
 import numpy as np
 import pytest
@@ -47,18 +50,19 @@ def test_aux_pairs_match_oracle(name, delta):
     assert aux.cpu().numpy().astype(np.int64).tolist() == ref.tolist()
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("f32x2", 1e-9)])
 @pytest.mark.parametrize("name,delta", CASES)
-def test_ri_factors_match_oracle(name, delta):
+def test_ri_factors_match_oracle(name, delta, prec, tol):
     m, aux = gpu_basis(name, delta)
     pd = O.pairs(name)
-    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux).cpu().numpy()
+    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux, prec).cpu().numpy()
     ref = acd.ri_factors(pd, aux.cpu().numpy().astype(np.int64))
     assert B.shape == ref.shape
-    np.testing.assert_allclose(B, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
+    np.testing.assert_allclose(B, ref, rtol=0, atol=tol * np.abs(ref).max())
     # exact on the basis densities: (B^T B)[aux] = their ERI columns
     a = aux.cpu().numpy().astype(np.int64)
     cols = np.stack([eri.eri_column(pd, int(P)) for P in a])
-    np.testing.assert_allclose(B.T @ B[:, a], cols.T, rtol=0, atol=1e-10 * np.abs(cols).max())
+    np.testing.assert_allclose(B.T @ B[:, a], cols.T, rtol=0, atol=tol * np.abs(cols).max())
 
 
 @pytest.mark.parametrize("name,delta", CASES)
@@ -74,22 +78,25 @@ def test_error_bound_on_gpu_factors(name, delta):
     assert err.min() >= -1e-10 * scale
 
 
+@pytest.mark.parametrize("prec", ["fp64", "f32x2"])
 @pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-4)])
-def test_qp_with_ri_factors(name, delta):
+def test_qp_with_ri_factors(name, delta, prec):
     """Transform and Newton on the GPU's B vs the oracle pipeline on the oracle's B.
 
-    The two B agree to 1e-10 of max|B| (rounding of the substitution); the
-    transform's cancellation magnifies that as in the fused pipeline, so the
-    roots are held to 1e-8 Ha (0.3 micro-eV) and the pole strengths to 1e-7."""
+    The two B agree to 1e-10 of max|B| (rounding of the substitution; float
+    pairs: 2e-11 of max|B| at this size); the transform's cancellation magnifies
+    that as in the fused pipeline, so the roots are held to 1e-8 Ha (0.3 micro-
+    eV) and the pole strengths to 1e-7 (float pairs: 1e-7 Ha and 1e-6)."""
     m, aux = gpu_basis(name, delta)
-    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux)
+    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux, prec)
     Lov, Lp = G.cds_cd_to_mo(B, dev(m.C), m.nocc, dev(m.orbitals))
     w, P, it, st = G.cds_qp_solve(Lov, Lp, dev(m.orbitals), dev(m.eps), m.nocc)
     ref_B = acd.ri_factors(O.pairs(name), aux.cpu().numpy().astype(np.int64))
     rov, rp = O.factors(name, ref_B)
     res = O.solve(name, rov, rp, m.orbitals)
-    np.testing.assert_allclose(w.cpu().numpy(), [r[0] for r in res], atol=1e-8, rtol=0)
-    np.testing.assert_allclose(P.cpu().numpy(), [r[1] for r in res], rtol=1e-7, atol=0)
+    tw, tp = (1e-8, 1e-7) if prec == "fp64" else (1e-7, 1e-6)
+    np.testing.assert_allclose(w.cpu().numpy(), [r[0] for r in res], atol=tw, rtol=0)
+    np.testing.assert_allclose(P.cpu().numpy(), [r[1] for r in res], rtol=tp, atol=0)
 
 
 def test_ri_edge_cases():
@@ -103,5 +110,13 @@ def test_ri_edge_cases():
     assert empty.shape == (0, m.nbf * (m.nbf + 1) // 2)
     # a repeated basis density makes the metric singular
     dup = torch.cat([aux, aux[:1]])
-    with pytest.raises(G.CdsError):
-        G.cds_ri_factors(xyz, alpha, dup)
+    for prec in ("fp64", "f32x2"):
+        with pytest.raises(G.CdsError):
+            G.cds_ri_factors(xyz, alpha, dup, prec)
+    with pytest.raises(Exception):
+        G.cds_ri_factors(xyz, alpha, aux, "bf16x3")
+    # a single basis density: B = X / sqrt(X[aux])
+    B1 = G.cds_ri_factors(xyz, alpha, aux[:1]).cpu().numpy()
+    x = eri.eri_column(O.pairs("c0"), int(aux[0]))
+    ref1 = x / np.sqrt(x[int(aux[0])])
+    np.testing.assert_allclose(B1[0], ref1, rtol=1e-12, atol=1e-14 * np.abs(ref1).max())

@@ -253,7 +253,7 @@ def test_bracketed_newton_full_size(run):
 def test_acd_ri_full_size(run):
     """Atomic Cholesky basis and V-approximation at C60 size: the basis equals
     the oracle's, sampled columns of B equal the oracle's L_m^-1 (rho~|rho_I)
-    within 1e-10 of max|B|, every one-centre density's error is <= delta, and
+    within 1e-10 of max|B| (float-pair form: 1e-9), every one-centre density's error is <= delta, and
     the quasiparticle solve on B converges for the quasiparticle poles."""
     from oracle import acd
     from scipy.linalg import cholesky, solve_triangular
@@ -262,11 +262,15 @@ def test_acd_ri_full_size(run):
     aux = G.cds_acd_aux_pairs(dev(m.basis.alpha), dev(m.basis.atom.astype(np.int32)), 1e-4)
     a = aux.cpu().numpy().astype(np.int64)
     assert a.tolist() == acd.aux_pairs(m.basis.alpha, m.basis.atom, 1e-4).tolist()
-    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux)
     rng = np.random.default_rng(11)
     cols = np.sort(rng.choice(pd.npair, 3000, replace=False))
     Lm = cholesky(eri.eri_from_pairs(pd, a[:, None], a[None, :]), lower=True)
     ref = solve_triangular(Lm, eri.eri_from_pairs(pd, a[:, None], cols[None, :]), lower=True)
+    Bf = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux, "f32x2")
+    Bh = Bf[:, torch.from_numpy(cols).to(DEV)].cpu().numpy()
+    np.testing.assert_allclose(Bh, ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    del Bf
+    B = G.cds_ri_factors(dev(m.basis.xyz), dev(m.basis.alpha), aux)
     Bh = B[:, torch.from_numpy(cols).to(DEV)].cpu().numpy()
     np.testing.assert_allclose(Bh, ref, rtol=0, atol=1e-10 * np.abs(ref).max())
     err = eri.eri_diagonal(pd) - (B * B).sum(dim=0).cpu().numpy()
