@@ -60,6 +60,8 @@ def parse():
     p.add_argument("--no-fp64-arm", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-mp2", action="store_true")
+    p.add_argument("--no-trtc", action="store_true",
+                   help="skip timing the tensor-core (TF32X3) transform on the step's vectors")
     p.add_argument("--no-acd", action="store_true",
                    help="skip the atomic-Cholesky-basis / V-approximation section")
     p.add_argument("--no-fuse", action="store_true",
@@ -504,6 +506,11 @@ def run_ours(args, dist: Dist):
     if not args.no_mp2:
         mp2 = run_mp2(m, Lov, eps, prec if prec != "fp64" else "bf16x3", pk)
 
+    # ---- tensor-core (TF32X3) transform of the same vectors: time and error ----
+    trtc = None
+    if not args.no_trtc:
+        trtc = run_transform_tc(m, L, C, orbs, Lov)
+
     # ---- atomic Cholesky basis + V-approximation in place of the full CD ----
     acd = None
     if not args.no_acd:
@@ -533,6 +540,7 @@ def run_ours(args, dist: Dist):
         "mp2": mp2,
         "bracketed_newton": bracketed,
         "acd": acd,
+        "transform_tc": trtc,
     }
     if not args.no_batched:
         result["batched"] = run_batched(args, device)
@@ -570,6 +578,36 @@ def run_mp2(m, Lov, eps, prec, pk, reps: int = 3):
             "roofline": {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach,
                          "peak": pk["bf16_tflops"], "frac": ach / pk["bf16_tflops"],
                          "note": "3 split products x 2 M (o v)^2 per evaluation"}}
+
+
+def run_transform_tc(m, L, C, orbs, Lov_ref):
+    """The transform as split-precision tcgen05 GEMMs (TF32X3) on the step's
+    Cholesky vectors: CUDA-event time of one call after a warm-up, and its
+    error against the step's float-pair Lov (FP32 accumulation meets the
+    cancellation of this C, |C| up to 106)."""
+    import torch
+    import paper_0912_1459_gb300 as G
+
+    lib = G.load()
+    M = L.shape[0]
+    ws = torch.empty(lib.cds_cd_to_mo_workspace_bytes(m.nbf, m.nbf, m.nocc, M, len(m.orbitals)),
+                     dtype=torch.uint8, device=L.device)
+    G.cds_cd_to_mo(L[:32], C, m.nocc, orbs, workspace=ws, precision="tf32x3")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    Lov, _ = G.cds_cd_to_mo(L, C, m.nocc, orbs, workspace=ws, precision="tf32x3")
+    b.record()
+    torch.cuda.synchronize()
+    t = a.elapsed_time(b)
+    err = float((Lov - Lov_ref).abs().max() / Lov_ref.abs().max())
+    # 3 split products x 2 flops x (GEMM 1 + GEMM 2 + GEMM 3) multiply-adds
+    N, o, v, np_ = m.nbf, m.nocc, m.nbf - m.nocc, len(m.orbitals)
+    flops = 3 * 2.0 * M * ((o + np_) * N * N + o * v * N + np_ * N * N)
+    return {"precision": "tf32x3", "ms": t, "tflops": flops / (t / 1e3) / 1e12,
+            "lov_rel_err_vs_f32x2": err,
+            "note": "opt-in; FP32 accumulation cannot carry the ~1e6 cancellation of this "
+                    "C = S^-1/2 Q, so the step keeps the float-pair transform"}
 
 
 def run_acd(m, delta, orbs, eps, prec, w_cd, P_cd):

@@ -65,9 +65,12 @@ typedef enum {
     CDS_PREC_FP64 = 0,
     CDS_PREC_BF16X3 = 2,
     CDS_PREC_FP16X3 = 3,
-    CDS_PREC_F32X2 = 4   /* decomposition and transform: (hi, lo) float pairs with exact
+    CDS_PREC_F32X2 = 4,  /* decomposition and transform: (hi, lo) float pairs with exact
                             product and sum errors, ~2^-44 relative per operation, on the
                             FP32 units */
+    CDS_PREC_TF32X3 = 5  /* transform: tcgen05 tensor cores, each operand split into TF32
+                            hi + lo, hi.hi + hi.lo + lo.hi with FP32 accumulation,
+                            ~2^-21 relative per product (BF16X3 there: ~2^-17) */
 } cds_precision;
 
 /* Newton status per orbital (paper Eq. NR). */
@@ -187,10 +190,13 @@ int cds_cd_static_max_nbf(void);
 
 size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, int32_t np);
 
-/* Asynchronous.  L: device [M][npair]; C: device [nbf][nmo]; orb: device [np]
- * int32 MO indices in [0, nmo).  precision: CDS_PREC_FP64 or CDS_PREC_F32X2.
- * Outputs (device, fp64): Lov [nocc][nmo-nocc][M], Lp [np][nmo][M] (Lp may be
- * NULL when np == 0). */
+/* Asynchronous (FP64, F32X2) or blocking (TF32X3, BF16X3: the tensor-core
+ * kernels' error word is read at the end, CDS_ERR_TIMEOUT if a bounded wait
+ * gave up).  L: device [M][npair]; C: device [nbf][nmo]; orb: device [np]
+ * int32 MO indices in [0, nmo).  precision: CDS_PREC_FP64, CDS_PREC_F32X2,
+ * CDS_PREC_TF32X3 or CDS_PREC_BF16X3 (the last two on sm_103 only, else
+ * CDS_ERR_UNSUPPORTED).  Outputs (device, fp64): Lov [nocc][nmo-nocc][M],
+ * Lp [np][nmo][M] (Lp may be NULL when np == 0). */
 int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
                  const double* C, const int32_t* orb, int32_t np, int32_t precision,
                  double* Lov, double* Lp, void* workspace, size_t workspace_bytes,
@@ -236,12 +242,12 @@ int cds_ri_factors(int32_t nbf, const double* xyz, const double* alpha, const in
                    size_t workspace_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
- * Decomposition and transform in one call (float-pair form).  Runs
- * cds_cd_decompose(F32X2) and cds_cd_to_mo(F32X2) with the transform of each
- * batch of 32 finished vectors overlapped with the decomposition of the next
- * ones, on two library streams (the decomposition's at the highest
- * priority), joined to `stream` on return.  The results are those of the two
- * calls in sequence.
+ * Decomposition and transform in one call.  Runs cds_cd_decompose(F32X2) and
+ * cds_cd_to_mo(tr_precision: CDS_PREC_F32X2, CDS_PREC_TF32X3 or
+ * CDS_PREC_BF16X3) with the transform of each batch of 32 finished vectors
+ * overlapped with the decomposition of the next ones, on two library streams
+ * (the decomposition's at the highest priority), joined to `stream` on
+ * return.  The results are those of the two calls in sequence.
  * Inputs and outputs as cds_cd_decompose and cds_cd_to_mo, except:
  *   Lov  [nocc][nmo-nocc][M] and Lp [np][nmo][M] are written compact for the
  *        final rank M, into caller buffers of room for max_rank in place of M;
@@ -254,7 +260,8 @@ size_t cds_cd_decompose_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t 
 int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const double* alpha,
                            const int32_t* atom, double delta, int32_t scheme, int32_t max_rank,
                            const double* C, int32_t nmo, int32_t nocc, const int32_t* orb,
-                           int32_t np, double* L, int32_t* piv, double* D, int32_t* M_out,
+                           int32_t np, int32_t tr_precision, double* L, int32_t* piv, double* D,
+                           int32_t* M_out,
                            double* delta_eff_out, double* Lov, double* Lp, void* workspace,
                            size_t workspace_bytes, cudaStream_t stream);
 

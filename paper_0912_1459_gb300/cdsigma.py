@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "CDS_OK", 1: "CDS_ERR_ARG", 2: "CDS_ERR_CUDA", 3: "CDS_ERR_NO
                 4: "CDS_ERR_RANK_CAP", 5: "CDS_ERR_NO_CONVERGENCE", 6: "CDS_ERR_WORKSPACE",
                 7: "CDS_ERR_UNSUPPORTED", 8: "CDS_ERR_TIMEOUT", 9: "CDS_ERR_CAPACITY"}
 SCHEMES = {"full": 0, "atomic": 1}
-PRECISIONS = {"fp64": 0, "bf16x3": 2, "fp16x3": 3, "f32x2": 4}
+PRECISIONS = {"fp64": 0, "bf16x3": 2, "fp16x3": 3, "f32x2": 4, "tf32x3": 5}
 QP_OK, QP_NO_CONVERGENCE, QP_NONFINITE = 0, 1, 2
 
 _lib: Optional[ctypes.CDLL] = None
@@ -58,7 +58,7 @@ _SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_int64), _vp]),
     "cds_cd_decompose_to_mo_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "cds_cd_decompose_to_mo": (ctypes.c_int, [_i32, _vp, _vp, _vp, _f64, _i32, _i32, _vp, _i32, _i32,
-                                              _vp, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32),
+                                              _vp, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32),
                                               ctypes.POINTER(_f64), _vp, _vp, _vp, _sz, _vp]),
     "cds_acd_workspace_bytes": (_sz, [_i32]),
     "cds_acd_aux_pairs": (ctypes.c_int, [_i32, _vp, _vp, _f64, _vp, _i32, ctypes.POINTER(_i32), _vp,
@@ -250,8 +250,12 @@ def cds_cd_decompose_to_mo(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.T
                            L_out: Optional[torch.Tensor] = None,
                            Lov_out: Optional[torch.Tensor] = None,
                            Lp_out: Optional[torch.Tensor] = None,
-                           workspace: Optional[torch.Tensor] = None):
+                           workspace: Optional[torch.Tensor] = None,
+                           transform: str = "f32x2"):
     """Float-pair decomposition and transform in one pipelined call.
+
+    transform: the transform's precision, "f32x2" (float pairs on the FP32
+    units), "tf32x3" or "bf16x3" (split-precision tensor-core GEMMs).
 
     Returns (L [M, npair], piv [M], D, delta_eff, Lov [o, v, M], Lp [np, nmo, M])."""
     lib = load()
@@ -284,7 +288,7 @@ def cds_cd_decompose_to_mo(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.T
     M, de = _i32(0), _f64(0.0)
     st = lib.cds_cd_decompose_to_mo(n, _p(xyz), _p(alpha), _p(atom), float(delta),
                                     SCHEMES[scheme], int(max_rank), _p(C), nmo, nocc, _p(orb),
-                                    np_, _p(L_out), _p(piv), _p(D), ctypes.byref(M),
+                                    np_, PRECISIONS[transform], _p(L_out), _p(piv), _p(D), ctypes.byref(M),
                                     ctypes.byref(de), _p(Lov_out), _p(Lp_out), _p(workspace),
                                     workspace.numel(), _stream(dev))
     _check(st, "cds_cd_decompose_to_mo")
@@ -376,7 +380,8 @@ def cds_cd_to_mo(L: torch.Tensor, C: torch.Tensor, nocc: int, orbitals: torch.Te
                  workspace: Optional[torch.Tensor] = None, precision: str = "fp64"):
     """AO->MO transform of the Cholesky vectors (paper Eq. transformation).
 
-    precision: "fp64" or "f32x2" (float-pair arithmetic on the FP32 units).
+    precision: "fp64", "f32x2" (float-pair arithmetic on the FP32 units), or
+    "tf32x3" / "bf16x3" (split-precision tcgen05 GEMMs).
     Returns (Lov [o, v, M], Lp [np, nmo, M])."""
     lib = load()
     L = _dev(L, torch.float64, "L")

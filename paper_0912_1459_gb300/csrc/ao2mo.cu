@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "ao2mo_tc.cuh"
 
 namespace cds {
 
@@ -495,7 +496,8 @@ extern "C" size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t
                                             int32_t np) {
     (void)M;
     if (nbf <= 0 || nocc < 0 || np < 0) return 0;
-    return ao_layout(nullptr, nbf, nmo, nocc, np).bytes;
+    return std::max(ao_layout(nullptr, nbf, nmo, nocc, np).bytes,
+                    tr_tc_workspace_bytes(nbf, nmo, nocc, np, kAoBatch, CDS_PREC_TF32X3));
 }
 
 extern "C" int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
@@ -504,11 +506,21 @@ extern "C" int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, c
                          cudaStream_t stream) {
     if (nbf <= 0 || nmo <= 0 || nmo > nbf || nocc < 0 || nocc > nmo || M < 0 || np < 0)
         return CDS_ERR_ARG;
-    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return CDS_ERR_UNSUPPORTED;
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2 && !is_tr_tc(precision))
+        return CDS_ERR_UNSUPPORTED;
     if (M == 0) return CDS_OK;
     if (!L || !C || !Lov || (np > 0 && (!orb || !Lp))) return CDS_ERR_ARG;
+    if (!workspace || workspace_bytes < cds_cd_to_mo_workspace_bytes(nbf, nmo, nocc, M, np))
+        return CDS_ERR_WORKSPACE;
+    if (is_tr_tc(precision)) {
+        int st = tr_tc_columns(nbf, nmo, nocc, C, orb, np, kAoBatch, precision, workspace, stream);
+        for (int32_t K0 = 0; st == CDS_OK && K0 < M; K0 += kAoBatch)
+            st = tr_tc_batch(nbf, nmo, nocc, np, L, nullptr, K0, std::min(kAoBatch, M - K0), M, Lov,
+                             Lp, kAoBatch, precision, workspace, stream);
+        if (st) return st;
+        return tr_tc_status(nbf, nmo, nocc, np, kAoBatch, precision, workspace, stream);
+    }
     AoLayout lay = ao_layout(workspace, nbf, nmo, nocc, np);
-    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
     if (precision == CDS_PREC_F32X2)
         return cd_to_mo_f32x2(nbf, nmo, nocc, M, L, C, orb, np, Lov, Lp, lay, stream);
     const int64_t npair = npair_of(nbf);
@@ -678,7 +690,8 @@ int stream_wait(cudaStream_t waiter, cudaStream_t on) {
 struct FusedLayout {
     void* cd;
     size_t cd_bytes;
-    AoLayout ao;
+    AoLayout ao;       // float-pair transform
+    void* tr;          // tensor-core transform (the same bytes as ao)
     double* lov_cap;   // [nocc][nv][max_rank]
     double* lp_cap;    // [np][nmo][max_rank]
     size_t bytes;
@@ -690,9 +703,12 @@ FusedLayout fused_layout(void* ws, int32_t nbf, int32_t nmo, int32_t nocc, int32
     l.cd_bytes = cd_workspace_bytes_for(nbf, true);
     Carver c(ws);
     l.cd = c.take<char>(l.cd_bytes);
-    const size_t ao_bytes = ao_layout(nullptr, nbf, nmo, nocc, np).bytes;
+    const size_t ao_bytes = std::max(ao_layout(nullptr, nbf, nmo, nocc, np).bytes,
+                                     tr_tc_workspace_bytes(nbf, nmo, nocc, np, kAoBatch,
+                                                           CDS_PREC_TF32X3));
     char* ao = c.take<char>(ao_bytes);
     l.ao = ao_layout(ao, nbf, nmo, nocc, np);
+    l.tr = ao;
     l.lov_cap = c.take<double>((size_t)std::max<int64_t>((int64_t)nocc * (nmo - nocc) * max_rank, 1));
     l.lp_cap = c.take<double>((size_t)std::max<int64_t>((int64_t)np * nmo * max_rank, 1));
     l.bytes = c.off;
@@ -712,7 +728,8 @@ extern "C" size_t cds_cd_decompose_to_mo_workspace_bytes(int32_t nbf, int32_t nm
 extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const double* alpha,
                                       const int32_t* atom, double delta, int32_t scheme,
                                       int32_t max_rank, const double* C, int32_t nmo,
-                                      int32_t nocc, const int32_t* orb, int32_t np, double* L,
+                                      int32_t nocc, const int32_t* orb, int32_t np,
+                                      int32_t tr_precision, double* L,
                                       int32_t* piv, double* D, int32_t* M_out,
                                       double* delta_eff_out, double* Lov, double* Lp,
                                       void* workspace, size_t workspace_bytes,
@@ -720,21 +737,30 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
     if (nbf <= 0 || nmo <= 0 || nmo > nbf || nocc < 0 || nocc > nmo || np < 0 || max_rank < 0)
         return CDS_ERR_ARG;
     if (!C || !Lov || !M_out || (np > 0 && (!orb || !Lp))) return CDS_ERR_ARG;
+    if (tr_precision != CDS_PREC_F32X2 && !is_tr_tc(tr_precision)) return CDS_ERR_UNSUPPORTED;
+    const bool tcx = is_tr_tc(tr_precision);
     FusedLayout lay = fused_layout(workspace, nbf, nmo, nocc, max_rank, np);
     if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
     PipeStreams ps;
     int st = pipeline_streams(&ps);
     if (st) return st;
     if ((st = stream_wait(ps.cd, stream)) || (st = stream_wait(ps.tr, stream))) return st;
-    st = f32x2_columns(nbf, nmo, nocc, C, orb, np, lay.ao, ps.tr);
+    st = tcx ? tr_tc_columns(nbf, nmo, nocc, C, orb, np, kAoBatch, tr_precision, lay.tr, ps.tr)
+             : f32x2_columns(nbf, nmo, nocc, C, orb, np, lay.ao, ps.tr);
     if (st) return st;
     const float2* Lf = reinterpret_cast<const float2*>(L);
+    // vectors [K0, K0 + kb) from float-pair rows (Lf) or FP64 rows (L)
+    auto transform = [&](const double* Ld, const float2* Lq, int32_t K0, int32_t kb) -> int {
+        return tcx ? tr_tc_batch(nbf, nmo, nocc, np, Ld, Lq, K0, kb, max_rank, lay.lov_cap,
+                                 lay.lp_cap, kAoBatch, tr_precision, lay.tr, ps.tr)
+                   : f32x2_batch(nbf, nmo, nocc, np, Ld, Lq, K0, kb, max_rank, lay.lov_cap,
+                                 lay.lp_cap, lay.ao, ps.tr);
+    };
     int32_t next = 0;   // first vector not yet handed to the transform
     CdChunkHook hook = [&](int32_t rows, bool done) -> int {
         while (next < rows && (done || next + kAoBatch <= rows)) {
             const int32_t kb = std::min(kAoBatch, rows - next);
-            int s2 = f32x2_batch(nbf, nmo, nocc, np, nullptr, Lf, next, kb, max_rank, lay.lov_cap,
-                                 lay.lp_cap, lay.ao, ps.tr);
+            int s2 = transform(nullptr, Lf, next, kb);
             if (s2) return s2;
             next += kb;
         }
@@ -752,10 +778,7 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
         if (next < M) {
             if ((st = stream_wait(ps.tr, ps.cd))) return st;
             for (; next < M; next += kAoBatch)
-                if ((st = f32x2_batch(nbf, nmo, nocc, np, L, nullptr, next,
-                                      std::min(kAoBatch, M - next), max_rank, lay.lov_cap,
-                                      lay.lp_cap, lay.ao, ps.tr)))
-                    return st;
+                if ((st = transform(L, nullptr, next, std::min(kAoBatch, M - next)))) return st;
         }
         if (nocc > 0 && nv > 0)
             CDS_CUDA_TRY(cudaMemcpy2DAsync(Lov, (size_t)M * sizeof(double), lay.lov_cap,
@@ -769,5 +792,8 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
                                            cudaMemcpyDeviceToDevice, ps.tr));
     }
     if ((st = stream_wait(stream, ps.cd)) || (st = stream_wait(stream, ps.tr))) return st;
+    if (tcx && M > 0 && (st = tr_tc_status(nbf, nmo, nocc, np, kAoBatch, tr_precision, lay.tr,
+                                           stream)))
+        return st;
     return cd_st;
 }

@@ -1,0 +1,28 @@
+// Tensor-core (tcgen05, split-precision TF32X3 / BF16X3) AO->MO transform.
+#pragma once
+
+#include "common.cuh"
+
+namespace cds {
+
+// Workspace for batches of at most kb_max vectors (precision CDS_PREC_TF32X3
+// or CDS_PREC_BF16X3).
+size_t tr_tc_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, int32_t kb_max,
+                             int32_t precision);
+// Split C into the operand rows (once per call; also clears the error word).
+int tr_tc_columns(int32_t nbf, int32_t nmo, int32_t nocc, const double* C, const int32_t* orb,
+                  int32_t np, int32_t kb_max, int32_t precision, void* ws, cudaStream_t stream);
+// Vectors [K0, K0 + kb) (FP64 rows of L, or float-pair rows Lf when given)
+// into Lov[i][a][K] and Lp[t][q][K], K stride ldK.
+int tr_tc_batch(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, const double* L,
+                const float2* Lf, int32_t K0, int32_t kb, int64_t ldK, double* Lov, double* Lp,
+                int32_t kb_max, int32_t precision, void* ws, cudaStream_t stream);
+// Blocking: the kernels' error word (0, or CDS_ERR_TIMEOUT from a bounded wait).
+int tr_tc_status(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, int32_t kb_max,
+                 int32_t precision, void* ws, cudaStream_t stream);
+
+inline bool is_tr_tc(int32_t precision) {
+    return precision == CDS_PREC_TF32X3 || precision == CDS_PREC_BF16X3;
+}
+
+}  // namespace cds
