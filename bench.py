@@ -60,8 +60,11 @@ def parse():
     p.add_argument("--no-fp64-arm", action="store_true")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-mp2", action="store_true")
+    p.add_argument("--transform", default="ozaki", choices=["ozaki", "f32x2"],
+                   help="transform of the pipelined step: exact-slice tcgen05 GEMMs or "
+                        "float-pair GEMMs on the FP32 units")
     p.add_argument("--no-trtc", action="store_true",
-                   help="skip timing the tensor-core (TF32X3) transform on the step's vectors")
+                   help="skip timing the other transform forms on the step's vectors")
     p.add_argument("--no-acd", action="store_true",
                    help="skip the atomic-Cholesky-basis / V-approximation section")
     p.add_argument("--no-fuse", action="store_true",
@@ -273,7 +276,7 @@ def run_ours(args, dist: Dist):
             # decomposition and transform pipelined in one call: one stage
             L, piv, D, de, Lov, Lp = G.cds_cd_decompose_to_mo(
                 xyz, al, at, args.delta, C, m.nocc, orbs, args.scheme, L_out=Lbuf,
-                Lov_out=lov_buf, Lp_out=lp_buf, workspace=fz_ws)
+                Lov_out=lov_buf, Lp_out=lp_buf, workspace=fz_ws, transform=args.transform)
             ev[1].record()
             ev[2].record()
         else:
@@ -425,12 +428,15 @@ def run_ours(args, dist: Dist):
                       "achieved": sig_flops_qp / (med["qp"] / 1e3) / 1e12,
                       "note": f"{sig_passes_qp} Sigma passes (nE=1); {split} split products per MAC"}
     if fused:
-        # one stage for both; both parts are bound by FP32 instruction issue
-        # (float-pair arithmetic): 12 FP32 instructions per float-pair
-        # multiply-add in the projections, 11 in the transform GEMMs
+        # one stage for both.  The decomposition is bound by FP32 instruction
+        # issue (12 FP32 instructions per float-pair multiply-add in the
+        # projections); the float-pair transform adds 11 per multiply-add on
+        # the same pipes, the exact-slice transform runs on the tensor pipe
         N, o, nv = m.nbf, m.nocc, m.nbf - m.nocc
         tr_macs = float(M) * N * ((o + n_orb) * N + o * nv + n_orb * N)
-        instr = (12.0 * 4 * cd_stats["streamed"] + 12.0 * cd_stats["extra"]) * npr + 11.0 * tr_macs
+        instr = (12.0 * 4 * cd_stats["streamed"] + 12.0 * cd_stats["extra"]) * npr
+        if args.transform == "f32x2":
+            instr += 11.0 * tr_macs
         med["cd_transform"] = med.pop("cd")
         med.pop("transform")
         roof.pop("cd")
@@ -438,10 +444,13 @@ def run_ours(args, dist: Dist):
         roof["cd_transform"] = {
             "bound": "alu", "unit": "T FP32 instr/s", "peak": pk["fp32_issue_tinstr"],
             "achieved": instr / (med["cd_transform"] / 1e3) / 1e12,
-            "note": (f"pipelined decomposition + transform (cds_cd_decompose_to_mo): float-pair "
-                     f"FMAs of the projections ({cd_stats['passes']} streaming passes, "
-                     f"{cd_stats['streamed']} vectors streamed) and of the transform GEMMs; "
-                     f"peak = 152 SMs x 128 FP32 lanes x 2.07 GHz"),
+            "note": (f"pipelined decomposition + transform (cds_cd_decompose_to_mo, transform "
+                     f"{args.transform}): float-pair FMAs of the projections "
+                     f"({cd_stats['passes']} streaming passes, {cd_stats['streamed']} vectors "
+                     f"streamed)" + (" and of the transform GEMMs" if args.transform == "f32x2"
+                                     else "; the transform's 21 slice-pair GEMMs run on the "
+                                          "tensor pipe beside them") +
+                     "; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz"),
             "cd_stats": cd_stats}
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
@@ -509,7 +518,8 @@ def run_ours(args, dist: Dist):
     # ---- tensor-core (TF32X3) transform of the same vectors: time and error ----
     trtc = None
     if not args.no_trtc:
-        trtc = run_transform_tc(m, L, C, orbs, Lov)
+        trtc = {p_: run_transform_tc(m, L, C, orbs, Lov, p_)
+                for p_ in ("f32x2", "ozaki", "tf32x3") if not (fused and p_ == args.transform)}
 
     # ---- atomic Cholesky basis + V-approximation in place of the full CD ----
     acd = None
@@ -523,7 +533,8 @@ def run_ours(args, dist: Dist):
         "config": {"workload": WORKLOAD,
                    "delta": args.delta, "scheme": args.scheme, "cholesky_rank": M,
                    "orbitals": n_orb, "energies_per_orbital": m.nE, "newton_conv_Ha": 1e-5,
-                   "precision": prec, "transform_precision": tr_prec,
+                   "precision": prec,
+                   "transform_precision": args.transform if fused else tr_prec,
                    "newton": "cached numerators" if cached else "recomputed integrals",
                    "parallelism": f"replicas{dist.world}",
                    "l2": "inputs larger than L2 (L is %.1f GB, Lov %.0f MB)" % (M * npr * 8 / 1e9, Lov.numel() * 8 / 1e6)},
@@ -580,11 +591,11 @@ def run_mp2(m, Lov, eps, prec, pk, reps: int = 3):
                          "note": "3 split products x 2 M (o v)^2 per evaluation"}}
 
 
-def run_transform_tc(m, L, C, orbs, Lov_ref):
-    """The transform as split-precision tcgen05 GEMMs (TF32X3) on the step's
-    Cholesky vectors: CUDA-event time of one call after a warm-up, and its
-    error against the step's float-pair Lov (FP32 accumulation meets the
-    cancellation of this C, |C| up to 106)."""
+def run_transform_tc(m, L, C, orbs, Lov_ref, prec):
+    """One transform form on the step's Cholesky vectors: CUDA-event time of
+    one call after a warm-up, and its error against the step's Lov.  TF32X3
+    accumulates in FP32 and cannot carry the cancellation of this C (|C| up
+    to 106); the exact-slice form (ozaki) and float pairs can."""
     import torch
     import paper_0912_1459_gb300 as G
 
@@ -592,22 +603,21 @@ def run_transform_tc(m, L, C, orbs, Lov_ref):
     M = L.shape[0]
     ws = torch.empty(lib.cds_cd_to_mo_workspace_bytes(m.nbf, m.nbf, m.nocc, M, len(m.orbitals)),
                      dtype=torch.uint8, device=L.device)
-    G.cds_cd_to_mo(L[:32], C, m.nocc, orbs, workspace=ws, precision="tf32x3")
+    G.cds_cd_to_mo(L[:32], C, m.nocc, orbs, workspace=ws, precision=prec)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record()
-    Lov, _ = G.cds_cd_to_mo(L, C, m.nocc, orbs, workspace=ws, precision="tf32x3")
+    Lov, _ = G.cds_cd_to_mo(L, C, m.nocc, orbs, workspace=ws, precision=prec)
     b.record()
     torch.cuda.synchronize()
     t = a.elapsed_time(b)
     err = float((Lov - Lov_ref).abs().max() / Lov_ref.abs().max())
-    # 3 split products x 2 flops x (GEMM 1 + GEMM 2 + GEMM 3) multiply-adds
+    # products per multiply-add: 3 split (tf32x3), 21 slice pairs (ozaki), 1 (f32x2)
     N, o, v, np_ = m.nbf, m.nocc, m.nbf - m.nocc, len(m.orbitals)
-    flops = 3 * 2.0 * M * ((o + np_) * N * N + o * v * N + np_ * N * N)
-    return {"precision": "tf32x3", "ms": t, "tflops": flops / (t / 1e3) / 1e12,
-            "lov_rel_err_vs_f32x2": err,
-            "note": "opt-in; FP32 accumulation cannot carry the ~1e6 cancellation of this "
-                    "C = S^-1/2 Q, so the step keeps the float-pair transform"}
+    macs = float(M) * ((o + np_) * N * N + o * v * N + np_ * N * N)
+    prods = {"tf32x3": 3, "ozaki": 21, "f32x2": 1}[prec]
+    return {"ms": t, "tflops_of_products": prods * 2.0 * macs / (t / 1e3) / 1e12,
+            "lov_rel_err_vs_step": err}
 
 
 def run_acd(m, delta, orbs, eps, prec, w_cd, P_cd):

@@ -68,9 +68,13 @@ typedef enum {
     CDS_PREC_F32X2 = 4,  /* decomposition and transform: (hi, lo) float pairs with exact
                             product and sum errors, ~2^-44 relative per operation, on the
                             FP32 units */
-    CDS_PREC_TF32X3 = 5  /* transform: tcgen05 tensor cores, each operand split into TF32
+    CDS_PREC_TF32X3 = 5, /* transform: tcgen05 tensor cores, each operand split into TF32
                             hi + lo, hi.hi + hi.lo + lo.hi with FP32 accumulation,
                             ~2^-21 relative per product (BF16X3 there: ~2^-17) */
+    CDS_PREC_OZAKI = 6   /* transform: tcgen05 tensor cores with exact slice products
+                            (rows cut into six 7-bit BF16 digits below a power-of-two
+                            scale, 21 slice pairs, exact FP32 sums for nbf <= 1040):
+                            ~2^-42 of the row scales, for ill-conditioned C */
 } cds_precision;
 
 /* Newton status per orbital (paper Eq. NR). */
@@ -194,8 +198,8 @@ size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int3
  * kernels' error word is read at the end, CDS_ERR_TIMEOUT if a bounded wait
  * gave up).  L: device [M][npair]; C: device [nbf][nmo]; orb: device [np]
  * int32 MO indices in [0, nmo).  precision: CDS_PREC_FP64, CDS_PREC_F32X2,
- * CDS_PREC_TF32X3 or CDS_PREC_BF16X3 (the last two on sm_103 only, else
- * CDS_ERR_UNSUPPORTED).  Outputs (device, fp64): Lov [nocc][nmo-nocc][M],
+ * CDS_PREC_TF32X3, CDS_PREC_BF16X3 or CDS_PREC_OZAKI (the last three on sm_103
+ * only, OZAKI for nbf <= 1040; else CDS_ERR_UNSUPPORTED).  Outputs (device, fp64): Lov [nocc][nmo-nocc][M],
  * Lp [np][nmo][M] (Lp may be NULL when np == 0). */
 int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
                  const double* C, const int32_t* orb, int32_t np, int32_t precision,
@@ -243,8 +247,8 @@ int cds_ri_factors(int32_t nbf, const double* xyz, const double* alpha, const in
 
 /* ------------------------------------------------------------------------
  * Decomposition and transform in one call.  Runs cds_cd_decompose(F32X2) and
- * cds_cd_to_mo(tr_precision: CDS_PREC_F32X2, CDS_PREC_TF32X3 or
- * CDS_PREC_BF16X3) with the transform of each batch of 32 finished vectors
+ * cds_cd_to_mo(tr_precision: CDS_PREC_F32X2, CDS_PREC_TF32X3, CDS_PREC_BF16X3
+ * or CDS_PREC_OZAKI) with the transform of each batch of 32 finished vectors
  * overlapped with the decomposition of the next ones, on two library streams
  * (the decomposition's at the highest priority), joined to `stream` on
  * return.  The results are those of the two calls in sequence.

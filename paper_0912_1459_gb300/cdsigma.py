@@ -25,7 +25,7 @@ STATUS_NAMES = {0: "CDS_OK", 1: "CDS_ERR_ARG", 2: "CDS_ERR_CUDA", 3: "CDS_ERR_NO
                 4: "CDS_ERR_RANK_CAP", 5: "CDS_ERR_NO_CONVERGENCE", 6: "CDS_ERR_WORKSPACE",
                 7: "CDS_ERR_UNSUPPORTED", 8: "CDS_ERR_TIMEOUT", 9: "CDS_ERR_CAPACITY"}
 SCHEMES = {"full": 0, "atomic": 1}
-PRECISIONS = {"fp64": 0, "bf16x3": 2, "fp16x3": 3, "f32x2": 4, "tf32x3": 5}
+PRECISIONS = {"fp64": 0, "bf16x3": 2, "fp16x3": 3, "f32x2": 4, "tf32x3": 5, "ozaki": 6}
 QP_OK, QP_NO_CONVERGENCE, QP_NONFINITE = 0, 1, 2
 
 _lib: Optional[ctypes.CDLL] = None
@@ -255,7 +255,8 @@ def cds_cd_decompose_to_mo(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.T
     """Float-pair decomposition and transform in one pipelined call.
 
     transform: the transform's precision, "f32x2" (float pairs on the FP32
-    units), "tf32x3" or "bf16x3" (split-precision tensor-core GEMMs).
+    units), "ozaki" (exact-slice tensor-core GEMMs), "tf32x3" or "bf16x3"
+    (split-precision tensor-core GEMMs, for well-conditioned C only).
 
     Returns (L [M, npair], piv [M], D, delta_eff, Lov [o, v, M], Lp [np, nmo, M])."""
     lib = load()
@@ -380,8 +381,9 @@ def cds_cd_to_mo(L: torch.Tensor, C: torch.Tensor, nocc: int, orbitals: torch.Te
                  workspace: Optional[torch.Tensor] = None, precision: str = "fp64"):
     """AO->MO transform of the Cholesky vectors (paper Eq. transformation).
 
-    precision: "fp64", "f32x2" (float-pair arithmetic on the FP32 units), or
-    "tf32x3" / "bf16x3" (split-precision tcgen05 GEMMs).
+    precision: "fp64", "f32x2" (float-pair arithmetic on the FP32 units),
+    "ozaki" (exact-slice tcgen05 GEMMs, nbf <= 1040), or "tf32x3" / "bf16x3"
+    (split-precision tcgen05 GEMMs, for well-conditioned C only).
     Returns (Lov [o, v, M], Lp [np, nmo, M])."""
     lib = load()
     L = _dev(L, torch.float64, "L")

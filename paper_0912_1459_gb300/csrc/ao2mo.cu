@@ -497,7 +497,7 @@ extern "C" size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t
     (void)M;
     if (nbf <= 0 || nocc < 0 || np < 0) return 0;
     return std::max(ao_layout(nullptr, nbf, nmo, nocc, np).bytes,
-                    tr_tc_workspace_bytes(nbf, nmo, nocc, np, kAoBatch, CDS_PREC_TF32X3));
+                    tr_any_workspace_bytes(nbf, nmo, nocc, np, kAoBatch));
 }
 
 extern "C" int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
@@ -513,12 +513,12 @@ extern "C" int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, c
     if (!workspace || workspace_bytes < cds_cd_to_mo_workspace_bytes(nbf, nmo, nocc, M, np))
         return CDS_ERR_WORKSPACE;
     if (is_tr_tc(precision)) {
-        int st = tr_tc_columns(nbf, nmo, nocc, C, orb, np, kAoBatch, precision, workspace, stream);
+        int st = tr_any_columns(precision, nbf, nmo, nocc, C, orb, np, kAoBatch, workspace, stream);
         for (int32_t K0 = 0; st == CDS_OK && K0 < M; K0 += kAoBatch)
-            st = tr_tc_batch(nbf, nmo, nocc, np, L, nullptr, K0, std::min(kAoBatch, M - K0), M, Lov,
-                             Lp, kAoBatch, precision, workspace, stream);
+            st = tr_any_batch(precision, nbf, nmo, nocc, np, L, nullptr, K0,
+                              std::min(kAoBatch, M - K0), M, Lov, Lp, kAoBatch, workspace, stream);
         if (st) return st;
-        return tr_tc_status(nbf, nmo, nocc, np, kAoBatch, precision, workspace, stream);
+        return tr_any_status(precision, nbf, nmo, nocc, np, kAoBatch, workspace, stream);
     }
     AoLayout lay = ao_layout(workspace, nbf, nmo, nocc, np);
     if (precision == CDS_PREC_F32X2)
@@ -704,8 +704,7 @@ FusedLayout fused_layout(void* ws, int32_t nbf, int32_t nmo, int32_t nocc, int32
     Carver c(ws);
     l.cd = c.take<char>(l.cd_bytes);
     const size_t ao_bytes = std::max(ao_layout(nullptr, nbf, nmo, nocc, np).bytes,
-                                     tr_tc_workspace_bytes(nbf, nmo, nocc, np, kAoBatch,
-                                                           CDS_PREC_TF32X3));
+                                     tr_any_workspace_bytes(nbf, nmo, nocc, np, kAoBatch));
     char* ao = c.take<char>(ao_bytes);
     l.ao = ao_layout(ao, nbf, nmo, nocc, np);
     l.tr = ao;
@@ -745,14 +744,14 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
     int st = pipeline_streams(&ps);
     if (st) return st;
     if ((st = stream_wait(ps.cd, stream)) || (st = stream_wait(ps.tr, stream))) return st;
-    st = tcx ? tr_tc_columns(nbf, nmo, nocc, C, orb, np, kAoBatch, tr_precision, lay.tr, ps.tr)
+    st = tcx ? tr_any_columns(tr_precision, nbf, nmo, nocc, C, orb, np, kAoBatch, lay.tr, ps.tr)
              : f32x2_columns(nbf, nmo, nocc, C, orb, np, lay.ao, ps.tr);
     if (st) return st;
     const float2* Lf = reinterpret_cast<const float2*>(L);
     // vectors [K0, K0 + kb) from float-pair rows (Lf) or FP64 rows (L)
     auto transform = [&](const double* Ld, const float2* Lq, int32_t K0, int32_t kb) -> int {
-        return tcx ? tr_tc_batch(nbf, nmo, nocc, np, Ld, Lq, K0, kb, max_rank, lay.lov_cap,
-                                 lay.lp_cap, kAoBatch, tr_precision, lay.tr, ps.tr)
+        return tcx ? tr_any_batch(tr_precision, nbf, nmo, nocc, np, Ld, Lq, K0, kb, max_rank,
+                                  lay.lov_cap, lay.lp_cap, kAoBatch, lay.tr, ps.tr)
                    : f32x2_batch(nbf, nmo, nocc, np, Ld, Lq, K0, kb, max_rank, lay.lov_cap,
                                  lay.lp_cap, lay.ao, ps.tr);
     };
@@ -792,8 +791,8 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
                                            cudaMemcpyDeviceToDevice, ps.tr));
     }
     if ((st = stream_wait(stream, ps.cd)) || (st = stream_wait(stream, ps.tr))) return st;
-    if (tcx && M > 0 && (st = tr_tc_status(nbf, nmo, nocc, np, kAoBatch, tr_precision, lay.tr,
-                                           stream)))
+    if (tcx && M > 0 &&
+        (st = tr_any_status(tr_precision, nbf, nmo, nocc, np, kAoBatch, lay.tr, stream)))
         return st;
     return cd_st;
 }

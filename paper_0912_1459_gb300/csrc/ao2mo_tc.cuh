@@ -1,6 +1,8 @@
 // Tensor-core (tcgen05, split-precision TF32X3 / BF16X3) AO->MO transform.
 #pragma once
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace cds {
@@ -21,8 +23,48 @@ int tr_tc_batch(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, const double
 int tr_tc_status(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, int32_t kb_max,
                  int32_t precision, void* ws, cudaStream_t stream);
 
+// Exact-slice (Ozaki) form, CDS_PREC_OZAKI: nbf <= 1040.
+size_t tr_oz_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, int32_t kb_max);
+int tr_oz_columns(int32_t nbf, int32_t nmo, int32_t nocc, const double* C, const int32_t* orb,
+                  int32_t np, int32_t kb_max, void* ws, cudaStream_t stream);
+int tr_oz_batch(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, const double* L,
+                const float2* Lf, int32_t K0, int32_t kb, int64_t ldK, double* Lov, double* Lp,
+                int32_t kb_max, void* ws, cudaStream_t stream);
+int tr_oz_status(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, int32_t kb_max, void* ws,
+                 cudaStream_t stream);
+
+// Tensor-core transform of any kind: columns once, then batches, then the
+// error word (precision CDS_PREC_TF32X3, CDS_PREC_BF16X3 or CDS_PREC_OZAKI).
+inline int tr_any_columns(int32_t precision, int32_t nbf, int32_t nmo, int32_t nocc,
+                          const double* C, const int32_t* orb, int32_t np, int32_t kb_max, void* ws,
+                          cudaStream_t stream) {
+    return precision == CDS_PREC_OZAKI
+               ? tr_oz_columns(nbf, nmo, nocc, C, orb, np, kb_max, ws, stream)
+               : tr_tc_columns(nbf, nmo, nocc, C, orb, np, kb_max, precision, ws, stream);
+}
+inline int tr_any_batch(int32_t precision, int32_t nbf, int32_t nmo, int32_t nocc, int32_t np,
+                        const double* L, const float2* Lf, int32_t K0, int32_t kb, int64_t ldK,
+                        double* Lov, double* Lp, int32_t kb_max, void* ws, cudaStream_t stream) {
+    return precision == CDS_PREC_OZAKI
+               ? tr_oz_batch(nbf, nmo, nocc, np, L, Lf, K0, kb, ldK, Lov, Lp, kb_max, ws, stream)
+               : tr_tc_batch(nbf, nmo, nocc, np, L, Lf, K0, kb, ldK, Lov, Lp, kb_max, precision, ws,
+                             stream);
+}
+inline int tr_any_status(int32_t precision, int32_t nbf, int32_t nmo, int32_t nocc, int32_t np,
+                         int32_t kb_max, void* ws, cudaStream_t stream) {
+    return precision == CDS_PREC_OZAKI
+               ? tr_oz_status(nbf, nmo, nocc, np, kb_max, ws, stream)
+               : tr_tc_status(nbf, nmo, nocc, np, kb_max, precision, ws, stream);
+}
+inline size_t tr_any_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np,
+                                     int32_t kb_max) {
+    return std::max(tr_tc_workspace_bytes(nbf, nmo, nocc, np, kb_max, CDS_PREC_TF32X3),
+                    tr_oz_workspace_bytes(nbf, nmo, nocc, np, kb_max));
+}
+
 inline bool is_tr_tc(int32_t precision) {
-    return precision == CDS_PREC_TF32X3 || precision == CDS_PREC_BF16X3;
+    return precision == CDS_PREC_TF32X3 || precision == CDS_PREC_BF16X3 ||
+           precision == CDS_PREC_OZAKI;
 }
 
 }  // namespace cds

@@ -16,9 +16,10 @@ Here, on well-conditioned inputs:
   requested orbitals, a single occupied orbital;
 * the pipelined decomposition + transform with the tensor-core transform
   equals the separate calls' results to the same bound;
-* the error model's other side: on the ring molecule the FP32-accumulated
-  form is off by far more than the float-pair form (documents why the
-  float-pair transform is the default).
+* the exact-slice form (OZAKI: six 7-bit BF16 slices per operand, exact
+  FP32 sums of the leading slice pairs) within 2e-5 everywhere, also on the
+  ring molecule, where the FP32-accumulated split form is off by more than
+  1e-3.
 """
 import numpy as np
 import pytest
@@ -34,7 +35,7 @@ if not torch.cuda.is_available():
 import paper_0912_1459_gb300 as G  # noqa: E402
 
 DEV = torch.device("cuda:0")
-TOL = {"tf32x3": 2e-6, "bf16x3": 5e-5}
+TOL = {"tf32x3": 2e-6, "bf16x3": 5e-5, "ozaki": 2e-5}
 
 
 def dev(a):
@@ -64,7 +65,7 @@ def case(request):
     return request.param, L, C, nocc, orbs, Lov, Lp
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "ozaki"])
 def test_tc_transform_matches_fp64(case, prec):
     name, L, C, nocc, orbs, Lov, Lp = case
     Lov2, Lp2 = G.cds_cd_to_mo(L, C, nocc, orbs, precision=prec)
@@ -73,7 +74,7 @@ def test_tc_transform_matches_fp64(case, prec):
     assert e_ov <= TOL[prec] and e_p <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "ozaki"])
 def test_tc_transform_ragged_shapes(case, prec):
     name, L, C, nocc, orbs, Lov, Lp = case
     # a rank that is not a multiple of the batch
@@ -89,7 +90,7 @@ def test_tc_transform_ragged_shapes(case, prec):
     assert rel_err(a, ref_a) <= TOL[prec] and rel_err(b, ref_b) <= TOL[prec]
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3", "ozaki"])
 def test_fused_with_tc_transform(prec):
     m = O.molecule("c0")
     xyz, al, at = dev(m.basis.xyz), dev(m.basis.alpha), dev(m.basis.atom.astype(np.int32))
@@ -102,15 +103,18 @@ def test_fused_with_tc_transform(prec):
     assert rel_err(Lov, ref_ov) <= TOL[prec] and rel_err(Lp, ref_p) <= TOL[prec]
 
 
-def test_ill_conditioned_coefficients_need_float_pairs():
-    """Ring molecule (max|C| = 294): the float-pair transform stays within
-    1e-7 of max|Lov| while the FP32-accumulated tensor-core form loses
-    more than 1e-3 (cancellation ratio ~1e6)."""
+def test_ill_conditioned_coefficients():
+    """Ring molecule (max|C| = 294, cancellation ratio ~1e6): the float-pair
+    transform stays within 1e-7 of max|Lov| and the exact-slice tensor-core
+    form within 2e-5, while the FP32-accumulated split form loses more than
+    1e-3."""
     m = O.molecule("c1")
     L = dev(O.decomposition("c1", m.delta).L[:64])
     C, orbs = dev(m.C), dev(m.orbitals)
-    ref = G.cds_cd_to_mo(L, C, m.nocc, orbs, precision="fp64")[0]
+    ref, ref_p = G.cds_cd_to_mo(L, C, m.nocc, orbs, precision="fp64")
     e_f2 = rel_err(G.cds_cd_to_mo(L, C, m.nocc, orbs, precision="f32x2")[0], ref)
     e_tc = rel_err(G.cds_cd_to_mo(L, C, m.nocc, orbs, precision="tf32x3")[0], ref)
-    print(f"ring: f32x2 {e_f2:.2e} tf32x3 {e_tc:.2e}")
-    assert e_f2 <= 1e-7 and e_tc > 1e-3
+    oz_ov, oz_p = G.cds_cd_to_mo(L, C, m.nocc, orbs, precision="ozaki")
+    e_oz, e_ozp = rel_err(oz_ov, ref), rel_err(oz_p, ref_p)
+    print(f"ring: f32x2 {e_f2:.2e} tf32x3 {e_tc:.2e} ozaki {e_oz:.2e} / {e_ozp:.2e}")
+    assert e_f2 <= 1e-7 and e_tc > 1e-3 and e_oz <= 2e-5 and e_ozp <= 2e-5
