@@ -27,7 +27,9 @@
 //   GEMM 3   Lp[t][q][K]     = sum_nu T[(o + t, K)][nu] C[nu][q]
 // with every operand sliced by rows (U rows (K, nu), Cj / C columns, T rows).
 //
-// Kernel: M tile 128, N tile 64; 3 TMA stages of {6 A slices, 6 B slices}
+// Kernel: M tile 128, N tile 64, tiles ordered N fastest (the CTAs that share
+// an A tile run together, so it is read from DRAM once); 3 TMA stages of
+// {6 A slices, 6 B slices}
 // (64-byte swizzled rows of 32 BF16); warp 0 = TMA producer, warp 1 = TMEM
 // allocator + MMA issuer (21 MMAs per 16 k), warps 2..5 = epilogue.  Every
 // wait is bounded and sets an error word instead of hanging.
@@ -173,7 +175,7 @@ k_oz_gemm(const __grid_constant__ Maps maps, const Args g, int32_t* __restrict__
             for (int i = 0; i < NSTAGE; ++i) last_parity[i] = -1;
             bool ok = true;
             for (int64_t tile = blockIdx.x; ok && tile < ntiles; tile += gridDim.x) {
-                const int mt = (int)(tile % g.mtiles), nt = (int)(tile / g.mtiles);
+                const int nt = (int)(tile % g.ntiles), mt = (int)(tile / g.ntiles);
                 for (int kb = 0; kb < g.kblocks; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, verr)) { ok = false; break; }
                     mbar_arrive_expect_tx(&full[stage], (uint32_t)STAGE_BYTES);
@@ -232,7 +234,7 @@ k_oz_gemm(const __grid_constant__ Maps maps, const Args g, int32_t* __restrict__
             const bool bad = !mbar_wait(tfull, aphase, verr) || *verr;
             if (epi_any(bad)) break;
             fence_after();
-            const int mt = (int)(tile % g.mtiles), nt = (int)(tile / g.mtiles);
+            const int nt = (int)(tile % g.ntiles), mt = (int)(tile / g.ntiles);
             const int64_t m = (int64_t)mt * TM + row;
             const bool mok = m < g.m;
             const int64_t ob = mok ? (m / g.kdiv) * g.rs_hi + (m % g.kdiv) * g.rs_lo : 0;

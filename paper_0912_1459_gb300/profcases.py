@@ -4,7 +4,8 @@ Each case builds only the inputs of one library call at C60 shape (N = 840,
 o = 180, v = 660) and runs it twice, so an ``ncu -k <kernel> -c <n>`` capture
 holds a few GB of device memory at most and replays in seconds:
 
-  python -m paper_0912_1459_gb300.profcases transform   # k_dfgemm / k_dgemm
+  python -m paper_0912_1459_gb300.profcases transform   # k_dfgemm (float pairs)
+  python -m paper_0912_1459_gb300.profcases transform_oz  # k_oz_gemm, k_oz_slice (exact slices)
   python -m paper_0912_1459_gb300.profcases sigma1      # k_sigma_tc, nE = 1
   python -m paper_0912_1459_gb300.profcases sigma64     # k_sigma_tc, nE = 64
   python -m paper_0912_1459_gb300.profcases cd          # k_cd_update, FP64 (C60, 1024 steps max)
@@ -39,9 +40,9 @@ def main(mode: str) -> None:
     m = W.config2()
     g = torch.Generator(device=dev)
     g.manual_seed(0)
-    if mode in ("transform", "transform64"):
+    if mode in ("transform", "transform64", "transform_oz"):
         L = torch.randn((128, G.npair(m.nbf)), dtype=torch.float64, device=dev, generator=g) * 1e-2
-        prec = "fp64" if mode == "transform64" else "f32x2"
+        prec = {"transform64": "fp64", "transform_oz": "ozaki"}.get(mode, "f32x2")
         for rep in range(2):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record()
