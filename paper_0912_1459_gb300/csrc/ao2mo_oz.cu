@@ -433,12 +433,9 @@ int run_gemm(const __nv_bfloat16* a, int64_t a_plane, const float* sa, int64_t a
     if (!make_slice_map(&maps.a, a, kdim, a_rows, ld, a_plane, TM) ||
         !make_slice_map(&maps.b, b, kdim, b_rows, ld, b_plane, TN))
         return CDS_ERR_CUDA;
-    static bool attr_set = false;
-    if (!attr_set) {
-        CDS_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)SMEM_BYTES));
-        attr_set = true;
-    }
+    // per launch: the attribute belongs to the current device
+    CDS_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)SMEM_BYTES));
     const int64_t tiles = (int64_t)g.mtiles * g.ntiles;
     const int grid = (int)std::min<int64_t>(tiles, device_sms());
     k_oz_gemm<<<grid, THREADS, SMEM_BYTES, stream>>>(maps, g, err);

@@ -419,12 +419,9 @@ int run_gemm(const void* a_hi, const void* a_lo, int64_t a_rows, const void* b_h
         !make_operand_map(&maps.b_hi, TF32, b_hi, kdim, b_rows, ld, g.tn) ||
         !make_operand_map(&maps.b_lo, TF32, b_lo, kdim, b_rows, ld, g.tn))
         return CDS_ERR_CUDA;
-    static bool attr_set = false;
-    if (!attr_set) {
-        CDS_CUDA_TRY(cudaFuncSetAttribute(k_tr_gemm<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)SMEM_BYTES));
-        attr_set = true;
-    }
+    // per launch: the attribute belongs to the current device
+    CDS_CUDA_TRY(cudaFuncSetAttribute(k_tr_gemm<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)SMEM_BYTES));
     const int64_t tiles = (int64_t)g.mtiles * g.ntiles;
     const int grid = (int)std::min<int64_t>(tiles, device_sms());
     k_tr_gemm<TF32><<<grid, THREADS, SMEM_BYTES, stream>>>(maps, g, err);
