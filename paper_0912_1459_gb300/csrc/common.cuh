@@ -9,6 +9,7 @@
 #include <functional>
 
 #include "cdsigma.h"
+#include "boys_table.h"
 
 #define CDS_CUDA_TRY(expr)                                   \
     do {                                                     \
@@ -78,17 +79,18 @@ __device__ __forceinline__ void eri_xs(double p, double px, double py, double pz
 // pi^3 (K_I/p)(K_J/q) / sqrt(x) (the point-charge form).
 __device__ __forceinline__ bool eri_is_far(double x, double s) { return x >= kErfOneT * s; }
 __device__ __forceinline__ double eri_far(double kk, double x) { return kPi3 * kk * rsqrt(x); }
-// T < kErfOneT: F0 through erf(sqrt T), or 1 - T/3 below T = 1e-10.  kk = (K_I/p)(K_J/q).
+// T < kErfOneT: F0(T) from its Taylor expansion around the nearest point of a
+// 1/16 grid (boys_table.h: F_0(T_i + d) = sum_m F_m(T_i) (-d)^m / m!, eight
+// terms, truncation below 2e-18).  kk = (K_I/p)(K_J/q).
 __device__ __forceinline__ double eri_near(double kk, double x, double s) {
     const double rs = rsqrt(s);
     const double T = x * (rs * rs);
-    double f;
-    if (T < 1e-10) {
-        f = 1.0 - T * (1.0 / 3.0);
-    } else {
-        const double rT = rsqrt(T);
-        f = kHalfSqrtPi * rT * erf(T * rT);
-    }
+    const int i = min(max(__double2int_rn(T * kBoysPerUnit), 0), kBoysPoints - 1);
+    const double d = T - (double)i * (1.0 / kBoysPerUnit);
+    const double* c = kBoysTaylor[i];
+    double f = c[kBoysOrder - 1];
+#pragma unroll
+    for (int m = kBoysOrder - 2; m >= 0; --m) f = fma(f, d, c[m]);
     return kTwoPi52 * kk * rs * f;
 }
 
