@@ -82,55 +82,53 @@ constexpr float kMidT = 16.f;   // erfc(sqrt T) small enough for FP32 above
 constexpr float kPi3Hi = (float)kPi3;
 constexpr float kPi3Lo = (float)(kPi3 - (double)kPi3Hi);
 
-// Integral column (rho_I|rho_P) in float pairs (blockDim.x == NT, grid-
-// stride over the pairs, NT per pass): pairs with T >= 16 in
-// float-pair arithmetic from the float-pair pair data (the point-charge form
-// pi^3 (K_I/p)(K_P/q) / sqrt(p q |P-Q|^2), times 1 - erfc(sqrt T) below
-// T = 36), the others gathered and evaluated in FP64 as in eri_column_fp64.
+constexpr float kTwoPi52Hi = (float)kTwoPi52;
+constexpr float kTwoPi52Lo = (float)(kTwoPi52 - (double)kTwoPi52Hi);
+
+// Integral column (rho_I|rho_P) in float pairs from the float-pair pair data
+// (grid-stride over the pairs, NT per pass), T = x / (p + q):
+//   T >= 16: the point-charge form pi^3 (K_I/p)(K_P/q) / sqrt(p q |P-Q|^2),
+//            times 1 - erfc(sqrt T) below T = 36;
+//   T < 16:  2 pi^(5/2) (K_I/p)(K_P/q) / sqrt(p + q) F0(T), F0 from its Taylor
+//            expansion around the nearest point of the 1/16 grid
+//            (kBoysTaylorF2, eight float-pair terms).
 // Values below the FP32 range (|K/p| < 1e-38, pairs of far-apart centres)
 // come out as 0, an absolute error far below any other in the decomposition.
 // The column is stored as float pairs.
 template <int NT>
 __device__ __forceinline__ void eri_column_df(PairSoA pd, PairF2 pf, int64_t n, int64_t P,
                                               float2* __restrict__ ecol, int bid, int nblk) {
-    __shared__ int near_i[NT];
-    __shared__ int near_n;
+    (void)pd;
     const float2 q = pf.p[P], qx = pf.Px[P], qy = pf.Py[P], qz = pf.Pz[P], kq = pf.Kp[P];
     const float2 pi3kq = df_mul(make_float2(kPi3Hi, kPi3Lo), kq);
-    for (int64_t I0 = (int64_t)bid * NT; I0 < n; I0 += (int64_t)nblk * NT) {
-        if (threadIdx.x == 0) near_n = 0;
-        __syncthreads();
-        const int64_t I = I0 + threadIdx.x;
-        if (I < n) {
-            const float2 pI = pf.p[I];
-            const float2 dx = df_add(pf.Px[I], df_neg(qx));
-            const float2 dy = df_add(pf.Py[I], df_neg(qy));
-            const float2 dz = df_add(pf.Pz[I], df_neg(qz));
-            const float2 d2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
-            const float2 x = df_mul(df_mul(pI, q), d2);
-            const float sf = pI.x + q.x;
-            if (x.x >= kMidT * sf) {
-                // T >= 16: F0 = (1/2) sqrt(pi/T) (1 - erfc(sqrt T)), and erfc(sqrt T)
-                // <= 1.6e-8 is needed only to FP32 precision (its error then stays
-                // below 1e-14 of F0); above T = 36 it is below half an ulp
-                float2 e = df_mul(df_mul(pf.Kp[I], pi3kq), df_rsqrt(x));
-                if (x.x < kFarT * sf) e = df_mul(e, make_float2(1.f, -erfcf(sqrtf(x.x / sf))));
-                ecol[I] = e;
-            } else {
-                near_i[atomicAdd(&near_n, 1)] = threadIdx.x;
-            }
+    const float2 tpkq = df_mul(make_float2(kTwoPi52Hi, kTwoPi52Lo), kq);
+    for (int64_t I = (int64_t)bid * NT + threadIdx.x; I < n; I += (int64_t)nblk * NT) {
+        const float2 pI = pf.p[I];
+        const float2 dx = df_add(pf.Px[I], df_neg(qx));
+        const float2 dy = df_add(pf.Py[I], df_neg(qy));
+        const float2 dz = df_add(pf.Pz[I], df_neg(qz));
+        const float2 d2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+        const float2 x = df_mul(df_mul(pI, q), d2);
+        const float sf = pI.x + q.x;
+        float2 e;
+        if (x.x >= kMidT * sf) {
+            // T >= 16: F0 = (1/2) sqrt(pi/T) (1 - erfc(sqrt T)), and erfc(sqrt T)
+            // <= 1.6e-8 is needed only to FP32 precision (its error then stays
+            // below 1e-14 of F0); above T = 36 it is below half an ulp
+            e = df_mul(df_mul(pf.Kp[I], pi3kq), df_rsqrt(x));
+            if (x.x < kFarT * sf) e = df_mul(e, make_float2(1.f, -erfcf(sqrtf(x.x / sf))));
+        } else {
+            const float2 rs = df_rsqrt(df_add(pI, q));                  // 1 / sqrt(p + q)
+            const float2 T = df_mul(x, df_mul(rs, rs));
+            const int i = min(max(__float2int_rn(T.x * (float)kBoysPerUnit), 0), kBoysPoints - 1);
+            const float2 d = df_add(T, make_float2(-(float)i * (1.f / (float)kBoysPerUnit), 0.f));
+            const float2* c = kBoysTaylorF2[i];
+            float2 f = c[kBoysOrder - 1];
+#pragma unroll
+            for (int m = kBoysOrder - 2; m >= 0; --m) f = df_add(df_mul(f, d), c[m]);
+            e = df_mul(df_mul(df_mul(pf.Kp[I], tpkq), rs), f);
         }
-        __syncthreads();
-        const int cnt = near_n;
-        const double qd = pd.p[P], qxd = pd.Px[P], qyd = pd.Py[P], qzd = pd.Pz[P], kqd = pd.Kp[P];
-        for (int j = threadIdx.x; j < cnt; j += NT) {
-            const int64_t J = I0 + near_i[j];
-            double x, sm;
-            eri_xs(pd.p[J], pd.Px[J], pd.Py[J], pd.Pz[J], qd, qxd, qyd, qzd, x, sm);
-            ecol[J] = to_f2(eri_is_far(x, sm) ? eri_far(pd.Kp[J] * kqd, x)
-                                              : eri_near(pd.Kp[J] * kqd, x, sm));
-        }
-        __syncthreads();   // near_n is reset by the next pass
+        ecol[I] = e;
     }
 }
 
