@@ -41,7 +41,7 @@ constexpr int kHostCheckEvery = 32;
 #define CDS_KSPEC 4
 #endif
 #ifndef CDS_KSPEC_ROWS
-#define CDS_KSPEC_ROWS 8
+#define CDS_KSPEC_ROWS 4
 #endif
 constexpr int kSpec = CDS_KSPEC;          // candidate pivots per speculative projection pass
 constexpr int kSpecRows = CDS_KSPEC_ROWS; // rows of L in flight per thread and iteration
