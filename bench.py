@@ -713,7 +713,7 @@ def run_batched(args, device):
     ev[0].record()
     M = b.cd_decompose(xyz, al, at, 1e-5)
     ev[1].record()
-    b.cd_to_mo(Cc, orb, precision="f32x2")
+    b.cd_to_mo(Cc, orb, precision=args.transform if args.precision != "fp64" else "fp64")
     ev[2].record()
     torch.cuda.synchronize()
     tuned = autotune.tune(b, orb, eps, E)
@@ -736,6 +736,7 @@ def run_batched(args, device):
     return {"clusters": len(mols), "nbf_range": [int(min(x[0] for x in spec)), int(max(x[0] for x in spec))],
             "solves": n_solves, "energies": int(sum(x[2] * x[3] for x in spec)),
             "cd_ms": ev[0].elapsed_time(ev[1]), "transform_ms": ev[1].elapsed_time(ev[2]),
+            "transform_precision": args.transform if args.precision != "fp64" else "fp64",
             "graph_ms": ms, "solves_per_s": n_solves / (ms / 1e3),
             "latency_ms_p50": float(np.percentile(lat_ms, 50)),
             "latency_ms_p99": float(np.percentile(lat_ms, 99)),

@@ -171,3 +171,24 @@ def test_autotuner_candidates_agree_and_cache(batch, tmp_path, monkeypatch):
     again = autotune.tune(b, inp["orb"], inp["eps"], inp["E"])
     assert again["cached"] is True and tuple(again["choice"]) == tuple(first["choice"])
     autotune.apply((16, 0))
+
+
+def test_batch_exact_slice_transform(batch):
+    """The batched transform with the exact-slice tensor-core form (ozaki):
+    every molecule's Lov / Lp within 5e-5 of its largest entry of the
+    float-pair transform (42-bit slices against the cancellation of
+    C = S^-1/2 Q); the float-pair results are restored afterwards."""
+    mols, b, M, inp = batch
+    ref = [(b.view("ov", c, (m.nocc, m.nbf - m.nocc, M[c])).clone(),
+            b.view("p", c, (len(m.orbitals), m.nbf, M[c])).clone()) for c, m in enumerate(mols)]
+    try:
+        b.cd_to_mo(inp["C"], inp["orb"], precision="ozaki")
+        torch.cuda.synchronize()
+        for c, m in enumerate(mols):
+            ov = b.view("ov", c, (m.nocc, m.nbf - m.nocc, M[c]))
+            p = b.view("p", c, (len(m.orbitals), m.nbf, M[c]))
+            assert (ov - ref[c][0]).abs().max().item() <= 5e-5 * ref[c][0].abs().max().item()
+            assert (p - ref[c][1]).abs().max().item() <= 5e-5 * ref[c][1].abs().max().item()
+    finally:
+        b.cd_to_mo(inp["C"], inp["orb"], precision="f32x2")
+        torch.cuda.synchronize()
