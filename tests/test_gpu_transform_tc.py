@@ -118,3 +118,20 @@ def test_ill_conditioned_coefficients():
     e_oz, e_ozp = rel_err(oz_ov, ref), rel_err(oz_p, ref_p)
     print(f"ring: f32x2 {e_f2:.2e} tf32x3 {e_tc:.2e} ozaki {e_oz:.2e} / {e_ozp:.2e}")
     assert e_f2 <= 1e-7 and e_tc > 1e-3 and e_oz <= 2e-5 and e_ozp <= 2e-5
+
+
+def test_exact_slice_rejects_bases_beyond_its_exactness_bound():
+    """The leading slice pairs sum exactly in FP32 only for contraction
+    lengths K <= 1040 (K 127^2 < 2^24): a larger basis is refused with
+    CDS_ERR_UNSUPPORTED instead of losing the exactness silently; rank 0 is a
+    no-op."""
+    N = 1100
+    L = torch.zeros((1, N * (N + 1) // 2), dtype=torch.float64, device=DEV)
+    C = torch.eye(N, dtype=torch.float64, device=DEV)
+    orbs = torch.tensor([0, 1], dtype=torch.int32, device=DEV)
+    with pytest.raises(G.CdsError):
+        G.cds_cd_to_mo(L, C, 10, orbs, precision="ozaki")
+    m = O.molecule("c0")
+    a, b = G.cds_cd_to_mo(torch.zeros((0, G.npair(m.nbf)), dtype=torch.float64, device=DEV),
+                          dev(m.C), m.nocc, dev(m.orbitals), precision="ozaki")
+    assert a.numel() == 0 and b.numel() == 0
