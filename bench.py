@@ -711,7 +711,7 @@ def run_batched(args, device):
     E = cat([W.energy_grid(mm.eps[mm.orbitals], mm.nE).ravel() for mm in mols])
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     ev[0].record()
-    M = b.cd_decompose(xyz, al, at, 1e-5)
+    M = b.cd_decompose(xyz, al, at, 1e-5, precision="f32x2" if args.precision != "fp64" else "fp64")
     ev[1].record()
     b.cd_to_mo(Cc, orb, precision=args.transform if args.precision != "fp64" else "fp64")
     ev[2].record()
@@ -736,6 +736,7 @@ def run_batched(args, device):
     return {"clusters": len(mols), "nbf_range": [int(min(x[0] for x in spec)), int(max(x[0] for x in spec))],
             "solves": n_solves, "energies": int(sum(x[2] * x[3] for x in spec)),
             "cd_ms": ev[0].elapsed_time(ev[1]), "transform_ms": ev[1].elapsed_time(ev[2]),
+            "cd_precision": "f32x2" if args.precision != "fp64" else "fp64",
             "transform_precision": args.transform if args.precision != "fp64" else "fp64",
             "graph_ms": ms, "solves_per_s": n_solves / (ms / 1e3),
             "latency_ms_p50": float(np.percentile(lat_ms, 50)),

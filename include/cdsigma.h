@@ -446,11 +446,15 @@ size_t cds_batch_workspace_bytes(int32_t nmol, const cds_mol* mols, int32_t prec
 
 /* Blocking.  Per molecule as cds_cd_decompose (delta and scheme shared);
  * M_out: host [nmol].  One update and one pivot-select launch per step for
- * the whole batch.  Returns the first non-OK molecule status. */
+ * the whole batch.  precision: CDS_PREC_FP64, or CDS_PREC_F32X2 (float-pair
+ * projections and vectors, FP64 integral column, residuals and pivot
+ * decisions; L converted to FP64 at the end).  Returns the first non-OK
+ * molecule status. */
 int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const double* xyz,
                            const double* alpha, const int32_t* atom, double delta,
-                           int32_t scheme, double* L, int32_t* piv, double* D, int32_t* M_out,
-                           void* workspace, size_t workspace_bytes, cudaStream_t stream);
+                           int32_t scheme, int32_t precision, double* L, int32_t* piv, double* D,
+                           int32_t* M_out, void* workspace, size_t workspace_bytes,
+                           cudaStream_t stream);
 
 /* Asynchronous.  M: host [nmol] ranks.  Per molecule as cds_cd_to_mo. */
 int cds_batch_cd_to_mo(int32_t nmol, const cds_mol* mols, const int32_t* M, const double* L,

@@ -91,7 +91,7 @@ _mp = ctypes.POINTER(CdsMol)
 _SIGNATURES.update({
     "cds_batch_offsets": (ctypes.c_int, [_i32, _mp, ctypes.POINTER(ctypes.c_int64)]),
     "cds_batch_workspace_bytes": (_sz, [_i32, _mp, _i32]),
-    "cds_batch_cd_decompose": (ctypes.c_int, [_i32, _mp, _vp, _vp, _vp, _f64, _i32, _vp, _vp, _vp,
+    "cds_batch_cd_decompose": (ctypes.c_int, [_i32, _mp, _vp, _vp, _vp, _f64, _i32, _i32, _vp, _vp, _vp,
                                               ctypes.POINTER(_i32), _vp, _sz, _vp]),
     "cds_batch_cd_to_mo": (ctypes.c_int, [_i32, _mp, ctypes.POINTER(_i32), _vp, _vp, _vp, _i32, _vp,
                                           _vp, _vp, _sz, _vp]),
@@ -617,9 +617,10 @@ class Batch:
     def _s(self):
         return _stream(self.dev)
 
-    def cd_decompose(self, xyz, alpha, atom, delta, scheme="full"):
+    def cd_decompose(self, xyz, alpha, atom, delta, scheme="full", precision="fp64"):
         st = self.lib.cds_batch_cd_decompose(self.n, self.mols, _p(xyz), _p(alpha), _p(atom),
-                                             float(delta), SCHEMES[scheme], _p(self.L), _p(self.piv),
+                                             float(delta), SCHEMES[scheme], PRECISIONS[precision],
+                                             _p(self.L), _p(self.piv),
                                              _p(self.D), self.M, _p(self.ws), self.ws.numel(),
                                              self._s())
         _check(st, "cds_batch_cd_decompose")

@@ -23,8 +23,8 @@ namespace cds {
 size_t cd_batch_workspace_bytes(int32_t nmol, const BatchMol* mols);
 int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* off,
                        const double* xyz, const double* alpha, const int32_t* atom, double delta,
-                       int32_t scheme, double* L, int32_t* piv, double* D, int32_t* M_out,
-                       void* ws, size_t ws_bytes, cudaStream_t stream);
+                       int32_t scheme, int32_t precision, double* L, int32_t* piv, double* D,
+                       int32_t* M_out, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 namespace {
 
@@ -284,9 +284,9 @@ static void* qp_part(void* ws, int32_t nmol, const cds_mol* mols) {
 
 extern "C" int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const double* xyz,
                                       const double* alpha, const int32_t* atom, double delta,
-                                      int32_t scheme, double* L, int32_t* piv, double* D,
-                                      int32_t* M_out, void* workspace, size_t workspace_bytes,
-                                      cudaStream_t stream) {
+                                      int32_t scheme, int32_t precision, double* L, int32_t* piv,
+                                      double* D, int32_t* M_out, void* workspace,
+                                      size_t workspace_bytes, cudaStream_t stream) {
     if (!mols_ok(nmol, mols) || !xyz || !alpha || !atom || !L || !piv || !D || !M_out)
         return CDS_ERR_ARG;
     if (!(delta >= 0.0) || (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC))
@@ -294,8 +294,9 @@ extern "C" int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const d
     if (workspace_bytes < cds_batch_workspace_bytes(nmol, mols, 0)) return CDS_ERR_WORKSPACE;
     std::vector<BatchMol> bm = to_internal(nmol, mols);
     std::vector<BatchOffsets> off = offsets_of(nmol, mols, nullptr);
-    return cd_batch_decompose(nmol, bm.data(), off.data(), xyz, alpha, atom, delta, scheme, L, piv,
-                              D, M_out, workspace, cd_batch_workspace_bytes(nmol, bm.data()), stream);
+    return cd_batch_decompose(nmol, bm.data(), off.data(), xyz, alpha, atom, delta, scheme,
+                              precision, L, piv, D, M_out, workspace,
+                              cd_batch_workspace_bytes(nmol, bm.data()), stream);
 }
 
 extern "C" int cds_batch_cd_to_mo(int32_t nmol, const cds_mol* mols, const int32_t* M,

@@ -1015,6 +1015,9 @@ __global__ void k_bcd_select(const CdMol* __restrict__ mols, int nmol, int32_t k
                    blockIdx.x - m.b0_sel, m.nb_sel);
 }
 
+// DF: float-pair projections and vectors (the column stays FP64), as the
+// non-speculative float-pair form of the single-molecule decomposition.
+template <bool DF>
 __global__ void __launch_bounds__(kUpdThreads, 3) k_bcd_project(const CdMol* __restrict__ mols,
                                                                 int nmol, int32_t k) {
     const int c = find_mol(mols, nmol, blockIdx.x, 1);
@@ -1022,15 +1025,16 @@ __global__ void __launch_bounds__(kUpdThreads, 3) k_bcd_project(const CdMol* __r
     if (k >= m.max_rank || m.ctrl->done) return;
     const int local = blockIdx.x - m.b0_prj;
     if (local < m.nb_eri) cd_eri_body(m.pd, m.n, m.ctrl, m.ecol, local, m.nb_eri);
-    else if (k > 0) cd_dot_body<false>(m.n, k, m.L, m.ctrl, local - m.nb_eri);
+    else if (k > 0) cd_dot_body<DF>(m.n, k, m.L, m.ctrl, local - m.nb_eri);
 }
 
+template <bool DF>
 __global__ void __launch_bounds__(kUpdThreads) k_bcd_update(const CdMol* __restrict__ mols,
                                                             int nmol, int32_t k) {
     const int c = find_mol(mols, nmol, blockIdx.x, 3);
     const CdMol& m = mols[c];
     if (k >= m.max_rank || m.ctrl->done) return;
-    cd_step_body<false, false>(m.n, k, m.max_rank, m.L, m.D, m.cand, m.ecol, nullptr,
+    cd_step_body<DF, false>(m.n, k, m.max_rank, m.L, m.D, m.cand, m.ecol, nullptr,
                                reinterpret_cast<long long*>(m.blk_a),
                                reinterpret_cast<long long*>(m.blk_b), m.blk_i, m.piv, m.ctrl,
                                blockIdx.x - m.b0_epi, m.nb_epi);
@@ -1067,8 +1071,10 @@ size_t cd_batch_workspace_bytes(int32_t nmol, const BatchMol* mols) {
 // Blocking: M[c] receives molecule c's rank; returns the first non-OK status.
 int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* off,
                        const double* xyz, const double* alpha, const int32_t* atom, double delta,
-                       int32_t scheme, double* L, int32_t* piv, double* D, int32_t* M_out,
-                       void* ws, size_t ws_bytes, cudaStream_t stream) {
+                       int32_t scheme, int32_t precision, double* L, int32_t* piv, double* D,
+                       int32_t* M_out, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return CDS_ERR_UNSUPPORTED;
+    const bool df = precision == CDS_PREC_F32X2;
     CdBatchLayout lay = cd_batch_layout(ws, nmol, mols);
     if (!ws || ws_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
     std::vector<CdMol> h(nmol);
@@ -1118,8 +1124,13 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
     for (int32_t k0 = 0; k0 <= kmax; k0 += kHostCheckEvery) {
         int32_t k1 = std::min(kmax, k0 + kHostCheckEvery);
         for (int32_t k = k0; k < k1; ++k) {
-            k_bcd_project<<<b_prj, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
-            k_bcd_update<<<b_epi, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
+            if (df) {
+                k_bcd_project<true><<<b_prj, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
+                k_bcd_update<true><<<b_epi, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
+            } else {
+                k_bcd_project<false><<<b_prj, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
+                k_bcd_update<false><<<b_epi, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
+            }
         }
         count_launches(2ull * (unsigned long long)(k1 - k0));
         CDS_CUDA_TRY(cudaGetLastError());
@@ -1135,6 +1146,11 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
         M_out[c] = hc[c].M;
         int st = hc[c].done ? hc[c].status : CDS_ERR_RANK_CAP;
         if (st && !status) status = st;
+        if (df && hc[c].M > 0) {   // the float-pair vectors back to FP64, in place
+            const int64_t cnt = (int64_t)hc[c].M * npair_of(mols[c].nbf);
+            k_pairs_to_fp64<<<(unsigned)((cnt + 255) / 256), 256, 0, stream>>>(L + off[c].L, cnt);
+            CDS_LAUNCH_CHECK();
+        }
     }
     return status;
 }

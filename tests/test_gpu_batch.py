@@ -192,3 +192,21 @@ def test_batch_exact_slice_transform(batch):
     finally:
         b.cd_to_mo(inp["C"], inp["orb"], precision="f32x2")
         torch.cuda.synchronize()
+
+
+def test_batch_float_pair_decomposition(batch):
+    """The batched decomposition in float pairs (float-pair projections and
+    vectors; FP64 column, residuals and pivot decisions) against the FP64
+    batch: every molecule's pivots identical, vectors within 1e-8 (the
+    single-molecule float-pair bar)."""
+    mols, b, M, inp = batch
+    spec = [(m.nbf, m.nocc, len(m.orbitals), m.nE, C.default_max_rank(m.nbf)) for m in mols]
+    bf = C.Batch(spec, DEV, "bf16x3")
+    Mf = bf.cd_decompose(inp["xyz"], inp["al"], inp["at"], mols[0].delta, precision="f32x2")
+    torch.cuda.synchronize()
+    assert Mf == M
+    for c, m in enumerate(mols):
+        npr = G.npair(m.nbf)
+        assert torch.equal(bf.view("piv", c, (M[c],)), b.view("piv", c, (M[c],)))
+        torch.testing.assert_close(bf.view("L", c, (M[c], npr)), b.view("L", c, (M[c], npr)),
+                                   rtol=0, atol=1e-8)
