@@ -1,6 +1,6 @@
 """Split-precision (BF16X3 / FP16X3, tcgen05) self-energy and Newton solve vs the FP64 oracle.
 
-Bar (the benchmark spec): quasiparticle energies within 0.1 meV = 3.67e-6 Ha of the
+Bar: quasiparticle energies within 0.1 meV = 3.67e-6 Ha of the
 FP64 oracle.  Sigma on the energy grid: |dSigma| <= 3.67e-6 Ha + 1e-5 |Sigma|
 (the relative part covers grid points next to a pole, where the same
 numerator error is amplified by the denominator).  Sizes: o = 6/40,
