@@ -970,6 +970,8 @@ namespace cds {
 
 struct CdMol {
     PairSoA pd;
+    PairF2 pf;        // float-pair mode: pair data as float pairs
+    float2* G;        // float-pair mode: [kSpec][n] candidate projections
     const int32_t* atom;
     double* L;
     double* D;
@@ -1015,9 +1017,6 @@ __global__ void k_bcd_select(const CdMol* __restrict__ mols, int nmol, int32_t k
                    blockIdx.x - m.b0_sel, m.nb_sel);
 }
 
-// DF: float-pair projections and vectors (the column stays FP64), as the
-// non-speculative float-pair form of the single-molecule decomposition.
-template <bool DF>
 __global__ void __launch_bounds__(kUpdThreads, 3) k_bcd_project(const CdMol* __restrict__ mols,
                                                                 int nmol, int32_t k) {
     const int c = find_mol(mols, nmol, blockIdx.x, 1);
@@ -1025,16 +1024,31 @@ __global__ void __launch_bounds__(kUpdThreads, 3) k_bcd_project(const CdMol* __r
     if (k >= m.max_rank || m.ctrl->done) return;
     const int local = blockIdx.x - m.b0_prj;
     if (local < m.nb_eri) cd_eri_body(m.pd, m.n, m.ctrl, m.ecol, local, m.nb_eri);
-    else if (k > 0) cd_dot_body<DF>(m.n, k, m.L, m.ctrl, local - m.nb_eri);
+    else if (k > 0) cd_dot_body<false>(m.n, k, m.L, m.ctrl, local - m.nb_eri);
 }
 
-template <bool DF>
+// Float-pair form, as the single-molecule k_cd_project_spec: each molecule's
+// integral column in float pairs, then, when its step starts a batch of
+// speculative candidates, the 4-candidate projection tiles.
+__global__ void __launch_bounds__(kUpdThreads, 3) k_bcd_project_spec(const CdMol* __restrict__ mols,
+                                                                     int nmol, int32_t k) {
+    const int c = find_mol(mols, nmol, blockIdx.x, 1);
+    const CdMol& m = mols[c];
+    if (k >= m.max_rank || m.ctrl->done) return;
+    const int local = blockIdx.x - m.b0_prj;
+    if (local < m.nb_eri)
+        cd_eri_body_df(m.pd, m.pf, m.n, m.ctrl, reinterpret_cast<float2*>(m.ecol), local, m.nb_eri);
+    else if (m.ctrl->pass)
+        cd_spec_dot_body(m.n, k, m.L, m.G, m.ctrl, local - m.nb_eri);
+}
+
+template <bool SPEC>
 __global__ void __launch_bounds__(kUpdThreads) k_bcd_update(const CdMol* __restrict__ mols,
                                                             int nmol, int32_t k) {
     const int c = find_mol(mols, nmol, blockIdx.x, 3);
     const CdMol& m = mols[c];
     if (k >= m.max_rank || m.ctrl->done) return;
-    cd_step_body<DF, false>(m.n, k, m.max_rank, m.L, m.D, m.cand, m.ecol, nullptr,
+    cd_step_body<SPEC, SPEC>(m.n, k, m.max_rank, m.L, m.D, m.cand, m.ecol, SPEC ? m.G : nullptr,
                                reinterpret_cast<long long*>(m.blk_a),
                                reinterpret_cast<long long*>(m.blk_b), m.blk_i, m.piv, m.ctrl,
                                blockIdx.x - m.b0_epi, m.nb_epi);
@@ -1049,7 +1063,8 @@ struct CdBatchLayout {
 
 static size_t cd_mol_bytes(int64_t n) {
     const size_t nb = (size_t)part_blocks(n);
-    return 6 * align_up(n * sizeof(double)) + align_up(n) + 3 * align_up(nb * sizeof(double));
+    return 6 * align_up(n * sizeof(double)) + align_up(n) + 3 * align_up(nb * sizeof(double)) +
+           5 * align_up(n * sizeof(float2)) + align_up((size_t)kSpec * n * sizeof(float2));
 }
 
 static CdBatchLayout cd_batch_layout(void* ws, int32_t nmol, const BatchMol* mols) {
@@ -1096,6 +1111,9 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
         m.blk_a = cv.take<double>(nb);
         m.blk_b = cv.take<double>(nb);
         m.blk_i = cv.take<long long>(nb);
+        m.pf = PairF2{cv.take<float2>(n), cv.take<float2>(n), cv.take<float2>(n),
+                      cv.take<float2>(n), cv.take<float2>(n)};
+        m.G = cv.take<float2>((size_t)kSpec * n);
         p += cd_mol_bytes(n);
         m.atom = atom + off[c].basis;
         m.L = L + off[c].L;
@@ -1112,6 +1130,10 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
         kmax = std::max(kmax, mols[c].max_rank);
         int st = build_pairs(mols[c].nbf, xyz + 3 * off[c].basis, alpha + off[c].basis, m.pd, stream);
         if (st) return st;
+        if (df) {
+            k_pairs_to_f2<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(m.pd, m.pf, n);
+            CDS_LAUNCH_CHECK();
+        }
     }
     CDS_CUDA_TRY(cudaMemcpyAsync(lay.mols, h.data(), sizeof(CdMol) * nmol, cudaMemcpyHostToDevice,
                                  stream));
@@ -1125,10 +1147,10 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
         int32_t k1 = std::min(kmax, k0 + kHostCheckEvery);
         for (int32_t k = k0; k < k1; ++k) {
             if (df) {
-                k_bcd_project<true><<<b_prj, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
+                k_bcd_project_spec<<<b_prj, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
                 k_bcd_update<true><<<b_epi, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
             } else {
-                k_bcd_project<false><<<b_prj, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
+                k_bcd_project<<<b_prj, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
                 k_bcd_update<false><<<b_epi, kUpdThreads, 0, stream>>>(lay.mols, nmol, k);
             }
         }
