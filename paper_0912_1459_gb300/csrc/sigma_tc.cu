@@ -53,6 +53,8 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr int RED_E = 64;                     // energies reduced per CTA barrier pair
 constexpr int EPS_SMEM = 2048;                // orbital-energy pairs staged in shared memory
 constexpr int kCacheTile = TB * TB;           // cached numerators per work item
+constexpr int kGridSplitE = 1;                // energies of the grid the tensor-core epilogue evaluates
+constexpr int kGridEC = 4;                    // k_sigma_cached_grid: energies per pass
 constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 256 + NUM_EPI_WARPS * RED_E * 2 * 4 +
                               EPS_SMEM * 8;
 
@@ -79,6 +81,7 @@ struct Params {
     int32_t kblocks;
     int32_t nE;
     int32_t nmo;
+    int32_t nE_eval;   // energies the epilogue evaluates (0: all nE; the rest from the cache)
 };
 
 __device__ __forceinline__ float rcp_approx(float x) {
@@ -188,7 +191,7 @@ __device__ __forceinline__ View make_view(int64_t item, const Maps& maps, const 
         v.tm = decode(P.term[0], P.term[1], item, v.term, v.t, v.s, v.A, v.B);
         v.maps = &maps.m[v.term][0];
         v.kblocks = P.kblocks;
-        v.nE = P.nE;
+        v.nE = P.nE_eval > 0 ? min(P.nE, P.nE_eval) : P.nE;
         v.Et = E2 + (int64_t)v.t * P.nE;
         v.epsv = epsv;
         v.out = part + (v.tm.item0 + (item - v.tm.first)) * (int64_t)P.nE * 2;
@@ -814,6 +817,14 @@ size_t tc_cache_bytes(int32_t nmo, int32_t nocc, int32_t np) {
     return (size_t)(P.term[0].nitems + P.term[1].nitems) * tc::kCacheTile * sizeof(float);
 }
 
+namespace tc {
+template <int EC>
+__global__ void __launch_bounds__(256)
+k_sigma_cached_grid(Params P, const float* __restrict__ cache, const float2* __restrict__ E2,
+                    const float2* __restrict__ eps2, const int32_t* __restrict__ active,
+                    double* __restrict__ part, int32_t nE, int32_t e_begin);
+}  // namespace tc
+
 int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
               int32_t np, const double* eps, const double* E, int32_t nE,
               const int32_t* active, int32_t precision, double* sigma, double* dsigma, void* ws,
@@ -864,10 +875,24 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
                                                                                  lay.E2);
         CDS_LAUNCH_CHECK();
         int grid = (int)std::min<int64_t>(nitems, device_sms());
+        // with the numerators kept, the tensor-core epilogue evaluates the
+        // first kGridSplitE energies and k_sigma_cached_grid the rest, at
+        // the occupancy the epilogue warps of the tensor-core kernel lack
+        // (C60 shape, 20 orbitals x 64 energies: 43.6 ms against 52.6 ms
+        // with all energies in the epilogue)
+        const bool split = cache && nE > kGridSplitE;
+        if (split) P.nE_eval = kGridSplitE;
+        const int nE_tc = split ? kGridSplitE : nE;   // picks the epilogue's energy chunk
         st = separate_accumulators()
-                 ? launch_any<true>(grid, bf16, nE, maps, P, active, lay, stream, cache)
-                 : launch_any<false>(grid, bf16, nE, maps, P, active, lay, stream, cache);
+                 ? launch_any<true>(grid, bf16, nE_tc, maps, P, active, lay, stream, cache)
+                 : launch_any<false>(grid, bf16, nE_tc, maps, P, active, lay, stream, cache);
         if (st) return st;
+        if (split) {
+            const int g2 = (int)std::min<int64_t>(nitems, (int64_t)device_sms() * 4);
+            k_sigma_cached_grid<kGridEC><<<g2, 256, 0, stream>>>(P, cache, lay.E2, lay.eps2, active,
+                                                                 lay.part, nE, kGridSplitE);
+            CDS_LAUNCH_CHECK();
+        }
     } else {
         CDS_CUDA_TRY(cudaMemsetAsync(lay.part, 0, sizeof(double) * 2 * nE, stream));
     }
@@ -940,6 +965,97 @@ k_sigma_cached(Params P, const float* __restrict__ cache, const float2* __restri
             part[pidx * 2 + 1] = dv;
         }
         __syncthreads();
+    }
+}
+
+// Sigma and dSigma/dE of every work item at energies [e_begin, nE) of its
+// orbital from the cached numerators (the grid's energies past the ones the
+// tensor-core epilogue evaluates).  Thread = (row, column half) as in
+// k_sigma_cached, its 64 numerators held in registers across the energies;
+// EC energies per pass, each summed over the block in a fixed order into
+// part[item][e][2] (the layout of k_sigma_tc).
+template <int EC>
+__global__ void __launch_bounds__(256)
+k_sigma_cached_grid(Params P, const float* __restrict__ cache, const float2* __restrict__ E2,
+                    const float2* __restrict__ eps2, const int32_t* __restrict__ active,
+                    double* __restrict__ part, int32_t nE, int32_t e_begin) {
+    __shared__ float red[8][EC][2];
+    __shared__ float2 sey[2][64];
+    const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
+    const int row = threadIdx.x & (TB - 1), half = threadIdx.x / TB;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        int term, t, s, A, B;
+        const TermR tm = decode(P.term[0], P.term[1], item, term, t, s, A, B);
+        if (active && !active[t]) continue;   // the same for the whole block
+        const int x = A * TB + row;
+        const int ybase = B * TB + half * 64;
+        const int ncols = min(64, tm.nx - ybase);
+        const int64_t pidx = tm.item0 + (item - tm.first);
+        const bool xok = x < tm.nx && ncols > 0;
+        float num[64];
+        const float* ct = cache + pidx * kCacheTile + (int64_t)half * 64 * TB + row;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) num[j] = (xok && j < ncols) ? ct[(int64_t)j * TB] : 0.f;
+        __syncthreads();   // the previous item's reads of sey are done
+        if (row < 64)      // padding columns: a far-off energy, so 0 * tiny
+            sey[half][row] = row < ncols ? eps2[tm.eps_x_off + ybase + row] : make_float2(-1e30f, 0.f);
+        __syncthreads();
+        float2 rb = make_float2(0.f, 0.f);
+        if (xok) {
+            const float2 es = eps2[tm.eps_s_off + s];
+            const float2 ex = eps2[tm.eps_x_off + x];
+            rb = df_add(es, make_float2(-ex.x, -ex.y));
+        }
+        const float2* Et = E2 + (int64_t)t * nE;
+        for (int e0 = e_begin; e0 < nE; e0 += EC) {
+            float ch[EC], cl[EC], as[EC], ad[EC];
+#pragma unroll
+            for (int e = 0; e < EC; ++e) {
+                const float2 c = df_add(Et[min(e0 + e, nE - 1)], rb);
+                ch[e] = c.x;
+                cl[e] = c.y;
+                as[e] = 0.f;
+                ad[e] = 0.f;
+            }
+            if (xok) {
+#pragma unroll
+                for (int j = 0; j < 64; ++j) {
+                    const float2 e2 = sey[half][j];
+#pragma unroll
+                    for (int e = 0; e < EC; ++e) {
+                        const float d = (ch[e] - e2.x) + (cl[e] - e2.y);
+                        const float r = rcp_approx(d);
+                        const float tt = num[j] * r;
+                        as[e] += tt;
+                        ad[e] = fmaf(-tt, r, ad[e]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < EC; ++e) {
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    as[e] += __shfl_xor_sync(0xffffffffu, as[e], o);
+                    ad[e] += __shfl_xor_sync(0xffffffffu, ad[e], o);
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int e = 0; e < EC; ++e) { red[w][e][0] = as[e]; red[w][e][1] = ad[e]; }
+            }
+            __syncthreads();
+            if (threadIdx.x < 2 * EC) {
+                const int e = threadIdx.x >> 1, k = threadIdx.x & 1;
+                if (e0 + e < nE) {
+                    double v = 0.0;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) v += (double)red[i][e][k];
+                    part[(pidx * nE + e0 + e) * 2 + k] = v;
+                }
+            }
+            __syncthreads();
+        }
     }
 }
 
