@@ -325,7 +325,10 @@ size_t cds_sigma2_cache_bytes(int32_t nmo, int32_t nocc, int32_t np);
 
 /* As cds_sigma2_diag (precision CDS_PREC_BF16X3 or CDS_PREC_FP16X3), plus
  * cache (device, caller-owned, >= cds_sigma2_cache_bytes): the numerators of
- * the orbitals Lp[0..np).  Asynchronous. */
+ * the orbitals Lp[0..np).  The tensor-core pass evaluates each orbital's
+ * first energy while storing the numerators; the other energies are summed
+ * from the stored numerators by a second kernel, so they equal
+ * cds_sigma2_diag's up to the order of the FP32 sums.  Asynchronous. */
 int cds_sigma2_diag_cache(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
                           const double* Lp, int32_t np, const double* eps, const double* E,
                           int32_t nE, int32_t precision, double* sigma, double* dsigma,
