@@ -210,7 +210,7 @@ __device__ __forceinline__ View make_view(int64_t item, const Maps& maps, const 
         v.tm = decode(md->term[0], md->term[1], r, v.term, v.t, v.s, v.A, v.B);
         v.maps = &md->m[v.term][0];
         v.kblocks = md->kblocks;
-        v.nE = md->nE;
+        v.nE = P.nE_eval > 0 ? min(md->nE, P.nE_eval) : md->nE;
         v.Et = E2 + md->E_off + (int64_t)v.t * md->nE;
         v.epsv = epsv + md->eps_off;
         v.out = part + md->part_base + r * (int64_t)md->nE * 2;
@@ -968,94 +968,128 @@ k_sigma_cached(Params P, const float* __restrict__ cache, const float2* __restri
     }
 }
 
-// Sigma and dSigma/dE of every work item at energies [e_begin, nE) of its
-// orbital from the cached numerators (the grid's energies past the ones the
-// tensor-core epilogue evaluates).  Thread = (row, column half) as in
+// Sigma and dSigma/dE of one work item at energies [e_begin, nE) of its
+// orbital from its cached numerators ct (the grid's energies past the ones
+// the tensor-core epilogue evaluates).  Thread = (row, column half) as in
 // k_sigma_cached, its 64 numerators held in registers across the energies;
 // EC energies per pass, each summed over the block in a fixed order into
-// part[item][e][2] (the layout of k_sigma_tc).
+// out[e][2] (the partial row of the item, the layout of k_sigma_tc).
+// Et: the orbital's energies; ev: the molecule's orbital energies.
+template <int EC>
+__device__ __forceinline__ void cached_grid_item(const TermR& tm, int t, int s, int A, int B,
+                                                 const float* __restrict__ ct_item,
+                                                 const float2* __restrict__ Et,
+                                                 const float2* __restrict__ ev, int32_t nE,
+                                                 int32_t e_begin, double* __restrict__ out) {
+    __shared__ float red[8][EC][2];
+    __shared__ float2 sey[2][64];
+    (void)t;
+    const int row = threadIdx.x & (TB - 1), half = threadIdx.x / TB;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x = A * TB + row;
+    const int ybase = B * TB + half * 64;
+    const int ncols = min(64, tm.nx - ybase);
+    const bool xok = x < tm.nx && ncols > 0;
+    float num[64];
+    const float* ct = ct_item + (int64_t)half * 64 * TB + row;
+#pragma unroll
+    for (int j = 0; j < 64; ++j) num[j] = (xok && j < ncols) ? ct[(int64_t)j * TB] : 0.f;
+    __syncthreads();   // the previous item's reads of sey are done
+    if (row < 64)      // padding columns: a far-off energy, so 0 * tiny
+        sey[half][row] = row < ncols ? ev[tm.eps_x_off + ybase + row] : make_float2(-1e30f, 0.f);
+    __syncthreads();
+    float2 rb = make_float2(0.f, 0.f);
+    if (xok) {
+        const float2 es = ev[tm.eps_s_off + s];
+        const float2 ex = ev[tm.eps_x_off + x];
+        rb = df_add(es, make_float2(-ex.x, -ex.y));
+    }
+    for (int e0 = e_begin; e0 < nE; e0 += EC) {
+        float ch[EC], cl[EC], as[EC], ad[EC];
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+            const float2 c = df_add(Et[min(e0 + e, nE - 1)], rb);
+            ch[e] = c.x;
+            cl[e] = c.y;
+            as[e] = 0.f;
+            ad[e] = 0.f;
+        }
+        if (xok) {
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                const float2 e2 = sey[half][j];
+#pragma unroll
+                for (int e = 0; e < EC; ++e) {
+                    const float d = (ch[e] - e2.x) + (cl[e] - e2.y);
+                    const float r = rcp_approx(d);
+                    const float tt = num[j] * r;
+                    as[e] += tt;
+                    ad[e] = fmaf(-tt, r, ad[e]);
+                }
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < EC; ++e) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                as[e] += __shfl_xor_sync(0xffffffffu, as[e], o);
+                ad[e] += __shfl_xor_sync(0xffffffffu, ad[e], o);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int e = 0; e < EC; ++e) { red[w][e][0] = as[e]; red[w][e][1] = ad[e]; }
+        }
+        __syncthreads();
+        if (threadIdx.x < 2 * EC) {
+            const int e = threadIdx.x >> 1, k = threadIdx.x & 1;
+            if (e0 + e < nE) {
+                double v = 0.0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v += (double)red[i][e][k];
+                out[(int64_t)(e0 + e) * 2 + k] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 template <int EC>
 __global__ void __launch_bounds__(256)
 k_sigma_cached_grid(Params P, const float* __restrict__ cache, const float2* __restrict__ E2,
                     const float2* __restrict__ eps2, const int32_t* __restrict__ active,
                     double* __restrict__ part, int32_t nE, int32_t e_begin) {
-    __shared__ float red[8][EC][2];
-    __shared__ float2 sey[2][64];
     const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
-    const int row = threadIdx.x & (TB - 1), half = threadIdx.x / TB;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         int term, t, s, A, B;
         const TermR tm = decode(P.term[0], P.term[1], item, term, t, s, A, B);
         if (active && !active[t]) continue;   // the same for the whole block
-        const int x = A * TB + row;
-        const int ybase = B * TB + half * 64;
-        const int ncols = min(64, tm.nx - ybase);
         const int64_t pidx = tm.item0 + (item - tm.first);
-        const bool xok = x < tm.nx && ncols > 0;
-        float num[64];
-        const float* ct = cache + pidx * kCacheTile + (int64_t)half * 64 * TB + row;
-#pragma unroll
-        for (int j = 0; j < 64; ++j) num[j] = (xok && j < ncols) ? ct[(int64_t)j * TB] : 0.f;
-        __syncthreads();   // the previous item's reads of sey are done
-        if (row < 64)      // padding columns: a far-off energy, so 0 * tiny
-            sey[half][row] = row < ncols ? eps2[tm.eps_x_off + ybase + row] : make_float2(-1e30f, 0.f);
-        __syncthreads();
-        float2 rb = make_float2(0.f, 0.f);
-        if (xok) {
-            const float2 es = eps2[tm.eps_s_off + s];
-            const float2 ex = eps2[tm.eps_x_off + x];
-            rb = df_add(es, make_float2(-ex.x, -ex.y));
+        cached_grid_item<EC>(tm, t, s, A, B, cache + pidx * kCacheTile, E2 + (int64_t)t * nE, eps2,
+                             nE, e_begin, part + pidx * (int64_t)nE * 2);
+    }
+}
+
+// The same over a batch of molecules (the grid pass of tc_batch_pass).
+template <int EC>
+__global__ void __launch_bounds__(256)
+k_sigma_cached_grid_batch(const MolDesc* __restrict__ mols, int32_t nmol, int64_t nitems,
+                          const float* __restrict__ cache, const float2* __restrict__ E2,
+                          const float2* __restrict__ eps2, double* __restrict__ part,
+                          int32_t e_begin) {
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        int lo = 0, hi = nmol - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (mols[mid].item_begin <= item) lo = mid; else hi = mid - 1;
         }
-        const float2* Et = E2 + (int64_t)t * nE;
-        for (int e0 = e_begin; e0 < nE; e0 += EC) {
-            float ch[EC], cl[EC], as[EC], ad[EC];
-#pragma unroll
-            for (int e = 0; e < EC; ++e) {
-                const float2 c = df_add(Et[min(e0 + e, nE - 1)], rb);
-                ch[e] = c.x;
-                cl[e] = c.y;
-                as[e] = 0.f;
-                ad[e] = 0.f;
-            }
-            if (xok) {
-#pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    const float2 e2 = sey[half][j];
-#pragma unroll
-                    for (int e = 0; e < EC; ++e) {
-                        const float d = (ch[e] - e2.x) + (cl[e] - e2.y);
-                        const float r = rcp_approx(d);
-                        const float tt = num[j] * r;
-                        as[e] += tt;
-                        ad[e] = fmaf(-tt, r, ad[e]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int e = 0; e < EC; ++e) {
-#pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    as[e] += __shfl_xor_sync(0xffffffffu, as[e], o);
-                    ad[e] += __shfl_xor_sync(0xffffffffu, ad[e], o);
-                }
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int e = 0; e < EC; ++e) { red[w][e][0] = as[e]; red[w][e][1] = ad[e]; }
-            }
-            __syncthreads();
-            if (threadIdx.x < 2 * EC) {
-                const int e = threadIdx.x >> 1, k = threadIdx.x & 1;
-                if (e0 + e < nE) {
-                    double v = 0.0;
-#pragma unroll
-                    for (int i = 0; i < 8; ++i) v += (double)red[i][e][k];
-                    part[(pidx * nE + e0 + e) * 2 + k] = v;
-                }
-            }
-            __syncthreads();
-        }
+        const MolDesc* md = mols + lo;
+        const int64_t r = item - md->item_begin;
+        int term, t, s, A, B;
+        const TermR tm = decode(md->term[0], md->term[1], r, term, t, s, A, B);
+        cached_grid_item<EC>(tm, t, s, A, B, cache + item * kCacheTile,
+                             E2 + md->E_off + (int64_t)t * md->nE, eps2 + md->eps_off, md->nE,
+                             e_begin, part + md->part_base + r * (int64_t)md->nE * 2);
     }
 }
 
@@ -1599,8 +1633,12 @@ int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_t
         Params dummy{};
         const float2* epsv = lay.eps2;
         const int order = tune_item_order();
+        // grid pass keeping the numerators: the epilogue evaluates the first
+        // kGridSplitE energies, k_sigma_cached_grid_batch the rest
+        const bool split = pass == 0 && cache_mode == 1 && max_nE > kGridSplitE;
+        if (split) dummy.nE_eval = kGridSplitE;
         decltype(&k_sigma_tc<1, true, true, true>) kern;
-        if (pass == 1)
+        if (pass == 1 || (split && kGridSplitE == 1))
             kern = bf16 ? k_sigma_tc<1, true, true, true> : k_sigma_tc<1, false, true, true>;
         else if (tune_energy_chunk() == 8)
             kern = bf16 ? k_sigma_tc<8, true, true, true> : k_sigma_tc<8, false, true, true>;
@@ -1612,6 +1650,12 @@ int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_t
                                                     stamps, lay.err, order,
                                                     cache_mode == 1 ? lay.cache : nullptr);
         CDS_LAUNCH_CHECK();
+        if (split) {
+            const int g2 = (int)std::min<int64_t>(nitems, 4LL * device_sms());
+            k_sigma_cached_grid_batch<kGridEC><<<g2, 256, 0, stream>>>(set, nmol, nitems, lay.cache, Ep,
+                                                                       lay.eps2, lay.part, kGridSplitE);
+            CDS_LAUNCH_CHECK();
+        }
     }
     if (np_total > 0) {
         dim3 g((unsigned)std::max(pass == 0 ? max_nE : 1, 1), (unsigned)np_total);
