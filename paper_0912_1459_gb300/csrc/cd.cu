@@ -14,7 +14,8 @@
 // waits).  k_cd_select picks the first pivot only.
 // The float-pair form streams L only at the first step of a batch, forming
 // the projections of four candidate pivots at once (k_cd_project_spec);
-// steps whose pivot is among them reuse those (cd_spec_dot_body).
+// steps whose pivot is among them reuse those (cd_spec_dot_body).  Its
+// integral column is in float pairs as well (eri_column_df).
 // All kernels read a device control block and return at once after the
 // decomposition has stopped, so the host enqueues steps ahead and checks the
 // control block only every few steps.

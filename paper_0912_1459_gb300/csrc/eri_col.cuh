@@ -134,9 +134,10 @@ __device__ __forceinline__ void eri_column_df(PairSoA pd, PairF2 pf, int64_t n, 
 
 // Integral column (rho_I|rho_P) into ecol (blockDim.x == NT, grid-stride over
 // the pairs of the molecule, NT per pass).  Most pairs lie far from a compact
-// pivot density (T >= 36: one reciprocal square root, no error function); the
-// few that need erf are gathered in shared memory and evaluated together, so
-// the warps do not all run the erf path for one lane each.
+// pivot density (T >= 36: one reciprocal square root, the point-charge form);
+// the few nearer ones (F0 from the Taylor table) are gathered in shared memory
+// and evaluated together, so the warps do not all run that path for one lane
+// each.
 template <int NT>
 __device__ __forceinline__ void eri_column_fp64(PairSoA pd, int64_t n, int64_t P,
                                                 double* __restrict__ ecol, int bid, int nblk) {
