@@ -939,15 +939,20 @@ k_sigma_cached(Params P, const float* __restrict__ cache, const float2* __restri
             const float2 c = df_add(E2[t], df_add(es, make_float2(-ex.x, -ex.y)));
             const float* ct = cache + pidx * kCacheTile + (int64_t)half * 64 * TB + row;
             const float2* ey2 = eps2 + tm.eps_x_off + ybase;
-#pragma unroll 8
-            for (int j = 0; j < ncols; ++j) {
-                const float n = ct[(int64_t)j * TB];
-                const float2 e2 = ey2[j];
-                const float d = (c.x - e2.x) + (c.y - e2.y);
-                const float r = rcp_approx(d);
-                const float tt = n * r;
-                as += tt;
-                ad = fmaf(-tt, r, ad);
+            // all 64 numerators in flight before the sums (the same order of sums)
+            float num[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) num[j] = j < ncols ? ct[(int64_t)j * TB] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                if (j < ncols) {
+                    const float2 e2 = ey2[j];
+                    const float d = (c.x - e2.x) + (c.y - e2.y);
+                    const float r = rcp_approx(d);
+                    const float tt = num[j] * r;
+                    as += tt;
+                    ad = fmaf(-tt, r, ad);
+                }
             }
         }
 #pragma unroll
@@ -1575,15 +1580,20 @@ k_sigma_cached_batch(const MolDesc* __restrict__ mols, int32_t nmol, int64_t nit
                                     df_add(es, make_float2(-ex.x, -ex.y)));
             const float* ct = cache + item * kCacheTile + (int64_t)half * 64 * TB + row;
             const float2* ey2 = ev + tm.eps_x_off + ybase;
-#pragma unroll 8
-            for (int j = 0; j < ncols; ++j) {
-                const float n = ct[(int64_t)j * TB];
-                const float2 e2 = ey2[j];
-                const float d = (c.x - e2.x) + (c.y - e2.y);
-                const float rr = rcp_approx(d);
-                const float tt = n * rr;
-                as += tt;
-                ad = fmaf(-tt, rr, ad);
+            // all 64 numerators in flight before the sums (the same order of sums)
+            float num[64];
+#pragma unroll
+            for (int j = 0; j < 64; ++j) num[j] = j < ncols ? ct[(int64_t)j * TB] : 0.f;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+                if (j < ncols) {
+                    const float2 e2 = ey2[j];
+                    const float d = (c.x - e2.x) + (c.y - e2.y);
+                    const float rr = rcp_approx(d);
+                    const float tt = num[j] * rr;
+                    as += tt;
+                    ad = fmaf(-tt, rr, ad);
+                }
             }
         }
 #pragma unroll
