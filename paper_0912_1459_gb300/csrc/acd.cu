@@ -26,6 +26,8 @@ struct AcdLayout {
     double* L;       // [npa][npa]
     int32_t* piv;    // [npa]
     double* D;       // [npa]
+    void* cd;        // the isolated atom's decomposition workspace
+    size_t cd_bytes;
     size_t bytes;
 };
 
@@ -38,6 +40,8 @@ AcdLayout acd_layout(void* ws, int32_t na) {
     l.L = c.take<double>((size_t)std::max<int64_t>(npa * npa, 1));
     l.piv = c.take<int32_t>((size_t)std::max<int64_t>(npa, 1));
     l.D = c.take<double>((size_t)std::max<int64_t>(npa, 1));
+    l.cd_bytes = cd_workspace_bytes_for(std::max(na, 1), false);
+    l.cd = c.take<unsigned char>(l.cd_bytes);
     l.bytes = c.off;
     return l;
 }
@@ -314,7 +318,7 @@ extern "C" int cds_acd_aux_pairs(int32_t nbf, const double* alpha, const int32_t
         for (int32_t i = 0; i < na; ++i) key[i] = a[fs[i]];
         auto it = picks.find(key);
         if (it == picks.end()) {
-            // the isolated atom's decomposition (allocation-free entry point)
+            // the isolated atom's decomposition, in this call's own workspace
             const int64_t npa = npair_of(na);
             std::vector<double> zeros(3 * (size_t)na, 0.0);
             CDS_CUDA_TRY(cudaMemcpyAsync(lay.xyz, zeros.data(), sizeof(double) * 3 * na,
@@ -323,9 +327,9 @@ extern "C" int cds_acd_aux_pairs(int32_t nbf, const double* alpha, const int32_t
                                          cudaMemcpyHostToDevice, stream));
             int32_t M = 0;
             double de = 0.0;
-            int st = cds_cd_decompose_static(na, lay.xyz, lay.alpha, nullptr, delta,
-                                             CDS_SCHEME_FULL, (int32_t)npa, lay.L, lay.piv, lay.D,
-                                             &M, &de, stream);
+            int st = cds_cd_decompose(na, lay.xyz, lay.alpha, nullptr, delta, CDS_SCHEME_FULL,
+                                      (int32_t)npa, CDS_PREC_FP64, lay.L, lay.piv, lay.D, &M, &de,
+                                      lay.cd, lay.cd_bytes, stream);
             if (st) return st;
             std::vector<int32_t> piv(M);
             if (M > 0)

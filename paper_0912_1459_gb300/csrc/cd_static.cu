@@ -13,8 +13,9 @@
 // (4 MiB); every GPU that loads the library holds it until the process exits.
 // Host code may not use the array's name as a device address (on the host it
 // is only a stand-in symbol), so the device address is looked up with
-// cudaGetSymbolAddress once per device, with that device current, the first
-// time the entry point runs there; that first call should therefore come
+// cudaGetSymbolAddress, with the device current, at every call made outside a
+// stream capture; a call inside a capture reuses the address of the last
+// uncaptured call on that device, so the first call on a device should come
 // before any stream capture.  All calls share the one array and it keeps the
 // previous call's contents: the decomposition re-initialises everything it
 // reads (pair data, candidate mask, control block) at the start of each call,
@@ -33,18 +34,26 @@ __device__ __align__(256) unsigned char g_cd_scratch[kStaticBytes];
 std::mutex g_lock;
 void* g_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once).
-int scratch_address(void** out) {
+// Device address of the scratch array on the current device.  Outside a
+// stream capture it is looked up at every call (the lookup allocates
+// nothing), so a context that was destroyed and re-created since the last
+// call, which reloads the module at a new address, never leaves a stale
+// address behind.  During a capture the address of the last uncaptured call
+// on this device is used; with none yet the call is refused.
+int scratch_address(cudaStream_t stream, void** out) {
     int dev = 0;
     CDS_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return CDS_ERR_UNSUPPORTED;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CDS_CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
     std::lock_guard<std::mutex> guard(g_lock);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* p = nullptr;
         CDS_CUDA_TRY(cudaGetSymbolAddress(&p, g_cd_scratch));
         if (!p) return CDS_ERR_CUDA;
         g_addr[dev] = p;
     }
+    if (!g_addr[dev]) return CDS_ERR_UNSUPPORTED;
     *out = g_addr[dev];
     return CDS_OK;
 }
@@ -61,7 +70,7 @@ extern "C" int cds_cd_decompose_static(int32_t nbf, const double* xyz, const dou
     if (need == 0) return CDS_ERR_ARG;
     if (need > kStaticBytes) return CDS_ERR_CAPACITY;
     void* ws = nullptr;
-    int st = scratch_address(&ws);
+    int st = scratch_address(stream, &ws);
     if (st) return st;
     return cds_cd_decompose(nbf, xyz, alpha, atom, delta, scheme, max_rank, CDS_PREC_FP64, L, piv,
                             D, M_out, delta_eff_out, ws, kStaticBytes, stream);

@@ -6,7 +6,8 @@ library.  Checked through the C ABI against the workspace entry point
 (cds_cd_decompose) on the same inputs, for two calls in a row (the shared
 array keeps the previous call's contents, which must not leak into the
 next result), with the tolerances of the Cholesky parity tests: identical
-pivots, vectors and residuals within 1e-11.  Collected last so a run that
+pivots, vectors and residuals within 1e-11.  The second call must leave the
+device's free memory and torch's pool unchanged.  Collected last so a run that
 stops at the first failure has already run every other test.
 """
 import numpy as np
@@ -38,12 +39,18 @@ def test_static_entry_point_matches_workspace_entry_point_twice():
         L, piv, D, de = G.cds_cd_decompose(xyz, al, at, delta, scheme, max_rank=1024)
         Lr, pr, Dr = L.cpu().numpy(), piv.cpu().numpy(), D.cpu().numpy()
         npr = G.npair(m.nbf)
-        for _ in range(2):
+        for call in range(2):
             Ls = torch.full((1024, npr), float("nan"), dtype=torch.float64, device=DEV)
             ps = torch.full((1024,), -1, dtype=torch.int32, device=DEV)
             Ds = torch.full((npr,), float("nan"), dtype=torch.float64, device=DEV)
+            torch.cuda.synchronize()
+            free0 = torch.cuda.mem_get_info(DEV)[0]
+            held0 = torch.cuda.memory_reserved(DEV)
             M, de_s = G.cdsigma.cds_cd_decompose_static(xyz, al, at, delta, scheme, Ls, ps, Ds)
             torch.cuda.synchronize()
+            if call == 1:   # after the first call (module and kernels loaded): no device memory taken
+                assert torch.cuda.mem_get_info(DEV)[0] >= free0
+                assert torch.cuda.memory_reserved(DEV) == held0
             assert M == Lr.shape[0]
             assert de_s == de
             assert np.array_equal(ps[:M].cpu().numpy(), pr)
