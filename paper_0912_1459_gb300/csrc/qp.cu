@@ -93,7 +93,7 @@ extern "C" int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* 
     if (nmo <= 0 || nocc < 0 || nocc > nmo || M < 0 || np < 0 || np > 65535 || max_iter < 1 ||
         !(conv >= 0.0))
         return CDS_ERR_ARG;
-    if (precision != CDS_PREC_FP64 && !is_split16(precision)) return CDS_ERR_UNSUPPORTED;
+    if (precision != CDS_PREC_FP64 && !is_split_tc(precision)) return CDS_ERR_UNSUPPORTED;
     if (np == 0) return CDS_OK;
     if (!Lp || !orb || !eps || !omega || !pole || !iters || !status) return CDS_ERR_ARG;
     QpLayout lay = qp_layout(workspace, nmo, nocc, M, np, precision);
@@ -132,9 +132,22 @@ static QpLayout qp_cached_layout(void* ws, int32_t nmo, int32_t nocc, int32_t np
     l.dsig = c.take<double>(np);
     l.active = c.take<int32_t>(np);
     l.nactive = c.take<int32_t>(1);
-    l.sigma_ws = c.take<char>(tc_cached_workspace_bytes(nmo, nocc, np));
+    l.sigma_ws = c.take<char>(std::max(tc_cached_workspace_bytes(nmo, nocc, np),
+                                       fp64_cached_workspace_bytes(nmo, nocc, np)));
     l.bytes = c.off;
     return l;
+}
+
+// Sigma at omega from a numerator cache of either form.
+static int sigma_from_cache(int32_t precision, int32_t nmo, int32_t nocc, int32_t np,
+                            const double* eps, const double* omega, const QpLayout& lay,
+                            const void* cache, cudaStream_t stream, bool first) {
+    if (precision == CDS_PREC_FP64)
+        return sigma2_cached_fp64(nmo, nocc, np, eps, omega, lay.active,
+                                  static_cast<const double*>(cache), lay.sig, lay.dsig,
+                                  static_cast<double*>(lay.sigma_ws), stream);
+    return sigma2_cached(nmo, nocc, np, eps, omega, lay.active, static_cast<const float*>(cache),
+                         lay.sig, lay.dsig, lay.sigma_ws, stream, first);
 }
 }  // namespace cds
 
@@ -145,7 +158,8 @@ extern "C" size_t cds_qp_cached_workspace_bytes(int32_t nmo, int32_t nocc, int32
 
 extern "C" int cds_qp_solve_cached(int32_t nmo, int32_t nocc, int32_t np, const int32_t* orb,
                                    const double* eps, double conv, int32_t max_iter,
-                                   const void* cache, size_t cache_bytes, double* omega,
+                                   const void* cache, size_t cache_bytes, int32_t precision,
+                                   double* omega,
                                    double* pole, int32_t* iters, int32_t* status,
                                    void* workspace, size_t workspace_bytes,
                                    cudaStream_t stream) {
@@ -154,7 +168,8 @@ extern "C" int cds_qp_solve_cached(int32_t nmo, int32_t nocc, int32_t np, const 
         return CDS_ERR_ARG;
     if (np == 0) return CDS_OK;
     if (!orb || !eps || !omega || !pole || !iters || !status || !cache) return CDS_ERR_ARG;
-    if (cache_bytes < tc_cache_bytes(nmo, nocc, np)) return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && !is_split_tc(precision)) return CDS_ERR_UNSUPPORTED;
+    if (cache_bytes < cds_sigma2_cache_bytes(nmo, nocc, np, precision)) return CDS_ERR_ARG;
     QpLayout lay = qp_cached_layout(workspace, nmo, nocc, np);
     if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
     const int nb = (np + 127) / 128;
@@ -163,9 +178,8 @@ extern "C" int cds_qp_solve_cached(int32_t nmo, int32_t nocc, int32_t np, const 
     CDS_LAUNCH_CHECK();
     int32_t h_active = np;
     for (int32_t it = 0; it < max_iter && h_active > 0; ++it) {
-        int st = sigma2_cached(nmo, nocc, np, eps, omega, lay.active,
-                               static_cast<const float*>(cache), lay.sig, lay.dsig, lay.sigma_ws,
-                               stream, it == 0);
+        int st = sigma_from_cache(precision, nmo, nocc, np, eps, omega, lay, cache, stream,
+                                  it == 0);
         if (st) return st;
         CDS_CUDA_TRY(cudaMemsetAsync(lay.nactive, 0, sizeof(int32_t), stream));
         k_qp_step<<<nb, 128, 0, stream>>>(eps, orb, np, lay.sig, lay.dsig, conv, omega, pole,
@@ -264,26 +278,10 @@ __global__ void k_qp_step_bracketed(const double* __restrict__ eps, const int32_
     }
 }
 
-}  // namespace
-}  // namespace cds
-
-extern "C" int cds_qp_solve_bracketed_cached(int32_t nmo, int32_t nocc, int32_t np,
-                                             const int32_t* orb, const double* eps, double conv,
-                                             int32_t max_iter, const void* cache,
-                                             size_t cache_bytes, double* omega, double* pole,
-                                             int32_t* iters, int32_t* status, double* bracket,
-                                             void* workspace, size_t workspace_bytes,
-                                             cudaStream_t stream) {
-    if (nmo <= 0 || nocc < 0 || nocc > nmo || np < 0 || np > 65535 || max_iter < 1 ||
-        !(conv >= 0.0))
-        return CDS_ERR_ARG;
-    if (np == 0) return CDS_OK;
-    if (!orb || !eps || !omega || !pole || !iters || !status || !bracket || !cache)
-        return CDS_ERR_ARG;
-    if (cache_bytes < tc_cache_bytes(nmo, nocc, np)) return CDS_ERR_ARG;
-    QpLayout lay = qp_cached_layout(workspace, nmo, nocc, np);
-    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
-    // brackets on the host from the orbital energies
+// Initial brackets of every orbital (host, from the orbital energies), copied
+// to bracket[np][2] on the device.  Blocking.
+int upload_brackets(int32_t nmo, int32_t nocc, int32_t np, const int32_t* orb, const double* eps,
+                    double* bracket, cudaStream_t stream) {
     std::vector<double> e(nmo), br(2 * (size_t)np);
     std::vector<int32_t> o(np);
     CDS_CUDA_TRY(cudaMemcpyAsync(e.data(), eps, sizeof(double) * nmo, cudaMemcpyDeviceToHost, stream));
@@ -296,15 +294,81 @@ extern "C" int cds_qp_solve_bracketed_cached(int32_t nmo, int32_t nocc, int32_t 
     }
     CDS_CUDA_TRY(cudaMemcpyAsync(bracket, br.data(), sizeof(double) * 2 * np,
                                  cudaMemcpyHostToDevice, stream));
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));   // br is a host temporary
+    return CDS_OK;
+}
+
+}  // namespace
+}  // namespace cds
+
+extern "C" int cds_qp_solve_bracketed(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                                      const double* Lp, const int32_t* orb, int32_t np,
+                                      const double* eps, double conv, int32_t max_iter,
+                                      int32_t precision, double* omega, double* pole,
+                                      int32_t* iters, int32_t* status, double* bracket,
+                                      void* workspace, size_t workspace_bytes,
+                                      cudaStream_t stream) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || M < 0 || np < 0 || np > 65535 || max_iter < 1 ||
+        !(conv >= 0.0))
+        return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && !is_split_tc(precision)) return CDS_ERR_UNSUPPORTED;
+    if (np == 0) return CDS_OK;
+    if (!Lp || !orb || !eps || !omega || !pole || !iters || !status || !bracket)
+        return CDS_ERR_ARG;
+    QpLayout lay = qp_layout(workspace, nmo, nocc, M, np, precision);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    int st = upload_brackets(nmo, nocc, np, orb, eps, bracket, stream);
+    if (st) return st;
     const int nb = (np + 127) / 128;
     k_qp_init<<<nb, 128, 0, stream>>>(eps, orb, np, nmo, omega, pole, iters, status, lay.active,
                                       lay.nactive);
     CDS_LAUNCH_CHECK();
     int32_t h_active = np;
     for (int32_t it = 0; it < max_iter && h_active > 0; ++it) {
-        int st = sigma2_cached(nmo, nocc, np, eps, omega, lay.active,
-                               static_cast<const float*>(cache), lay.sig, lay.dsig, lay.sigma_ws,
-                               stream, it == 0);
+        st = sigma2_dispatch(nmo, nocc, M, Lov, Lp, np, eps, omega, 1, precision, lay.active,
+                             lay.sig, lay.dsig, lay.sigma_ws, stream, it == 0);
+        if (st) return st;
+        CDS_CUDA_TRY(cudaMemsetAsync(lay.nactive, 0, sizeof(int32_t), stream));
+        k_qp_step_bracketed<<<nb, 128, 0, stream>>>(eps, orb, np, lay.sig, lay.dsig, conv, omega,
+                                                    pole, bracket, iters, status, lay.active,
+                                                    lay.nactive);
+        CDS_LAUNCH_CHECK();
+        CDS_CUDA_TRY(cudaMemcpyAsync(&h_active, lay.nactive, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, stream));
+        CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    return h_active > 0 ? CDS_ERR_NO_CONVERGENCE : CDS_OK;
+}
+
+extern "C" int cds_qp_solve_bracketed_cached(int32_t nmo, int32_t nocc, int32_t np,
+                                             const int32_t* orb, const double* eps, double conv,
+                                             int32_t max_iter, const void* cache,
+                                             size_t cache_bytes, int32_t precision,
+                                             double* omega, double* pole,
+                                             int32_t* iters, int32_t* status, double* bracket,
+                                             void* workspace, size_t workspace_bytes,
+                                             cudaStream_t stream) {
+    if (nmo <= 0 || nocc < 0 || nocc > nmo || np < 0 || np > 65535 || max_iter < 1 ||
+        !(conv >= 0.0))
+        return CDS_ERR_ARG;
+    if (np == 0) return CDS_OK;
+    if (!orb || !eps || !omega || !pole || !iters || !status || !bracket || !cache)
+        return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && !is_split_tc(precision)) return CDS_ERR_UNSUPPORTED;
+    if (cache_bytes < cds_sigma2_cache_bytes(nmo, nocc, np, precision)) return CDS_ERR_ARG;
+    QpLayout lay = qp_cached_layout(workspace, nmo, nocc, np);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    // brackets on the host from the orbital energies
+    int st0 = upload_brackets(nmo, nocc, np, orb, eps, bracket, stream);
+    if (st0) return st0;
+    const int nb = (np + 127) / 128;
+    k_qp_init<<<nb, 128, 0, stream>>>(eps, orb, np, nmo, omega, pole, iters, status, lay.active,
+                                      lay.nactive);
+    CDS_LAUNCH_CHECK();
+    int32_t h_active = np;
+    for (int32_t it = 0; it < max_iter && h_active > 0; ++it) {
+        int st = sigma_from_cache(precision, nmo, nocc, np, eps, omega, lay, cache, stream,
+                                  it == 0);
         if (st) return st;
         CDS_CUDA_TRY(cudaMemsetAsync(lay.nactive, 0, sizeof(int32_t), stream));
         k_qp_step_bracketed<<<nb, 128, 0, stream>>>(eps, orb, np, lay.sig, lay.dsig, conv, omega,

@@ -42,17 +42,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait on one mbarrier phase; false after TIMEOUT_NS or if another
-// role has already flagged an error.
+// Bounded wait on one mbarrier phase; false after limit_ns (TIMEOUT_NS by
+// default; the error word then holds CDS_ERR_TIMEOUT) or if another role has
+// already flagged an error.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int32_t* err,
-                                          bool stop_on_err = true) {
+                                          bool stop_on_err = true,
+                                          unsigned long long limit_ns = TIMEOUT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     unsigned long long t0 = gtimer();
     for (uint32_t it = 1;; ++it) {
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 255u) == 0) {
             if (stop_on_err && *err) return false;
-            if (gtimer() - t0 > TIMEOUT_NS) {
+            if (gtimer() - t0 > limit_ns) {
                 atomicExch((int32_t*)err, (int32_t)CDS_ERR_TIMEOUT);
                 return false;
             }
