@@ -5,13 +5,17 @@
 // roots w_t = e_q + Sigma_qq(w_t):
 //   dl/dtheta = sum_t W_t (de_qt/dtheta + dSigma_t/dtheta),
 //   W_t = g_t P_t,  P_t = 1 / (1 - dSigma_t/dw)|w_t       (Eq. ps at the root).
-// Per work item (orbital t, spectator s, block pair A <= B) the kernel
-// recomputes the two exchange-paired tiles X_xy, X_yx in FP64 (the MO
-// integrals are recomputed, never stored) and forms
+// FP64 path, one orbital t at a time: per work item (spectator s, block pair
+// A <= B) the kernel recomputes the two exchange-paired tiles X_xy, X_yx in
+// FP64 (the MO integrals are recomputed, never stored across orbitals) and
+// forms
 //   G_xy = dSigma/dX_xy = (4 X_xy - 2 X_yx) / D_xy,
-// writing G (n_orb * nx * ns * nx values per sum of Eq. SE) and the energy
-// partials n / D^2 (per orbital).  The factor gradients are then FP64 GEMMs:
-//   dLq[t][x] = sum_(s,y) G[t][x][s][y] B[s][y],   dB[s][y] = sum_(t,x) G[t][x][s][y] Lq[t][x].
+// writing the orbital's G (nx * ns * nx values per sum of Eq. SE) and the
+// energy partials n / D^2.  Once the orbital's dSigma/dw is complete, G is
+// scaled by W_t and the factor gradients are FP64 GEMMs:
+//   dLq[t][x] = sum_(s,y) G[x][s][y] B[s][y],   dB[s][y] += sum_x G[x][s][y] Lq[t][x],
+// so the workspace holds one orbital's G (o*v*o + v*o*v doubles), not all.
+// The tensor-core form (adjoint_tc.cu) serves the split precisions.
 #include "sigma.cuh"
 
 namespace cds {
@@ -29,23 +33,21 @@ constexpr int TB = 32, JK = 16;
 
 struct AdjTerm {
     SigmaTerm tm;
-    double* G;          // [np][nx][ns][nx]
+    double* G;          // [nx][ns][nx] of the orbital in work
     int32_t s_eps_off;  // offsets of the spectator / pair orbitals in eps
     int32_t x_eps_off;
 };
 
 // One work item per block: FP64 tiles, then G and the energy partials.
 __global__ void __launch_bounds__(256)
-k_adj_g(AdjTerm at, int32_t M, int32_t nmo, const double* __restrict__ omega,
+k_adj_g(AdjTerm at, int32_t t, int32_t M, int32_t nmo, const double* __restrict__ omega,
         double* __restrict__ deps_t /* [np][nmo] */, double* __restrict__ dsig_t /* [np] */) {
     __shared__ double sA1[TB][JK + 1], sB1[TB][JK + 1], sA2[TB][JK + 1], sB2[TB][JK + 1];
     __shared__ double srow[TB], scol[TB], sspec;
     const SigmaTerm& tm = at.tm;
     const int32_t nb = nblocks_of(tm.nx, TB);
     const int64_t npb = npairs_of(nb);
-    const int64_t item = blockIdx.x;
-    const int32_t t = (int32_t)(item / (tm.ns * npb));
-    const int64_t r = item - (int64_t)t * tm.ns * npb;
+    const int64_t r = blockIdx.x;   // item of orbital t: (spectator, block pair)
     const int32_t s = (int32_t)(r / npb);
     int32_t A, B;
     block_pair(r - (int64_t)s * npb, nb, A, B);
@@ -90,7 +92,7 @@ k_adj_g(AdjTerm at, int32_t M, int32_t nmo, const double* __restrict__ omega,
     const double w = omega[t];
     const double es = tm.eps_s[s];
     double spec = 0.0;
-    const int64_t gt = (int64_t)t * tm.nx * tm.ns * tm.nx;
+    const int64_t gt = 0;   // G holds orbital t only
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -139,12 +141,12 @@ __global__ void k_adj_weights(int32_t np, int32_t nmo, const int32_t* __restrict
     }
 }
 
-// G[t] *= W[t]
-__global__ void k_scale_rows(double* __restrict__ G, int64_t per, int32_t np,
-                             const double* __restrict__ W) {
+// G *= g_t / (1 - dSigma_t/dw) for one orbital t
+__global__ void k_scale_orbital(double* __restrict__ G, int64_t n, int32_t t,
+                                const double* __restrict__ g, const double* __restrict__ dsig_t) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= per * np) return;
-    G[i] *= W[i / per];
+    if (i >= n) return;
+    G[i] *= g[t] / (1.0 - dsig_t[t]);
 }
 
 // dst[a][j][J] = src[j][a][J]  (or dst += ... with add)
@@ -172,11 +174,11 @@ __global__ void k_gather_rows(const double* __restrict__ Lp, int32_t np, int32_t
 }
 
 struct AdjLayout {
-    double* G0;        // first sum  [np][o][v][o]
-    double* G1;        // second sum [np][v][o][v]
+    double* G0;        // first sum of orbital t   [o][v][o]
+    double* G1;        // second sum of orbital t  [v][o][v]
     double* Lvo;       // [v][o][M]
-    double* Aq;        // [np][max(o, v)][M] gathered orbital rows
-    double* dB;        // [max(o v, v o)][M]
+    double* Aq;        // [max(o, v)][M] gathered rows of orbital t
+    double* dB;        // [v][o][M] first-sum factor gradient, summed over orbitals
     double* deps_t;    // [np][nmo]
     double* dsig_t;    // [np]
     double* W;         // [np]
@@ -187,12 +189,12 @@ AdjLayout adj_layout(void* ws, int32_t nmo, int32_t nocc, int32_t M, int32_t np)
     const int64_t o = nocc, v = nmo - nocc;
     Carver c(ws);
     AdjLayout l;
-    l.G0 = c.take<double>((size_t)std::max<int64_t>(np * o * v * o, 1));
-    l.G1 = c.take<double>((size_t)std::max<int64_t>(np * v * o * v, 1));
+    l.G0 = c.take<double>((size_t)std::max<int64_t>(o * v * o, 1));
+    l.G1 = c.take<double>((size_t)std::max<int64_t>(v * o * v, 1));
     l.Lvo = c.take<double>((size_t)std::max<int64_t>(v * o * M, 1));
-    l.Aq = c.take<double>((size_t)std::max<int64_t>(np * std::max(o, v) * M, 1));
+    l.Aq = c.take<double>((size_t)std::max<int64_t>(std::max(o, v) * M, 1));
     l.dB = c.take<double>((size_t)std::max<int64_t>(o * v * M, 1));
-    l.deps_t = c.take<double>((size_t)std::max<int64_t>(np * nmo, 1));
+    l.deps_t = c.take<double>((size_t)std::max<int64_t>((int64_t)np * nmo, 1));
     l.dsig_t = c.take<double>((size_t)std::max(np, 1));
     l.W = c.take<double>((size_t)std::max(np, 1));
     l.bytes = c.off;
@@ -200,23 +202,49 @@ AdjLayout adj_layout(void* ws, int32_t nmo, int32_t nocc, int32_t M, int32_t np)
 }
 
 }  // namespace
+
+// d_eps = sum_t W_t (dSigma_t/de + e_qt) from the per-orbital energy partials
+// and dSigma_t/dw (shared with the tensor-core form).
+int adj_finish(int32_t np, int32_t nmo, const int32_t* orb, const double* g, const double* dsig_t,
+               const double* deps_t, double* W, double* d_eps, cudaStream_t stream) {
+    k_adj_weights<<<(nmo + 127) / 128, 128, 0, stream>>>(np, nmo, orb, g, dsig_t, deps_t, W, d_eps);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
 }  // namespace cds
 
 using namespace cds;
 
+namespace cds {
+size_t adj_tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np,
+                              int32_t precision);
+int adj_tc_gradient(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
+                    const int32_t* orb, int32_t np, const double* eps, const double* omega,
+                    const double* g, int32_t precision, double* d_eps, double* d_Lov,
+                    double* d_Lp, void* workspace, size_t workspace_bytes, cudaStream_t stream);
+}  // namespace cds
+
 extern "C" size_t cds_qp_gradient_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M,
-                                                  int32_t np) {
+                                                  int32_t np, int32_t precision) {
     if (nmo <= 0 || nocc < 0 || nocc > nmo || M < 0 || np < 0) return 0;
-    return adj_layout(nullptr, nmo, nocc, M, np).bytes;
+    if (precision == CDS_PREC_FP64) return adj_layout(nullptr, nmo, nocc, M, np).bytes;
+    if (precision == CDS_PREC_BF16X3 || precision == CDS_PREC_TF32X3)
+        return adj_tc_workspace_bytes(nmo, nocc, M, np, precision);
+    return 0;
 }
 
 extern "C" int cds_qp_gradient(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
                                const double* Lp, const int32_t* orb, int32_t np,
                                const double* eps, const double* omega, const double* g,
-                               double* d_eps, double* d_Lov, double* d_Lp, void* workspace,
-                               size_t workspace_bytes, cudaStream_t stream) {
+                               int32_t precision, double* d_eps, double* d_Lov, double* d_Lp,
+                               void* workspace, size_t workspace_bytes, cudaStream_t stream) {
     if (nmo <= 0 || nocc <= 0 || nocc >= nmo || M <= 0 || np <= 0 || np > 65535) return CDS_ERR_ARG;
     if (!Lov || !Lp || !orb || !eps || !omega || !g || !d_eps || !d_Lov || !d_Lp) return CDS_ERR_ARG;
+    if (precision == CDS_PREC_BF16X3 || precision == CDS_PREC_TF32X3)
+        return adj_tc_gradient(nmo, nocc, M, Lov, Lp, orb, np, eps, omega, g, precision, d_eps,
+                               d_Lov, d_Lp, workspace, workspace_bytes, stream);
+    if (precision != CDS_PREC_FP64) return CDS_ERR_UNSUPPORTED;
     AdjLayout lay = adj_layout(workspace, nmo, nocc, M, np);
     if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
     const int32_t o = nocc, v = nmo - nocc;
@@ -224,48 +252,51 @@ extern "C" int cds_qp_gradient(int32_t nmo, int32_t nocc, int32_t M, const doubl
     make_terms(nmo, nocc, M, Lov, Lp, eps, t0, t1);
     CDS_CUDA_TRY(cudaMemsetAsync(lay.deps_t, 0, sizeof(double) * np * nmo, stream));
     CDS_CUDA_TRY(cudaMemsetAsync(lay.dsig_t, 0, sizeof(double) * np, stream));
-    CDS_CUDA_TRY(cudaMemsetAsync(lay.G0, 0, sizeof(double) * (size_t)np * o * v * o, stream));
-    CDS_CUDA_TRY(cudaMemsetAsync(lay.G1, 0, sizeof(double) * (size_t)np * v * o * v, stream));
+    CDS_CUDA_TRY(cudaMemsetAsync(d_Lov, 0, sizeof(double) * (size_t)o * v * M, stream));
     AdjTerm a0{t0, lay.G0, nocc, 0}, a1{t1, lay.G1, 0, nocc};
-    const int64_t n0 = (int64_t)np * t0.ns * npairs_of(nblocks_of(t0.nx, TB));
-    const int64_t n1 = (int64_t)np * t1.ns * npairs_of(nblocks_of(t1.nx, TB));
-    k_adj_g<<<(unsigned)n0, 256, 0, stream>>>(a0, M, nmo, omega, lay.deps_t, lay.dsig_t);
-    CDS_LAUNCH_CHECK();
-    k_adj_g<<<(unsigned)n1, 256, 0, stream>>>(a1, M, nmo, omega, lay.deps_t, lay.dsig_t);
-    CDS_LAUNCH_CHECK();
-    k_adj_weights<<<(nmo + 127) / 128, 128, 0, stream>>>(np, nmo, orb, g, lay.dsig_t, lay.deps_t,
-                                                          lay.W, d_eps);
-    CDS_LAUNCH_CHECK();
+    const int64_t n0 = (int64_t)t0.ns * npairs_of(nblocks_of(t0.nx, TB));
+    const int64_t n1 = (int64_t)t1.ns * npairs_of(nblocks_of(t1.nx, TB));
     const int64_t per0 = (int64_t)o * v * o, per1 = (int64_t)v * o * v;
-    k_scale_rows<<<(unsigned)((per0 * np + 255) / 256), 256, 0, stream>>>(lay.G0, per0, np, lay.W);
-    CDS_LAUNCH_CHECK();
-    k_scale_rows<<<(unsigned)((per1 * np + 255) / 256), 256, 0, stream>>>(lay.G1, per1, np, lay.W);
-    CDS_LAUNCH_CHECK();
     // first sum: x = i (occupied rows of Lp), B[s=a][y=j] = Lov[j][a] -> Lvo[a][j]
     k_swap01<<<(unsigned)(((int64_t)o * v * M + 255) / 256), 256, 0, stream>>>(Lov, o, v, M, lay.Lvo, 0);
     CDS_LAUNCH_CHECK();
-    int st = launch_dgemm_strided(o, M, v * o, np, lay.G0, (int64_t)v * o, 1, per0, lay.Lvo, M, 1, 0,
-                                  d_Lp, M, 1, (int64_t)nmo * M, stream);
-    if (st) return st;
-    k_gather_rows<<<(unsigned)(((int64_t)np * o * M + 255) / 256), 256, 0, stream>>>(Lp, np, nmo, 0, o, M, lay.Aq);
+    for (int32_t t = 0; t < np; ++t) {
+        // the orbital's G (every (x, s, y) written by exactly one item) and
+        // energy partials
+        k_adj_g<<<(unsigned)n0, 256, 0, stream>>>(a0, t, M, nmo, omega, lay.deps_t, lay.dsig_t);
+        CDS_LAUNCH_CHECK();
+        k_adj_g<<<(unsigned)n1, 256, 0, stream>>>(a1, t, M, nmo, omega, lay.deps_t, lay.dsig_t);
+        CDS_LAUNCH_CHECK();
+        k_scale_orbital<<<(unsigned)((per0 + 255) / 256), 256, 0, stream>>>(lay.G0, per0, t, g,
+                                                                            lay.dsig_t);
+        CDS_LAUNCH_CHECK();
+        k_scale_orbital<<<(unsigned)((per1 + 255) / 256), 256, 0, stream>>>(lay.G1, per1, t, g,
+                                                                            lay.dsig_t);
+        CDS_LAUNCH_CHECK();
+        double* dLq = d_Lp + (int64_t)t * nmo * M;
+        // first sum: dLq[i] = sum_(a,j) G0[i][a][j] Lvo[a][j];  dB[a][j] += sum_i G0[i][a][j] Lq[i]
+        int st = launch_dgemm_strided(o, M, v * o, 1, lay.G0, (int64_t)v * o, 1, 0, lay.Lvo, M, 1,
+                                      0, dLq, M, 1, 0, stream);
+        if (st) return st;
+        k_gather_rows<<<(unsigned)(((int64_t)o * M + 255) / 256), 256, 0, stream>>>(
+            Lp + (int64_t)t * nmo * M, 1, nmo, 0, o, M, lay.Aq);
+        CDS_LAUNCH_CHECK();
+        st = launch_dgemm_strided(v * o, M, o, 1, lay.G0, 1, (int64_t)v * o, 0, lay.Aq, M, 1, 0,
+                                  lay.dB, M, 1, 0, stream, t > 0);
+        if (st) return st;
+        // second sum: x = a (virtual rows of Lp), B[s=i][y=b] = Lov[i][b]
+        st = launch_dgemm_strided(v, M, o * v, 1, lay.G1, (int64_t)o * v, 1, 0, Lov, M, 1, 0,
+                                  dLq + (int64_t)nocc * M, M, 1, 0, stream);
+        if (st) return st;
+        k_gather_rows<<<(unsigned)(((int64_t)v * M + 255) / 256), 256, 0, stream>>>(
+            Lp + (int64_t)t * nmo * M, 1, nmo, nocc, v, M, lay.Aq);
+        CDS_LAUNCH_CHECK();
+        st = launch_dgemm_strided(o * v, M, v, 1, lay.G1, 1, (int64_t)o * v, 0, lay.Aq, M, 1, 0,
+                                  d_Lov, M, 1, 0, stream, true);
+        if (st) return st;
+    }
+    // d_Lov += dB  ([a][j] -> [j][a])
+    k_swap01<<<(unsigned)(((int64_t)o * v * M + 255) / 256), 256, 0, stream>>>(lay.dB, v, o, M, d_Lov, 1);
     CDS_LAUNCH_CHECK();
-    st = launch_dgemm_strided(v * o, M, np * o, 1, lay.G0, 1, (int64_t)v * o, 0, lay.Aq, M, 1, 0,
-                              lay.dB, M, 1, 0, stream);
-    if (st) return st;
-    k_swap01<<<(unsigned)(((int64_t)o * v * M + 255) / 256), 256, 0, stream>>>(lay.dB, v, o, M, d_Lov, 0);
-    CDS_LAUNCH_CHECK();
-    // second sum: x = a (virtual rows of Lp), B[s=i][y=b] = Lov[i][b]
-    st = launch_dgemm_strided(v, M, o * v, np, lay.G1, (int64_t)o * v, 1, per1, Lov, M, 1, 0,
-                              d_Lp + (int64_t)nocc * M, M, 1, (int64_t)nmo * M, stream);
-    if (st) return st;
-    k_gather_rows<<<(unsigned)(((int64_t)np * v * M + 255) / 256), 256, 0, stream>>>(Lp, np, nmo, nocc, v, M, lay.Aq);
-    CDS_LAUNCH_CHECK();
-    st = launch_dgemm_strided(o * v, M, np * v, 1, lay.G1, 1, (int64_t)o * v, 0, lay.Aq, M, 1, 0,
-                              lay.dB, M, 1, 0, stream);
-    if (st) return st;
-    // d_Lov += dB  (same [o][v] order): swap with d0 = 1 is an elementwise add
-    k_swap01<<<(unsigned)(((int64_t)o * v * M + 255) / 256), 256, 0, stream>>>(lay.dB, 1, o * v, M, d_Lov, 1);
-    CDS_LAUNCH_CHECK();
-    // W-weighted factor gradients of the rows are already in d_Lp (G carried W)
-    return CDS_OK;
+    return adj_finish(np, nmo, orb, g, lay.dsig_t, lay.deps_t, lay.W, d_eps, stream);
 }

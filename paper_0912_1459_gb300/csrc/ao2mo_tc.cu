@@ -29,11 +29,14 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <type_traits>
 
 #include "common.cuh"
 #include "tcgen05.cuh"
 #include "ao2mo_tc.cuh"
+#include "split.cuh"
 
 namespace cds {
 namespace trc {
@@ -53,7 +56,7 @@ constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 256;
 
 template <bool TF32>
 struct Fmt {
-    using E = std::conditional_t<TF32, float, uint16_t>;   // operand container
+    using E = SplitE<TF32>;                                   // operand container
     static constexpr int KE = ROW_BYTES / (int)sizeof(E);   // elements per k-block
     // instruction descriptor (without N): D f32, A/B tf32 (format 2) or
     // bf16 (format 1), both K-major, M = 128
@@ -72,42 +75,8 @@ struct Args {
     double* out;   // FP64 output, or null for the split output
     void* out_hi;  // split output (operand containers)
     void* out_lo;
+    int32_t accumulate;   // FP64 output: add to it instead of overwriting
 };
-
-// x = hi + lo with hi rounded to TF32 (round to nearest, ties away from zero,
-// on the 13 dropped mantissa bits) and lo the FP32 remainder; the input is
-// the float pair (f, r), x = f + r.
-__device__ __forceinline__ void split_tf32(float f, float r, float& hi, float& lo) {
-    const uint32_t u = (__float_as_uint(f) + 0x1000u) & 0xFFFFE000u;
-    hi = __uint_as_float(u);
-    lo = (f - hi) + r;   // f - hi is exact (same binade or one apart)
-}
-__device__ __forceinline__ void split_bf16(float f, float r, uint16_t& hi, uint16_t& lo) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(f);
-    const __nv_bfloat16 l = __float2bfloat16_rn((f - __bfloat162float(h)) + r);
-    hi = __bfloat16_as_ushort(h);
-    lo = __bfloat16_as_ushort(l);
-}
-template <bool TF32>
-__device__ __forceinline__ void split_store(float f, float r, typename Fmt<TF32>::E* hi,
-                                            typename Fmt<TF32>::E* lo, int64_t e) {
-    if constexpr (TF32) {
-        float h, l;
-        split_tf32(f, r, h, l);
-        hi[e] = h;
-        lo[e] = l;
-    } else {
-        uint16_t h, l;
-        split_bf16(f, r, h, l);
-        hi[e] = h;
-        lo[e] = l;
-    }
-}
-// x as an FP32 pair (f, r): f = fl(x), r = fl(x - f)
-__device__ __forceinline__ void pair_of_double(double x, float& f, float& r) {
-    f = (float)x;
-    r = (float)(x - (double)f);
-}
 
 // Barrier over the 128 epilogue threads that ORs a flag across them.
 __device__ __forceinline__ bool epi_any(bool v) {
@@ -257,7 +226,8 @@ k_tr_gemm(const __grid_constant__ Maps maps, const Args g, int32_t* __restrict__
                             if (c0 + j < ncols) {
                                 const int64_t e = ob + (int64_t)(c_base + c0 + j) * g.cs;
                                 if (g.out) {
-                                    g.out[e] = (double)xh[j] + (double)xx[j];
+                                    const double v = (double)xh[j] + (double)xx[j];
+                                    g.out[e] = g.accumulate ? g.out[e] + v : v;
                                 } else {
                                     // hi.hi + cross as an exact FP32 pair (two-sum)
                                     const float s = xh[j] + xx[j];
@@ -346,6 +316,7 @@ inline int32_t ld_of(int32_t N) { return (N + 7) / 8 * 8; }   // 16-byte row str
 struct Layout {
     void *ct_hi, *ct_lo, *cj_hi, *cj_lo, *u_hi, *u_lo, *t_hi, *t_lo;
     int32_t* err;
+    unsigned long long* cnorm;   // largest column 1-norm of C (FP64 bits)
     size_t bytes;
 };
 
@@ -364,8 +335,19 @@ Layout layout(void* ws, int32_t N, int32_t nmo, int32_t nocc, int32_t np, int32_
     l.t_hi = take(nc * kb_max * ld);
     l.t_lo = take(nc * kb_max * ld);
     l.err = c.take<int32_t>(4);
+    l.cnorm = c.take<unsigned long long>(1);
     l.bytes = c.off;
     return l;
+}
+
+// out = max_q sum_mu |C[mu][q]| (non-negative doubles order as their bits).
+__global__ void k_col_norm1(const double* __restrict__ C, int32_t N, int32_t nmo,
+                            unsigned long long* __restrict__ out) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nmo) return;
+    double s = 0.0;
+    for (int mu = 0; mu < N; ++mu) s += fabs(C[(int64_t)mu * nmo + q]);
+    atomicMax(out, (unsigned long long)__double_as_longlong(s));
 }
 
 // 2-D operand {k (contiguous, extent kdim), rows} as a 3-D map with a unit
@@ -396,7 +378,7 @@ template <bool TF32>
 int run_gemm(const void* a_hi, const void* a_lo, int64_t a_rows, const void* b_hi,
              const void* b_lo, int64_t b_rows, int32_t kdim, int32_t ld, int64_t kdiv,
              int64_t rs_hi, int64_t rs_lo, int64_t cs, double* out, void* out_hi, void* out_lo,
-             int32_t* err, cudaStream_t stream) {
+             int32_t* err, cudaStream_t stream, bool accumulate = false) {
     if (a_rows <= 0 || b_rows <= 0 || kdim <= 0) return CDS_OK;
     if (a_rows > INT32_MAX - TM) return CDS_ERR_ARG;
     Args g;
@@ -413,6 +395,7 @@ int run_gemm(const void* a_hi, const void* a_lo, int64_t a_rows, const void* b_h
     g.out = out;
     g.out_hi = out_hi;
     g.out_lo = out_lo;
+    g.accumulate = accumulate ? 1 : 0;
     Maps maps;
     if (!make_operand_map(&maps.a_hi, TF32, a_hi, kdim, a_rows, ld, TM) ||
         !make_operand_map(&maps.a_lo, TF32, a_lo, kdim, a_rows, ld, TM) ||
@@ -429,11 +412,34 @@ int run_gemm(const void* a_hi, const void* a_lo, int64_t a_rows, const void* b_h
     return CDS_OK;
 }
 
+// The split products carry ~u = 2^-21 (TF32X3) or 2^-17 (BF16X3) of each
+// product, so an element of C^T A C is off by up to ~u |C_p|_1 |C_q|_1 max|A|
+// while the element itself is O(max|A|) (C^T S C = 1): ill-conditioned C
+// (large column 1-norms, strong cancellation) makes the result meaningless.
+// The call is refused when u max_q |C_q|_1^2 > 2^-8 (the exact-slice form
+// serves those bases).  Blocking.
+template <bool TF32>
+int check_conditioning(int32_t N, int32_t nmo, const double* C, const Layout& l,
+                       cudaStream_t stream) {
+    CDS_CUDA_TRY(cudaMemsetAsync(l.cnorm, 0, sizeof(unsigned long long), stream));
+    k_col_norm1<<<(nmo + 127) / 128, 128, 0, stream>>>(C, N, nmo, l.cnorm);
+    CDS_LAUNCH_CHECK();
+    unsigned long long h = 0;
+    CDS_CUDA_TRY(cudaMemcpyAsync(&h, l.cnorm, sizeof(h), cudaMemcpyDeviceToHost, stream));
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    double n1;
+    memcpy(&n1, &h, sizeof(n1));
+    const double u = TF32 ? std::ldexp(1.0, -21) : std::ldexp(1.0, -17);
+    return (u * n1 * n1 <= std::ldexp(1.0, -8)) ? CDS_OK : CDS_ERR_UNSUPPORTED;
+}
+
 template <bool TF32>
 int columns(int32_t N, int32_t nmo, int32_t nocc, const double* C, const int32_t* orb, int32_t np,
             const Layout& l, cudaStream_t stream) {
     using E = typename Fmt<TF32>::E;
     const int64_t tot = (int64_t)(nmo + nocc + np) * N;
+    const int cst = check_conditioning<TF32>(N, nmo, C, l, stream);
+    if (cst) return cst;
     CDS_CUDA_TRY(cudaMemsetAsync(l.err, 0, sizeof(int32_t), stream));
     k_split_c<TF32><<<(unsigned)((tot + 255) / 256), 256, 0, stream>>>(
         C, N, nmo, nocc, orb, np, ld_of(N), (E*)l.ct_hi, (E*)l.ct_lo, (E*)l.cj_hi, (E*)l.cj_lo);
@@ -476,6 +482,21 @@ int batch(int32_t N, int32_t nmo, int32_t nocc, int32_t np, const double* L, con
 }
 
 }  // namespace trc
+
+int tr_split_gemm(int32_t precision, const void* a_hi, const void* a_lo, int64_t a_rows,
+                  const void* b_hi, const void* b_lo, int64_t b_rows, int32_t kdim, int32_t ld,
+                  int64_t kdiv, int64_t rs_hi, int64_t rs_lo, int64_t cs, double* out,
+                  bool accumulate, int32_t* err, cudaStream_t stream) {
+    if (!tc::device_ok()) return CDS_ERR_UNSUPPORTED;
+    if (!out || kdiv <= 0 || ld < kdim) return CDS_ERR_ARG;
+    if (precision == CDS_PREC_TF32X3)
+        return trc::run_gemm<true>(a_hi, a_lo, a_rows, b_hi, b_lo, b_rows, kdim, ld, kdiv, rs_hi,
+                                   rs_lo, cs, out, nullptr, nullptr, err, stream, accumulate);
+    if (precision == CDS_PREC_BF16X3)
+        return trc::run_gemm<false>(a_hi, a_lo, a_rows, b_hi, b_lo, b_rows, kdim, ld, kdiv, rs_hi,
+                                    rs_lo, cs, out, nullptr, nullptr, err, stream, accumulate);
+    return CDS_ERR_UNSUPPORTED;
+}
 
 size_t tr_tc_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, int32_t kb_max,
                              int32_t precision) {

@@ -23,6 +23,18 @@ int tr_tc_batch(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, const double
 int tr_tc_status(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, int32_t kb_max,
                  int32_t precision, void* ws, cudaStream_t stream);
 
+// The split-precision GEMM of the transform as a building block (precision
+// CDS_PREC_TF32X3 or CDS_PREC_BF16X3): D[m][c] = sum_k A[m][k] B[c][k] with
+// both operands given as split hi/lo rows (k contiguous, row stride ld
+// elements, 16-byte aligned rows), a_rows x kdim and b_rows x kdim; FP64
+// output element (m, c) at out[(m / kdiv) rs_hi + (m % kdiv) rs_lo + c cs],
+// written or (accumulate) added.  Asynchronous; the kernel's error word is
+// err (device int32, cleared by the caller).
+int tr_split_gemm(int32_t precision, const void* a_hi, const void* a_lo, int64_t a_rows,
+                  const void* b_hi, const void* b_lo, int64_t b_rows, int32_t kdim, int32_t ld,
+                  int64_t kdiv, int64_t rs_hi, int64_t rs_lo, int64_t cs, double* out,
+                  bool accumulate, int32_t* err, cudaStream_t stream);
+
 // Exact-slice (Ozaki) form, CDS_PREC_OZAKI: nbf <= 1040.
 size_t tr_oz_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t np, int32_t kb_max);
 int tr_oz_columns(int32_t nbf, int32_t nmo, int32_t nocc, const double* C, const int32_t* orb,
