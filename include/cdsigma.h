@@ -55,12 +55,14 @@ typedef enum { CDS_SCHEME_FULL = 0, CDS_SCHEME_ATOMIC = 1 } cds_scheme;
 
 /* Arithmetic of the J-contractions in sigma2 / qp_solve.
  * FP64: binary64 throughout (CUDA cores).
- * BF16X3 / FP16X3: each factor split s*x = hi + lo with hi, lo bf16 (s = 1)
- *   or fp16 (s = a power of two with max|s x| <= 1024); the products
- *   hi*hi + hi*lo + lo*hi run on tcgen05 tensor cores with fp32 accumulation.
- *   Denominators are double-fp32 pairs, per-element sums fp32, cross-tile sums
- *   and the Newton step fp64.  FP16X3 carries ~22 significant bits per factor,
- *   BF16X3 ~17. */
+ * BF16X3 / FP16X3 / TF32X3: each factor split s*x = hi + lo with hi, lo bf16
+ *   (s = 1), fp16 (s = a power of two with max|s x| <= 1024) or tf32 (s = 1,
+ *   FP32 containers); the products hi*hi + hi*lo + lo*hi run on tcgen05
+ *   tensor cores with fp32 accumulation.  Denominators are double-fp32
+ *   pairs, per-element sums fp32, cross-tile sums and the Newton step fp64.
+ *   FP16X3 carries ~22 significant bits per factor, BF16X3 ~17, TF32X3 ~22.
+ *   TF32X3 serves the single-molecule self-energy, Newton and adjoint calls
+ *   and the transform; MP2 and the batched calls take BF16X3 / FP16X3. */
 typedef enum {
     CDS_PREC_FP64 = 0,
     CDS_PREC_BF16X3 = 2,
@@ -68,9 +70,10 @@ typedef enum {
     CDS_PREC_F32X2 = 4,  /* decomposition and transform: (hi, lo) float pairs with exact
                             product and sum errors, ~2^-44 relative per operation, on the
                             FP32 units */
-    CDS_PREC_TF32X3 = 5, /* transform: tcgen05 tensor cores, each operand split into TF32
-                            hi + lo, hi.hi + hi.lo + lo.hi with FP32 accumulation,
-                            ~2^-21 relative per product (BF16X3 there: ~2^-17) */
+    CDS_PREC_TF32X3 = 5, /* self-energy, Newton, adjoint and transform: tcgen05 tensor
+                            cores, each operand split into TF32 hi + lo, hi.hi + hi.lo +
+                            lo.hi with FP32 accumulation, ~2^-21 relative per product
+                            (BF16X3: ~2^-17) */
     CDS_PREC_OZAKI = 6   /* transform: tcgen05 tensor cores with exact slice products
                             (rows cut into six 7-bit BF16 digits below a power-of-two
                             scale, 21 slice pairs, exact FP32 sums for nbf <= 1040):
@@ -89,6 +92,16 @@ const char* cds_errstr(int status);
 /* Number of CUDA kernels this library has launched in this process (all
  * devices, all streams); monotone, thread-safe. */
 unsigned long long cds_launch_count(void);
+
+/* Check of the bounded device-side wait (no counterpart in the paper).  Every
+ * wait of the tensor-core kernels on an mbarrier gives up after a limit (2 s)
+ * and writes CDS_ERR_TIMEOUT to the call's error word instead of hanging or
+ * trapping.  This call runs that same wait on a barrier phase that nothing
+ * completes, with a limit of `seconds` (0 < seconds <= 2), so that it must
+ * give up; the kernel then returns normally.  err: device int32 error word
+ * (caller-owned).  Blocking; returns the word (CDS_ERR_TIMEOUT when the wait
+ * gave up as designed), or CDS_ERR_ARG / CDS_ERR_CUDA. */
+int cds_wait_check(double seconds, int32_t* err, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
  * Electron-repulsion integrals over s-type Gaussians (paper Sec. II.A,
@@ -169,9 +182,11 @@ int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precision, int32_t*
  * results as cds_cd_decompose, without the workspace: the scratch is a fixed
  * device array inside the library (CDS_CD_STATIC_SCRATCH_BYTES, held on every
  * GPU that loads the library until the process exits).  The call allocates
- * nothing (no cudaMalloc, no library allocator).  Its first call on a device
- * resolves the array's device address with that device current; make that
- * first call before any stream capture.  Calls share the array: two calls
+ * nothing (no cudaMalloc, no library allocator).  Every call made outside a
+ * stream capture resolves the array's device address with the device current;
+ * a call inside a capture reuses the last one resolved on that device
+ * (CDS_ERR_UNSUPPORTED if none), so make the first call on a device before
+ * any stream capture.  Calls share the array: two calls
  * whose GPU work overlaps race.  Returns CDS_ERR_CAPACITY when the basis needs
  * more scratch than the array holds (nbf > cds_cd_static_max_nbf()).
  * ---------------------------------------------------------------------- */
@@ -199,7 +214,10 @@ size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int3
  * gave up).  L: device [M][npair]; C: device [nbf][nmo]; orb: device [np]
  * int32 MO indices in [0, nmo).  precision: CDS_PREC_FP64, CDS_PREC_F32X2,
  * CDS_PREC_TF32X3, CDS_PREC_BF16X3 or CDS_PREC_OZAKI (the last three on sm_103
- * only, OZAKI for nbf <= 1040; else CDS_ERR_UNSUPPORTED).  Outputs (device, fp64): Lov [nocc][nmo-nocc][M],
+ * only, OZAKI for nbf <= 1040; else CDS_ERR_UNSUPPORTED).  TF32X3 / BF16X3
+ * accumulate in FP32 and lose ~u |C_p|_1 |C_q|_1 of each element (u = 2^-21
+ * / 2^-17): they return CDS_ERR_UNSUPPORTED when u max_q |C_q|_1^2 > 2^-8
+ * (ill-conditioned C; use CDS_PREC_OZAKI or CDS_PREC_F32X2 there).  Outputs (device, fp64): Lov [nocc][nmo-nocc][M],
  * Lp [np][nmo][M] (Lp may be NULL when np == 0). */
 int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
                  const double* C, const int32_t* orb, int32_t np, int32_t precision,
@@ -224,7 +242,9 @@ size_t cds_acd_workspace_bytes(int32_t max_atom_funcs);
  * function).  Output (host, caller-owned): aux [capacity] packed pair indices
  * of the basis densities, centres ascending, each centre's in its type's
  * pivot order; *naux their number.  CDS_ERR_CAPACITY if more than capacity
- * (*naux still set).  Atoms must fit cds_cd_static_max_nbf(). */
+ * (*naux still set).  Each isolated atom is decomposed in the caller's
+ * workspace (cds_acd_workspace_bytes of the largest atom), so calls on
+ * different workspaces may overlap. */
 int cds_acd_aux_pairs(int32_t nbf, const double* alpha, const int32_t* atom, double delta,
                       int32_t* aux, int32_t capacity, int32_t* naux, void* workspace,
                       size_t workspace_bytes, cudaStream_t stream);
@@ -312,23 +332,27 @@ int cds_qp_solve(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
  * Cached numerators ("pole-cached" Newton).  In Eq. SE every element's
  * numerator (2 X_xy - X_yx) X_xy is independent of the energy; only the
  * denominator E + e_s - e_x - e_y moves.  cds_sigma2_diag_cache runs
- * cds_sigma2_diag (split precisions) and also stores the numerators of every
- * work item, as computed by the tensor-core epilogue, in a caller buffer of
- * cds_sigma2_cache_bytes (~0.38 GB per orbital at C60 shapes);
- * cds_qp_solve_cached then runs the Newton iteration of cds_qp_solve with
- * each Sigma(w) evaluated from that buffer, streaming it once per pass
- * instead of recomputing the integrals.  Per element the arithmetic is the
- * epilogue's; only the order of the sums differs.
+ * cds_sigma2_diag and also stores the numerators of every work item, as the
+ * kernel formed them, in a caller buffer of cds_sigma2_cache_bytes (split
+ * precisions: FP32, 128 x 128 items, ~0.38 GB per orbital at C60 shapes;
+ * FP64: 32 x 32 items, ~0.45 GB per orbital); cds_qp_solve_cached then runs
+ * the Newton iteration of cds_qp_solve with each Sigma(w) evaluated from that
+ * buffer, streaming it once per pass instead of recomputing the integrals.
+ * Per element the arithmetic is the recomputing kernel's; in FP64 the order
+ * of the sums too (equal results at equal energies), in the split precisions
+ * only the order of the FP32 sums differs.
  * ---------------------------------------------------------------------- */
 
-size_t cds_sigma2_cache_bytes(int32_t nmo, int32_t nocc, int32_t np);
+size_t cds_sigma2_cache_bytes(int32_t nmo, int32_t nocc, int32_t np, int32_t precision);
 
-/* As cds_sigma2_diag (precision CDS_PREC_BF16X3 or CDS_PREC_FP16X3), plus
- * cache (device, caller-owned, >= cds_sigma2_cache_bytes): the numerators of
- * the orbitals Lp[0..np).  The tensor-core pass evaluates each orbital's
- * first energy while storing the numerators; the other energies are summed
- * from the stored numerators by a second kernel, so they equal
- * cds_sigma2_diag's up to the order of the FP32 sums.  Asynchronous. */
+/* As cds_sigma2_diag (precision CDS_PREC_FP64, CDS_PREC_BF16X3, CDS_PREC_FP16X3
+ * or CDS_PREC_TF32X3), plus cache (device, caller-owned, >=
+ * cds_sigma2_cache_bytes of the same precision): the numerators of the
+ * orbitals Lp[0..np).  Split precisions: the tensor-core pass evaluates each
+ * orbital's first energy while storing the numerators; the other energies
+ * are summed from the stored numerators by a second kernel, so they equal
+ * cds_sigma2_diag's up to the order of the FP32 sums.  FP64: one pass
+ * evaluates every energy and stores the numerators.  Asynchronous. */
 int cds_sigma2_diag_cache(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
                           const double* Lp, int32_t np, const double* eps, const double* E,
                           int32_t nE, int32_t precision, double* sigma, double* dsigma,
@@ -338,12 +362,26 @@ int cds_sigma2_diag_cache(int32_t nmo, int32_t nocc, int32_t M, const double* Lo
 size_t cds_qp_cached_workspace_bytes(int32_t nmo, int32_t nocc, int32_t np);
 
 /* As cds_qp_solve, with Sigma from a cache that cds_sigma2_diag_cache filled
- * for the same orbitals (orb[t] = the orbital of Lp[t]).  Blocking. */
+ * for the same orbitals (orb[t] = the orbital of Lp[t]) in `precision` (the
+ * cache's form).  Blocking. */
 int cds_qp_solve_cached(int32_t nmo, int32_t nocc, int32_t np, const int32_t* orb,
                         const double* eps, double conv, int32_t max_iter, const void* cache,
-                        size_t cache_bytes, double* omega, double* pole, int32_t* iters,
+                        size_t cache_bytes, int32_t precision, double* omega, double* pole,
+                        int32_t* iters,
                         int32_t* status, void* workspace, size_t workspace_bytes,
                         cudaStream_t stream);
+
+/* Safeguarded Newton recomputing Sigma from the factors (not in the paper; a
+ * variant of Eq. iter): the bracket rule of cds_qp_solve_bracketed_cached
+ * below with each Sigma(w) evaluated as in cds_qp_solve (precision
+ * CDS_PREC_FP64, CDS_PREC_BF16X3, CDS_PREC_FP16X3 or CDS_PREC_TF32X3; workspace
+ * cds_qp_workspace_bytes).  bracket (device, [np][2], caller-owned) receives
+ * the final bracket.  Blocking. */
+int cds_qp_solve_bracketed(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
+                           const double* Lp, const int32_t* orb, int32_t np, const double* eps,
+                           double conv, int32_t max_iter, int32_t precision, double* omega,
+                           double* pole, int32_t* iters, int32_t* status, double* bracket,
+                           void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /* Safeguarded Newton from cached numerators (not in the paper; a variant of
  * Eq. iter).  Every pole of Sigma_qq lies at e_i + e_j - e_a or e_a + e_b -
@@ -357,7 +395,8 @@ int cds_qp_solve_cached(int32_t nmo, int32_t nocc, int32_t np, const int32_t* or
  * otherwise as cds_qp_solve_cached. */
 int cds_qp_solve_bracketed_cached(int32_t nmo, int32_t nocc, int32_t np, const int32_t* orb,
                                   const double* eps, double conv, int32_t max_iter,
-                                  const void* cache, size_t cache_bytes, double* omega,
+                                  const void* cache, size_t cache_bytes, int32_t precision,
+                                  double* omega,
                                   double* pole, int32_t* iters, int32_t* status,
                                   double* bracket, void* workspace, size_t workspace_bytes,
                                   cudaStream_t stream);
@@ -390,20 +429,32 @@ int cds_mp2_energy(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
  *   dl/dtheta = sum_t g_t P_t (de_qt/dtheta + dSigma_t/dtheta),
  *   P_t = 1/(1 - dSigma_t/dw) at w_t (the implicit-function theorem),
  * with dSigma/dX_xy = (4 X_xy - 2 X_yx) / D_xy for the MO integrals
- * X = (qx|sy), recomputed tile by tile in FP64 (never stored).
+ * X = (qx|sy), recomputed from the factors for each orbital (never stored
+ * for all orbitals at once).
  * ---------------------------------------------------------------------- */
 
-size_t cds_qp_gradient_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np);
+size_t cds_qp_gradient_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np,
+                                       int32_t precision);
 
-/* Asynchronous, FP64.  Inputs as cds_qp_solve plus omega (device [np],
- * converged roots) and g (device [np] upstream gradients).  Outputs (device):
- * d_eps [nmo], d_Lov [nocc][nmo-nocc][M], d_Lp [np][nmo][M].  Workspace holds
- * dSigma/dX for every orbital: np*(o*v*o + v*o*v) doubles plus copies of the
- * factors.  Requires 0 < nocc < nmo. */
+/* Asynchronous (FP64) or blocking (split precisions: the tensor-core error
+ * word is read at the end, CDS_ERR_TIMEOUT if a bounded wait gave up).
+ * Inputs as cds_qp_solve plus omega (device [np], converged roots) and g
+ * (device [np] upstream gradients).  Outputs (device, fp64 arrays): d_eps
+ * [nmo], d_Lov [nocc][nmo-nocc][M], d_Lp [np][nmo][M].  precision:
+ *   CDS_PREC_FP64: X and dSigma/dX recomputed per orbital in FP64 on the CUDA
+ *     cores, FP64 GEMMs; workspace holds one orbital's dSigma/dX
+ *     (o*v*o + v*o*v doubles) plus copies of the factors;
+ *   CDS_PREC_BF16X3 / CDS_PREC_TF32X3: X = (qx|sy) recomputed by split-
+ *     precision tcgen05 GEMMs (hi.hi + hi.lo + lo.hi, FP32 accumulation), the
+ *     factor gradients by the same GEMMs on split dSigma/dX, ~1e-5 relative
+ *     (FP32-accumulation accuracy, stored in the fp64 outputs); orbitals go
+ *     in chunks of at most 8, and the workspace holds one chunk's split
+ *     dSigma/dX in two layouts (~0.8 GB per orbital at o = 180, v = 660).
+ * Requires 0 < nocc < nmo. */
 int cds_qp_gradient(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
                     const int32_t* orb, int32_t np, const double* eps, const double* omega,
-                    const double* g, double* d_eps, double* d_Lov, double* d_Lp, void* workspace,
-                    size_t workspace_bytes, cudaStream_t stream);
+                    const double* g, int32_t precision, double* d_eps, double* d_Lov,
+                    double* d_Lp, void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 size_t cds_cd_to_mo_backward_workspace_bytes(int32_t nbf, int32_t nmo, int32_t np);
 

@@ -65,14 +65,17 @@ _SIGNATURES = {
                                          _sz, _vp]),
     "cds_ri_workspace_bytes": (_sz, [_i32, _i32, _i32]),
     "cds_ri_factors": (ctypes.c_int, [_i32, _vp, _vp, _vp, _i32, _i32, _vp, _vp, _sz, _vp]),
-    "cds_sigma2_cache_bytes": (_sz, [_i32, _i32, _i32]),
+    "cds_sigma2_cache_bytes": (_sz, [_i32, _i32, _i32, _i32]),
     "cds_sigma2_diag_cache": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _i32, _i32,
                                              _vp, _vp, _vp, _sz, _vp, _sz, _vp]),
     "cds_qp_cached_workspace_bytes": (_sz, [_i32, _i32, _i32]),
-    "cds_qp_solve_cached": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _f64, _i32, _vp, _sz, _vp, _vp,
-                                           _vp, _vp, _vp, _sz, _vp]),
+    "cds_qp_solve_cached": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _f64, _i32, _vp, _sz, _i32, _vp,
+                                           _vp, _vp, _vp, _vp, _sz, _vp]),
     "cds_qp_solve_bracketed_cached": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _f64, _i32, _vp, _sz,
-                                                     _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+                                                     _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "cds_qp_solve_bracketed": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _f64, _i32,
+                                              _i32, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "cds_wait_check": (ctypes.c_int, [_f64, _vp, _vp]),
     "cds_mp2_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32]),
     "cds_mp2_energy": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _i32, _vp, _vp, _vp, _sz, _vp]),
 }
@@ -460,6 +463,47 @@ def cds_qp_solve(Lov: torch.Tensor, Lp: torch.Tensor, orbitals: torch.Tensor, ep
     return omega, pole, iters, status
 
 
+def cds_qp_solve_bracketed(Lov: torch.Tensor, Lp: torch.Tensor, orbitals: torch.Tensor,
+                           eps: torch.Tensor, nocc: int, conv: float = 1e-5, max_iter: int = 100,
+                           precision: str = "fp64", workspace: Optional[torch.Tensor] = None,
+                           raise_on_nonconvergence: bool = False):
+    """Safeguarded Newton inside the pole-free interval around each e_q, Sigma
+    recomputed from the factors.  Returns (omega, pole, iters, status, bracket [np, 2])."""
+    lib = load()
+    Lov = _dev(Lov, torch.float64, "Lov")
+    Lp = _dev(Lp, torch.float64, "Lp")
+    orb = _dev(orbitals, torch.int32, "orbitals")
+    eps = _dev(eps, torch.float64, "eps")
+    dev = Lp.device
+    np_, nmo, M = Lp.shape
+    prec = PRECISIONS[precision]
+    omega = torch.empty(np_, dtype=torch.float64, device=dev)
+    pole = torch.empty(np_, dtype=torch.float64, device=dev)
+    iters = torch.empty(np_, dtype=torch.int32, device=dev)
+    status = torch.empty(np_, dtype=torch.int32, device=dev)
+    bracket = torch.empty((np_, 2), dtype=torch.float64, device=dev)
+    need = lib.cds_qp_workspace_bytes(nmo, nocc, M, np_, prec)
+    if workspace is None or workspace.numel() < need:
+        workspace = _workspace(need, dev)
+    st = lib.cds_qp_solve_bracketed(nmo, nocc, M, _p(Lov), _p(Lp), _p(orb), np_, _p(eps),
+                                    float(conv), int(max_iter), prec, _p(omega), _p(pole),
+                                    _p(iters), _p(status), _p(bracket), _p(workspace),
+                                    workspace.numel(), _stream(dev))
+    if st == 5 and not raise_on_nonconvergence:
+        st = CDS_OK
+    _check(st, "cds_qp_solve_bracketed")
+    return omega, pole, iters, status, bracket
+
+
+def cds_wait_check(seconds: float = 0.05, device: Optional[torch.device] = None) -> int:
+    """Run the tensor-core kernels' bounded wait on a barrier nothing completes;
+    returns the status word it leaves (CDS_ERR_TIMEOUT = 8 when it gave up)."""
+    lib = load()
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    err = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    return int(lib.cds_wait_check(float(seconds), _p(err), _stream(dev)))
+
+
 def cds_sigma2_diag_cache(Lov: torch.Tensor, Lp: torch.Tensor, eps: torch.Tensor, nocc: int,
                           E: torch.Tensor, precision: str = "bf16x3",
                           cache: Optional[torch.Tensor] = None,
@@ -478,7 +522,7 @@ def cds_sigma2_diag_cache(Lov: torch.Tensor, Lp: torch.Tensor, eps: torch.Tensor
     prec = PRECISIONS[precision]
     sigma = torch.empty((np_, nE), dtype=torch.float64, device=dev)
     dsigma = torch.empty((np_, nE), dtype=torch.float64, device=dev)
-    cb = lib.cds_sigma2_cache_bytes(nmo, nocc, np_)
+    cb = lib.cds_sigma2_cache_bytes(nmo, nocc, np_, prec)
     if cache is None or cache.numel() < cb:
         cache = torch.empty(max(cb, 1), dtype=torch.uint8, device=dev)
     need = lib.cds_sigma2_workspace_bytes(nmo, nocc, M, np_, nE, prec)
@@ -494,9 +538,10 @@ def cds_sigma2_diag_cache(Lov: torch.Tensor, Lp: torch.Tensor, eps: torch.Tensor
 def cds_qp_solve_cached(cache: torch.Tensor, orbitals: torch.Tensor, eps: torch.Tensor, nmo: int,
                         nocc: int, conv: float = 1e-5, max_iter: int = 50,
                         workspace: Optional[torch.Tensor] = None,
-                        raise_on_nonconvergence: bool = False):
+                        raise_on_nonconvergence: bool = False, precision: str = "bf16x3"):
     """Newton quasiparticle solve (Eq. iter, Eq. ps, Eq. NR) with Sigma from the
-    numerators cds_sigma2_diag_cache stored.  Returns (omega, pole, iters, status)."""
+    numerators cds_sigma2_diag_cache stored (in `precision`, the cache's form).
+    Returns (omega, pole, iters, status)."""
     lib = load()
     orb = _dev(orbitals, torch.int32, "orbitals")
     eps = _dev(eps, torch.float64, "eps")
@@ -510,7 +555,8 @@ def cds_qp_solve_cached(cache: torch.Tensor, orbitals: torch.Tensor, eps: torch.
     if workspace is None or workspace.numel() < need:
         workspace = _workspace(need, dev)
     st = lib.cds_qp_solve_cached(nmo, nocc, np_, _p(orb), _p(eps), float(conv), int(max_iter),
-                                 _p(cache), cache.numel(), _p(omega), _p(pole), _p(iters),
+                                 _p(cache), cache.numel(), PRECISIONS[precision], _p(omega),
+                                 _p(pole), _p(iters),
                                  _p(status), _p(workspace), workspace.numel(), _stream(dev))
     if st == 5 and not raise_on_nonconvergence:
         st = CDS_OK
@@ -521,7 +567,8 @@ def cds_qp_solve_cached(cache: torch.Tensor, orbitals: torch.Tensor, eps: torch.
 def cds_qp_solve_bracketed_cached(cache: torch.Tensor, orbitals: torch.Tensor, eps: torch.Tensor,
                                   nmo: int, nocc: int, conv: float = 1e-5, max_iter: int = 100,
                                   workspace: Optional[torch.Tensor] = None,
-                                  raise_on_nonconvergence: bool = False):
+                                  raise_on_nonconvergence: bool = False,
+                                  precision: str = "bf16x3"):
     """Safeguarded Newton inside the pole-free interval around each e_q, Sigma
     from cached numerators.  Returns (omega, pole, iters, status, bracket [np, 2])."""
     lib = load()
@@ -538,7 +585,8 @@ def cds_qp_solve_bracketed_cached(cache: torch.Tensor, orbitals: torch.Tensor, e
     if workspace is None or workspace.numel() < need:
         workspace = _workspace(need, dev)
     st = lib.cds_qp_solve_bracketed_cached(nmo, nocc, np_, _p(orb), _p(eps), float(conv),
-                                           int(max_iter), _p(cache), cache.numel(), _p(omega),
+                                           int(max_iter), _p(cache), cache.numel(),
+                                           PRECISIONS[precision], _p(omega),
                                            _p(pole), _p(iters), _p(status), _p(bracket),
                                            _p(workspace), workspace.numel(), _stream(dev))
     if st == 5 and not raise_on_nonconvergence:
@@ -701,17 +749,20 @@ def cds_tune_get(knob: int) -> int:
 # adjoint
 # ---------------------------------------------------------------------------
 _SIGNATURES.update({
-    "cds_qp_gradient_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32]),
-    "cds_qp_gradient": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp,
-                                       _vp, _vp, _vp, _sz, _vp]),
+    "cds_qp_gradient_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
+    "cds_qp_gradient": (ctypes.c_int, [_i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp, _vp, _i32,
+                                       _vp, _vp, _vp, _vp, _sz, _vp]),
     "cds_cd_to_mo_backward_workspace_bytes": (_sz, [_i32, _i32, _i32]),
     "cds_cd_to_mo_backward": (ctypes.c_int, [_i32, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _vp, _vp,
                                              _vp, _vp, _sz, _vp]),
 })
 
 
-def cds_qp_gradient(Lov, Lp, orbitals, eps, nocc, omega, g):
-    """dl/d(eps, Lov, Lp) for upstream gradients g of converged roots omega."""
+def cds_qp_gradient(Lov, Lp, orbitals, eps, nocc, omega, g, precision: str = "fp64"):
+    """dl/d(eps, Lov, Lp) for upstream gradients g of converged roots omega.
+
+    precision "fp64" (FP64 CUDA cores) or "bf16x3" / "tf32x3" (tensor cores,
+    FP32 accumulation)."""
     lib = load()
     Lov = _dev(Lov, torch.float64, "Lov")
     Lp = _dev(Lp, torch.float64, "Lp")
@@ -724,9 +775,10 @@ def cds_qp_gradient(Lov, Lp, orbitals, eps, nocc, omega, g):
     d_eps = torch.empty(nmo, dtype=torch.float64, device=dev)
     d_Lov = torch.empty_like(Lov)
     d_Lp = torch.empty_like(Lp)
-    ws = _workspace(lib.cds_qp_gradient_workspace_bytes(nmo, nocc, M, np_), dev)
+    prec = PRECISIONS[precision]
+    ws = _workspace(lib.cds_qp_gradient_workspace_bytes(nmo, nocc, M, np_, prec), dev)
     _check(lib.cds_qp_gradient(nmo, nocc, M, _p(Lov), _p(Lp), _p(orb), np_, _p(eps), _p(omega),
-                               _p(g), _p(d_eps), _p(d_Lov), _p(d_Lp), _p(ws), ws.numel(),
+                               _p(g), prec, _p(d_eps), _p(d_Lov), _p(d_Lp), _p(ws), ws.numel(),
                                _stream(dev)), "cds_qp_gradient")
     return d_eps, d_Lov, d_Lp
 
@@ -750,15 +802,20 @@ def cds_cd_to_mo_backward(L, C, nocc, orbitals, d_Lov, d_Lp):
 
 class QPEnergies(torch.autograd.Function):
     """Quasiparticle energies of the given orbitals as a differentiable
-    function of (eps, Lov, Lp): forward = cds_qp_solve, backward = the
-    hand-written adjoint (cds_qp_gradient) at the converged roots."""
+    function of (eps, Lov, Lp): forward = cds_qp_solve (or the safeguarded
+    cds_qp_solve_bracketed), backward = the hand-written adjoint
+    (cds_qp_gradient) at the converged roots, in grad_precision (default: FP64
+    after an FP64 solve, BF16X3 tensor cores after a split-precision one)."""
 
     @staticmethod
-    def forward(ctx, eps, Lov, Lp, orbitals, nocc, conv=1e-12, max_iter=100, precision="fp64"):
-        w, P, it, st = cds_qp_solve(Lov, Lp, orbitals, eps, nocc, conv=conv, max_iter=max_iter,
-                                    precision=precision)
+    def forward(ctx, eps, Lov, Lp, orbitals, nocc, conv=1e-12, max_iter=100, precision="fp64",
+                bracketed=False, grad_precision=None):
+        solve = cds_qp_solve_bracketed if bracketed else cds_qp_solve
+        w, P, it, st = solve(Lov, Lp, orbitals, eps, nocc, conv=conv, max_iter=max_iter,
+                             precision=precision)[:4]
         ctx.save_for_backward(eps, Lov, Lp, orbitals, w)
         ctx.nocc = nocc
+        ctx.grad_precision = grad_precision or ("fp64" if precision == "fp64" else "bf16x3")
         ctx.mark_non_differentiable(st)
         return w, st
 
@@ -766,9 +823,10 @@ class QPEnergies(torch.autograd.Function):
     def backward(ctx, gw, gst):
         eps, Lov, Lp, orbitals, w = ctx.saved_tensors
         if gw is None:
-            return (None,) * 8
-        d_eps, d_Lov, d_Lp = cds_qp_gradient(Lov, Lp, orbitals, eps, ctx.nocc, w, gw.contiguous())
-        return d_eps, d_Lov, d_Lp, None, None, None, None, None
+            return (None,) * 10
+        d_eps, d_Lov, d_Lp = cds_qp_gradient(Lov, Lp, orbitals, eps, ctx.nocc, w, gw.contiguous(),
+                                             ctx.grad_precision)
+        return d_eps, d_Lov, d_Lp, None, None, None, None, None, None, None
 
 
 class MOFactors(torch.autograd.Function):

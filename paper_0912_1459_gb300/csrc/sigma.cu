@@ -13,12 +13,14 @@ namespace cds {
 constexpr int kTB64 = 32;   // pair-index block of the FP64 path
 constexpr int kJK64 = 16;   // J depth per shared-memory stage
 constexpr int kEChunk = 64; // energies reduced per pass over the tile
+constexpr int64_t kCacheItem64 = kTB64 * kTB64;   // cached numerators per FP64 work item
 
 // One work item per block: two 32x32 FP64 tiles over all J, then the fused
 // denominator-weighted reduction for every energy.
 __global__ void __launch_bounds__(256)
 k_sigma_fp64(SigmaTerm tm, int32_t M, int32_t nE, const double* __restrict__ E,
-             const int32_t* __restrict__ active, int64_t item0, double* __restrict__ part) {
+             const int32_t* __restrict__ active, int64_t item0, double* __restrict__ part,
+             double* __restrict__ cache) {
     __shared__ double sred[8][kEChunk][2];   // per-warp partial sums
     __shared__ double sA1[kTB64][kJK64 + 1], sB1[kTB64][kJK64 + 1];
     __shared__ double sA2[kTB64][kJK64 + 1], sB2[kTB64][kJK64 + 1];
@@ -85,6 +87,11 @@ k_sigma_fp64(SigmaTerm tm, int32_t M, int32_t nE, const double* __restrict__ E,
             num[e] = (A == B) ? (2.0 * x1 - x2) * x1 : 2.0 * (x1 * x1 + x2 * x2 - x1 * x2);
             base[e] = ok[e] ? es - tm.eps_x[x] - tm.eps_x[y] : 0.0;
         }
+    if (cache) {   // the numerators of this item, [element k][thread] (coalesced)
+        double* c = cache + (item0 + item) * kCacheItem64;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) c[k * 256 + tid] = num[k];
+    }
     const int lane = tid & 31, w = tid >> 5;
     for (int e0 = 0; e0 < nE; e0 += kEChunk) {
         const int ne = min(kEChunk, nE - e0);
@@ -144,6 +151,59 @@ __global__ void k_sigma_reduce(const double* __restrict__ part, int64_t per_t0, 
     }
 }
 
+// Sigma and dSigma/dE at one energy per orbital (E[t]) from the numerators a
+// k_sigma_fp64 pass stored: per element the arithmetic of k_sigma_fp64's
+// epilogue (same denominator, same order of sums), so the result equals the
+// recomputing kernel's at the same energy bit for bit; streams 8 KB per item
+// instead of recomputing the integrals.
+__global__ void __launch_bounds__(256)
+k_sigma_fp64_cached(SigmaTerm tm, const double* __restrict__ E, const int32_t* __restrict__ active,
+                    int64_t item0, int64_t nitems, const double* __restrict__ cache,
+                    double* __restrict__ part) {
+    __shared__ double sred[8][2];
+    const int32_t nb = nblocks_of(tm.nx, kTB64);
+    const int64_t npb = npairs_of(nb);
+    const int tid = threadIdx.x, tr = tid / 16, tc = tid % 16;
+    const int lane = tid & 31, w = tid >> 5;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int32_t t = (int32_t)(item / (tm.ns * npb));
+        const int64_t r = item - (int64_t)t * tm.ns * npb;
+        const int32_t s = (int32_t)(r / npb);
+        int32_t A, B;
+        block_pair(r - (int64_t)s * npb, nb, A, B);
+        if (active && !active[t]) continue;   // the same for the whole block
+        const double* c = cache + (item0 + item) * kCacheItem64;
+        double num[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) num[k] = c[k * 256 + tid];
+        const double Ee = E[t], es = tm.eps_s[s];
+        double sv = 0.0, dv = 0.0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int x = A * kTB64 + tr * 2 + k / 2, y = B * kTB64 + tc * 2 + k % 2;
+            if (x >= tm.nx || y >= tm.nx) continue;
+            const double base = es - tm.eps_x[x] - tm.eps_x[y];
+            const double rcp = 1.0 / (Ee + base);
+            const double nr = num[k] * rcp;
+            sv += nr;
+            dv -= nr * rcp;
+        }
+        for (int o = 16; o; o >>= 1) {
+            sv += __shfl_xor_sync(0xffffffffu, sv, o);
+            dv += __shfl_xor_sync(0xffffffffu, dv, o);
+        }
+        if (lane == 0) { sred[w][0] = sv; sred[w][1] = dv; }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int ww = 0; ww < 8; ++ww) { a += sred[ww][0]; b += sred[ww][1]; }
+            part[(item0 + item) * 2] = a;
+            part[(item0 + item) * 2 + 1] = b;
+        }
+        __syncthreads();
+    }
+}
+
 // The two terms of Eq. SE for the factor layout of cds_cd_to_mo.
 void make_terms(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
                 const double* eps, SigmaTerm& t0, SigmaTerm& t1) {
@@ -170,19 +230,26 @@ size_t fp64_part_bytes(int32_t nmo, int32_t nocc, int32_t np, int32_t nE) {
     return align_up((size_t)items * nE * 2 * sizeof(double));
 }
 
+size_t fp64_cache_bytes(int32_t nmo, int32_t nocc, int32_t np) {
+    SigmaTerm t0{}, t1{};
+    make_terms(nmo, nocc, 1, nullptr, nullptr, nullptr, t0, t1);
+    const int64_t items = items_of(t0, np, kTB64) + items_of(t1, np, kTB64);
+    return (size_t)items * kCacheItem64 * sizeof(double);
+}
+
 int sigma2_fp64(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const double* Lp,
                 int32_t np, const double* eps, const double* E, int32_t nE,
                 const int32_t* active, double* sigma, double* dsigma, double* part,
-                cudaStream_t stream) {
+                cudaStream_t stream, double* cache) {
     SigmaTerm t0, t1;
     make_terms(nmo, nocc, M, Lov, Lp, eps, t0, t1);
     int64_t n0 = items_of(t0, np, kTB64), n1 = items_of(t1, np, kTB64);
     if (n0 > 0) {
-        k_sigma_fp64<<<(unsigned)n0, 256, 0, stream>>>(t0, M, nE, E, active, 0, part);
+        k_sigma_fp64<<<(unsigned)n0, 256, 0, stream>>>(t0, M, nE, E, active, 0, part, cache);
         CDS_LAUNCH_CHECK();
     }
     if (n1 > 0) {
-        k_sigma_fp64<<<(unsigned)n1, 256, 0, stream>>>(t1, M, nE, E, active, n0, part);
+        k_sigma_fp64<<<(unsigned)n1, 256, 0, stream>>>(t1, M, nE, E, active, n0, part, cache);
         CDS_LAUNCH_CHECK();
     }
     if (n0 + n1 == 0) {
@@ -193,6 +260,41 @@ int sigma2_fp64(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const d
     dim3 grid(nE, np);
     k_sigma_reduce<<<grid, 256, 0, stream>>>(part, np ? n0 / np : 0, n0, np ? n1 / np : 0, nE,
                                             active, sigma, dsigma);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
+size_t fp64_cached_workspace_bytes(int32_t nmo, int32_t nocc, int32_t np) {
+    return fp64_part_bytes(nmo, nocc, np, 1);
+}
+
+int sigma2_cached_fp64(int32_t nmo, int32_t nocc, int32_t np, const double* eps, const double* E,
+                       const int32_t* active, const double* cache, double* sigma, double* dsigma,
+                       double* part, cudaStream_t stream) {
+    SigmaTerm t0, t1;
+    make_terms(nmo, nocc, 1, nullptr, nullptr, eps, t0, t1);
+    const int64_t n0 = items_of(t0, np, kTB64), n1 = items_of(t1, np, kTB64);
+    if (n0 + n1 == 0) {
+        CDS_CUDA_TRY(cudaMemsetAsync(sigma, 0, sizeof(double) * np, stream));
+        if (dsigma) CDS_CUDA_TRY(cudaMemsetAsync(dsigma, 0, sizeof(double) * np, stream));
+        return CDS_OK;
+    }
+    int sms = 0, dev = 0;
+    CDS_CUDA_TRY(cudaGetDevice(&dev));
+    CDS_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t gmax = (int64_t)std::max(sms, 1) * 8;
+    if (n0 > 0) {
+        k_sigma_fp64_cached<<<(unsigned)std::min(n0, gmax), 256, 0, stream>>>(t0, E, active, 0,
+                                                                              n0, cache, part);
+        CDS_LAUNCH_CHECK();
+    }
+    if (n1 > 0) {
+        k_sigma_fp64_cached<<<(unsigned)std::min(n1, gmax), 256, 0, stream>>>(t1, E, active, n0,
+                                                                              n1, cache, part);
+        CDS_LAUNCH_CHECK();
+    }
+    k_sigma_reduce<<<dim3(1, np), 256, 0, stream>>>(part, np ? n0 / np : 0, n0, np ? n1 / np : 0, 1,
+                                                    active, sigma, dsigma);
     CDS_LAUNCH_CHECK();
     return CDS_OK;
 }
@@ -247,7 +349,7 @@ static int mp2_fp64(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, con
         CDS_CUDA_TRY(cudaMemsetAsync(ep, 0, sizeof(double) * std::max(nocc, 1), stream));
         return sum_fixed(ep, nocc, e_total, stream);
     }
-    k_sigma_fp64<<<(unsigned)n, 256, 0, stream>>>(t, M, 1, eps, nullptr, 0, part);
+    k_sigma_fp64<<<(unsigned)n, 256, 0, stream>>>(t, M, 1, eps, nullptr, 0, part, nullptr);
     CDS_LAUNCH_CHECK();
     k_sigma_reduce<<<dim3(1, nocc), 256, 0, stream>>>(part, 0, 0, n / nocc, 1, nullptr, ep,
                                                      nullptr);
@@ -258,7 +360,8 @@ static int mp2_fp64(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, con
 size_t sigma_ws_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE,
                       int32_t precision) {
     if (precision == CDS_PREC_FP64) return fp64_part_bytes(nmo, nocc, np, nE);
-    if (is_split16(precision)) return tc_workspace_bytes(nmo, nocc, M, np, nE);
+    if (is_split_tc(precision))
+        return tc_workspace_bytes(nmo, nocc, M, np, nE, precision == CDS_PREC_TF32X3);
     return 0;
 }
 
@@ -268,8 +371,8 @@ int sigma2_dispatch(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, con
                     void* ws, cudaStream_t stream, bool resplit) {
     if (precision == CDS_PREC_FP64)
         return sigma2_fp64(nmo, nocc, M, Lov, Lp, np, eps, E, nE, active, sigma, dsigma,
-                           static_cast<double*>(ws), stream);
-    if (is_split16(precision))
+                           static_cast<double*>(ws), stream, nullptr);
+    if (is_split_tc(precision))
         return sigma2_tc(nmo, nocc, M, Lov, Lp, np, eps, E, nE, active, precision, sigma, dsigma,
                          ws, stream, resplit);
     return CDS_ERR_UNSUPPORTED;
@@ -296,7 +399,7 @@ extern "C" int cds_sigma2_diag(int32_t nmo, int32_t nocc, int32_t M, const doubl
                                double* dsigma, void* workspace, size_t workspace_bytes,
                                cudaStream_t stream) {
     if (!sigma_args_ok(nmo, nocc, M, np, nE)) return CDS_ERR_ARG;
-    if (precision != CDS_PREC_FP64 && !is_split16(precision)) return CDS_ERR_UNSUPPORTED;
+    if (precision != CDS_PREC_FP64 && !is_split_tc(precision)) return CDS_ERR_UNSUPPORTED;
     if (np == 0) return CDS_OK;
     if (!Lp || !eps || !E || !sigma || (nocc > 0 && nocc < nmo && !Lov)) return CDS_ERR_ARG;
     size_t need = sigma_ws_bytes(nmo, nocc, M, np, nE, precision);
@@ -331,9 +434,12 @@ extern "C" int cds_mp2_energy(int32_t nmo, int32_t nocc, int32_t M, const double
     return mp2_tc(nmo, nocc, M, Lov, eps, precision, e_pair, e_total, workspace, stream);
 }
 
-extern "C" size_t cds_sigma2_cache_bytes(int32_t nmo, int32_t nocc, int32_t np) {
+extern "C" size_t cds_sigma2_cache_bytes(int32_t nmo, int32_t nocc, int32_t np,
+                                         int32_t precision) {
     if (nmo <= 0 || nocc < 0 || nocc > nmo || np < 0) return 0;
-    return tc_cache_bytes(nmo, nocc, np);
+    if (precision == CDS_PREC_FP64) return fp64_cache_bytes(nmo, nocc, np);
+    if (is_split_tc(precision)) return tc_cache_bytes(nmo, nocc, np);
+    return 0;
 }
 
 extern "C" int cds_sigma2_diag_cache(int32_t nmo, int32_t nocc, int32_t M, const double* Lov,
@@ -343,13 +449,16 @@ extern "C" int cds_sigma2_diag_cache(int32_t nmo, int32_t nocc, int32_t M, const
                                      size_t cache_bytes, void* workspace, size_t workspace_bytes,
                                      cudaStream_t stream) {
     if (!sigma_args_ok(nmo, nocc, M, np, nE)) return CDS_ERR_ARG;
-    if (!is_split16(precision)) return CDS_ERR_UNSUPPORTED;
+    if (precision != CDS_PREC_FP64 && !is_split_tc(precision)) return CDS_ERR_UNSUPPORTED;
     if (np == 0) return CDS_OK;
     if (!Lp || !eps || !E || !sigma || !cache || (nocc > 0 && nocc < nmo && !Lov))
         return CDS_ERR_ARG;
-    if (cache_bytes < tc_cache_bytes(nmo, nocc, np)) return CDS_ERR_ARG;
+    if (cache_bytes < cds_sigma2_cache_bytes(nmo, nocc, np, precision)) return CDS_ERR_ARG;
     size_t need = sigma_ws_bytes(nmo, nocc, M, np, nE, precision);
     if (need && (!workspace || workspace_bytes < need)) return CDS_ERR_WORKSPACE;
+    if (precision == CDS_PREC_FP64)
+        return sigma2_fp64(nmo, nocc, M, Lov, Lp, np, eps, E, nE, nullptr, sigma, dsigma,
+                           static_cast<double*>(workspace), stream, static_cast<double*>(cache));
     return sigma2_tc(nmo, nocc, M, Lov, Lp, np, eps, E, nE, nullptr, precision, sigma, dsigma,
                      workspace, stream, true, static_cast<float*>(cache));
 }

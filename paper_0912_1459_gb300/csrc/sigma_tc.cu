@@ -22,7 +22,10 @@
 // Warp roles (320 threads): warp 0 = TMA producer (one thread), warp 1 = TMEM
 // allocator + MMA issuer (one thread), warps 2..9 = epilogue.  Shared memory
 // holds 3 stages of 8 operand tiles (128 rows x 32 bf16, 64-byte swizzle);
-// TMEM holds two accumulator pairs (512 columns) so the epilogue of one item
+// TMEM (512 columns) holds either one tile pair with separate hi.hi and
+// cross-term accumulators (the default split modes; single-buffered, so the
+// epilogue of one item and the MMAs of the next alternate) or, with the three
+// products in one accumulator, two tile pairs so the epilogue of one item
 // overlaps the MMAs of the next.  Every wait is bounded (2 s of %globaltimer)
 // and sets an error word instead of hanging.
 #include <cuda.h>
@@ -58,11 +61,18 @@ constexpr int kGridEC = 4;                    // k_sigma_cached_grid: energies p
 constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 256 + NUM_EPI_WARPS * RED_E * 2 * 4 +
                               EPS_SMEM * 8;
 
-// kind::f16 instruction descriptor: D f32, A/B bf16 (format 1) or fp16
-// (format 0), both K-major, M = N = 128.
-template <bool BF16>
+// Operand formats of the split products: FMT 0 = fp16, 1 = bf16 (kind::f16,
+// 16-bit containers, K = 16 per MMA), 2 = tf32 (kind::tf32, 32-bit
+// containers, K = 8 per MMA).  A k-block is one 64-byte row either way.
+constexpr int FMT_TF32 = 2;
+template <int FMT>
+__host__ __device__ constexpr int kb_elems() { return FMT == FMT_TF32 ? KB / 2 : KB; }
+
+// Instruction descriptor: D f32, A/B format fp16 (0), bf16 (1) or tf32 (2),
+// both K-major, M = N = 128.
+template <int FMT>
 __host__ __device__ constexpr uint32_t idesc() {
-    return (1u << 4) | ((BF16 ? 1u : 0u) << 7) | ((BF16 ? 1u : 0u) << 10) |
+    return (1u << 4) | ((uint32_t)FMT << 7) | ((uint32_t)FMT << 10) |
            ((uint32_t)(TB >> 3) << 17) | ((uint32_t)(TB >> 4) << 24);
 }
 
@@ -236,7 +246,7 @@ __device__ __forceinline__ int64_t item_at(int64_t k, int64_t n, int order) {
     return b + k < e ? b + k : -1;
 }
 
-template <int EC, bool BF16, bool SEP, bool BATCH>
+template <int EC, int FMT, bool SEP, bool BATCH>
 __global__ void __launch_bounds__(THREADS, 1)
 k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __restrict__ mols,
            int32_t nmol, int64_t nitems_batch, const float2* __restrict__ E2,
@@ -244,7 +254,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
            const float* __restrict__ inv_scale, double* __restrict__ part,
            unsigned long long* __restrict__ stamps, int32_t* __restrict__ err, int32_t order,
            float* __restrict__ cache) {
-    constexpr uint32_t ID = idesc<BF16>();
+    constexpr uint32_t ID = idesc<FMT>();
     constexpr int NBUF = SEP ? 1 : 2;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -311,7 +321,7 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
                     mbar_arrive_expect_tx(&full[stage], bytes);
                     last_parity[stage] = (int32_t)phase;
                     const uint32_t st = smem_u32(stages + stage * STAGE_BYTES);
-                    const int k0 = kb * KB;
+                    const int k0 = kb * kb_elems<FMT>();
                     tma_load_3d(st + 0 * TILE_BYTES, mq_hi, &full[stage], k0, A * TB, t);
                     tma_load_3d(st + 1 * TILE_BYTES, mq_lo, &full[stage], k0, A * TB, t);
                     tma_load_3d(st + 2 * TILE_BYTES, mb_hi, &full[stage], k0, bB1, bB2);
@@ -361,15 +371,24 @@ k_sigma_tc(const __grid_constant__ Maps maps, const Params P, const MolDesc* __r
                     const uint32_t b2h = diag ? a1h : base + 6 * TILE_BYTES;
                     const uint32_t b2l = diag ? a1l : base + 7 * TILE_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < KB / 16; ++kk) {
+                    for (int kk = 0; kk < 2; ++kk) {   // 32 bytes of k per MMA
                         const uint32_t off = kk * 32;
                         const uint32_t first = (kb | kk) ? 1u : 0u;
-                        mma_f16(d1, sdesc(a1h + off), sdesc(b1h + off), IDn, first);
-                        mma_f16(d1x, sdesc(a1h + off), sdesc(b1l + off), IDn, SEP ? first : 1u);
-                        mma_f16(d1x, sdesc(a1l + off), sdesc(b1h + off), IDn, 1u);
-                        mma_f16(d2, sdesc(a2h + off), sdesc(b2h + off), IDn, first);
-                        mma_f16(d2x, sdesc(a2h + off), sdesc(b2l + off), IDn, SEP ? first : 1u);
-                        mma_f16(d2x, sdesc(a2l + off), sdesc(b2h + off), IDn, 1u);
+                        if constexpr (FMT == FMT_TF32) {
+                            mma_tf32(d1, sdesc(a1h + off), sdesc(b1h + off), IDn, first);
+                            mma_tf32(d1x, sdesc(a1h + off), sdesc(b1l + off), IDn, SEP ? first : 1u);
+                            mma_tf32(d1x, sdesc(a1l + off), sdesc(b1h + off), IDn, 1u);
+                            mma_tf32(d2, sdesc(a2h + off), sdesc(b2h + off), IDn, first);
+                            mma_tf32(d2x, sdesc(a2h + off), sdesc(b2l + off), IDn, SEP ? first : 1u);
+                            mma_tf32(d2x, sdesc(a2l + off), sdesc(b2h + off), IDn, 1u);
+                        } else {
+                            mma_f16(d1, sdesc(a1h + off), sdesc(b1h + off), IDn, first);
+                            mma_f16(d1x, sdesc(a1h + off), sdesc(b1l + off), IDn, SEP ? first : 1u);
+                            mma_f16(d1x, sdesc(a1l + off), sdesc(b1h + off), IDn, 1u);
+                            mma_f16(d2, sdesc(a2h + off), sdesc(b2h + off), IDn, first);
+                            mma_f16(d2x, sdesc(a2h + off), sdesc(b2l + off), IDn, SEP ? first : 1u);
+                            mma_f16(d2x, sdesc(a2l + off), sdesc(b2h + off), IDn, 1u);
+                        }
                     }
                     mma_commit(&empty[stage]);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
@@ -580,6 +599,22 @@ __global__ void k_split16(const double* __restrict__ src, int64_t rows, int32_t 
     }
 }
 
+// hi = tf32(x) (round to nearest on the 13 dropped bits), lo = fl32(x - hi);
+// the MMA reads lo's top 19 bits.  No scaling (FP32 exponent range); columns
+// J >= M are zero.
+__global__ void k_split_tf32(const double* __restrict__ src, int64_t rows, int32_t M, int32_t Mp,
+                             float* __restrict__ hi, float* __restrict__ lo) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= rows * Mp) return;
+    int64_t r = e / Mp;
+    int J = (int)(e - r * Mp);
+    const double x = J < M ? src[r * M + J] : 0.0;
+    const float f = (float)x;
+    const float h = __uint_as_float((__float_as_uint(f) + 0x1000u) & 0xFFFFE000u);
+    hi[e] = h;
+    lo[e] = (float)(x - (double)h);
+}
+
 // FP64 values as (hi, lo) float pairs: hi = fl32(x), lo = fl32(x - hi).
 __global__ void k_to_pairs(const double* __restrict__ x, int64_t n, float2* __restrict__ out) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -624,7 +659,8 @@ __global__ void k_tc_reduce(const double* __restrict__ part, int64_t per_t0, int
 }
 
 struct TcLayout {
-    uint16_t *lp_hi, *lp_lo, *lov_hi, *lov_lo;   // bf16 or fp16 bit patterns
+    uint16_t *lp_hi, *lp_lo, *lov_hi, *lov_lo;   // bf16 or fp16 bit patterns (tf32: pairs of
+                                                 // uint16 per 32-bit element)
     double* part;
     unsigned long long* amax;                    // [2]: max |Lp|, max |Lov|
     float* inv;                                  // 1 / (s_Lp s_Lov)
@@ -641,14 +677,16 @@ int64_t tc_items(int32_t nx, int32_t ns, int32_t np) {
     return (int64_t)np * ns * npairs_of(nblocks_of(nx, TB));
 }
 
-TcLayout tc_layout(void* ws, int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE) {
+TcLayout tc_layout(void* ws, int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE,
+                   bool tf32 = false) {
     const int32_t Mp = padded(std::max(M, 1)), nv = nmo - nocc;
+    const size_t w = tf32 ? 2 : 1;   // uint16 units per operand element
     Carver c(ws);
     TcLayout l;
-    l.lp_hi = c.take<uint16_t>((size_t)np * nmo * Mp);
-    l.lp_lo = c.take<uint16_t>((size_t)np * nmo * Mp);
-    l.lov_hi = c.take<uint16_t>((size_t)nocc * nv * Mp);
-    l.lov_lo = c.take<uint16_t>((size_t)nocc * nv * Mp);
+    l.lp_hi = c.take<uint16_t>((size_t)np * nmo * Mp * w);
+    l.lp_lo = c.take<uint16_t>((size_t)np * nmo * Mp * w);
+    l.lov_hi = c.take<uint16_t>((size_t)nocc * nv * Mp * w);
+    l.lov_lo = c.take<uint16_t>((size_t)nocc * nv * Mp * w);
     int64_t items = tc_items(nocc, nv, np) + tc_items(nv, nocc, np);
     l.part = c.take<double>((size_t)std::max<int64_t>(items, 1) * nE * 2);
     l.amax = c.take<unsigned long long>(2);
@@ -673,16 +711,21 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
     return fn;
 }
 
-// 3-D 16-bit map {d0 (J, contiguous), d1, d2} with byte strides s1, s2.
-bool make_map(CUtensorMap* m, bool bf16, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
+// 3-D operand map {d0 (J, contiguous), d1, d2} with byte strides s1, s2, of
+// format fmt (0 fp16, 1 bf16, 2 tf32 in FP32 containers); box {one 64-byte
+// row of J, b1, b2}.
+bool make_map(CUtensorMap* m, int fmt, const void* base, uint64_t d0, uint64_t d1, uint64_t d2,
               uint64_t s1, uint64_t s2, uint32_t b1, uint32_t b2) {
     auto enc = encoder();
     if (!enc) return false;
     cuuint64_t dims[3] = {d0, d1, d2};
     cuuint64_t strides[2] = {s1, s2};
-    cuuint32_t box[3] = {(cuuint32_t)KB, b1, b2};
+    cuuint32_t box[3] = {(cuuint32_t)(fmt == FMT_TF32 ? KB / 2 : KB), b1, b2};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
+    const CUtensorMapDataType dt = fmt == FMT_TF32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : fmt == 1      ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    CUresult r = enc(m, dt, 3,
                      const_cast<void*>(base), dims, strides,
                      box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -730,17 +773,18 @@ bool device_ok() {
 
 }  // namespace tc
 
-size_t tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE) {
-    return tc::tc_layout(nullptr, nmo, nocc, M, np, nE).bytes;
+size_t tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE,
+                          bool tf32) {
+    return tc::tc_layout(nullptr, nmo, nocc, M, np, nE, tf32).bytes;
 }
 
 namespace tc {
-template <int EC, bool BF16, bool SEP>
+template <int EC, int FMT, bool SEP>
 static int launch_tc(int grid, const Maps& maps, const Params& P, const int32_t* active,
                      const TcLayout& lay, cudaStream_t stream, float* cache) {
-    CDS_CUDA_TRY(cudaFuncSetAttribute(k_sigma_tc<EC, BF16, SEP, false>,
+    CDS_CUDA_TRY(cudaFuncSetAttribute(k_sigma_tc<EC, FMT, SEP, false>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES));
-    k_sigma_tc<EC, BF16, SEP, false><<<grid, THREADS, SMEM_BYTES, stream>>>(
+    k_sigma_tc<EC, FMT, SEP, false><<<grid, THREADS, SMEM_BYTES, stream>>>(
         maps, P, nullptr, 0, 0, lay.E2, lay.eps2, active, lay.inv, lay.part, nullptr, lay.err,
         tune_item_order(), cache);
     CDS_LAUNCH_CHECK();
@@ -748,14 +792,35 @@ static int launch_tc(int grid, const Maps& maps, const Params& P, const int32_t*
 }
 
 template <bool SEP>
-static int launch_any(int grid, bool bf16, int nE, const Maps& maps, const Params& P,
+static int launch_any(int grid, int fmt, int nE, const Maps& maps, const Params& P,
                       const int32_t* active, const TcLayout& lay, cudaStream_t stream,
                       float* cache = nullptr) {
     if (nE == 1)
-        return bf16 ? launch_tc<1, true, SEP>(grid, maps, P, active, lay, stream, cache)
-                    : launch_tc<1, false, SEP>(grid, maps, P, active, lay, stream, cache);
-    return bf16 ? launch_tc<16, true, SEP>(grid, maps, P, active, lay, stream, cache)
-                : launch_tc<16, false, SEP>(grid, maps, P, active, lay, stream, cache);
+        return fmt == FMT_TF32 ? launch_tc<1, FMT_TF32, SEP>(grid, maps, P, active, lay, stream, cache)
+               : fmt == 1      ? launch_tc<1, 1, SEP>(grid, maps, P, active, lay, stream, cache)
+                               : launch_tc<1, 0, SEP>(grid, maps, P, active, lay, stream, cache);
+    return fmt == FMT_TF32 ? launch_tc<16, FMT_TF32, SEP>(grid, maps, P, active, lay, stream, cache)
+           : fmt == 1      ? launch_tc<16, 1, SEP>(grid, maps, P, active, lay, stream, cache)
+                           : launch_tc<16, 0, SEP>(grid, maps, P, active, lay, stream, cache);
+}
+
+// TF32 operands: no scale (1 / (s_A s_B) = 1).
+static int split_all_tf32(const double* Lp, const double* Lov, int64_t rows_p, int64_t rows_ov,
+                          int32_t M, int32_t Mp, const TcLayout& lay, cudaStream_t stream) {
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.amax, 0, 2 * sizeof(unsigned long long), stream));
+    const int64_t n1 = rows_p * Mp;
+    k_split_tf32<<<(unsigned)((n1 + 255) / 256), 256, 0, stream>>>(
+        Lp, rows_p, M, Mp, (float*)lay.lp_hi, (float*)lay.lp_lo);
+    CDS_LAUNCH_CHECK();
+    const int64_t n2 = rows_ov * Mp;
+    if (n2 > 0) {
+        k_split_tf32<<<(unsigned)((n2 + 255) / 256), 256, 0, stream>>>(
+            Lov, rows_ov, M, Mp, (float*)lay.lov_hi, (float*)lay.lov_lo);
+        CDS_LAUNCH_CHECK();
+    }
+    k_inv_scale<<<1, 1, 0, stream>>>(lay.amax, 1, lay.inv);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
 }
 
 template <typename T>
@@ -831,21 +896,24 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
               cudaStream_t stream, bool resplit, float* cache) {
     using namespace tc;
     if (!device_ok()) return CDS_ERR_UNSUPPORTED;
-    const bool bf16 = precision == CDS_PREC_BF16X3;
+    const int fmt = precision == CDS_PREC_TF32X3 ? FMT_TF32 : precision == CDS_PREC_BF16X3 ? 1 : 0;
     const int32_t nv = nmo - nocc;
     const int32_t Mp = padded(std::max(M, 1));
-    TcLayout lay = tc_layout(ws, nmo, nocc, M, np, nE);
+    TcLayout lay = tc_layout(ws, nmo, nocc, M, np, nE, fmt == FMT_TF32);
     int st = CDS_OK;
     if (resplit)
-        st = bf16 ? split_all<__nv_bfloat16>(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M, Mp,
-                                             lay, stream)
-                  : split_all<__half>(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M, Mp, lay,
-                                      stream);
+        st = fmt == FMT_TF32
+                 ? split_all_tf32(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M, Mp, lay, stream)
+             : fmt == 1 ? split_all<__nv_bfloat16>(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M,
+                                                   Mp, lay, stream)
+                        : split_all<__half>(Lp, Lov, (int64_t)np * nmo, (int64_t)nocc * nv, M, Mp,
+                                            lay, stream);
     if (st) return st;
     Params P{};
     Maps maps;
     memset(&maps, 0, sizeof(maps));
-    const uint64_t rowb = (uint64_t)Mp * 2;
+    const uint64_t ebytes = fmt == FMT_TF32 ? 4 : 2;
+    const uint64_t rowb = (uint64_t)Mp * ebytes;
     // term 0 (first sum of Eq. SE): x = occupied rows of Lp, bulk L^J_{a j}
     // read from Lov[j][a] with spectator a as map dim 1 and y = j as dim 2.
     // term 1 (second sum): x = virtual rows of Lp, bulk Lov[i][b], spectator i dim 2.
@@ -853,17 +921,17 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
     build_terms(nmo, nocc, np, P);
     for (int k = 0; k < 2; ++k) {
         if (P.term[k].nitems == 0) continue;
-        const uint16_t* qb_hi = lay.lp_hi + (k == 0 ? 0 : (size_t)nocc * Mp);
-        const uint16_t* qb_lo = lay.lp_lo + (k == 0 ? 0 : (size_t)nocc * Mp);
-        bool ok = make_map(&maps.m[k][0], bf16, qb_hi, Mp, nx[k], np, rowb, rowb * nmo, TB, 1) &&
-                  make_map(&maps.m[k][1], bf16, qb_lo, Mp, nx[k], np, rowb, rowb * nmo, TB, 1) &&
-                  make_map(&maps.m[k][2], bf16, lay.lov_hi, Mp, nv, nocc, rowb, rowb * nv,
+        const char* qb_hi = (const char*)lay.lp_hi + (k == 0 ? 0 : (size_t)nocc * rowb);
+        const char* qb_lo = (const char*)lay.lp_lo + (k == 0 ? 0 : (size_t)nocc * rowb);
+        bool ok = make_map(&maps.m[k][0], fmt, qb_hi, Mp, nx[k], np, rowb, rowb * nmo, TB, 1) &&
+                  make_map(&maps.m[k][1], fmt, qb_lo, Mp, nx[k], np, rowb, rowb * nmo, TB, 1) &&
+                  make_map(&maps.m[k][2], fmt, lay.lov_hi, Mp, nv, nocc, rowb, rowb * nv,
                            k == 0 ? 1 : TB, k == 0 ? TB : 1) &&
-                  make_map(&maps.m[k][3], bf16, lay.lov_lo, Mp, nv, nocc, rowb, rowb * nv,
+                  make_map(&maps.m[k][3], fmt, lay.lov_lo, Mp, nv, nocc, rowb, rowb * nv,
                            k == 0 ? 1 : TB, k == 0 ? TB : 1);
         if (!ok) return CDS_ERR_CUDA;
     }
-    P.kblocks = Mp / KB;
+    P.kblocks = fmt == FMT_TF32 ? Mp / (KB / 2) : Mp / KB;
     P.nE = nE;
     P.nmo = nmo;
     const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
@@ -884,8 +952,8 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
         if (split) P.nE_eval = kGridSplitE;
         const int nE_tc = split ? kGridSplitE : nE;   // picks the epilogue's energy chunk
         st = separate_accumulators()
-                 ? launch_any<true>(grid, bf16, nE_tc, maps, P, active, lay, stream, cache)
-                 : launch_any<false>(grid, bf16, nE_tc, maps, P, active, lay, stream, cache);
+                 ? launch_any<true>(grid, fmt, nE_tc, maps, P, active, lay, stream, cache)
+                 : launch_any<false>(grid, fmt, nE_tc, maps, P, active, lay, stream, cache);
         if (st) return st;
         if (split) {
             const int g2 = (int)std::min<int64_t>(nitems, (int64_t)device_sms() * 4);

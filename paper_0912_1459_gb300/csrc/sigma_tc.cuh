@@ -1,11 +1,13 @@
-// Tensor-core (tcgen05, 16-bit split-precision) path of the self-energy.
+// Tensor-core (tcgen05, split-precision BF16X3 / FP16X3 / TF32X3) path of the
+// self-energy.
 #pragma once
 
 #include "sigma.cuh"
 
 namespace cds {
 
-size_t tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE);
+size_t tc_workspace_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE,
+                          bool tf32 = false);
 
 // resplit = false reuses the 16-bit operand splits a previous call with the
 // same Lov, Lp and workspace left in ws (the Newton iterations of one solve).
@@ -22,6 +24,16 @@ size_t tc_cached_workspace_bytes(int32_t nmo, int32_t nocc, int32_t np);
 int sigma2_cached(int32_t nmo, int32_t nocc, int32_t np, const double* eps, const double* E,
                   const int32_t* active, const float* cache, double* sigma, double* dsigma,
                   void* ws, cudaStream_t stream, bool first);
+
+// FP64 form of the same: k_sigma_fp64 stores each 32 x 32 item's numerators
+// (fp64_cache_bytes) when given a cache, and sigma2_cached_fp64 evaluates
+// Sigma at one energy per orbital from them (workspace
+// fp64_cached_workspace_bytes).
+size_t fp64_cache_bytes(int32_t nmo, int32_t nocc, int32_t np);
+size_t fp64_cached_workspace_bytes(int32_t nmo, int32_t nocc, int32_t np);
+int sigma2_cached_fp64(int32_t nmo, int32_t nocc, int32_t np, const double* eps, const double* E,
+                       const int32_t* active, const double* cache, double* sigma, double* dsigma,
+                       double* part, cudaStream_t stream);
 
 // MP2 correlation energy (Eq. MP2) on the tensor-core kernel: e_pair[i] =
 // sum_{j,a,b}, e_total = sum_i e_pair[i] (either may be null).
@@ -58,6 +70,10 @@ int tune_newton_cache();   // CDS_TUNE_NEWTON_CACHE
 
 inline bool is_split16(int32_t precision) {
     return precision == CDS_PREC_BF16X3 || precision == CDS_PREC_FP16X3;
+}
+// Split precisions of the single-molecule self-energy (also TF32X3).
+inline bool is_split_tc(int32_t precision) {
+    return is_split16(precision) || precision == CDS_PREC_TF32X3;
 }
 
 size_t sigma_ws_bytes(int32_t nmo, int32_t nocc, int32_t M, int32_t np, int32_t nE,

@@ -101,7 +101,7 @@ def test_sigma_fp64_one_orbital_against_oracle(run):
     np.testing.assert_allclose(ds.cpu().numpy()[0], rds, rtol=1e-10, atol=0)
 
 
-@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp16x3", "bf16x3", "tf32x3"])
 def test_mixed_within_tenth_of_mev_full_size(run, prec):
     m, L, piv, D, de, Lov, Lp = run
     sel = [8, 9, 10, 11, 19]                  # around the gap: HOMO-1, HOMO, LUMO, LUMO+1, LUMO+9

@@ -29,7 +29,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3", "tf32x3"])
 @pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-5)])
 def test_cached_newton_matches_recompute_and_oracle(name, delta, prec):
     m = O.molecule(name)
@@ -121,3 +121,34 @@ def test_grid_from_cached_numerators(name, delta):
     torch.testing.assert_close(d1, d0, rtol=1e-5, atol=1e-8)
     s64, _ = G.cds_sigma2_diag(rov, rp, eps, m.nocc, E, "fp64")
     assert (s1 - s64).abs().max().item() <= 3.67e-6 + 1e-5 * s64.abs().max().item()
+
+
+@pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-5)])
+def test_fp64_cached_newton_equals_recomputing_fp64(name, delta):
+    """FP64 numerator cache: the grid pass equals cds_sigma2_diag (FP64) bit
+    for bit, and Newton from the cache (plain and safeguarded) reaches the
+    recomputing FP64 solvers' roots exactly (same per-element arithmetic and
+    order of sums at every energy), i.e. the oracle's within 1e-10 Ha."""
+    import workloads as W
+    m = O.molecule(name)
+    ref = O.decomposition(name, delta)
+    Lov, Lp = O.factors(name, ref.L)
+    rov, rp, eps, orbs = dev(Lov), dev(Lp), dev(m.eps), dev(m.orbitals)
+    E = dev(W.energy_grid(m.eps[m.orbitals], 8))
+    s0, d0 = G.cds_sigma2_diag(rov, rp, eps, m.nocc, E, "fp64")
+    s1, d1, cache = G.cds_sigma2_diag_cache(rov, rp, eps, m.nocc, E, "fp64")
+    assert torch.equal(s0, s1) and torch.equal(d0, d1)
+    w0, P0, it0, st0 = G.cds_qp_solve(rov, rp, orbs, eps, m.nocc, conv=1e-10, precision="fp64")
+    w1, P1, it1, st1 = G.cds_qp_solve_cached(cache, orbs, eps, m.nbf, m.nocc, conv=1e-10,
+                                             precision="fp64")
+    assert torch.equal(w0, w1) and torch.equal(P0, P1) and torch.equal(it0, it1)
+    assert torch.equal(st0, st1)
+    b0 = G.cds_qp_solve_bracketed(rov, rp, orbs, eps, m.nocc, conv=1e-10, precision="fp64")
+    b1 = G.cds_qp_solve_bracketed_cached(cache, orbs, eps, m.nbf, m.nocc, conv=1e-10,
+                                         precision="fp64")
+    for a, b in zip(b0, b1):
+        assert torch.equal(a, b)
+    res = O.solve(name, Lov, Lp, m.orbitals, conv=1e-10)
+    for t, (w, P, it, st) in enumerate(res):
+        if st == 0:
+            assert abs(float(w1[t]) - w) <= 1e-10

@@ -1,4 +1,4 @@
-"""Split-precision (BF16X3 / FP16X3, tcgen05) self-energy and Newton solve vs the FP64 oracle.
+"""Split-precision (BF16X3 / FP16X3 / TF32X3, tcgen05) self-energy and Newton solve vs the FP64 oracle.
 
 Bar: quasiparticle energies within 0.1 meV = 3.67e-6 Ha of the
 FP64 oracle.  Sigma on the energy grid: |dSigma| <= 3.67e-6 Ha + 1e-5 |Sigma|
@@ -30,7 +30,7 @@ def dev(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3", "tf32x3"])
 @pytest.mark.parametrize("name,delta,nE", [("c0", 1e-6, 16), ("c0", 1e-6, 1), ("c1", 1e-5, 16),
                                           ("c1", 1e-5, 5)])
 def test_sigma_split_vs_oracle(name, delta, nE, prec):
@@ -48,7 +48,7 @@ def test_sigma_split_vs_oracle(name, delta, nE, prec):
     assert np.all(np.abs(ds - rds) <= 1e-5 * (1 + np.abs(rds)))
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3", "tf32x3"])
 def test_sigma_split_matches_fp64_gpu_path(prec):
     m = O.molecule("c1")
     ref = O.decomposition("c1", 1e-5)
@@ -59,7 +59,7 @@ def test_sigma_split_matches_fp64_gpu_path(prec):
     assert np.abs(a.cpu().numpy() - b.cpu().numpy()).max() <= TOL_QP
 
 
-@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3"])
+@pytest.mark.parametrize("prec", ["bf16x3", "fp16x3", "tf32x3"])
 @pytest.mark.parametrize("name,delta", [("c0", 1e-6), ("c1", 1e-5)])
 def test_qp_split_within_tenth_of_mev(name, delta, prec):
     m = O.molecule(name)
