@@ -143,8 +143,9 @@ size_t cds_cd_workspace_bytes(int32_t nbf);
  * per step, with the vectors held as float pairs while the decomposition runs;
  * integral columns, L^k, the residual diagonal and the pivot search stay FP64;
  * L is returned in FP64 either way).  F32X2 also speculates: one streaming
- * pass forms the projections of the step's pivot and of three likely next
- * pivots (the largest residuals of other blocks), and the following steps
+ * pass forms the projections of the step's pivot and of a few likely next
+ * pivots (the largest residuals of other blocks; cds_cd_candidates() in all),
+ * and the following steps
  * whose pivots are among them reuse those projections plus the few vectors
  * made since.  The pivot rule and the result are those of the plain
  * algorithm; only the grouping of each sum differs (see cds_cd_stats).
@@ -168,11 +169,16 @@ int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
  * streamed the stored vectors, streamed = vectors read by those passes in
  * total, extra = vectors added to a candidate projection by the steps in
  * between (F32X2 speculative projections: a pass forms the projections of
- * the pivot and of three likely next pivots; a later step whose pivot is
+ * the pivot and of a few likely next pivots; a later step whose pivot is
  * among them adds only the vectors made since).  FP64 streams at every step:
  * passes = M, streamed = M(M-1)/2, extra = 0. */
 int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precision, int32_t* passes,
                  int64_t* streamed, int64_t* extra, cudaStream_t stream);
+
+/* Candidate pivots whose projections one F32X2 streaming pass forms (host
+ * only; a later step continues the pass while its pivot is among them and
+ * fewer than that many steps have passed since). */
+int cds_cd_candidates(void);
 
 /* ------------------------------------------------------------------------
  * Allocation-free Cholesky decomposition.  The paper has no counterpart: this

@@ -45,6 +45,7 @@ _SIGNATURES = {
                                                _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f64),
                                                _vp]),
     "cds_cd_static_max_nbf": (ctypes.c_int, []),
+    "cds_cd_candidates": (ctypes.c_int, []),
     "cds_cd_to_mo_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "cds_cd_to_mo": (ctypes.c_int, [_i32, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _i32, _vp, _vp,
                                     _vp, _sz, _vp]),
@@ -352,6 +353,11 @@ def cds_cd_stats(nbf: int, workspace: torch.Tensor, precision: str = "fp64") -> 
                             ctypes.byref(st_), ctypes.byref(ex), _stream(workspace.device)),
            "cds_cd_stats")
     return {"passes": p.value, "streamed": st_.value, "extra": ex.value}
+
+
+def cd_candidates() -> int:
+    """Candidate pivots per speculative (F32X2) streaming pass."""
+    return int(load().cds_cd_candidates())
 
 
 def cds_cd_decompose_static(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,

@@ -46,7 +46,7 @@ constexpr int kHostCheckEvery = 32;
 #endif
 constexpr int kSpec = CDS_KSPEC;          // candidate pivots per speculative projection pass
 constexpr int kSpecRows = CDS_KSPEC_ROWS; // rows of L in flight per thread and iteration
-constexpr int kSpecChunk = 1024;  // pivot columns staged per shared-memory chunk
+constexpr int kSpecChunk = 4096 / kSpec;   // pivot columns staged per shared-memory chunk (32 KB)
 
 struct CdCtrl {
     double scale;      // max initial diagonal (all pairs)
@@ -384,7 +384,7 @@ __device__ __forceinline__ void cd_dot_body(int64_t n, int32_t k, double* __rest
 // the set, or a full batch, starts the next batch.  The sums are the same as
 // the plain left-looking ones, grouped differently.  Tile layout as
 // cd_dot_body, with kSpec accumulators per pair instead of four partial sums.
-static_assert(kSpec * kUpdPairs <= kUpdThreads, "one (candidate, pair) output per thread");
+static_assert(kUpdWarps * kUpdPairs <= kSpecChunk, "warp partials fit the staging buffer");
 __device__ __forceinline__ void cd_spec_dot_body(int64_t n, int32_t k,
                                                  const double* __restrict__ L,
                                                  float2* __restrict__ G, const CdCtrl* ctrl,
@@ -449,13 +449,15 @@ __device__ __forceinline__ void cd_spec_dot_body(int64_t n, int32_t k,
 #pragma unroll
         for (int c = 0; c < kSpec; ++c) red[w][c][lane + 32 * r] = acc[r][c];
     __syncthreads();
-    const int c = threadIdx.x / kUpdPairs, pp = threadIdx.x - c * kUpdPairs;
-    const int64_t I = base + pp;
-    if (c < kSpec && I < n) {
-        float2 sum = red[0][c][pp];
+    for (int idx = threadIdx.x; idx < kSpec * kUpdPairs; idx += blockDim.x) {
+        const int c = idx / kUpdPairs, pp = idx - c * kUpdPairs;
+        const int64_t I = base + pp;
+        if (I < n) {
+            float2 sum = red[0][c][pp];
 #pragma unroll
-        for (int v = 1; v < kUpdWarps; ++v) sum = df_add(sum, red[v][c][pp]);
-        G[(int64_t)c * n + I] = sum;
+            for (int v = 1; v < kUpdWarps; ++v) sum = df_add(sum, red[v][c][pp]);
+            G[(int64_t)c * n + I] = sum;
+        }
     }
     __syncthreads();   // red aliases lp, which the next tile restages
 }
@@ -841,6 +843,8 @@ using namespace cds;
 
 // Enough for either precision.
 extern "C" size_t cds_cd_workspace_bytes(int32_t nbf) { return cd_workspace_bytes_for(nbf, true); }
+
+extern "C" int cds_cd_candidates(void) { return kSpec; }
 
 extern "C" int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precision,
                             int32_t* passes, int64_t* streamed, int64_t* extra,
