@@ -149,6 +149,17 @@ size_t cds_cd_workspace_bytes(int32_t nbf);
  * whose pivots are among them reuse those projections plus the few vectors
  * made since.  The pivot rule and the result are those of the plain
  * algorithm; only the grouping of each sum differs (see cds_cd_stats).
+ * CDS_PREC_OZAKI: the F32X2 decomposition whose streaming passes run on the
+ * tcgen05 tensor cores for 32 candidates at once (a pass serves up to 64
+ * steps): each stored element is also kept as a 56-bit fixed-point number
+ * below its pair's power-of-two scale (> sqrt of the initial diagonal), in
+ * eight exact BF16 slices of 7 bits, and the pass multiplies these slices
+ * with exact products and exact FP32 sums (36 slice pairs; nbf up to ~1440,
+ * the candidate search holding the block maxima in shared memory); the steps
+ * in between add the vectors made since in float pairs.  The pivot sequence
+ * is the FP64 one (tested at C60 size).  Its workspace is
+ * cds_cd_workspace_bytes_prec (the slice store takes 16 bytes per pair and
+ * vector of max_rank).
  * Inputs (device): xyz, alpha, atom.  Outputs (device, caller-owned):
  *   L     [max_rank][npair] fp64, rows 0..M-1 written;
  *   piv   [max_rank] int32 packed pivot index of each vector;
@@ -175,10 +186,16 @@ int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
 int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precision, int32_t* passes,
                  int64_t* streamed, int64_t* extra, cudaStream_t stream);
 
-/* Candidate pivots whose projections one F32X2 streaming pass forms (host
- * only; a later step continues the pass while its pivot is among them and
- * fewer than that many steps have passed since). */
-int cds_cd_candidates(void);
+/* Candidate pivots whose projections one streaming pass of the given
+ * precision forms (host only; a later step continues the pass while its
+ * pivot is among them and the pass is not full -- 4 steps for F32X2, 64 for
+ * OZAKI): 4 for F32X2, 32 for OZAKI, 1 for FP64 (every step streams). */
+int cds_cd_candidates(int32_t precision);
+
+/* Workspace of cds_cd_decompose for one precision and max_rank (OZAKI holds a
+ * slice store of max_rank columns; cds_cd_workspace_bytes covers FP64 and
+ * F32X2 for any max_rank). */
+size_t cds_cd_workspace_bytes_prec(int32_t nbf, int32_t max_rank, int32_t precision);
 
 /* ------------------------------------------------------------------------
  * Allocation-free Cholesky decomposition.  The paper has no counterpart: this
@@ -272,9 +289,10 @@ int cds_ri_factors(int32_t nbf, const double* xyz, const double* alpha, const in
                    size_t workspace_bytes, cudaStream_t stream);
 
 /* ------------------------------------------------------------------------
- * Decomposition and transform in one call.  Runs cds_cd_decompose(F32X2) and
- * cds_cd_to_mo(tr_precision: CDS_PREC_F32X2, CDS_PREC_TF32X3, CDS_PREC_BF16X3
- * or CDS_PREC_OZAKI) with the transform of each batch of 32 finished vectors
+ * Decomposition and transform in one call.  Runs cds_cd_decompose
+ * (cd_precision: CDS_PREC_F32X2 or CDS_PREC_OZAKI) and cds_cd_to_mo
+ * (tr_precision: CDS_PREC_F32X2, CDS_PREC_TF32X3, CDS_PREC_BF16X3 or
+ * CDS_PREC_OZAKI) with the transform of each batch of 32 finished vectors
  * overlapped with the decomposition of the next ones, on two library streams
  * (the decomposition's at the highest priority), joined to `stream` on
  * return.  The results are those of the two calls in sequence.
@@ -286,11 +304,12 @@ int cds_ri_factors(int32_t nbf, const double* xyz, const double* alpha, const in
  * Blocking, like cds_cd_decompose.
  * ---------------------------------------------------------------------- */
 size_t cds_cd_decompose_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc,
-                                              int32_t max_rank, int32_t np);
+                                              int32_t max_rank, int32_t np, int32_t cd_precision);
 int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const double* alpha,
                            const int32_t* atom, double delta, int32_t scheme, int32_t max_rank,
                            const double* C, int32_t nmo, int32_t nocc, const int32_t* orb,
-                           int32_t np, int32_t tr_precision, double* L, int32_t* piv, double* D,
+                           int32_t np, int32_t tr_precision, int32_t cd_precision, double* L,
+                           int32_t* piv, double* D,
                            int32_t* M_out,
                            double* delta_eff_out, double* Lov, double* Lp, void* workspace,
                            size_t workspace_bytes, cudaStream_t stream);

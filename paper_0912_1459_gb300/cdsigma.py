@@ -45,7 +45,8 @@ _SIGNATURES = {
                                                _vp, ctypes.POINTER(_i32), ctypes.POINTER(_f64),
                                                _vp]),
     "cds_cd_static_max_nbf": (ctypes.c_int, []),
-    "cds_cd_candidates": (ctypes.c_int, []),
+    "cds_cd_candidates": (ctypes.c_int, [_i32]),
+    "cds_cd_workspace_bytes_prec": (_sz, [_i32, _i32, _i32]),
     "cds_cd_to_mo_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "cds_cd_to_mo": (ctypes.c_int, [_i32, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _i32, _vp, _vp,
                                     _vp, _sz, _vp]),
@@ -57,9 +58,9 @@ _SIGNATURES = {
                                     _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "cds_cd_stats": (ctypes.c_int, [_i32, _vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64), _vp]),
-    "cds_cd_decompose_to_mo_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
+    "cds_cd_decompose_to_mo_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32, _i32]),
     "cds_cd_decompose_to_mo": (ctypes.c_int, [_i32, _vp, _vp, _vp, _f64, _i32, _i32, _vp, _i32, _i32,
-                                              _vp, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32),
+                                              _vp, _i32, _i32, _i32, _vp, _vp, _vp, ctypes.POINTER(_i32),
                                               ctypes.POINTER(_f64), _vp, _vp, _vp, _sz, _vp]),
     "cds_acd_workspace_bytes": (_sz, [_i32]),
     "cds_acd_aux_pairs": (ctypes.c_int, [_i32, _vp, _vp, _f64, _vp, _i32, ctypes.POINTER(_i32), _vp,
@@ -235,7 +236,7 @@ def cds_cd_decompose(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,
         raise ValueError("L_out must be a contiguous [max_rank, npair] float64 tensor")
     piv = torch.empty(max(max_rank, 1), dtype=torch.int32, device=dev)
     D = torch.empty(npr, dtype=torch.float64, device=dev)
-    need = lib.cds_cd_workspace_bytes(n)
+    need = lib.cds_cd_workspace_bytes_prec(n, int(max_rank), PRECISIONS[precision])
     if workspace is None or workspace.numel() < need:
         workspace = _workspace(need, dev)
     M = _i32(0)
@@ -255,12 +256,14 @@ def cds_cd_decompose_to_mo(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.T
                            Lov_out: Optional[torch.Tensor] = None,
                            Lp_out: Optional[torch.Tensor] = None,
                            workspace: Optional[torch.Tensor] = None,
-                           transform: str = "f32x2"):
+                           transform: str = "f32x2", cd_precision: str = "f32x2"):
     """Float-pair decomposition and transform in one pipelined call.
 
     transform: the transform's precision, "f32x2" (float pairs on the FP32
     units), "ozaki" (exact-slice tensor-core GEMMs), "tf32x3" or "bf16x3"
     (split-precision tensor-core GEMMs, for well-conditioned C only).
+    cd_precision: "f32x2" (speculative float-pair passes) or "ozaki" (the
+    passes on the tensor cores, 64 candidates).
 
     Returns (L [M, npair], piv [M], D, delta_eff, Lov [o, v, M], Lp [np, nmo, M])."""
     lib = load()
@@ -287,13 +290,15 @@ def cds_cd_decompose_to_mo(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.T
         Lp_out = torch.empty(max(np_ * nmo * max_rank, 1), dtype=torch.float64, device=dev)
     piv = torch.empty(max(max_rank, 1), dtype=torch.int32, device=dev)
     D = torch.empty(npr, dtype=torch.float64, device=dev)
-    need = lib.cds_cd_decompose_to_mo_workspace_bytes(n, nmo, nocc, max_rank, np_)
+    need = lib.cds_cd_decompose_to_mo_workspace_bytes(n, nmo, nocc, max_rank, np_,
+                                                      PRECISIONS[cd_precision])
     if workspace is None or workspace.numel() < need:
         workspace = _workspace(need, dev)
     M, de = _i32(0), _f64(0.0)
     st = lib.cds_cd_decompose_to_mo(n, _p(xyz), _p(alpha), _p(atom), float(delta),
                                     SCHEMES[scheme], int(max_rank), _p(C), nmo, nocc, _p(orb),
-                                    np_, PRECISIONS[transform], _p(L_out), _p(piv), _p(D), ctypes.byref(M),
+                                    np_, PRECISIONS[transform], PRECISIONS[cd_precision], _p(L_out),
+                                    _p(piv), _p(D), ctypes.byref(M),
                                     ctypes.byref(de), _p(Lov_out), _p(Lp_out), _p(workspace),
                                     workspace.numel(), _stream(dev))
     _check(st, "cds_cd_decompose_to_mo")
@@ -355,9 +360,9 @@ def cds_cd_stats(nbf: int, workspace: torch.Tensor, precision: str = "fp64") -> 
     return {"passes": p.value, "streamed": st_.value, "extra": ex.value}
 
 
-def cd_candidates() -> int:
-    """Candidate pivots per speculative (F32X2) streaming pass."""
-    return int(load().cds_cd_candidates())
+def cd_candidates(precision: str = "f32x2") -> int:
+    """Candidate pivots per streaming pass of the decomposition's precision."""
+    return int(load().cds_cd_candidates(PRECISIONS[precision]))
 
 
 def cds_cd_decompose_static(xyz: torch.Tensor, alpha: torch.Tensor, atom: torch.Tensor,

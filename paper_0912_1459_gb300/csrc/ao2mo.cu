@@ -698,9 +698,9 @@ struct FusedLayout {
 };
 
 FusedLayout fused_layout(void* ws, int32_t nbf, int32_t nmo, int32_t nocc, int32_t max_rank,
-                         int32_t np) {
+                         int32_t np, int32_t cd_precision) {
     FusedLayout l;
-    l.cd_bytes = cd_workspace_bytes_for(nbf, true);
+    l.cd_bytes = cd_workspace_bytes_prec(nbf, max_rank, cd_precision);
     Carver c(ws);
     l.cd = c.take<char>(l.cd_bytes);
     const size_t ao_bytes = std::max(ao_layout(nullptr, nbf, nmo, nocc, np).bytes,
@@ -718,17 +718,19 @@ FusedLayout fused_layout(void* ws, int32_t nbf, int32_t nmo, int32_t nocc, int32
 }  // namespace cds
 
 extern "C" size_t cds_cd_decompose_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc,
-                                                         int32_t max_rank, int32_t np) {
+                                                         int32_t max_rank, int32_t np,
+                                                         int32_t cd_precision) {
     if (nbf <= 0 || nmo <= 0 || nmo > nbf || nocc < 0 || nocc > nmo || max_rank < 0 || np < 0)
         return 0;
-    return fused_layout(nullptr, nbf, nmo, nocc, max_rank, np).bytes;
+    if (cd_precision != CDS_PREC_F32X2 && cd_precision != CDS_PREC_OZAKI) return 0;
+    return fused_layout(nullptr, nbf, nmo, nocc, max_rank, np, cd_precision).bytes;
 }
 
 extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const double* alpha,
                                       const int32_t* atom, double delta, int32_t scheme,
                                       int32_t max_rank, const double* C, int32_t nmo,
                                       int32_t nocc, const int32_t* orb, int32_t np,
-                                      int32_t tr_precision, double* L,
+                                      int32_t tr_precision, int32_t cd_precision, double* L,
                                       int32_t* piv, double* D, int32_t* M_out,
                                       double* delta_eff_out, double* Lov, double* Lp,
                                       void* workspace, size_t workspace_bytes,
@@ -737,8 +739,9 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
         return CDS_ERR_ARG;
     if (!C || !Lov || !M_out || (np > 0 && (!orb || !Lp))) return CDS_ERR_ARG;
     if (tr_precision != CDS_PREC_F32X2 && !is_tr_tc(tr_precision)) return CDS_ERR_UNSUPPORTED;
+    if (cd_precision != CDS_PREC_F32X2 && cd_precision != CDS_PREC_OZAKI) return CDS_ERR_UNSUPPORTED;
     const bool tcx = is_tr_tc(tr_precision);
-    FusedLayout lay = fused_layout(workspace, nbf, nmo, nocc, max_rank, np);
+    FusedLayout lay = fused_layout(workspace, nbf, nmo, nocc, max_rank, np, cd_precision);
     if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
     PipeStreams ps;
     int st = pipeline_streams(&ps);
@@ -767,7 +770,7 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
     };
     int32_t M = 0;
     const int cd_st = cd_decompose_run(nbf, xyz, alpha, atom, delta, scheme, max_rank,
-                                       CDS_PREC_F32X2, L, piv, D, &M, delta_eff_out, lay.cd,
+                                       cd_precision, L, piv, D, &M, delta_eff_out, lay.cd,
                                        lay.cd_bytes, ps.cd, &hook, ps.tr);
     *M_out = M;
     const int32_t nv = nmo - nocc;

@@ -19,58 +19,17 @@
 // All kernels read a device control block and return at once after the
 // decomposition has stopped, so the host enqueues steps ahead and checks the
 // control block only every few steps.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <vector>
 
 #include "common.cuh"
+#include "cd.cuh"
 #include "eri_col.cuh"
 #include "sigma_tc.cuh"
 
 namespace cds {
-
-constexpr int kCdThreads = 128;
-constexpr int kUpdWarps = 8;                  // k_cd_update: warps splitting the K sum
-constexpr int kUpdThreads = 32 * kUpdWarps;
-constexpr int kUpdPairs = 64;                 // k_cd_project: pairs per projection tile
-constexpr int kStepPer = 2;                   // k_cd_update: pairs per thread
-constexpr int kStepChunk = kStepPer * kUpdThreads;   // k_cd_update: contiguous pairs per block
-constexpr int kCdChunk = 2048;   // pivot row L^K_P staged in shared memory in chunks
-constexpr double kTieRel = 1e-12;
-constexpr double kNotPdRel = 1e-10;
-constexpr int kHostCheckEvery = 32;
-#ifndef CDS_KSPEC
-#define CDS_KSPEC 4
-#endif
-#ifndef CDS_KSPEC_ROWS
-#define CDS_KSPEC_ROWS 4
-#endif
-constexpr int kSpec = CDS_KSPEC;          // candidate pivots per speculative projection pass
-constexpr int kSpecRows = CDS_KSPEC_ROWS; // rows of L in flight per thread and iteration
-constexpr int kSpecChunk = 4096 / kSpec;   // pivot columns staged per shared-memory chunk (32 KB)
-
-struct CdCtrl {
-    double scale;      // max initial diagonal (all pairs)
-    double delta_eff;  // max(delta, npair * 2^-52 * scale)
-    double G;          // max candidate residual after the last update
-    double Dmin;       // min residual after the last update
-    double DP;         // residual of the current pivot
-    double rDP;        // 1 / sqrt(DP)
-    float2 rDPf;       // the same as a float pair
-    int64_t P;         // current pivot
-    int32_t done;      // decomposition stopped
-    int32_t status;    // cds_status
-    int32_t M;         // vectors produced
-    int32_t _pad;
-    unsigned int counter;  // last-block-done counter
-    unsigned int _pad2;
-    // speculative projections (float-pair mode): the pivots of the current
-    // batch's candidate set, the batch's first step, the slot of the current
-    // pivot in the set, and whether this step streams L (a new batch)
-    long long S[kSpec];
-    int32_t k0, slot, pass, passes;     // passes: batches started (streaming passes)
-    long long streamed;                  // sum over passes of the vectors streamed (k0)
-    long long extra;                     // sum over continued steps of the vectors added (k - k0)
-};
 
 __device__ __forceinline__ double warp_max(double v) {
     for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -239,6 +198,8 @@ __device__ void cd_select_body(int64_t n, int32_t k, int32_t max_rank,
                 piv[k] = (int32_t)m;
                 ctrl->S[0] = m;
                 for (int i = 1; i < kSpec; ++i) ctrl->S[i] = -1;
+                ctrl->STc[0] = m;
+                for (int i = 1; i < kSpecTC; ++i) ctrl->STc[i] = -1;
                 ctrl->k0 = k;
                 ctrl->slot = 0;
                 ctrl->pass = 1;
@@ -462,6 +423,65 @@ __device__ __forceinline__ void cd_spec_dot_body(int64_t n, int32_t k,
     __syncthreads();   // red aliases lp, which the next tile restages
 }
 
+// ---------------------------------------------------------------------------
+// Exact-slice tensor-core form (CDS_PREC_OZAKI).  Every stored element L^K_I
+// is kept, besides its float pair in L, as a 56-bit fixed-point number below
+// the pair's scale sigma_I = 2^e_I > sqrt(D0_I) >= |L^K_I| (the residual
+// matrix stays positive semidefinite, so sum_K (L^K_I)^2 <= D0_I), cut into
+// eight 7-bit digits held as exact BF16 slices in a K-major store
+// [slice][pair][kcap]; a streaming pass multiplies the store with the
+// candidates' rows on the tensor cores (cd_tc.cu).
+// ---------------------------------------------------------------------------
+__global__ void k_cd_tc_scales(const double* __restrict__ D, int64_t n, float* __restrict__ sig) {
+    const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (I >= n) return;
+    const double r = sqrt(fmax(D[I], 0.0));
+    int e = 0;
+    if (r > 0.0) frexp(r, &e);   // r = f 2^e, f in [0.5, 1): r < 2^e
+    sig[I] = ldexpf(1.f, e);
+}
+
+// The digit slices of x / sigma (sigma = 2^e > |x|), x a float pair:
+// q = trunc(x 2^(Q-e)) (|q| < 2^Q, Q = 56 bits), digit s = bits
+// [Q-7(s+1), Q-7s) of |q|, slice s = sign(x) digit 2^(-7(s+1)) (exact in BF16).
+__device__ __forceinline__ void tc_slices(float2 x, int e, uint16_t (&out)[kSlicesTC]) {
+    constexpr int QB = kSlicesTC * kBitsTC;
+    long long q = __float2ll_rz(ldexpf(x.x, QB - e)) + __float2ll_rz(ldexpf(x.y, QB - e));
+    const long long qmax = (1LL << QB) - 1;
+    q = q > qmax ? qmax : (q < -qmax ? -qmax : q);
+    const bool neg = q < 0;
+    const unsigned long long aq = (unsigned long long)(neg ? -q : q);
+#pragma unroll
+    for (int s = 0; s < kSlicesTC; ++s) {
+        const int d = (int)((aq >> (QB - kBitsTC * (s + 1))) & ((1ull << kBitsTC) - 1));
+        out[s] = __bfloat16_as_ushort(__float2bfloat16_rn(ldexpf((float)(neg ? -d : d),
+                                                                 -kBitsTC * (s + 1))));
+    }
+}
+
+// Eight consecutive columns K0.. K0+7 (zero at K >= k) of one row of L, sliced
+// with exponent e, stored as one 16-byte segment per slice plane.
+__device__ __forceinline__ void tc_store8(const float2* __restrict__ Lf, int64_t n, int64_t I,
+                                          int32_t K0, int32_t k, int e,
+                                          __nv_bfloat16* __restrict__ planes, int64_t plane,
+                                          int64_t off) {
+    uint32_t w[kSlicesTC][4];
+#pragma unroll
+    for (int j = 0; j < 8; j += 2) {
+        uint16_t d0[kSlicesTC], d1[kSlicesTC];
+        const float2 v0 = (I >= 0 && K0 + j < k) ? Lf[(int64_t)(K0 + j) * n + I] : make_float2(0.f, 0.f);
+        const float2 v1 = (I >= 0 && K0 + j + 1 < k) ? Lf[(int64_t)(K0 + j + 1) * n + I]
+                                                     : make_float2(0.f, 0.f);
+        tc_slices(v0, e, d0);
+        tc_slices(v1, e, d1);
+#pragma unroll
+        for (int s = 0; s < kSlicesTC; ++s) w[s][j / 2] = (uint32_t)d0[s] | ((uint32_t)d1[s] << 16);
+    }
+#pragma unroll
+    for (int s = 0; s < kSlicesTC; ++s)
+        *reinterpret_cast<uint4*>(planes + s * plane + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+}
+
 // Order-preserving map of binary64 values to int64 (its own inverse), so the
 // residual extrema reduce on the integer units instead of the narrow FP64 pipe.
 __device__ __forceinline__ long long key_of(double d) {
@@ -515,7 +535,7 @@ __device__ long long block_min_ll(long long v) {
 // passes without any entry passing, possible only when the band reaches below
 // delta_eff, moves the search to the next such block).  DF: proj and L^k are
 // (hi, lo) float pairs.
-template <bool DF, bool SPEC>
+template <bool DF, bool SPEC, bool TC = false>
 __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_rank,
                                              double* __restrict__ L, double* __restrict__ D,
                                              const uint8_t* __restrict__ cand,
@@ -527,6 +547,7 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
                                              int32_t* __restrict__ piv, CdCtrl* ctrl, int bid,
                                              int nblk) {
     static_assert(!SPEC || DF, "speculative projections are a float-pair mode");
+    static_assert(!TC || SPEC, "the tensor-core form is a speculative form");
     const int64_t P = ctrl->P;
     const double rDP = ctrl->rDP;
     const float2 rDPf = ctrl->rDPf;
@@ -536,14 +557,20 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
     int32_t k0 = 0, extra = 0;
     const float2* Gs = Gp;
     float2 lpP[kSpec - 1];
+    __shared__ float2 s_lp[TC ? kBatchTC : 1];   // TC: pivot values of the vectors since the pass
     if constexpr (SPEC) {
         k0 = ctrl->k0;
         extra = k - k0;
         Gs = Gp + (int64_t)ctrl->slot * n;
         const float2* Lf = reinterpret_cast<const float2*>(L);
+        if constexpr (TC) {
+            for (int i = threadIdx.x; i < extra; i += blockDim.x) s_lp[i] = Lf[(int64_t)(k0 + i) * n + P];
+            __syncthreads();
+        } else {
 #pragma unroll
-        for (int i = 0; i < kSpec - 1; ++i)
-            lpP[i] = i < extra ? Lf[(int64_t)(k0 + i) * n + P] : make_float2(0.f, 0.f);
+            for (int i = 0; i < kSpec - 1; ++i)
+                lpP[i] = i < extra ? Lf[(int64_t)(k0 + i) * n + P] : make_float2(0.f, 0.f);
+        }
     }
     long long mx_i = LLONG_MAX;   // SPEC: lowest index holding the block's candidate maximum
 #pragma unroll
@@ -554,11 +581,17 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
             double d;
             if constexpr (SPEC) {
                 // everything but the residual in float pairs (column, projection, L^k)
-                float2 acc = Gs[I];
                 const float2* Lf = reinterpret_cast<const float2*>(L);
+                float2 acc;
+                if constexpr (TC) {
+                    acc = k0 > 0 ? Gs[I] : make_float2(0.f, 0.f);   // nothing precedes step 0
+                    for (int i = 0; i < extra; ++i) df_fma(acc, Lf[(int64_t)(k0 + i) * n + I], s_lp[i]);
+                } else {
+                    acc = Gs[I];
 #pragma unroll
-                for (int i = 0; i < kSpec - 1; ++i)
-                    if (i < extra) df_fma(acc, Lf[(int64_t)(k0 + i) * n + I], lpP[i]);
+                    for (int i = 0; i < kSpec - 1; ++i)
+                        if (i < extra) df_fma(acc, Lf[(int64_t)(k0 + i) * n + I], lpP[i]);
+                }
                 const float2 e = reinterpret_cast<const float2*>(ecol)[I];
                 const float2 lf = df_mul(df_add(e, df_neg(acc)), rDPf);
                 *reinterpret_cast<float2*>(slot) = lf;
@@ -652,19 +685,48 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
     // SPEC: does step k+1 continue the batch (its pivot is in the candidate
     // set and the batch is not full), or start a new one?  A new set holds the
     // pivot and the maxima of the blocks with the largest residuals.
-    __shared__ long long s_spec[kSpec];
+    // TC: 32 candidates, a batch of up to 64 steps; the block maxima are held
+    // in shared memory while the candidates are taken in order.
+    constexpr int NS = TC ? kSpecTC : kSpec;
+    constexpr int NB = TC ? kBatchTC : kSpec;
+    __shared__ long long s_spec[NS];
     __shared__ int s_hit;
     if constexpr (SPEC) {
         if (!stop) {
+            const long long* Sset = TC ? ctrl->STc : ctrl->S;
             if (threadIdx.x == 0) {
                 s_hit = -1;
-                if (made - ctrl->k0 < kSpec)
-                    for (int c = 0; c < kSpec; ++c)
-                        if (ctrl->S[c] == pick) s_hit = c;
+                if (made - ctrl->k0 < NB)
+                    for (int c = 0; c < NS; ++c)
+                        if (Sset[c] == pick) s_hit = c;
                 s_spec[0] = pick;
             }
             __syncthreads();
-            if (s_hit < 0) {
+            if (s_hit < 0 && TC) {
+                __shared__ long long s_key[TC ? kMaxBlocksTC : 1], s_idx[TC ? kMaxBlocksTC : 1];
+                const long long de_key = __double_as_longlong(de);
+                for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+                    const long long key = __ldcg(blk_a + i), idx = __ldcg(blk_i + i);
+                    s_key[i] = (idx >= 0 && idx != pick && key > de_key) ? key : -1;
+                    s_idx[i] = idx;
+                }
+                __syncthreads();
+                for (int c = 1; c < NS; ++c) {
+                    long long best = -1, dummy = LLONG_MAX;
+                    for (int i = threadIdx.x; i < nblk; i += blockDim.x) best = max(best, s_key[i]);
+                    block_maxmin_ll(best, dummy);
+                    long long first = LLONG_MAX;
+                    if (best >= 0)
+                        for (int i = threadIdx.x; i < nblk; i += blockDim.x)
+                            if (s_key[i] == best) first = min(first, (long long)i);
+                    first = block_min_ll(first);
+                    if (threadIdx.x == 0) {
+                        s_spec[c] = first == LLONG_MAX ? -1 : s_idx[first];
+                        if (first != LLONG_MAX) s_key[first] = -1;
+                    }
+                    __syncthreads();
+                }
+            } else if (s_hit < 0) {
                 const long long de_key = __double_as_longlong(de);
                 for (int c = 1; c < kSpec; ++c) {
                     long long best = -1, dummy = LLONG_MAX;
@@ -711,7 +773,13 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
                     ctrl->pass = 0;
                     ctrl->extra += made - ctrl->k0;
                 } else {
-                    for (int c = 0; c < kSpec; ++c) ctrl->S[c] = s_spec[c];
+                    if constexpr (TC) {
+                        // the store's complete column groups after the last pass
+                        ctrl->kdone = (ctrl->k0 / kGroupTC) * kGroupTC;
+                        for (int c = 0; c < kSpecTC; ++c) ctrl->STc[c] = s_spec[c];
+                    } else {
+                        for (int c = 0; c < kSpec; ++c) ctrl->S[c] = s_spec[c];
+                    }
                     ctrl->k0 = made;
                     ctrl->slot = 0;
                     ctrl->pass = 1;
@@ -750,8 +818,54 @@ k_cd_project_spec(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __r
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) cd_spec_dot_body(n, k, L, G, ctrl, t);
 }
 
+// Step k, part 1 of the exact-slice tensor-core form: every block takes its
+// share of the integral column; when step k starts a pass, the blocks then
+// bring the slice store up to date (column groups [kdone, k rounded up),
+// zero at K >= k) and slice the candidates' rows [0, k) into the B planes,
+// for the projection GEMM that follows.
+__global__ void __launch_bounds__(kUpdThreads, 4)
+k_cd_project_tc(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __restrict__ L,
+                float2* __restrict__ ecol, const float* __restrict__ sigA,
+                __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B,
+                float* __restrict__ sigB, int32_t kcap, const CdCtrl* ctrl) {
+    if (ctrl->done) return;
+    cd_eri_body_df(pd, pf, n, ctrl, ecol, blockIdx.x, gridDim.x);
+    if (ctrl->pass == 0 || k == 0) return;
+    const float2* Lf = reinterpret_cast<const float2*>(L);
+    const int32_t kd = ctrl->kdone;
+    const int32_t kend = (k + kGroupTC - 1) / kGroupTC * kGroupTC;
+    const int64_t planeA = n * (int64_t)kcap, planeB = (int64_t)kSpecTC * kcap;
+    const int q8 = kGroupTC / 8;   // 16-byte segments per group and plane
+    // A: items (group, pair, segment), segment fastest, so a warp writes whole rows
+    const int64_t itemsA = (int64_t)((kend - kd) / kGroupTC) * n * q8;
+    const int64_t itemsB = (int64_t)kSpecTC * (kend / 8);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < itemsA + itemsB;
+         it += stride) {
+        if (it < itemsA) {
+            const int seg = (int)(it % q8);
+            const int64_t r = it / q8;
+            const int64_t I = r % n;
+            const int32_t K0 = kd + (int32_t)(r / n) * kGroupTC + seg * 8;
+            int e = 0;
+            frexpf(sigA[I], &e);   // sigma = 2^(e-1)
+            tc_store8(Lf, n, I, K0, k, e - 1, A, planeA, I * kcap + K0);
+        } else {
+            const int64_t r = it - itemsA;
+            const int c = (int)(r % kSpecTC);
+            const int32_t K0 = (int32_t)(r / kSpecTC) * 8;
+            const long long Sc = ctrl->STc[c];
+            const float sg = Sc >= 0 ? sigA[Sc] : 1.f;
+            int e = 0;
+            frexpf(sg, &e);
+            tc_store8(Lf, n, Sc >= 0 ? Sc : -1, K0, k, e - 1, B, planeB, (int64_t)c * kcap + K0);
+            if (K0 == 0) sigB[c] = sg;
+        }
+    }
+}
+
 // Step k, part 2: vector k, residuals, next pivot.
-template <bool DF, bool SPEC>
+template <bool DF, bool SPEC, bool TC = false>
 __global__ void __launch_bounds__(kUpdThreads)
 k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
             double* __restrict__ D, const uint8_t* __restrict__ cand,
@@ -759,7 +873,7 @@ k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
             double* __restrict__ blk_a, double* __restrict__ blk_b,
             long long* __restrict__ blk_i, int32_t* __restrict__ piv, CdCtrl* ctrl) {
     if (ctrl->done) return;
-    cd_step_body<DF, SPEC>(n, k, max_rank, L, D, cand, ecol, G,
+    cd_step_body<DF, SPEC, TC>(n, k, max_rank, L, D, cand, ecol, G,
                            reinterpret_cast<long long*>(blk_a),
                            reinterpret_cast<long long*>(blk_b), blk_i, piv, ctrl, blockIdx.x,
                            gridDim.x);
@@ -777,7 +891,14 @@ struct CdLayout {
     PairSoA pd;
     uint8_t* cand;
     double* ecol;     // integral column of the current step
-    float2* G;        // [kSpec][npair] candidate projections (float-pair mode)
+    float2* G;        // [kSpec][npair] candidate projections (float-pair mode; [kSpecTC] in TC)
+    // exact-slice tensor-core form
+    __nv_bfloat16* A; // slice store [kSlicesTC][npair][kcap]
+    __nv_bfloat16* B; // candidate rows [kSlicesTC][kSpecTC][kcap]
+    float* sigA;      // [npair] pair scales
+    float* sigB;      // [kSpecTC] candidate scales
+    int32_t* err;     // the GEMM's bounded-wait error word
+    int32_t kcap;
     PairF2 pf;        // pair data as float pairs (float-pair mode)
     double* blk_a;
     double* blk_b;
@@ -805,12 +926,22 @@ static int sm_count() {
 }
 static int sel_blocks(int64_t n) { return (int)std::min<int64_t>(4 * 152, (n + kCdThreads - 1) / kCdThreads); }
 
-// spec: room for the candidate projections of the float-pair mode
-static CdLayout cd_layout(void* ws, int32_t nbf, bool spec = true) {
+// Column capacity of the slice store for max_rank vectors.
+static int32_t tc_kcap(int32_t max_rank) {
+    return std::max(1, (max_rank + kGroupTC - 1) / kGroupTC) * kGroupTC;
+}
+
+// spec: room for the candidate projections of the float-pair mode; tc (with
+// max_rank): also the tensor-core form's slice store and candidate rows
+static CdLayout cd_layout(void* ws, int32_t nbf, bool spec = true, bool tc = false,
+                          int32_t max_rank = 0) {
     int64_t n = npair_of(nbf);
     int nb = part_blocks(n);
+    spec = spec || tc;
     Carver c(ws);
     CdLayout l;
+    l.kcap = tc ? tc_kcap(max_rank) : 0;
+    l.ctrl = c.take<CdCtrl>(1);   // first: at the same offset in every form (cds_cd_stats)
     l.pd.p = c.take<double>(n);
     l.pd.Px = c.take<double>(n);
     l.pd.Py = c.take<double>(n);
@@ -818,7 +949,12 @@ static CdLayout cd_layout(void* ws, int32_t nbf, bool spec = true) {
     l.pd.Kp = c.take<double>(n);
     l.cand = c.take<uint8_t>(n);
     l.ecol = c.take<double>(n);
-    l.G = spec ? c.take<float2>((size_t)kSpec * n) : nullptr;
+    l.G = spec ? c.take<float2>((size_t)(tc ? kSpecTC : kSpec) * n) : nullptr;
+    l.A = tc ? c.take<__nv_bfloat16>((size_t)kSlicesTC * n * l.kcap) : nullptr;
+    l.B = tc ? c.take<__nv_bfloat16>((size_t)kSlicesTC * kSpecTC * l.kcap) : nullptr;
+    l.sigA = tc ? c.take<float>(n) : nullptr;
+    l.sigB = tc ? c.take<float>(kSpecTC) : nullptr;
+    l.err = tc ? c.take<int32_t>(4) : nullptr;
     l.pf.p = spec ? c.take<float2>(n) : nullptr;
     l.pf.Px = spec ? c.take<float2>(n) : nullptr;
     l.pf.Py = spec ? c.take<float2>(n) : nullptr;
@@ -827,7 +963,6 @@ static CdLayout cd_layout(void* ws, int32_t nbf, bool spec = true) {
     l.blk_a = c.take<double>(nb);
     l.blk_b = c.take<double>(nb);
     l.blk_i = c.take<long long>(nb);
-    l.ctrl = c.take<CdCtrl>(1);
     l.bytes = c.off;
     return l;
 }
@@ -837,6 +972,14 @@ size_t cd_workspace_bytes_for(int32_t nbf, bool f32x2) {
     return cd_layout(nullptr, nbf, f32x2).bytes;
 }
 
+size_t cd_workspace_bytes_prec(int32_t nbf, int32_t max_rank, int32_t precision) {
+    if (nbf < 0 || max_rank < 0) return 0;
+    if (precision == CDS_PREC_OZAKI) return cd_layout(nullptr, nbf, true, true, max_rank).bytes;
+    if (precision == CDS_PREC_F32X2) return cd_layout(nullptr, nbf, true).bytes;
+    if (precision == CDS_PREC_FP64) return cd_layout(nullptr, nbf, false).bytes;
+    return 0;
+}
+
 }  // namespace cds
 
 using namespace cds;
@@ -844,18 +987,25 @@ using namespace cds;
 // Enough for either precision.
 extern "C" size_t cds_cd_workspace_bytes(int32_t nbf) { return cd_workspace_bytes_for(nbf, true); }
 
-extern "C" int cds_cd_candidates(void) { return kSpec; }
+extern "C" int cds_cd_candidates(int32_t precision) {
+    return precision == CDS_PREC_OZAKI ? kSpecTC : precision == CDS_PREC_F32X2 ? kSpec : 1;
+}
+
+extern "C" size_t cds_cd_workspace_bytes_prec(int32_t nbf, int32_t max_rank, int32_t precision) {
+    return cd_workspace_bytes_prec(nbf, max_rank, precision);
+}
 
 extern "C" int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precision,
                             int32_t* passes, int64_t* streamed, int64_t* extra,
                             cudaStream_t stream) {
     if (nbf <= 0 || !workspace || !passes || !streamed || !extra) return CDS_ERR_ARG;
-    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return CDS_ERR_UNSUPPORTED;
-    CdLayout lay = cd_layout(const_cast<void*>(workspace), nbf, precision == CDS_PREC_F32X2);
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2 && precision != CDS_PREC_OZAKI)
+        return CDS_ERR_UNSUPPORTED;
+    CdLayout lay = cd_layout(const_cast<void*>(workspace), nbf, precision != CDS_PREC_FP64);
     CdCtrl h{};
     CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, stream));
     CDS_CUDA_TRY(cudaStreamSynchronize(stream));
-    if (precision == CDS_PREC_F32X2) {
+    if (precision != CDS_PREC_FP64) {
         *passes = h.passes;
         *streamed = h.streamed;
         *extra = h.extra;
@@ -881,14 +1031,17 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
                      const CdChunkHook* on_chunk, cudaStream_t convert_after) {
     if (nbf <= 0 || !xyz || !alpha || !L || !piv || !D || !M_out || max_rank < 0)
         return CDS_ERR_ARG;
-    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2) return CDS_ERR_UNSUPPORTED;
-    const bool df = precision == CDS_PREC_F32X2;
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2 && precision != CDS_PREC_OZAKI)
+        return CDS_ERR_UNSUPPORTED;
+    const bool tcm = precision == CDS_PREC_OZAKI;
+    const bool df = precision == CDS_PREC_F32X2 || tcm;
     if (!(delta >= 0.0)) return CDS_ERR_ARG;
     if (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC) return CDS_ERR_ARG;
     if (scheme == CDS_SCHEME_ATOMIC && !atom) return CDS_ERR_ARG;
     int64_t n = npair_of(nbf);
-    CdLayout lay = cd_layout(workspace, nbf, df);
+    CdLayout lay = cd_layout(workspace, nbf, df, tcm, max_rank);
     if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    if (tcm && step_blocks(n) > kMaxBlocksTC) return CDS_ERR_UNSUPPORTED;
     int st = build_pairs(nbf, xyz, alpha, lay.pd, stream);
     if (st) return st;
     if (df) {
@@ -906,11 +1059,36 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
     k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, 0, max_rank, D, lay.cand, lay.blk_i, piv,
                                               lay.ctrl);
     CDS_LAUNCH_CHECK();
+    // tensor-core form: pair scales from the initial diagonal, the GEMM's
+    // tensor maps (fixed for the whole decomposition) and error word
+    CdTcGemm* gemm = nullptr;
+    struct GemmGuard {
+        CdTcGemm*& g;
+        ~GemmGuard() { if (g) cd_tc_gemm_free(g); }
+    } guard{gemm};
+    if (tcm) {
+        k_cd_tc_scales<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(D, n, lay.sigA);
+        CDS_LAUNCH_CHECK();
+        CDS_CUDA_TRY(cudaMemsetAsync(lay.err, 0, sizeof(int32_t), stream));
+        st = cd_tc_gemm_setup(&gemm, n, lay.kcap, lay.A, lay.B, lay.sigA, lay.sigB, lay.G,
+                              lay.ctrl, lay.err);
+        if (st) return st;
+    }
     CdCtrl h{};
     for (int32_t k0 = 0; k0 <= max_rank; k0 += kHostCheckEvery) {
         int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
         for (int32_t k = k0; k < k1; ++k) {
-            if (df) {
+            if (tcm) {
+                k_cd_project_tc<<<nres, kUpdThreads, 0, stream>>>(
+                    lay.pd, lay.pf, n, k, L, reinterpret_cast<float2*>(lay.ecol), lay.sigA, lay.A,
+                    lay.B, lay.sigB, lay.kcap, lay.ctrl);
+                CDS_CUDA_TRY(cudaGetLastError());
+                st = cd_tc_gemm_launch(gemm, stream);
+                if (st) return st;
+                k_cd_update<true, true, true><<<nu, kUpdThreads, 0, stream>>>(
+                    n, k, max_rank, L, D, lay.cand, lay.ecol, lay.G, lay.blk_a, lay.blk_b,
+                    lay.blk_i, piv, lay.ctrl);
+            } else if (df) {
                 k_cd_project_spec<<<nres, kUpdThreads, 0, stream>>>(
                     lay.pd, lay.pf, n, k, L, lay.G, reinterpret_cast<float2*>(lay.ecol),
                     dot_tiles(n), lay.ctrl);
@@ -948,6 +1126,12 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
         const int64_t cnt = (int64_t)h.M * n;
         k_pairs_to_fp64<<<(unsigned)((cnt + 255) / 256), 256, 0, stream>>>(L, cnt);
         CDS_LAUNCH_CHECK();
+    }
+    if (tcm) {   // a bounded wait of the projection GEMM gave up
+        int32_t e = 0;
+        CDS_CUDA_TRY(cudaMemcpyAsync(&e, lay.err, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+        CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (e) return CDS_ERR_TIMEOUT;
     }
     if (!h.done) return CDS_ERR_RANK_CAP;
     return h.status;

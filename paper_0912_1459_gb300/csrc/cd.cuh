@@ -1,0 +1,82 @@
+// Shared declarations of the Cholesky decomposition kernels (cd.cu) and its
+// exact-slice tensor-core projection GEMM (cd_tc.cu).
+#pragma once
+
+#include "common.cuh"
+
+namespace cds {
+
+constexpr int kCdThreads = 128;
+constexpr int kUpdWarps = 8;                  // k_cd_update: warps splitting the K sum
+constexpr int kUpdThreads = 32 * kUpdWarps;
+constexpr int kUpdPairs = 64;                 // k_cd_project: pairs per projection tile
+constexpr int kStepPer = 2;                   // k_cd_update: pairs per thread
+constexpr int kStepChunk = kStepPer * kUpdThreads;   // k_cd_update: contiguous pairs per block
+constexpr int kCdChunk = 2048;   // pivot row L^K_P staged in shared memory in chunks
+constexpr double kTieRel = 1e-12;
+constexpr double kNotPdRel = 1e-10;
+constexpr int kHostCheckEvery = 32;
+#ifndef CDS_KSPEC
+#define CDS_KSPEC 4
+#endif
+#ifndef CDS_KSPEC_ROWS
+#define CDS_KSPEC_ROWS 4
+#endif
+constexpr int kSpec = CDS_KSPEC;          // candidate pivots per speculative projection pass
+constexpr int kSpecRows = CDS_KSPEC_ROWS; // rows of L in flight per thread and iteration
+constexpr int kSpecChunk = 4096 / kSpec;   // pivot columns staged per shared-memory chunk (32 KB)
+// Exact-slice tensor-core form (CDS_PREC_OZAKI): candidates per streaming
+// pass, the longest batch of steps one pass serves, the column group of the
+// slice store (one 64-byte TMA row of BF16), the slices per element and the
+// bits per slice (56-bit fixed point below a per-pair power-of-two scale).
+constexpr int kSpecTC = 32;
+constexpr int kBatchTC = 64;
+constexpr int kGroupTC = 32;
+constexpr int kSlicesTC = 8;
+constexpr int kBitsTC = 7;
+constexpr int kMaxBlocksTC = 2048;   // update blocks the candidate search holds in shared memory
+
+struct CdCtrl {
+    double scale;      // max initial diagonal (all pairs)
+    double delta_eff;  // max(delta, npair * 2^-52 * scale)
+    double G;          // max candidate residual after the last update
+    double Dmin;       // min residual after the last update
+    double DP;         // residual of the current pivot
+    double rDP;        // 1 / sqrt(DP)
+    float2 rDPf;       // the same as a float pair
+    int64_t P;         // current pivot
+    int32_t done;      // decomposition stopped
+    int32_t status;    // cds_status
+    int32_t M;         // vectors produced
+    int32_t _pad;
+    unsigned int counter;  // last-block-done counter
+    unsigned int _pad2;
+    // speculative projections (float-pair mode): the pivots of the current
+    // batch's candidate set, the batch's first step, the slot of the current
+    // pivot in the set, and whether this step streams L (a new batch)
+    long long S[kSpec];
+    int32_t k0, slot, pass, passes;     // passes: batches started (streaming passes)
+    long long streamed;                  // sum over passes of the vectors streamed (k0)
+    long long extra;                     // sum over continued steps of the vectors added (k - k0)
+    // exact-slice tensor-core form: its candidate set, and the columns of the
+    // slice store that are final (a multiple of kGroupTC)
+    long long STc[kSpecTC];
+    int32_t kdone;
+    int32_t _pad3;
+};
+
+// The exact-slice projection GEMM of one step (cd_tc.cu).  Enqueued at every
+// step of the tensor-core form; it returns at once unless the step starts a
+// streaming pass (ctrl->pass), and then forms, for the pass's candidate set,
+//   G[c][I] = sum_{K < k0} L^K_I L^K_{S_c}     (float pairs, [kSpecTC][n]),
+// from the slice store (A: planes [kSlicesTC][n][kcap] of pair rows) and
+// the candidate rows (B: planes [kSlicesTC][kSpecTC][kcap]), both scaled by
+// the per-row powers of two sigA / sigB.
+struct CdTcGemm;
+int cd_tc_gemm_setup(CdTcGemm** out, int64_t n, int32_t kcap, const void* a_planes,
+                     const void* b_planes, const float* sigA, const float* sigB, float2* G,
+                     const CdCtrl* ctrl, int32_t* err);
+int cd_tc_gemm_launch(const CdTcGemm* g, cudaStream_t stream);
+void cd_tc_gemm_free(CdTcGemm* g);
+
+}  // namespace cds

@@ -122,6 +122,9 @@ int build_pairs(int32_t nbf, const double* xyz, const double* alpha, PairSoA pd,
 // Workspace of cds_cd_decompose for one precision (f32x2 needs the candidate
 // projections as well).
 size_t cd_workspace_bytes_for(int32_t nbf, bool f32x2);
+// Workspace of cds_cd_decompose for a precision (FP64, F32X2, or OZAKI: the
+// tensor-core form, whose slice store holds max_rank columns).
+size_t cd_workspace_bytes_prec(int32_t nbf, int32_t max_rank, int32_t precision);
 // Called after each host check of the decomposition: (rows of L final, stopped).
 using CdChunkHook = std::function<int(int32_t, bool)>;
 int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const int32_t* atom,

@@ -100,6 +100,45 @@ def test_cd_f32x2_parity(name, delta, scheme):
     np.testing.assert_allclose(D, ref.D, rtol=0, atol=1e-9)
 
 
+@pytest.mark.parametrize("name,delta,scheme", [
+    ("c0", 1e-6, "full"), ("c0", 1e-6, "atomic"), ("c1", 1e-4, "full"), ("c1", 1e-5, "full"),
+    ("c1", 1e-6, "full"), ("c1", 1e-5, "atomic"),
+])
+def test_cd_tensor_core_parity(name, delta, scheme):
+    """Exact-slice tensor-core passes (CDS_PREC_OZAKI: the stored vectors as
+    42-bit fixed point below each pair's scale sigma_I > sqrt(D0_I), 32
+    candidates per pass): the oracle's pivots; vectors within
+    tol = max(1e-9, 1e-11 / sqrt(delta)) -- a projection carries ~2^-42
+    sigma_I sigma_P sqrt(k) of truncation and L^k divides it by sqrt(D_P) >=
+    sqrt(delta) (about 4e-13 x 2 x 20 = 1e-11 here); L^T L and the residuals
+    within the same."""
+    m = O.molecule(name)
+    ref = O.decomposition(name, delta, scheme)
+    L, piv, D, de = gpu_cd(m, delta, scheme, precision="ozaki")
+    tol = max(1e-9, 1e-11 / np.sqrt(delta))
+    assert de == pytest.approx(ref.delta_eff, rel=1e-14)
+    assert np.array_equal(piv, ref.piv)
+    np.testing.assert_allclose(L, ref.L, rtol=0, atol=tol)
+    sub = np.random.default_rng(2).choice(L.shape[1], min(L.shape[1], 600), replace=False)
+    np.testing.assert_allclose(L[:, sub].T @ L[:, sub], ref.L[:, sub].T @ ref.L[:, sub],
+                               rtol=0, atol=tol)
+    np.testing.assert_allclose(D, ref.D, rtol=0, atol=tol)
+
+
+def test_cd_tensor_core_refuses_bases_beyond_its_candidate_search():
+    """The tensor-core form keeps the update blocks' maxima in shared memory:
+    more than 2048 blocks of 512 pairs (nbf > 1447) is refused before any
+    launch with CDS_ERR_UNSUPPORTED."""
+    n = 1460
+    rng = np.random.default_rng(0)
+    xyz = dev(rng.uniform(0, 40, (n, 3)))
+    a = dev(np.full(n, 0.5))
+    at = dev(np.arange(n, dtype=np.int32))
+    with pytest.raises(G.CdsError) as ei:
+        G.cds_cd_decompose(xyz, a, at, 1e-4, "full", max_rank=1, precision="ozaki")
+    assert ei.value.status == 7
+
+
 def test_cd_precision_rejected():
     m = O.molecule("c0")
     with pytest.raises(G.CdsError) as ei:
@@ -244,28 +283,37 @@ def test_tiny_case_against_stored_oracle_values():
         assert float(P[t]) == pytest.approx(r["pole"], rel=1e-8)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "f32x2"])
+@pytest.mark.parametrize("precision", ["fp64", "f32x2", "ozaki"])
 def test_cd_stats_counters(precision):
-    """cds_cd_stats: FP64 streams at every step; the float-pair form streams at
-    the first step of each batch of at most four, and a continued step adds
-    between one and three vectors."""
+    """cds_cd_stats: FP64 streams at every step; the speculative forms stream
+    at the first step of each batch of at most B steps (4 for float pairs, 64
+    on the tensor cores, whose passes project 32 candidates), and a continued
+    step adds between one and B-1 vectors."""
     m = O.molecule("c1")
     xyz, a, at = basis_dev(m)
-    ws = torch.empty(G.load().cds_cd_workspace_bytes(m.nbf), dtype=torch.uint8, device=DEV)
-    L, piv, D, de = G.cds_cd_decompose(xyz, a, at, 1e-5, "full", workspace=ws, precision=precision)
+    prec = G.cdsigma.PRECISIONS[precision]
+    ws = torch.empty(G.load().cds_cd_workspace_bytes_prec(m.nbf, 1024, prec), dtype=torch.uint8,
+                     device=DEV)
+    L, piv, D, de = G.cds_cd_decompose(xyz, a, at, 1e-5, "full", max_rank=1024, workspace=ws,
+                                       precision=precision)
     M = L.shape[0]
     st = G.cdsigma.cds_cd_stats(m.nbf, ws, precision)
+    ncand = G.cdsigma.cd_candidates(precision)
     if precision == "fp64":
+        assert ncand == 1
         assert st == {"passes": M, "streamed": M * (M - 1) // 2, "extra": 0}
     else:
-        assert (M + 3) // 4 <= st["passes"] <= M
+        assert ncand == {"f32x2": 4, "ozaki": 32}[precision]
+        B = {"f32x2": 4, "ozaki": 64}[precision]
+        assert (M + B - 1) // B <= st["passes"] <= M
         assert 0 < st["streamed"] < M * (M - 1) // 2
         cont = M - st["passes"]
-        assert cont <= st["extra"] <= 3 * cont
+        assert cont <= st["extra"] <= (B - 1) * cont
 
 
+@pytest.mark.parametrize("cdp", ["f32x2", "ozaki"])
 @pytest.mark.parametrize("name,delta,orbs", [("c1", 1e-5, None), ("c0", 1e-6, []), ("c1", 1e-4, [39, 40])])
-def test_fused_decompose_to_mo_matches_separate_calls(name, delta, orbs):
+def test_fused_decompose_to_mo_matches_separate_calls(name, delta, orbs, cdp):
     """cds_cd_decompose_to_mo (float-pair CD with the transform overlapped) gives
     the pivots and vectors of cds_cd_decompose(F32X2) and the factors of
     cds_cd_to_mo(F32X2) on them.  The pipelined transform reads the float-pair
@@ -274,10 +322,10 @@ def test_fused_decompose_to_mo_matches_separate_calls(name, delta, orbs):
     m = O.molecule(name)
     xyz, a, at = basis_dev(m)
     orb = dev(np.asarray(m.orbitals if orbs is None else orbs, dtype=np.int32))
-    L1, piv1, D1, de1 = G.cds_cd_decompose(xyz, a, at, delta, "full", precision="f32x2")
+    L1, piv1, D1, de1 = G.cds_cd_decompose(xyz, a, at, delta, "full", precision=cdp)
     Lov1, Lp1 = G.cds_cd_to_mo(L1, dev(m.C), m.nocc, orb, precision="f32x2")
     L2, piv2, D2, de2, Lov2, Lp2 = G.cds_cd_decompose_to_mo(xyz, a, at, delta, dev(m.C), m.nocc,
-                                                           orb)
+                                                           orb, cd_precision=cdp)
     assert torch.equal(piv1, piv2) and torch.equal(L1, L2) and torch.equal(D1, D2)
     assert Lov2.shape == Lov1.shape and Lp2.shape == Lp1.shape
     scale = Lov1.abs().max().item()
