@@ -1,11 +1,13 @@
 """Autotuner for the batched tensor-core self-energy.
 
 Times captured-graph replays of the actual batch for every combination of
-the library's kernel configuration (energies per epilogue pass 8 / 16, item
-order interleaved / blocked), keeps the fastest, and caches the choice in a
-JSON file keyed by the batch's shape signature (molecule sizes, orbital and
-energy counts, Cholesky ranks, precision), so a repeated batch shape is tuned
-once.
+the library's kernel configuration -- energies per epilogue pass (8 / 16),
+work-item order (interleaved / blocked) and how the Newton passes evaluate
+Sigma (recomputing the integrals on the tensor cores, or streaming the
+numerators the grid pass kept) -- keeps the fastest, and caches the choice
+in a JSON file keyed by the batch's shape signature (molecule sizes, orbital
+and energy counts, Cholesky ranks, precision), so a repeated batch shape is
+tuned once.
 """
 from __future__ import annotations
 
@@ -18,7 +20,8 @@ import torch
 
 from . import cdsigma as C
 
-CANDIDATES = [(16, 0), (16, 1), (8, 0), (8, 1)]   # (energy chunk, item order)
+# (energy chunk, item order, Newton from kept numerators)
+CANDIDATES = [(c, o, k) for k in (1, 0) for c in (16, 8) for o in (0, 1)]
 
 
 def cache_path() -> str:
@@ -50,13 +53,14 @@ def _store(cache: dict) -> None:
 def apply(choice) -> None:
     C.cds_tune_set(C.TUNE_ENERGY_CHUNK, int(choice[0]))
     C.cds_tune_set(C.TUNE_ITEM_ORDER, int(choice[1]))
+    C.cds_tune_set(C.TUNE_NEWTON_CACHE, int(choice[2]))
 
 
 def tune(batch: "C.Batch", orb, eps, E, reps: int = 2, use_cache: bool = True) -> dict:
     """Pick and apply the fastest configuration for this batch.
 
-    Returns {"choice": (chunk, order), "ms": {candidate: ms}, "cached": bool}."""
-    key = signature(batch)
+    Returns {"choice": (chunk, order, cache), "ms": {candidate: ms}, "cached": bool}."""
+    key = "v2:" + signature(batch)
     cache = _load() if use_cache else {}
     if key in cache:
         choice = tuple(cache[key]["choice"])
@@ -75,7 +79,7 @@ def tune(batch: "C.Batch", orb, eps, E, reps: int = 2, use_cache: bool = True) -
             g.launch()
         t1.record()
         torch.cuda.synchronize()
-        timings[f"{cand[0]},{cand[1]}"] = t0.elapsed_time(t1) / reps
+        timings[",".join(str(x) for x in cand)] = t0.elapsed_time(t1) / reps
         del g
     best = min(timings, key=timings.get)
     choice = tuple(int(x) for x in best.split(","))

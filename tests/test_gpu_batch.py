@@ -153,24 +153,33 @@ def test_autotuner_candidates_agree_and_cache(batch, tmp_path, monkeypatch):
     from paper_0912_1459_gb300 import autotune
     mols, b, M, inp = batch
     monkeypatch.setenv("CDS_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
-    results = []
+    results = {}
     for cand in autotune.CANDIDATES:
         autotune.apply(cand)
         g = b.graph(inp["orb"], inp["eps"], inp["E"])
         g.launch()
         torch.cuda.synchronize()
-        results.append((b.sigma.clone(), b.omega.clone()))
+        results[cand] = (b.sigma.clone(), b.omega.clone(), b.pole.clone(), b.status.clone())
         del g
-    for s_, w_ in results[1:]:
-        # items are reduced per orbital in a fixed order, so the configuration
-        # changes only which CTA computes an item, not the arithmetic
-        torch.testing.assert_close(s_, results[0][0], rtol=1e-13, atol=1e-13)
-        torch.testing.assert_close(w_, results[0][1], rtol=1e-13, atol=1e-13)
+    for cand, (s_, w_, p_, st_) in results.items():
+        # items are reduced per orbital in a fixed order, so the chunk and the
+        # order change only which CTA computes an item, not the arithmetic
+        ref = results[(16, 0, cand[2])]
+        torch.testing.assert_close(s_, ref[0], rtol=1e-13, atol=1e-13)
+        torch.testing.assert_close(w_, ref[1], rtol=1e-13, atol=1e-13)
+    # Newton from the kept numerators against recomputed integrals: the same
+    # per-element arithmetic, FP32 sums in another order -- the grid within
+    # 1e-5 relative, quasiparticle roots (P >= 0.5, converged) within 1e-7 Ha
+    a, r = results[(16, 0, 1)], results[(16, 0, 0)]
+    torch.testing.assert_close(a[0], r[0], rtol=1e-5, atol=1e-8)
+    qp = (a[3] == 0) & (r[3] == 0) & (r[2] >= 0.5)
+    assert int(qp.sum()) >= 10
+    assert (a[1] - r[1])[qp].abs().max().item() <= 1e-7
     first = autotune.tune(b, inp["orb"], inp["eps"], inp["E"])
     assert first["cached"] is False and tuple(first["choice"]) in autotune.CANDIDATES
     again = autotune.tune(b, inp["orb"], inp["eps"], inp["E"])
     assert again["cached"] is True and tuple(again["choice"]) == tuple(first["choice"])
-    autotune.apply((16, 0))
+    autotune.apply((16, 0, 1))
 
 
 def test_batch_exact_slice_transform(batch):
