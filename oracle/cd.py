@@ -87,12 +87,14 @@ def select_pivot(D: np.ndarray, cand: np.ndarray, scale: float, delta_eff: float
 def decompose(pd: PairData, delta: float, scheme: str = "full",
               atom: Optional[np.ndarray] = None, max_rank: Optional[int] = None,
               column: Optional[Callable[[int], np.ndarray]] = None,
-              tie_rel: float = TIE_REL) -> CDResult:
+              tie_rel: float = TIE_REL, diagonal: Optional[np.ndarray] = None) -> CDResult:
     """Cholesky vectors L^K (Eq. CD) by Gram-Schmidt steps (Eq. gs_coulomb).
 
     ``column(P)`` returns (rho_I|rho_P) for all I; by default it is computed
     on the fly from the closed-form integral.  Pass ``lambda P: V[:, P]`` to
-    decompose an explicit supermatrix.
+    decompose an explicit supermatrix.  ``diagonal`` (the (rho_I|rho_I)) goes
+    with a ``column`` of another basis (contracted shells); ``pd`` then only
+    supplies npair and the pair list (mu, nu) for the atomic candidate set.
     """
     n = pd.npair
     if column is None:
@@ -101,7 +103,7 @@ def decompose(pd: PairData, delta: float, scheme: str = "full",
     if max_rank is None:
         max_rank = n
     cand = candidate_mask(pd, atom, scheme)
-    D = eri_diagonal(pd)
+    D = eri_diagonal(pd) if diagonal is None else np.array(diagonal, dtype=np.float64)
     scale = float(D.max())
     delta_eff = effective_delta(delta, n, scale)
     L = np.zeros((min(max_rank, n, 256), n))

@@ -35,7 +35,7 @@ __all__ = [
     "geometric_exponents", "ring_centres", "truncated_icosahedron",
     "random_cube_centres", "ball_centres", "make_basis", "s_overlap",
     "mo_coefficients", "orbital_energies", "gap_orbitals", "energy_grid",
-    "make_molecule", "npair",
+    "make_molecule", "npair", "ShellInput", "shell_basis", "shell_config",
 ]
 
 
@@ -242,3 +242,79 @@ def config3(seed: int = 3, n_clusters: int = 64) -> list[Molecule]:
                                  geometric_exponents(0.1, 10.0, 10), nocc, orbs,
                                  nE, 1e-5, rng, seed))
     return out
+
+
+# ---------------------------------------------------------------------------
+# Contracted Cartesian shells (s, p, d): seeded stand-ins for the paper's
+# contracted cc-pVXZ sets (Sec. III), which are not available here.
+# ---------------------------------------------------------------------------
+_CART = {0: [(0, 0, 0)],
+         1: [(1, 0, 0), (0, 1, 0), (0, 0, 1)],
+         2: [(2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2)]}
+
+
+def _dfact(n: int) -> int:
+    return 1 if n <= 0 else n * _dfact(n - 2)
+
+
+@dataclasses.dataclass
+class ShellInput:
+    """Per basis function: centre, Cartesian exponents (l, m, n), and its
+    primitives [start[f], start[f+1]) with exponents and coefficients (the
+    coefficients make the contracted function's self-overlap 1)."""
+    xyz: np.ndarray      # [nbf, 3] float64
+    lmn: np.ndarray      # [nbf, 3] int32
+    start: np.ndarray    # [nbf + 1] int32
+    exps: np.ndarray     # [nprim] float64
+    coefs: np.ndarray    # [nprim] float64
+    atom: np.ndarray     # [nbf] int32
+    centres: np.ndarray
+
+    @property
+    def nbf(self) -> int:
+        return int(self.lmn.shape[0])
+
+
+def shell_basis(centres: np.ndarray, shells, rng: np.random.Generator) -> ShellInput:
+    """shells: list of (l, exponents) per centre (the same on every centre);
+    contraction coefficients drawn uniform in [0.2, 1], then scaled so that
+    each Cartesian function has unit self-overlap (one-centre Gaussian
+    moments: int x^2k exp(-c x^2) dx = (2k-1)!! / (2c)^k sqrt(pi / c))."""
+    coefs_by_shell = [rng.uniform(0.2, 1.0, len(e)) for _, e in shells]
+    xyz, lmn, start, exps, coefs, atom = [], [], [0], [], [], []
+    for a, A in enumerate(np.asarray(centres, dtype=np.float64)):
+        for (l, e), c in zip(shells, coefs_by_shell):
+            e = np.asarray(e, dtype=np.float64)
+            for comp in _CART[l]:
+                S = 0.0
+                for i in range(len(e)):
+                    for j in range(len(e)):
+                        g = e[i] + e[j]
+                        m = 1.0
+                        for k in comp:
+                            m *= _dfact(2 * k - 1) / (2.0 * g) ** k * math.sqrt(math.pi / g)
+                        S += c[i] * c[j] * m
+                xyz.append(A)
+                lmn.append(comp)
+                exps.extend(e.tolist())
+                coefs.extend((c / math.sqrt(S)).tolist())
+                start.append(start[-1] + len(e))
+                atom.append(a)
+    return ShellInput(np.array(xyz), np.array(lmn, dtype=np.int32),
+                      np.array(start, dtype=np.int32), np.array(exps), np.array(coefs),
+                      np.array(atom, dtype=np.int32), np.asarray(centres, dtype=np.float64))
+
+
+def shell_config(ncentre: int = 6, seed: int = 7) -> ShellInput:
+    """Contracted s/p/d test basis: ncentre centres uniform in a cube of side
+    2 ncentre^(1/3) + 4 bohr (separation >= 1.5), per centre a 3-primitive
+    s, a 1-primitive s, a 2-primitive p and a 1-primitive d shell (11
+    Cartesian functions), exponents a seeded geometric ladder."""
+    rng = np.random.default_rng(seed)
+    side = 2.0 * ncentre ** (1.0 / 3.0) + 4.0
+    centres = random_cube_centres(ncentre, side, 1.5, rng)
+    shells = [(0, geometric_exponents(0.3, 12.0, 3) * rng.uniform(0.9, 1.1)),
+              (0, [0.12 * rng.uniform(0.9, 1.1)]),
+              (1, geometric_exponents(0.25, 2.5, 2) * rng.uniform(0.9, 1.1)),
+              (2, [0.8 * rng.uniform(0.9, 1.1)])]
+    return shell_basis(centres, shells, rng)
