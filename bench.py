@@ -53,16 +53,22 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "fp64"])
+    p.add_argument("--precision", default="bf16x3", choices=["bf16x3", "fp16x3", "tf32x3", "fp64"])
     p.add_argument("--delta", type=float, default=1e-4)
     p.add_argument("--scheme", default="full", choices=["full", "atomic"])
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-fp64-arm", action="store_true")
+    p.add_argument("--no-fp64-arm", action="store_true",
+                   help="skip the measured all-FP64 GPU step and the per-orbital accuracy tables")
+    p.add_argument("--no-adjoint", action="store_true",
+                   help="skip timing the adjoint of 8 gap orbitals")
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--no-mp2", action="store_true")
     p.add_argument("--transform", default="ozaki", choices=["ozaki", "f32x2"],
                    help="transform of the pipelined step: exact-slice tcgen05 GEMMs or "
                         "float-pair GEMMs on the FP32 units")
+    p.add_argument("--cd-precision", default="ozaki", choices=["f32x2", "ozaki"],
+                   help="decomposition of the pipelined step: speculative float-pair passes (4 "
+                        "candidates) or exact-slice tensor-core passes (32 candidates)")
     p.add_argument("--no-trtc", action="store_true",
                    help="skip timing the other transform forms on the step's vectors")
     p.add_argument("--no-acd", action="store_true",
@@ -255,7 +261,8 @@ def run_ours(args, dist: Dist):
     max_rank = 2048 if args.delta >= 1e-5 else 4096
     npr = G.npair(m.nbf)
     Lbuf = torch.empty((max_rank, npr), dtype=torch.float64, device=device)
-    cd_ws = torch.empty(lib.cds_cd_workspace_bytes(m.nbf), dtype=torch.uint8, device=device)
+    cd_ws = torch.empty(lib.cds_cd_workspace_bytes_prec(m.nbf, max_rank, G.cdsigma.PRECISIONS[
+        args.cd_precision if prec != "fp64" else "fp64"]), dtype=torch.uint8, device=device)
     cached = args.newton == "cached" and prec != "fp64"
     cache = (torch.empty(lib.cds_sigma2_cache_bytes(m.nbf, m.nocc, n_orb, G.cdsigma.PRECISIONS[prec]), dtype=torch.uint8,
                          device=device) if cached else None)
@@ -265,8 +272,9 @@ def run_ours(args, dist: Dist):
         nv = m.nbf - m.nocc
         lov_buf = torch.empty(m.nocc * nv * max_rank, dtype=torch.float64, device=device)
         lp_buf = torch.empty(n_orb * m.nbf * max_rank, dtype=torch.float64, device=device)
-        fz_ws = torch.empty(lib.cds_cd_decompose_to_mo_workspace_bytes(m.nbf, m.nbf, m.nocc,
-                                                                       max_rank, n_orb),
+        fz_ws = torch.empty(lib.cds_cd_decompose_to_mo_workspace_bytes(
+                                m.nbf, m.nbf, m.nocc, max_rank, n_orb,
+                                G.cdsigma.PRECISIONS[args.cd_precision]),
                             dtype=torch.uint8, device=device)
 
     def step(xyz, al, at, C, eps, orbs, E, ws=None):
@@ -276,7 +284,8 @@ def run_ours(args, dist: Dist):
             # decomposition and transform pipelined in one call: one stage
             L, piv, D, de, Lov, Lp = G.cds_cd_decompose_to_mo(
                 xyz, al, at, args.delta, C, m.nocc, orbs, args.scheme, L_out=Lbuf,
-                Lov_out=lov_buf, Lp_out=lp_buf, workspace=fz_ws, transform=args.transform)
+                Lov_out=lov_buf, Lp_out=lp_buf, workspace=fz_ws, transform=args.transform,
+                cd_precision=args.cd_precision)
             ev[1].record()
             ev[2].record()
         else:
@@ -322,6 +331,12 @@ def run_ours(args, dist: Dist):
 
     # ---- timed region: device-resident inputs (all > L2: L is GBs) ----
     clocks = Clocks(device.index if device.index is not None else 0)
+    # the tensor-core decomposition's projection GEMM, the step's dominant
+    # kernel, is timed by the library with CUDA events around each of its
+    # launches, on the stream it launches on, in extra steps after the timed
+    # ones (the 1,792 event records of a step would slow the timed steps' host
+    # loop by ~4 %)
+    gemm_timed = fused and args.cd_precision == "ozaki"
     dist.barrier()
     torch.cuda.synchronize()
     launches0 = G.cds_launch_count()
@@ -341,6 +356,13 @@ def run_ours(args, dist: Dist):
     dist.barrier()
     clk = clocks.stop()
     launches = G.cds_launch_count() - launches0
+    if gemm_timed:
+        G.cdsigma.cds_cd_gemm_timing(True)
+        for _ in range(args.steps):
+            step(xyz, al, at, C, eps, orbs, E, ws)
+        torch.cuda.synchronize()
+        gemm_ms, gemm_launches = G.cdsigma.cds_cd_gemm_time()
+        G.cdsigma.cds_cd_gemm_timing(False)
     elapsed_ms = t0.elapsed_time(t1)
     for ev in evs:
         for k, (a, b) in zip(stage_ms, [(0, 1), (1, 2), (2, 3), (3, 4)]):
@@ -376,7 +398,7 @@ def run_ours(args, dist: Dist):
     # ---- rooflines (per call, CUDA events on the launching stream) ----
     fm = flops_model(m, M)
     cd_stats = G.cdsigma.cds_cd_stats(m.nbf, fz_ws if fused else cd_ws,
-                                      "f32x2" if tr_prec != "fp64" else "fp64")
+                                      args.cd_precision if tr_prec != "fp64" else "fp64")
     cd_bytes = float(npr) * (8.0 * cd_stats["streamed"] + 8.0 * cd_stats["extra"] +
                              32.0 * cd_stats["passes"] + 89.0 * M)
     pk = peaks()
@@ -427,7 +449,47 @@ def run_ours(args, dist: Dist):
                       "peak": pk["bf16_tflops"] if prec != "fp64" else pk["fp64_tflops"],
                       "achieved": sig_flops_qp / (med["qp"] / 1e3) / 1e12,
                       "note": f"{sig_passes_qp} Sigma passes (nE=1); {split} split products per MAC"}
-    if fused:
+    if fused and gemm_timed:
+        # one stage for both: the decomposition's HBM bytes (slice store read by
+        # the passes, the float-pair extras, the per-step column / vector /
+        # residual traffic); the transform runs on the tensor pipe beside it
+        stage_bytes = float(npr) * (16.0 * cd_stats["streamed"] + 8.0 * cd_stats["extra"] +
+                                    89.0 * M)
+        med["cd_transform"] = med.pop("cd")
+        med.pop("transform")
+        roof.pop("cd")
+        roof.pop("transform")
+        roof["cd_transform"] = {
+            "bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
+            "achieved": stage_bytes / (med["cd_transform"] / 1e3) / 1e9,
+            "note": (f"pipelined decomposition (tensor-core passes) + exact-slice transform: "
+                     f"bytes = npair*(16*streamed + 8*extra + 89*M) ({cd_stats['passes']} "
+                     f"passes, {cd_stats['streamed']} vectors streamed, {cd_stats['extra']} "
+                     f"extra); the transform's slice-pair GEMMs run on the tensor pipe beside it"),
+            "cd_stats": cd_stats}
+        # the dominant kernel: k_cd_gemm_tc, per launch.  Algorithmic bytes of
+        # a decomposition: the slice store (8 BF16 slices = 16 bytes per pair
+        # and stored vector) read once per pass, the candidates' slices
+        # (16 bytes x 32 per vector), the projections written (32 float pairs
+        # = 256 bytes per pair) and the pair scales read (4 bytes per pair) at
+        # every pass with k0 > 0
+        gemm_bytes = (16.0 * npr * cd_stats["streamed"] + 512.0 * cd_stats["streamed"] +
+                      260.0 * npr * max(cd_stats["passes"] - 1, 0))
+        per_launch = gemm_bytes * args.steps / max(gemm_launches, 1)
+        avg_ms = gemm_ms / max(gemm_launches, 1)
+        roof["cd_gemm"] = {
+            "bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
+            "achieved": per_launch / (avg_ms / 1e3) / 1e9,
+            "kernel": "k_cd_gemm_tc", "launches": gemm_launches, "ms_total": gemm_ms,
+            "bytes_per_launch": per_launch,
+            "note": (f"k_cd_gemm_tc (tcgen05 exact-slice projections of the decomposition's "
+                     f"streaming passes) in {args.steps} more steps of the same pipeline after "
+                     f"the timed ones: {gemm_launches} launches, CUDA events around each on its "
+                     f"stream (early returns of the steps that start no pass included); bytes "
+                     f"per decomposition = npair*(16*streamed + 260*(passes-1)) + 512*streamed "
+                     f"({cd_stats['passes']} passes, {cd_stats['streamed']} vectors streamed)"),
+            "cd_stats": cd_stats}
+    elif fused:
         # one stage for both.  The decomposition is bound by FP32 instruction
         # issue (12 FP32 instructions per float-pair multiply-add in the
         # projections); the float-pair transform adds 11 per multiply-add on
@@ -452,7 +514,7 @@ def run_ours(args, dist: Dist):
                                           "tensor pipe beside them") +
                      "; peak = 152 SMs x 128 FP32 lanes x 2.07 GHz"),
             "cd_stats": cd_stats}
-    if fused:
+    if fused and not gemm_timed:
         # the dominant kernels (k_cd_project_spec + k_cd_update, 62 % of the
         # step's launch list) timed alone: one float-pair decomposition on the
         # current stream, the one it launches on, bracketed by CUDA events
@@ -462,20 +524,28 @@ def run_ours(args, dist: Dist):
             torch.cuda.synchronize()
             a0.record()
             G.cds_cd_decompose(xyz, al, at, args.delta, args.scheme, L_out=Lbuf, workspace=cd_ws,
-                               precision="f32x2")
+                               precision=args.cd_precision)
             a1.record()
             torch.cuda.synchronize()
             cd_alone.append(a0.elapsed_time(a1))
         t_cd = min(cd_alone)
-        cd_instr = (12.0 * 4 * cd_stats["streamed"] + 12.0 * cd_stats["extra"]) * npr
+        # the method's own work: the left-looking projections, npair M(M-1)/2
+        # float-pair multiply-adds of 12 FP32 instructions each (the speculative
+        # candidates' extra projections are not counted)
+        cd_instr = 12.0 * npr * M * (M - 1) / 2.0
+        spec_instr = (12.0 * G.cdsigma.cd_candidates() * cd_stats["streamed"] +
+                      12.0 * cd_stats["extra"]) * npr
         roof["cd_kernels"] = {
             "bound": "alu", "unit": "T FP32 instr/s", "peak": pk["fp32_issue_tinstr"],
             "achieved": cd_instr / (t_cd / 1e3) / 1e12, "ms": t_cd,
+            "issued_incl_speculation_tinstr_s": spec_instr / (t_cd / 1e3) / 1e12,
             "note": (f"k_cd_project_spec + k_cd_update (float-pair decomposition, M = {M}) timed "
-                     f"alone after the timed steps (best of 2 calls): float-pair FMAs of the "
-                     f"projections, 12 FP32 instructions each ({cd_stats['passes']} streaming "
-                     f"passes, {cd_stats['streamed']} vectors streamed, 4 candidates); peak = "
-                     f"152 SMs x 128 FP32 lanes x 2.07 GHz"),
+                     f"alone after the timed steps (best of 2 calls) on the stream they launch "
+                     f"on; achieved = the method's npair*M(M-1)/2 float-pair multiply-adds x 12 "
+                     f"FP32 instructions / time ({cd_stats['passes']} streaming passes, "
+                     f"{cd_stats['streamed']} vectors streamed, "
+                     f"{G.cdsigma.cd_candidates()} candidates per pass); peak = 152 SMs x 128 "
+                     f"FP32 lanes x 2.07 GHz (unit counts and the maximum clock, not measured)"),
             "cd_stats": cd_stats}
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
@@ -484,48 +554,11 @@ def run_ours(args, dist: Dist):
     dominant = max(med, key=med.get)
     # the stage that dominates the step is the pipelined decomposition +
     # transform; the kernels that dominate it are the decomposition's
-    dominant_roof = "cd_kernels" if fused else dominant
-
-    # ---- FP64 GPU arm on a subset, and mixed-vs-FP64 accuracy ----
-    fp64 = None
-    if not args.no_fp64_arm and prec != "fp64":
-        sub = [n_orb // 2 - 1, n_orb // 2]        # HOMO, LUMO
-        subt = torch.tensor(sub, device=device)
-        torch.cuda.synchronize()
-        a = time.perf_counter()
-        s64, _ = G.cds_sigma2_diag(Lov, Lp[subt], eps, m.nocc, E[subt][:, :1], "fp64")
-        torch.cuda.synchronize()
-        t_pass64 = time.perf_counter() - a
-        a = time.perf_counter()
-        w64, P64, it64, st64 = G.cds_qp_solve(Lov, Lp[subt], orbs[subt], eps, m.nocc, conv=1e-5,
-                                              max_iter=50, precision="fp64")
-        torch.cuda.synchronize()
-        t_qp64 = time.perf_counter() - a
-        wm, Pm, itm, stm = G.cds_qp_solve(Lov, Lp[subt], orbs[subt], eps, m.nocc, conv=1e-5,
-                                          max_iter=50, precision=prec)
-        smix, _ = G.cds_sigma2_diag(Lov, Lp[subt], eps, m.nocc, E[subt][:, :1], prec)
-        torch.cuda.synchronize()
-        # FP64 self-energy stages for all 20 orbitals, scaled from the subset:
-        # one pass per orbital per energy chunk ~ t_pass64 / 2, Newton as measured
-        per_orb_grid64 = t_pass64 / len(sub)
-        fp64_stage_s = n_orb * per_orb_grid64 + t_qp64 / len(sub) * n_orb
-        mixed_stage_s = (med["sigma_grid"] + med["qp"]) / 1e3
-        fp64 = {
-            "orbitals": [int(m.orbitals[i]) for i in sub],
-            "qp_abs_err_meV": (np.abs(wm.cpu().numpy() - w64.cpu().numpy()) * HARTREE_EV * 1e3).tolist(),
-            "sigma_abs_err_meV": (np.abs(smix.cpu().numpy() - s64.cpu().numpy()).ravel()
-                                  * HARTREE_EV * 1e3).tolist(),
-            "fp64_sigma_pass_s_per_orbital": per_orb_grid64,
-            "fp64_qp_s_per_orbital": t_qp64 / len(sub),
-            "fp64_status": st64.cpu().tolist(), "mixed_status": stm.cpu().tolist(),
-            "note": "FP64 Sigma grid estimated at one pass per orbital (nE=1 cost; the 64-energy "
-                    "FP64 epilogue adds more), so the FP64 stage time is a lower bound",
-            "stage_solves_per_s": {"mixed": n_orb / mixed_stage_s,
-                                   "fp64_lower_bound": n_orb / fp64_stage_s},
-        }
+    dominant_roof = ("cd_gemm" if gemm_timed else "cd_kernels") if fused else dominant
 
     # ---- safeguarded Newton on the same numerators (quasiparticle roots) ----
     bracketed = None
+    wb = None
     if cached:
         torch.cuda.synchronize()
         a0 = time.perf_counter()
@@ -537,6 +570,16 @@ def run_ours(args, dist: Dist):
                      "note": "Newton kept inside the pole-free interval around each e_q "
                              "(cds_qp_solve_bracketed_cached): the quasiparticle root of every "
                              "orbital; wall time incl. the host-side bracket"}
+
+    # ---- the all-FP64 GPU step, measured once, and per-orbital accuracy ----
+    fp64 = None
+    if not args.no_fp64_arm and prec != "fp64":
+        fp64 = run_fp64_step(args, m, xyz, al, at, C, eps, orbs, E, Lov, Lp, w, wb, value, pk)
+
+    # ---- adjoint of the 8 orbitals around the gap (tensor cores) ----
+    adjoint = None
+    if not args.no_adjoint and prec != "fp64":
+        adjoint = run_adjoint(m, Lov, Lp, orbs, eps, wb if wb is not None else w, pk)
 
     # ---- MP2 correlation energy (Eq. MP2) on the same factors ----
     mp2 = None
@@ -577,7 +620,8 @@ def run_ours(args, dist: Dist):
         "gpu_launches": int(launches),
         "clocks": clk,
         "peaks": pk,
-        "fp64_arm": fp64,
+        "fp64_step": fp64,
+        "adjoint": adjoint,
         "mp2": mp2,
         "bracketed_newton": bracketed,
         "acd": acd,
@@ -589,6 +633,118 @@ def run_ours(args, dist: Dist):
         result["cpu_baseline"] = cpu_baseline(m, M, iters)
     dist.done()
     return result
+
+
+def run_fp64_step(args, m, xyz, al, at, C, eps, orbs, E, Lov_mx, Lp_mx, w_mx, wb_mx, value_mx,
+                  pk):
+    """One whole step of the method in FP64 on the GPU, timed stage by stage
+    with CUDA events on the stream the calls launch on: FP64 decomposition
+    (same delta and scheme), FP64 transform, the Sigma grid (64 energies) in
+    FP64 keeping the FP64 numerators, and Newton from them (plain, as in the
+    timed step; the safeguarded roots follow, untimed).  Per orbital, the
+    quasiparticle energies of the split-precision forms (the timed step's
+    BF16X3, and TF32X3 on the same factors) against these FP64 ones."""
+    import torch
+    import paper_0912_1459_gb300 as G
+
+    n_orb = len(m.orbitals)
+    dev = eps.device
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    L, piv, D, de = G.cds_cd_decompose(xyz, al, at, args.delta, args.scheme, precision="fp64",
+                                       max_rank=2048 if args.delta >= 1e-5 else 4096)
+    ev[1].record()
+    Lov, Lp = G.cds_cd_to_mo(L, C, m.nocc, orbs, precision="fp64")
+    ev[2].record()
+    sig, dsig, cache64 = G.cds_sigma2_diag_cache(Lov, Lp, eps, m.nocc, E, "fp64")
+    ev[3].record()
+    w, P, it, st = G.cds_qp_solve_cached(cache64, orbs, eps, m.nbf, m.nocc, conv=1e-5, max_iter=50,
+                                         precision="fp64")
+    ev[4].record()
+    torch.cuda.synchronize()
+    stages = {k: ev[i].elapsed_time(ev[i + 1])
+              for i, k in enumerate(("cd", "transform", "sigma_grid", "qp"))}
+    total_ms = sum(stages.values())
+    wb, Pb, _, stb, _ = G.cds_qp_solve_bracketed_cached(cache64, orbs, eps, m.nbf, m.nocc,
+                                                        precision="fp64")
+    w64, P64, st64 = w.cpu().numpy(), P.cpu().numpy(), st.cpu().numpy()
+    wb64 = wb.cpu().numpy()
+    qp = (st64 == 0) & (P64 >= 0.5)
+    mev = lambda x: (np.abs(x) * HARTREE_EV * 1e3).tolist()  # noqa: E731
+    forms = {}
+    # the timed step's own results (BF16X3 on its float-pair / exact-slice factors)
+    e_plain = np.asarray(w_mx.cpu().numpy()) - w64
+    forms[args.precision + " (timed step)"] = {
+        "plain_newton_abs_err_meV": mev(e_plain),
+        "max_over_qp_poles_meV": float(np.max(np.abs(e_plain[qp])) * HARTREE_EV * 1e3) if qp.any() else None,
+        "bracketed_abs_err_meV": mev(wb_mx.cpu().numpy() - wb64) if wb_mx is not None else None}
+    # TF32X3 on the same factors: Sigma grid keeping numerators, Newton from them
+    for p2 in ("tf32x3",):
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a0.record()
+        _, _, cache2 = G.cds_sigma2_diag_cache(Lov_mx, Lp_mx, eps, m.nocc, E, p2)
+        w2, P2, _, st2 = G.cds_qp_solve_cached(cache2, orbs, eps, m.nbf, m.nocc, conv=1e-5,
+                                               max_iter=50, precision=p2)
+        a1.record()
+        torch.cuda.synchronize()
+        wb2 = G.cds_qp_solve_bracketed_cached(cache2, orbs, eps, m.nbf, m.nocc, precision=p2)[0]
+        e2 = w2.cpu().numpy() - w64
+        forms[p2] = {"sigma_grid_plus_newton_ms": a0.elapsed_time(a1),
+                     "plain_newton_abs_err_meV": mev(e2),
+                     "max_over_qp_poles_meV": float(np.max(np.abs(e2[qp])) * HARTREE_EV * 1e3) if qp.any() else None,
+                     "bracketed_abs_err_meV": mev(wb2.cpu().numpy() - wb64)}
+        del cache2
+    del cache64
+    v64 = n_orb / (total_ms / 1e3)
+    return {"stages_ms": stages, "ms": total_ms, "solves_per_s": v64,
+            "mixed_over_fp64": value_mx / v64, "cholesky_rank": int(L.shape[0]),
+            "orbitals": [int(q) for q in m.orbitals], "fp64_pole": P64.tolist(),
+            "fp64_status": st64.tolist(), "fp64_bracketed_status": stb.cpu().tolist(),
+            "qp_poles": int(qp.sum()), "forms": forms,
+            "note": "measured once after the timed steps: FP64 CD + FP64 transform + FP64 Sigma "
+                    "grid (64 energies, numerators kept) + FP64 Newton from them; errors per "
+                    "orbital against it, plain Newton (Eq. iter) and safeguarded roots; "
+                    "max_over_qp_poles covers the orbitals whose FP64 root has P >= 0.5"}
+
+
+def run_adjoint(m, Lov, Lp, orbs, eps, omega, pk, reps: int = 3):
+    """The hand-written adjoint (cds_qp_gradient, BF16X3 tensor cores) for the
+    8 orbitals around the gap (HOMO-3 .. LUMO+3) at the given roots: CUDA-event
+    time of one call after a warm-up, and the rate of its tensor work."""
+    import torch
+    import paper_0912_1459_gb300 as G
+
+    n_orb = len(m.orbitals)
+    mid = n_orb // 2
+    sel = torch.arange(mid - 4, mid + 4, device=Lp.device)
+    Lp8 = Lp[sel].contiguous()
+    o8, w8 = orbs[sel].contiguous(), omega[sel].contiguous()
+    g = torch.ones(8, dtype=torch.float64, device=Lp.device)
+    G.cdsigma.cds_qp_gradient(Lov, Lp8, o8, eps, m.nocc, w8, g, "bf16x3")
+    ms = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        G.cdsigma.cds_qp_gradient(Lov, Lp8, o8, eps, m.nocc, w8, g, "bf16x3")
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    o, v, M = Lov.shape
+    # per orbital: X (both sums), dLq and dLov GEMMs, each 2 M (o v)(o + v) MACs-as-flops,
+    # 3 split products
+    flops = 8 * 3 * 3 * 2.0 * M * (o * v) * (o + v)
+    ach = flops / (t / 1e3) / 1e12
+    return {"orbitals": [int(q) for q in o8.cpu().tolist()], "precision": "bf16x3", "ms": t,
+            "roofline": {"bound": "tensor", "unit": "TFLOP/s", "achieved": ach,
+                         "peak": pk["bf16_tflops"], "frac": ach / pk["bf16_tflops"],
+                         "note": "3 GEMMs per orbital (X, dLq, dLov), 2 M (o v)(o+v) flops each, "
+                                 "x 3 split products; of measured burst BF16 peak"},
+            "note": "d(eps, Lov, Lp) of sum_t w_t at the safeguarded roots; the G pass, "
+                    "splits and transposes included in the time"}
 
 
 def run_mp2(m, Lov, eps, prec, pk, reps: int = 3):
@@ -810,9 +966,14 @@ def oracle_sample(m, M_full: int, iters_per_orbital: float, n_cd=(24, 48), n_tr=
             "stage_s_estimate": {"cd": t_cd, "transform": t_tr, "sigma_grid": t_grid, "qp": t_qp}}
 
 
+# One sample size for both oracle legs (cpu_baseline here, the reference arm's
+# steps), so that they model the same step from the same measurements.
+ORACLE_SAMPLE = {"n_cd": (32, 64), "n_tr": 4}
+
+
 def cpu_baseline(m, M, iters):
-    # ~15 s of oracle work on 8-16 host cores
-    return oracle_sample(m, M, float(np.mean(iters)), n_cd=(128, 256), n_tr=8)
+    # ~10-20 s of oracle work on the host cores
+    return oracle_sample(m, M, float(np.mean(iters)), **ORACLE_SAMPLE)
 
 
 def run_reference(args, dist: Dist):
@@ -825,17 +986,17 @@ def run_reference(args, dist: Dist):
     for _ in range(args.warmup):
         oracle_sample(m, M_full, iters, n_cd=(4, 8), n_tr=1)
     vals, walls = [], []
-    a = time.perf_counter()
     for _ in range(args.steps):
-        s = oracle_sample(m, M_full, iters, n_cd=(8, 16), n_tr=2)
+        s = oracle_sample(m, M_full, iters, **ORACLE_SAMPLE)
         vals.append(s["value"])
         walls.append(s["sample_wall_s"])
-    wall = time.perf_counter() - a
     value = float(np.median(vals))
     cb = {"value": value, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
-          "sample": s["sample"]}
+          "sample": s["sample"] + f"; sample wall time {np.median(walls):.1f} s per step"}
+    # ms_per_step: the modelled time of one whole step (20 solves / value),
+    # not the wall time of the bounded sample
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / args.steps * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 20.0 / value * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "delta": args.delta, "scheme": args.scheme,

@@ -197,6 +197,41 @@ int cds_cd_candidates(int32_t precision);
  * F32X2 for any max_rank). */
 size_t cds_cd_workspace_bytes_prec(int32_t nbf, int32_t max_rank, int32_t precision);
 
+/* Kernel timing of the OZAKI decomposition's projection GEMM (the tcgen05
+ * kernel that forms a pass's candidate projections; Eq. gs_coulomb).  While
+ * enabled, every cds_cd_decompose / cds_cd_decompose_to_mo with
+ * CDS_PREC_OZAKI records a CUDA event pair around each GEMM launch on the
+ * stream the launch uses (not under stream capture) and adds the elapsed
+ * times of the steps that ran to process-wide totals.  The GEMM is enqueued
+ * at every step and returns at once unless the step starts a pass, so the
+ * totals include those early returns.  cds_cd_gemm_timing(enable) switches it
+ * and clears the totals; cds_cd_gemm_time reads them (*ms summed, *launches
+ * counted).  Host only; not for concurrent decompositions.  Returns CDS_OK
+ * (CDS_ERR_ARG on a NULL pointer). */
+int cds_cd_gemm_timing(int32_t enable);
+int cds_cd_gemm_time(double* ms, int64_t* launches);
+
+/* ------------------------------------------------------------------------
+ * The decomposition over contracted Cartesian Gaussian shells (the paper's
+ * basis sets are contracted shells with higher angular momentum, Sec. III;
+ * Eq. integral is the same Coulomb integral over their products).  Basis
+ * function f (device arrays): centre xyz[f][3], Cartesian exponents
+ * lmn[f][3] with l + m + n <= 2 (s, p, Cartesian d), primitives
+ * [start[f], start[f+1]) of exps[] / coefs[] (the coefficients carry the
+ * function's normalisation): chi_f = sum_k coefs[k] x^l y^m z^n exp(-exps[k] r^2)
+ * about its centre.  Integrals: McMurchie-Davidson (Hermite expansion and
+ * Hermite Coulomb integrals) in FP64, one thread per pair; the pivot rule,
+ * stop rule, candidate sets, outputs and errors are those of
+ * cds_cd_decompose (precision FP64; workspace cds_cd_workspace_bytes).
+ * CDS_ERR_UNSUPPORTED for a function beyond d.  Blocking.
+ * ---------------------------------------------------------------------- */
+int cds_cd_decompose_shells(int32_t nbf, const double* xyz, const int32_t* lmn,
+                            const int32_t* start, const double* exps, const double* coefs,
+                            const int32_t* atom, double delta, int32_t scheme, int32_t max_rank,
+                            double* L, int32_t* piv, double* D, int32_t* M_out,
+                            double* delta_eff_out, void* workspace, size_t workspace_bytes,
+                            cudaStream_t stream);
+
 /* ------------------------------------------------------------------------
  * Allocation-free Cholesky decomposition.  The paper has no counterpart: this
  * is a service for callers that cannot allocate device memory where they call

@@ -46,6 +46,11 @@ _SIGNATURES = {
                                                _vp]),
     "cds_cd_static_max_nbf": (ctypes.c_int, []),
     "cds_cd_candidates": (ctypes.c_int, [_i32]),
+    "cds_cd_gemm_timing": (ctypes.c_int, [_i32]),
+    "cds_cd_gemm_time": (ctypes.c_int, [ctypes.POINTER(_f64), ctypes.POINTER(ctypes.c_int64)]),
+    "cds_cd_decompose_shells": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _vp, _vp, _f64, _i32, _i32,
+                                               _vp, _vp, _vp, ctypes.POINTER(_i32),
+                                               ctypes.POINTER(_f64), _vp, _sz, _vp]),
     "cds_cd_workspace_bytes_prec": (_sz, [_i32, _i32, _i32]),
     "cds_cd_to_mo_workspace_bytes": (_sz, [_i32, _i32, _i32, _i32, _i32]),
     "cds_cd_to_mo": (ctypes.c_int, [_i32, _i32, _i32, _i32, _vp, _vp, _vp, _i32, _i32, _vp, _vp,
@@ -358,6 +363,50 @@ def cds_cd_stats(nbf: int, workspace: torch.Tensor, precision: str = "fp64") -> 
                             ctypes.byref(st_), ctypes.byref(ex), _stream(workspace.device)),
            "cds_cd_stats")
     return {"passes": p.value, "streamed": st_.value, "extra": ex.value}
+
+
+def cds_cd_decompose_shells(xyz: torch.Tensor, lmn: torch.Tensor, start: torch.Tensor,
+                            exps: torch.Tensor, coefs: torch.Tensor, atom: torch.Tensor,
+                            delta: float, scheme: str = "full", max_rank: Optional[int] = None):
+    """The decomposition over contracted Cartesian shells (FP64).
+
+    Returns (L [M, npair], piv [M] int32, D [npair], delta_eff)."""
+    lib = load()
+    xyz = _dev(xyz, torch.float64, "xyz")
+    lmn = _dev(lmn, torch.int32, "lmn")
+    start = _dev(start, torch.int32, "start")
+    exps = _dev(exps, torch.float64, "exps")
+    coefs = _dev(coefs, torch.float64, "coefs")
+    atom = _dev(atom, torch.int32, "atom")
+    dev = xyz.device
+    n = lmn.shape[0]
+    npr = npair(n)
+    if max_rank is None:
+        max_rank = default_max_rank(n)
+    L = torch.empty((max(max_rank, 1), npr), dtype=torch.float64, device=dev)
+    piv = torch.empty(max(max_rank, 1), dtype=torch.int32, device=dev)
+    D = torch.empty(npr, dtype=torch.float64, device=dev)
+    ws = _workspace(lib.cds_cd_workspace_bytes(n), dev)
+    M, de = _i32(0), _f64(0.0)
+    st = lib.cds_cd_decompose_shells(n, _p(xyz), _p(lmn), _p(start), _p(exps), _p(coefs),
+                                     _p(atom), float(delta), SCHEMES[scheme], int(max_rank),
+                                     _p(L), _p(piv), _p(D), ctypes.byref(M), ctypes.byref(de),
+                                     _p(ws), ws.numel(), _stream(dev))
+    _check(st, "cds_cd_decompose_shells")
+    return L[:M.value], piv[:M.value], D, de.value
+
+
+def cds_cd_gemm_timing(enable: bool) -> None:
+    """Switch the event timing of the OZAKI decomposition's projection GEMM
+    (every launch, on its stream) and clear its totals."""
+    _check(load().cds_cd_gemm_timing(1 if enable else 0), "cds_cd_gemm_timing")
+
+
+def cds_cd_gemm_time() -> tuple[float, int]:
+    """(milliseconds summed, launches) of the GEMM since timing was switched."""
+    ms, n = _f64(0.0), ctypes.c_int64(0)
+    _check(load().cds_cd_gemm_time(ctypes.byref(ms), ctypes.byref(n)), "cds_cd_gemm_time")
+    return ms.value, n.value
 
 
 def cd_candidates(precision: str = "f32x2") -> int:

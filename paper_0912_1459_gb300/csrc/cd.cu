@@ -84,13 +84,19 @@ __device__ bool last_block(unsigned int* counter, int nblk) {
 __device__ void cd_init_body(PairSoA pd, const int32_t* __restrict__ atom, int32_t scheme,
                              int64_t n, double delta, double* __restrict__ D,
                              uint8_t* __restrict__ cand, double* __restrict__ blk_a,
-                             double* __restrict__ blk_b, CdCtrl* ctrl, int bid, int nblk) {
+                             double* __restrict__ blk_b, CdCtrl* ctrl, int bid, int nblk,
+                             bool given = false) {
     double mx_all = -INFINITY, mx_cand = -INFINITY;
     for (int64_t I = bid * (int64_t)blockDim.x + threadIdx.x; I < n;
          I += (int64_t)nblk * blockDim.x) {
-        double p = pd.p[I], px = pd.Px[I], py = pd.Py[I], pz = pd.Pz[I], k = pd.Kp[I];
-        double d = eri_pair(p, px, py, pz, k, p, px, py, pz, k);
-        D[I] = d;
+        double d;
+        if (given) {   // the diagonal was made by another integral kernel (contracted shells)
+            d = D[I];
+        } else {
+            double p = pd.p[I], px = pd.Px[I], py = pd.Py[I], pz = pd.Pz[I], k = pd.Kp[I];
+            d = eri_pair(p, px, py, pz, k, p, px, py, pz, k);
+            D[I] = d;
+        }
         uint8_t c = 1;
         if (scheme == CDS_SCHEME_ATOMIC) {
             int32_t mu, nu;
@@ -126,8 +132,10 @@ __device__ void cd_init_body(PairSoA pd, const int32_t* __restrict__ atom, int32
 
 __global__ void k_cd_init(PairSoA pd, const int32_t* __restrict__ atom, int32_t scheme, int64_t n,
                           double delta, double* __restrict__ D, uint8_t* __restrict__ cand,
-                          double* __restrict__ blk_a, double* __restrict__ blk_b, CdCtrl* ctrl) {
-    cd_init_body(pd, atom, scheme, n, delta, D, cand, blk_a, blk_b, ctrl, blockIdx.x, gridDim.x);
+                          double* __restrict__ blk_a, double* __restrict__ blk_b, CdCtrl* ctrl,
+                          int given = 0) {
+    cd_init_body(pd, atom, scheme, n, delta, D, cand, blk_a, blk_b, ctrl, blockIdx.x, gridDim.x,
+                 given != 0);
 }
 
 // Pivot for vector k (k vectors already made): stop test, rank cap, then the
@@ -428,9 +436,10 @@ __device__ __forceinline__ void cd_spec_dot_body(int64_t n, int32_t k,
 // is kept, besides its float pair in L, as a 56-bit fixed-point number below
 // the pair's scale sigma_I = 2^e_I > sqrt(D0_I) >= |L^K_I| (the residual
 // matrix stays positive semidefinite, so sum_K (L^K_I)^2 <= D0_I), cut into
-// eight 7-bit digits held as exact BF16 slices in a K-major store
-// [slice][pair][kcap]; a streaming pass multiplies the store with the
-// candidates' rows on the tensor cores (cd_tc.cu).
+// eight 7-bit digits held as exact BF16 slices in a store blocked by
+// 32-column groups, [group][slice][pair][32] (one group's tile of 128 pairs
+// is 8 KB of contiguous memory per slice); a streaming pass multiplies the
+// store with the candidates' rows on the tensor cores (cd_tc.cu).
 // ---------------------------------------------------------------------------
 __global__ void k_cd_tc_scales(const double* __restrict__ D, int64_t n, float* __restrict__ sig) {
     const int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -460,11 +469,15 @@ __device__ __forceinline__ void tc_slices(float2 x, int e, uint16_t (&out)[kSlic
 }
 
 // Eight consecutive columns K0.. K0+7 (zero at K >= k) of one row of L, sliced
-// with exponent e, stored as one 16-byte segment per slice plane.
+// with exponent e, stored as one 16-byte segment per slice: row `row` of a
+// group-blocked store [group][slice][rows][kGroupTC].
 __device__ __forceinline__ void tc_store8(const float2* __restrict__ Lf, int64_t n, int64_t I,
                                           int32_t K0, int32_t k, int e,
-                                          __nv_bfloat16* __restrict__ planes, int64_t plane,
-                                          int64_t off) {
+                                          __nv_bfloat16* __restrict__ store, int64_t rows,
+                                          int64_t row) {
+    const int64_t plane = rows * kGroupTC;
+    const int64_t off = ((int64_t)(K0 / kGroupTC) * kSlicesTC * rows + row) * kGroupTC +
+                        K0 % kGroupTC;
     uint32_t w[kSlicesTC][4];
 #pragma unroll
     for (int j = 0; j < 8; j += 2) {
@@ -479,7 +492,7 @@ __device__ __forceinline__ void tc_store8(const float2* __restrict__ Lf, int64_t
     }
 #pragma unroll
     for (int s = 0; s < kSlicesTC; ++s)
-        *reinterpret_cast<uint4*>(planes + s * plane + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
+        *reinterpret_cast<uint4*>(store + s * plane + off) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
 }
 
 // Order-preserving map of binary64 values to int64 (its own inverse), so the
@@ -573,6 +586,37 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
         }
     }
     long long mx_i = LLONG_MAX;   // SPEC: lowest index holding the block's candidate maximum
+    // TC: the pass's projection plus the vectors made since, for this thread's
+    // pairs, with four rows of L in flight per pair (the rows are a batch's
+    // worth of recent vectors, up to 63 of them)
+    float2 accTC[kStepPer];
+    if constexpr (TC) {
+        const float2* Lf = reinterpret_cast<const float2*>(L);
+#pragma unroll
+        for (int r = 0; r < kStepPer; ++r) {
+            const int64_t I = base + r * kUpdThreads + threadIdx.x;
+            accTC[r] = (k0 > 0 && I < n) ? Gs[I] : make_float2(0.f, 0.f);   // nothing precedes step 0
+        }
+        constexpr int kDepth = 4;
+        for (int i0 = 0; i0 < extra; i0 += kDepth) {
+            float2 v[kStepPer][kDepth];
+#pragma unroll
+            for (int r = 0; r < kStepPer; ++r) {
+                const int64_t I = base + r * kUpdThreads + threadIdx.x;
+#pragma unroll
+                for (int j = 0; j < kDepth; ++j)
+                    v[r][j] = (I < n && i0 + j < extra) ? Lf[(int64_t)(k0 + i0 + j) * n + I]
+                                                        : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < kDepth; ++j)
+                if (i0 + j < extra) {
+                    const float2 lp = s_lp[i0 + j];
+#pragma unroll
+                    for (int r = 0; r < kStepPer; ++r) df_fma(accTC[r], v[r][j], lp);
+                }
+        }
+    }
 #pragma unroll
     for (int r = 0; r < kStepPer; ++r) {
         const int64_t I = base + r * kUpdThreads + threadIdx.x;
@@ -584,8 +628,7 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
                 const float2* Lf = reinterpret_cast<const float2*>(L);
                 float2 acc;
                 if constexpr (TC) {
-                    acc = k0 > 0 ? Gs[I] : make_float2(0.f, 0.f);   // nothing precedes step 0
-                    for (int i = 0; i < extra; ++i) df_fma(acc, Lf[(int64_t)(k0 + i) * n + I], s_lp[i]);
+                    acc = accTC[r];
                 } else {
                     acc = Gs[I];
 #pragma unroll
@@ -827,14 +870,13 @@ __global__ void __launch_bounds__(kUpdThreads, 4)
 k_cd_project_tc(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __restrict__ L,
                 float2* __restrict__ ecol, const float* __restrict__ sigA,
                 __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B,
-                float* __restrict__ sigB, int32_t kcap, const CdCtrl* ctrl) {
+                float* __restrict__ sigB, const CdCtrl* ctrl) {
     if (ctrl->done) return;
     cd_eri_body_df(pd, pf, n, ctrl, ecol, blockIdx.x, gridDim.x);
     if (ctrl->pass == 0 || k == 0) return;
     const float2* Lf = reinterpret_cast<const float2*>(L);
     const int32_t kd = ctrl->kdone;
     const int32_t kend = (k + kGroupTC - 1) / kGroupTC * kGroupTC;
-    const int64_t planeA = n * (int64_t)kcap, planeB = (int64_t)kSpecTC * kcap;
     const int q8 = kGroupTC / 8;   // 16-byte segments per group and plane
     // A: items (group, pair, segment), segment fastest, so a warp writes whole rows
     const int64_t itemsA = (int64_t)((kend - kd) / kGroupTC) * n * q8;
@@ -849,7 +891,7 @@ k_cd_project_tc(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __res
             const int32_t K0 = kd + (int32_t)(r / n) * kGroupTC + seg * 8;
             int e = 0;
             frexpf(sigA[I], &e);   // sigma = 2^(e-1)
-            tc_store8(Lf, n, I, K0, k, e - 1, A, planeA, I * kcap + K0);
+            tc_store8(Lf, n, I, K0, k, e - 1, A, n, I);
         } else {
             const int64_t r = it - itemsA;
             const int c = (int)(r % kSpecTC);
@@ -858,15 +900,16 @@ k_cd_project_tc(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __res
             const float sg = Sc >= 0 ? sigA[Sc] : 1.f;
             int e = 0;
             frexpf(sg, &e);
-            tc_store8(Lf, n, Sc >= 0 ? Sc : -1, K0, k, e - 1, B, planeB, (int64_t)c * kcap + K0);
+            tc_store8(Lf, n, Sc >= 0 ? Sc : -1, K0, k, e - 1, B, kSpecTC, c);
             if (K0 == 0) sigB[c] = sg;
         }
     }
 }
 
-// Step k, part 2: vector k, residuals, next pivot.
+// Step k, part 2: vector k, residuals, next pivot.  Five blocks per SM keep
+// the C60-shaped grid (690 blocks of 512 pairs) in one wave.
 template <bool DF, bool SPEC, bool TC = false>
-__global__ void __launch_bounds__(kUpdThreads)
+__global__ void __launch_bounds__(kUpdThreads, 5)
 k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
             double* __restrict__ D, const uint8_t* __restrict__ cand,
             const double* __restrict__ ecol, const float2* __restrict__ G,
@@ -893,8 +936,8 @@ struct CdLayout {
     double* ecol;     // integral column of the current step
     float2* G;        // [kSpec][npair] candidate projections (float-pair mode; [kSpecTC] in TC)
     // exact-slice tensor-core form
-    __nv_bfloat16* A; // slice store [kSlicesTC][npair][kcap]
-    __nv_bfloat16* B; // candidate rows [kSlicesTC][kSpecTC][kcap]
+    __nv_bfloat16* A; // slice store [kcap / kGroupTC][kSlicesTC][npair][kGroupTC]
+    __nv_bfloat16* B; // candidate rows [kcap / kGroupTC][kSlicesTC][kSpecTC][kGroupTC]
     float* sigA;      // [npair] pair scales
     float* sigB;      // [kSpecTC] candidate scales
     int32_t* err;     // the GEMM's bounded-wait error word
@@ -1019,6 +1062,15 @@ extern "C" int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precisio
 
 namespace cds {
 
+// Timing of the tensor-core projection GEMM (cds_cd_gemm_timing): process-wide
+// totals over the launches made while it is on.
+struct GemmTiming {
+    bool on = false;
+    double ms = 0.0;
+    long long launches = 0;
+};
+static GemmTiming g_gemm_timing;
+
 // The decomposition of cds_cd_decompose.  on_chunk (may be null) runs after
 // every host check with the number of rows of L that are final and whether
 // the decomposition has stopped; before the float-pair rows are converted to
@@ -1074,6 +1126,22 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
                               lay.ctrl, lay.err);
         if (st) return st;
     }
+    // CUDA events around every GEMM launch of the steps that run (one pair per
+    // step of a host-check chunk, reused), summed after each check
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CDS_CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
+    const bool timing = tcm && g_gemm_timing.on && cap == cudaStreamCaptureStatusNone;
+    std::vector<cudaEvent_t> tev;
+    struct EventGuard {
+        std::vector<cudaEvent_t>& v;
+        ~EventGuard() { for (cudaEvent_t e : v) cudaEventDestroy(e); }
+    } tev_guard{tev};
+    if (timing)
+        for (int i = 0; i < 2 * kHostCheckEvery; ++i) {
+            cudaEvent_t e;
+            CDS_CUDA_TRY(cudaEventCreate(&e));
+            tev.push_back(e);
+        }
     CdCtrl h{};
     for (int32_t k0 = 0; k0 <= max_rank; k0 += kHostCheckEvery) {
         int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
@@ -1081,10 +1149,12 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
             if (tcm) {
                 k_cd_project_tc<<<nres, kUpdThreads, 0, stream>>>(
                     lay.pd, lay.pf, n, k, L, reinterpret_cast<float2*>(lay.ecol), lay.sigA, lay.A,
-                    lay.B, lay.sigB, lay.kcap, lay.ctrl);
+                    lay.B, lay.sigB, lay.ctrl);
                 CDS_CUDA_TRY(cudaGetLastError());
+                if (timing) CDS_CUDA_TRY(cudaEventRecord(tev[2 * (k - k0)], stream));
                 st = cd_tc_gemm_launch(gemm, stream);
                 if (st) return st;
+                if (timing) CDS_CUDA_TRY(cudaEventRecord(tev[2 * (k - k0) + 1], stream));
                 k_cd_update<true, true, true><<<nu, kUpdThreads, 0, stream>>>(
                     n, k, max_rank, L, D, lay.cand, lay.ecol, lay.G, lay.blk_a, lay.blk_b,
                     lay.blk_i, piv, lay.ctrl);
@@ -1103,10 +1173,19 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
                     lay.blk_i, piv, lay.ctrl);
             }
         }
-        count_launches(2ull * (unsigned long long)(k1 - k0));
+        count_launches((tcm ? 3ull : 2ull) * (unsigned long long)(k1 - k0));
         CDS_CUDA_TRY(cudaGetLastError());
         CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, stream));
         CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (timing) {   // the steps that ran (k < M once the decomposition has stopped)
+            const int32_t kr = h.done ? std::min(k1, h.M) : k1;
+            for (int32_t k = k0; k < kr; ++k) {
+                float ms = 0.f;
+                CDS_CUDA_TRY(cudaEventElapsedTime(&ms, tev[2 * (k - k0)], tev[2 * (k - k0) + 1]));
+                g_gemm_timing.ms += ms;
+                ++g_gemm_timing.launches;
+            }
+        }
         if (on_chunk && *on_chunk) {
             st = (*on_chunk)(h.done ? h.M : k1, h.done != 0);
             if (st) return st;
@@ -1147,6 +1226,91 @@ extern "C" int cds_cd_decompose(int32_t nbf, const double* xyz, const double* al
     return cds::cd_decompose_run(nbf, xyz, alpha, atom, delta, scheme, max_rank, precision, L,
                                  piv, D, M_out, delta_eff_out, workspace, workspace_bytes, stream,
                                  nullptr, nullptr);
+}
+
+extern "C" int cds_cd_gemm_timing(int32_t enable) {
+    cds::g_gemm_timing.on = enable != 0;
+    cds::g_gemm_timing.ms = 0.0;
+    cds::g_gemm_timing.launches = 0;
+    return CDS_OK;
+}
+
+extern "C" int cds_cd_gemm_time(double* ms, int64_t* launches) {
+    if (!ms || !launches) return CDS_ERR_ARG;
+    *ms = cds::g_gemm_timing.ms;
+    *launches = cds::g_gemm_timing.launches;
+    return CDS_OK;
+}
+
+namespace cds {
+int shell_diag(int32_t nbf, const double* xyz, const int32_t* lmn, const int32_t* start,
+               const double* exps, const double* coefs, double* D, cudaStream_t stream);
+int shell_column(int32_t nbf, const double* xyz, const int32_t* lmn, const int32_t* start,
+                 const double* exps, const double* coefs, const int64_t* P, const int32_t* done,
+                 double* ecol, cudaStream_t stream);
+}  // namespace cds
+
+// The same decomposition over contracted Cartesian shells (FP64): the
+// diagonal and the columns come from the contracted-shell integral kernels
+// (shells.cu), the projections, updates and pivot rule are the s-type ones.
+extern "C" int cds_cd_decompose_shells(int32_t nbf, const double* xyz, const int32_t* lmn,
+                                       const int32_t* start, const double* exps,
+                                       const double* coefs, const int32_t* atom, double delta,
+                                       int32_t scheme, int32_t max_rank, double* L, int32_t* piv,
+                                       double* D, int32_t* M_out, double* delta_eff_out,
+                                       void* workspace, size_t workspace_bytes,
+                                       cudaStream_t stream) {
+    if (nbf <= 0 || !xyz || !lmn || !start || !exps || !coefs || !L || !piv || !D || !M_out ||
+        max_rank < 0 || !(delta >= 0.0))
+        return CDS_ERR_ARG;
+    if (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC) return CDS_ERR_ARG;
+    if (scheme == CDS_SCHEME_ATOMIC && !atom) return CDS_ERR_ARG;
+    {   // every function s, p or d (l + m + n <= 2): the kernels' bound
+        std::vector<int32_t> h(3 * (size_t)nbf);
+        CDS_CUDA_TRY(cudaMemcpyAsync(h.data(), lmn, sizeof(int32_t) * 3 * nbf,
+                                     cudaMemcpyDeviceToHost, stream));
+        CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+        for (int32_t f = 0; f < nbf; ++f) {
+            const int32_t l = h[3 * f], m = h[3 * f + 1], k = h[3 * f + 2];
+            if (l < 0 || m < 0 || k < 0 || l + m + k > 2) return CDS_ERR_UNSUPPORTED;
+        }
+    }
+    const int64_t n = npair_of(nbf);
+    CdLayout lay = cd_layout(workspace, nbf, false);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    int st = shell_diag(nbf, xyz, lmn, start, exps, coefs, D, stream);
+    if (st) return st;
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, sizeof(CdCtrl), stream));
+    const int nb = cd_blocks(n), ns = sel_blocks(n), nu = step_blocks(n);
+    k_cd_init<<<nb, kCdThreads, 0, stream>>>(lay.pd, atom, scheme, n, delta, D, lay.cand,
+                                            lay.blk_a, lay.blk_b, lay.ctrl, 1);
+    CDS_LAUNCH_CHECK();
+    k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, 0, max_rank, D, lay.cand, lay.blk_i, piv,
+                                              lay.ctrl);
+    CDS_LAUNCH_CHECK();
+    CdCtrl h{};
+    for (int32_t k0 = 0; k0 <= max_rank; k0 += kHostCheckEvery) {
+        const int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
+        for (int32_t k = k0; k < k1; ++k) {
+            st = shell_column(nbf, xyz, lmn, start, exps, coefs, &lay.ctrl->P, &lay.ctrl->done,
+                              lay.ecol, stream);
+            if (st) return st;
+            k_cd_project<false><<<dot_tiles(n), kUpdThreads, 0, stream>>>(lay.pd, n, k, L, lay.ecol,
+                                                                           0, lay.ctrl);
+            k_cd_update<false, false><<<nu, kUpdThreads, 0, stream>>>(
+                n, k, max_rank, L, D, lay.cand, lay.ecol, nullptr, lay.blk_a, lay.blk_b,
+                lay.blk_i, piv, lay.ctrl);
+        }
+        count_launches(3ull * (unsigned long long)(k1 - k0));
+        CDS_CUDA_TRY(cudaGetLastError());
+        CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, stream));
+        CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+        if (h.done) break;
+    }
+    *M_out = h.M;
+    if (delta_eff_out) *delta_eff_out = h.delta_eff;
+    if (!h.done) return CDS_ERR_RANK_CAP;
+    return h.status;
 }
 
 

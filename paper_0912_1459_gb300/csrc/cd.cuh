@@ -69,8 +69,9 @@ struct CdCtrl {
 // step of the tensor-core form; it returns at once unless the step starts a
 // streaming pass (ctrl->pass), and then forms, for the pass's candidate set,
 //   G[c][I] = sum_{K < k0} L^K_I L^K_{S_c}     (float pairs, [kSpecTC][n]),
-// from the slice store (A: planes [kSlicesTC][n][kcap] of pair rows) and
-// the candidate rows (B: planes [kSlicesTC][kSpecTC][kcap]), both scaled by
+// from the slice store (A: [kcap / kGroupTC][kSlicesTC][n][kGroupTC], pair
+// rows blocked by 32-column groups) and the candidate rows (B: the same with
+// kSpecTC rows), both scaled by
 // the per-row powers of two sigA / sigB.
 struct CdTcGemm;
 int cd_tc_gemm_setup(CdTcGemm** out, int64_t n, int32_t kcap, const void* a_planes,

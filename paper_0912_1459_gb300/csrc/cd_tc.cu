@@ -9,25 +9,40 @@
 // sigma_I = a power of two above sqrt(D0_I) (so |L^K_I| < sigma_I for every K,
 // Cauchy-Schwarz on the residual matrix), cut into eight 7-bit digits stored
 // as exact BF16 slices (the error-free splitting of Ozaki, Ogita, Oishi and
-// Rump, 2012, as in the exact-slice transform).  The products of slice pairs
-// (s, t) with s + t <= 9 (1-based; 36 pairs) are exact; the dropped ones are
-// below 2^-56 of sigma_I sigma_S per term.  Each of the 15 leading pairs
-// (s + t <= 6) has a TMEM accumulator of its own, where its FP32 sum is exact
-// for up to 1040 terms (K 127^2 < 2^24), so the K range runs in chunks of
-// 1024; the 21 smaller pairs (terms below 2^-35 of sigma_I sigma_S) share a
-// sixteenth, whose rounding stays near 1e-14 of sigma_I sigma_S.  The
-// epilogue adds the sixteen in float pairs, scales by sigma_I sigma_S and
-// adds the chunk to G.  Fewer bits or more sharing are not enough: a 42-bit
-// store (~4e-11 on the vectors) or 15 pairs in one rounded accumulator
-// (~1e-10) break the symmetry ties of the pivot rule differently from FP64,
-// whose band is 1e-12 of the largest diagonal.
+// Rump, 2012, as in the exact-slice transform): slice s holds d_s 2^-7(s+1).
+// The products of slice pairs (s, t) with s + t <= 7 (36 pairs) are kept; the
+// dropped ones are below 2^-56 of sigma_I sigma_S per term.  Fewer bits are
+// not enough: a 42-bit store (~4e-11 on the vectors) breaks the symmetry ties
+// of the pivot rule differently from FP64, whose band is 1e-12 of the largest
+// diagonal.
 //
-// Kernel: M tile 128 pairs, N = 32 candidates (16 accumulators x 32 columns
-// fill TMEM), 2 TMA stages of {8 A slices, 8 B slices} (64-byte swizzled rows
-// of 32 BF16), warp 0 = TMA producer, warp 1 = TMEM allocator + MMA issuer (72
-// MMAs per 32 columns), warps 2..5 = epilogue.  The launch is enqueued at every step and returns at once unless
-// the control block marks a pass.  Every wait is bounded and sets an error
-// word instead of hanging.
+// Shape.  The MMA's M side is 128 pairs (one pair slice s per MMA), its N
+// side 128 columns: four groups g = 0..3 of the 32 candidates, read as a
+// window of a stack of candidate slices [3 zero groups][t = 0]..[t = 7]
+// shifted so that column group g holds slice t = g - s (zero when negative)
+// or t = g + 4 - s.  Each column group then receives products of one weight
+// u = s + t, and two accumulators cover the 36 pairs with 12 MMAs of
+// 128 x 128 x 16 per 16 columns of K:
+//   X (u = g):      s = 0..3,  t = g - s;
+//   Y (u = g + 4):  s = 0..7,  t = g + 4 - s.
+// (One MMA of N = 32 per slice pair would re-read the 128-row pair operand
+// 36 times; the tensor pipe's operand reads then bound the kernel.)  A column
+// of an accumulator adds at most eight slice pairs of one weight, each term
+// below 127^2 units of 2^-7(u+2), so its FP32 sum is exact for up to 128
+// columns of K (8 x 128 x 127^2 < 2^24): K runs in chunks of 128, and the
+// epilogue adds a chunk's eight group values per candidate in float pairs,
+// finest first, keeps the tile's sum over the chunks in registers and at the
+// end scales it by sigma_I sigma_S (powers of two).
+//
+// Kernel: M tile 128 pairs; TMEM holds two buffers of the two accumulators
+// (2 x 2 x 128 columns), so the epilogue of one chunk overlaps the MMAs of
+// the next; 2 TMA stages of {8 pair slices (64 KB), 8 candidate slices
+// (16 KB) behind 6 KB of zero groups}; the stores are blocked by 32-column
+// groups, [group][slice][row][32], so each stage is two boxes of contiguous
+// rows (64-byte swizzled).  Warp 0 = TMA producer, warp 1 = TMEM allocator +
+// MMA issuer, warps 2..5 = epilogue (one pair row per thread).  The launch is
+// enqueued at every step and returns at once unless the control block marks a
+// pass.  Every wait is bounded and sets an error word instead of hanging.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -41,62 +56,61 @@ namespace cdtc {
 
 using namespace tc;
 
-constexpr int S = kSlicesTC;
-constexpr int NACC = 16;
-constexpr int TM = 128;
-constexpr int TN = kSpecTC;                      // 32 candidates
+constexpr int S = kSlicesTC;                     // 8 slices
+constexpr int NC = kSpecTC;                      // 32 candidates
 constexpr int KE = kGroupTC;                     // BF16 per k-block (64-byte rows)
-constexpr int CHUNK_KB = 32;                     // k-blocks per exact chunk (1024 <= 1040)
-constexpr int NSTAGE = 2;
+constexpr int TM = 128;                          // pairs per tile
+constexpr int TN = 4 * NC;                       // 128: four column groups of candidates
+constexpr int ZG = 3;                            // zero groups below the candidate slices
 constexpr int A_SLICE = TM * 64;                 // 8 KB
-constexpr int B_SLICE = TN * 64;                 // 2 KB
-constexpr int STAGE_BYTES = S * (A_SLICE + B_SLICE);   // 80 KB
+constexpr int GRP = NC * 64;                     // 2 KB: one group of 32 candidate rows
+constexpr int B_OFF = S * A_SLICE;               // 64 KB
+constexpr int STAGE_BYTES = B_OFF + (ZG + S) * GRP;  // 86 KB
+constexpr uint32_t TX_BYTES = S * A_SLICE + S * GRP; // loaded per stage (the zeros are not)
+constexpr int NSTAGE = 2;
+constexpr int CHUNK_KB = 4;                      // k-blocks per exact chunk (128 columns)
+constexpr int NACC = 2;
+constexpr int BUF_COLS = NACC * TN;              // 256 TMEM columns per buffer
+constexpr uint32_t TMEM_COLS = 512;
 constexpr int EPI_WARPS = 4;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
-constexpr uint32_t TMEM_COLS = 512;              // 16 x 32
 constexpr size_t SMEM_BYTES = 1024 + NSTAGE * STAGE_BYTES + 256;
-static_assert(TN == 32 && NACC * TN <= (int)TMEM_COLS, "accumulators fit TMEM");
+static_assert(2 * BUF_COLS <= (int)TMEM_COLS, "two accumulator buffers fit TMEM");
+static_assert(SMEM_BYTES <= 232448, "shared memory");
+static_assert(A_SLICE % 512 == 0 && GRP % 512 == 0 && STAGE_BYTES % 1024 == 0,
+              "swizzle atoms stay aligned");
+static_assert(8 * CHUNK_KB * KE * 127 * 127 < (1 << 24), "chunk sums are exact in FP32");
 
-// kind::f16 descriptor: D f32, A/B bf16, K-major, N = 32, M = 128
+// kind::f16 descriptor: D f32, A/B bf16, K-major, N = 128, M = 128
 constexpr uint32_t ID = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TN >> 3) << 17) |
                         ((uint32_t)(TM >> 4) << 24);
 
-// Slice pairs (s, t), s + t <= 7 (0-based), leading first; accumulators
-// 0..14 take the pairs with s + t <= 4 one each, 15 the 21 with s + t in 5..7.
-constexpr int UMAX = 7;
-constexpr int NPAIRS = (UMAX + 1) * (UMAX + 2) / 2;   // 36 (every s, t < 8 with s + t <= 7)
-struct PairTab {
-    int s[NPAIRS], t[NPAIRS], acc[NPAIRS], first[NPAIRS];
+// The 12 MMAs of 16 columns of K: accumulator, pair slice s and the first
+// stack group of the candidate window (column group g reads stack group
+// w + g, candidate slice w + g - ZG).
+struct MmaTab {
+    int acc[12], s[12], w[12], first[12];
 };
-__host__ __device__ constexpr PairTab make_pairs() {
-    PairTab p{};
-    bool seen[NACC] = {};
+__host__ __device__ constexpr MmaTab make_mmas() {
+    MmaTab m{};
     int n = 0;
-    for (int u = 0; u <= UMAX; ++u)
-        for (int s = 0; s <= u; ++s) {
-            const int acc = u <= 4 ? n : NACC - 1;
-            p.s[n] = s;
-            p.t[n] = u - s;
-            p.acc[n] = acc;
-            p.first[n] = seen[acc] ? 0 : 1;
-            seen[acc] = true;
-            ++n;
-        }
-    return p;
+    for (int s = 0; s < 4; ++s, ++n) { m.acc[n] = 0; m.s[n] = s; m.w[n] = ZG - s; m.first[n] = s == 0; }
+    for (int s = 0; s < 8; ++s, ++n) { m.acc[n] = 1; m.s[n] = s; m.w[n] = ZG + 4 - s; m.first[n] = s == 0; }
+    return m;
 }
-static_assert(make_pairs().acc[14] == 14 && make_pairs().acc[NPAIRS - 1] == NACC - 1,
-              "pair table");
+static_assert(make_mmas().w[3] == 0 && make_mmas().w[11] == 0 && make_mmas().w[4] + 3 == ZG + S - 1,
+              "windows stay inside the stack");
 
 struct Maps {
-    CUtensorMap a, b;   // 3-D {k, rows, slice}
+    CUtensorMap a, b;   // a: pair slices, b: candidate slices; 3-D {k in group, rows, group x S + slice}
 };
 
 struct Args {
     int64_t n;          // pair rows
     int32_t mtiles;
     const float* sa;    // [n] pair scales
-    const float* sb;    // [TN] candidate scales
-    float2* G;          // [TN][n]
+    const float* sb;    // [NC] candidate scales
+    float2* G;          // [NC][n]
     const CdCtrl* ctrl;
 };
 
@@ -146,22 +160,27 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
     uint64_t* bars = (uint64_t*)(smem + NSTAGE * STAGE_BYTES);
     uint64_t* full = bars;
     uint64_t* empty = bars + NSTAGE;
-    uint64_t* tfull = bars + 2 * NSTAGE;
-    uint64_t* tempty = tfull + 1;
-    uint32_t* tmem_slot = (uint32_t*)(tempty + 1);
+    uint64_t* tfull = bars + 2 * NSTAGE;    // [2]
+    uint64_t* tempty = tfull + 2;           // [2]
+    uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // work unit = (tile, chunk): a CTA takes tiles round robin and every chunk
-    // of its tile in order, so the chunks of one G tile are added by one CTA
+    // of its tile in order, so one CTA sums a tile's chunks
     const int64_t my_units = g.mtiles > (int64_t)blockIdx.x
                                  ? ((g.mtiles - 1 - blockIdx.x) / gridDim.x + 1) * nchunk
                                  : 0;
     volatile int32_t* verr = err;
 
+    // the zero groups below the candidate slices of every stage (never loaded)
+    constexpr int ZQ = ZG * GRP / 16;
+    for (int i = threadIdx.x; i < NSTAGE * ZQ; i += blockDim.x)
+        reinterpret_cast<uint4*>(stages + (i / ZQ) * STAGE_BYTES + B_OFF)[i % ZQ] =
+            make_uint4(0, 0, 0, 0);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
         for (int i = 0; i < NSTAGE; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        mbar_init(tfull, 1);
-        mbar_init(tempty, EPI_WARPS);
+        for (int i = 0; i < 2; ++i) { mbar_init(&tfull[i], 1); mbar_init(&tempty[i], EPI_WARPS); }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -188,14 +207,11 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
                 const int kb1 = min(kblocks, (ch + 1) * CHUNK_KB);
                 for (int kb = ch * CHUNK_KB; kb < kb1; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, verr)) { ok = false; break; }
-                    mbar_arrive_expect_tx(&full[stage], (uint32_t)STAGE_BYTES);
+                    mbar_arrive_expect_tx(&full[stage], TX_BYTES);
                     last_parity[stage] = (int32_t)phase;
                     const uint32_t st = smem_u32(stages + stage * STAGE_BYTES);
-                    for (int s = 0; s < S; ++s) {
-                        tma_load_3d(st + s * A_SLICE, &maps.a, &full[stage], kb * KE, mt * TM, s);
-                        tma_load_3d(st + S * A_SLICE + s * B_SLICE, &maps.b, &full[stage], kb * KE,
-                                    0, s);
-                    }
+                    tma_load_3d(st, &maps.a, &full[stage], 0, mt * TM, kb * S);
+                    tma_load_3d(st + B_OFF + ZG * GRP, &maps.b, &full[stage], 0, 0, kb * S);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -205,15 +221,17 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------- MMA issuer ----------------
-            constexpr PairTab kPairs = make_pairs();
+            constexpr MmaTab kM = make_mmas();
             int stage = 0;
-            uint32_t phase = 0, aphase = 0;
+            uint32_t phase = 0;
             bool ok = true;
             for (int64_t j = 0; ok && j < my_units; ++j) {
-                const int ch = (int)(j % nchunk);
+                const int ch = (int)(j % nchunk), buf = (int)(j & 1);
+                const uint32_t use = (uint32_t)((j >> 1) & 1);
                 const int kbeg = ch * CHUNK_KB, kb1 = min(kblocks, (ch + 1) * CHUNK_KB);
-                if (!mbar_wait(tempty, aphase ^ 1u, verr)) break;
+                if (!mbar_wait(&tempty[buf], use ^ 1u, verr)) break;
                 fence_after();
+                const uint32_t dbase = tmem + (uint32_t)(buf * BUF_COLS);
                 for (int kb = kbeg; kb < kb1; ++kb) {
                     if (!mbar_wait(&full[stage], phase, verr)) { ok = false; break; }
                     fence_after();
@@ -222,62 +240,70 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
                     for (int kk = 0; kk < 2; ++kk) {   // 16 BF16 (32 bytes) of k per MMA
                         const uint32_t off = kk * 32;
 #pragma unroll
-                        for (int p = 0; p < NPAIRS; ++p) {
-                            const uint32_t en = ((kb > kbeg) || kk || !kPairs.first[p]) ? 1u : 0u;
-                            mma_f16(tmem + (uint32_t)kPairs.acc[p] * TN,
-                                    sdesc(base + kPairs.s[p] * A_SLICE + off),
-                                    sdesc(base + S * A_SLICE + kPairs.t[p] * B_SLICE + off), ID, en);
+                        for (int q = 0; q < 12; ++q) {
+                            const uint32_t en = ((kb > kbeg) || kk || !kM.first[q]) ? 1u : 0u;
+                            mma_f16(dbase + (uint32_t)(kM.acc[q] * TN),
+                                    sdesc(base + kM.s[q] * A_SLICE + off),
+                                    sdesc(base + B_OFF + kM.w[q] * GRP + off), ID, en);
                         }
                     }
                     mma_commit(&empty[stage]);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
                 if (!ok) break;
-                mma_commit(tfull);
-                aphase ^= 1u;
+                mma_commit(&tfull[buf]);
             }
         }
     } else {
         // ---------------- epilogue (4 warps, one pair row per thread) ----------------
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
-        uint32_t aphase = 0;
+        float2 acc[NC];
         for (int64_t j = 0; j < my_units; ++j) {
-            const bool bad = !mbar_wait(tfull, aphase, verr) || *verr;
+            const int buf = (int)(j & 1);
+            const uint32_t use = (uint32_t)((j >> 1) & 1);
+            const bool bad = !mbar_wait(&tfull[buf], use, verr) || *verr;
             if (epi_any(bad)) break;
             fence_after();
             const int mt = (int)(blockIdx.x + (j / nchunk) * gridDim.x), ch = (int)(j % nchunk);
-            const int64_t I = (int64_t)mt * TM + row;
-            const bool ok = I < g.n;
-            const float sa = ok ? g.sa[I] : 0.f;
-            const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16);
-            if ((int64_t)mt * TM + quad * 32 < g.n) {
-#pragma unroll 1
-                for (int c0 = 0; c0 < TN; c0 += 8) {
-                    float a[NACC][8];
+            const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BUF_COLS);
 #pragma unroll
-                    for (int q = 0; q < NACC; ++q) tmem_ld8(ta + (uint32_t)q * TN + c0, a[q]);
-                    tmem_wait_ld();
-                    if (ok) {
+            for (int c0 = 0; c0 < NC; c0 += 8) {
+                float x[4][8], y[4][8];
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
-                            const int c = c0 + j;
-                            // smallest first: the shared rest, then the exact pairs
-                            float2 v = make_float2(a[NACC - 1][j], 0.f);
+                for (int gq = 0; gq < 4; ++gq) {
+                    tmem_ld8(ta + (uint32_t)(gq * NC + c0), x[gq]);
+                    tmem_ld8(ta + (uint32_t)(TN + gq * NC + c0), y[gq]);
+                }
+                tmem_wait_ld();
 #pragma unroll
-                            for (int q = NACC - 2; q >= 0; --q) v = pair_add(v, a[q][j]);
-                            const float st = sa * g.sb[c];   // power of two: exact scaling
-                            v = make_float2(v.x * st, v.y * st);
-                            float2* dst = g.G + (int64_t)c * g.n + I;
-                            *dst = ch == 0 ? v : pair_add2(*dst, v);
-                        }
+                for (int i = 0; i < 8; ++i) {
+                    // weights 7, 6, 5, 4 (Y), then 3, 2, 1, 0 (X): finest first
+                    float2 v = two_sum(y[3][i], y[2][i]);
+                    v = pair_add(v, y[1][i]);
+                    v = pair_add(v, y[0][i]);
+                    v = pair_add(v, x[3][i]);
+                    v = pair_add(v, x[2][i]);
+                    v = pair_add(v, x[1][i]);
+                    v = pair_add(v, x[0][i]);
+                    acc[c0 + i] = ch == 0 ? v : pair_add2(acc[c0 + i], v);
+                }
+            }
+            // this buffer is read: the MMAs may reuse it
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[buf]);
+            if (ch == nchunk - 1) {   // the tile's last chunk: scale and store
+                const int64_t I = (int64_t)mt * TM + row;
+                if (I < g.n) {
+                    const float sa = g.sa[I];
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const float st = sa * g.sb[c];   // power of two: exact scaling
+                        g.G[(int64_t)c * g.n + I] = make_float2(acc[c].x * st, acc[c].y * st);
                     }
                 }
             }
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(tempty);
-            aphase ^= 1u;
         }
     }
 
@@ -290,12 +316,14 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
     }
 }
 
+// Group-blocked store [kcap / 32][S][rows][32] BF16: a box is the S slices of
+// box_rows rows of one group.
 bool make_map(CUtensorMap* m, const void* base, uint64_t kcap, uint64_t rows, uint32_t box_rows) {
     auto enc = encoder();
     if (!enc) return false;
-    cuuint64_t dims[3] = {kcap, rows, (cuuint64_t)S};
-    cuuint64_t strides[2] = {kcap * 2, rows * kcap * 2};
-    cuuint32_t box[3] = {(cuuint32_t)KE, box_rows, 1};
+    cuuint64_t dims[3] = {(cuuint64_t)KE, rows, (kcap / KE) * S};
+    cuuint64_t strides[2] = {KE * 2, rows * KE * 2};
+    cuuint32_t box[3] = {(cuuint32_t)KE, box_rows, (cuuint32_t)S};
     cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box,
                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
@@ -321,7 +349,7 @@ int cd_tc_gemm_setup(CdTcGemm** out, int64_t n, int32_t kcap, const void* a_plan
     CdTcGemm* g = new (std::nothrow) CdTcGemm;
     if (!g) return CDS_ERR_ARG;
     if (!make_map(&g->maps.a, a_planes, (uint64_t)kcap, (uint64_t)n, TM) ||
-        !make_map(&g->maps.b, b_planes, (uint64_t)kcap, (uint64_t)TN, TN)) {
+        !make_map(&g->maps.b, b_planes, (uint64_t)kcap, (uint64_t)NC, NC)) {
         delete g;
         return CDS_ERR_CUDA;
     }

@@ -10,6 +10,9 @@ holds a few GB of device memory at most and replays in seconds:
   python -m paper_0912_1459_gb300.profcases sigma64     # k_sigma_tc, nE = 64
   python -m paper_0912_1459_gb300.profcases cd          # k_cd_update, FP64 (C60, 1024 steps max)
   python -m paper_0912_1459_gb300.profcases cdf         # k_cd_update, float pairs
+  python -m paper_0912_1459_gb300.profcases cdoz        # k_cd_gemm_tc, k_cd_project_tc,
+                                                        # k_cd_update (tensor-core passes; 512
+                                                        # steps, 4.4 GB on the device)
 
 Factors are seeded random numbers of the right shape and magnitude (the
 kernels' cost does not depend on their values).
@@ -58,16 +61,24 @@ def main(mode: str) -> None:
         E = d(W.energy_grid(m.eps[m.orbitals[9:11]], nE))
         for _ in range(2):
             G.cds_sigma2_diag(Lov, Lp, d(m.eps), m.nocc, E, "bf16x3")
-    elif mode in ("cd", "cdf"):
+    elif mode in ("cd", "cdf", "cdoz"):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        L, _, _, _ = G.cds_cd_decompose(d(m.basis.xyz), d(m.basis.alpha),
-                                        d(m.basis.atom.astype(np.int32)), 1e-4, "full",
-                                        max_rank=1024,
-                                        precision="f32x2" if mode == "cdf" else "fp64")
+        rank = 512 if mode == "cdoz" else 1024
+        try:
+            L, _, _, _ = G.cds_cd_decompose(d(m.basis.xyz), d(m.basis.alpha),
+                                            d(m.basis.atom.astype(np.int32)), 1e-4, "full",
+                                            max_rank=rank,
+                                            precision={"cdf": "f32x2", "cdoz": "ozaki"}.get(
+                                                mode, "fp64"))
+            M = L.shape[0]
+        except G.CdsError as e:   # the first `rank` steps are all a profile needs
+            if e.status != 4:
+                raise
+            M = rank
         b.record()
         torch.cuda.synchronize()
-        print(f"decomposition: M = {L.shape[0]}, {a.elapsed_time(b):.1f} ms")
+        print(f"decomposition: {M} steps, {a.elapsed_time(b):.1f} ms")
     else:
         raise SystemExit(f"unknown case {mode!r}")
     torch.cuda.synchronize()

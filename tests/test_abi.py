@@ -32,6 +32,10 @@ def test_host_only_calls(lib):
     assert so.cds_cd_workspace_bytes(-1) == 0
     assert so.cds_sigma2_workspace_bytes(24, 6, 100, 2, 16, 0) > 0
     assert so.cds_sigma2_workspace_bytes(24, 6, 100, 2, 0, 0) == 0
+    # the GEMM timing switch and totals are host state only
+    lib.cds_cd_gemm_timing(True)
+    assert lib.cds_cd_gemm_time() == (0.0, 0)
+    lib.cds_cd_gemm_timing(False)
 
 
 def test_argument_errors_before_any_launch(lib):

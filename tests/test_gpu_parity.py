@@ -106,11 +106,12 @@ def test_cd_f32x2_parity(name, delta, scheme):
 ])
 def test_cd_tensor_core_parity(name, delta, scheme):
     """Exact-slice tensor-core passes (CDS_PREC_OZAKI: the stored vectors as
-    42-bit fixed point below each pair's scale sigma_I > sqrt(D0_I), 32
+    56-bit fixed point below each pair's scale sigma_I > sqrt(D0_I), 32
     candidates per pass): the oracle's pivots; vectors within
-    tol = max(1e-9, 1e-11 / sqrt(delta)) -- a projection carries ~2^-42
-    sigma_I sigma_P sqrt(k) of truncation and L^k divides it by sqrt(D_P) >=
-    sqrt(delta) (about 4e-13 x 2 x 20 = 1e-11 here); L^T L and the residuals
+    tol = max(1e-9, 1e-11 / sqrt(delta)) -- a projection carries ~2^-56
+    sigma_I sigma_P k of truncation plus the shared accumulator's rounding
+    (~1e-14 sigma_I sigma_P), and L^k divides it by sqrt(D_P) >= sqrt(delta);
+    the bound keeps the 42-bit analysis' margin; L^T L and the residuals
     within the same."""
     m = O.molecule(name)
     ref = O.decomposition(name, delta, scheme)
