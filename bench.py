@@ -214,6 +214,9 @@ def flops_model(m, M: int) -> dict:
     }
 
 
+CD_GEMM_TRAFFIC_PER_BYTE = 2.985491304e9 / 2.985677584e9
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     meas = {}
@@ -550,6 +553,12 @@ def run_ours(args, dist: Dist):
     for r in roof.values():
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
+    if "cd_gemm" in roof:
+        # DRAM bytes per algorithmic byte of k_cd_gemm_tc from one ncu capture
+        # (the pass at k0 = 504 of the C60-shaped decomposition, 4.4 GB case:
+        # 2.985491 GB of dram__bytes_read + write against 2.985678 GB), scaled
+        # to this run's average launch; traffic grows with the columns streamed
+        roof["cd_gemm"]["traffic"] = CD_GEMM_TRAFFIC_PER_BYTE * roof["cd_gemm"]["bytes_per_launch"]
     # (traffic stays null until an ncu capture of the current kernels exists)
     dominant = max(med, key=med.get)
     # the stage that dominates the step is the pipelined decomposition +
@@ -891,9 +900,12 @@ def run_batched(args, device):
     lat_ms = (st[1:] - st[0]) / 1e6
     n_solves = int(sum(len(mm.orbitals) for mm in mols))
     status = b.status[:n_solves].cpu().numpy()
+    cd_ms, tr_ms = ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2])
+    whole_ms = cd_ms + tr_ms + ms
     return {"clusters": len(mols), "nbf_range": [int(min(x[0] for x in spec)), int(max(x[0] for x in spec))],
             "solves": n_solves, "energies": int(sum(x[2] * x[3] for x in spec)),
-            "cd_ms": ev[0].elapsed_time(ev[1]), "transform_ms": ev[1].elapsed_time(ev[2]),
+            "cd_ms": cd_ms, "transform_ms": tr_ms,
+            "whole_ms": whole_ms, "whole_solves_per_s": n_solves / (whole_ms / 1e3),
             "cd_precision": "f32x2" if args.precision != "fp64" else "fp64",
             "transform_precision": args.transform if args.precision != "fp64" else "fp64",
             "graph_ms": ms, "solves_per_s": n_solves / (ms / 1e3),
@@ -901,9 +913,11 @@ def run_batched(args, device):
             "latency_ms_p99": float(np.percentile(lat_ms, 99)),
             "converged": int((status == 0).sum()), "ranks": [int(x) for x in M],
             "autotune": {"choice": list(tuned["choice"]), "ms": tuned["ms"], "cached": tuned["cached"]},
-            "note": "graph = Sigma on every cluster's energy grid + Newton (50 passes max) in one "
-                    "replay; latency = device stamp of a cluster's last retired orbital minus the "
-                    "replay's start stamp"}
+            "note": "whole = batched decomposition + transform + one graph replay (every "
+                    "cluster from its basis to its roots); graph = Sigma on every cluster's "
+                    "energy grid + Newton (50 passes max) in one replay, solves_per_s counts "
+                    "the graph alone; latency = device stamp of a cluster's last retired orbital "
+                    "minus the replay's start stamp"}
 
 
 # ----------------------------------------------------------------------------
