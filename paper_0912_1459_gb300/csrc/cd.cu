@@ -558,7 +558,7 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
                                              long long* __restrict__ blk_b,
                                              long long* __restrict__ blk_i,
                                              int32_t* __restrict__ piv, CdCtrl* ctrl, int bid,
-                                             int nblk) {
+                                             int nblk, PairF2 pf = PairF2{}) {
     static_assert(!SPEC || DF, "speculative projections are a float-pair mode");
     static_assert(!TC || SPEC, "the tensor-core form is a speculative form");
     const int64_t P = ctrl->P;
@@ -586,6 +586,10 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
         }
     }
     long long mx_i = LLONG_MAX;   // SPEC: lowest index holding the block's candidate maximum
+    // TC: the integral column is formed here, element by element, from the
+    // pivot's pair data
+    PivotF2 pv;
+    if constexpr (TC) pv = pivot_f2(pf, P);
     // TC: the pass's projection plus the vectors made since, for this thread's
     // pairs, with four rows of L in flight per pair (the rows are a batch's
     // worth of recent vectors, up to 63 of them)
@@ -635,7 +639,9 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
                     for (int i = 0; i < kSpec - 1; ++i)
                         if (i < extra) df_fma(acc, Lf[(int64_t)(k0 + i) * n + I], lpP[i]);
                 }
-                const float2 e = reinterpret_cast<const float2*>(ecol)[I];
+                float2 e;
+                if constexpr (TC) e = eri_elem_df(pf, I, pv);
+                else e = reinterpret_cast<const float2*>(ecol)[I];
                 const float2 lf = df_mul(df_add(e, df_neg(acc)), rDPf);
                 *reinterpret_cast<float2*>(slot) = lf;
                 const float2 l2 = df_mul(lf, lf);
@@ -861,19 +867,18 @@ k_cd_project_spec(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __r
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) cd_spec_dot_body(n, k, L, G, ctrl, t);
 }
 
-// Step k, part 1 of the exact-slice tensor-core form: every block takes its
-// share of the integral column; when step k starts a pass, the blocks then
-// bring the slice store up to date (column groups [kdone, k rounded up),
-// zero at K >= k) and slice the candidates' rows [0, k) into the B planes,
-// for the projection GEMM that follows.
+// Step k, part 1 of the exact-slice tensor-core form (the integral column is
+// formed in the update): when step k starts a pass, the blocks bring the
+// slice store up to date (column groups [kdone, k rounded up), zero at
+// K >= k) and slice the candidates' rows [0, k) into the B planes, for the
+// projection GEMM that follows; otherwise the kernel returns at once.
 __global__ void __launch_bounds__(kUpdThreads, 4)
-k_cd_project_tc(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __restrict__ L,
-                float2* __restrict__ ecol, const float* __restrict__ sigA,
-                __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B,
-                float* __restrict__ sigB, const CdCtrl* ctrl) {
-    if (ctrl->done) return;
-    cd_eri_body_df(pd, pf, n, ctrl, ecol, blockIdx.x, gridDim.x);
-    if (ctrl->pass == 0 || k == 0) return;
+k_cd_project_tc(int64_t n, int32_t k, const double* __restrict__ L,
+                const float* __restrict__ sigA, __nv_bfloat16* __restrict__ A,
+                __nv_bfloat16* __restrict__ B, float* __restrict__ sigB, const CdCtrl* ctrl) {
+    pdl_trigger();
+    pdl_wait();
+    if (ctrl->done || ctrl->pass == 0 || k == 0) return;
     const float2* Lf = reinterpret_cast<const float2*>(L);
     const int32_t kd = ctrl->kdone;
     const int32_t kend = (k + kGroupTC - 1) / kGroupTC * kGroupTC;
@@ -914,12 +919,17 @@ k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
             double* __restrict__ D, const uint8_t* __restrict__ cand,
             const double* __restrict__ ecol, const float2* __restrict__ G,
             double* __restrict__ blk_a, double* __restrict__ blk_b,
-            long long* __restrict__ blk_i, int32_t* __restrict__ piv, CdCtrl* ctrl) {
+            long long* __restrict__ blk_i, int32_t* __restrict__ piv, CdCtrl* ctrl,
+            PairF2 pf = PairF2{}) {
+    if constexpr (TC) {
+        pdl_trigger();
+        pdl_wait();
+    }
     if (ctrl->done) return;
     cd_step_body<DF, SPEC, TC>(n, k, max_rank, L, D, cand, ecol, G,
                            reinterpret_cast<long long*>(blk_a),
                            reinterpret_cast<long long*>(blk_b), blk_i, piv, ctrl, blockIdx.x,
-                           gridDim.x);
+                           gridDim.x, pf);
 }
 
 // Float pairs (hi, lo) of the first count elements of L back to FP64, in place.
@@ -1147,17 +1157,17 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
         int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
         for (int32_t k = k0; k < k1; ++k) {
             if (tcm) {
-                k_cd_project_tc<<<nres, kUpdThreads, 0, stream>>>(
-                    lay.pd, lay.pf, n, k, L, reinterpret_cast<float2*>(lay.ecol), lay.sigA, lay.A,
-                    lay.B, lay.sigB, lay.ctrl);
-                CDS_CUDA_TRY(cudaGetLastError());
+                CDS_CUDA_TRY(launch_pdl(k_cd_project_tc, (unsigned)nres, kUpdThreads, 0, stream, n,
+                                        k, (const double*)L, (const float*)lay.sigA, lay.A, lay.B,
+                                        lay.sigB, (const CdCtrl*)lay.ctrl));
                 if (timing) CDS_CUDA_TRY(cudaEventRecord(tev[2 * (k - k0)], stream));
                 st = cd_tc_gemm_launch(gemm, stream);
                 if (st) return st;
                 if (timing) CDS_CUDA_TRY(cudaEventRecord(tev[2 * (k - k0) + 1], stream));
-                k_cd_update<true, true, true><<<nu, kUpdThreads, 0, stream>>>(
-                    n, k, max_rank, L, D, lay.cand, lay.ecol, lay.G, lay.blk_a, lay.blk_b,
-                    lay.blk_i, piv, lay.ctrl);
+                CDS_CUDA_TRY(launch_pdl(k_cd_update<true, true, true>, (unsigned)nu, kUpdThreads, 0,
+                                        stream, n, k, max_rank, L, D, (const uint8_t*)lay.cand,
+                                        (const double*)lay.ecol, (const float2*)lay.G, lay.blk_a,
+                                        lay.blk_b, lay.blk_i, piv, lay.ctrl, lay.pf));
             } else if (df) {
                 k_cd_project_spec<<<nres, kUpdThreads, 0, stream>>>(
                     lay.pd, lay.pf, n, k, L, lay.G, reinterpret_cast<float2*>(lay.ecol),

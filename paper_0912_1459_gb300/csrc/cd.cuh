@@ -36,6 +36,32 @@ constexpr int kSlicesTC = 8;
 constexpr int kBitsTC = 7;
 constexpr int kMaxBlocksTC = 2048;   // update blocks the candidate search holds in shared memory
 
+// Programmatic dependent launch of the per-step kernels of the tensor-core
+// form: each kernel lets the next one be scheduled as soon as all its own
+// blocks run (pdl_trigger) and waits for its predecessor's completion and
+// memory before it reads anything (pdl_wait; a no-op in a normal launch), so
+// the launch of step k+1's kernels overlaps the serial tail of step k's.
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... K, typename... A>
+inline cudaError_t launch_pdl(void (*kern)(K...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t stream, A&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);
+}
+
 struct CdCtrl {
     double scale;      // max initial diagonal (all pairs)
     double delta_eff;  // max(delta, npair * 2^-52 * scale)

@@ -147,6 +147,8 @@ __device__ __forceinline__ bool epi_any(bool v) {
 
 __global__ void __launch_bounds__(THREADS, 1)
 k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restrict__ err) {
+    pdl_trigger();
+    pdl_wait();
     // the same decision in every thread: nothing to do unless this step starts a pass
     if (g.ctrl->done || !g.ctrl->pass) return;
     const int32_t k0 = g.ctrl->k0;
@@ -372,9 +374,8 @@ int cd_tc_gemm_setup(CdTcGemm** out, int64_t n, int32_t kcap, const void* a_plan
 }
 
 int cd_tc_gemm_launch(const CdTcGemm* g, cudaStream_t stream) {
-    cdtc::k_cd_gemm_tc<<<g->grid, cdtc::THREADS, cdtc::SMEM_BYTES, stream>>>(g->maps, g->args,
-                                                                            g->err);
-    CDS_LAUNCH_CHECK();
+    CDS_CUDA_TRY(launch_pdl(cdtc::k_cd_gemm_tc, (unsigned)g->grid, cdtc::THREADS, cdtc::SMEM_BYTES,
+                            stream, g->maps, g->args, g->err));
     return CDS_OK;
 }
 

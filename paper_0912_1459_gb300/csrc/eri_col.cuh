@@ -95,41 +95,60 @@ constexpr float kTwoPi52Lo = (float)(kTwoPi52 - (double)kTwoPi52Hi);
 // Values below the FP32 range (|K/p| < 1e-38, pairs of far-apart centres)
 // come out as 0, an absolute error far below any other in the decomposition.
 // The column is stored as float pairs.
+// The pivot density's part of the float-pair column: its pair data and the
+// constants pi^3 K_P/q and 2 pi^(5/2) K_P/q.
+struct PivotF2 {
+    float2 q, qx, qy, qz, pi3kq, tpkq;
+};
+__device__ __forceinline__ PivotF2 pivot_f2(PairF2 pf, int64_t P) {
+    PivotF2 v;
+    v.q = pf.p[P];
+    v.qx = pf.Px[P];
+    v.qy = pf.Py[P];
+    v.qz = pf.Pz[P];
+    const float2 kq = pf.Kp[P];
+    v.pi3kq = df_mul(make_float2(kPi3Hi, kPi3Lo), kq);
+    v.tpkq = df_mul(make_float2(kTwoPi52Hi, kTwoPi52Lo), kq);
+    return v;
+}
+
+// One element (rho_I|rho_P) of the column.
+__device__ __forceinline__ float2 eri_elem_df(PairF2 pf, int64_t I, const PivotF2& v) {
+    const float2 pI = pf.p[I];
+    const float2 dx = df_add(pf.Px[I], df_neg(v.qx));
+    const float2 dy = df_add(pf.Py[I], df_neg(v.qy));
+    const float2 dz = df_add(pf.Pz[I], df_neg(v.qz));
+    const float2 d2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
+    const float2 x = df_mul(df_mul(pI, v.q), d2);
+    const float sf = pI.x + v.q.x;
+    float2 e;
+    if (x.x >= kMidT * sf) {
+        // T >= 16: F0 = (1/2) sqrt(pi/T) (1 - erfc(sqrt T)), and erfc(sqrt T)
+        // <= 1.6e-8 is needed only to FP32 precision (its error then stays
+        // below 1e-14 of F0); above T = 36 it is below half an ulp
+        e = df_mul(df_mul(pf.Kp[I], v.pi3kq), df_rsqrt(x));
+        if (x.x < kFarT * sf) e = df_mul(e, make_float2(1.f, -erfcf(sqrtf(x.x / sf))));
+    } else {
+        const float2 rs = df_rsqrt(df_add(pI, v.q));                  // 1 / sqrt(p + q)
+        const float2 T = df_mul(x, df_mul(rs, rs));
+        const int i = min(max(__float2int_rn(T.x * (float)kBoysPerUnit), 0), kBoysPoints - 1);
+        const float2 d = df_add(T, make_float2(-(float)i * (1.f / (float)kBoysPerUnit), 0.f));
+        const float2* c = kBoysTaylorF2[i];
+        float2 f = c[kBoysOrder - 1];
+#pragma unroll
+        for (int m = kBoysOrder - 2; m >= 0; --m) f = df_add(df_mul(f, d), c[m]);
+        e = df_mul(df_mul(df_mul(pf.Kp[I], v.tpkq), rs), f);
+    }
+    return e;
+}
+
 template <int NT>
 __device__ __forceinline__ void eri_column_df(PairSoA pd, PairF2 pf, int64_t n, int64_t P,
                                               float2* __restrict__ ecol, int bid, int nblk) {
     (void)pd;
-    const float2 q = pf.p[P], qx = pf.Px[P], qy = pf.Py[P], qz = pf.Pz[P], kq = pf.Kp[P];
-    const float2 pi3kq = df_mul(make_float2(kPi3Hi, kPi3Lo), kq);
-    const float2 tpkq = df_mul(make_float2(kTwoPi52Hi, kTwoPi52Lo), kq);
-    for (int64_t I = (int64_t)bid * NT + threadIdx.x; I < n; I += (int64_t)nblk * NT) {
-        const float2 pI = pf.p[I];
-        const float2 dx = df_add(pf.Px[I], df_neg(qx));
-        const float2 dy = df_add(pf.Py[I], df_neg(qy));
-        const float2 dz = df_add(pf.Pz[I], df_neg(qz));
-        const float2 d2 = df_add(df_add(df_mul(dx, dx), df_mul(dy, dy)), df_mul(dz, dz));
-        const float2 x = df_mul(df_mul(pI, q), d2);
-        const float sf = pI.x + q.x;
-        float2 e;
-        if (x.x >= kMidT * sf) {
-            // T >= 16: F0 = (1/2) sqrt(pi/T) (1 - erfc(sqrt T)), and erfc(sqrt T)
-            // <= 1.6e-8 is needed only to FP32 precision (its error then stays
-            // below 1e-14 of F0); above T = 36 it is below half an ulp
-            e = df_mul(df_mul(pf.Kp[I], pi3kq), df_rsqrt(x));
-            if (x.x < kFarT * sf) e = df_mul(e, make_float2(1.f, -erfcf(sqrtf(x.x / sf))));
-        } else {
-            const float2 rs = df_rsqrt(df_add(pI, q));                  // 1 / sqrt(p + q)
-            const float2 T = df_mul(x, df_mul(rs, rs));
-            const int i = min(max(__float2int_rn(T.x * (float)kBoysPerUnit), 0), kBoysPoints - 1);
-            const float2 d = df_add(T, make_float2(-(float)i * (1.f / (float)kBoysPerUnit), 0.f));
-            const float2* c = kBoysTaylorF2[i];
-            float2 f = c[kBoysOrder - 1];
-#pragma unroll
-            for (int m = kBoysOrder - 2; m >= 0; --m) f = df_add(df_mul(f, d), c[m]);
-            e = df_mul(df_mul(df_mul(pf.Kp[I], tpkq), rs), f);
-        }
-        ecol[I] = e;
-    }
+    const PivotF2 v = pivot_f2(pf, P);
+    for (int64_t I = (int64_t)bid * NT + threadIdx.x; I < n; I += (int64_t)nblk * NT)
+        ecol[I] = eri_elem_df(pf, I, v);
 }
 
 // Integral column (rho_I|rho_P) into ecol (blockDim.x == NT, grid-stride over
