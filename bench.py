@@ -867,7 +867,9 @@ def run_batched(args, device):
 
     mols = W.config3()
     spec = [(mm.nbf, mm.nocc, len(mm.orbitals), mm.nE, C.default_max_rank(mm.nbf)) for mm in mols]
-    b = C.Batch(spec, device, "bf16x3" if args.precision == "fp64" else args.precision)
+    cdp = "fp64" if args.precision == "fp64" else args.cd_precision
+    b = C.Batch(spec, device, "bf16x3" if args.precision == "fp64" else args.precision,
+                cd_precision=cdp)
     cat = lambda xs: torch.from_numpy(np.ascontiguousarray(np.concatenate(xs))).to(device)  # noqa: E731
     xyz = cat([mm.basis.xyz.ravel() for mm in mols])
     al = cat([mm.basis.alpha for mm in mols])
@@ -878,7 +880,7 @@ def run_batched(args, device):
     E = cat([W.energy_grid(mm.eps[mm.orbitals], mm.nE).ravel() for mm in mols])
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     ev[0].record()
-    M = b.cd_decompose(xyz, al, at, 1e-5, precision="f32x2" if args.precision != "fp64" else "fp64")
+    M = b.cd_decompose(xyz, al, at, 1e-5, precision=cdp)
     ev[1].record()
     b.cd_to_mo(Cc, orb, precision=args.transform if args.precision != "fp64" else "fp64")
     ev[2].record()
@@ -906,7 +908,7 @@ def run_batched(args, device):
             "solves": n_solves, "energies": int(sum(x[2] * x[3] for x in spec)),
             "cd_ms": cd_ms, "transform_ms": tr_ms,
             "whole_ms": whole_ms, "whole_solves_per_s": n_solves / (whole_ms / 1e3),
-            "cd_precision": "f32x2" if args.precision != "fp64" else "fp64",
+            "cd_precision": cdp,
             "transform_precision": args.transform if args.precision != "fp64" else "fp64",
             "graph_ms": ms, "solves_per_s": n_solves / (ms / 1e3),
             "latency_ms_p50": float(np.percentile(lat_ms, 50)),

@@ -539,8 +539,12 @@ int cds_cd_to_mo_backward(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, con
  *   8 Lov [nocc][nbf-nocc][M]                        9 Lp [np][nbf][M]
  * (row nmol holds the totals).  Local MO indices in orb; atom indices are the
  * molecule's own.  The workspace (cds_batch_workspace_bytes) holds a
- * scratch part shared by the decomposition and the transform and a part
- * holding the self-energy / Newton state that a graph (below) refers to.
+ * scratch part shared by the decomposition and the transform, a part
+ * holding the self-energy / Newton state that a graph (below) refers to,
+ * and 8 worker slots: the library runs per-molecule work (the tensor-core
+ * decomposition, the transform) on 8 host threads, each with a library
+ * stream of its own, ordered after the caller's stream and before its later
+ * work.
  * ---------------------------------------------------------------------- */
 
 typedef struct {
@@ -556,13 +560,22 @@ typedef struct {
 /* Host only.  offs: host [(nmol + 1) * CDS_BATCH_NOFF]. */
 int cds_batch_offsets(int32_t nmol, const cds_mol* mols, int64_t* offs);
 
+/* Host only.  precision CDS_PREC_OZAKI sizes the worker slots for the
+ * tensor-core decomposition of the largest molecule as well; any other value
+ * sizes them for the transforms.  The calls accept a workspace without the
+ * slots (the scratch and state parts only); the transform then runs the
+ * molecules one after the other on the caller's stream, and the tensor-core
+ * decomposition returns CDS_ERR_WORKSPACE. */
 size_t cds_batch_workspace_bytes(int32_t nmol, const cds_mol* mols, int32_t precision);
 
 /* Blocking.  Per molecule as cds_cd_decompose (delta and scheme shared);
- * M_out: host [nmol].  One update and one pivot-select launch per step for
- * the whole batch.  precision: CDS_PREC_FP64, or CDS_PREC_F32X2 (float-pair
+ * M_out: host [nmol].  precision: CDS_PREC_FP64, or CDS_PREC_F32X2 (float-pair
  * projections and vectors, FP64 integral column, residuals and pivot
- * decisions; L converted to FP64 at the end).  Returns the first non-OK
+ * decisions; L converted to FP64 at the end): one update and one
+ * pivot-select launch per step for the whole batch.  CDS_PREC_OZAKI: each
+ * molecule's tensor-core decomposition (as cds_cd_decompose), the largest
+ * molecules first, on the worker threads (the workspace needs the slots of
+ * cds_batch_workspace_bytes(..., CDS_PREC_OZAKI)).  Returns the first non-OK
  * molecule status. */
 int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const double* xyz,
                            const double* alpha, const int32_t* atom, double delta,
@@ -570,7 +583,9 @@ int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const double* xyz,
                            int32_t* M_out, void* workspace, size_t workspace_bytes,
                            cudaStream_t stream);
 
-/* Asynchronous.  M: host [nmol] ranks.  Per molecule as cds_cd_to_mo. */
+/* Asynchronous (blocking while the worker threads enqueue and, for the
+ * exact-slice form, read each molecule's error word).  M: host [nmol] ranks.
+ * Per molecule as cds_cd_to_mo. */
 int cds_batch_cd_to_mo(int32_t nmol, const cds_mol* mols, const int32_t* M, const double* L,
                        const double* C, const int32_t* orb, int32_t precision, double* Lov,
                        double* Lp, void* workspace, size_t workspace_bytes, cudaStream_t stream);

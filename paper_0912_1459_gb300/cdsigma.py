@@ -689,9 +689,10 @@ class Batch:
 
     ``mols``: list of (nbf, nocc, np, nE, max_rank).  Holds the offsets, the
     workspace and the output buffers; the methods call the cds_batch_* entry
-    points and return per-molecule views."""
+    points and return per-molecule views.  ``cd_precision="ozaki"`` sizes the
+    workspace for the tensor-core decomposition of every molecule."""
 
-    def __init__(self, mols, device, precision: str = "bf16x3"):
+    def __init__(self, mols, device, precision: str = "bf16x3", cd_precision: str = "f32x2"):
         self.lib = load()
         self.dev = torch.device(device)
         self.n = len(mols)
@@ -704,6 +705,9 @@ class Batch:
         self.total = self.off[self.n]
         self.prec = precision
         need = self.lib.cds_batch_workspace_bytes(self.n, self.mols, PRECISIONS[precision])
+        if cd_precision == "ozaki":
+            need = max(need, self.lib.cds_batch_workspace_bytes(self.n, self.mols,
+                                                                PRECISIONS["ozaki"]))
         self.ws = _workspace(need, self.dev)
         f64 = dict(dtype=torch.float64, device=self.dev)
         i32 = dict(dtype=torch.int32, device=self.dev)

@@ -1,9 +1,13 @@
 // Batched form of the path: many molecules of uneven size, orbital count and
 // energy count per call.
 //
-//  * Cholesky decomposition: one update and one select launch per step for
-//    the whole batch (cd.cu, cd_batch_decompose).
-//  * Transform: per molecule, in order, sharing one workspace.
+//  * Cholesky decomposition: FP64 / float pairs: one update and one select
+//    launch per step for the whole batch (cd.cu, cd_batch_decompose); the
+//    tensor-core form (CDS_PREC_OZAKI): each molecule's own decomposition,
+//    the molecules spread over kWorkers host threads, each driving a library
+//    stream of its own, so the latency-bound steps of small molecules run
+//    side by side.
+//  * Transform: per molecule, on the same worker threads and streams.
 //  * Self-energy: the work items of every molecule in one persistent
 //    tcgen05 launch (sigma_tc.cu, tc_batch_pass), per-molecule descriptors in
 //    device memory.
@@ -14,11 +18,15 @@
 //    work), replayed with one launch.
 // Per-molecule completion times are stamped on the device with %globaltimer.
 #include <algorithm>
+#include <atomic>
+#include <mutex>
+#include <thread>
 #include <vector>
 
 #include "sigma_tc.cuh"
 
 namespace cds {
+
 
 size_t cd_batch_workspace_bytes(int32_t nmol, const BatchMol* mols);
 int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* off,
@@ -66,6 +74,95 @@ std::vector<BatchOffsets> offsets_of(int32_t nmol, const cds_mol* mols, BatchOff
     }
     if (total) *total = t;
     return o;
+}
+
+// ---- per-molecule work on worker threads with library streams of their own ----
+constexpr int kWorkers = 8;
+
+int worker_streams(cudaStream_t (&out)[kWorkers]) {
+    static std::mutex lock;
+    static cudaStream_t per_dev[64][kWorkers] = {};
+    int dev = 0;
+    CDS_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return CDS_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> guard(lock);
+    for (int t = 0; t < kWorkers; ++t) {
+        if (!per_dev[dev][t])
+            CDS_CUDA_TRY(cudaStreamCreateWithFlags(&per_dev[dev][t], cudaStreamNonBlocking));
+        out[t] = per_dev[dev][t];
+    }
+    return CDS_OK;
+}
+
+// Largest molecules first (pairs x capacity), so the threads finish together.
+std::vector<int> by_size(int32_t nmol, const cds_mol* mols) {
+    std::vector<int> order(nmol);
+    for (int c = 0; c < nmol; ++c) order[c] = c;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return npair_of(mols[a].nbf) * mols[a].max_rank > npair_of(mols[b].nbf) * mols[b].max_rank;
+    });
+    return order;
+}
+
+// job(c, stream, slot) for every molecule c, slot = the worker's index (its
+// workspace slot); the workers' streams start after the work enqueued on
+// `stream` so far, and `stream` waits for all of them.  Returns the first
+// non-OK status in molecule order.
+template <class Job>
+int run_workers(int32_t nmol, const cds_mol* mols, cudaStream_t stream, Job job) {
+    cudaStream_t ws[kWorkers];
+    int st = worker_streams(ws);
+    if (st) return st;
+    int dev = 0;
+    CDS_CUDA_TRY(cudaGetDevice(&dev));
+    cudaEvent_t start, done[kWorkers];
+    CDS_CUDA_TRY(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    for (int t = 0; t < kWorkers; ++t)
+        CDS_CUDA_TRY(cudaEventCreateWithFlags(&done[t], cudaEventDisableTiming));
+    CDS_CUDA_TRY(cudaEventRecord(start, stream));
+    const std::vector<int> order = by_size(nmol, mols);
+    std::vector<int> status(nmol, CDS_OK);
+    std::vector<int> werr(kWorkers, CDS_OK);
+    std::atomic<int> next{0};
+    auto worker = [&](int t) {
+        if (cudaSetDevice(dev) != cudaSuccess || cudaStreamWaitEvent(ws[t], start, 0) != cudaSuccess) {
+            werr[t] = CDS_ERR_CUDA;
+            return;
+        }
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= nmol) break;
+            status[order[i]] = job(order[i], ws[t], t);
+        }
+        if (cudaEventRecord(done[t], ws[t]) != cudaSuccess) werr[t] = CDS_ERR_CUDA;
+    };
+    const int nt = std::min<int>(kWorkers, nmol);
+    std::vector<std::thread> threads;
+    for (int t = 0; t < nt; ++t) threads.emplace_back(worker, t);
+    for (std::thread& th : threads) th.join();
+    int res = CDS_OK;
+    for (int t = 0; t < nt; ++t) {
+        if (!res && werr[t]) res = werr[t];
+        if (!werr[t] && cudaStreamWaitEvent(stream, done[t], 0) != cudaSuccess && !res)
+            res = CDS_ERR_CUDA;
+    }
+    for (int c = 0; c < nmol && !res; ++c) res = status[c];
+    cudaEventDestroy(start);
+    for (int t = 0; t < kWorkers; ++t) cudaEventDestroy(done[t]);
+    return res;
+}
+
+// Bytes of one worker's slot: the largest molecule's tensor-core
+// decomposition workspace (when precision is OZAKI) or transform workspace.
+size_t worker_slot_bytes(int32_t nmol, const cds_mol* mols, int32_t precision) {
+    size_t b = 0;
+    for (int c = 0; c < nmol; ++c) {
+        b = std::max(b, cds_cd_to_mo_workspace_bytes(mols[c].nbf, mols[c].nbf, mols[c].nocc,
+                                                     mols[c].max_rank, mols[c].np));
+        if (precision == CDS_PREC_OZAKI)
+            b = std::max(b, cd_workspace_bytes_prec(mols[c].nbf, mols[c].max_rank, CDS_PREC_OZAKI));
+    }
+    return align_up(b);
 }
 
 // Per-orbital data of the batched Newton solve.
@@ -255,8 +352,11 @@ extern "C" int cds_batch_offsets(int32_t nmol, const cds_mol* mols, int64_t* off
     return CDS_OK;
 }
 
-extern "C" size_t cds_batch_workspace_bytes(int32_t nmol, const cds_mol* mols, int32_t precision) {
-    if (!mols_ok(nmol, mols)) return 0;
+// [CD or transform scratch | Sigma / Newton state]: the second part must
+// outlive the first when a graph of the second is replayed.  Worker slots
+// (optional) follow: the per-molecule tensor-core decompositions and the
+// concurrent transforms.
+static size_t base_bytes(int32_t nmol, const cds_mol* mols) {
     std::vector<BatchMol> bm = to_internal(nmol, mols);
     BatchOffsets tot;
     offsets_of(nmol, mols, &tot);
@@ -265,11 +365,22 @@ extern "C" size_t cds_batch_workspace_bytes(int32_t nmol, const cds_mol* mols, i
     for (int c = 0; c < nmol; ++c)
         tr = std::max(tr, cds_cd_to_mo_workspace_bytes(mols[c].nbf, mols[c].nbf, mols[c].nocc,
                                                        mols[c].max_rank, mols[c].np));
-    size_t qp = qp_batch_layout(nullptr, nmol, bm.data(), tot.orb).bytes;
-    (void)precision;
-    // [CD or transform scratch | Sigma / Newton state]: the second part must
-    // outlive the first when a graph of the second is replayed
-    return align_up(std::max(cd, tr)) + qp;
+    return align_up(std::max(cd, tr)) +
+           align_up(qp_batch_layout(nullptr, nmol, bm.data(), tot.orb).bytes);
+}
+
+extern "C" size_t cds_batch_workspace_bytes(int32_t nmol, const cds_mol* mols, int32_t precision) {
+    if (!mols_ok(nmol, mols)) return 0;
+    return base_bytes(nmol, mols) + kWorkers * worker_slot_bytes(nmol, mols, precision);
+}
+
+// The worker slots of a workspace of `bytes` bytes for `precision`, or null
+// when it has none that large.
+static char* worker_part(void* ws, size_t bytes, int32_t nmol, const cds_mol* mols,
+                         int32_t precision) {
+    const size_t base = base_bytes(nmol, mols);
+    if (bytes < base + kWorkers * worker_slot_bytes(nmol, mols, precision)) return nullptr;
+    return static_cast<char*>(ws) + base;
 }
 
 static void* qp_part(void* ws, int32_t nmol, const cds_mol* mols) {
@@ -291,7 +402,24 @@ extern "C" int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const d
         return CDS_ERR_ARG;
     if (!(delta >= 0.0) || (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC))
         return CDS_ERR_ARG;
-    if (workspace_bytes < cds_batch_workspace_bytes(nmol, mols, 0)) return CDS_ERR_WORKSPACE;
+    if (precision == CDS_PREC_OZAKI) {
+        char* slots = worker_part(workspace, workspace_bytes, nmol, mols, CDS_PREC_OZAKI);
+        if (!slots) return CDS_ERR_WORKSPACE;
+        const size_t slot = worker_slot_bytes(nmol, mols, CDS_PREC_OZAKI);
+        std::vector<BatchOffsets> off = offsets_of(nmol, mols, nullptr);
+        return run_workers(nmol, mols, stream, [&](int c, cudaStream_t s, int t) {
+            const cds_mol& m = mols[c];
+            int32_t Mc = 0;
+            const int st = cd_decompose_run(m.nbf, xyz + 3 * off[c].basis, alpha + off[c].basis,
+                                            atom + off[c].basis, delta, scheme, m.max_rank,
+                                            CDS_PREC_OZAKI, L + off[c].L, piv + off[c].piv,
+                                            D + off[c].pair, &Mc, nullptr,
+                                            slots + (size_t)t * slot, slot, s, nullptr, nullptr);
+            M_out[c] = Mc;
+            return st;
+        });
+    }
+    if (workspace_bytes < base_bytes(nmol, mols)) return CDS_ERR_WORKSPACE;
     std::vector<BatchMol> bm = to_internal(nmol, mols);
     std::vector<BatchOffsets> off = offsets_of(nmol, mols, nullptr);
     return cd_batch_decompose(nmol, bm.data(), off.data(), xyz, alpha, atom, delta, scheme,
@@ -304,11 +432,21 @@ extern "C" int cds_batch_cd_to_mo(int32_t nmol, const cds_mol* mols, const int32
                                   int32_t precision, double* Lov, double* Lp, void* workspace,
                                   size_t workspace_bytes, cudaStream_t stream) {
     if (!mols_ok(nmol, mols) || !M || !L || !C || !Lov || !Lp) return CDS_ERR_ARG;
-    if (workspace_bytes < cds_batch_workspace_bytes(nmol, mols, precision)) return CDS_ERR_WORKSPACE;
+    if (workspace_bytes < base_bytes(nmol, mols)) return CDS_ERR_WORKSPACE;
     std::vector<BatchOffsets> off = offsets_of(nmol, mols, nullptr);
+    for (int c = 0; c < nmol; ++c)
+        if (M[c] < 0 || M[c] > mols[c].max_rank) return CDS_ERR_ARG;
+    if (char* slots = worker_part(workspace, workspace_bytes, nmol, mols, 0)) {
+        const size_t slot = worker_slot_bytes(nmol, mols, 0);
+        return run_workers(nmol, mols, stream, [&](int c, cudaStream_t s, int t) {
+            const cds_mol& m = mols[c];
+            return cds_cd_to_mo(m.nbf, m.nbf, m.nocc, M[c], L + off[c].L, C + off[c].C,
+                                orb + off[c].orb, m.np, precision, Lov + off[c].ov, Lp + off[c].p,
+                                slots + (size_t)t * slot, slot, s);
+        });
+    }
     for (int c = 0; c < nmol; ++c) {
         const cds_mol& m = mols[c];
-        if (M[c] < 0 || M[c] > m.max_rank) return CDS_ERR_ARG;
         size_t need = cds_cd_to_mo_workspace_bytes(m.nbf, m.nbf, m.nocc, M[c], m.np);
         int st = cds_cd_to_mo(m.nbf, m.nbf, m.nocc, M[c], L + off[c].L, C + off[c].C,
                               orb + off[c].orb, m.np, precision, Lov + off[c].ov, Lp + off[c].p,
@@ -325,7 +463,7 @@ extern "C" int cds_batch_sigma2(int32_t nmol, const cds_mol* mols, const int32_t
                                 size_t workspace_bytes, cudaStream_t stream) {
     if (!mols_ok(nmol, mols) || !M || !Lov || !Lp || !eps || !E || !sigma) return CDS_ERR_ARG;
     if (!is_split16(precision)) return CDS_ERR_UNSUPPORTED;
-    if (workspace_bytes < cds_batch_workspace_bytes(nmol, mols, precision)) return CDS_ERR_WORKSPACE;
+    if (workspace_bytes < base_bytes(nmol, mols)) return CDS_ERR_WORKSPACE;
     std::vector<BatchMol> bm = to_internal(nmol, mols);
     BatchOffsets tot;
     std::vector<BatchOffsets> off = offsets_of(nmol, mols, &tot);
@@ -347,7 +485,7 @@ extern "C" int cds_batch_qp_solve(int32_t nmol, const cds_mol* mols, const int32
         !status || max_iter < 1 || !(conv >= 0.0))
         return CDS_ERR_ARG;
     if (!is_split16(precision)) return CDS_ERR_UNSUPPORTED;
-    if (workspace_bytes < cds_batch_workspace_bytes(nmol, mols, precision)) return CDS_ERR_WORKSPACE;
+    if (workspace_bytes < base_bytes(nmol, mols)) return CDS_ERR_WORKSPACE;
     std::vector<BatchMol> bm = to_internal(nmol, mols);
     BatchOffsets tot;
     std::vector<BatchOffsets> off = offsets_of(nmol, mols, &tot);
@@ -375,7 +513,7 @@ extern "C" int cds_batch_graph_create(int32_t nmol, const cds_mol* mols, const i
         !pole || !iters || !status || max_iter < 1 || !(conv >= 0.0))
         return CDS_ERR_ARG;
     if (!is_split16(precision)) return CDS_ERR_UNSUPPORTED;
-    if (workspace_bytes < cds_batch_workspace_bytes(nmol, mols, precision)) return CDS_ERR_WORKSPACE;
+    if (workspace_bytes < base_bytes(nmol, mols)) return CDS_ERR_WORKSPACE;
     std::vector<BatchMol> bm = to_internal(nmol, mols);
     BatchOffsets tot;
     std::vector<BatchOffsets> off = offsets_of(nmol, mols, &tot);

@@ -219,3 +219,21 @@ def test_batch_float_pair_decomposition(batch):
         assert torch.equal(bf.view("piv", c, (M[c],)), b.view("piv", c, (M[c],)))
         torch.testing.assert_close(bf.view("L", c, (M[c], npr)), b.view("L", c, (M[c], npr)),
                                    rtol=0, atol=1e-8)
+
+
+def test_batch_tensor_core_decomposition(batch):
+    """The batched decomposition with the tensor-core passes (each molecule's
+    own decomposition on the library's worker threads and streams) against
+    the FP64 batch: every molecule's pivots identical, vectors within 1e-9
+    (the single-molecule tensor-core bar)."""
+    mols, b, M, inp = batch
+    spec = [(m.nbf, m.nocc, len(m.orbitals), m.nE, C.default_max_rank(m.nbf)) for m in mols]
+    bt = C.Batch(spec, DEV, "bf16x3", cd_precision="ozaki")
+    Mt = bt.cd_decompose(inp["xyz"], inp["al"], inp["at"], mols[0].delta, precision="ozaki")
+    torch.cuda.synchronize()
+    assert Mt == M
+    for c, m in enumerate(mols):
+        npr = G.npair(m.nbf)
+        assert torch.equal(bt.view("piv", c, (M[c],)), b.view("piv", c, (M[c],)))
+        torch.testing.assert_close(bt.view("L", c, (M[c], npr)), b.view("L", c, (M[c], npr)),
+                                   rtol=0, atol=1e-9)
