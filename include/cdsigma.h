@@ -154,12 +154,16 @@ size_t cds_cd_workspace_bytes(int32_t nbf);
  * steps): each stored element is also kept as a 56-bit fixed-point number
  * below its pair's power-of-two scale (> sqrt of the initial diagonal), in
  * eight exact BF16 slices of 7 bits, and the pass multiplies these slices
- * with exact products and exact FP32 sums (36 slice pairs; nbf up to ~1440,
- * the candidate search holding the block maxima in shared memory); the steps
- * in between add the vectors made since in float pairs.  The pivot sequence
- * is the FP64 one (tested at C60 size).  Its workspace is
- * cds_cd_workspace_bytes_prec (the slice store takes 16 bytes per pair and
- * vector of max_rank).
+ * with exact products and exact FP32 sums (36 slice pairs; at most 2048 x 512
+ * pairs after screening, the candidate search holding the block maxima in
+ * shared memory, else CDS_ERR_UNSUPPORTED); the steps
+ * in between add the vectors made since in float pairs.  Pairs whose initial
+ * diagonal is below 1e-40 of the largest are screened out (Schwarz: each of
+ * their vector elements is below 1e-20 of the square root of the largest
+ * diagonal); they return L = 0 and D = D0, and the steps run on the other
+ * pairs only.  The pivot sequence is the FP64 one (tested at C60 size).  Its
+ * workspace is cds_cd_workspace_bytes_prec (the slice store takes 16 bytes
+ * and the compact vectors 8 bytes per pair and vector of max_rank).
  * Inputs (device): xyz, alpha, atom.  Outputs (device, caller-owned):
  *   L     [max_rank][npair] fp64, rows 0..M-1 written;
  *   piv   [max_rank] int32 packed pivot index of each vector;
@@ -633,10 +637,19 @@ int cds_graph_destroy(cds_graph* graph);
  *     CTAs (default), 1 = each CTA takes a contiguous range;
  *   CDS_TUNE_NEWTON_CACHE: 1 = the batched grid pass keeps the numerators
  *     and the batched Newton passes evaluate Sigma from them (default), 0 =
- *     each Newton pass recomputes the integrals.
+ *     each Newton pass recomputes the integrals;
+ *   CDS_TUNE_CD_GRAPH: the tensor-core decomposition replays each chunk of
+ *     32 steps as one CUDA graph (one launch instead of 96) when max_rank is
+ *     at least this value and the stream is not a default stream (0 = never;
+ *     default 512; the batched form's worker threads launch step by step);
+ *   CDS_TUNE_PIPE_SPLIT: in cds_cd_decompose_to_mo with a tensor-core
+ *     transform, the transform's GEMMs take at most this many CTAs (one per
+ *     SM) and the decomposition's projection GEMM the other SMs, so the two
+ *     streams run side by side (0 = no split, default).
  * Graphs keep the configuration they were captured with.
  * ---------------------------------------------------------------------- */
-enum { CDS_TUNE_ENERGY_CHUNK = 0, CDS_TUNE_ITEM_ORDER = 1, CDS_TUNE_NEWTON_CACHE = 2 };
+enum { CDS_TUNE_ENERGY_CHUNK = 0, CDS_TUNE_ITEM_ORDER = 1, CDS_TUNE_NEWTON_CACHE = 2,
+       CDS_TUNE_CD_GRAPH = 3, CDS_TUNE_PIPE_SPLIT = 4 };
 int cds_tune_set(int32_t knob, int32_t value);   /* CDS_ERR_ARG on an invalid pair */
 int cds_tune_get(int32_t knob);                  /* -1 for an unknown knob */
 

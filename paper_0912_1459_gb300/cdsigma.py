@@ -798,7 +798,7 @@ class BatchGraph:
             self.h = None
 
 
-TUNE_ENERGY_CHUNK, TUNE_ITEM_ORDER, TUNE_NEWTON_CACHE = 0, 1, 2
+TUNE_ENERGY_CHUNK, TUNE_ITEM_ORDER, TUNE_NEWTON_CACHE, TUNE_CD_GRAPH, TUNE_PIPE_SPLIT = 0, 1, 2, 3, 4
 
 
 def cds_tune_set(knob: int, value: int) -> None:

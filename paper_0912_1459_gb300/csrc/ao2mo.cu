@@ -653,6 +653,14 @@ extern "C" int cds_cd_to_mo_backward(int32_t nbf, int32_t nmo, int32_t nocc, int
 // the end); two strided copies compact them at the end.
 // ===========================================================================
 namespace cds {
+int& pipe_tr_ctas() {
+    static thread_local int v = 0;
+    return v;
+}
+namespace tc {
+int tune_pipe_split();
+}
+
 namespace {
 
 struct PipeStreams {
@@ -758,6 +766,11 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
                    : f32x2_batch(nbf, nmo, nocc, np, Ld, Lq, K0, kb, max_rank, lay.lov_cap,
                                  lay.lp_cap, lay.ao, ps.tr);
     };
+    // the SM split while this thread runs the pipeline
+    struct SplitGuard {
+        SplitGuard(int v) { pipe_tr_ctas() = v; }
+        ~SplitGuard() { pipe_tr_ctas() = 0; }
+    } split_guard(tcx ? tc::tune_pipe_split() : 0);
     int32_t next = 0;   // first vector not yet handed to the transform
     CdChunkHook hook = [&](int32_t rows, bool done) -> int {
         while (next < rows && (done || next + kAoBatch <= rows)) {

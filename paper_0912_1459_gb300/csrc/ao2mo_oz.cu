@@ -437,7 +437,8 @@ int run_gemm(const __nv_bfloat16* a, int64_t a_plane, const float* sa, int64_t a
     CDS_CUDA_TRY(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)SMEM_BYTES));
     const int64_t tiles = (int64_t)g.mtiles * g.ntiles;
-    const int grid = (int)std::min<int64_t>(tiles, device_sms());
+    const int cap = pipe_tr_ctas() > 0 ? std::min(pipe_tr_ctas(), device_sms()) : device_sms();
+    const int grid = (int)std::min<int64_t>(tiles, cap);
     k_oz_gemm<<<grid, THREADS, SMEM_BYTES, stream>>>(maps, g, err);
     CDS_LAUNCH_CHECK();
     return CDS_OK;

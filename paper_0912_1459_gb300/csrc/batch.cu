@@ -414,7 +414,9 @@ extern "C" int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const d
                                             atom + off[c].basis, delta, scheme, m.max_rank,
                                             CDS_PREC_OZAKI, L + off[c].L, piv + off[c].piv,
                                             D + off[c].pair, &Mc, nullptr,
-                                            slots + (size_t)t * slot, slot, s, nullptr, nullptr);
+                                            slots + (size_t)t * slot, slot, s, nullptr, nullptr,
+                                            false);   // chunk graphs: 570 against 370 ms
+                                                      // (64 clusters, 8 threads)
             M_out[c] = Mc;
             return st;
         });

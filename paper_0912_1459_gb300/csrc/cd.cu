@@ -837,6 +837,7 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
                 }
             }
         }
+        if constexpr (TC) ctrl->kstep = made;   // every block of this step has read it
         ctrl->counter = 0;
     }
 }
@@ -873,12 +874,14 @@ k_cd_project_spec(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __r
 // K >= k) and slice the candidates' rows [0, k) into the B planes, for the
 // projection GEMM that follows; otherwise the kernel returns at once.
 __global__ void __launch_bounds__(kUpdThreads, 4)
-k_cd_project_tc(int64_t n, int32_t k, const double* __restrict__ L,
-                const float* __restrict__ sigA, __nv_bfloat16* __restrict__ A,
-                __nv_bfloat16* __restrict__ B, float* __restrict__ sigB, const CdCtrl* ctrl) {
+k_cd_project_tc(int64_t n, const double* __restrict__ L, const float* __restrict__ sigA,
+                __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B,
+                float* __restrict__ sigB, const CdCtrl* ctrl) {
     pdl_trigger();
     pdl_wait();
-    if (ctrl->done || ctrl->pass == 0 || k == 0) return;
+    if (ctrl->done || ctrl->pass == 0) return;
+    const int32_t k = ctrl->kstep;   // the step number lives on the device (graph replays)
+    if (k == 0) return;
     const float2* Lf = reinterpret_cast<const float2*>(L);
     const int32_t kd = ctrl->kdone;
     const int32_t kend = (k + kGroupTC - 1) / kGroupTC * kGroupTC;
@@ -926,10 +929,123 @@ k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
         pdl_wait();
     }
     if (ctrl->done) return;
+    if constexpr (TC) k = ctrl->kstep;   // the step number lives on the device (graph replays)
     cd_step_body<DF, SPEC, TC>(n, k, max_rank, L, D, cand, ecol, G,
                            reinterpret_cast<long long*>(blk_a),
                            reinterpret_cast<long long*>(blk_b), blk_i, piv, ctrl, blockIdx.x,
                            gridDim.x, pf);
+}
+
+// ---- screening of the tensor-core form (kScreenRel) ----
+__device__ __forceinline__ int block_excl_scan(int v, int* total) {
+    __shared__ int warp_sums[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int s = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;   // inclusive over warps
+    }
+    __syncthreads();
+    const int before = (w > 0 ? warp_sums[w - 1] : 0) + x - v;
+    *total = warp_sums[nw - 1];
+    __syncthreads();
+    return before;
+}
+
+// Live pairs per compaction block.
+__global__ void __launch_bounds__(kScanThreads)
+k_screen_count(const double* __restrict__ D, int64_t n, const CdCtrl* ctrl, int32_t* cnt) {
+    const double thr = kScreenRel * ctrl->scale;
+    const int64_t I0 = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    int v = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) v += (I0 + i < n && D[I0 + i] >= thr) ? 1 : 0;
+    int total = 0;
+    block_excl_scan(v, &total);
+    if (threadIdx.x == 0) cnt[blockIdx.x] = total;
+}
+
+// Exclusive prefix over the block counts (one block), the total into ctrl.
+__global__ void __launch_bounds__(1024) k_screen_scan(int32_t* cnt, int nb, CdCtrl* ctrl) {
+    int run = 0;
+    for (int b0 = 0; b0 < nb; b0 += blockDim.x) {
+        const int b = b0 + threadIdx.x;
+        const int v = b < nb ? cnt[b] : 0;
+        int total = 0;
+        const int before = block_excl_scan(v, &total);
+        if (b < nb) cnt[b] = run + before;
+        run += total;
+    }
+    if (threadIdx.x == 0) ctrl->nlive = run;
+}
+
+// The live pairs in packed order: live[j] = I, and their data gathered (pair
+// data as float pairs, candidate flag, initial diagonal).
+__global__ void __launch_bounds__(kScanThreads)
+k_screen_gather(PairSoA pd, const double* __restrict__ D, const uint8_t* __restrict__ cand,
+                int64_t n, const CdCtrl* ctrl, const int32_t* __restrict__ cnt,
+                int32_t* __restrict__ live, PairF2 pf, double* __restrict__ Dc,
+                uint8_t* __restrict__ candc) {
+    const double thr = kScreenRel * ctrl->scale;
+    const int64_t I0 = (int64_t)blockIdx.x * kScanChunk + threadIdx.x * kScanPer;
+    bool f[kScanPer];
+    int v = 0;
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        f[i] = I0 + i < n && D[I0 + i] >= thr;
+        v += f[i] ? 1 : 0;
+    }
+    int total = 0;
+    int pos = cnt[blockIdx.x] + block_excl_scan(v, &total);
+#pragma unroll
+    for (int i = 0; i < kScanPer; ++i) {
+        if (!f[i]) continue;
+        const int64_t I = I0 + i;
+        live[pos] = (int32_t)I;
+        Dc[pos] = D[I];
+        candc[pos] = cand[I];
+        pf.p[pos] = to_f2(pd.p[I]);
+        pf.Px[pos] = to_f2(pd.Px[I]);
+        pf.Py[pos] = to_f2(pd.Py[I]);
+        pf.Pz[pos] = to_f2(pd.Pz[I]);
+        pf.Kp[pos] = to_f2(pd.Kp[I]);
+        ++pos;
+    }
+}
+
+// Rows [r0, r0 + nrows) of the compact vectors into the full rows of L (whose
+// screened entries were zeroed), as float pairs.
+__global__ void k_screen_scatter(const double* __restrict__ Lc, int64_t nc,
+                                 const int32_t* __restrict__ live, double* __restrict__ L,
+                                 int64_t n, int32_t r0, int32_t nrows) {
+    const int64_t total = (int64_t)nrows * nc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = r0 + i / nc, j = i % nc;
+        L[r * n + live[j]] = Lc[r * nc + j];
+    }
+}
+
+// Pivots back to packed indices; the live pairs' residuals into D (the
+// screened ones keep D0).
+__global__ void k_screen_finish(const int32_t* __restrict__ pivc, int32_t M,
+                                const int32_t* __restrict__ live, int32_t* __restrict__ piv,
+                                const double* __restrict__ Dc, int64_t nc, double* __restrict__ D) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < M) piv[i] = live[pivc[i]];
+    if (i < nc) D[live[i]] = Dc[i];
 }
 
 // Float pairs (hi, lo) of the first count elements of L back to FP64, in place.
@@ -952,6 +1068,13 @@ struct CdLayout {
     float* sigB;      // [kSpecTC] candidate scales
     int32_t* err;     // the GEMM's bounded-wait error word
     int32_t kcap;
+    // screening (tensor-core form): the live pairs and the compact problem
+    int32_t* live;    // [npair] packed index of live pair j
+    int32_t* scan;    // [npair / kScanChunk + 1] block counts / offsets
+    double* Dc;       // [npair] compact residual diagonal
+    uint8_t* candc;   // [npair] compact candidate flags
+    int32_t* pivc;    // [max_rank] compact pivots
+    double* Lc;       // [max_rank][npair] compact vectors (float pairs)
     PairF2 pf;        // pair data as float pairs (float-pair mode)
     double* blk_a;
     double* blk_b;
@@ -1008,6 +1131,12 @@ static CdLayout cd_layout(void* ws, int32_t nbf, bool spec = true, bool tc = fal
     l.sigA = tc ? c.take<float>(n) : nullptr;
     l.sigB = tc ? c.take<float>(kSpecTC) : nullptr;
     l.err = tc ? c.take<int32_t>(4) : nullptr;
+    l.live = tc ? c.take<int32_t>(n) : nullptr;
+    l.scan = tc ? c.take<int32_t>(n / kScanChunk + 2) : nullptr;
+    l.Dc = tc ? c.take<double>(n) : nullptr;
+    l.candc = tc ? c.take<uint8_t>(n) : nullptr;
+    l.pivc = tc ? c.take<int32_t>(std::max(max_rank, 1)) : nullptr;
+    l.Lc = tc ? c.take<double>((size_t)std::max(max_rank, 1) * n) : nullptr;
     l.pf.p = spec ? c.take<float2>(n) : nullptr;
     l.pf.Px = spec ? c.take<float2>(n) : nullptr;
     l.pf.Py = spec ? c.take<float2>(n) : nullptr;
@@ -1081,66 +1210,53 @@ struct GemmTiming {
 };
 static GemmTiming g_gemm_timing;
 
-// The decomposition of cds_cd_decompose.  on_chunk (may be null) runs after
-// every host check with the number of rows of L that are final and whether
-// the decomposition has stopped; before the float-pair rows are converted to
-// FP64 at the end, stream waits for convert_after (may be null), so work that
-// reads the float-pair rows can run on another stream meanwhile.
-int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const int32_t* atom,
-                     double delta, int32_t scheme, int32_t max_rank, int32_t precision, double* L,
-                     int32_t* piv, double* D, int32_t* M_out, double* delta_eff_out,
-                     void* workspace, size_t workspace_bytes, cudaStream_t stream,
-                     const CdChunkHook* on_chunk, cudaStream_t convert_after) {
-    if (nbf <= 0 || !xyz || !alpha || !L || !piv || !D || !M_out || max_rank < 0)
-        return CDS_ERR_ARG;
-    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2 && precision != CDS_PREC_OZAKI)
-        return CDS_ERR_UNSUPPORTED;
-    const bool tcm = precision == CDS_PREC_OZAKI;
-    const bool df = precision == CDS_PREC_F32X2 || tcm;
-    if (!(delta >= 0.0)) return CDS_ERR_ARG;
-    if (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC) return CDS_ERR_ARG;
-    if (scheme == CDS_SCHEME_ATOMIC && !atom) return CDS_ERR_ARG;
-    int64_t n = npair_of(nbf);
-    CdLayout lay = cd_layout(workspace, nbf, df, tcm, max_rank);
-    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
-    if (tcm && step_blocks(n) > kMaxBlocksTC) return CDS_ERR_UNSUPPORTED;
-    int st = build_pairs(nbf, xyz, alpha, lay.pd, stream);
-    if (st) return st;
-    if (df) {
-        k_pairs_to_f2<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(lay.pd, lay.pf, n);
-        CDS_LAUNCH_CHECK();
-    }
-    CDS_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, sizeof(CdCtrl), stream));
+// The tensor-core form after the initial diagonal: screening, then the steps
+// on the compact problem of the live pairs (vectors in lay.Lc, scattered into
+// L's full rows after each host check, so the hook sees float-pair rows as
+// in the float-pair form).
+static int cd_run_tc(int64_t n, int32_t max_rank, double* L, int32_t* piv, double* D,
+                     int32_t* M_out, double* delta_eff_out, const CdLayout& lay,
+                     cudaStream_t stream, const CdChunkHook* on_chunk,
+                     cudaStream_t convert_after, bool chunk_graph) {
+    const int nsb = (int)((n + kScanChunk - 1) / kScanChunk);
+    k_screen_count<<<nsb, kScanThreads, 0, stream>>>(D, n, lay.ctrl, lay.scan);
+    CDS_LAUNCH_CHECK();
+    k_screen_scan<<<1, 1024, 0, stream>>>(lay.scan, nsb, lay.ctrl);
+    CDS_LAUNCH_CHECK();
+    k_screen_gather<<<nsb, kScanThreads, 0, stream>>>(lay.pd, D, lay.cand, n, lay.ctrl, lay.scan,
+                                                      lay.live, lay.pf, lay.Dc, lay.candc);
+    CDS_LAUNCH_CHECK();
+    int32_t nlive = 0;
+    CDS_CUDA_TRY(cudaMemcpyAsync(&nlive, &lay.ctrl->nlive, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 stream));
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (nlive <= 0) return CDS_ERR_NOT_PD;   // no diagonal passed the test: NaN or a zero scale
+    const int64_t nc = nlive;
+    if (step_blocks(nc) > kMaxBlocksTC) return CDS_ERR_UNSUPPORTED;
     const int nsm = sm_count();
-    const int nb = cd_blocks(n), ns = sel_blocks(n);
-    const int ne = eri_blocks(n, nsm), np_ = ne + dot_tiles(n), nu = step_blocks(n);
-    const int nres = (int)std::min<int64_t>(4 * nsm, dot_tiles(n));   // resident grid
-    k_cd_init<<<nb, kCdThreads, 0, stream>>>(lay.pd, atom, scheme, n, delta, D, lay.cand,
-                                            lay.blk_a, lay.blk_b, lay.ctrl);
+    const int ns = sel_blocks(nc), nu = step_blocks(nc);
+    const int nres = (int)std::min<int64_t>(4 * nsm, dot_tiles(nc));   // resident grid
+    k_cd_select<<<ns, kCdThreads, 0, stream>>>(nc, 0, max_rank, lay.Dc, lay.candc, lay.blk_i,
+                                              lay.pivc, lay.ctrl);
     CDS_LAUNCH_CHECK();
-    k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, 0, max_rank, D, lay.cand, lay.blk_i, piv,
-                                              lay.ctrl);
+    // pair scales from the initial diagonal, the GEMM's tensor maps (fixed for
+    // the whole decomposition) and error word
+    k_cd_tc_scales<<<(unsigned)((nc + 255) / 256), 256, 0, stream>>>(lay.Dc, nc, lay.sigA);
     CDS_LAUNCH_CHECK();
-    // tensor-core form: pair scales from the initial diagonal, the GEMM's
-    // tensor maps (fixed for the whole decomposition) and error word
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.err, 0, sizeof(int32_t), stream));
     CdTcGemm* gemm = nullptr;
     struct GemmGuard {
         CdTcGemm*& g;
         ~GemmGuard() { if (g) cd_tc_gemm_free(g); }
     } guard{gemm};
-    if (tcm) {
-        k_cd_tc_scales<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(D, n, lay.sigA);
-        CDS_LAUNCH_CHECK();
-        CDS_CUDA_TRY(cudaMemsetAsync(lay.err, 0, sizeof(int32_t), stream));
-        st = cd_tc_gemm_setup(&gemm, n, lay.kcap, lay.A, lay.B, lay.sigA, lay.sigB, lay.G,
+    int st = cd_tc_gemm_setup(&gemm, nc, lay.kcap, lay.A, lay.B, lay.sigA, lay.sigB, lay.G,
                               lay.ctrl, lay.err);
-        if (st) return st;
-    }
+    if (st) return st;
     // CUDA events around every GEMM launch of the steps that run (one pair per
     // step of a host-check chunk, reused), summed after each check
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CDS_CUDA_TRY(cudaStreamIsCapturing(stream, &cap));
-    const bool timing = tcm && g_gemm_timing.on && cap == cudaStreamCaptureStatusNone;
+    const bool timing = g_gemm_timing.on && cap == cudaStreamCaptureStatusNone;
     std::vector<cudaEvent_t> tev;
     struct EventGuard {
         std::vector<cudaEvent_t>& v;
@@ -1152,38 +1268,68 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
             CDS_CUDA_TRY(cudaEventCreate(&e));
             tev.push_back(e);
         }
+    // the kernels of steps [k0, k1) (each reads its step number from ctrl)
+    auto enqueue = [&](int32_t k0, int32_t k1) -> int {
+        for (int32_t k = k0; k < k1; ++k) {
+            CDS_CUDA_TRY(launch_pdl(k_cd_project_tc, (unsigned)nres, kUpdThreads, 0, stream, nc,
+                                    (const double*)lay.Lc, (const float*)lay.sigA, lay.A, lay.B,
+                                    lay.sigB, (const CdCtrl*)lay.ctrl));
+            if (timing) CDS_CUDA_TRY(cudaEventRecord(tev[2 * (k - k0)], stream));
+            const int s2 = cd_tc_gemm_launch(gemm, stream);
+            if (s2) return s2;
+            if (timing) CDS_CUDA_TRY(cudaEventRecord(tev[2 * (k - k0) + 1], stream));
+            CDS_CUDA_TRY(launch_pdl(k_cd_update<true, true, true>, (unsigned)nu, kUpdThreads, 0,
+                                    stream, nc, k, max_rank, lay.Lc, lay.Dc,
+                                    (const uint8_t*)lay.candc, (const double*)lay.ecol,
+                                    (const float2*)lay.G, lay.blk_a, lay.blk_b, lay.blk_i,
+                                    lay.pivc, lay.ctrl, lay.pf));
+        }
+        return CDS_OK;
+    };
+    // a full chunk of steps as one CUDA graph, replayed at every host check
+    // (one launch instead of 3 x kHostCheckEvery): not under capture or
+    // timing, not on a default stream (no capture there), and only for
+    // decompositions long enough to repay the instantiation
+    cudaGraphExec_t chunk = nullptr;
+    struct ExecGuard {
+        cudaGraphExec_t& e;
+        ~ExecGuard() { if (e) cudaGraphExecDestroy(e); }
+    } chunk_guard{chunk};
+    const int graph_min = tc::tune_cd_graph();
+    const bool default_stream =
+        stream == nullptr || stream == cudaStreamLegacy || stream == cudaStreamPerThread;
+    if (chunk_graph && !timing && cap == cudaStreamCaptureStatusNone && !default_stream &&
+        graph_min > 0 && max_rank >= std::max(graph_min, kHostCheckEvery)) {
+        cudaGraph_t g = nullptr;
+        CDS_CUDA_TRY(cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal));
+        const int s2 = enqueue(0, kHostCheckEvery);
+        const cudaError_t ce = cudaStreamEndCapture(stream, &g);
+        if (s2) {
+            if (g) cudaGraphDestroy(g);
+            return s2;
+        }
+        CDS_CUDA_TRY(ce);
+        const cudaError_t ie = cudaGraphInstantiate(&chunk, g, 0);
+        cudaGraphDestroy(g);
+        CDS_CUDA_TRY(ie);
+    }
     CdCtrl h{};
     for (int32_t k0 = 0; k0 <= max_rank; k0 += kHostCheckEvery) {
-        int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
-        for (int32_t k = k0; k < k1; ++k) {
-            if (tcm) {
-                CDS_CUDA_TRY(launch_pdl(k_cd_project_tc, (unsigned)nres, kUpdThreads, 0, stream, n,
-                                        k, (const double*)L, (const float*)lay.sigA, lay.A, lay.B,
-                                        lay.sigB, (const CdCtrl*)lay.ctrl));
-                if (timing) CDS_CUDA_TRY(cudaEventRecord(tev[2 * (k - k0)], stream));
-                st = cd_tc_gemm_launch(gemm, stream);
-                if (st) return st;
-                if (timing) CDS_CUDA_TRY(cudaEventRecord(tev[2 * (k - k0) + 1], stream));
-                CDS_CUDA_TRY(launch_pdl(k_cd_update<true, true, true>, (unsigned)nu, kUpdThreads, 0,
-                                        stream, n, k, max_rank, L, D, (const uint8_t*)lay.cand,
-                                        (const double*)lay.ecol, (const float2*)lay.G, lay.blk_a,
-                                        lay.blk_b, lay.blk_i, piv, lay.ctrl, lay.pf));
-            } else if (df) {
-                k_cd_project_spec<<<nres, kUpdThreads, 0, stream>>>(
-                    lay.pd, lay.pf, n, k, L, lay.G, reinterpret_cast<float2*>(lay.ecol),
-                    dot_tiles(n), lay.ctrl);
-                k_cd_update<true, true><<<nu, kUpdThreads, 0, stream>>>(
-                    n, k, max_rank, L, D, lay.cand, lay.ecol, lay.G, lay.blk_a, lay.blk_b,
-                    lay.blk_i, piv, lay.ctrl);
-            } else {
-                k_cd_project<false><<<np_, kUpdThreads, 0, stream>>>(lay.pd, n, k, L, lay.ecol, ne,
-                                                                     lay.ctrl);
-                k_cd_update<false, false><<<nu, kUpdThreads, 0, stream>>>(
-                    n, k, max_rank, L, D, lay.cand, lay.ecol, nullptr, lay.blk_a, lay.blk_b,
-                    lay.blk_i, piv, lay.ctrl);
-            }
+        const int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
+        if (chunk && k1 - k0 == kHostCheckEvery) {
+            CDS_CUDA_TRY(cudaGraphLaunch(chunk, stream));
+        } else if ((st = enqueue(k0, k1))) {
+            return st;
         }
-        count_launches((tcm ? 3ull : 2ull) * (unsigned long long)(k1 - k0));
+        count_launches(3ull * (unsigned long long)(k1 - k0));
+        if (k1 > k0) {   // this chunk's rows into L's full rows (screened entries 0)
+            CDS_CUDA_TRY(cudaMemsetAsync(L + (int64_t)k0 * n, 0,
+                                         (size_t)(k1 - k0) * n * sizeof(double), stream));
+            const int64_t items = (int64_t)(k1 - k0) * nc;
+            k_screen_scatter<<<(unsigned)std::min<int64_t>((items + 255) / 256, 8 * nsm), 256, 0,
+                               stream>>>(lay.Lc, nc, lay.live, L, n, k0, k1 - k0);
+            CDS_LAUNCH_CHECK();
+        }
         CDS_CUDA_TRY(cudaGetLastError());
         CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, stream));
         CDS_CUDA_TRY(cudaStreamSynchronize(stream));
@@ -1204,7 +1350,11 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
     }
     *M_out = h.M;
     if (delta_eff_out) *delta_eff_out = h.delta_eff;
-    if (df && h.M > 0) {
+    const int64_t fin = std::max<int64_t>(h.M, nc);
+    k_screen_finish<<<(unsigned)((fin + 255) / 256), 256, 0, stream>>>(lay.pivc, h.M, lay.live,
+                                                                       piv, lay.Dc, nc, D);
+    CDS_LAUNCH_CHECK();
+    if (h.M > 0) {
         if (convert_after) {
             cudaEvent_t ev;
             CDS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -1216,11 +1366,98 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
         k_pairs_to_fp64<<<(unsigned)((cnt + 255) / 256), 256, 0, stream>>>(L, cnt);
         CDS_LAUNCH_CHECK();
     }
-    if (tcm) {   // a bounded wait of the projection GEMM gave up
-        int32_t e = 0;
-        CDS_CUDA_TRY(cudaMemcpyAsync(&e, lay.err, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    int32_t e = 0;   // a bounded wait of the projection GEMM gave up
+    CDS_CUDA_TRY(cudaMemcpyAsync(&e, lay.err, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (e) return CDS_ERR_TIMEOUT;
+    if (!h.done) return CDS_ERR_RANK_CAP;
+    return h.status;
+}
+
+// The decomposition of cds_cd_decompose.  on_chunk (may be null) runs after
+// every host check with the number of rows of L that are final and whether
+// the decomposition has stopped; before the float-pair rows are converted to
+// FP64 at the end, stream waits for convert_after (may be null), so work that
+// reads the float-pair rows can run on another stream meanwhile.
+int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const int32_t* atom,
+                     double delta, int32_t scheme, int32_t max_rank, int32_t precision, double* L,
+                     int32_t* piv, double* D, int32_t* M_out, double* delta_eff_out,
+                     void* workspace, size_t workspace_bytes, cudaStream_t stream,
+                     const CdChunkHook* on_chunk, cudaStream_t convert_after, bool chunk_graph) {
+    if (nbf <= 0 || !xyz || !alpha || !L || !piv || !D || !M_out || max_rank < 0)
+        return CDS_ERR_ARG;
+    if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2 && precision != CDS_PREC_OZAKI)
+        return CDS_ERR_UNSUPPORTED;
+    const bool tcm = precision == CDS_PREC_OZAKI;
+    const bool df = precision == CDS_PREC_F32X2;
+    if (!(delta >= 0.0)) return CDS_ERR_ARG;
+    if (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC) return CDS_ERR_ARG;
+    if (scheme == CDS_SCHEME_ATOMIC && !atom) return CDS_ERR_ARG;
+    int64_t n = npair_of(nbf);
+    CdLayout lay = cd_layout(workspace, nbf, df || tcm, tcm, max_rank);
+    if (!workspace || workspace_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    int st = build_pairs(nbf, xyz, alpha, lay.pd, stream);
+    if (st) return st;
+    if (df) {
+        k_pairs_to_f2<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(lay.pd, lay.pf, n);
+        CDS_LAUNCH_CHECK();
+    }
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, sizeof(CdCtrl), stream));
+    const int nsm = sm_count();
+    const int nb = cd_blocks(n), ns = sel_blocks(n);
+    const int ne = eri_blocks(n, nsm), np_ = ne + dot_tiles(n), nu = step_blocks(n);
+    const int nres = (int)std::min<int64_t>(4 * nsm, dot_tiles(n));   // resident grid
+    k_cd_init<<<nb, kCdThreads, 0, stream>>>(lay.pd, atom, scheme, n, delta, D, lay.cand,
+                                            lay.blk_a, lay.blk_b, lay.ctrl);
+    CDS_LAUNCH_CHECK();
+    if (tcm)
+        return cd_run_tc(n, max_rank, L, piv, D, M_out, delta_eff_out, lay, stream, on_chunk,
+                         convert_after, chunk_graph);
+    k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, 0, max_rank, D, lay.cand, lay.blk_i, piv,
+                                              lay.ctrl);
+    CDS_LAUNCH_CHECK();
+    CdCtrl h{};
+    for (int32_t k0 = 0; k0 <= max_rank; k0 += kHostCheckEvery) {
+        int32_t k1 = std::min(max_rank, k0 + kHostCheckEvery);
+        for (int32_t k = k0; k < k1; ++k) {
+            if (df) {
+                k_cd_project_spec<<<nres, kUpdThreads, 0, stream>>>(
+                    lay.pd, lay.pf, n, k, L, lay.G, reinterpret_cast<float2*>(lay.ecol),
+                    dot_tiles(n), lay.ctrl);
+                k_cd_update<true, true><<<nu, kUpdThreads, 0, stream>>>(
+                    n, k, max_rank, L, D, lay.cand, lay.ecol, lay.G, lay.blk_a, lay.blk_b,
+                    lay.blk_i, piv, lay.ctrl);
+            } else {
+                k_cd_project<false><<<np_, kUpdThreads, 0, stream>>>(lay.pd, n, k, L, lay.ecol, ne,
+                                                                     lay.ctrl);
+                k_cd_update<false, false><<<nu, kUpdThreads, 0, stream>>>(
+                    n, k, max_rank, L, D, lay.cand, lay.ecol, nullptr, lay.blk_a, lay.blk_b,
+                    lay.blk_i, piv, lay.ctrl);
+            }
+        }
+        count_launches(2ull * (unsigned long long)(k1 - k0));
+        CDS_CUDA_TRY(cudaGetLastError());
+        CDS_CUDA_TRY(cudaMemcpyAsync(&h, lay.ctrl, sizeof(CdCtrl), cudaMemcpyDeviceToHost, stream));
         CDS_CUDA_TRY(cudaStreamSynchronize(stream));
-        if (e) return CDS_ERR_TIMEOUT;
+        if (on_chunk && *on_chunk) {
+            st = (*on_chunk)(h.done ? h.M : k1, h.done != 0);
+            if (st) return st;
+        }
+        if (h.done) break;
+    }
+    *M_out = h.M;
+    if (delta_eff_out) *delta_eff_out = h.delta_eff;
+    if (df && h.M > 0) {
+        if (convert_after) {
+            cudaEvent_t ev;
+            CDS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+            CDS_CUDA_TRY(cudaEventRecord(ev, convert_after));
+            CDS_CUDA_TRY(cudaStreamWaitEvent(stream, ev, 0));
+            CDS_CUDA_TRY(cudaEventDestroy(ev));
+        }
+        const int64_t cnt = (int64_t)h.M * n;
+        k_pairs_to_fp64<<<(unsigned)((cnt + 255) / 256), 256, 0, stream>>>(L, cnt);
+        CDS_LAUNCH_CHECK();
     }
     if (!h.done) return CDS_ERR_RANK_CAP;
     return h.status;

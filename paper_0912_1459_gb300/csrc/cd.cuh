@@ -88,8 +88,20 @@ struct CdCtrl {
     // slice store that are final (a multiple of kGroupTC)
     long long STc[kSpecTC];
     int32_t kdone;
-    int32_t _pad3;
+    int32_t nlive;     // tensor-core form: pairs kept after screening
+    int32_t kstep;     // tensor-core form: the step the kernels run next
+    int32_t _pad4;
 };
+
+// Tensor-core form: pairs whose initial diagonal is below kScreenRel of the
+// largest are left out of the decomposition (Schwarz: every L^K_I of such a
+// pair is below sqrt(D0_I), i.e. below 1e-20 sqrt(max D0); their vectors are
+// returned as 0 and their residual as D0_I, and no other pair's arithmetic
+// involves them).
+constexpr double kScreenRel = 1e-40;
+constexpr int kScanPer = 4;                        // pairs per thread in the compaction
+constexpr int kScanThreads = 256;
+constexpr int kScanChunk = kScanPer * kScanThreads;   // pairs per compaction block
 
 // The exact-slice projection GEMM of one step (cd_tc.cu).  Enqueued at every
 // step of the tensor-core form; it returns at once unless the step starts a

@@ -362,7 +362,10 @@ int cd_tc_gemm_setup(CdTcGemm** out, int64_t n, int32_t kcap, const void* a_plan
     g->args.G = G;
     g->args.ctrl = ctrl;
     g->err = err;
-    g->grid = (int)std::min<int64_t>(g->args.mtiles, tc::device_sms());
+    // in the pipeline the transform holds pipe_tr_ctas() SMs: take the others
+    const int sms = tc::device_sms();
+    const int avail = pipe_tr_ctas() > 0 && pipe_tr_ctas() < sms ? sms - pipe_tr_ctas() : sms;
+    g->grid = (int)std::min<int64_t>(g->args.mtiles, avail);
     // the attribute belongs to the current device: set it at every setup
     if (cudaFuncSetAttribute(k_cd_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)SMEM_BYTES) != cudaSuccess) {

@@ -125,11 +125,17 @@ size_t cd_workspace_bytes_for(int32_t nbf, bool f32x2);
 // Workspace of cds_cd_decompose for a precision (FP64, F32X2, or OZAKI: the
 // tensor-core form, whose slice store holds max_rank columns).
 size_t cd_workspace_bytes_prec(int32_t nbf, int32_t max_rank, int32_t precision);
+// SM split of the pipelined decomposition + transform (cds_cd_decompose_to_mo
+// sets it for the calling thread while it runs): the transform's tensor-core
+// GEMMs take at most this many CTAs, the decomposition's projection GEMM the
+// rest of the SMs; 0 = no split.
+int& pipe_tr_ctas();
 // Called after each host check of the decomposition: (rows of L final, stopped).
 using CdChunkHook = std::function<int(int32_t, bool)>;
 int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const int32_t* atom,
                      double delta, int32_t scheme, int32_t max_rank, int32_t precision, double* L,
                      int32_t* piv, double* D, int32_t* M_out, double* delta_eff_out,
                      void* workspace, size_t workspace_bytes, cudaStream_t stream,
-                     const CdChunkHook* on_chunk, cudaStream_t convert_after);
+                     const CdChunkHook* on_chunk, cudaStream_t convert_after,
+                     bool chunk_graph = true);
 }

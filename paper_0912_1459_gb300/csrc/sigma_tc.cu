@@ -737,7 +737,11 @@ bool make_map(CUtensorMap* m, int fmt, const void* base, uint64_t d0, uint64_t d
 static std::atomic<int> g_energy_chunk{16};
 static std::atomic<int> g_item_order{0};
 static std::atomic<int> g_newton_cache{1};
+static std::atomic<int> g_cd_graph{512};
+static std::atomic<int> g_pipe_split{0};
+int tune_pipe_split() { return g_pipe_split.load(); }
 int tune_energy_chunk() { return g_energy_chunk.load(); }
+int tune_cd_graph() { return g_cd_graph.load(); }
 int tune_item_order() { return g_item_order.load(); }
 int tune_newton_cache() { return g_newton_cache.load(); }
 
@@ -1763,6 +1767,16 @@ extern "C" int cds_tune_set(int32_t knob, int32_t value) {
         g_newton_cache = value;
         return CDS_OK;
     }
+    if (knob == CDS_TUNE_CD_GRAPH) {
+        if (value < 0) return CDS_ERR_ARG;
+        g_cd_graph = value;
+        return CDS_OK;
+    }
+    if (knob == CDS_TUNE_PIPE_SPLIT) {
+        if (value < 0) return CDS_ERR_ARG;
+        g_pipe_split = value;
+        return CDS_OK;
+    }
     return CDS_ERR_ARG;
 }
 
@@ -1771,5 +1785,7 @@ extern "C" int cds_tune_get(int32_t knob) {
     if (knob == CDS_TUNE_ENERGY_CHUNK) return g_energy_chunk.load();
     if (knob == CDS_TUNE_ITEM_ORDER) return g_item_order.load();
     if (knob == CDS_TUNE_NEWTON_CACHE) return g_newton_cache.load();
+    if (knob == CDS_TUNE_CD_GRAPH) return g_cd_graph.load();
+    if (knob == CDS_TUNE_PIPE_SPLIT) return g_pipe_split.load();
     return -1;
 }

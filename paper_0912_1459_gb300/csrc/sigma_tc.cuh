@@ -66,6 +66,8 @@ int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_t
                   void* ws, cudaStream_t stream, int32_t cache_mode);
 namespace tc {
 int tune_newton_cache();   // CDS_TUNE_NEWTON_CACHE
+int tune_cd_graph();       // CDS_TUNE_CD_GRAPH
+int tune_pipe_split();     // CDS_TUNE_PIPE_SPLIT
 }
 
 inline bool is_split16(int32_t precision) {

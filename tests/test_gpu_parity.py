@@ -126,14 +126,41 @@ def test_cd_tensor_core_parity(name, delta, scheme):
     np.testing.assert_allclose(D, ref.D, rtol=0, atol=tol)
 
 
+def test_cd_tensor_core_chunk_graph():
+    """On a stream of its own (not a default stream) and with max_rank >= 512
+    the tensor-core decomposition replays each 32-step chunk as one CUDA
+    graph, the step number read from the device: the oracle's pivots and
+    the same vectors as the step-by-step launches (bit for bit), with the
+    graph switched on and off through CDS_TUNE_CD_GRAPH."""
+    m = O.molecule("c1")
+    ref = O.decomposition("c1", 1e-5, "full")
+    xyz, a, at = dev(m.basis.xyz), dev(m.basis.alpha), dev(m.basis.atom.astype(np.int32))
+    s = torch.cuda.Stream()
+    out = {}
+    try:
+        for knob in (512, 0):
+            G.cdsigma.cds_tune_set(G.cdsigma.TUNE_CD_GRAPH, knob)
+            with torch.cuda.stream(s):
+                L, piv, D, de = G.cds_cd_decompose(xyz, a, at, 1e-5, "full", max_rank=1024,
+                                                   precision="ozaki")
+            s.synchronize()
+            out[knob] = (L.cpu().numpy(), piv.cpu().numpy().astype(np.int64), D.cpu().numpy())
+    finally:
+        G.cdsigma.cds_tune_set(G.cdsigma.TUNE_CD_GRAPH, 512)
+    assert np.array_equal(out[512][1], ref.piv)
+    assert np.array_equal(out[512][0], out[0][0]) and np.array_equal(out[512][2], out[0][2])
+    np.testing.assert_allclose(out[512][0], ref.L, rtol=0, atol=1e-9)
+
+
 def test_cd_tensor_core_refuses_bases_beyond_its_candidate_search():
     """The tensor-core form keeps the update blocks' maxima in shared memory:
-    more than 2048 blocks of 512 pairs (nbf > 1447) is refused before any
-    launch with CDS_ERR_UNSUPPORTED."""
+    more than 2048 blocks of 512 pairs left after screening (here every pair
+    of 1460 diffuse functions in a 20-bohr cube is kept) is refused before
+    the first step with CDS_ERR_UNSUPPORTED."""
     n = 1460
     rng = np.random.default_rng(0)
-    xyz = dev(rng.uniform(0, 40, (n, 3)))
-    a = dev(np.full(n, 0.5))
+    xyz = dev(rng.uniform(0, 20, (n, 3)))
+    a = dev(np.full(n, 0.05))
     at = dev(np.arange(n, dtype=np.int32))
     with pytest.raises(G.CdsError) as ei:
         G.cds_cd_decompose(xyz, a, at, 1e-4, "full", max_rank=1, precision="ozaki")
