@@ -214,7 +214,7 @@ def flops_model(m, M: int) -> dict:
     }
 
 
-CD_GEMM_TRAFFIC_PER_BYTE = 2.985491304e9 / 2.985677584e9
+CD_GEMM_TRAFFIC_PER_BYTE = 1.837544792e9 / 1.838065024e9
 
 
 def peaks():
@@ -365,6 +365,12 @@ def run_ours(args, dist: Dist):
             step(xyz, al, at, C, eps, orbs, E, ws)
         torch.cuda.synchronize()
         gemm_ms, gemm_launches = G.cdsigma.cds_cd_gemm_time()
+        # the same kernel with the decomposition alone (no transform beside it)
+        G.cdsigma.cds_cd_gemm_timing(True)
+        G.cds_cd_decompose(xyz, al, at, args.delta, args.scheme, L_out=Lbuf, workspace=cd_ws,
+                           precision="ozaki")
+        torch.cuda.synchronize()
+        gemm_alone_ms, gemm_alone_launches = G.cdsigma.cds_cd_gemm_time()
         G.cdsigma.cds_cd_gemm_timing(False)
     elapsed_ms = t0.elapsed_time(t1)
     for ev in evs:
@@ -453,11 +459,14 @@ def run_ours(args, dist: Dist):
                       "achieved": sig_flops_qp / (med["qp"] / 1e3) / 1e12,
                       "note": f"{sig_passes_qp} Sigma passes (nE=1); {split} split products per MAC"}
     if fused and gemm_timed:
+        # the pairs the tensor-core form kept after screening
+        nlive = G.cdsigma.cds_cd_live_pairs(m.nbf, fz_ws, "ozaki")
         # one stage for both: the decomposition's HBM bytes (slice store read by
         # the passes, the float-pair extras, the per-step column / vector /
-        # residual traffic); the transform runs on the tensor pipe beside it
-        stage_bytes = float(npr) * (16.0 * cd_stats["streamed"] + 8.0 * cd_stats["extra"] +
-                                    89.0 * M)
+        # residual traffic) over the live pairs; the transform runs on the
+        # tensor pipe beside it
+        stage_bytes = float(nlive) * (16.0 * cd_stats["streamed"] + 8.0 * cd_stats["extra"] +
+                                      89.0 * M)
         med["cd_transform"] = med.pop("cd")
         med.pop("transform")
         roof.pop("cd")
@@ -466,9 +475,10 @@ def run_ours(args, dist: Dist):
             "bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
             "achieved": stage_bytes / (med["cd_transform"] / 1e3) / 1e9,
             "note": (f"pipelined decomposition (tensor-core passes) + exact-slice transform: "
-                     f"bytes = npair*(16*streamed + 8*extra + 89*M) ({cd_stats['passes']} "
-                     f"passes, {cd_stats['streamed']} vectors streamed, {cd_stats['extra']} "
-                     f"extra); the transform's slice-pair GEMMs run on the tensor pipe beside it"),
+                     f"bytes = nlive*(16*streamed + 8*extra + 89*M) ({nlive} live of {npr} "
+                     f"pairs, {cd_stats['passes']} passes, {cd_stats['streamed']} vectors "
+                     f"streamed, {cd_stats['extra']} extra); the transform's slice-pair GEMMs run "
+                     f"on the tensor pipe beside it"),
             "cd_stats": cd_stats}
         # the dominant kernel: k_cd_gemm_tc, per launch.  Algorithmic bytes of
         # a decomposition: the slice store (8 BF16 slices = 16 bytes per pair
@@ -476,10 +486,11 @@ def run_ours(args, dist: Dist):
         # (16 bytes x 32 per vector), the projections written (32 float pairs
         # = 256 bytes per pair) and the pair scales read (4 bytes per pair) at
         # every pass with k0 > 0
-        gemm_bytes = (16.0 * npr * cd_stats["streamed"] + 512.0 * cd_stats["streamed"] +
-                      260.0 * npr * max(cd_stats["passes"] - 1, 0))
+        gemm_bytes = (16.0 * nlive * cd_stats["streamed"] + 512.0 * cd_stats["streamed"] +
+                      260.0 * nlive * max(cd_stats["passes"] - 1, 0))
         per_launch = gemm_bytes * args.steps / max(gemm_launches, 1)
         avg_ms = gemm_ms / max(gemm_launches, 1)
+        alone_gbs = gemm_bytes / (gemm_alone_ms / 1e3) / 1e9 if gemm_alone_ms > 0 else None
         roof["cd_gemm"] = {
             "bound": "hbm", "unit": "GB/s", "peak": pk["hbm_gbs"],
             "achieved": per_launch / (avg_ms / 1e3) / 1e9,
@@ -489,8 +500,15 @@ def run_ours(args, dist: Dist):
                      f"streaming passes) in {args.steps} more steps of the same pipeline after "
                      f"the timed ones: {gemm_launches} launches, CUDA events around each on its "
                      f"stream (early returns of the steps that start no pass included); bytes "
-                     f"per decomposition = npair*(16*streamed + 260*(passes-1)) + 512*streamed "
-                     f"({cd_stats['passes']} passes, {cd_stats['streamed']} vectors streamed)"),
+                     f"per decomposition = nlive*(16*streamed + 260*(passes-1)) + 512*streamed "
+                     f"({nlive} live pairs, {cd_stats['passes']} passes, {cd_stats['streamed']} "
+                     f"vectors streamed)"),
+            "nlive": nlive,
+            "alone": {"achieved": alone_gbs, "ms_total": gemm_alone_ms,
+                      "launches": gemm_alone_launches,
+                      "frac": alone_gbs / pk["hbm_gbs"] if alone_gbs else None,
+                      "note": "one cds_cd_decompose (tensor-core form) with no transform beside it, "
+                              "the same events"},
             "cd_stats": cd_stats}
     elif fused:
         # one stage for both.  The decomposition is bound by FP32 instruction
@@ -555,9 +573,10 @@ def run_ours(args, dist: Dist):
         r["traffic"] = None
     if "cd_gemm" in roof:
         # DRAM bytes per algorithmic byte of k_cd_gemm_tc from one ncu capture
-        # (the pass at k0 = 504 of the C60-shaped decomposition, 4.4 GB case:
-        # 2.985491 GB of dram__bytes_read + write against 2.985678 GB), scaled
-        # to this run's average launch; traffic grows with the columns streamed
+        # (the pass at k0 = 510 of the C60-shaped decomposition, 217,440 live
+        # pairs, 512 columns: 1.837545 GB of dram__bytes_read + write against
+        # 1.838065 GB), scaled to this run's average launch; traffic grows with
+        # the columns streamed
         roof["cd_gemm"]["traffic"] = CD_GEMM_TRAFFIC_PER_BYTE * roof["cd_gemm"]["bytes_per_launch"]
     # (traffic stays null until an ncu capture of the current kernels exists)
     dominant = max(med, key=med.get)

@@ -190,6 +190,12 @@ int cds_cd_decompose(int32_t nbf, const double* xyz, const double* alpha,
 int cds_cd_stats(int32_t nbf, const void* workspace, int32_t precision, int32_t* passes,
                  int64_t* streamed, int64_t* extra, cudaStream_t stream);
 
+/* Pairs the last cds_cd_decompose in this workspace kept after screening
+ * (blocking): CDS_PREC_OZAKI leaves out pairs whose initial diagonal is below
+ * 1e-40 of the largest; FP64 and F32X2 keep all npair. */
+int cds_cd_live_pairs(int32_t nbf, const void* workspace, int32_t precision, int64_t* nlive,
+                      cudaStream_t stream);
+
 /* Candidate pivots whose projections one streaming pass of the given
  * precision forms (host only; a later step continues the pass while its
  * pivot is among them and the pass is not full -- 4 steps for F32X2, 64 for

@@ -46,6 +46,7 @@ _SIGNATURES = {
                                                _vp]),
     "cds_cd_static_max_nbf": (ctypes.c_int, []),
     "cds_cd_candidates": (ctypes.c_int, [_i32]),
+    "cds_cd_live_pairs": (ctypes.c_int, [_i32, _vp, _i32, ctypes.POINTER(ctypes.c_int64), _vp]),
     "cds_cd_gemm_timing": (ctypes.c_int, [_i32]),
     "cds_cd_gemm_time": (ctypes.c_int, [ctypes.POINTER(_f64), ctypes.POINTER(ctypes.c_int64)]),
     "cds_cd_decompose_shells": (ctypes.c_int, [_i32, _vp, _vp, _vp, _vp, _vp, _vp, _f64, _i32, _i32,
@@ -407,6 +408,14 @@ def cds_cd_gemm_time() -> tuple[float, int]:
     ms, n = _f64(0.0), ctypes.c_int64(0)
     _check(load().cds_cd_gemm_time(ctypes.byref(ms), ctypes.byref(n)), "cds_cd_gemm_time")
     return ms.value, n.value
+
+
+def cds_cd_live_pairs(nbf: int, workspace: torch.Tensor, precision: str = "ozaki") -> int:
+    """Pairs the last decomposition in ``workspace`` kept after screening."""
+    n = ctypes.c_int64(0)
+    _check(load().cds_cd_live_pairs(nbf, _p(workspace), PRECISIONS[precision], ctypes.byref(n),
+                                    _stream(workspace.device)), "cds_cd_live_pairs")
+    return n.value
 
 
 def cd_candidates(precision: str = "f32x2") -> int:
