@@ -558,9 +558,7 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
                                              long long* __restrict__ blk_b,
                                              long long* __restrict__ blk_i,
                                              int32_t* __restrict__ piv, CdCtrl* ctrl, int bid,
-                                             int nblk, PairF2 pf = PairF2{},
-                                             long long* __restrict__ blk_lo = nullptr,
-                                             double* __restrict__ blk_lov = nullptr) {
+                                             int nblk, PairF2 pf = PairF2{}) {
     static_assert(!SPEC || DF, "speculative projections are a float-pair mode");
     static_assert(!TC || SPEC, "the tensor-core form is a speculative form");
     const int64_t P = ctrl->P;
@@ -596,10 +594,6 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
     // pairs, with four rows of L in flight per pair (the rows are a batch's
     // worth of recent vectors, up to 63 of them)
     float2 accTC[kStepPer];
-    double dvTC[kStepPer];   // TC: this thread's new residuals and candidate flags
-    bool cvTC[kStepPer];
-#pragma unroll
-    for (int r = 0; r < kStepPer; ++r) { dvTC[r] = 0.0; cvTC[r] = false; }
     if constexpr (TC) {
         const float2* Lf = reinterpret_cast<const float2*>(L);
 #pragma unroll
@@ -673,7 +667,6 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
             }
             if (I == P) d = 0.0;
             D[I] = d;
-            if constexpr (TC) { dvTC[r] = d; cvTC[r] = cand[I] != 0; }
             const long long bits = __double_as_longlong(d);
             if (cand[I]) {
                 const long long key = bits > 0 ? bits : 0LL;
@@ -685,26 +678,6 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
     long long mine = mx;
     block_maxmin_ll(mx, mn);
     if constexpr (SPEC) mx_i = block_min_ll(mine == mx && mx >= 0 ? mx_i : LLONG_MAX);
-    if constexpr (TC) {
-        // the lowest index within the tie band of the block's own maximum
-        // (and above delta_eff), with its residual: when that entry also lies
-        // in the band of the global maximum it is the pivot of the block
-        const double bthr = (mx >= 0 ? __longlong_as_double(mx) : -1.0) - kTieRel * ctrl->scale;
-        const double de0 = ctrl->delta_eff;
-        long long lo = LLONG_MAX;
-        double lov = 0.0;
-#pragma unroll
-        for (int r = kStepPer - 1; r >= 0; --r) {   // I increases with r: keep the lowest
-            const int64_t I = base + r * kUpdThreads + threadIdx.x;
-            if (I < n && cvTC[r] && fmax(dvTC[r], 0.0) >= bthr && dvTC[r] > de0) {
-                lo = I;
-                lov = dvTC[r];
-            }
-        }
-        const long long blo = block_min_ll(lo);
-        if (blo != LLONG_MAX && lo == blo) { blk_lo[bid] = blo; blk_lov[bid] = lov; }
-        if (threadIdx.x == 0 && blo == LLONG_MAX) blk_lo[bid] = -1;
-    }
     if (threadIdx.x == 0) {
         blk_a[bid] = mx;
         blk_b[bid] = mn;
@@ -713,16 +686,9 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
     if (!last_block(&ctrl->counter, nblk)) return;
 
     long long A = -1, B = LLONG_MAX;
-    constexpr int kCacheA = 8;   // TC: this thread's block maxima, kept for the search
-    long long ca[kCacheA];
-    {
-        int j = 0;
-        for (int i = threadIdx.x; i < nblk; i += blockDim.x, ++j) {
-            const long long a = __ldcg(blk_a + i);
-            if (TC && j < kCacheA) ca[j] = a;
-            A = max(A, a);
-            B = min(B, __ldcg(blk_b + i));
-        }
+    for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
+        A = max(A, __ldcg(blk_a + i));
+        B = min(B, __ldcg(blk_b + i));
     }
     block_maxmin_ll(A, B);
     const double G = A < 0 ? -INFINITY : __longlong_as_double(A);
@@ -732,7 +698,6 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
     int32_t status = CDS_OK;
     bool stop = true;
     long long pick = -1;
-    double pickD = -1.0;   // TC: the pivot's residual when the fast path found it
     if (Dmin < -kNotPdRel * scale || !(G == G)) {
         status = CDS_ERR_NOT_PD;
     } else if (G <= de) {
@@ -744,26 +709,12 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
         int from = 0;
         for (;;) {
             long long bl = LLONG_MAX;
-            {
-                int j = 0;
-                for (int i = threadIdx.x; i < nblk; i += blockDim.x, ++j) {
-                    if (i < from) continue;
-                    const long long a = (TC && j < kCacheA) ? ca[j] : __ldcg(blk_a + i);
-                    const double m = __longlong_as_double(a);   // -1: NaN, fails
-                    if (m >= thr && m > de) { bl = i; break; }
-                }
+            for (int i = from + threadIdx.x; i < nblk; i += blockDim.x) {
+                const double m = __longlong_as_double(__ldcg(blk_a + i));   // -1: NaN, fails
+                if (m >= thr && m > de) { bl = i; break; }
             }
             bl = block_min_ll(bl);
             if (bl == LLONG_MAX) break;
-            if constexpr (TC) {   // the block's own lowest in-band entry, when it is in this band
-                const long long lo = __ldcg(blk_lo + bl);
-                const double lov = __ldcg(blk_lov + bl);
-                if (lo >= 0 && fmax(lov, 0.0) >= thr && lov > de) {
-                    pick = lo;
-                    pickD = lov;
-                    break;
-                }
-            }
             long long best = LLONG_MAX;
 #pragma unroll
             for (int r = 0; r < kStepPer; ++r) {
@@ -858,7 +809,7 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
             ctrl->M = made;
         } else {
             ctrl->P = pick;
-            ctrl->DP = (TC && pickD >= 0.0) ? pickD : __ldcg(D + pick);
+            ctrl->DP = __ldcg(D + pick);
             ctrl->rDP = 1.0 / sqrt(ctrl->DP);
             {
                 const float h = (float)ctrl->rDP;
@@ -972,8 +923,7 @@ k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
             const double* __restrict__ ecol, const float2* __restrict__ G,
             double* __restrict__ blk_a, double* __restrict__ blk_b,
             long long* __restrict__ blk_i, int32_t* __restrict__ piv, CdCtrl* ctrl,
-            PairF2 pf = PairF2{}, long long* __restrict__ blk_lo = nullptr,
-            double* __restrict__ blk_lov = nullptr) {
+            PairF2 pf = PairF2{}) {
     if constexpr (TC) {
         pdl_trigger();
         pdl_wait();
@@ -983,7 +933,7 @@ k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
     cd_step_body<DF, SPEC, TC>(n, k, max_rank, L, D, cand, ecol, G,
                            reinterpret_cast<long long*>(blk_a),
                            reinterpret_cast<long long*>(blk_b), blk_i, piv, ctrl, blockIdx.x,
-                           gridDim.x, pf, blk_lo, blk_lov);
+                           gridDim.x, pf);
 }
 
 // ---- screening of the tensor-core form (kScreenRel) ----
@@ -1129,8 +1079,6 @@ struct CdLayout {
     double* blk_a;
     double* blk_b;
     long long* blk_i;
-    long long* blk_lo;   // tensor-core form: each block's lowest in-band entry
-    double* blk_lov;     // and its residual
     CdCtrl* ctrl;
     size_t bytes;
 };
@@ -1197,8 +1145,6 @@ static CdLayout cd_layout(void* ws, int32_t nbf, bool spec = true, bool tc = fal
     l.blk_a = c.take<double>(nb);
     l.blk_b = c.take<double>(nb);
     l.blk_i = c.take<long long>(nb);
-    l.blk_lo = tc ? c.take<long long>(nb) : nullptr;
-    l.blk_lov = tc ? c.take<double>(nb) : nullptr;
     l.bytes = c.off;
     return l;
 }
@@ -1353,7 +1299,7 @@ static int cd_run_tc(int64_t n, int32_t max_rank, double* L, int32_t* piv, doubl
                                     stream, nc, k, max_rank, lay.Lc, lay.Dc,
                                     (const uint8_t*)lay.candc, (const double*)lay.ecol,
                                     (const float2*)lay.G, lay.blk_a, lay.blk_b, lay.blk_i,
-                                    lay.pivc, lay.ctrl, lay.pf, lay.blk_lo, lay.blk_lov));
+                                    lay.pivc, lay.ctrl, lay.pf));
         }
         return CDS_OK;
     };
