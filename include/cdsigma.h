@@ -651,11 +651,14 @@ int cds_graph_destroy(cds_graph* graph);
  *   CDS_TUNE_PIPE_SPLIT: in cds_cd_decompose_to_mo with a tensor-core
  *     transform, the transform's GEMMs take at most this many CTAs (one per
  *     SM) and the decomposition's projection GEMM the other SMs, so the two
- *     streams run side by side (0 = no split, default).
+ *     streams run side by side (0 = no split, default);
+ *   CDS_TUNE_GRID_EC: energies per pass of the kernels that evaluate the
+ *     Sigma grid from the kept numerators (the register tile: 64 numerators x
+ *     this many energies per thread), 2, 4 (default) or 8.
  * Graphs keep the configuration they were captured with.
  * ---------------------------------------------------------------------- */
 enum { CDS_TUNE_ENERGY_CHUNK = 0, CDS_TUNE_ITEM_ORDER = 1, CDS_TUNE_NEWTON_CACHE = 2,
-       CDS_TUNE_CD_GRAPH = 3, CDS_TUNE_PIPE_SPLIT = 4 };
+       CDS_TUNE_CD_GRAPH = 3, CDS_TUNE_PIPE_SPLIT = 4, CDS_TUNE_GRID_EC = 5 };
 int cds_tune_set(int32_t knob, int32_t value);   /* CDS_ERR_ARG on an invalid pair */
 int cds_tune_get(int32_t knob);                  /* -1 for an unknown knob */
 

@@ -1,13 +1,14 @@
 """Autotuner for the batched tensor-core self-energy.
 
-Times captured-graph replays of the actual batch for every combination of
-the library's kernel configuration -- energies per epilogue pass (8 / 16),
-work-item order (interleaved / blocked) and how the Newton passes evaluate
-Sigma (recomputing the integrals on the tensor cores, or streaming the
-numerators the grid pass kept) -- keeps the fastest, and caches the choice
-in a JSON file keyed by the batch's shape signature (molecule sizes, orbital
-and energy counts, Cholesky ranks, precision), so a repeated batch shape is
-tuned once.
+Times captured-graph replays of the actual batch for the library's kernel
+configurations -- energies per epilogue pass of the tensor-core kernel
+(8 / 16), work-item order (interleaved / blocked), the register tile of the
+kernel that evaluates the grid from the kept numerators (2 / 4 / 8 energies
+per pass) and how the Newton passes evaluate Sigma (streaming the kept
+numerators; one candidate recomputes the integrals on the tensor cores) --
+keeps the fastest, and caches the choice in a JSON file keyed by the batch's
+shape signature (molecule sizes, orbital and energy counts, Cholesky ranks,
+precision), so a repeated batch shape is tuned once.
 """
 from __future__ import annotations
 
@@ -20,8 +21,9 @@ import torch
 
 from . import cdsigma as C
 
-# (energy chunk, item order, Newton from kept numerators)
-CANDIDATES = [(c, o, k) for k in (1, 0) for c in (16, 8) for o in (0, 1)]
+# (energy chunk, item order, Newton from kept numerators, grid energies per pass)
+CANDIDATES = ([(c, o, 1, ec) for c in (16, 8) for o in (0, 1) for ec in (4, 8, 2)] +
+              [(16, 0, 0, 4)])
 
 
 def cache_path() -> str:
@@ -54,13 +56,14 @@ def apply(choice) -> None:
     C.cds_tune_set(C.TUNE_ENERGY_CHUNK, int(choice[0]))
     C.cds_tune_set(C.TUNE_ITEM_ORDER, int(choice[1]))
     C.cds_tune_set(C.TUNE_NEWTON_CACHE, int(choice[2]))
+    C.cds_tune_set(C.TUNE_GRID_EC, int(choice[3]) if len(choice) > 3 else 4)
 
 
 def tune(batch: "C.Batch", orb, eps, E, reps: int = 2, use_cache: bool = True) -> dict:
     """Pick and apply the fastest configuration for this batch.
 
-    Returns {"choice": (chunk, order, cache), "ms": {candidate: ms}, "cached": bool}."""
-    key = "v2:" + signature(batch)
+    Returns {"choice": (chunk, order, cache, grid_ec), "ms": {candidate: ms}, "cached": bool}."""
+    key = "v3:" + signature(batch)
     cache = _load() if use_cache else {}
     if key in cache:
         choice = tuple(cache[key]["choice"])

@@ -807,7 +807,8 @@ class BatchGraph:
             self.h = None
 
 
-TUNE_ENERGY_CHUNK, TUNE_ITEM_ORDER, TUNE_NEWTON_CACHE, TUNE_CD_GRAPH, TUNE_PIPE_SPLIT = 0, 1, 2, 3, 4
+TUNE_ENERGY_CHUNK, TUNE_ITEM_ORDER, TUNE_NEWTON_CACHE, TUNE_CD_GRAPH, TUNE_PIPE_SPLIT, TUNE_GRID_EC = (
+    0, 1, 2, 3, 4, 5)
 
 
 def cds_tune_set(knob: int, value: int) -> None:

@@ -739,6 +739,8 @@ static std::atomic<int> g_item_order{0};
 static std::atomic<int> g_newton_cache{1};
 static std::atomic<int> g_cd_graph{512};
 static std::atomic<int> g_pipe_split{0};
+static std::atomic<int> g_grid_ec{kGridEC};
+int tune_grid_ec() { return g_grid_ec.load(); }
 int tune_pipe_split() { return g_pipe_split.load(); }
 int tune_energy_chunk() { return g_energy_chunk.load(); }
 int tune_cd_graph() { return g_cd_graph.load(); }
@@ -961,8 +963,18 @@ int sigma2_tc(int32_t nmo, int32_t nocc, int32_t M, const double* Lov, const dou
         if (st) return st;
         if (split) {
             const int g2 = (int)std::min<int64_t>(nitems, (int64_t)device_sms() * 4);
-            k_sigma_cached_grid<kGridEC><<<g2, 256, 0, stream>>>(P, cache, lay.E2, lay.eps2, active,
-                                                                 lay.part, nE, kGridSplitE);
+            // energies per pass: the autotuner's choice (CDS_TUNE_GRID_EC)
+            const int ec = tune_grid_ec();
+            if (ec == 2)
+                k_sigma_cached_grid<2><<<g2, 256, 0, stream>>>(P, cache, lay.E2, lay.eps2, active,
+                                                               lay.part, nE, kGridSplitE);
+            else if (ec == 8)
+                k_sigma_cached_grid<8><<<g2, 256, 0, stream>>>(P, cache, lay.E2, lay.eps2, active,
+                                                               lay.part, nE, kGridSplitE);
+            else
+                k_sigma_cached_grid<kGridEC><<<g2, 256, 0, stream>>>(P, cache, lay.E2, lay.eps2,
+                                                                     active, lay.part, nE,
+                                                                     kGridSplitE);
             CDS_LAUNCH_CHECK();
         }
     } else {
@@ -1734,8 +1746,17 @@ int tc_batch_pass(int32_t nmol, const BatchMol* mols, int32_t pass, int64_t nE_t
         CDS_LAUNCH_CHECK();
         if (split) {
             const int g2 = (int)std::min<int64_t>(nitems, 4LL * device_sms());
-            k_sigma_cached_grid_batch<kGridEC><<<g2, 256, 0, stream>>>(set, nmol, nitems, lay.cache, Ep,
-                                                                       lay.eps2, lay.part, kGridSplitE);
+            const int ec = tune_grid_ec();
+            if (ec == 2)
+                k_sigma_cached_grid_batch<2><<<g2, 256, 0, stream>>>(set, nmol, nitems, lay.cache, Ep,
+                                                                     lay.eps2, lay.part, kGridSplitE);
+            else if (ec == 8)
+                k_sigma_cached_grid_batch<8><<<g2, 256, 0, stream>>>(set, nmol, nitems, lay.cache, Ep,
+                                                                     lay.eps2, lay.part, kGridSplitE);
+            else
+                k_sigma_cached_grid_batch<kGridEC><<<g2, 256, 0, stream>>>(set, nmol, nitems,
+                                                                           lay.cache, Ep, lay.eps2,
+                                                                           lay.part, kGridSplitE);
             CDS_LAUNCH_CHECK();
         }
     }
@@ -1777,6 +1798,11 @@ extern "C" int cds_tune_set(int32_t knob, int32_t value) {
         g_pipe_split = value;
         return CDS_OK;
     }
+    if (knob == CDS_TUNE_GRID_EC) {
+        if (value != 2 && value != 4 && value != 8) return CDS_ERR_ARG;
+        g_grid_ec = value;
+        return CDS_OK;
+    }
     return CDS_ERR_ARG;
 }
 
@@ -1787,5 +1813,6 @@ extern "C" int cds_tune_get(int32_t knob) {
     if (knob == CDS_TUNE_NEWTON_CACHE) return g_newton_cache.load();
     if (knob == CDS_TUNE_CD_GRAPH) return g_cd_graph.load();
     if (knob == CDS_TUNE_PIPE_SPLIT) return g_pipe_split.load();
+    if (knob == CDS_TUNE_GRID_EC) return g_grid_ec.load();
     return -1;
 }

@@ -68,6 +68,7 @@ namespace tc {
 int tune_newton_cache();   // CDS_TUNE_NEWTON_CACHE
 int tune_cd_graph();       // CDS_TUNE_CD_GRAPH
 int tune_pipe_split();     // CDS_TUNE_PIPE_SPLIT
+int tune_grid_ec();        // CDS_TUNE_GRID_EC
 }
 
 inline bool is_split16(int32_t precision) {

@@ -162,15 +162,16 @@ def test_autotuner_candidates_agree_and_cache(batch, tmp_path, monkeypatch):
         results[cand] = (b.sigma.clone(), b.omega.clone(), b.pole.clone(), b.status.clone())
         del g
     for cand, (s_, w_, p_, st_) in results.items():
-        # items are reduced per orbital in a fixed order, so the chunk and the
-        # order change only which CTA computes an item, not the arithmetic
-        ref = results[(16, 0, cand[2])]
+        # items are reduced per orbital in a fixed order, so the chunk, the
+        # order and the grid kernel's energies per pass change only which CTA
+        # or which pass computes a value, not the arithmetic
+        ref = results[(16, 0, cand[2], 4)]
         torch.testing.assert_close(s_, ref[0], rtol=1e-13, atol=1e-13)
         torch.testing.assert_close(w_, ref[1], rtol=1e-13, atol=1e-13)
     # Newton from the kept numerators against recomputed integrals: the same
     # per-element arithmetic, FP32 sums in another order -- the grid within
     # 1e-5 relative, quasiparticle roots (P >= 0.5, converged) within 1e-7 Ha
-    a, r = results[(16, 0, 1)], results[(16, 0, 0)]
+    a, r = results[(16, 0, 1, 4)], results[(16, 0, 0, 4)]
     torch.testing.assert_close(a[0], r[0], rtol=1e-5, atol=1e-8)
     qp = (a[3] == 0) & (r[3] == 0) & (r[2] >= 0.5)
     assert int(qp.sum()) >= 10
@@ -179,7 +180,7 @@ def test_autotuner_candidates_agree_and_cache(batch, tmp_path, monkeypatch):
     assert first["cached"] is False and tuple(first["choice"]) in autotune.CANDIDATES
     again = autotune.tune(b, inp["orb"], inp["eps"], inp["E"])
     assert again["cached"] is True and tuple(again["choice"]) == tuple(first["choice"])
-    autotune.apply((16, 0, 1))
+    autotune.apply((16, 0, 1, 4))
 
 
 def test_batch_exact_slice_transform(batch):
