@@ -915,9 +915,11 @@ k_cd_project_tc(int64_t n, const double* __restrict__ L, const float* __restrict
 }
 
 // Step k, part 2: vector k, residuals, next pivot.  Five blocks per SM keep
-// the C60-shaped grid (690 blocks of 512 pairs) in one wave.
+// the C60-shaped grid (690 blocks of 512 pairs) in one wave; the tensor-core
+// form runs on the screened pairs (425 blocks at C60), where four blocks per
+// SM do, and takes the registers (64) that its column and projection need.
 template <bool DF, bool SPEC, bool TC = false>
-__global__ void __launch_bounds__(kUpdThreads, 5)
+__global__ void __launch_bounds__(kUpdThreads, TC ? 4 : 5)
 k_cd_update(int64_t n, int32_t k, int32_t max_rank, double* __restrict__ L,
             double* __restrict__ D, const uint8_t* __restrict__ cand,
             const double* __restrict__ ecol, const float2* __restrict__ G,
