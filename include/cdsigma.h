@@ -346,7 +346,11 @@ int cds_ri_factors(int32_t nbf, const double* xyz, const double* alpha, const in
  *        final rank M, into caller buffers of room for max_rank in place of M;
  *   the workspace (cds_cd_decompose_to_mo_workspace_bytes) holds both calls'
  *        workspaces and max_rank-strided staging copies of Lov and Lp.
- * Blocking, like cds_cd_decompose.
+ * Blocking, like cds_cd_decompose.  The two library streams belong to the
+ * device, so calls from several host threads share them (their work
+ * interleaves in stream order).  On the library stream the tensor-core
+ * decomposition replays its 32-step chunks as a CUDA graph (CDS_TUNE_CD_GRAPH);
+ * CDS_TUNE_PIPE_SPLIT divides the SMs between the two streams.
  * ---------------------------------------------------------------------- */
 size_t cds_cd_decompose_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc,
                                               int32_t max_rank, int32_t np, int32_t cd_precision);
