@@ -8,6 +8,8 @@ holds a few GB of device memory at most and replays in seconds:
   python -m paper_0912_1459_gb300.profcases transform_oz  # k_oz_gemm, k_oz_slice (exact slices)
   python -m paper_0912_1459_gb300.profcases sigma1      # k_sigma_tc, nE = 1
   python -m paper_0912_1459_gb300.profcases sigma64     # k_sigma_tc, nE = 64
+  python -m paper_0912_1459_gb300.profcases grid        # k_sigma_tc (nE = 1, keeps the
+                                                        # numerators), k_sigma_cached_grid (63)
   python -m paper_0912_1459_gb300.profcases cd          # k_cd_update, FP64 (C60, 1024 steps max)
   python -m paper_0912_1459_gb300.profcases cdf         # k_cd_update, float pairs
   python -m paper_0912_1459_gb300.profcases cdoz        # k_cd_gemm_tc, k_cd_project_tc,
@@ -53,6 +55,13 @@ def main(mode: str) -> None:
             b.record()
             torch.cuda.synchronize()
             print(f"transform of {L.shape[0]} vectors: {a.elapsed_time(b):.2f} ms")
+    elif mode == "grid":
+        Lov = torch.randn((m.nocc, m.nbf - m.nocc, 896), dtype=torch.float64, device=dev,
+                          generator=g) * 1e-2
+        Lp = torch.randn((2, m.nbf, 896), dtype=torch.float64, device=dev, generator=g) * 1e-2
+        E = d(W.energy_grid(m.eps[m.orbitals[9:11]], 64))
+        for _ in range(2):
+            G.cds_sigma2_diag_cache(Lov, Lp, d(m.eps), m.nocc, E, "bf16x3")
     elif mode in ("sigma1", "sigma64"):
         nE = 64 if mode == "sigma64" else 1
         Lov = torch.randn((m.nocc, m.nbf - m.nocc, 896), dtype=torch.float64, device=dev,
