@@ -1061,8 +1061,11 @@ k_sigma_cached(Params P, const float* __restrict__ cache, const float2* __restri
 // orbital from its cached numerators ct (the grid's energies past the ones
 // the tensor-core epilogue evaluates).  Thread = (row, column half) as in
 // k_sigma_cached, its 64 numerators held in registers across the energies;
-// EC energies per pass, each summed over the block in a fixed order into
-// out[e][2] (the partial row of the item, the layout of k_sigma_tc).
+// EC energies per pass, each summed over its warp; the warps' sums wait in
+// shared memory for up to kRedE energies and are then added over the block
+// in a fixed order into out[e][2] (the partial row of the item, the layout
+// of k_sigma_tc), so the block meets at a barrier once per kRedE energies
+// instead of twice per pass.
 // Et: the orbital's energies; ev: the molecule's orbital energies.
 template <int EC>
 __device__ __forceinline__ void cached_grid_item(const TermR& tm, int t, int s, int A, int B,
@@ -1070,7 +1073,9 @@ __device__ __forceinline__ void cached_grid_item(const TermR& tm, int t, int s, 
                                                  const float2* __restrict__ Et,
                                                  const float2* __restrict__ ev, int32_t nE,
                                                  int32_t e_begin, double* __restrict__ out) {
-    __shared__ float red[8][EC][2];
+    constexpr int kRedE = 64;   // a multiple of every EC
+    static_assert(kRedE % EC == 0, "energy chunk");
+    __shared__ float red[8][kRedE][2];
     __shared__ float2 sey[2][64];
     (void)t;
     const int row = threadIdx.x & (TB - 1), half = threadIdx.x / TB;
@@ -1093,6 +1098,7 @@ __device__ __forceinline__ void cached_grid_item(const TermR& tm, int t, int s, 
         const float2 ex = ev[tm.eps_x_off + x];
         rb = df_add(es, make_float2(-ex.x, -ex.y));
     }
+    int fbase = e_begin;   // first energy of the chunk in red
     for (int e0 = e_begin; e0 < nE; e0 += EC) {
         float ch[EC], cl[EC], as[EC], ad[EC];
 #pragma unroll
@@ -1127,19 +1133,24 @@ __device__ __forceinline__ void cached_grid_item(const TermR& tm, int t, int s, 
         }
         if (lane == 0) {
 #pragma unroll
-            for (int e = 0; e < EC; ++e) { red[w][e][0] = as[e]; red[w][e][1] = ad[e]; }
-        }
-        __syncthreads();
-        if (threadIdx.x < 2 * EC) {
-            const int e = threadIdx.x >> 1, k = threadIdx.x & 1;
-            if (e0 + e < nE) {
-                double v = 0.0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) v += (double)red[i][e][k];
-                out[(int64_t)(e0 + e) * 2 + k] = v;
+            for (int e = 0; e < EC; ++e) {
+                red[w][e0 - fbase + e][0] = as[e];
+                red[w][e0 - fbase + e][1] = ad[e];
             }
         }
-        __syncthreads();
+        if (e0 + EC - fbase >= kRedE || e0 + EC >= nE) {   // the chunk is full or done
+            __syncthreads();
+            const int cnt = min(nE, e0 + EC) - fbase;
+            for (int i = threadIdx.x; i < 2 * cnt; i += blockDim.x) {
+                const int e = i >> 1, k = i & 1;
+                double v = 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v += (double)red[j][e][k];
+                out[(int64_t)(fbase + e) * 2 + k] = v;
+            }
+            __syncthreads();
+            fbase = e0 + EC;
+        }
     }
 }
 

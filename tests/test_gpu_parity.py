@@ -126,6 +126,32 @@ def test_cd_tensor_core_parity(name, delta, scheme):
     np.testing.assert_allclose(D, ref.D, rtol=0, atol=tol)
 
 
+def test_cd_tensor_core_screening():
+    """Screening of the tensor-core form: the pairs kept are exactly those
+    with D0_I >= 1e-40 max D0 (oracle diagonal); the others return L = 0 and
+    their initial diagonal, and every kept pair matches the oracle."""
+    m = O.molecule("c1")
+    ref = O.decomposition("c1", 1e-5, "full")
+    pd = eri.PairData(m.basis.xyz, m.basis.alpha)
+    D0 = eri.eri_diagonal(pd)
+    live = D0 >= 1e-40 * D0.max()
+    assert 0 < live.sum() < pd.npair          # the ring has negligible pairs
+    xyz, a, at = dev(m.basis.xyz), dev(m.basis.alpha), dev(m.basis.atom.astype(np.int32))
+    lib = G.load()
+    ws = torch.empty(lib.cds_cd_workspace_bytes_prec(m.nbf, 1024, 6), dtype=torch.uint8,
+                     device=DEV)
+    L, piv, D, de = G.cds_cd_decompose(xyz, a, at, 1e-5, "full", max_rank=1024, workspace=ws,
+                                       precision="ozaki")
+    torch.cuda.synchronize()
+    assert G.cdsigma.cds_cd_live_pairs(m.nbf, ws, "ozaki") == int(live.sum())
+    L, D = L.cpu().numpy(), D.cpu().numpy()
+    assert np.array_equal(piv.cpu().numpy().astype(np.int64), ref.piv)
+    assert not L[:, ~live].any()
+    np.testing.assert_allclose(D[~live], D0[~live], rtol=1e-12, atol=1e-30 * D0.max())
+    np.testing.assert_allclose(L[:, live], ref.L[:, live], rtol=0, atol=1e-9)
+    assert np.abs(ref.L[:, ~live]).max() <= 1e-19     # what screening leaves out
+
+
 def test_cd_tensor_core_chunk_graph():
     """On a stream of its own (not a default stream) and with max_rank >= 512
     the tensor-core decomposition replays each 32-step chunk as one CUDA
