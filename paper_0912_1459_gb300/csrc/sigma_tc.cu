@@ -1004,10 +1004,27 @@ __global__ void __launch_bounds__(256)
 k_sigma_cached(Params P, const float* __restrict__ cache, const float2* __restrict__ E2,
                const float2* __restrict__ eps2, const int32_t* __restrict__ active,
                double* __restrict__ part) {
-    __shared__ float red[8][2];
+    // the warps' sums of up to kItems items wait in shared memory and are
+    // added over the block (fixed order) at one barrier pair per kItems items
+    constexpr int kItems = 16;
+    __shared__ float red[kItems][8][2];
+    __shared__ int64_t slot_pidx[kItems];
+    int nslot = 0;
     const int64_t nitems = P.term[0].nitems + P.term[1].nitems;
     const int row = threadIdx.x & (TB - 1), half = threadIdx.x / TB;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    auto flush = [&]() {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * nslot; i += blockDim.x) {
+            const int sl = i >> 1, k = i & 1;
+            double v = 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v += (double)red[sl][j][k];
+            part[slot_pidx[sl] * 2 + k] = v;
+        }
+        __syncthreads();
+        nslot = 0;
+    };
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         int term, t, s, A, B;
         const TermR tm = decode(P.term[0], P.term[1], item, term, t, s, A, B);
@@ -1044,17 +1061,11 @@ k_sigma_cached(Params P, const float* __restrict__ cache, const float2* __restri
             as += __shfl_xor_sync(0xffffffffu, as, o);
             ad += __shfl_xor_sync(0xffffffffu, ad, o);
         }
-        if (lane == 0) { red[w][0] = as; red[w][1] = ad; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double sv = 0.0, dv = 0.0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { sv += (double)red[i][0]; dv += (double)red[i][1]; }
-            part[pidx * 2] = sv;
-            part[pidx * 2 + 1] = dv;
-        }
-        __syncthreads();
+        if (lane == 0) { red[nslot][w][0] = as; red[nslot][w][1] = ad; }
+        if (threadIdx.x == 0) slot_pidx[nslot] = pidx;
+        if (++nslot == kItems) flush();
     }
+    if (nslot > 0) flush();
 }
 
 // Sigma and dSigma/dE of one work item at energies [e_begin, nE) of its
@@ -1088,7 +1099,7 @@ __device__ __forceinline__ void cached_grid_item(const TermR& tm, int t, int s, 
     const float* ct = ct_item + (int64_t)half * 64 * TB + row;
 #pragma unroll
     for (int j = 0; j < 64; ++j) num[j] = (xok && j < ncols) ? ct[(int64_t)j * TB] : 0.f;
-    __syncthreads();   // the previous item's reads of sey are done
+    // the previous item's reads of sey ended before its last flush's barriers
     if (row < 64)      // padding columns: a far-off energy, so 0 * tiny
         sey[half][row] = row < ncols ? ev[tm.eps_x_off + ybase + row] : make_float2(-1e30f, 0.f);
     __syncthreads();
@@ -1649,9 +1660,25 @@ k_sigma_cached_batch(const MolDesc* __restrict__ mols, int32_t nmol, int64_t nit
                      const float* __restrict__ cache, const float2* __restrict__ w2,
                      const float2* __restrict__ eps2, const int32_t* __restrict__ active,
                      double* __restrict__ part) {
-    __shared__ float red[8][2];
+    // as k_sigma_cached: warp sums of up to kItems items, one barrier pair
+    constexpr int kItems = 16;
+    __shared__ float red[kItems][8][2];
+    __shared__ double* slot_out[kItems];
+    int nslot = 0;
     const int row = threadIdx.x & (TB - 1), half = threadIdx.x / TB;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    auto flush = [&]() {
+        __syncthreads();
+        for (int i = threadIdx.x; i < 2 * nslot; i += blockDim.x) {
+            const int sl = i >> 1, k = i & 1;
+            double v = 0.0;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v += (double)red[sl][j][k];
+            slot_out[sl][k] = v;
+        }
+        __syncthreads();
+        nslot = 0;
+    };
     for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
         int lo = 0, hi = nmol - 1;
         while (lo < hi) {
@@ -1696,18 +1723,11 @@ k_sigma_cached_batch(const MolDesc* __restrict__ mols, int32_t nmol, int64_t nit
             as += __shfl_xor_sync(0xffffffffu, as, o);
             ad += __shfl_xor_sync(0xffffffffu, ad, o);
         }
-        if (lane == 0) { red[w][0] = as; red[w][1] = ad; }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double sv = 0.0, dv = 0.0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) { sv += (double)red[i][0]; dv += (double)red[i][1]; }
-            double* out = part + md->part_base + r * (int64_t)md->nE * 2;
-            out[0] = sv;
-            out[1] = dv;
-        }
-        __syncthreads();
+        if (lane == 0) { red[nslot][w][0] = as; red[nslot][w][1] = ad; }
+        if (threadIdx.x == 0) slot_out[nslot] = part + md->part_base + r * (int64_t)md->nE * 2;
+        if (++nslot == kItems) flush();
     }
+    if (nslot > 0) flush();
 }
 }  // namespace tc
 
