@@ -33,6 +33,11 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
                        const double* xyz, const double* alpha, const int32_t* atom, double delta,
                        int32_t scheme, int32_t precision, double* L, int32_t* piv, double* D,
                        int32_t* M_out, void* ws, size_t ws_bytes, cudaStream_t stream);
+size_t cd_tc_batch_workspace_bytes(int32_t nmol, const BatchMol* mols);
+int cd_batch_decompose_tc(int32_t nmol, const BatchMol* mols, const BatchOffsets* off,
+                          const double* xyz, const double* alpha, const int32_t* atom,
+                          double delta, int32_t scheme, double* L, int32_t* piv, double* D,
+                          int32_t* M_out, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 namespace {
 
@@ -152,16 +157,12 @@ int run_workers(int32_t nmol, const cds_mol* mols, cudaStream_t stream, Job job)
     return res;
 }
 
-// Bytes of one worker's slot: the largest molecule's tensor-core
-// decomposition workspace (when precision is OZAKI) or transform workspace.
-size_t worker_slot_bytes(int32_t nmol, const cds_mol* mols, int32_t precision) {
+// Bytes of one worker's slot: the largest molecule's transform workspace.
+size_t worker_slot_bytes(int32_t nmol, const cds_mol* mols) {
     size_t b = 0;
-    for (int c = 0; c < nmol; ++c) {
+    for (int c = 0; c < nmol; ++c)
         b = std::max(b, cds_cd_to_mo_workspace_bytes(mols[c].nbf, mols[c].nbf, mols[c].nocc,
                                                      mols[c].max_rank, mols[c].np));
-        if (precision == CDS_PREC_OZAKI)
-            b = std::max(b, cd_workspace_bytes_prec(mols[c].nbf, mols[c].max_rank, CDS_PREC_OZAKI));
-    }
     return align_up(b);
 }
 
@@ -369,17 +370,23 @@ static size_t base_bytes(int32_t nmol, const cds_mol* mols) {
            align_up(qp_batch_layout(nullptr, nmol, bm.data(), tot.orb).bytes);
 }
 
-extern "C" size_t cds_batch_workspace_bytes(int32_t nmol, const cds_mol* mols, int32_t precision) {
-    if (!mols_ok(nmol, mols)) return 0;
-    return base_bytes(nmol, mols) + kWorkers * worker_slot_bytes(nmol, mols, precision);
+// The tensor-core decomposition's region (CDS_PREC_OZAKI) follows the slots.
+static size_t tc_cd_bytes(int32_t nmol, const cds_mol* mols, int32_t precision) {
+    if (precision != CDS_PREC_OZAKI) return 0;
+    std::vector<BatchMol> bm = to_internal(nmol, mols);
+    return cd_tc_batch_workspace_bytes(nmol, bm.data());
 }
 
-// The worker slots of a workspace of `bytes` bytes for `precision`, or null
-// when it has none that large.
-static char* worker_part(void* ws, size_t bytes, int32_t nmol, const cds_mol* mols,
-                         int32_t precision) {
+extern "C" size_t cds_batch_workspace_bytes(int32_t nmol, const cds_mol* mols, int32_t precision) {
+    if (!mols_ok(nmol, mols)) return 0;
+    return base_bytes(nmol, mols) + kWorkers * worker_slot_bytes(nmol, mols) +
+           tc_cd_bytes(nmol, mols, precision);
+}
+
+// The worker slots of a workspace of `bytes` bytes, or null when it has none.
+static char* worker_part(void* ws, size_t bytes, int32_t nmol, const cds_mol* mols) {
     const size_t base = base_bytes(nmol, mols);
-    if (bytes < base + kWorkers * worker_slot_bytes(nmol, mols, precision)) return nullptr;
+    if (bytes < base + kWorkers * worker_slot_bytes(nmol, mols)) return nullptr;
     return static_cast<char*>(ws) + base;
 }
 
@@ -403,23 +410,14 @@ extern "C" int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const d
     if (!(delta >= 0.0) || (scheme != CDS_SCHEME_FULL && scheme != CDS_SCHEME_ATOMIC))
         return CDS_ERR_ARG;
     if (precision == CDS_PREC_OZAKI) {
-        char* slots = worker_part(workspace, workspace_bytes, nmol, mols, CDS_PREC_OZAKI);
-        if (!slots) return CDS_ERR_WORKSPACE;
-        const size_t slot = worker_slot_bytes(nmol, mols, CDS_PREC_OZAKI);
+        const size_t before = base_bytes(nmol, mols) + kWorkers * worker_slot_bytes(nmol, mols);
+        const size_t need = tc_cd_bytes(nmol, mols, precision);
+        if (!workspace || workspace_bytes < before + need) return CDS_ERR_WORKSPACE;
+        std::vector<BatchMol> bm = to_internal(nmol, mols);
         std::vector<BatchOffsets> off = offsets_of(nmol, mols, nullptr);
-        return run_workers(nmol, mols, stream, [&](int c, cudaStream_t s, int t) {
-            const cds_mol& m = mols[c];
-            int32_t Mc = 0;
-            const int st = cd_decompose_run(m.nbf, xyz + 3 * off[c].basis, alpha + off[c].basis,
-                                            atom + off[c].basis, delta, scheme, m.max_rank,
-                                            CDS_PREC_OZAKI, L + off[c].L, piv + off[c].piv,
-                                            D + off[c].pair, &Mc, nullptr,
-                                            slots + (size_t)t * slot, slot, s, nullptr, nullptr,
-                                            false);   // chunk graphs: 570 against 370 ms
-                                                      // (64 clusters, 8 threads)
-            M_out[c] = Mc;
-            return st;
-        });
+        return cd_batch_decompose_tc(nmol, bm.data(), off.data(), xyz, alpha, atom, delta, scheme,
+                                     L, piv, D, M_out, static_cast<char*>(workspace) + before,
+                                     need, stream);
     }
     if (workspace_bytes < base_bytes(nmol, mols)) return CDS_ERR_WORKSPACE;
     std::vector<BatchMol> bm = to_internal(nmol, mols);
@@ -438,8 +436,8 @@ extern "C" int cds_batch_cd_to_mo(int32_t nmol, const cds_mol* mols, const int32
     std::vector<BatchOffsets> off = offsets_of(nmol, mols, nullptr);
     for (int c = 0; c < nmol; ++c)
         if (M[c] < 0 || M[c] > mols[c].max_rank) return CDS_ERR_ARG;
-    if (char* slots = worker_part(workspace, workspace_bytes, nmol, mols, 0)) {
-        const size_t slot = worker_slot_bytes(nmol, mols, 0);
+    if (char* slots = worker_part(workspace, workspace_bytes, nmol, mols)) {
+        const size_t slot = worker_slot_bytes(nmol, mols);
         return run_workers(nmol, mols, stream, [&](int c, cudaStream_t s, int t) {
             const cds_mol& m = mols[c];
             return cds_cd_to_mo(m.nbf, m.nbf, m.nocc, M[c], L + off[c].L, C + off[c].C,

@@ -752,29 +752,43 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
             }
             __syncthreads();
             if (s_hit < 0 && TC) {
-                __shared__ long long s_key[TC ? kMaxBlocksTC : 1], s_idx[TC ? kMaxBlocksTC : 1];
+                // the blocks by (maximum descending, block index ascending), a
+                // bitonic sort in shared memory; the first NS - 1 eligible ones
+                // are the candidates after the pivot
+                __shared__ long long s_key[TC ? kMaxBlocksTC : 1];
+                __shared__ int32_t s_blk[TC ? kMaxBlocksTC : 1];
                 const long long de_key = __double_as_longlong(de);
-                for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
-                    const long long key = __ldcg(blk_a + i), idx = __ldcg(blk_i + i);
-                    s_key[i] = (idx >= 0 && idx != pick && key > de_key) ? key : -1;
-                    s_idx[i] = idx;
+                int P = 1;
+                while (P < nblk) P <<= 1;
+                for (int i = threadIdx.x; i < P; i += blockDim.x) {
+                    long long key = LLONG_MIN;
+                    if (i < nblk) {
+                        const long long a = __ldcg(blk_a + i), idx = __ldcg(blk_i + i);
+                        key = (idx >= 0 && idx != pick && a > de_key) ? a : -1;
+                    }
+                    s_key[i] = key;
+                    s_blk[i] = i;
                 }
                 __syncthreads();
-                for (int c = 1; c < NS; ++c) {
-                    long long best = -1, dummy = LLONG_MAX;
-                    for (int i = threadIdx.x; i < nblk; i += blockDim.x) best = max(best, s_key[i]);
-                    block_maxmin_ll(best, dummy);
-                    long long first = LLONG_MAX;
-                    if (best >= 0)
-                        for (int i = threadIdx.x; i < nblk; i += blockDim.x)
-                            if (s_key[i] == best) first = min(first, (long long)i);
-                    first = block_min_ll(first);
-                    if (threadIdx.x == 0) {
-                        s_spec[c] = first == LLONG_MAX ? -1 : s_idx[first];
-                        if (first != LLONG_MAX) s_key[first] = -1;
+                for (int size = 2; size <= P; size <<= 1)
+                    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                        for (int t = threadIdx.x; t < P / 2; t += blockDim.x) {
+                            const int lo = 2 * stride * (t / stride) + t % stride, hi = lo + stride;
+                            const long long ka = s_key[lo], kb = s_key[hi];
+                            const int ia = s_blk[lo], ib = s_blk[hi];
+                            const bool hi_first = kb > ka || (kb == ka && ib < ia);
+                            if (hi_first == ((lo & size) == 0)) {   // out of order for this run
+                                s_key[lo] = kb; s_key[hi] = ka;
+                                s_blk[lo] = ib; s_blk[hi] = ia;
+                            }
+                        }
+                        __syncthreads();
                     }
-                    __syncthreads();
-                }
+                if (threadIdx.x > 0 && threadIdx.x < NS)
+                    s_spec[threadIdx.x] = (threadIdx.x - 1 < P && s_key[threadIdx.x - 1] >= 0)
+                                              ? __ldcg(blk_i + s_blk[threadIdx.x - 1])
+                                              : -1;
+                __syncthreads();
             } else if (s_hit < 0) {
                 const long long de_key = __double_as_longlong(de);
                 for (int c = 1; c < kSpec; ++c) {
@@ -823,8 +837,8 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
                     ctrl->extra += made - ctrl->k0;
                 } else {
                     if constexpr (TC) {
-                        // the store's complete column groups after the last pass
-                        ctrl->kdone = (ctrl->k0 / kGroupTC) * kGroupTC;
+                        // the store holds the rows before the last pass's step
+                        ctrl->kdone = ctrl->k0;
                         for (int c = 0; c < kSpecTC; ++c) ctrl->STc[c] = s_spec[c];
                     } else {
                         for (int c = 0; c < kSpec; ++c) ctrl->S[c] = s_spec[c];
@@ -868,50 +882,89 @@ k_cd_project_spec(PairSoA pd, PairF2 pf, int64_t n, int32_t k, const double* __r
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) cd_spec_dot_body(n, k, L, G, ctrl, t);
 }
 
+// Item `it` of the slicing that precedes a pass at step k.  Items
+// [0, itemsA) bring the slice store up to date: the 8-column segments
+// [s0, s0 + nseg) of every pair, the segment fastest (rows below k sliced,
+// the rest zero); the rest slice the candidates' rows [0, k) into the B
+// planes.
+__device__ __forceinline__ void tc_slice_item(int64_t it, int64_t itemsA, int64_t n,
+                                              const float2* __restrict__ Lf,
+                                              const float* __restrict__ sigA,
+                                              __nv_bfloat16* __restrict__ A,
+                                              __nv_bfloat16* __restrict__ B,
+                                              float* __restrict__ sigB, const CdCtrl* ctrl,
+                                              int32_t k, int32_t s0, int32_t nseg) {
+    if (it < itemsA) {
+        const int64_t I = it / nseg;
+        const int32_t K0 = (s0 + (int32_t)(it - I * nseg)) * 8;
+        if (K0 >= k) {   // zero columns above the last vector
+            const int64_t plane = n * kGroupTC;
+            const int64_t off = ((int64_t)(K0 / kGroupTC) * kSlicesTC * n + I) * kGroupTC +
+                                K0 % kGroupTC;
+#pragma unroll
+            for (int q = 0; q < kSlicesTC; ++q)
+                *reinterpret_cast<uint4*>(A + q * plane + off) = make_uint4(0, 0, 0, 0);
+            return;
+        }
+        int e = 0;
+        frexpf(sigA[I], &e);   // sigma = 2^(e-1)
+        tc_store8(Lf, n, I, K0, k, e - 1, A, n, I);
+    } else {
+        const int64_t r = it - itemsA;
+        const int c = (int)(r % kSpecTC);
+        const int32_t K0 = (int32_t)(r / kSpecTC) * 8;
+        const long long Sc = ctrl->STc[c];
+        const float sg = Sc >= 0 ? sigA[Sc] : 1.f;
+        int e = 0;
+        frexpf(sg, &e);
+        tc_store8(Lf, n, Sc >= 0 ? Sc : -1, K0, k, e - 1, B, kSpecTC, c);
+        if (K0 == 0) sigB[c] = sg;
+    }
+}
+
+// The slicing of step k (no items unless the step starts a pass after the
+// first step).  Segments below the previous pass's step kd hold final rows;
+// those from its segment on are sliced again up to k, and the segments
+// above k up to the group boundary must read zero: the previous pass zeroed
+// its own group's, so only a new group's are written.
+__device__ __forceinline__ void tc_slice_counts(const CdCtrl* ctrl, int64_t n, int32_t& k,
+                                                int32_t& s0, int32_t& nseg, int64_t& itemsA,
+                                                int64_t& itemsB) {
+    itemsA = itemsB = 0;
+    k = s0 = nseg = 0;
+    if (ctrl->done || ctrl->pass == 0) return;
+    k = ctrl->kstep;   // the step number lives on the device (graph replays)
+    if (k == 0) return;
+    const int32_t kd = ctrl->kdone;
+    const int32_t kend = (k + kGroupTC - 1) / kGroupTC * kGroupTC;
+    const int32_t kend_prev = (kd + kGroupTC - 1) / kGroupTC * kGroupTC;
+    const int32_t s1 = (kend > kend_prev ? kend : (k + 7) / 8 * 8) / 8;
+    s0 = kd / 8;
+    nseg = s1 - s0;
+    itemsA = (int64_t)nseg * n;
+    itemsB = (int64_t)kSpecTC * (kend / 8);
+}
+
 // Step k, part 1 of the exact-slice tensor-core form (the integral column is
 // formed in the update): when step k starts a pass, the blocks bring the
-// slice store up to date (column groups [kdone, k rounded up), zero at
-// K >= k) and slice the candidates' rows [0, k) into the B planes, for the
-// projection GEMM that follows; otherwise the kernel returns at once.
+// slice store up to date (the rows made since the previous pass, zero above
+// k to the group boundary) and slice the candidates' rows [0, k) into the B
+// planes, for the projection GEMM that follows; otherwise the kernel returns
+// at once.
 __global__ void __launch_bounds__(kUpdThreads, 4)
 k_cd_project_tc(int64_t n, const double* __restrict__ L, const float* __restrict__ sigA,
                 __nv_bfloat16* __restrict__ A, __nv_bfloat16* __restrict__ B,
                 float* __restrict__ sigB, const CdCtrl* ctrl) {
     pdl_trigger();
     pdl_wait();
-    if (ctrl->done || ctrl->pass == 0) return;
-    const int32_t k = ctrl->kstep;   // the step number lives on the device (graph replays)
-    if (k == 0) return;
+    int32_t k, s0, nseg;
+    int64_t itemsA, itemsB;
+    tc_slice_counts(ctrl, n, k, s0, nseg, itemsA, itemsB);
     const float2* Lf = reinterpret_cast<const float2*>(L);
-    const int32_t kd = ctrl->kdone;
-    const int32_t kend = (k + kGroupTC - 1) / kGroupTC * kGroupTC;
-    const int q8 = kGroupTC / 8;   // 16-byte segments per group and plane
-    // A: items (group, pair, segment), segment fastest, so a warp writes whole rows
-    const int64_t itemsA = (int64_t)((kend - kd) / kGroupTC) * n * q8;
-    const int64_t itemsB = (int64_t)kSpecTC * (kend / 8);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < itemsA + itemsB;
-         it += stride) {
-        if (it < itemsA) {
-            const int seg = (int)(it % q8);
-            const int64_t r = it / q8;
-            const int64_t I = r % n;
-            const int32_t K0 = kd + (int32_t)(r / n) * kGroupTC + seg * 8;
-            int e = 0;
-            frexpf(sigA[I], &e);   // sigma = 2^(e-1)
-            tc_store8(Lf, n, I, K0, k, e - 1, A, n, I);
-        } else {
-            const int64_t r = it - itemsA;
-            const int c = (int)(r % kSpecTC);
-            const int32_t K0 = (int32_t)(r / kSpecTC) * 8;
-            const long long Sc = ctrl->STc[c];
-            const float sg = Sc >= 0 ? sigA[Sc] : 1.f;
-            int e = 0;
-            frexpf(sg, &e);
-            tc_store8(Lf, n, Sc >= 0 ? Sc : -1, K0, k, e - 1, B, kSpecTC, c);
-            if (K0 == 0) sigB[c] = sg;
-        }
-    }
+         it += stride)
+        tc_slice_item(it, itemsA, n, Lf, sigA, A, B, sigB, ctrl, k, s0, nseg);
 }
 
 // Step k, part 2: vector k, residuals, next pivot.  Five blocks per SM keep
@@ -1794,6 +1847,388 @@ int cd_batch_decompose(int32_t nmol, const BatchMol* mols, const BatchOffsets* o
         }
     }
     return status;
+}
+
+// ---------------------------------------------------------------------------
+// Batched tensor-core form: every molecule's screening, then the steps of all
+// molecules together, three launches per step for the whole batch (slicing,
+// projection GEMM, update), each molecule with its own control block, live
+// pairs, slice store and stop test.  A molecule's compact vectors ([max_rank]
+// rows of its live pairs, float pairs) live at the start of its own rows of
+// L and are spread into the full rows at the end.
+// ---------------------------------------------------------------------------
+struct CdMolTC {
+    PairF2 pf;            // live pairs' data as float pairs
+    double* L;            // compact vectors [max_rank][n] (float pairs)
+    double* D;            // compact residual diagonal
+    uint8_t* cand;
+    int32_t* piv;         // compact pivots
+    float* sigA;
+    __nv_bfloat16* A;
+    __nv_bfloat16* B;
+    float* sigB;
+    float2* G;
+    double* blk_a;
+    double* blk_b;
+    long long* blk_i;
+    CdCtrl* ctrl;
+    int64_t n;            // live pairs
+    int32_t max_rank;
+    int32_t b0_epi, nb_epi;
+    int32_t _pad;
+};
+static_assert(sizeof(CdMolTC) % 8 == 0 && sizeof(CdMolTC) / 8 <= kUpdThreads, "table entry copy");
+
+// Slicing before the passes of the molecules that start one at this step:
+// their items numbered molecule by molecule, spread over the grid.
+__global__ void __launch_bounds__(kUpdThreads, 4)
+k_bcd_project_tc(const CdMolTC* __restrict__ mols, int nmol) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ long long s_pre[kMaxMolsTC + 1];
+    for (int c = threadIdx.x; c < nmol; c += blockDim.x) {
+        int32_t k, s0, nseg;
+        int64_t a, b;
+        tc_slice_counts(mols[c].ctrl, mols[c].n, k, s0, nseg, a, b);
+        s_pre[c + 1] = a + b;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) warp_prefix_smem(s_pre, nmol);
+    __syncthreads();
+    const long long total = s_pre[nmol];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int c = -1;
+    long long lo = 0, hi = 0;
+    int32_t k = 0, s0 = 0, nseg = 0;
+    int64_t itemsA = 0, itemsB = 0;
+    for (int64_t it = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; it < total; it += stride) {
+        if (it >= hi) {   // the molecule of item it: the last one with s_pre[c] <= it
+            int l = 0, h = nmol - 1;
+            while (l < h) {
+                const int mid = (l + h + 1) >> 1;
+                if (s_pre[mid] <= it) l = mid; else h = mid - 1;
+            }
+            c = l;
+            lo = s_pre[c];
+            hi = s_pre[c + 1];
+            tc_slice_counts(mols[c].ctrl, mols[c].n, k, s0, nseg, itemsA, itemsB);
+        }
+        const CdMolTC& m = mols[c];
+        tc_slice_item(it - lo, itemsA, m.n, reinterpret_cast<const float2*>(m.L), m.sigA, m.A,
+                      m.B, m.sigB, m.ctrl, k, s0, nseg);
+    }
+}
+
+// Vector k, residuals and next pivot of every molecule still running; block b
+// belongs to molecule blk_mol[b].
+__global__ void __launch_bounds__(kUpdThreads, 4)
+k_bcd_update_tc(const CdMolTC* __restrict__ mols, const int32_t* __restrict__ blk_mol) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ CdMolTC m;   // the molecule's table entry, read by every thread from here
+    if (threadIdx.x < sizeof(CdMolTC) / 8)
+        reinterpret_cast<long long*>(&m)[threadIdx.x] =
+            reinterpret_cast<const long long*>(mols + blk_mol[blockIdx.x])[threadIdx.x];
+    __syncthreads();
+    if (m.ctrl->done) return;
+    cd_step_body<true, true, true>(m.n, m.ctrl->kstep, m.max_rank, m.L, m.D, m.cand, nullptr, m.G,
+                                   reinterpret_cast<long long*>(m.blk_a),
+                                   reinterpret_cast<long long*>(m.blk_b), m.blk_i, m.piv, m.ctrl,
+                                   (int)blockIdx.x - m.b0_epi, m.nb_epi, m.pf);
+}
+
+// Rows [0, M) of the compact vectors (float pairs, a copy) into the full FP64
+// rows of L, whose screened entries were zeroed.
+__global__ void k_bcd_tc_scatter(const float2* __restrict__ Lc, int64_t nc,
+                                 const int32_t* __restrict__ live, double* __restrict__ L,
+                                 int64_t n, int32_t M) {
+    const int64_t total = (int64_t)M * nc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / nc, j = i - r * nc;
+        const float2 v = Lc[i];
+        L[r * n + live[j]] = (double)v.x + (double)v.y;
+    }
+}
+
+// One molecule's region of the batched tensor-core workspace.
+struct TcMolLay {
+    PairSoA pd;
+    PairF2 pf;
+    uint8_t* cand;
+    int32_t* live;
+    int32_t* scan;
+    double* Dc;
+    uint8_t* candc;
+    int32_t* pivc;
+    float2* G;
+    __nv_bfloat16* A;
+    __nv_bfloat16* B;
+    float* sigA;
+    float* sigB;
+    double* blk_a;
+    double* blk_b;
+    long long* blk_i;
+    int32_t kcap;
+};
+
+static TcMolLay tc_mol_carve(Carver& c, int64_t n, int32_t max_rank) {
+    TcMolLay l;
+    const int nb = part_blocks(n);
+    l.kcap = tc_kcap(max_rank);
+    l.pd.p = c.take<double>(n);
+    l.pd.Px = c.take<double>(n);
+    l.pd.Py = c.take<double>(n);
+    l.pd.Pz = c.take<double>(n);
+    l.pd.Kp = c.take<double>(n);
+    l.pf.p = c.take<float2>(n);
+    l.pf.Px = c.take<float2>(n);
+    l.pf.Py = c.take<float2>(n);
+    l.pf.Pz = c.take<float2>(n);
+    l.pf.Kp = c.take<float2>(n);
+    l.cand = c.take<uint8_t>(n);
+    l.live = c.take<int32_t>(n);
+    l.scan = c.take<int32_t>(n / kScanChunk + 2);
+    l.Dc = c.take<double>(n);
+    l.candc = c.take<uint8_t>(n);
+    l.pivc = c.take<int32_t>(std::max(max_rank, 1));
+    l.G = c.take<float2>((size_t)kSpecTC * n);
+    l.A = c.take<__nv_bfloat16>((size_t)kSlicesTC * n * l.kcap);
+    l.B = c.take<__nv_bfloat16>((size_t)kSlicesTC * kSpecTC * l.kcap);
+    l.sigA = c.take<float>(n);
+    l.sigB = c.take<float>(kSpecTC);
+    l.blk_a = c.take<double>(nb);
+    l.blk_b = c.take<double>(nb);
+    l.blk_i = c.take<long long>(nb);
+    return l;
+}
+
+struct CdTcBatchLayout {
+    CdMolTC* mols;
+    CdTcMolGemm* gmols;
+    char* maps;           // [nmol] tensor-map pairs
+    CdCtrl* ctrl;
+    int32_t* blk_mol;
+    int32_t* err;
+    float2* scratch;      // the compact rows of one molecule, copied before the scatter
+    size_t bytes;
+};
+
+static CdTcBatchLayout cd_tc_batch_layout(void* ws, int32_t nmol, const BatchMol* mols,
+                                          std::vector<TcMolLay>* per) {
+    Carver c(ws);
+    CdTcBatchLayout l;
+    int64_t nblk = 0, scratch = 1;
+    for (int i = 0; i < nmol; ++i) {
+        const int64_t n = npair_of(mols[i].nbf);
+        nblk += step_blocks(n);
+        scratch = std::max<int64_t>(scratch, (int64_t)mols[i].max_rank * n);
+    }
+    l.mols = c.take<CdMolTC>(std::max(nmol, 1));
+    l.gmols = c.take<CdTcMolGemm>(std::max(nmol, 1));
+    l.maps = c.take<char>(cd_tc_maps_bytes() * std::max(nmol, 1));
+    l.ctrl = c.take<CdCtrl>(std::max(nmol, 1));
+    l.blk_mol = c.take<int32_t>(std::max<int64_t>(nblk, 1));
+    l.err = c.take<int32_t>(4);
+    l.scratch = c.take<float2>(scratch);
+    if (per) per->resize(nmol);
+    for (int i = 0; i < nmol; ++i) {
+        TcMolLay m = tc_mol_carve(c, npair_of(mols[i].nbf), mols[i].max_rank);
+        if (per) (*per)[i] = m;
+    }
+    l.bytes = c.off;
+    return l;
+}
+
+size_t cd_tc_batch_workspace_bytes(int32_t nmol, const BatchMol* mols) {
+    return cd_tc_batch_layout(nullptr, nmol, mols, nullptr).bytes;
+}
+
+// Molecules [g0, g1) of the batch (at most kMaxMolsTC), their screening done:
+// the steps, then every molecule's rows, pivots and residuals.
+static int cd_tc_batch_group(int32_t g0, int32_t g1, const BatchMol* mols,
+                             const BatchOffsets* off, const std::vector<TcMolLay>& ml,
+                             const CdTcBatchLayout& lay, double* L, int32_t* piv, double* D,
+                             int32_t* M_out, int* status, cudaStream_t stream) {
+    const int nm = g1 - g0;
+    const int nsm = sm_count();
+    std::vector<CdCtrl> hc(nm);
+    CDS_CUDA_TRY(cudaMemcpyAsync(hc.data(), lay.ctrl + g0, sizeof(CdCtrl) * nm,
+                                 cudaMemcpyDeviceToHost, stream));
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    std::vector<CdMolTC> h(nm);
+    std::vector<CdTcMolGemm> hg(nm);
+    // host copies of the tensor maps (64-byte aligned, as the type requires)
+    std::vector<char> maps_raw(cd_tc_maps_bytes() * nm + 64);
+    char* hmaps = maps_raw.data() + (64 - reinterpret_cast<uintptr_t>(maps_raw.data()) % 64) % 64;
+    std::vector<int32_t> bm;
+    std::vector<int64_t> nlive(nm, 0);
+    int32_t kmax = 0;
+    for (int i = 0; i < nm; ++i) {
+        const int c = g0 + i;
+        const TcMolLay& m = ml[c];
+        const int64_t nc = hc[i].nlive;
+        CdMolTC& d = h[i];
+        d = CdMolTC{};
+        d.ctrl = lay.ctrl + c;
+        if (nc <= 0) {   // no diagonal passed the test: NaN or a zero scale
+            CdCtrl stop = hc[i];
+            stop.done = 1;
+            stop.status = CDS_ERR_NOT_PD;
+            stop.M = 0;
+            CDS_CUDA_TRY(cudaMemcpyAsync(lay.ctrl + c, &stop, sizeof(CdCtrl),
+                                         cudaMemcpyHostToDevice, stream));
+            CDS_CUDA_TRY(cudaStreamSynchronize(stream));   // `stop` is a stack copy
+            hc[i] = stop;
+            hg[i] = CdTcMolGemm{1, m.sigA, m.sigB, m.G, lay.ctrl + c};
+            const int st = cd_tc_maps_encode(hmaps + cd_tc_maps_bytes() * i, 1, m.kcap,
+                                             m.A, m.B);
+            if (st) return st;
+            continue;
+        }
+        if (step_blocks(nc) > kMaxBlocksTC) return CDS_ERR_UNSUPPORTED;
+        nlive[i] = nc;
+        d.pf = m.pf;
+        d.L = L + off[c].L;
+        d.D = m.Dc;
+        d.cand = m.candc;
+        d.piv = m.pivc;
+        d.sigA = m.sigA;
+        d.A = m.A;
+        d.B = m.B;
+        d.sigB = m.sigB;
+        d.G = m.G;
+        d.blk_a = m.blk_a;
+        d.blk_b = m.blk_b;
+        d.blk_i = m.blk_i;
+        d.n = nc;
+        d.max_rank = mols[c].max_rank;
+        d.nb_epi = step_blocks(nc);
+        kmax = std::max(kmax, mols[c].max_rank);
+        k_cd_select<<<sel_blocks(nc), kCdThreads, 0, stream>>>(nc, 0, d.max_rank, m.Dc, m.candc,
+                                                               m.blk_i, m.pivc, lay.ctrl + c);
+        CDS_LAUNCH_CHECK();
+        k_cd_tc_scales<<<(unsigned)((nc + 255) / 256), 256, 0, stream>>>(m.Dc, nc, m.sigA);
+        CDS_LAUNCH_CHECK();
+        hg[i] = CdTcMolGemm{nc, m.sigA, m.sigB, m.G, lay.ctrl + c};
+        const int st = cd_tc_maps_encode(hmaps + cd_tc_maps_bytes() * i, nc, m.kcap, m.A,
+                                         m.B);
+        if (st) return st;
+    }
+    // the update grid: the largest molecules' blocks first, so the blocks
+    // scheduled last (and the serial ends of their steps) are short
+    std::vector<int> order;
+    for (int i = 0; i < nm; ++i)
+        if (nlive[i] > 0) order.push_back(i);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return nlive[a] > nlive[b]; });
+    for (int i : order) {
+        h[i].b0_epi = (int32_t)bm.size();
+        for (int b = 0; b < h[i].nb_epi; ++b) bm.push_back(i);
+    }
+    if (!bm.empty()) {
+        CDS_CUDA_TRY(cudaMemcpyAsync(lay.mols + g0, h.data(), sizeof(CdMolTC) * nm,
+                                     cudaMemcpyHostToDevice, stream));
+        CDS_CUDA_TRY(cudaMemcpyAsync(lay.gmols + g0, hg.data(), sizeof(CdTcMolGemm) * nm,
+                                     cudaMemcpyHostToDevice, stream));
+        CDS_CUDA_TRY(cudaMemcpyAsync(lay.maps + cd_tc_maps_bytes() * g0, hmaps,
+                                     cd_tc_maps_bytes() * nm, cudaMemcpyHostToDevice, stream));
+        CDS_CUDA_TRY(cudaMemcpyAsync(lay.blk_mol, bm.data(), sizeof(int32_t) * bm.size(),
+                                     cudaMemcpyHostToDevice, stream));
+        const CdMolTC* dm = lay.mols + g0;
+        const unsigned nupd = (unsigned)bm.size();
+        for (int32_t k0 = 0; k0 <= kmax; k0 += kHostCheckEvery) {
+            const int32_t k1 = std::min(kmax, k0 + kHostCheckEvery);
+            for (int32_t k = k0; k < k1; ++k) {
+                CDS_CUDA_TRY(launch_pdl(k_bcd_project_tc, (unsigned)(4 * nsm), kUpdThreads, 0,
+                                        stream, dm, nm));
+                const int s2 = cd_tc_batch_gemm_launch(lay.gmols + g0,
+                                                       lay.maps + cd_tc_maps_bytes() * g0, nm,
+                                                       lay.err, stream);
+                if (s2) return s2;
+                CDS_CUDA_TRY(launch_pdl(k_bcd_update_tc, nupd, kUpdThreads, 0, stream, dm,
+                                        (const int32_t*)lay.blk_mol));
+            }
+            count_launches(3ull * (unsigned long long)(k1 - k0));
+            CDS_CUDA_TRY(cudaGetLastError());
+            CDS_CUDA_TRY(cudaMemcpyAsync(hc.data(), lay.ctrl + g0, sizeof(CdCtrl) * nm,
+                                         cudaMemcpyDeviceToHost, stream));
+            CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+            bool all = true;
+            for (int i = 0; i < nm; ++i) all = all && hc[i].done;
+            if (all) break;
+        }
+    }
+    for (int i = 0; i < nm; ++i) {
+        const int c = g0 + i;
+        const int64_t n = npair_of(mols[c].nbf), nc = nlive[i];
+        M_out[c] = hc[i].M;
+        status[c] = hc[i].done ? hc[i].status : CDS_ERR_RANK_CAP;
+        if (nc <= 0) continue;
+        const int32_t M = hc[i].M;
+        double* Lm = L + off[c].L;
+        if (M > 0) {
+            CDS_CUDA_TRY(cudaMemcpyAsync(lay.scratch, Lm, (size_t)M * nc * sizeof(float2),
+                                         cudaMemcpyDeviceToDevice, stream));
+            CDS_CUDA_TRY(cudaMemsetAsync(Lm, 0, (size_t)M * n * sizeof(double), stream));
+            const int64_t items = (int64_t)M * nc;
+            k_bcd_tc_scatter<<<(unsigned)std::min<int64_t>((items + 255) / 256, 8 * nsm), 256, 0,
+                               stream>>>(lay.scratch, nc, ml[c].live, Lm, n, M);
+            CDS_LAUNCH_CHECK();
+        }
+        const int64_t fin = std::max<int64_t>(M, nc);
+        k_screen_finish<<<(unsigned)((fin + 255) / 256), 256, 0, stream>>>(
+            ml[c].pivc, M, ml[c].live, piv + off[c].piv, ml[c].Dc, nc, D + off[c].pair);
+        CDS_LAUNCH_CHECK();
+    }
+    return CDS_OK;
+}
+
+// Blocking: M_out[c] receives molecule c's rank; returns the first non-OK
+// status in molecule order.
+int cd_batch_decompose_tc(int32_t nmol, const BatchMol* mols, const BatchOffsets* off,
+                          const double* xyz, const double* alpha, const int32_t* atom,
+                          double delta, int32_t scheme, double* L, int32_t* piv, double* D,
+                          int32_t* M_out, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    std::vector<TcMolLay> ml;
+    const CdTcBatchLayout lay = cd_tc_batch_layout(ws, nmol, mols, &ml);
+    if (!ws || ws_bytes < lay.bytes) return CDS_ERR_WORKSPACE;
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.ctrl, 0, sizeof(CdCtrl) * nmol, stream));
+    CDS_CUDA_TRY(cudaMemsetAsync(lay.err, 0, sizeof(int32_t), stream));
+    // every molecule's diagonal, candidates and live pairs
+    for (int c = 0; c < nmol; ++c) {
+        const int64_t n = npair_of(mols[c].nbf);
+        const TcMolLay& m = ml[c];
+        int st = build_pairs(mols[c].nbf, xyz + 3 * off[c].basis, alpha + off[c].basis, m.pd,
+                             stream);
+        if (st) return st;
+        double* Dm = D + off[c].pair;
+        k_cd_init<<<cd_blocks(n), kCdThreads, 0, stream>>>(m.pd, atom + off[c].basis, scheme, n,
+                                                           delta, Dm, m.cand, m.blk_a, m.blk_b,
+                                                           lay.ctrl + c);
+        CDS_LAUNCH_CHECK();
+        const int nsb = (int)((n + kScanChunk - 1) / kScanChunk);
+        k_screen_count<<<nsb, kScanThreads, 0, stream>>>(Dm, n, lay.ctrl + c, m.scan);
+        CDS_LAUNCH_CHECK();
+        k_screen_scan<<<1, 1024, 0, stream>>>(m.scan, nsb, lay.ctrl + c);
+        CDS_LAUNCH_CHECK();
+        k_screen_gather<<<nsb, kScanThreads, 0, stream>>>(m.pd, Dm, m.cand, n, lay.ctrl + c,
+                                                          m.scan, m.live, m.pf, m.Dc, m.candc);
+        CDS_LAUNCH_CHECK();
+    }
+    std::vector<int> status(nmol, CDS_OK);
+    for (int32_t g0 = 0; g0 < nmol; g0 += kMaxMolsTC) {
+        const int st = cd_tc_batch_group(g0, std::min(nmol, g0 + kMaxMolsTC), mols, off, ml, lay,
+                                         L, piv, D, M_out, status.data(), stream);
+        if (st) return st;
+    }
+    int32_t e = 0;   // a bounded wait of the projection GEMM gave up
+    CDS_CUDA_TRY(cudaMemcpyAsync(&e, lay.err, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    CDS_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (e) return CDS_ERR_TIMEOUT;
+    for (int c = 0; c < nmol; ++c)
+        if (status[c]) return status[c];
+    return CDS_OK;
 }
 
 }  // namespace cds

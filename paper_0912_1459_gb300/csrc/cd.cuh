@@ -84,8 +84,8 @@ struct CdCtrl {
     int32_t k0, slot, pass, passes;     // passes: batches started (streaming passes)
     long long streamed;                  // sum over passes of the vectors streamed (k0)
     long long extra;                     // sum over continued steps of the vectors added (k - k0)
-    // exact-slice tensor-core form: its candidate set, and the columns of the
-    // slice store that are final (a multiple of kGroupTC)
+    // exact-slice tensor-core form: its candidate set, and the step of the
+    // previous pass (the slice store holds every row before it)
     long long STc[kSpecTC];
     int32_t kdone;
     int32_t nlive;     // tensor-core form: pairs kept after screening
@@ -117,5 +117,42 @@ int cd_tc_gemm_setup(CdTcGemm** out, int64_t n, int32_t kcap, const void* a_plan
                      const CdCtrl* ctrl, int32_t* err);
 int cd_tc_gemm_launch(const CdTcGemm* g, cudaStream_t stream);
 void cd_tc_gemm_free(CdTcGemm* g);
+
+// Batched form: one launch per step for up to kMaxMolsTC molecules, each with
+// its own two tensor maps (cd_tc_maps_bytes() bytes per molecule, 64-byte
+// aligned, in device memory) and this table entry; the tiles of the
+// molecules that start a pass at the step are spread over one CTA per SM.
+constexpr int kMaxMolsTC = 1024;
+struct CdTcMolGemm {
+    int64_t n;            // pair rows (the live pairs)
+    const float* sa;      // [n] pair scales
+    const float* sb;      // [kSpecTC] candidate scales
+    float2* G;            // [kSpecTC][n]
+    const CdCtrl* ctrl;
+};
+// Inclusive prefix, in place, of pre[1 .. nmol] (shared memory), and pre[0] = 0;
+// run by the 32 threads of one warp.
+template <typename T>
+__device__ __forceinline__ void warp_prefix_smem(T* pre, int nmol) {
+    const int lane = threadIdx.x & 31;
+    T run = 0;
+    for (int c0 = 0; c0 < nmol; c0 += 32) {
+        const int c = c0 + lane;
+        T x = c < nmol ? pre[c + 1] : T(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const T y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (c < nmol) pre[c + 1] = run + x;
+        run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) pre[0] = 0;
+}
+size_t cd_tc_maps_bytes();
+int cd_tc_maps_encode(void* out, int64_t n, int32_t kcap, const void* a_planes,
+                      const void* b_planes);
+int cd_tc_batch_gemm_launch(const CdTcMolGemm* mols, const void* maps, int32_t nmol,
+                            int32_t* err, cudaStream_t stream);
 
 }  // namespace cds

@@ -145,19 +145,25 @@ __device__ __forceinline__ bool epi_any(bool v) {
     return r != 0;
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
-k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restrict__ err) {
-    pdl_trigger();
-    pdl_wait();
-    // the same decision in every thread: nothing to do unless this step starts a pass
-    if (g.ctrl->done || !g.ctrl->pass) return;
-    const int32_t k0 = g.ctrl->k0;
-    if (k0 <= 0) return;   // the first step projects on nothing (the update takes 0)
-    const int kblocks = (k0 + KE - 1) / KE;
-    const int nchunk = (kblocks + CHUNK_KB - 1) / CHUNK_KB;
+// One M tile of a pass: the molecule's maps, the tile row, its K extent and
+// where the projections go.
+struct TileRef {
+    const CUtensorMap* a;
+    const CUtensorMap* b;
+    int mt;             // tile of 128 pair rows
+    int kblocks;        // 32-column k-blocks of the pass (k0 rounded up)
+    int nchunk;         // exact chunks of CHUNK_KB k-blocks
+    int64_t n;          // pair rows of the molecule
+    const float* sa;
+    const float* sb;
+    float2* G;
+};
 
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+// The three roles over the tiles src.tile(0 .. src.count()-1) of this CTA,
+// every chunk of a tile in order (one CTA sums a tile's chunks).  The TMEM
+// buffer of the u-th chunk overall is u & 1, in every role.
+template <class Src>
+__device__ __forceinline__ void gemm_roles(const Src& src, uint8_t* smem, int32_t* err) {
     uint8_t* stages = smem;
     uint64_t* bars = (uint64_t*)(smem + NSTAGE * STAGE_BYTES);
     uint64_t* full = bars;
@@ -167,11 +173,7 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
     uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // work unit = (tile, chunk): a CTA takes tiles round robin and every chunk
-    // of its tile in order, so one CTA sums a tile's chunks
-    const int64_t my_units = g.mtiles > (int64_t)blockIdx.x
-                                 ? ((g.mtiles - 1 - blockIdx.x) / gridDim.x + 1) * nchunk
-                                 : 0;
+    const int ntiles = src.count();
     volatile int32_t* verr = err;
 
     // the zero groups below the candidate slices of every stage (never loaded)
@@ -204,16 +206,15 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
             int32_t last_parity[NSTAGE];
             for (int i = 0; i < NSTAGE; ++i) last_parity[i] = -1;
             bool ok = true;
-            for (int64_t j = 0; ok && j < my_units; ++j) {
-                const int mt = (int)(blockIdx.x + (j / nchunk) * gridDim.x), ch = (int)(j % nchunk);
-                const int kb1 = min(kblocks, (ch + 1) * CHUNK_KB);
-                for (int kb = ch * CHUNK_KB; kb < kb1; ++kb) {
+            for (int j = 0; ok && j < ntiles; ++j) {
+                const TileRef t = src.tile(j);
+                for (int kb = 0; kb < t.kblocks; ++kb) {
                     if (!mbar_wait(&empty[stage], phase ^ 1u, verr)) { ok = false; break; }
                     mbar_arrive_expect_tx(&full[stage], TX_BYTES);
                     last_parity[stage] = (int32_t)phase;
                     const uint32_t st = smem_u32(stages + stage * STAGE_BYTES);
-                    tma_load_3d(st, &maps.a, &full[stage], 0, mt * TM, kb * S);
-                    tma_load_3d(st + B_OFF + ZG * GRP, &maps.b, &full[stage], 0, 0, kb * S);
+                    tma_load_3d(st, t.a, &full[stage], 0, t.mt * TM, kb * S);
+                    tma_load_3d(st + B_OFF + ZG * GRP, t.b, &full[stage], 0, 0, kb * S);
                     if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                 }
             }
@@ -225,35 +226,38 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
             // ---------------- MMA issuer ----------------
             constexpr MmaTab kM = make_mmas();
             int stage = 0;
-            uint32_t phase = 0;
+            uint32_t phase = 0, u = 0;
             bool ok = true;
-            for (int64_t j = 0; ok && j < my_units; ++j) {
-                const int ch = (int)(j % nchunk), buf = (int)(j & 1);
-                const uint32_t use = (uint32_t)((j >> 1) & 1);
-                const int kbeg = ch * CHUNK_KB, kb1 = min(kblocks, (ch + 1) * CHUNK_KB);
-                if (!mbar_wait(&tempty[buf], use ^ 1u, verr)) break;
-                fence_after();
-                const uint32_t dbase = tmem + (uint32_t)(buf * BUF_COLS);
-                for (int kb = kbeg; kb < kb1; ++kb) {
-                    if (!mbar_wait(&full[stage], phase, verr)) { ok = false; break; }
+            for (int j = 0; ok && j < ntiles; ++j) {
+                const TileRef t = src.tile(j);
+                for (int ch = 0; ok && ch < t.nchunk; ++ch, ++u) {
+                    const int buf = (int)(u & 1);
+                    const uint32_t use = (u >> 1) & 1;
+                    const int kbeg = ch * CHUNK_KB, kb1 = min(t.kblocks, (ch + 1) * CHUNK_KB);
+                    if (!mbar_wait(&tempty[buf], use ^ 1u, verr)) { ok = false; break; }
                     fence_after();
-                    const uint32_t base = smem_u32(stages + stage * STAGE_BYTES);
+                    const uint32_t dbase = tmem + (uint32_t)(buf * BUF_COLS);
+                    for (int kb = kbeg; kb < kb1; ++kb) {
+                        if (!mbar_wait(&full[stage], phase, verr)) { ok = false; break; }
+                        fence_after();
+                        const uint32_t base = smem_u32(stages + stage * STAGE_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {   // 16 BF16 (32 bytes) of k per MMA
-                        const uint32_t off = kk * 32;
+                        for (int kk = 0; kk < 2; ++kk) {   // 16 BF16 (32 bytes) of k per MMA
+                            const uint32_t off = kk * 32;
 #pragma unroll
-                        for (int q = 0; q < 12; ++q) {
-                            const uint32_t en = ((kb > kbeg) || kk || !kM.first[q]) ? 1u : 0u;
-                            mma_f16(dbase + (uint32_t)(kM.acc[q] * TN),
-                                    sdesc(base + kM.s[q] * A_SLICE + off),
-                                    sdesc(base + B_OFF + kM.w[q] * GRP + off), ID, en);
+                            for (int q = 0; q < 12; ++q) {
+                                const uint32_t en = ((kb > kbeg) || kk || !kM.first[q]) ? 1u : 0u;
+                                mma_f16(dbase + (uint32_t)(kM.acc[q] * TN),
+                                        sdesc(base + kM.s[q] * A_SLICE + off),
+                                        sdesc(base + B_OFF + kM.w[q] * GRP + off), ID, en);
+                            }
                         }
+                        mma_commit(&empty[stage]);
+                        if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
                     }
-                    mma_commit(&empty[stage]);
-                    if (++stage == NSTAGE) { stage = 0; phase ^= 1u; }
+                    if (!ok) break;
+                    mma_commit(&tfull[buf]);
                 }
-                if (!ok) break;
-                mma_commit(&tfull[buf]);
             }
         }
     } else {
@@ -261,48 +265,52 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
         const int quad = warp & 3;
         const int row = quad * 32 + lane;
         float2 acc[NC];
-        for (int64_t j = 0; j < my_units; ++j) {
-            const int buf = (int)(j & 1);
-            const uint32_t use = (uint32_t)((j >> 1) & 1);
-            const bool bad = !mbar_wait(&tfull[buf], use, verr) || *verr;
-            if (epi_any(bad)) break;
-            fence_after();
-            const int mt = (int)(blockIdx.x + (j / nchunk) * gridDim.x), ch = (int)(j % nchunk);
-            const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BUF_COLS);
+        uint32_t u = 0;
+        bool stop = false;
+        for (int j = 0; !stop && j < ntiles; ++j) {
+            const TileRef t = src.tile(j);
+            for (int ch = 0; ch < t.nchunk; ++ch, ++u) {
+                const int buf = (int)(u & 1);
+                const uint32_t use = (u >> 1) & 1;
+                const bool bad = !mbar_wait(&tfull[buf], use, verr) || *verr;
+                if (epi_any(bad)) { stop = true; break; }
+                fence_after();
+                const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * BUF_COLS);
 #pragma unroll
-            for (int c0 = 0; c0 < NC; c0 += 8) {
-                float x[4][8], y[4][8];
+                for (int c0 = 0; c0 < NC; c0 += 8) {
+                    float x[4][8], y[4][8];
 #pragma unroll
-                for (int gq = 0; gq < 4; ++gq) {
-                    tmem_ld8(ta + (uint32_t)(gq * NC + c0), x[gq]);
-                    tmem_ld8(ta + (uint32_t)(TN + gq * NC + c0), y[gq]);
+                    for (int gq = 0; gq < 4; ++gq) {
+                        tmem_ld8(ta + (uint32_t)(gq * NC + c0), x[gq]);
+                        tmem_ld8(ta + (uint32_t)(TN + gq * NC + c0), y[gq]);
+                    }
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        // weights 7, 6, 5, 4 (Y), then 3, 2, 1, 0 (X): finest first
+                        float2 v = two_sum(y[3][i], y[2][i]);
+                        v = pair_add(v, y[1][i]);
+                        v = pair_add(v, y[0][i]);
+                        v = pair_add(v, x[3][i]);
+                        v = pair_add(v, x[2][i]);
+                        v = pair_add(v, x[1][i]);
+                        v = pair_add(v, x[0][i]);
+                        acc[c0 + i] = ch == 0 ? v : pair_add2(acc[c0 + i], v);
+                    }
                 }
-                tmem_wait_ld();
+                // this buffer is read: the MMAs may reuse it
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[buf]);
+                if (ch == t.nchunk - 1) {   // the tile's last chunk: scale and store
+                    const int64_t I = (int64_t)t.mt * TM + row;
+                    if (I < t.n) {
+                        const float sa = t.sa[I];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    // weights 7, 6, 5, 4 (Y), then 3, 2, 1, 0 (X): finest first
-                    float2 v = two_sum(y[3][i], y[2][i]);
-                    v = pair_add(v, y[1][i]);
-                    v = pair_add(v, y[0][i]);
-                    v = pair_add(v, x[3][i]);
-                    v = pair_add(v, x[2][i]);
-                    v = pair_add(v, x[1][i]);
-                    v = pair_add(v, x[0][i]);
-                    acc[c0 + i] = ch == 0 ? v : pair_add2(acc[c0 + i], v);
-                }
-            }
-            // this buffer is read: the MMAs may reuse it
-            fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[buf]);
-            if (ch == nchunk - 1) {   // the tile's last chunk: scale and store
-                const int64_t I = (int64_t)mt * TM + row;
-                if (I < g.n) {
-                    const float sa = g.sa[I];
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const float st = sa * g.sb[c];   // power of two: exact scaling
-                        g.G[(int64_t)c * g.n + I] = make_float2(acc[c].x * st, acc[c].y * st);
+                        for (int c = 0; c < NC; ++c) {
+                            const float st = sa * t.sb[c];   // power of two: exact scaling
+                            t.G[(int64_t)c * t.n + I] = make_float2(acc[c].x * st, acc[c].y * st);
+                        }
                     }
                 }
             }
@@ -316,6 +324,82 @@ k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restric
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(TMEM_COLS));
     }
+}
+
+// The tiles of one molecule, round robin over the grid.
+struct OneSrc {
+    const Maps* maps;
+    const Args* g;
+    int kblocks, nchunk;
+    __device__ int count() const {
+        return g->mtiles > (int)blockIdx.x ? (g->mtiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    }
+    __device__ TileRef tile(int j) const {
+        return TileRef{&maps->a, &maps->b, (int)blockIdx.x + j * (int)gridDim.x, kblocks, nchunk,
+                       g->n, g->sa, g->sb, g->G};
+    }
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_cd_gemm_tc(const __grid_constant__ Maps maps, const Args g, int32_t* __restrict__ err) {
+    pdl_trigger();
+    pdl_wait();
+    // the same decision in every thread: nothing to do unless this step starts a pass
+    if (g.ctrl->done || !g.ctrl->pass) return;
+    const int32_t k0 = g.ctrl->k0;
+    if (k0 <= 0) return;   // the first step projects on nothing (the update takes 0)
+    const int kblocks = (k0 + KE - 1) / KE;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const OneSrc src{&maps, &g, kblocks, (kblocks + CHUNK_KB - 1) / CHUNK_KB};
+    gemm_roles(src, smem, err);
+}
+
+// Batched form: the tiles of every molecule that starts a pass at this step,
+// numbered molecule by molecule (s_pre: exclusive prefix of the molecules'
+// tile counts), round robin over the grid.
+struct BatchSrc {
+    const CdTcMolGemm* mols;
+    const Maps* maps;
+    const int* pre;     // shared: [nmol + 1]
+    int nmol, total;
+    __device__ int count() const {
+        return total > (int)blockIdx.x ? (total - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    }
+    __device__ TileRef tile(int j) const {
+        const int t = (int)blockIdx.x + j * (int)gridDim.x;
+        int lo = 0, hi = nmol - 1;   // last molecule with pre[c] <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (pre[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const CdTcMolGemm& m = mols[lo];
+        const int kblocks = (m.ctrl->k0 + KE - 1) / KE;
+        return TileRef{&maps[lo].a, &maps[lo].b, t - pre[lo], kblocks,
+                       (kblocks + CHUNK_KB - 1) / CHUNK_KB, m.n, m.sa, m.sb, m.G};
+    }
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+k_bcd_gemm_tc(const CdTcMolGemm* __restrict__ mols, const Maps* __restrict__ maps, int nmol,
+              int32_t* __restrict__ err) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ int s_pre[kMaxMolsTC + 1];
+    for (int c = threadIdx.x; c < nmol; c += blockDim.x) {
+        const CdCtrl* ctrl = mols[c].ctrl;
+        const bool on = !ctrl->done && ctrl->pass && ctrl->k0 > 0;
+        s_pre[c + 1] = on ? (int)((mols[c].n + TM - 1) / TM) : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) warp_prefix_smem(s_pre, nmol);
+    __syncthreads();
+    const int total = s_pre[nmol];
+    if (total == 0) return;   // the same decision in every thread
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const BatchSrc src{mols, maps, s_pre, nmol, total};
+    gemm_roles(src, smem, err);
 }
 
 // Group-blocked store [kcap / 32][S][rows][32] BF16: a box is the S slices of
@@ -383,5 +467,36 @@ int cd_tc_gemm_launch(const CdTcGemm* g, cudaStream_t stream) {
 }
 
 void cd_tc_gemm_free(CdTcGemm* g) { delete g; }
+
+size_t cd_tc_maps_bytes() { return sizeof(cdtc::Maps); }
+
+int cd_tc_maps_encode(void* out, int64_t n, int32_t kcap, const void* a_planes,
+                      const void* b_planes) {
+    using namespace cdtc;
+    if (!tc::device_ok()) return CDS_ERR_UNSUPPORTED;
+    if (n <= 0 || kcap <= 0 || kcap % KE != 0 || n > INT32_MAX - TM) return CDS_ERR_ARG;
+    Maps* m = static_cast<Maps*>(out);
+    if (!make_map(&m->a, a_planes, (uint64_t)kcap, (uint64_t)n, TM) ||
+        !make_map(&m->b, b_planes, (uint64_t)kcap, (uint64_t)NC, NC))
+        return CDS_ERR_CUDA;
+    return CDS_OK;
+}
+
+int cd_tc_batch_gemm_launch(const CdTcMolGemm* mols, const void* maps, int32_t nmol,
+                            int32_t* err, cudaStream_t stream) {
+    using namespace cdtc;
+    if (nmol <= 0 || nmol > kMaxMolsTC) return CDS_ERR_ARG;
+    static thread_local int attr_dev = -1;   // the attribute belongs to a device
+    int dev = 0;
+    CDS_CUDA_TRY(cudaGetDevice(&dev));
+    if (attr_dev != dev) {
+        CDS_CUDA_TRY(cudaFuncSetAttribute(k_bcd_gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)SMEM_BYTES));
+        attr_dev = dev;
+    }
+    CDS_CUDA_TRY(launch_pdl(k_bcd_gemm_tc, (unsigned)tc::device_sms(), THREADS, SMEM_BYTES, stream,
+                            mols, static_cast<const Maps*>(maps), (int)nmol, err));
+    return CDS_OK;
+}
 
 }  // namespace cds

@@ -223,10 +223,12 @@ def test_batch_float_pair_decomposition(batch):
 
 
 def test_batch_tensor_core_decomposition(batch):
-    """The batched decomposition with the tensor-core passes (each molecule's
-    own decomposition on the library's worker threads and streams) against
-    the FP64 batch: every molecule's pivots identical, vectors within 1e-9
-    (the single-molecule tensor-core bar)."""
+    """The batched decomposition with the tensor-core passes (every
+    molecule's screening, then three launches per step for the whole batch)
+    against the FP64 batch: every molecule's pivots identical, vectors within
+    1e-9 (the single-molecule tensor-core bar); and against the
+    single-molecule tensor-core call: the same arithmetic per molecule, so
+    pivots, vectors and residuals bit for bit."""
     mols, b, M, inp = batch
     spec = [(m.nbf, m.nocc, len(m.orbitals), m.nE, C.default_max_rank(m.nbf)) for m in mols]
     bt = C.Batch(spec, DEV, "bf16x3", cd_precision="ozaki")
@@ -237,4 +239,73 @@ def test_batch_tensor_core_decomposition(batch):
         npr = G.npair(m.nbf)
         assert torch.equal(bt.view("piv", c, (M[c],)), b.view("piv", c, (M[c],)))
         torch.testing.assert_close(bt.view("L", c, (M[c], npr)), b.view("L", c, (M[c], npr)),
+                                   rtol=0, atol=1e-9)
+    for c in (0, 3, 7):
+        m = mols[c]
+        npr = G.npair(m.nbf)
+        L1, p1, D1, _ = G.cds_cd_decompose(dev(m.basis.xyz), dev(m.basis.alpha),
+                                           dev(m.basis.atom.astype(np.int32)), m.delta, "full",
+                                           precision="ozaki")
+        assert L1.shape[0] == M[c]
+        assert torch.equal(bt.view("piv", c, (M[c],)), p1)
+        assert torch.equal(bt.view("L", c, (M[c], npr)), L1)
+        assert torch.equal(bt.view("D", c, (npr,)), D1)
+
+
+def test_batch_tensor_core_atomic(batch):
+    """The atomic pivot restriction (Sec. II.A) in the batched tensor-core
+    form: pivots identical to the FP64 batch, every pivot a one-centre pair,
+    vectors within 1e-9."""
+    mols, _, _, inp = batch
+    spec = [(m.nbf, m.nocc, len(m.orbitals), m.nE, C.default_max_rank(m.nbf)) for m in mols]
+    b64 = C.Batch(spec, DEV, "bf16x3")
+    M64 = b64.cd_decompose(inp["xyz"], inp["al"], inp["at"], mols[0].delta, "atomic")
+    bt = C.Batch(spec, DEV, "bf16x3", cd_precision="ozaki")
+    Mt = bt.cd_decompose(inp["xyz"], inp["al"], inp["at"], mols[0].delta, "atomic",
+                         precision="ozaki")
+    torch.cuda.synchronize()
+    assert Mt == M64
+    for c, m in enumerate(mols):
+        npr = G.npair(m.nbf)
+        pv = bt.view("piv", c, (Mt[c],))
+        assert torch.equal(pv, b64.view("piv", c, (Mt[c],)))
+        mu, nu = eri.pair_list(m.nbf)
+        p = pv.cpu().numpy()
+        assert np.all(m.basis.atom[mu[p]] == m.basis.atom[nu[p]])
+        torch.testing.assert_close(bt.view("L", c, (Mt[c], npr)), b64.view("L", c, (Mt[c], npr)),
+                                   rtol=0, atol=1e-9)
+
+
+def test_batch_tensor_core_many_molecules():
+    """More molecules than one batched launch takes (1024): the batch runs in
+    groups.  1030 small clusters (1..3 centres, seeded), pivots identical to
+    the FP64 batch and vectors within 1e-9."""
+    rng = np.random.default_rng(11)
+    nmol = 1030
+    xyz, al, at, spec, nbfs = [], [], [], [], []
+    for c in range(nmol):
+        nat = int(rng.integers(1, 4))
+        cen = rng.uniform(0.0, 3.0, (nat, 3))
+        ex = W.geometric_exponents(0.2, 6.0, 4)
+        for a in range(nat):
+            for e in ex:
+                xyz.append(cen[a])
+                al.append(e)
+                at.append(a)
+        nbf = 4 * nat
+        nbfs.append(nbf)
+        spec.append((nbf, 1, 1, 1, C.default_max_rank(nbf)))
+    xyz = dev(np.array(xyz).ravel())
+    al = dev(np.array(al))
+    at = dev(np.array(at, dtype=np.int32))
+    b64 = C.Batch(spec, DEV, "bf16x3")
+    M64 = b64.cd_decompose(xyz, al, at, 1e-6)
+    bt = C.Batch(spec, DEV, "bf16x3", cd_precision="ozaki")
+    Mt = bt.cd_decompose(xyz, al, at, 1e-6, precision="ozaki")
+    torch.cuda.synchronize()
+    assert Mt == M64
+    for c in list(range(0, nmol, 97)) + [1023, 1024, 1029]:
+        npr = G.npair(nbfs[c])
+        assert torch.equal(bt.view("piv", c, (Mt[c],)), b64.view("piv", c, (Mt[c],)))
+        torch.testing.assert_close(bt.view("L", c, (Mt[c], npr)), b64.view("L", c, (Mt[c], npr)),
                                    rtol=0, atol=1e-9)
