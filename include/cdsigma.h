@@ -555,10 +555,12 @@ int cds_cd_to_mo_backward(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, con
  * molecule's own.  The workspace (cds_batch_workspace_bytes) holds a
  * scratch part shared by the decomposition and the transform, a part
  * holding the self-energy / Newton state that a graph (below) refers to,
- * and 8 worker slots: the library runs per-molecule work (the tensor-core
- * decomposition, the transform) on 8 host threads, each with a library
- * stream of its own, ordered after the caller's stream and before its later
- * work.
+ * 8 worker slots: the library runs the per-molecule transforms on 8 host
+ * threads, each with a library stream of its own, ordered after the
+ * caller's stream and before its later work; and, sized for
+ * CDS_PREC_OZAKI only, the region of the batched tensor-core decomposition
+ * (every molecule's slice store [max_rank rounded up to 32][8][npair] BF16,
+ * candidate projections and pair data).
  * ---------------------------------------------------------------------- */
 
 typedef struct {
@@ -574,23 +576,27 @@ typedef struct {
 /* Host only.  offs: host [(nmol + 1) * CDS_BATCH_NOFF]. */
 int cds_batch_offsets(int32_t nmol, const cds_mol* mols, int64_t* offs);
 
-/* Host only.  precision CDS_PREC_OZAKI sizes the worker slots for the
- * tensor-core decomposition of the largest molecule as well; any other value
- * sizes them for the transforms.  The calls accept a workspace without the
- * slots (the scratch and state parts only); the transform then runs the
- * molecules one after the other on the caller's stream, and the tensor-core
- * decomposition returns CDS_ERR_WORKSPACE. */
+/* Host only.  precision CDS_PREC_OZAKI adds the region of the batched
+ * tensor-core decomposition after the worker slots; any other value leaves
+ * it out.  The calls accept a workspace without the slots (the scratch and
+ * state parts only); the transform then runs the molecules one after the
+ * other on the caller's stream, and the tensor-core decomposition returns
+ * CDS_ERR_WORKSPACE. */
 size_t cds_batch_workspace_bytes(int32_t nmol, const cds_mol* mols, int32_t precision);
 
 /* Blocking.  Per molecule as cds_cd_decompose (delta and scheme shared);
  * M_out: host [nmol].  precision: CDS_PREC_FP64, or CDS_PREC_F32X2 (float-pair
  * projections and vectors, FP64 integral column, residuals and pivot
  * decisions; L converted to FP64 at the end): one update and one
- * pivot-select launch per step for the whole batch.  CDS_PREC_OZAKI: each
- * molecule's tensor-core decomposition (as cds_cd_decompose), the largest
- * molecules first, on the worker threads (the workspace needs the slots of
- * cds_batch_workspace_bytes(..., CDS_PREC_OZAKI)).  Returns the first non-OK
- * molecule status. */
+ * pivot-select launch per step for the whole batch.  CDS_PREC_OZAKI: the
+ * tensor-core form of cds_cd_decompose for every molecule (the same
+ * screening, pivots and arithmetic, so the same results bit for bit), its
+ * steps batched: three launches per step (slicing, projection GEMM, update)
+ * for up to 1024 molecules, larger batches in groups of 1024 (the workspace
+ * needs the region of cds_batch_workspace_bytes(..., CDS_PREC_OZAKI)); a
+ * molecule's compact vectors are held in its own rows of L during the
+ * steps.  Returns the first non-OK molecule status (CDS_ERR_TIMEOUT first
+ * when a bounded wait of the projection GEMM gave up). */
 int cds_batch_cd_decompose(int32_t nmol, const cds_mol* mols, const double* xyz,
                            const double* alpha, const int32_t* atom, double delta,
                            int32_t scheme, int32_t precision, double* L, int32_t* piv, double* D,
@@ -651,7 +657,7 @@ int cds_graph_destroy(cds_graph* graph);
  *   CDS_TUNE_CD_GRAPH: the tensor-core decomposition replays each chunk of
  *     32 steps as one CUDA graph (one launch instead of 96) when max_rank is
  *     at least this value and the stream is not a default stream (0 = never;
- *     default 512; the batched form's worker threads launch step by step);
+ *     default 512; the batched form launches step by step);
  *   CDS_TUNE_PIPE_SPLIT: in cds_cd_decompose_to_mo with a tensor-core
  *     transform, the transform's GEMMs take at most this many CTAs (one per
  *     SM) and the decomposition's projection GEMM the other SMs, so the two

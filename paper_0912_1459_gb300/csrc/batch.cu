@@ -3,11 +3,11 @@
 //
 //  * Cholesky decomposition: FP64 / float pairs: one update and one select
 //    launch per step for the whole batch (cd.cu, cd_batch_decompose); the
-//    tensor-core form (CDS_PREC_OZAKI): each molecule's own decomposition,
-//    the molecules spread over kWorkers host threads, each driving a library
-//    stream of its own, so the latency-bound steps of small molecules run
-//    side by side.
-//  * Transform: per molecule, on the same worker threads and streams.
+//    tensor-core form (CDS_PREC_OZAKI): every molecule's screening, then
+//    three launches per step for the whole batch (cd.cu,
+//    cd_batch_decompose_tc).
+//  * Transform: per molecule, the molecules spread over kWorkers host
+//    threads, each driving a library stream of its own.
 //  * Self-energy: the work items of every molecule in one persistent
 //    tcgen05 launch (sigma_tc.cu, tc_batch_pass), per-molecule descriptors in
 //    device memory.

@@ -685,6 +685,7 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
     }
     if (!last_block(&ctrl->counter, nblk)) return;
 
+    __shared__ double s_dp;   // the residual of the next pivot
     long long A = -1, B = LLONG_MAX;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
         A = max(A, __ldcg(blk_a + i));
@@ -716,16 +717,26 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
             bl = block_min_ll(bl);
             if (bl == LLONG_MAX) break;
             long long best = LLONG_MAX;
+            double dbest = 0.0;
 #pragma unroll
             for (int r = 0; r < kStepPer; ++r) {
                 const int64_t I = bl * kStepChunk + r * kUpdThreads + threadIdx.x;
                 if (I < n) {
                     const double d = __ldcg(D + I);
-                    if (cand[I] && fmax(d, 0.0) >= thr && d > de) best = min(best, (long long)I);
+                    if (cand[I] && fmax(d, 0.0) >= thr && d > de && I < best) {
+                        best = (long long)I;
+                        dbest = d;
+                    }
                 }
             }
+            const long long mine_best = best;
             best = block_min_ll(best);
-            if (best != LLONG_MAX) { pick = best; break; }
+            if (best != LLONG_MAX) {
+                if (mine_best == best) s_dp = dbest;   // the pivot's residual, for DP
+                __syncthreads();
+                pick = best;
+                break;
+            }
             from = (int)bl + 1;
         }
         if (pick >= 0) stop = false;
@@ -823,11 +834,12 @@ __device__ __forceinline__ void cd_step_body(int64_t n, int32_t k, int32_t max_r
             ctrl->M = made;
         } else {
             ctrl->P = pick;
-            ctrl->DP = __ldcg(D + pick);
-            ctrl->rDP = 1.0 / sqrt(ctrl->DP);
+            const double DP = s_dp, rDP = 1.0 / sqrt(DP);
+            ctrl->DP = DP;
+            ctrl->rDP = rDP;
             {
-                const float h = (float)ctrl->rDP;
-                ctrl->rDPf = make_float2(h, (float)(ctrl->rDP - (double)h));
+                const float h = (float)rDP;
+                ctrl->rDPf = make_float2(h, (float)(rDP - (double)h));
             }
             piv[made] = (int32_t)pick;
             if constexpr (SPEC) {

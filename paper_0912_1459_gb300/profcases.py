@@ -15,6 +15,11 @@ holds a few GB of device memory at most and replays in seconds:
   python -m paper_0912_1459_gb300.profcases cdoz        # k_cd_gemm_tc, k_cd_project_tc,
                                                         # k_cd_update (tensor-core passes; 512
                                                         # steps, 4.4 GB on the device)
+  python -m paper_0912_1459_gb300.profcases bcd         # batched tensor-core decomposition of
+                                                        # the 64 clusters (launch lists only:
+                                                        # ~70 GB on the device)
+  python -m paper_0912_1459_gb300.profcases bcd8        # the same for 8 clusters of 240..300
+                                                        # functions, rank capacity 640 (8 GB)
 
 Factors are seeded random numbers of the right shape and magnitude (the
 kernels' cost does not depend on their values).
@@ -88,6 +93,28 @@ def main(mode: str) -> None:
         b.record()
         torch.cuda.synchronize()
         print(f"decomposition: {M} steps, {a.elapsed_time(b):.1f} ms")
+    elif mode in ("bcd", "bcd8"):
+        mols = W.config3()
+        cap = None
+        if mode == "bcd8":
+            mols = [c for c in mols if 240 <= c.nbf <= 300][:8]
+            cap = 640
+        spec = [(c.nbf, c.nocc, len(c.orbitals), c.nE, cap or G.default_max_rank(c.nbf))
+                for c in mols]
+        bt = G.Batch(spec, dev, "bf16x3", cd_precision="ozaki")
+
+        def cat(xs):
+            return d(np.concatenate(xs))
+        xyz = cat([c.basis.xyz.ravel() for c in mols])
+        al = cat([c.basis.alpha for c in mols])
+        at = cat([c.basis.atom.astype(np.int32) for c in mols])
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        M = bt.cd_decompose(xyz, al, at, mols[0].delta, precision="ozaki")
+        b.record()
+        torch.cuda.synchronize()
+        print(f"batched decomposition of {len(mols)} clusters (ranks {min(M)}..{max(M)}): "
+              f"{a.elapsed_time(b):.1f} ms")
     else:
         raise SystemExit(f"unknown case {mode!r}")
     torch.cuda.synchronize()
