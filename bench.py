@@ -214,7 +214,7 @@ def flops_model(m, M: int) -> dict:
     }
 
 
-CD_GEMM_TRAFFIC_PER_BYTE = 1.837544792e9 / 1.838065024e9
+CD_GEMM_TRAFFIC_PER_BYTE = 1.837708936e9 / 1.838065024e9
 
 
 def peaks():
