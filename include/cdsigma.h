@@ -275,6 +275,10 @@ int cds_cd_static_max_nbf(void);
  *   B^K_pq = sum_{mu,nu} C_{mu p} L^K_{mu nu} C_{nu q},  fp64.
  * ---------------------------------------------------------------------- */
 
+/* Host only.  Workspace of cds_cd_to_mo for M vectors.  The tensor-core forms
+ * transform the vectors in batches of max(32, about 65,536 / nbf rounded up
+ * to 32) vectors, at most M, so the workspace grows with M up to that batch;
+ * a workspace sized for a larger M serves any smaller one. */
 size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, int32_t np);
 
 /* Asynchronous (FP64, F32X2) or blocking (TF32X3, BF16X3: the tensor-core

@@ -25,6 +25,15 @@ constexpr int kGB = 64;   // output tile (rows and cols)
 constexpr int kGK = 16;   // depth of a shared-memory stage
 constexpr int kAoBatch = 32;
 
+// Vectors per batch of the tensor-core forms in cds_cd_to_mo (all M vectors
+// known up front): enough that the first GEMM has about 64 k rows (kb x N),
+// so small bases do not run as many tiny launches; at least kAoBatch, at most
+// M.  Each vector's results do not depend on the batch it is in.
+static int32_t tr_batch(int32_t nbf, int32_t M) {
+    const int32_t want = ((65536 / std::max(nbf, 1) + kAoBatch - 1) / kAoBatch) * kAoBatch;
+    return std::max(1, std::min(M, std::max(kAoBatch, want)));
+}
+
 struct StridedMat {
     const double* p;
     int64_t rs, cs, bs;   // element strides: row, column, batch
@@ -494,10 +503,9 @@ using namespace cds;
 
 extern "C" size_t cds_cd_to_mo_workspace_bytes(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M,
                                             int32_t np) {
-    (void)M;
     if (nbf <= 0 || nocc < 0 || np < 0) return 0;
     return std::max(ao_layout(nullptr, nbf, nmo, nocc, np).bytes,
-                    tr_any_workspace_bytes(nbf, nmo, nocc, np, kAoBatch));
+                    tr_any_workspace_bytes(nbf, nmo, nocc, np, tr_batch(nbf, std::max(M, 1))));
 }
 
 extern "C" int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, const double* L,
@@ -513,12 +521,13 @@ extern "C" int cds_cd_to_mo(int32_t nbf, int32_t nmo, int32_t nocc, int32_t M, c
     if (!workspace || workspace_bytes < cds_cd_to_mo_workspace_bytes(nbf, nmo, nocc, M, np))
         return CDS_ERR_WORKSPACE;
     if (is_tr_tc(precision)) {
-        int st = tr_any_columns(precision, nbf, nmo, nocc, C, orb, np, kAoBatch, workspace, stream);
-        for (int32_t K0 = 0; st == CDS_OK && K0 < M; K0 += kAoBatch)
-            st = tr_any_batch(precision, nbf, nmo, nocc, np, L, nullptr, K0,
-                              std::min(kAoBatch, M - K0), M, Lov, Lp, kAoBatch, workspace, stream);
+        const int32_t kb = tr_batch(nbf, M);
+        int st = tr_any_columns(precision, nbf, nmo, nocc, C, orb, np, kb, workspace, stream);
+        for (int32_t K0 = 0; st == CDS_OK && K0 < M; K0 += kb)
+            st = tr_any_batch(precision, nbf, nmo, nocc, np, L, nullptr, K0, std::min(kb, M - K0),
+                              M, Lov, Lp, kb, workspace, stream);
         if (st) return st;
-        return tr_any_status(precision, nbf, nmo, nocc, np, kAoBatch, workspace, stream);
+        return tr_any_status(precision, nbf, nmo, nocc, np, kb, workspace, stream);
     }
     AoLayout lay = ao_layout(workspace, nbf, nmo, nocc, np);
     if (precision == CDS_PREC_F32X2)
