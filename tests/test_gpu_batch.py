@@ -309,3 +309,39 @@ def test_batch_tensor_core_many_molecules():
         assert torch.equal(bt.view("piv", c, (Mt[c],)), b64.view("piv", c, (Mt[c],)))
         torch.testing.assert_close(bt.view("L", c, (Mt[c], npr)), b64.view("L", c, (Mt[c], npr)),
                                    rtol=0, atol=1e-9)
+
+
+def test_batch_tensor_core_degenerate_molecules():
+    """Edge cases in one batched tensor-core call, against the FP64 batch:
+    a single function (one pair), a molecule whose diagonal is below delta
+    from the start (rank 0), two coincident functions (a rank-deficient
+    supermatrix), and an ordinary cluster."""
+    rng = np.random.default_rng(5)
+    parts = []   # (xyz [n,3], alpha [n], atom [n])
+    parts.append((np.zeros((1, 3)), np.array([0.9]), np.zeros(1, np.int32)))
+    parts.append((np.array([[0.0, 0, 0], [0.5, 0, 0]]), np.array([1e-7, 2e-7]),
+                  np.zeros(2, np.int32)))
+    parts.append((np.array([[0.0, 0, 0], [0.0, 0, 0], [1.2, 0, 0]]), np.array([0.7, 0.7, 1.3]),
+                  np.array([0, 0, 1], np.int32)))
+    cen = rng.uniform(0, 4, (5, 3))
+    ex = W.geometric_exponents(0.2, 6.0, 4)
+    parts.append((np.repeat(cen, 4, axis=0), np.tile(ex, 5), np.repeat(np.arange(5), 4).astype(np.int32)))
+    spec = [(len(p[1]), 0, 1, 1, C.default_max_rank(len(p[1]))) for p in parts]
+    xyz = dev(np.concatenate([p[0].ravel() for p in parts]))
+    al = dev(np.concatenate([p[1] for p in parts]))
+    at = dev(np.concatenate([p[2] for p in parts]))
+    delta = 1e-3
+    b64 = C.Batch(spec, DEV, "bf16x3")
+    M64 = b64.cd_decompose(xyz, al, at, delta)
+    bt = C.Batch(spec, DEV, "bf16x3", cd_precision="ozaki")
+    Mt = bt.cd_decompose(xyz, al, at, delta, precision="ozaki")
+    torch.cuda.synchronize()
+    assert Mt == M64
+    assert Mt[0] == 1 and Mt[1] == 0 and Mt[2] < G.npair(3)
+    for c, p in enumerate(parts):
+        npr = G.npair(len(p[1]))
+        assert torch.equal(bt.view("piv", c, (Mt[c],)), b64.view("piv", c, (Mt[c],)))
+        torch.testing.assert_close(bt.view("L", c, (Mt[c], npr)), b64.view("L", c, (Mt[c], npr)),
+                                   rtol=0, atol=1e-9)
+        torch.testing.assert_close(bt.view("D", c, (npr,)), b64.view("D", c, (npr,)),
+                                   rtol=0, atol=1e-9)
