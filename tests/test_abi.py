@@ -49,3 +49,23 @@ def test_argument_errors_before_any_launch(lib):
                               None) == 7
     assert so.cds_qp_solve(24, 6, 10, None, None, None, 1, None, 1e-5, 0, 0, None, None, None,
                            None, None, 0, None) == 1
+
+
+def test_batch_workspace_sizes(lib):
+    """Host-side sizing of the batched workspace.  The tensor-core
+    decomposition (CDS_PREC_OZAKI) adds its own region after the worker slots.
+    The region holds every molecule's slice store: 8 BF16 slices per pair and
+    column of max_rank rounded up to 32, and more besides.  The transform's
+    workspace grows with the number of vectors up to its batch size."""
+    so = lib.load()
+    spec = [(40, 8, 4, 8, 240), (120, 24, 6, 16, 512), (7, 1, 1, 1, 28)]
+    mols = (lib.CdsMol * len(spec))(*[lib.CdsMol(*m) for m in spec])
+    other = so.cds_batch_workspace_bytes(len(spec), mols, lib.PRECISIONS["bf16x3"])
+    oz = so.cds_batch_workspace_bytes(len(spec), mols, lib.PRECISIONS["ozaki"])
+    assert other > 0
+    stores = sum(16 * lib.npair(n) * ((r + 31) // 32 * 32) for n, _, _, _, r in spec)
+    assert oz - other >= stores
+    assert so.cds_batch_workspace_bytes(0, mols, lib.PRECISIONS["ozaki"]) == 0
+    # the transform: more vectors need more room, up to the batch size
+    w = [so.cds_cd_to_mo_workspace_bytes(100, 100, 20, m, 4) for m in (1, 32, 320, 700, 2000)]
+    assert w[0] <= w[1] <= w[2] <= w[3] == w[4]
