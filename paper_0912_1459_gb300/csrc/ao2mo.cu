@@ -780,11 +780,19 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
         SplitGuard(int v) { pipe_tr_ctas() = v; }
         ~SplitGuard() { pipe_tr_ctas() = 0; }
     } split_guard(tcx ? tc::tune_pipe_split() : 0);
+    // The tensor-core decomposition never reads L's rows once they are
+    // written (it works on its compact copy), so each batch's rows go to FP64
+    // right after their transform, on the transform's stream, instead of all
+    // rows at the end; the float-pair decomposition keeps reading them, so
+    // it converts at the end.
+    const bool convert_by_batch = cd_precision == CDS_PREC_OZAKI;
+    const int64_t npr = npair_of(nbf);
     int32_t next = 0;   // first vector not yet handed to the transform
     CdChunkHook hook = [&](int32_t rows, bool done) -> int {
         while (next < rows && (done || next + kAoBatch <= rows)) {
             const int32_t kb = std::min(kAoBatch, rows - next);
             int s2 = transform(nullptr, Lf, next, kb);
+            if (!s2 && convert_by_batch) s2 = pairs_to_fp64(L + (int64_t)next * npr, kb * npr, ps.tr);
             if (s2) return s2;
             next += kb;
         }
@@ -793,9 +801,14 @@ extern "C" int cds_cd_decompose_to_mo(int32_t nbf, const double* xyz, const doub
     int32_t M = 0;
     const int cd_st = cd_decompose_run(nbf, xyz, alpha, atom, delta, scheme, max_rank,
                                        cd_precision, L, piv, D, &M, delta_eff_out, lay.cd,
-                                       lay.cd_bytes, ps.cd, &hook, ps.tr);
+                                       lay.cd_bytes, ps.cd, &hook, ps.tr, true, !convert_by_batch);
     *M_out = M;
     const int32_t nv = nmo - nocc;
+    if (convert_by_batch && next < M) {   // rows no batch took (a stop before the last check)
+        if ((st = stream_wait(ps.tr, ps.cd))) return st;
+        if ((st = pairs_to_fp64(L + (int64_t)next * npr, (int64_t)(M - next) * npr, ps.tr)))
+            return st;
+    }
     if (M > 0 && (cd_st == CDS_OK || cd_st == CDS_ERR_RANK_CAP)) {
         // the last host check reports the stop, so every vector has been
         // handed over; should any remain, take them from the converted rows

@@ -1123,6 +1123,13 @@ __global__ void k_pairs_to_fp64(double* __restrict__ L, int64_t count) {
     L[i] = (double)v.x + (double)v.y;
 }
 
+int pairs_to_fp64(double* L, int64_t count, cudaStream_t stream) {
+    if (count <= 0) return CDS_OK;
+    k_pairs_to_fp64<<<(unsigned)((count + 255) / 256), 256, 0, stream>>>(L, count);
+    CDS_LAUNCH_CHECK();
+    return CDS_OK;
+}
+
 struct CdLayout {
     PairSoA pd;
     uint8_t* cand;
@@ -1301,7 +1308,7 @@ static GemmTiming g_gemm_timing;
 static int cd_run_tc(int64_t n, int32_t max_rank, double* L, int32_t* piv, double* D,
                      int32_t* M_out, double* delta_eff_out, const CdLayout& lay,
                      cudaStream_t stream, const CdChunkHook* on_chunk,
-                     cudaStream_t convert_after, bool chunk_graph) {
+                     cudaStream_t convert_after, bool chunk_graph, bool convert) {
     const int nsb = (int)((n + kScanChunk - 1) / kScanChunk);
     k_screen_count<<<nsb, kScanThreads, 0, stream>>>(D, n, lay.ctrl, lay.scan);
     CDS_LAUNCH_CHECK();
@@ -1438,7 +1445,7 @@ static int cd_run_tc(int64_t n, int32_t max_rank, double* L, int32_t* piv, doubl
     k_screen_finish<<<(unsigned)((fin + 255) / 256), 256, 0, stream>>>(lay.pivc, h.M, lay.live,
                                                                        piv, lay.Dc, nc, D);
     CDS_LAUNCH_CHECK();
-    if (h.M > 0) {
+    if (h.M > 0 && convert) {
         if (convert_after) {
             cudaEvent_t ev;
             CDS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
@@ -1462,12 +1469,14 @@ static int cd_run_tc(int64_t n, int32_t max_rank, double* L, int32_t* piv, doubl
 // every host check with the number of rows of L that are final and whether
 // the decomposition has stopped; before the float-pair rows are converted to
 // FP64 at the end, stream waits for convert_after (may be null), so work that
-// reads the float-pair rows can run on another stream meanwhile.
+// reads the float-pair rows can run on another stream meanwhile.  With
+// convert false the float-pair rows are left to the caller (pairs_to_fp64).
 int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const int32_t* atom,
                      double delta, int32_t scheme, int32_t max_rank, int32_t precision, double* L,
                      int32_t* piv, double* D, int32_t* M_out, double* delta_eff_out,
                      void* workspace, size_t workspace_bytes, cudaStream_t stream,
-                     const CdChunkHook* on_chunk, cudaStream_t convert_after, bool chunk_graph) {
+                     const CdChunkHook* on_chunk, cudaStream_t convert_after, bool chunk_graph,
+                     bool convert) {
     if (nbf <= 0 || !xyz || !alpha || !L || !piv || !D || !M_out || max_rank < 0)
         return CDS_ERR_ARG;
     if (precision != CDS_PREC_FP64 && precision != CDS_PREC_F32X2 && precision != CDS_PREC_OZAKI)
@@ -1496,7 +1505,7 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
     CDS_LAUNCH_CHECK();
     if (tcm)
         return cd_run_tc(n, max_rank, L, piv, D, M_out, delta_eff_out, lay, stream, on_chunk,
-                         convert_after, chunk_graph);
+                         convert_after, chunk_graph, convert);
     k_cd_select<<<ns, kCdThreads, 0, stream>>>(n, 0, max_rank, D, lay.cand, lay.blk_i, piv,
                                               lay.ctrl);
     CDS_LAUNCH_CHECK();
@@ -1531,7 +1540,7 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
     }
     *M_out = h.M;
     if (delta_eff_out) *delta_eff_out = h.delta_eff;
-    if (df && h.M > 0) {
+    if (df && h.M > 0 && convert) {
         if (convert_after) {
             cudaEvent_t ev;
             CDS_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));

@@ -137,5 +137,7 @@ int cd_decompose_run(int32_t nbf, const double* xyz, const double* alpha, const 
                      int32_t* piv, double* D, int32_t* M_out, double* delta_eff_out,
                      void* workspace, size_t workspace_bytes, cudaStream_t stream,
                      const CdChunkHook* on_chunk, cudaStream_t convert_after,
-                     bool chunk_graph = true);
+                     bool chunk_graph = true, bool convert = true);
+// Float pairs (hi, lo) of the first count elements of L back to FP64, in place.
+int pairs_to_fp64(double* L, int64_t count, cudaStream_t stream);
 }
