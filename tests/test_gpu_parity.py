@@ -386,3 +386,33 @@ def test_fused_decompose_to_mo_matches_separate_calls(name, delta, orbs, cdp):
     assert (Lov1 - Lov2).abs().max().item() <= 1e-8 * scale
     if Lp1.numel():
         assert (Lp1 - Lp2).abs().max().item() <= 1e-8 * Lp1.abs().max().item()
+
+
+def test_fused_rank_cap_rows_are_fp64():
+    """A pipelined tensor-core call stopped by its rank cap (CDS_ERR_RANK_CAP)
+    at 40 vectors: the last, partial batch of rows is transformed and
+    converted to FP64 at the stop, so L equals the standalone decomposition's
+    (which converts all rows at its end) and the factors match the separate
+    transform's."""
+    m = O.molecule("c1")
+    xyz, a, at = basis_dev(m)
+    orb = dev(np.asarray(m.orbitals, dtype=np.int32))
+    cap, npr = 40, G.npair(m.nbf)
+    L1 = torch.empty((cap, npr), dtype=torch.float64, device=DEV)
+    with pytest.raises(G.CdsError) as ei:
+        G.cds_cd_decompose(xyz, a, at, 1e-6, "full", max_rank=cap, L_out=L1, precision="ozaki")
+    assert ei.value.status == 4
+    L2 = torch.empty((cap, npr), dtype=torch.float64, device=DEV)
+    nv = m.nbf - m.nocc
+    Lov2 = torch.empty(m.nocc * nv * cap, dtype=torch.float64, device=DEV)
+    Lp2 = torch.empty(len(m.orbitals) * m.nbf * cap, dtype=torch.float64, device=DEV)
+    with pytest.raises(G.CdsError) as ei:
+        G.cds_cd_decompose_to_mo(xyz, a, at, 1e-6, dev(m.C), m.nocc, orb, max_rank=cap,
+                                 L_out=L2, Lov_out=Lov2, Lp_out=Lp2, transform="ozaki",
+                                 cd_precision="ozaki")
+    assert ei.value.status == 4
+    assert torch.equal(L1, L2)
+    Lov1, Lp1 = G.cds_cd_to_mo(L1, dev(m.C), m.nocc, orb, precision="ozaki")
+    Lov2 = Lov2[:m.nocc * nv * cap].view(m.nocc, nv, cap)
+    scale = Lov1.abs().max().item()
+    assert (Lov1 - Lov2).abs().max().item() <= 1e-8 * scale
